@@ -1,0 +1,219 @@
+"""The oracle's FR right-hand side, RK4 stepper and reductions.
+
+Public state layout (shared with the C ABI): one flat float64 array, tets
+first then prisms, each block [elem][var][upt].
+
+RHS (reference-space FR with the DG correction; Sec. 2.1 casts every
+operator application as C <- c1 A B + c2 C, Eq. 1):
+  1. u_f = M0 u                                   (Table 2's M0)
+  2. NS: common solution C at every flux point, Delta = C - u_f
+  3. NS: corrected reference gradient  g_d = D_d u + M3 (n^_d Delta),
+     physical gradient  grad_m u = (1/J) sum_d S[d][m] g_d
+  4. NS: gradient at flux points  M0 grad_m u
+  5. transformed flux at solution points  F~_d = sum_m S[d][m] F_m(u, grad u)
+  6. common transformed normal flux at flux points  F~c = F_c.n |S^T n^|
+  7. R = -(1/J) [ sum_d D_d F~_d + M3 (F~c - sum_d n^_d M0 F~_d) ]
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import physics
+from .mesh import Mesh
+
+NVARS = 5
+
+
+class Solver:
+    def __init__(self, mesh, p, gamma=1.4, mu=0.0, prandtl=0.72, viscous=False,
+                 ldg_beta=0.5, ldg_tau=0.1, rho_inf=1.0, vel_inf=(1.0, 0.0, 0.0),
+                 p_inf=None, t_wall=None):
+        self.m = Mesh(mesh, p)
+        self.p = p
+        self.gamma = gamma
+        self.mu = mu
+        self.prandtl = prandtl
+        self.viscous = viscous
+        self.beta = ldg_beta
+        self.tau = ldg_tau
+        self.rho_inf = rho_inf
+        self.vel_inf = np.asarray(vel_inf, dtype=np.float64)
+        self.p_inf = (1.0 / gamma if p_inf is None else p_inf)
+        self.t_wall = self.p_inf / rho_inf if t_wall is None else t_wall
+        m = self.m
+        self.types = m.types
+        self.nu = {t: m.ops[t].nu for t in self.types}
+        self.sizes = {t: m.ne[t] * NVARS * self.nu[t] for t in self.types}
+        self.ndof = sum(self.sizes.values())
+        self.n_pairs = m.pa.size
+        self.na = m.gn[m.pa]
+        self.sign = physics.ldg_sign(self.na)
+
+    # -- layout helpers ------------------------------------------------------
+    def split(self, flat):
+        out, off = {}, 0
+        for t in self.types:
+            n = self.sizes[t]
+            out[t] = flat[off:off + n].reshape(self.m.ne[t], NVARS, self.nu[t])
+            off += n
+        return out
+
+    def join(self, d):
+        return np.concatenate([d[t].reshape(-1) for t in self.types])
+
+    def upts_xyz(self):
+        """Physical solution-point coordinates in the public layout with the
+        variable axis replaced by x, y, z."""
+        return np.concatenate([self.m.upts_x[t].transpose(0, 2, 1).reshape(-1)
+                               for t in self.types])
+
+    def upts_xyz_points(self):
+        """(n_points, 3) physical coordinates, point order of the public layout."""
+        return np.concatenate([self.m.upts_x[t].reshape(-1, 3) for t in self.types])
+
+    def state_from_points(self, q):
+        """(n_points, 5) values in upts_xyz_points order -> public layout."""
+        out, off = [], 0
+        for t in self.types:
+            ne, nu = self.m.ne[t], self.nu[t]
+            blk = q[off:off + ne * nu].reshape(ne, nu, NVARS).transpose(0, 2, 1)
+            out.append(blk.reshape(-1))
+            off += ne * nu
+        return np.concatenate(out)
+
+    # -- boundary states -------------------------------------------------------
+    def _boundary(self, ub, nb):
+        """(inviscid ghost, common solution) at boundary flux points."""
+        ghost = np.empty_like(ub)
+        cb = np.empty_like(ub)
+        tags = self.m.btag
+        wall = tags == 1
+        far = tags == 2
+        if np.any(~(wall | far)):
+            raise ValueError("unknown boundary tag")
+        if np.any(wall):
+            g, c = physics.wall_states(ub[wall], self.gamma, self.t_wall)
+            ghost[wall], cb[wall] = g, c
+        if np.any(far):
+            g = physics.farfield_state(ub[far], nb[far], self.gamma, self.rho_inf,
+                                       self.vel_inf, self.p_inf)
+            ghost[far], cb[far] = g, g
+        return ghost, cb
+
+    # -- the right-hand side ---------------------------------------------------
+    def rhs(self, u_flat):
+        m, g = self.m, self.gamma
+        u = self.split(np.asarray(u_flat, dtype=np.float64))
+        ops = m.ops
+        # 1. interpolate to flux points
+        uf = {t: u[t] @ ops[t].M0.T for t in self.types}
+        UF = m.to_global(uf)
+        ua, ub = UF[m.pa], UF[m.pb]
+        na = self.na
+        ubnd = UF[m.bg]
+        nb = m.gn[m.bg]
+        ghost, cb = self._boundary(ubnd, nb)
+
+        grad = {}
+        if self.viscous:
+            # 2. common solution and jumps
+            C = physics.ldg_common_solution(ua, ub, self.sign, self.beta)
+            DL = np.empty_like(UF)
+            DL[m.pa] = C - ua
+            DL[m.pb] = C - ub
+            DL[m.bg] = cb - ubnd
+            delta = m.from_global(DL)
+            # 3. corrected gradient, physical
+            for t in self.types:
+                op = ops[t]
+                gh = np.stack([u[t] @ op.D[d].T + (op.fnorm[:, d] * delta[t]) @ op.M3.T
+                               for d in range(3)], axis=-1)           # (ne, V, nu, d)
+                grad[t] = (np.einsum("ejdm,evjd->evjm", m.S[t], gh)
+                           / m.J[t][:, None, :, None])                # (ne, V, nu, m)
+            # 4. gradients at flux points
+            gradf = {t: np.stack([grad[t][..., k] @ ops[t].M0.T for k in range(3)],
+                                 axis=-1) for t in self.types}        # (ne, V, nf, m)
+            GF = np.concatenate([gradf[t].transpose(0, 2, 1, 3).reshape(-1, NVARS, 3)
+                                 for t in self.types])
+
+        # 5. transformed flux at solution points
+        R = {}
+        Ft = {}
+        for t in self.types:
+            up = u[t].transpose(0, 2, 1)                                  # (ne, nu, V)
+            F = physics.inviscid_flux(up, g)
+            if self.viscous:
+                F = F - physics.viscous_flux(up, grad[t].transpose(0, 2, 1, 3), g,
+                                             self.mu, self.prandtl)
+            Ft[t] = np.einsum("ejdm,ejvm->evjd", m.S[t], F)              # (ne, V, nu, d)
+
+        # 6. common normal flux
+        Fc = physics.rusanov(ua, ub, na, g)
+        Fcb = physics.rusanov(ubnd, ghost, nb, g)
+        if self.viscous:
+            fva = physics.viscous_flux(ua, GF[m.pa], g, self.mu, self.prandtl)
+            fvb = physics.viscous_flux(ub, GF[m.pb], g, self.mu, self.prandtl)
+            Fc = (Fc - physics.ldg_viscous_normal(fva, fvb, na, self.sign, self.beta)
+                  + self.tau * (ua - ub))
+            fvbnd = physics.viscous_flux(cb, GF[m.bg], g, self.mu, self.prandtl)
+            Fcb = (Fcb - np.einsum("...vm,...m->...v", fvbnd, nb)
+                   + self.tau * (ubnd - cb))
+        FC = np.empty_like(UF)
+        FC[m.pa] = Fc * m.gmag[m.pa][:, None]
+        FC[m.pb] = -Fc * m.gmag[m.pb][:, None]
+        FC[m.bg] = Fcb * m.gmag[m.bg][:, None]
+        fc = m.from_global(FC)
+
+        # 7. divergence plus correction, scaled by -1/J
+        for t in self.types:
+            op = ops[t]
+            div = sum(Ft[t][..., d] @ op.D[d].T for d in range(3))
+            fn_int = sum(op.fnorm[:, d] * (Ft[t][..., d] @ op.M0.T) for d in range(3))
+            R[t] = -(div + (fc[t] - fn_int) @ op.M3.T) / m.J[t][:, None, :]
+        return self.join(R)
+
+    # -- time stepping and reductions ----------------------------------------
+    def rk4_step(self, u, dt):
+        k1 = self.rhs(u)
+        k2 = self.rhs(u + 0.5 * dt * k1)
+        k3 = self.rhs(u + 0.5 * dt * k2)
+        k4 = self.rhs(u + dt * k3)
+        return u + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+
+    def integrals(self, u_flat):
+        """sum_e sum_j w_j J_j u_j per conserved variable."""
+        u = self.split(np.asarray(u_flat, dtype=np.float64))
+        tot = np.zeros(NVARS)
+        for t in self.types:
+            wJ = self.m.ops[t].w[None, :] * self.m.J[t]
+            tot += np.einsum("ej,evj->v", wJ, u[t])
+        return tot
+
+    def kinetic_energy(self, u_flat):
+        u = self.split(np.asarray(u_flat, dtype=np.float64))
+        ke = 0.0
+        for t in self.types:
+            wJ = self.m.ops[t].w[None, :] * self.m.J[t]
+            k = 0.5 * np.sum(u[t][:, 1:4, :] ** 2, axis=1) / u[t][:, 0, :]
+            ke += float(np.sum(wJ * k))
+        return ke
+
+    def volume(self):
+        return sum(float(np.sum(self.m.ops[t].w[None, :] * self.m.J[t]))
+                   for t in self.types)
+
+    def dt_cfl(self, u_flat, cfl):
+        """cfl * min_e r_e / max |v| + c, r_e = 3 V_e / A_e."""
+        u = self.split(np.asarray(u_flat, dtype=np.float64))
+        rmin = np.inf
+        smax = 0.0
+        for t in self.types:
+            op = self.m.ops[t]
+            V = np.sum(op.w[None, :] * self.m.J[t], axis=1)
+            A = np.sum(op.fw[None, :] * self.m.fmag[t], axis=1)
+            rmin = min(rmin, float(np.min(3.0 * V / A)))
+            up = u[t].transpose(0, 2, 1)
+            _, v, _ = physics.primitives(up, self.gamma)
+            s = np.linalg.norm(v, axis=-1) + physics.sound_speed(up, self.gamma)
+            smax = max(smax, float(np.max(s)))
+        return cfl * rmin / smax

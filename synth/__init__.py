@@ -1,0 +1,18 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and by the oracle.
+
+This package generates meshes (node coordinates, element connectivity,
+boundary-face tags, periodic translations) and closed-form initial
+conditions evaluated at caller-supplied coordinates.  It holds none of the
+flux-reconstruction arithmetic: no solution/flux points, no operators, no
+geometry factors, no face matching.  Both implementations compute those on
+their own from what this package returns.
+"""
+from .meshgen import (  # noqa: F401
+    BC_WALL, BC_FARFIELD, ETYPE_TET, ETYPE_PRI, TET_FACES, PRI_FACES,
+    layered_box, vortex_box, boundary_layer_box, tgv_box, batch_problem_params,
+    batch_problem_mesh, mesh_counts,
+)
+from .ics import (  # noqa: F401
+    isentropic_vortex, taylor_green, perturbed_freestream, uniform_state,
+    random_smooth_state,
+)

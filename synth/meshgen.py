@@ -1,0 +1,273 @@
+"""Structured-then-split mixed prism/tetrahedron meshes with seeded node jitter.
+
+Every mesh is a logically structured box of hexahedral cells.  The cells of
+the first ``n_prism_layers`` layers along ``layer_axis`` are each split into
+two triangular prisms extruded along that axis; the remaining cells are each
+split into six Kuhn (Freudenthal) tetrahedra along the cell's min-to-max
+diagonal.  The prism base quads are cut along the same min-to-max diagonal,
+so every face is conforming, including the prism/tet transition and all
+periodic wraps.  This stands in for the paper's mixed cylinder mesh
+(prisms in the near-wall layer, tets in the far field; Sec. 3.3), which is
+not available.
+
+Vertex order conventions (the only conventions the mesh format carries):
+
+* tet: vertices 0..3 map to reference vertices (-1,-1,-1), (1,-1,-1),
+  (-1,1,-1), (-1,-1,1); local faces are the vertex triples in ``TET_FACES``.
+* prism: vertices 0..2 form the bottom triangle (reference zeta=-1),
+  vertices 3..5 the top triangle (zeta=+1), vertex a+3 above vertex a;
+  local faces are the vertex lists in ``PRI_FACES`` (two triangles, then
+  three quads).
+
+Both element kinds are emitted with positive orientation.
+
+Returned meshes are dicts with
+``xyz`` (n_nodes, 3) float64, ``tet`` (n_tet, 4) int64, ``pri`` (n_pri, 6)
+int64, ``bface`` (n_bface, 4) int64 rows (etype, elem, local face, bc tag)
+and ``period`` (3,) float64 (0 = axis not periodic).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+ETYPE_TET = 0
+ETYPE_PRI = 1
+BC_WALL = 1        # no-slip isothermal wall
+BC_FARFIELD = 2    # Riemann-invariant far field
+
+TET_FACES = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
+PRI_FACES = ((0, 1, 2), (3, 4, 5), (0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5))
+
+# (a0, a1, a2) axis orders that are even permutations of (x, y, z), keyed by
+# the layer axis a2; a base triangle counter-clockwise in (a0, a1) extruded
+# along +a2 is then positively oriented.
+_AXES = {2: (0, 1, 2), 1: (2, 0, 1), 0: (1, 2, 0)}
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def layered_box(coords, layer_axis, n_prism_layers, periodic, bcs=None,
+                jitter=0.0, seed=0):
+    """Build a mixed prism/tet box mesh.
+
+    coords: three increasing 1-D arrays, the node coordinates along x, y, z.
+    layer_axis: axis (0, 1, 2) of the prism extrusion; layers are counted
+        from the low end of this axis.
+    n_prism_layers: number of cell layers (from the low end) split into prisms.
+    periodic: three bools.  A periodic axis has period coords[-1]-coords[0]
+        and its last node plane is the translate of its first.
+    bcs: dict {(axis, side): tag} for each non-periodic side (side 0 = low,
+        1 = high).  Missing sides default to BC_FARFIELD.
+    jitter: node jitter as a fraction of the local cell size per component;
+        nodes on non-periodic boundaries are not moved, and periodic images
+        move identically.
+    seed: PCG64 seed of the jitter.
+    """
+    bcs = dict(bcs or {})
+    axes = _AXES[layer_axis]
+    ax_coords = [np.asarray(coords[a], dtype=np.float64) for a in axes]
+    ncell = [len(c) - 1 for c in ax_coords]
+    nnode = [n + 1 for n in ncell]
+    per = [bool(periodic[a]) for a in axes]
+
+    # node grid in (a0, a1, a2) order, id = (i2 * nn1 + i1) * nn0 + i0
+    g0, g1, g2 = np.meshgrid(*ax_coords, indexing="ij")
+    grid = np.stack([g0, g1, g2], axis=-1)          # (nn0, nn1, nn2, 3) in axis order
+
+    if jitter > 0.0:
+        rng = _rng(seed)
+        amp = []
+        for k in range(3):
+            c = ax_coords[k]
+            h = np.diff(c)
+            left = np.concatenate([[h[-1] if per[k] else h[0]], h])
+            right = np.concatenate([h, [h[0] if per[k] else h[-1]]])
+            amp.append(jitter * np.minimum(left, right))
+        jit = rng.uniform(-1.0, 1.0, size=grid.shape)
+        for k in range(3):
+            shape = [1, 1, 1]
+            shape[k] = nnode[k]
+            jit[..., k] *= amp[k].reshape(shape)
+        for k in range(3):
+            sl_last = [slice(None)] * 3
+            sl_first = [slice(None)] * 3
+            sl_last[k] = -1
+            sl_first[k] = 0
+            if per[k]:
+                jit[tuple(sl_last)] = jit[tuple(sl_first)]
+        for k in range(3):
+            if not per[k]:
+                for idx in (0, -1):
+                    sl = [slice(None)] * 3
+                    sl[k] = idx
+                    jit[tuple(sl)] = 0.0
+        grid = grid + jit
+
+    # back to physical (x, y, z) component order
+    xyz_axis = grid.reshape(-1, 3, order="F")       # id order: i0 fastest
+    xyz = np.empty_like(xyz_axis)
+    for k, a in enumerate(axes):
+        xyz[:, a] = xyz_axis[:, k]
+
+    def nid(i0, i1, i2):
+        return (i2 * nnode[1] + i1) * nnode[0] + i0
+
+    c0, c1, c2 = np.meshgrid(np.arange(ncell[0]), np.arange(ncell[1]),
+                             np.arange(ncell[2]), indexing="ij")
+    c0 = c0.ravel(order="F")
+    c1 = c1.ravel(order="F")
+    c2 = c2.ravel(order="F")
+    is_pri_cell = c2 < n_prism_layers
+
+    pri_list, pri_gidx = [], []
+    tet_list, tet_gidx = [], []
+    # prisms: base triangles cut along the (0,0)-(1,1) diagonal
+    tris = (((0, 0), (1, 0), (1, 1)), ((0, 0), (1, 1), (0, 1)))
+    pc0, pc1, pc2 = c0[is_pri_cell], c1[is_pri_cell], c2[is_pri_cell]
+    for tri in tris:
+        verts, gidx = [], []
+        for d2 in (0, 1):
+            for (d0, d1) in tri:
+                verts.append(nid(pc0 + d0, pc1 + d1, pc2 + d2))
+                gidx.append(np.stack([pc0 + d0, pc1 + d1, pc2 + d2], axis=-1))
+        pri_list.append(np.stack(verts, axis=-1))
+        pri_gidx.append(np.stack(gidx, axis=1))
+    # Kuhn tets: monotone lattice paths from (0,0,0) to (1,1,1)
+    tc0, tc1, tc2 = c0[~is_pri_cell], c1[~is_pri_cell], c2[~is_pri_cell]
+    for perm in itertools.permutations(range(3)):
+        path = [np.zeros(3, dtype=np.int64)]
+        for k in perm:
+            nxt = path[-1].copy()
+            nxt[k] += 1
+            path.append(nxt)
+        e1, e2, e3 = path[1] - path[0], path[2] - path[0], path[3] - path[0]
+        if np.linalg.det(np.stack([e1, e2, e3]).astype(float)) < 0.0:
+            path = [path[0], path[2], path[1], path[3]]
+        verts, gidx = [], []
+        for d in path:
+            verts.append(nid(tc0 + d[0], tc1 + d[1], tc2 + d[2]))
+            gidx.append(np.stack([tc0 + d[0], tc1 + d[1], tc2 + d[2]], axis=-1))
+        tet_list.append(np.stack(verts, axis=-1))
+        tet_gidx.append(np.stack(gidx, axis=1))
+
+    # interleave the pieces of each cell so that element order follows cells
+    pri = (np.stack(pri_list, axis=1).reshape(-1, 6) if pri_list
+           else np.zeros((0, 6), np.int64))
+    pri_g = (np.stack(pri_gidx, axis=1).reshape(-1, 6, 3) if pri_gidx
+             else np.zeros((0, 6, 3), np.int64))
+    tet = (np.stack(tet_list, axis=1).reshape(-1, 4) if tet_list
+           else np.zeros((0, 4), np.int64))
+    tet_g = (np.stack(tet_gidx, axis=1).reshape(-1, 4, 3) if tet_gidx
+             else np.zeros((0, 4, 3), np.int64))
+
+    # boundary faces on non-periodic sides
+    bface = []
+    for etype, conn_g, faces in ((ETYPE_TET, tet_g, TET_FACES),
+                                 (ETYPE_PRI, pri_g, PRI_FACES)):
+        if len(conn_g) == 0:
+            continue
+        for lf, fv in enumerate(faces):
+            fg = conn_g[:, list(fv), :]          # (ne, nfv, 3) grid indices
+            for k in range(3):
+                if per[k]:
+                    continue
+                for side, target in ((0, 0), (1, ncell[k])):
+                    on = np.all(fg[:, :, k] == target, axis=1)
+                    if np.any(on):
+                        tag = bcs.get((axes[k], side), BC_FARFIELD)
+                        el = np.nonzero(on)[0]
+                        bface.append(np.stack([np.full_like(el, etype), el,
+                                               np.full_like(el, lf),
+                                               np.full_like(el, tag)], axis=-1))
+    bface = (np.concatenate(bface).astype(np.int64) if bface
+             else np.zeros((0, 4), np.int64))
+
+    period = np.zeros(3)
+    for k, a in enumerate(axes):
+        if per[k]:
+            period[a] = ax_coords[k][-1] - ax_coords[k][0]
+    return {"xyz": np.ascontiguousarray(xyz), "tet": tet.astype(np.int64),
+            "pri": pri.astype(np.int64), "bface": bface, "period": period}
+
+
+def vortex_box(n=4, jitter=0.05, seed=0, n_prism_layers=None, lo=-5.0, hi=5.0):
+    """Periodic cube [lo,hi]^3 of n^3 cells: lower half prisms, upper half
+    Kuhn tets (the isentropic-vortex workload; 4^3 cells, seed 0 gives 64
+    prisms and 192 tets)."""
+    c = np.linspace(lo, hi, n + 1)
+    npl = n // 2 if n_prism_layers is None else n_prism_layers
+    return layered_box((c, c, c), 2, npl, (True, True, True), jitter=jitter,
+                       seed=seed)
+
+
+def boundary_layer_box(nx=75, nz=12, n_prism_layers=32, n_tet_layers=22,
+                       h0=0.03208, ratio=1.1, lx=20.0, ly=20.0, lz=math.pi,
+                       jitter=0.05, seed=1):
+    """Box [0,lx]x[0,ly]x[0,lz]: geometrically stretched prism layers on a
+    no-slip wall at y=0 under uniform Kuhn-tet layers up to y=ly; far field
+    at x=0, x=lx, y=ly; periodic in z.  The defaults give 57,600 prisms and
+    118,800 tets."""
+    yb = h0 * (ratio ** np.arange(n_prism_layers + 1) - 1.0) / (ratio - 1.0)
+    yt = np.linspace(yb[-1], ly, n_tet_layers + 1)[1:]
+    y = np.concatenate([yb, yt])
+    x = np.linspace(0.0, lx, nx + 1)
+    z = np.linspace(0.0, lz, nz + 1)
+    bcs = {(1, 0): BC_WALL, (1, 1): BC_FARFIELD, (0, 0): BC_FARFIELD,
+           (0, 1): BC_FARFIELD}
+    return layered_box((x, y, z), 1, n_prism_layers, (False, False, True),
+                       bcs=bcs, jitter=jitter, seed=seed)
+
+
+def tgv_box(n=24, jitter=0.0, seed=0):
+    """Periodic cube [0,2pi]^3 of n^3 cells, lower half prisms, upper half tets."""
+    c = np.linspace(0.0, 2.0 * math.pi, n + 1)
+    return layered_box((c, c, c), 2, n // 2, (True, True, True), jitter=jitter,
+                       seed=seed)
+
+
+def mesh_counts(mesh):
+    return len(mesh["tet"]), len(mesh["pri"])
+
+
+def batch_problem_params(i, seed=3, n_lo=1000, n_hi=80000):
+    """Draw (n_elements, prism:tet ratio, order) of batched problem i:
+    n log-uniform in [n_lo, n_hi], ratio = n_pri/n_tet uniform in [0, 1],
+    order uniform in {1, 2, 3, 4}."""
+    rng = _rng([seed, i])
+    n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+    r = float(rng.uniform(0.0, 1.0))
+    p = int(rng.integers(1, 5))
+    return n, r, p
+
+
+def batch_problem_mesh(i, seed=3):
+    """A periodic vortex box m x m x nz whose element count and prism:tet
+    ratio approximate batch_problem_params(i): a layer of m^2 cells gives
+    2 m^2 prisms or 6 m^2 tets, nz = kp + kt layers with kp/kt chosen so that
+    2 kp / (6 kt) ~ r."""
+    n, r, p = batch_problem_params(i, seed)
+    # elements = m^2 (2 kp + 6 kt); pick kt, kp from the ratio, then m
+    best = None
+    for nz in range(2, 41):
+        for kp in range(0, nz):
+            kt = nz - kp
+            rr = 2.0 * kp / (6.0 * kt)
+            per_layer = 2 * kp + 6 * kt
+            m = max(2, int(round(math.sqrt(n / per_layer))))
+            ne = m * m * per_layer
+            score = abs(math.log(ne / n)) + 2.0 * abs(rr - r)
+            if best is None or score < best[0]:
+                best = (score, m, kp, kt)
+    _, m, kp, kt = best
+    nz = kp + kt
+    L = 10.0
+    cxy = np.linspace(-L / 2, L / 2, m + 1)
+    cz = np.linspace(-L / 2, L / 2, nz + 1)
+    mesh = layered_box((cxy, cxy, cz), 2, kp, (True, True, True), jitter=0.05,
+                       seed=1000 + i)
+    return mesh, p

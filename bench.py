@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Throughput of the FR right-hand side on the boundary-layer workload.
+
+Workload: compressible Navier-Stokes, p = 4, FP64, on a box
+[0,20] x [0,20] x [0,pi] with 32 stretched prism layers (57,600 prisms) on
+a no-slip wall under Kuhn tets (118,800 tets), Re = 3900, Ma = 0.2,
+uniform inflow plus a 1% seeded velocity perturbation: 42,390,000 DOF.
+One step = one classic RK4 step = 4 RHS evaluations (the whole hot path:
+interpolation, common solution, corrected gradients, fluxes, common
+fluxes, divergence + correction, register update).
+
+Metric: GDOF/s = DOF x RHS evaluations / second (whole job: with N ranks
+each rank advances its own copy of the workload; weak scaling).
+
+--impl reference times the CPU oracle (the plain FP64 numpy solver used as
+the correctness reference) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ORDER = 4
+GAMMA = 1.4
+MACH = 0.2
+REYNOLDS = 3900.0
+METRIC = "FR RHS GDOF/s, mixed prism/tet p=4, FP64 vs FP32/split/learned; % roofline"
+UNIT = "GDOF/s"
+WORKLOAD = "boundary-layer box NS p=4 FP64: 57,600 prisms + 118,800 tets, Re=3900, Ma=0.2, RK4"
+# a bounded sample of the same workload for the CPU oracle: the same
+# generator with 15 instead of 75 cells along x (1/5 of the elements)
+CPU_SAMPLE_NX = 15
+
+
+def flow_params():
+    p_inf = 1.0 / (GAMMA * MACH ** 2)
+    return dict(viscous=True, mu=1.0 / REYNOLDS, gamma=GAMMA, prandtl=0.72, ldg_beta=0.5,
+                ldg_tau=0.1, rho_inf=1.0, vel_inf=(1.0, 0.0, 0.0), p_inf=p_inf, t_wall=p_inf)
+
+
+def points_to_public(q, counts):
+    """(n_points, 5) values in public point order -> public layout."""
+    out, off = [], 0
+    for ne, nu in counts:
+        if ne == 0:
+            continue
+        blk = q[off:off + ne * nu].reshape(ne, nu, 5).transpose(0, 2, 1)
+        out.append(blk.reshape(-1))
+        off += ne * nu
+    return np.concatenate(out)
+
+
+def min_edge(mesh):
+    xyz = mesh["xyz"]
+    h = np.inf
+    for key, pairs in (("tet", [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]),
+                       ("pri", [(0, 1), (1, 2), (2, 0), (0, 3), (1, 4), (2, 5)])):
+        c = mesh[key]
+        if len(c) == 0:
+            continue
+        for a, b in pairs:
+            h = min(h, float(np.min(np.linalg.norm(xyz[c[:, a]] - xyz[c[:, b]], axis=1))))
+    return h
+
+
+def time_step_size(mesh, order):
+    """dt = 0.1 h_min / ((|v| + c) (p+1)^2), a conservative explicit limit."""
+    c_inf = 1.0 / MACH
+    return 0.1 * min_edge(mesh) / ((1.0 + c_inf) * (order + 1) ** 2)
+
+
+def gemm_flops(ctx, kclass):
+    """Algorithmic FP64 flops of one launch class, summed over both element
+    types, for one RHS evaluation: 2 x (operator rows) x (operator columns)
+    x (5 variables x elements) per operator application."""
+    i = ctx.info
+    tot = 0.0
+    for ne, nu, nf in ((i["n_tet"], i["nu_tet"], i["nf_tet"]), (i["n_pri"], i["nu_pri"], i["nf_pri"])):
+        if ne == 0:
+            continue
+        cols = 5.0 * ne
+        if kclass == "M0":
+            tot += 2.0 * nf * nu * cols
+        elif kclass == "grad":
+            tot += 2.0 * 3 * nu * (nu + nf) * cols
+        elif kclass == "M0_grad":
+            tot += 2.0 * nf * nu * 3 * cols
+        elif kclass == "div":
+            tot += 2.0 * nu * (3 * nu + nf) * cols
+    return tot
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (runs in a child process with one BLAS thread)
+# ---------------------------------------------------------------------------
+def cpu_oracle_child(nrhs):
+    import synth
+    from oracle.solver import Solver
+    mesh = synth.boundary_layer_box(nx=CPU_SAMPLE_NX)
+    prm = flow_params()
+    sol = Solver(mesh, ORDER, gamma=prm["gamma"], mu=prm["mu"], prandtl=prm["prandtl"],
+                 viscous=True, ldg_beta=prm["ldg_beta"], ldg_tau=prm["ldg_tau"],
+                 rho_inf=prm["rho_inf"], vel_inf=prm["vel_inf"], p_inf=prm["p_inf"],
+                 t_wall=prm["t_wall"])
+    u = sol.state_from_points(synth.perturbed_freestream(sol.upts_xyz_points(), seed=2))
+    times = []
+    for _ in range(nrhs):
+        t0 = time.perf_counter()
+        r = sol.rhs(u)
+        times.append(time.perf_counter() - t0)
+    assert np.all(np.isfinite(r))
+    nt, npri = len(mesh["tet"]), len(mesh["pri"])
+    print(json.dumps({"ndof": sol.ndof, "times": times, "n_tet": nt, "n_pri": npri}))
+
+
+def run_cpu_oracle(nrhs):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle-child", str(nrhs)],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(f"cpu oracle failed: {r.stderr[-2000:]}")
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return res
+
+
+def cpu_baseline_entry(nrhs=1):
+    res = run_cpu_oracle(nrhs)
+    t = statistics.median(res["times"])
+    return {"value": res["ndof"] / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one NS p=4 RHS of the same generator at nx={CPU_SAMPLE_NX} "
+                       f"({res['n_pri']} prisms + {res['n_tet']} tets, {res['ndof']} DOF), "
+                       f"median of {nrhs}, setup excluded, 1 BLAS thread")}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-oracle-child", type=int, default=0)
+    args = ap.parse_args()
+
+    if args.cpu_oracle_child:
+        cpu_oracle_child(args.cpu_oracle_child)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        nrhs = args.warmup + args.steps
+        res = run_cpu_oracle(nrhs)
+        times = res["times"][args.warmup:] or res["times"]
+        t = sum(times) / len(times)
+        val = res["ndof"] / t / 1e9
+        cb = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": (f"one NS p=4 RHS per step on the nx={CPU_SAMPLE_NX} sample "
+                         f"({res['ndof']} DOF), 1 BLAS thread")}
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": WORKLOAD + f" (oracle sample nx={CPU_SAMPLE_NX})"},
+                          "cpu_baseline": cb,
+                          "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    # CPU baseline first (child process, before any CUDA work in this one)
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu_base = cpu_baseline_entry(1)
+        except Exception as e:  # reported, not fatal
+            cpu_base = {"error": str(e)[:300]}
+
+    import torch
+    import synth
+    from paper_1409_0405_gb300 import fr
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    mesh = synth.boundary_layer_box()
+    ctx = fr.Context(mesh, ORDER, **flow_params())
+    counts = [(ctx.info["n_tet"], ctx.info["nu_tet"]), (ctx.info["n_pri"], ctx.info["nu_pri"])]
+    u0 = points_to_public(synth.perturbed_freestream(ctx.upts_points(), seed=2), counts)
+    dt = time_step_size(mesh, ORDER)
+    ndof = ctx.ndof
+
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    ctx.set_state(u0, sp)
+    for _ in range(max(args.warmup, 0)):
+        ctx.step(dt, 1, sp)
+    torch.cuda.synchronize()
+
+    # --- timed region: K RK4 steps, inputs resident in HBM (all > L2) ---
+    gpu_uuid = torch.cuda.get_device_properties(local).uuid
+    sampler = ClockSampler(f"GPU-{gpu_uuid}")
+    ctx.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with sampler:
+        time.sleep(0.3)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.step(dt, 1, sp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    classes, launches = ctx.profile_read()
+    ctx.profile(False)
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * ndof * 4.0 / (ms_step * 1e-3) / 1e9
+    state_ok = ctx.reduce(stream=sp, check=False)[6] == 0.0
+
+    # --- e2e through the C ABI with host buffers ---
+    pin_in = torch.from_numpy(u0).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    hin, hout = pin_in.numpy(), pin_out.numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_state(hin, sp)
+        ctx.step(dt, 1, sp)
+        ctx.get_state(hout, sp)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * ndof * 4.0 / e2e_s / 1e9
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # --- roofline of the dominant kernel class ---
+    dom = max(classes, key=lambda k: classes[k][0])
+    dom_ms, dom_n = classes[dom]
+    peaks = measured_peaks()
+    fp64_peak_derived = 152 * 2 * 2 * 2.07  # GFLOP/s: SMs x FMA/clk x 2 flop x GHz
+    try:
+        fp64_peak_meas = fr.peak_fp64(sp)
+    except Exception:
+        fp64_peak_meas = None
+    if dom in ("M0", "grad", "M0_grad", "div"):
+        flops = gemm_flops(ctx, dom) * 4 * args.steps  # per RHS x 4 RHS per step
+        achieved = flops / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": fp64_peak_derived / 1e3,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak_derived, "traffic": None,
+                "kernel": f"k_gemm ({dom})", "launches": dom_n,
+                "avg_launch_ms": dom_ms / max(dom_n, 1),
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "peak_measured_fma_probe": (fp64_peak_meas / 1e3) if fp64_peak_meas else None}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": None, "kernel": dom}
+    all_gemm = sum(gemm_flops(ctx, k) for k in ("M0", "grad", "M0_grad", "div")) * 4 * args.steps
+    clocks = sampler.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "ndof": ndof, "rhs_per_step": 4, "dt": dt,
+                   "l2": "inputs > L2 (state 339 MB per register, scratch > 4 GB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "state_finite_after_timed_steps": bool(state_ok)},
+        "roofline": roof,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in classes.items()},
+        "gemm_fp64_tflops": all_gemm / (sum(classes[k][0] for k in ("M0", "grad", "M0_grad", "div")) * 1e-3) / 1e12,
+        "cpu_baseline": cpu_base,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(ndof * 8),
+                "d2h_bytes_per_step": int(ndof * 8), "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

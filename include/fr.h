@@ -1,0 +1,208 @@
+/*
+ * fr.h - C ABI of the GB300 flux-reconstruction (FR) right-hand-side engine.
+ *
+ * The engine evaluates the FR semi-discretisation of the compressible Euler
+ * and Navier-Stokes equations (constant viscosity, Sec. 3.4) on mixed
+ * prism/tetrahedral meshes (Sec. 3.3) and advances it with classic RK4
+ * (Table 1 lists Euler, RK4 and RK45 steppers).  Every operator application
+ * is a constant operator matrix times a row-major state matrix,
+ * C <- c1 A B + c2 C (Sec. 2.1, Eq. 1); everything else is point-wise
+ * (Sec. 2.1).  All device work runs in this library's CUDA kernels on the
+ * current CUDA device; there is no CPU fallback.
+ *
+ * Conventions shared with callers
+ * -------------------------------
+ * Conserved variables per point: rho, rho*u, rho*v, rho*w, E (5 values);
+ * ideal gas p = (gamma-1)(E - rho|v|^2/2).
+ *
+ * Public state layout ("public layout"): one float64 array, tetrahedra
+ * first then prisms, each block [element][variable][solution point]
+ * (element slowest, point fastest).  Its length is fr_ndof().
+ *
+ * Element vertex order: tet vertices 0..3 map to reference vertices
+ * (-1,-1,-1), (1,-1,-1), (-1,1,-1), (-1,-1,1).  Prism vertices 0..2 form the
+ * zeta=-1 triangle (-1,-1), (1,-1), (-1,1); vertex a+3 lies above vertex a
+ * at zeta=+1.  Local faces: tet (0,1,2), (0,1,3), (0,2,3), (1,2,3); prism
+ * (0,1,2), (3,4,5), (0,1,4,3), (1,2,5,4), (2,0,3,5).
+ *
+ * Solution points: the Blyth-Pozrikidis barycentric set built from the p+1
+ * Gauss-Legendre nodes (tet: order k, j, i slowest to fastest; prism:
+ * triangle set x Gauss-Legendre in zeta, zeta slowest).  The paper fixes only
+ * their number (Table 2).
+ *
+ * Errors: every int-returning call returns FR_OK (0) or a negative FR_ERR_*
+ * code; nothing throws or aborts across the ABI.  fr_strerror() describes a
+ * code; fr_last_error() gives the detail of the most recent failure on the
+ * calling thread.
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FR_NVARS 5
+
+enum {
+    FR_OK = 0,
+    FR_ERR_ARG = -1,        /* invalid argument (null pointer, bad size, ...) */
+    FR_ERR_MESH = -2,       /* J <= 0, unmatched or non-conforming face, bad tag */
+    FR_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    FR_ERR_NONFINITE = -4,  /* NaN/Inf or non-positive density/pressure found */
+    FR_ERR_TIMEOUT = -5,    /* reserved: a bounded device wait gave up */
+    FR_ERR_NOMEM = -6,      /* host or device allocation failed */
+    FR_ERR_UNSUPPORTED = -7 /* valid request this build does not implement */
+};
+
+enum { FR_ETYPE_TET = 0, FR_ETYPE_PRI = 1 };
+enum { FR_BC_WALL = 1, FR_BC_FARFIELD = 2 };
+/* Arithmetic of the operator applications (Table 1: single and double). */
+enum { FR_FP64 = 0, FR_FP32 = 1 };
+
+typedef struct fr_ctx fr_ctx; /* opaque; owned by the library */
+
+/* Mesh description.  All arrays are caller-owned, read during fr_create only. */
+typedef struct {
+    int64_t n_nodes;
+    const double *xyz;    /* [n_nodes][3] node coordinates */
+    int64_t n_tet;
+    const int64_t *tet;   /* [n_tet][4] node ids, vertex order above */
+    int64_t n_pri;
+    const int64_t *pri;   /* [n_pri][6] node ids, vertex order above */
+    int64_t n_bface;
+    const int64_t *bface; /* [n_bface][4]: etype, element, local face, bc tag */
+    double period[3];     /* periodic translation per axis; 0 = not periodic */
+} fr_mesh;
+
+/* Gas, viscous and boundary parameters. */
+typedef struct {
+    double gamma;     /* ratio of specific heats */
+    double mu;        /* constant dynamic viscosity (Sec. 3.4) */
+    double prandtl;   /* Prandtl number */
+    double ldg_beta;  /* LDG common-solution bias, switch along a fixed direction */
+    double ldg_tau;   /* LDG penalty on the normal flux */
+    int viscous;      /* 0: Euler, 1: Navier-Stokes */
+    int precision;    /* FR_FP64 or FR_FP32 operator arithmetic */
+    double rho_inf;   /* far-field density */
+    double vel_inf[3];/* far-field velocity */
+    double p_inf;     /* far-field pressure */
+    double t_wall;    /* wall temperature p/rho (gas constant 1) */
+} fr_params;
+
+/*
+ * fr_create: validate the mesh, build points, operators (M0 of Table 2 and
+ * the gradient, divergence and DG-correction operators), geometry and face
+ * connectivity on the host, and upload them to the current CUDA device.
+ * order: polynomial order p in 1..4 (the paper exercises p = 1..4, Sec. 3.4).
+ * On success *out receives a context the caller frees with fr_destroy.
+ * Errors: FR_ERR_ARG, FR_ERR_MESH, FR_ERR_NOMEM, FR_ERR_CUDA.
+ */
+int fr_create(const fr_mesh *mesh, int order, const fr_params *params, fr_ctx **out);
+
+/* Free all host and device memory of the context.  NULL is ignored. */
+void fr_destroy(fr_ctx *ctx);
+
+/* Number of float64 values of the public state layout (5 x total points). */
+int fr_ndof(const fr_ctx *ctx, int64_t *ndof);
+
+/*
+ * fr_info: sizes of the context.  out (caller-owned, 8 int64) receives
+ * n_tet, n_pri, order, nupts(tet), nupts(pri), nfpts(tet), nfpts(pri),
+ * number of interface flux-point pairs.
+ */
+int fr_info(const fr_ctx *ctx, int64_t *out);
+
+/* Physical solution-point coordinates, public layout with the variable
+ * axis replaced by x, y, z (3 values per point).  xyz: host array of
+ * 3*fr_ndof()/5 doubles, caller-owned.  Synchronous. */
+int fr_upts(const fr_ctx *ctx, double *xyz);
+
+/* Copy a host state in the public layout into / out of the context's
+ * internal solution register.  Host arrays are caller-owned, fr_ndof()
+ * doubles.  Synchronous on the given stream (NULL = legacy default). */
+int fr_set_state(fr_ctx *ctx, const double *u_host, void *cuda_stream);
+int fr_get_state(fr_ctx *ctx, double *u_host, void *cuda_stream);
+
+/*
+ * fr_rhs: r = R(u), the FR right-hand side du/dt of the semi-discrete
+ * system, for a state given in the public layout.  u_dev and r_dev are
+ * caller-owned device pointers of fr_ndof() doubles (they may not alias).
+ * Asynchronous on cuda_stream (a cudaStream_t; NULL = legacy default).
+ * The context's scratch buffers are shared by all calls: calls on one
+ * context must not overlap in time.
+ */
+int fr_rhs(fr_ctx *ctx, const double *u_dev, double *r_dev, void *cuda_stream);
+
+/*
+ * fr_step: nsteps classic RK4 steps of size dt on the internal solution
+ * register (set by fr_set_state).  Four RHS evaluations per step; the
+ * register update is fused into the divergence operator's epilogue.
+ * Asynchronous on cuda_stream; contains no host synchronisation.
+ */
+int fr_step(fr_ctx *ctx, double dt, int nsteps, void *cuda_stream);
+
+/*
+ * fr_reduce: integrals of the internal solution register.  out (host,
+ * caller-owned, 7 doubles) receives sum_e sum_j w_j J_j u_j for the 5
+ * conserved variables, the kinetic energy integral, and the number of
+ * points whose state is non-finite or has non-positive density/pressure.
+ * Synchronous.  Returns FR_ERR_NONFINITE (with out filled) if that count
+ * is non-zero.
+ */
+int fr_reduce(fr_ctx *ctx, double *out, void *cuda_stream);
+
+/*
+ * fr_operator: host-only query (no GPU needed) of one operator matrix the
+ * engine builds for (etype, order), row-major float64.  which:
+ *   0 M0   (nf x nu)        interpolation to flux points (Table 2)
+ *   1 D    (3*nu x nu)      reference gradient, row (j, d), d fastest
+ *   2 M3   (nu x nf)        DG correction (lift) of flux-point jumps
+ *   3 AGRAD (3*nu x (nu+nf)) [D | n^ (x) M3], corrected gradient operator
+ *   4 ADIV (nu x (3*nu+nf)) [M1 - M3 M2 | M3] with the divergence
+ *                           M1[j][(i,d)] = D[(j,d)][i] and
+ *                           M2[f][(i,d)] = n^_d(f) M0[f][i]
+ *   5 W    (nu x 1)         quadrature weights of the solution points
+ *   6 UPTS (nu x 3)         reference solution points
+ *   7 FPTS (nf x 3)         reference flux points
+ *   8 FNORM (nf x 3)        outward unit reference normal per flux point
+ * With out == NULL only *rows and *cols are written.  Errors: FR_ERR_ARG.
+ */
+int fr_operator(int etype, int order, int which, double *out, int64_t *rows, int64_t *cols);
+
+/*
+ * Launch accounting.  fr_profile(ctx, enable) resets the counters; while
+ * enabled, every kernel launch of fr_rhs/fr_step is bracketed by a CUDA
+ * event pair on its stream.  fr_profile_read synchronises on those events
+ * and writes, per kernel class (7 entries, caller-owned arrays), the summed
+ * device milliseconds and the launch counts, plus the total number of
+ * kernel launches since the last reset (counted with profiling on or off).
+ * Classes: 0 M0 interpolation, 1 common solution, 2 corrected gradient,
+ * 3 M0 on gradients, 4 point-wise flux, 5 common normal flux,
+ * 6 divergence + correction (+ RK update).
+ */
+#define FR_NKCLASS 7
+int fr_profile(fr_ctx *ctx, int enable);
+int fr_profile_read(fr_ctx *ctx, double *ms, int64_t *count, int64_t *launches);
+
+/*
+ * fr_peak_fp64: measured FP64 FMA throughput of the current device, the
+ * denominator of the FP64 roofline.  Runs a kernel of independent FMA
+ * chains (no memory traffic) on cuda_stream, times it with CUDA events and
+ * writes GFLOP/s (2 flop per FMA) to *gflops.  Synchronous.
+ */
+int fr_peak_fp64(double *gflops, void *cuda_stream);
+
+/* Static description of an error code. */
+const char *fr_strerror(int code);
+
+/* Detail of the most recent error on the calling thread ("" if none). */
+const char *fr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FR_H */

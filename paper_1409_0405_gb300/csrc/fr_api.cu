@@ -1,0 +1,635 @@
+// C ABI of the FR engine (declared in include/fr.h): context creation,
+// device memory, and the RHS / RK4 launch sequences.
+//
+// One RHS evaluation (Sec. 2.1: operator applications C <- c1 A B + c2 C
+// interleaved with point-wise kernels), per element type t:
+//   UF_t  = M0 U_t                                   (Table 2's M0)
+//   NS:   DUF = C - u_f at every flux point          (common solution)
+//         GU_t = (1/J) S^T [D | n^(x)M3] [U_t; DUF_t] (corrected gradient)
+//         GUF_t = M0 GU_t
+//   FT_t  = S (F_inv - F_vis) at solution points
+//   FC    = (common normal flux) |S^T n^| at every flux point
+//   R_t   = -(1/J) [M1 - M3 M2 | M3] [FT_t; FC_t]   (+ fused RK4 update)
+// Internal layout of a state-like matrix: [point][variable][element], the
+// element index padded to np_t (a multiple of 32) and fastest, so every
+// operator application is a plain row-major GEMM over V*np_t columns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fr_internal.h"
+#include "fr_kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_err(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+}  // namespace
+
+using namespace fr;
+
+struct DevType {
+    int present = 0;
+    int64_t ne = 0, np = 0;
+    int nu = 0, nf = 0;
+    double *U = nullptr, *Us = nullptr, *Uacc = nullptr, *R = nullptr;  // [nu][V][np]
+    double *UF = nullptr, *DUF = nullptr, *FC = nullptr;                 // [nf][V][np]
+    double *GU = nullptr, *FT = nullptr;                                  // [nu][3][V][np]
+    double *GUF = nullptr;                                                // [nf][3][V][np]
+    double *S = nullptr;                                                  // [nu][9][np]
+    double *invJ = nullptr, *wJ = nullptr;                                // [nu][np]
+    double *M0 = nullptr, *AGRAD = nullptr, *ADIV = nullptr;
+    std::vector<double> xu;  // host: ne x nu x 3 physical solution points
+};
+
+struct fr_ctx {
+    fr_params prm{};
+    int order = 0;
+    int device = 0;
+    DevType T[2];
+    int64_t npairs = 0, nbnd = 0;
+    int *ta = nullptr, *fa = nullptr, *ea = nullptr, *tb = nullptr, *fb = nullptr, *eb = nullptr;
+    double *nrm = nullptr, *maga = nullptr, *magb = nullptr;
+    int *bt = nullptr, *bf = nullptr, *be = nullptr, *btag = nullptr;
+    double *bn = nullptr, *bmag = nullptr;
+    double *red = nullptr;  // reduction partials + result
+    int red_blocks[2] = {0, 0};
+    std::vector<void *> allocs;
+    // launch accounting: count of kernel launches, and (when profiling is
+    // on) a CUDA event pair around every launch, tagged by kernel class
+    int64_t launches = 0;
+    int prof = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+constexpr int64_t kPad = 32;
+
+template <class T>
+int dev_alloc(fr_ctx *c, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return FR_OK;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(FR_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    e = cudaMemset(q, 0, count * sizeof(T));
+    if (e != cudaSuccess) return set_err(FR_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+    *p = (T *)q;
+    return FR_OK;
+}
+
+template <class T>
+int upload(fr_ctx *c, T **p, const std::vector<T> &h) {
+    int rc = dev_alloc(c, p, h.size());
+    if (rc) return rc;
+    if (h.empty()) return FR_OK;
+    cudaError_t e = cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_err(FR_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    return FR_OK;
+}
+
+int cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return FR_OK;
+    return set_err(FR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+Phys phys_of(const fr_ctx *c) {
+    Phys ph{};
+    ph.gamma = c->prm.gamma;
+    ph.mu = c->prm.mu;
+    ph.prandtl = c->prm.prandtl;
+    ph.beta = c->prm.ldg_beta;
+    ph.tau = c->prm.ldg_tau;
+    ph.rho_inf = c->prm.rho_inf;
+    for (int k = 0; k < 3; ++k) ph.vinf[k] = c->prm.vel_inf[k];
+    ph.p_inf = c->prm.p_inf;
+    ph.t_wall = c->prm.t_wall;
+    ph.viscous = c->prm.viscous;
+    return ph;
+}
+
+Fields fields_of(const fr_ctx *c) {
+    Fields F{};
+    for (int t = 0; t < 2; ++t) {
+        F.UF[t] = c->T[t].UF;
+        F.DUF[t] = c->T[t].DUF;
+        F.GUF[t] = c->T[t].GUF;
+        F.FC[t] = c->T[t].FC;
+        F.np[t] = c->T[t].np;
+    }
+    return F;
+}
+
+Pairs pairs_of(const fr_ctx *c) {
+    return Pairs{c->npairs, c->ta, c->fa, c->ea, c->tb, c->fb, c->eb, c->nrm, c->maga, c->magb};
+}
+
+Bnd bnd_of(const fr_ctx *c) { return Bnd{c->nbnd, c->bt, c->bf, c->be, c->btag, c->bn, c->bmag}; }
+
+enum KClass { K_M0 = 0, K_COMMON_SOL, K_GRAD, K_M0_GRAD, K_FLUX, K_COMMON_FLUX, K_DIV, K_NCLASS };
+
+cudaEvent_t next_event(fr_ctx *c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// Launch one kernel through `fn`, counting it and, when profiling, timing it
+// with an event pair recorded on the launch stream.
+template <class F>
+cudaError_t launch(fr_ctx *c, int kclass, cudaStream_t s, F fn) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof) {
+        a = next_event(c);
+        b = next_event(c);
+        if (a && b) cudaEventRecord(a, s);
+    }
+    cudaError_t e = fn();
+    ++c->launches;
+    if (c->prof && a && b) {
+        cudaEventRecord(b, s);
+        c->prof_ev.push_back({kclass, {a, b}});
+    }
+    return e;
+}
+
+// One RHS evaluation on the stage input `in[t]`; the final operator
+// application either stores R (rk == nullptr) or applies the RK update.
+struct RKStage {
+    double c_acc, c_stage;
+    int first, last;
+};
+
+int rhs_internal(fr_ctx *c, double *const in[2], const RKStage *rk, cudaStream_t s) {
+    const Phys ph = phys_of(c);
+    const Fields F = fields_of(c);
+    int rc;
+    // 1. interpolate to flux points
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        GemmArgs g;
+        g.M = D.nf;
+        g.N = (int64_t)NV * D.np;
+        g.K1 = D.nu;
+        g.A = D.M0;
+        g.B1 = in[t];
+        g.ldb1 = g.N;
+        g.C = D.UF;
+        g.ldc = g.N;
+        g.mode = GEMM_STORE;
+        if ((rc = cuda_check(launch(c, K_M0, s, [&] { return launch_gemm_f64(g, s); }), "gemm M0"))) return rc;
+    }
+    if (c->prm.viscous) {
+        // 2. common solution and jumps
+        if ((rc = cuda_check(launch(c, K_COMMON_SOL, s, [&] { return launch_common_solution(pairs_of(c), bnd_of(c), F, ph, s); }), "common solution")))
+            return rc;
+        // 3. corrected physical gradient; 4. gradient at flux points
+        for (int t = 0; t < 2; ++t) {
+            DevType &D = c->T[t];
+            if (!D.present) continue;
+            GemmArgs g;
+            g.M = 3 * D.nu;
+            g.N = (int64_t)NV * D.np;
+            g.K1 = D.nu;
+            g.K2 = D.nf;
+            g.A = D.AGRAD;
+            g.B1 = in[t];
+            g.ldb1 = g.N;
+            g.B2 = D.DUF;
+            g.ldb2 = g.N;
+            g.C = D.GU;  // [nu][3][V][np]: row (j, m), N columns
+            g.ldc = g.N;
+            g.mode = GEMM_GRAD;
+            g.np = D.np;
+            g.invJ = D.invJ;
+            g.S = D.S;
+            if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return launch_gemm_f64(g, s); }), "gemm grad"))) return rc;
+            GemmArgs h;
+            h.M = D.nf;
+            h.N = 3 * (int64_t)NV * D.np;
+            h.K1 = D.nu;
+            h.A = D.M0;
+            h.B1 = D.GU;
+            h.ldb1 = h.N;
+            h.C = D.GUF;
+            h.ldc = h.N;
+            h.mode = GEMM_STORE;
+            if ((rc = cuda_check(launch(c, K_M0_GRAD, s, [&] { return launch_gemm_f64(h, s); }), "gemm M0 grad"))) return rc;
+        }
+    }
+    // 5. transformed flux at solution points
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch(c, K_FLUX, s, [&] { return launch_flux(D.nu, D.ne, D.np, in[t], D.GU, D.S, D.FT, ph, s); }), "flux"))) return rc;
+    }
+    // 6. common normal flux at every flux point
+    if ((rc = cuda_check(launch(c, K_COMMON_FLUX, s, [&] { return launch_common_flux(pairs_of(c), bnd_of(c), F, ph, s); }), "common flux"))) return rc;
+    // 7. divergence plus correction
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        GemmArgs g;
+        g.M = D.nu;
+        g.N = (int64_t)NV * D.np;
+        g.K1 = 3 * D.nu;
+        g.K2 = D.nf;
+        g.A = D.ADIV;
+        g.B1 = D.FT;
+        g.ldb1 = g.N;
+        g.B2 = D.FC;
+        g.ldb2 = g.N;
+        g.ldc = g.N;
+        g.np = D.np;
+        g.invJ = D.invJ;
+        if (rk) {
+            g.mode = GEMM_DIV_RK;
+            g.U = D.U;
+            g.Uacc = D.Uacc;
+            g.Us = D.Us;
+            g.c_acc = rk->c_acc;
+            g.c_stage = rk->c_stage;
+            g.rk_first = rk->first;
+            g.rk_last = rk->last;
+        } else {
+            g.mode = GEMM_DIV;
+            g.C = D.R;
+        }
+        if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return launch_gemm_f64(g, s); }), "gemm div"))) return rc;
+    }
+    return FR_OK;
+}
+
+int64_t ndof_of(const fr_ctx *c) {
+    int64_t n = 0;
+    for (int t = 0; t < 2; ++t)
+        if (c->T[t].present) n += c->T[t].ne * NV * c->T[t].nu;
+    return n;
+}
+
+int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c) {
+    if (!mesh || !prm) return set_err(FR_ERR_ARG, "null mesh or params");
+    if (order < 1 || order > 4) return set_err(FR_ERR_ARG, "order must be in 1..4");
+    if (mesh->n_nodes <= 0 || !mesh->xyz) return set_err(FR_ERR_ARG, "mesh has no nodes");
+    if (mesh->n_tet < 0 || mesh->n_pri < 0 || mesh->n_bface < 0)
+        return set_err(FR_ERR_ARG, "negative element or face count");
+    if (mesh->n_tet + mesh->n_pri == 0) return set_err(FR_ERR_ARG, "mesh has no elements");
+    if ((mesh->n_tet && !mesh->tet) || (mesh->n_pri && !mesh->pri) || (mesh->n_bface && !mesh->bface))
+        return set_err(FR_ERR_ARG, "null connectivity array");
+    if (mesh->n_tet > (1LL << 30) || mesh->n_pri > (1LL << 30))
+        return set_err(FR_ERR_ARG, "element count too large");
+    if (prm->precision != FR_FP64) return set_err(FR_ERR_UNSUPPORTED, "only FR_FP64 is built");
+    if (!(prm->gamma > 1.0) || prm->mu < 0.0 || (prm->viscous && !(prm->prandtl > 0.0)))
+        return set_err(FR_ERR_ARG, "invalid gas parameters");
+    c->prm = *prm;
+    c->order = order;
+
+    std::string err;
+    RefOps ops[2];
+    for (int t = 0; t < 2; ++t) {
+        int rc = build_ref_ops(t, order, ops[t], err);
+        if (rc) return set_err(rc, err);
+    }
+    TypeGeo geo[2];
+    int rc = build_geometry(mesh, ops, geo, err);
+    if (rc) return set_err(rc, err);
+    Faces faces;
+    rc = build_faces(mesh, ops, geo, faces, err);
+    if (rc) return set_err(rc, err);
+
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(FR_ERR_CUDA, "no usable CUDA device");
+    }
+    const int64_t ne[2] = {mesh->n_tet, mesh->n_pri};
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        D.present = ne[t] > 0;
+        if (!D.present) continue;
+        D.ne = ne[t];
+        D.np = (ne[t] + kPad - 1) / kPad * kPad;
+        D.nu = ops[t].nu;
+        D.nf = ops[t].nf;
+        const size_t su = (size_t)D.nu * NV * D.np, sf = (size_t)D.nf * NV * D.np;
+        if ((rc = dev_alloc(c, &D.U, su)) || (rc = dev_alloc(c, &D.Us, su)) || (rc = dev_alloc(c, &D.Uacc, su)) ||
+            (rc = dev_alloc(c, &D.R, su)) || (rc = dev_alloc(c, &D.UF, sf)) || (rc = dev_alloc(c, &D.FC, sf)) ||
+            (rc = dev_alloc(c, &D.FT, 3 * su)))
+            return rc;
+        if (prm->viscous) {
+            if ((rc = dev_alloc(c, &D.DUF, sf)) || (rc = dev_alloc(c, &D.GU, 3 * su)) ||
+                (rc = dev_alloc(c, &D.GUF, 3 * sf)))
+                return rc;
+        }
+        // geometry in the internal layout
+        std::vector<double> S((size_t)D.nu * 9 * D.np, 0.0), iJ((size_t)D.nu * D.np, 0.0),
+            wJ((size_t)D.nu * D.np, 0.0);
+        const TypeGeo &G = geo[t];
+        for (int64_t e = 0; e < D.ne; ++e)
+            for (int j = 0; j < D.nu; ++j) {
+                const size_t ij = (size_t)e * D.nu + j;
+                for (int k = 0; k < 9; ++k) S[((size_t)j * 9 + k) * D.np + e] = G.S[9 * ij + k];
+                iJ[(size_t)j * D.np + e] = 1.0 / G.J[ij];
+                wJ[(size_t)j * D.np + e] = ops[t].W[j] * G.J[ij];
+            }
+        if ((rc = upload(c, &D.S, S)) || (rc = upload(c, &D.invJ, iJ)) || (rc = upload(c, &D.wJ, wJ)) ||
+            (rc = upload(c, &D.M0, ops[t].M0)) || (rc = upload(c, &D.AGRAD, ops[t].AGRAD)) ||
+            (rc = upload(c, &D.ADIV, ops[t].ADIV)))
+            return rc;
+        D.xu = G.xu;
+    }
+    c->npairs = (int64_t)faces.ta.size();
+    c->nbnd = (int64_t)faces.bt.size();
+    if ((rc = upload(c, &c->ta, faces.ta)) || (rc = upload(c, &c->fa, faces.fa)) || (rc = upload(c, &c->ea, faces.ea)) ||
+        (rc = upload(c, &c->tb, faces.tb)) || (rc = upload(c, &c->fb, faces.fb)) || (rc = upload(c, &c->eb, faces.eb)) ||
+        (rc = upload(c, &c->nrm, faces.n)) || (rc = upload(c, &c->maga, faces.maga)) ||
+        (rc = upload(c, &c->magb, faces.magb)) || (rc = upload(c, &c->bt, faces.bt)) ||
+        (rc = upload(c, &c->bf, faces.bf)) || (rc = upload(c, &c->be, faces.be)) ||
+        (rc = upload(c, &c->btag, faces.btag)) || (rc = upload(c, &c->bn, faces.bn)) ||
+        (rc = upload(c, &c->bmag, faces.bmag)))
+        return rc;
+    int nbt = 0;
+    for (int t = 0; t < 2; ++t) {
+        c->red_blocks[t] = c->T[t].present ? 152 * 2 : 0;
+        nbt += c->red_blocks[t];
+    }
+    if ((rc = dev_alloc(c, &c->red, (size_t)nbt * 7 + 8))) return rc;
+    return cuda_check(cudaDeviceSynchronize(), "fr_create sync");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fr_strerror(int code) {
+    switch (code) {
+        case FR_OK:
+            return "success";
+        case FR_ERR_ARG:
+            return "invalid argument";
+        case FR_ERR_MESH:
+            return "invalid mesh";
+        case FR_ERR_CUDA:
+            return "CUDA error";
+        case FR_ERR_NONFINITE:
+            return "non-finite or non-physical state";
+        case FR_ERR_TIMEOUT:
+            return "device wait timed out";
+        case FR_ERR_NOMEM:
+            return "out of memory";
+        case FR_ERR_UNSUPPORTED:
+            return "unsupported request";
+    }
+    return "unknown error";
+}
+
+const char *fr_last_error(void) { return g_last_error.c_str(); }
+
+int fr_create(const fr_mesh *mesh, int order, const fr_params *params, fr_ctx **out) {
+    if (!out) return set_err(FR_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    fr_ctx *c = new (std::nothrow) fr_ctx();
+    if (!c) return set_err(FR_ERR_NOMEM, "host allocation");
+    int rc;
+    try {
+        rc = create_impl(mesh, order, params, c);
+    } catch (const std::bad_alloc &) {
+        rc = set_err(FR_ERR_NOMEM, "host allocation during set-up");
+    } catch (...) {
+        rc = set_err(FR_ERR_ARG, "unexpected exception during set-up");
+    }
+    if (rc) {
+        fr_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return FR_OK;
+}
+
+void fr_destroy(fr_ctx *c) {
+    if (!c) return;
+    for (void *p : c->allocs) cudaFree(p);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+int fr_profile(fr_ctx *c, int enable) {
+    if (!c) return set_err(FR_ERR_ARG, "null context");
+    c->prof = enable ? 1 : 0;
+    c->prof_ev.clear();
+    c->ev_used = 0;
+    c->launches = 0;
+    return FR_OK;
+}
+
+int fr_profile_read(fr_ctx *c, double *ms, int64_t *count, int64_t *launches) {
+    if (!c || !ms || !count || !launches) return set_err(FR_ERR_ARG, "null argument");
+    for (int k = 0; k < K_NCLASS; ++k) {
+        ms[k] = 0.0;
+        count[k] = 0;
+    }
+    int rc;
+    for (auto &pe : c->prof_ev) {
+        if ((rc = cuda_check(cudaEventSynchronize(pe.second.second), "profile sync"))) return rc;
+        float t = 0.f;
+        if ((rc = cuda_check(cudaEventElapsedTime(&t, pe.second.first, pe.second.second), "profile elapsed")))
+            return rc;
+        ms[pe.first] += t;
+        count[pe.first] += 1;
+    }
+    *launches = c->launches;
+    return FR_OK;
+}
+
+int fr_ndof(const fr_ctx *c, int64_t *ndof) {
+    if (!c || !ndof) return set_err(FR_ERR_ARG, "null argument");
+    *ndof = ndof_of(c);
+    return FR_OK;
+}
+
+int fr_info(const fr_ctx *c, int64_t *out) {
+    if (!c || !out) return set_err(FR_ERR_ARG, "null argument");
+    out[0] = c->T[0].ne;
+    out[1] = c->T[1].ne;
+    out[2] = c->order;
+    out[3] = nupts_of(0, c->order);
+    out[4] = nupts_of(1, c->order);
+    out[5] = nfpts_of(0, c->order);
+    out[6] = nfpts_of(1, c->order);
+    out[7] = c->npairs;
+    return FR_OK;
+}
+
+int fr_upts(const fr_ctx *c, double *xyz) {
+    if (!c || !xyz) return set_err(FR_ERR_ARG, "null argument");
+    size_t off = 0;
+    for (int t = 0; t < 2; ++t) {
+        const DevType &D = c->T[t];
+        if (!D.present) continue;
+        for (int64_t e = 0; e < D.ne; ++e)
+            for (int k = 0; k < 3; ++k)
+                for (int j = 0; j < D.nu; ++j) xyz[off++] = D.xu[((size_t)e * D.nu + j) * 3 + k];
+    }
+    return FR_OK;
+}
+
+int fr_set_state(fr_ctx *c, const double *u, void *stream) {
+    if (!c || !u) return set_err(FR_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t off = 0;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        const size_t n = (size_t)D.ne * NV * D.nu;
+        int rc;
+        if ((rc = cuda_check(cudaMemcpyAsync(D.R, u + off, n * sizeof(double), cudaMemcpyHostToDevice, s),
+                             "set_state copy")))
+            return rc;
+        if ((rc = cuda_check(launch_pub_to_int(D.nu, D.ne, D.np, D.R, D.U, s), "set_state layout"))) return rc;
+        off += n;
+    }
+    return cuda_check(cudaStreamSynchronize(s), "set_state sync");
+}
+
+int fr_get_state(fr_ctx *c, double *u, void *stream) {
+    if (!c || !u) return set_err(FR_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t off = 0;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        const size_t n = (size_t)D.ne * NV * D.nu;
+        int rc;
+        if ((rc = cuda_check(launch_int_to_pub(D.nu, D.ne, D.np, D.U, D.R, s), "get_state layout"))) return rc;
+        if ((rc = cuda_check(cudaMemcpyAsync(u + off, D.R, n * sizeof(double), cudaMemcpyDeviceToHost, s),
+                             "get_state copy")))
+            return rc;
+        off += n;
+    }
+    return cuda_check(cudaStreamSynchronize(s), "get_state sync");
+}
+
+int fr_rhs(fr_ctx *c, const double *u_dev, double *r_dev, void *stream) {
+    if (!c || !u_dev || !r_dev) return set_err(FR_ERR_ARG, "null argument");
+    if (u_dev == r_dev) return set_err(FR_ERR_ARG, "u and r may not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t off = 0;
+    double *in[2] = {nullptr, nullptr};
+    int rc;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_pub_to_int(D.nu, D.ne, D.np, u_dev + off, D.Us, s), "rhs layout in")))
+            return rc;
+        in[t] = D.Us;
+        off += (size_t)D.ne * NV * D.nu;
+    }
+    if ((rc = rhs_internal(c, in, nullptr, s))) return rc;
+    off = 0;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_int_to_pub(D.nu, D.ne, D.np, D.R, r_dev + off, s), "rhs layout out")))
+            return rc;
+        off += (size_t)D.ne * NV * D.nu;
+    }
+    return FR_OK;
+}
+
+int fr_step(fr_ctx *c, double dt, int nsteps, void *stream) {
+    if (!c || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double ca[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+    const double cs[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+    for (int it = 0; it < nsteps; ++it)
+        for (int st = 0; st < 4; ++st) {
+            double *in[2] = {nullptr, nullptr};
+            for (int t = 0; t < 2; ++t)
+                if (c->T[t].present) in[t] = st == 0 ? c->T[t].U : c->T[t].Us;
+            RKStage rk{ca[st], cs[st], st == 0, st == 3};
+            int rc = rhs_internal(c, in, &rk, s);
+            if (rc) return rc;
+        }
+    return FR_OK;
+}
+
+int fr_reduce(fr_ctx *c, double *out, void *stream) {
+    if (!c || !out) return set_err(FR_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int off = 0, rc;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_reduce_partial(D.nu, D.ne, D.np, D.U, D.wJ, c->prm.gamma, c->red + (size_t)off * 7,
+                                                   c->red_blocks[t], s),
+                             "reduce")))
+            return rc;
+        off += c->red_blocks[t];
+    }
+    double *res = c->red + (size_t)off * 7;
+    if ((rc = cuda_check(launch_reduce_final(c->red, off, res, s), "reduce final"))) return rc;
+    if ((rc = cuda_check(cudaMemcpyAsync(out, res, 7 * sizeof(double), cudaMemcpyDeviceToHost, s), "reduce copy")))
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(s), "reduce sync"))) return rc;
+    if (out[6] != 0.0) return set_err(FR_ERR_NONFINITE, "non-finite or non-physical state");
+    return FR_OK;
+}
+
+int fr_peak_fp64(double *gflops, void *stream) {
+    if (!gflops) return set_err(FR_ERR_ARG, "null argument");
+    return cuda_check(probe_fp64(gflops, (cudaStream_t)stream), "fp64 probe");
+}
+
+int fr_operator(int etype, int order, int which, double *out, int64_t *rows, int64_t *cols) {
+    if (!rows || !cols) return set_err(FR_ERR_ARG, "null rows/cols");
+    RefOps o;
+    std::string err;
+    int rc;
+    try {
+        rc = build_ref_ops(etype, order, o, err);
+    } catch (...) {
+        return set_err(FR_ERR_NOMEM, "host allocation");
+    }
+    if (rc) return set_err(rc, err);
+    const std::vector<double> *src = nullptr;
+    int64_t r = 0, cc = 0;
+    switch (which) {
+        case 0: src = &o.M0; r = o.nf; cc = o.nu; break;
+        case 1: src = &o.D; r = 3 * o.nu; cc = o.nu; break;
+        case 2: src = &o.M3; r = o.nu; cc = o.nf; break;
+        case 3: src = &o.AGRAD; r = 3 * o.nu; cc = o.nu + o.nf; break;
+        case 4: src = &o.ADIV; r = o.nu; cc = 3 * o.nu + o.nf; break;
+        case 5: src = &o.W; r = o.nu; cc = 1; break;
+        case 6: src = &o.upts; r = o.nu; cc = 3; break;
+        case 7: src = &o.fpts; r = o.nf; cc = 3; break;
+        case 8: src = &o.fnorm; r = o.nf; cc = 3; break;
+        default: return set_err(FR_ERR_ARG, "unknown operator id");
+    }
+    *rows = r;
+    *cols = cc;
+    if (out) std::memcpy(out, src->data(), sizeof(double) * (size_t)(r * cc));
+    return FR_OK;
+}
+
+}  // extern "C"

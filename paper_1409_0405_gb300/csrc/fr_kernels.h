@@ -1,0 +1,88 @@
+// Launch interface of the FR engine's CUDA kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fr {
+
+// Epilogues of the operator application C <- A [B1; B2] (Sec. 2.1, Eq. 1).
+enum GemmMode {
+    GEMM_STORE = 0,  // C = A B
+    GEMM_GRAD = 1,   // rows (j, d): C(j, m) = (1/J) sum_d S[d][m] (A B)(j, d)
+    GEMM_DIV = 2,    // C(j) = -(1/J_j) (A B)(j)
+    GEMM_DIV_RK = 3  // r = -(1/J)(A B); fused RK4 register update
+};
+
+struct GemmArgs {
+    int M = 0;            // rows of A and C
+    int64_t N = 0;        // columns of B and C
+    int K1 = 0, K2 = 0;   // A = [A1 | A2], B = [B1; B2]
+    const double *A = nullptr;  // M x (K1 + K2), row-major
+    const double *B1 = nullptr;
+    int64_t ldb1 = 0;
+    const double *B2 = nullptr;
+    int64_t ldb2 = 0;
+    double *C = nullptr;
+    int64_t ldc = 0;
+    int mode = GEMM_STORE;
+    int64_t np = 0;             // element stride: column n belongs to element n % np
+    const double *invJ = nullptr;  // [nu][np]
+    const double *S = nullptr;     // [nu][9][np]
+    // GEMM_DIV_RK: with r the RHS,
+    //   rk_first: Uacc = U + c_acc r,  else Uacc += c_acc r
+    //   !rk_last: Us = U + c_stage r;  rk_last: U = Uacc + c_acc r
+    double *U = nullptr, *Uacc = nullptr, *Us = nullptr;
+    double c_acc = 0, c_stage = 0;
+    int rk_first = 0, rk_last = 0;
+};
+
+cudaError_t launch_gemm_f64(const GemmArgs &g, cudaStream_t s);
+
+struct Phys {
+    double gamma, mu, prandtl, beta, tau;
+    double rho_inf, vinf[3], p_inf, t_wall;
+    int viscous;
+};
+
+// Per-type field pointers (index 0 tet, 1 prism); nullptr for an absent type.
+struct Fields {
+    const double *UF[2];   // [nf][V][np]
+    double *DUF[2];        // [nf][V][np]
+    const double *GUF[2];  // [nf][3][V][np]
+    double *FC[2];         // [nf][V][np]
+    int64_t np[2];
+};
+
+struct Pairs {
+    int64_t n;
+    const int *ta, *fa, *ea, *tb, *fb, *eb;
+    const double *nrm, *maga, *magb;
+};
+
+struct Bnd {
+    int64_t n;
+    const int *bt, *bf, *be, *btag;
+    const double *bn, *bmag;
+};
+
+cudaError_t launch_common_solution(const Pairs &P, const Bnd &B, const Fields &F, const Phys &ph,
+                                   cudaStream_t s);
+cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const Fields &F, const Phys &ph,
+                               cudaStream_t s);
+// transformed flux at the solution points of one type
+cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const double *U, const double *GU,
+                        const double *S, double *FT, const Phys &ph, cudaStream_t s);
+// public [e][v][j] <-> internal [j][v][e]
+cudaError_t launch_pub_to_int(int nu, int64_t ne, int64_t np, const double *pub, double *in,
+                              cudaStream_t s);
+cudaError_t launch_int_to_pub(int nu, int64_t ne, int64_t np, const double *in, double *pub,
+                              cudaStream_t s);
+// per-block partial integrals (7 per block) of one type's register
+cudaError_t launch_reduce_partial(int nu, int64_t ne, int64_t np, const double *U, const double *wJ,
+                                  double gamma, double *partial, int nblocks, cudaStream_t s);
+cudaError_t launch_reduce_final(const double *partial, int nblocks, double *out, cudaStream_t s);
+// measured FP64 FMA throughput (GFLOP/s) of the current device
+cudaError_t probe_fp64(double *gflops, cudaStream_t s);
+
+}  // namespace fr

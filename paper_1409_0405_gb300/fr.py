@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libfr.so (the C ABI declared in include/fr.h).
+
+Argument marshalling only: every step of the FR right-hand side runs in
+the library's CUDA kernels.  PyTorch is used by callers for device memory
+and streams; this module passes raw pointers.  Loading fails loudly when
+the shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfr.so")
+
+FR_OK = 0
+FR_ERR_ARG = -1
+FR_ERR_MESH = -2
+FR_ERR_CUDA = -3
+FR_ERR_NONFINITE = -4
+FR_ERR_TIMEOUT = -5
+FR_ERR_NOMEM = -6
+FR_ERR_UNSUPPORTED = -7
+FR_FP64 = 0
+FR_FP32 = 1
+NVARS = 5
+
+OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
+          "FPTS": 7, "FNORM": 8}
+
+# every entry point declared in include/fr.h
+EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
+           "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_reduce",
+           "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
+           "fr_last_error")
+KCLASSES = ("M0", "common_solution", "grad", "M0_grad", "flux", "common_flux", "div")
+
+
+class FRMesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("xyz", C.POINTER(C.c_double)),
+                ("n_tet", C.c_int64), ("tet", C.POINTER(C.c_int64)),
+                ("n_pri", C.c_int64), ("pri", C.POINTER(C.c_int64)),
+                ("n_bface", C.c_int64), ("bface", C.POINTER(C.c_int64)),
+                ("period", C.c_double * 3)]
+
+
+class FRParams(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("prandtl", C.c_double),
+                ("ldg_beta", C.c_double), ("ldg_tau", C.c_double),
+                ("viscous", C.c_int), ("precision", C.c_int),
+                ("rho_inf", C.c_double), ("vel_inf", C.c_double * 3),
+                ("p_inf", C.c_double), ("t_wall", C.c_double)]
+
+
+class FRError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libfr.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built; run paper_1409_0405_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    lib.fr_create.argtypes = [C.POINTER(FRMesh), C.c_int, C.POINTER(FRParams), C.POINTER(vp)]
+    lib.fr_destroy.argtypes = [vp]
+    lib.fr_destroy.restype = None
+    lib.fr_ndof.argtypes = [vp, i64p]
+    lib.fr_info.argtypes = [vp, i64p]
+    lib.fr_upts.argtypes = [vp, dp]
+    lib.fr_set_state.argtypes = [vp, dp, vp]
+    lib.fr_get_state.argtypes = [vp, dp, vp]
+    lib.fr_rhs.argtypes = [vp, vp, vp, vp]
+    lib.fr_step.argtypes = [vp, C.c_double, C.c_int, vp]
+    lib.fr_reduce.argtypes = [vp, dp, vp]
+    lib.fr_operator.argtypes = [C.c_int, C.c_int, C.c_int, dp, i64p, i64p]
+    lib.fr_profile.argtypes = [vp, C.c_int]
+    lib.fr_profile_read.argtypes = [vp, dp, i64p, i64p]
+    lib.fr_peak_fp64.argtypes = [dp, vp]
+    lib.fr_peak_fp64.restype = C.c_int
+    lib.fr_strerror.argtypes = [C.c_int]
+    lib.fr_strerror.restype = C.c_char_p
+    lib.fr_last_error.argtypes = []
+    lib.fr_last_error.restype = C.c_char_p
+    for name in ("fr_create", "fr_ndof", "fr_info", "fr_upts", "fr_set_state",
+                 "fr_get_state", "fr_rhs", "fr_step", "fr_reduce", "fr_operator",
+                 "fr_profile", "fr_profile_read"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != FR_OK:
+        lib = load()
+        raise FRError(rc, f"{lib.fr_strerror(rc).decode()}: {lib.fr_last_error().decode()}")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def operator(etype, order, which):
+    """Host-only operator query (no GPU needed): returns a float64 matrix."""
+    lib = load()
+    rows, cols = C.c_int64(), C.c_int64()
+    wid = OP_IDS[which] if isinstance(which, str) else int(which)
+    et = {"tet": 0, "pri": 1}.get(etype, etype)
+    _check(lib.fr_operator(et, order, wid, None, C.byref(rows), C.byref(cols)))
+    out = np.empty((rows.value, cols.value), dtype=np.float64)
+    _check(lib.fr_operator(et, order, wid, _dptr(out), C.byref(rows), C.byref(cols)))
+    return out
+
+
+def peak_fp64(stream=None):
+    """Measured FP64 FMA throughput of the current GPU in GFLOP/s."""
+    lib = load()
+    g = C.c_double()
+    _check(lib.fr_peak_fp64(C.byref(g), C.c_void_p(stream) if stream else None))
+    return g.value
+
+
+def default_params(viscous=False, mu=0.0, gamma=1.4, prandtl=0.72, ldg_beta=0.5,
+                   ldg_tau=0.1, rho_inf=1.0, vel_inf=(1.0, 0.0, 0.0), p_inf=None,
+                   t_wall=None, precision=FR_FP64):
+    p_inf = 1.0 / gamma if p_inf is None else p_inf
+    t_wall = p_inf / rho_inf if t_wall is None else t_wall
+    return dict(gamma=gamma, mu=mu, prandtl=prandtl, ldg_beta=ldg_beta, ldg_tau=ldg_tau,
+                viscous=int(viscous), precision=precision, rho_inf=rho_inf,
+                vel_inf=tuple(vel_inf), p_inf=p_inf, t_wall=t_wall)
+
+
+class Context:
+    """One fr_ctx: mesh + order + parameters resident on the current GPU."""
+
+    def __init__(self, mesh, order, **params):
+        lib = load()
+        prm = default_params(**params)
+        self._keep = {
+            "xyz": np.ascontiguousarray(mesh["xyz"], dtype=np.float64),
+            "tet": np.ascontiguousarray(mesh["tet"], dtype=np.int64).reshape(-1, 4),
+            "pri": np.ascontiguousarray(mesh["pri"], dtype=np.int64).reshape(-1, 6),
+            "bface": np.ascontiguousarray(mesh.get("bface", np.zeros((0, 4))), dtype=np.int64).reshape(-1, 4),
+        }
+        k = self._keep
+        m = FRMesh()
+        m.n_nodes = len(k["xyz"])
+        m.xyz = _dptr(k["xyz"])
+        m.n_tet = len(k["tet"])
+        m.tet = k["tet"].ctypes.data_as(C.POINTER(C.c_int64))
+        m.n_pri = len(k["pri"])
+        m.pri = k["pri"].ctypes.data_as(C.POINTER(C.c_int64))
+        m.n_bface = len(k["bface"])
+        m.bface = k["bface"].ctypes.data_as(C.POINTER(C.c_int64))
+        per = np.asarray(mesh.get("period", np.zeros(3)), dtype=np.float64)
+        m.period = (C.c_double * 3)(*per)
+        p = FRParams()
+        for key, val in prm.items():
+            if key == "vel_inf":
+                p.vel_inf = (C.c_double * 3)(*val)
+            else:
+                setattr(p, key, val)
+        self.params = prm
+        h = C.c_void_p()
+        _check(lib.fr_create(C.byref(m), int(order), C.byref(p), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        n = C.c_int64()
+        _check(lib.fr_ndof(h, C.byref(n)))
+        self.ndof = n.value
+        info = (C.c_int64 * 8)()
+        _check(lib.fr_info(h, info))
+        self.info = dict(zip(("n_tet", "n_pri", "order", "nu_tet", "nu_pri", "nf_tet",
+                              "nf_pri", "npairs"), list(info)))
+        self.order = order
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- queries ---------------------------------------------------------------
+    def upts(self):
+        """(ndof/5*3,) physical solution-point coordinates, public layout."""
+        out = np.empty(self.ndof // NVARS * 3, dtype=np.float64)
+        _check(self._lib.fr_upts(self._h, _dptr(out)))
+        return out
+
+    def upts_points(self):
+        """(n_points, 3) coordinates in public point order."""
+        x = self.upts()
+        blocks, off = [], 0
+        for ne, nu in ((self.info["n_tet"], self.info["nu_tet"]), (self.info["n_pri"], self.info["nu_pri"])):
+            if ne == 0:
+                continue
+            blk = x[off:off + ne * 3 * nu].reshape(ne, 3, nu).transpose(0, 2, 1).reshape(-1, 3)
+            blocks.append(blk)
+            off += ne * 3 * nu
+        return np.concatenate(blocks)
+
+    # -- compute ---------------------------------------------------------------
+    def set_state(self, u, stream=None):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.size == self.ndof
+        _check(self._lib.fr_set_state(self._h, _dptr(u), stream))
+
+    def get_state(self, out=None, stream=None):
+        out = np.empty(self.ndof, dtype=np.float64) if out is None else out
+        _check(self._lib.fr_get_state(self._h, _dptr(out), stream))
+        return out
+
+    def rhs(self, u_ptr, r_ptr, stream=None):
+        """r = R(u) for device pointers (ints, e.g. tensor.data_ptr())."""
+        _check(self._lib.fr_rhs(self._h, C.c_void_p(u_ptr), C.c_void_p(r_ptr),
+                                C.c_void_p(stream) if stream else None))
+
+    def step(self, dt, nsteps=1, stream=None):
+        _check(self._lib.fr_step(self._h, float(dt), int(nsteps),
+                                 C.c_void_p(stream) if stream else None))
+
+    def profile(self, enable=True):
+        _check(self._lib.fr_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{class: (ms, count)} and the total launch count since the reset."""
+        ms = np.zeros(len(KCLASSES))
+        cnt = np.zeros(len(KCLASSES), dtype=np.int64)
+        tot = C.c_int64()
+        _check(self._lib.fr_profile_read(self._h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
+                                         C.byref(tot)))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KCLASSES)}, tot.value
+
+    def reduce(self, stream=None, check=True):
+        out = np.empty(7, dtype=np.float64)
+        rc = self._lib.fr_reduce(self._h, _dptr(out), C.c_void_p(stream) if stream else None)
+        if rc == FR_ERR_NONFINITE and not check:
+            return out
+        _check(rc)
+        return out

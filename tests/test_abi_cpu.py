@@ -1,0 +1,114 @@
+"""The C ABI on the CPU: the library builds and loads, exports every entry
+point include/fr.h declares, its host-built operators agree with the
+oracle's exact ones (two independent constructions), and mesh validation
+rejects bad meshes before any device work.  No GPU is needed."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis
+from tests._cases import library
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fr_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = library()
+    from paper_1409_0405_gb300 import fr
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(fr.EXPORTS) == names
+
+
+def test_strerror():
+    lib = library()
+    assert lib.fr_strerror(0) == b"success"
+    assert b"mesh" in lib.fr_strerror(-2)
+
+
+@pytest.mark.parametrize("etype", ["tet", "pri"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_host_operators_match_oracle(etype, p):
+    library()
+    from paper_1409_0405_gb300 import fr
+    op = basis.operators(etype, p)
+    np.testing.assert_allclose(fr.operator(etype, p, "UPTS"), op.upts, atol=1e-14)
+    np.testing.assert_allclose(fr.operator(etype, p, "FPTS"), op.fpts, atol=1e-14)
+    np.testing.assert_allclose(fr.operator(etype, p, "M0"), op.M0, atol=1e-13)
+    D = np.stack([op.D[d] for d in range(3)], 1).reshape(-1, op.nu)
+    np.testing.assert_allclose(fr.operator(etype, p, "D"), D, atol=1e-12)
+    np.testing.assert_allclose(fr.operator(etype, p, "M3"), op.M3, atol=1e-12 * np.abs(op.M3).max())
+    np.testing.assert_allclose(fr.operator(etype, p, "W")[:, 0], op.w, atol=1e-14)
+    np.testing.assert_allclose(fr.operator(etype, p, "FNORM"), op.fnorm, atol=1e-15)
+    # the fused operators are the documented combinations
+    AG = fr.operator(etype, p, "AGRAD")
+    nu, nf = op.nu, op.nf
+    for d in range(3):
+        np.testing.assert_allclose(AG[d::3, :nu], op.D[d], atol=1e-12)
+        np.testing.assert_allclose(AG[d::3, nu:], op.fnorm[:, d] * op.M3, atol=1e-11)
+    AD = fr.operator(etype, p, "ADIV")
+    np.testing.assert_allclose(AD[:, 3 * nu:], op.M3, atol=1e-11)
+    for d in range(3):
+        M132 = op.D[d] - op.M3 @ (op.fnorm[:, d:d + 1] * op.M0)
+        np.testing.assert_allclose(AD[:, d:3 * nu:3], M132, atol=1e-11)
+
+
+def test_operator_bad_arguments():
+    lib = library()
+    import ctypes as C
+    r, c = C.c_int64(), C.c_int64()
+    assert lib.fr_operator(2, 2, 0, None, C.byref(r), C.byref(c)) == -1
+    assert lib.fr_operator(0, 5, 0, None, C.byref(r), C.byref(c)) == -1
+    assert lib.fr_operator(0, 2, 99, None, C.byref(r), C.byref(c)) == -1
+
+
+def _create_rc(mesh, p=2, **kw):
+    from paper_1409_0405_gb300 import fr
+    try:
+        fr.Context(mesh, p, **kw)
+    except fr.FRError as e:
+        return e.code
+    return 0
+
+
+def test_mesh_errors_detected_on_host():
+    library()
+    from paper_1409_0405_gb300 import fr
+    m = synth.vortex_box()
+    bad = dict(m)
+    bad["tet"] = m["tet"].copy()
+    bad["tet"][0, [1, 2]] = bad["tet"][0, [2, 1]]           # inverted element
+    assert _create_rc(bad) == fr.FR_ERR_MESH
+    nop = dict(m)
+    nop["period"] = np.zeros(3)                              # free faces, no period
+    assert _create_rc(nop) == fr.FR_ERR_MESH
+    oob = dict(m)
+    oob["pri"] = m["pri"].copy()
+    oob["pri"][3, 0] = 10 ** 9                               # node id out of range
+    assert _create_rc(oob) == fr.FR_ERR_MESH
+    bf = synth.boundary_layer_box(nx=3, nz=2, n_prism_layers=2, n_tet_layers=2)
+    bf["bface"] = bf["bface"].copy()
+    bf["bface"][0, 3] = 7                                    # unknown tag
+    assert _create_rc(bf) == fr.FR_ERR_MESH
+    assert _create_rc(m, p=0) == fr.FR_ERR_ARG
+    assert _create_rc(m, p=2, precision=7) == fr.FR_ERR_UNSUPPORTED
+
+
+def test_create_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    library()
+    from paper_1409_0405_gb300 import fr
+    assert _create_rc(synth.vortex_box()) == fr.FR_ERR_CUDA

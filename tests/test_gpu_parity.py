@@ -1,0 +1,152 @@
+"""CUDA path against the oracle, element by element (GPU).
+
+Tolerance: the FP64 path must match the oracle to 1e-12 relative per
+conserved variable (max |gpu - oracle| / max |oracle|) on the RHS and on
+states after RK4 steps.  Cases span several GEMM column tiles with ragged
+tails, both element types alone and mixed, orders 1..4, Euler and
+Navier-Stokes, periodic, wall and far-field boundaries, and the full-size
+boundary-layer workload (57,600 prisms + 118,800 tets, p = 4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from tests._cases import (bl_params, gpu_rhs, library, make_pair, per_var_rel_err, state)
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    library()
+
+
+def _check_rhs(sol, ctx, u, tol=TOL):
+    ref = sol.rhs(u)
+    got = gpu_rhs(ctx, u)
+    err = per_var_rel_err(sol, ref, got)
+    assert np.all(err <= tol), err
+    return err
+
+
+def test_solution_points_match_oracle():
+    sol, ctx = make_pair(synth.vortex_box(), 3)
+    np.testing.assert_allclose(ctx.upts(), sol.upts_xyz(), atol=1e-13)
+
+
+def test_vortex_euler_p2_rhs():
+    """The isentropic-vortex workload: 64 prisms + 192 tets, p = 2, Euler."""
+    sol, ctx = make_pair(synth.vortex_box(), 2)
+    _check_rhs(sol, ctx, state(sol, "vortex"))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_rhs_all_orders_periodic(p, viscous):
+    sol, ctx = make_pair(synth.vortex_box(), p, viscous=viscous, mu=0.05)
+    _check_rhs(sol, ctx, state(sol, "smooth", seed=p))
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_rhs_wall_and_farfield_ns(p):
+    """No-slip wall, far field and a periodic axis, stretched jittered
+    prism layers under Kuhn tets."""
+    m = synth.boundary_layer_box(nx=7, nz=3, n_prism_layers=5, n_tet_layers=3)
+    sol, ctx = make_pair(m, p, **bl_params(mu=0.01))
+    _check_rhs(sol, ctx, state(sol, "bl"))
+
+
+@pytest.mark.parametrize("n,npl", [(5, 2), (6, 0), (3, 3), (7, 3)])
+def test_rhs_ragged_and_single_type(n, npl):
+    """Element counts that are not multiples of the padding or the column
+    tile; tets only (npl = 0) and prisms only (npl = n)."""
+    m = synth.vortex_box(n=n, n_prism_layers=npl)
+    sol, ctx = make_pair(m, 3, viscous=True, mu=0.02)
+    _check_rhs(sol, ctx, state(sol, "smooth", seed=n))
+
+
+def test_vortex_rk4_100_steps():
+    """The vortex workload advanced 100 RK4 steps at CFL 0.1."""
+    sol, ctx = make_pair(synth.vortex_box(), 2)
+    u = state(sol, "vortex")
+    dt = sol.dt_cfl(u, 0.1)
+    ctx.set_state(u)
+    ctx.step(dt, 100)
+    got = ctx.get_state()
+    ref = u
+    for _ in range(100):
+        ref = sol.rk4_step(ref, dt)
+    err = per_var_rel_err(sol, ref, got)
+    assert np.all(err <= TOL), err
+    # conserved totals (periodic box) do not drift
+    out = ctx.reduce()
+    np.testing.assert_allclose(out[:5], sol.integrals(u), rtol=1e-12, atol=1e-9)
+
+
+def test_ns_boundary_layer_rk4_steps():
+    m = synth.boundary_layer_box(nx=6, nz=3, n_prism_layers=4, n_tet_layers=3)
+    sol, ctx = make_pair(m, 3, **bl_params(mu=0.01))
+    u = state(sol, "bl")
+    dt = 0.2 * sol.dt_cfl(u, 0.1)
+    ctx.set_state(u)
+    ctx.step(dt, 3)
+    ref = u
+    for _ in range(3):
+        ref = sol.rk4_step(ref, dt)
+    err = per_var_rel_err(sol, ref, ctx.get_state())
+    assert np.all(err <= TOL), err
+
+
+def test_reductions_match_oracle():
+    sol, ctx = make_pair(synth.vortex_box(), 2)
+    u = state(sol, "vortex")
+    ctx.set_state(u)
+    out = ctx.reduce()
+    np.testing.assert_allclose(out[:5], sol.integrals(u), rtol=1e-13)
+    np.testing.assert_allclose(out[5], sol.kinetic_energy(u), rtol=1e-13)
+    assert out[6] == 0.0
+
+
+def test_nonphysical_state_is_reported():
+    from paper_1409_0405_gb300 import fr
+    sol, ctx = make_pair(synth.vortex_box(), 1)
+    u = state(sol, "vortex")
+    bad = u.copy()
+    bad[0] = -1.0            # negative density at point 0 of element 0
+    bad[7] = np.nan          # a non-finite momentum at point 3 of element 0
+    ctx.set_state(bad)
+    with pytest.raises(fr.FRError) as ei:
+        ctx.reduce()
+    assert ei.value.code == fr.FR_ERR_NONFINITE
+    assert ctx.reduce(check=False)[6] == 2.0
+
+
+def test_state_roundtrip_and_launch_count():
+    sol, ctx = make_pair(synth.vortex_box(), 2, viscous=True, mu=0.01)
+    u = state(sol, "smooth", seed=9)
+    ctx.set_state(u)
+    np.testing.assert_array_equal(ctx.get_state(), u)
+    ctx.profile(True)
+    ctx.step(1e-4, 2)
+    classes, launches = ctx.profile_read()
+    # per RK stage: 2 types x (M0, grad, M0 grad, flux, div) + 2 face kernels
+    assert launches == 2 * 4 * 12
+    assert sum(c for _, c in classes.values()) == launches
+    ctx.profile(False)
+
+
+def test_full_size_boundary_layer_rhs():
+    """The full boundary-layer workload: 57,600 prisms + 118,800 tets at
+    p = 4, Navier-Stokes, Re = 3900, Ma = 0.2: every output of one RHS."""
+    m = synth.boundary_layer_box()
+    sol, ctx = make_pair(m, 4, **bl_params())
+    u = state(sol, "bl")
+    err = _check_rhs(sol, ctx, u)
+    assert math.isfinite(float(err.max()))

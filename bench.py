@@ -4,7 +4,8 @@
 Workload: compressible Navier-Stokes, p = 4, FP64, on a box
 [0,20] x [0,20] x [0,pi] with 32 stretched prism layers (57,600 prisms) on
 a no-slip wall under Kuhn tets (118,800 tets), Re = 3900, Ma = 0.2,
-uniform inflow plus a 1% seeded velocity perturbation: 42,390,000 DOF.
+uniform inflow plus a 1% seeded velocity perturbation, with a tanh wall
+profile of thickness 0.5 so that it satisfies no-slip: 42,390,000 DOF.
 One step = one classic RK4 step = 4 RHS evaluations (the whole hot path:
 interpolation, common solution, corrected gradients, fluxes, common
 fluxes, divergence + correction, register update).
@@ -43,6 +44,9 @@ WORKLOAD = "boundary-layer box NS p=4 FP64: 57,600 prisms + 118,800 tets, Re=390
 # a bounded sample of the same workload for the CPU oracle: the same
 # generator with 15 instead of 75 cells along x (1/5 of the elements)
 CPU_SAMPLE_NX = 15
+# the inflow carries a tanh(y/0.5) wall profile so the initial state
+# satisfies the no-slip condition
+WALL_DELTA = 0.5
 
 
 def flow_params():
@@ -180,7 +184,8 @@ def cpu_oracle_child(nrhs):
                  viscous=True, ldg_beta=prm["ldg_beta"], ldg_tau=prm["ldg_tau"],
                  rho_inf=prm["rho_inf"], vel_inf=prm["vel_inf"], p_inf=prm["p_inf"],
                  t_wall=prm["t_wall"])
-    u = sol.state_from_points(synth.perturbed_freestream(sol.upts_xyz_points(), seed=2))
+    u = sol.state_from_points(synth.perturbed_freestream(sol.upts_xyz_points(), seed=2,
+                                                         wall_delta=WALL_DELTA))
     times = []
     for _ in range(nrhs):
         t0 = time.perf_counter()
@@ -220,6 +225,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=75,
+                    help="cells along x (75 = the full workload; smaller for profiling)")
     ap.add_argument("--cpu-oracle-child", type=int, default=0)
     args = ap.parse_args()
 
@@ -254,7 +261,7 @@ def main():
 
     # CPU baseline first (child process, before any CUDA work in this one)
     cpu_base = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.nx == 75:
         try:
             cpu_base = cpu_baseline_entry(1)
         except Exception as e:  # reported, not fatal
@@ -273,10 +280,11 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    mesh = synth.boundary_layer_box()
+    mesh = synth.boundary_layer_box(nx=args.nx)
     ctx = fr.Context(mesh, ORDER, **flow_params())
     counts = [(ctx.info["n_tet"], ctx.info["nu_tet"]), (ctx.info["n_pri"], ctx.info["nu_pri"])]
-    u0 = points_to_public(synth.perturbed_freestream(ctx.upts_points(), seed=2), counts)
+    u0 = points_to_public(synth.perturbed_freestream(ctx.upts_points(), seed=2,
+                                                     wall_delta=WALL_DELTA), counts)
     dt = time_step_size(mesh, ORDER)
     ndof = ctx.ndof
 
@@ -360,19 +368,21 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": None, "kernel": dom}
-    all_gemm = sum(gemm_flops(ctx, k) for k in ("M0", "grad", "M0_grad", "div")) * 4 * args.steps
+    gemm_classes = ("M0", "grad", "M0_grad", "div")
+    all_gemm = sum(gemm_flops(ctx, k) for k in gemm_classes) * 4 * args.steps
     clocks = sampler.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "ndof": ndof, "rhs_per_step": 4, "dt": dt,
+        "config": {"workload": WORKLOAD if args.nx == 75 else WORKLOAD + f" (reduced: nx={args.nx})",
+                   "ndof": ndof, "rhs_per_step": 4, "dt": dt,
                    "l2": "inputs > L2 (state 339 MB per register, scratch > 4 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "state_finite_after_timed_steps": bool(state_ok)},
         "roofline": roof,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in classes.items()},
-        "gemm_fp64_tflops": all_gemm / (sum(classes[k][0] for k in ("M0", "grad", "M0_grad", "div")) * 1e-3) / 1e12,
+        "gemm_fp64_tflops": all_gemm / (sum(classes[k][0] for k in gemm_classes) * 1e-3) / 1e12,
         "cpu_baseline": cpu_base,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(ndof * 8),
                 "d2h_bytes_per_step": int(ndof * 8), "steps": e2e_steps},

@@ -162,8 +162,8 @@ int fr_reduce(fr_ctx *ctx, double *out, void *cuda_stream);
  *   2 M3   (nu x nf)        DG correction (lift) of flux-point jumps
  *   3 AGRAD (3*nu x (nu+nf)) [D | n^ (x) M3], corrected gradient operator
  *   4 ADIV (nu x (3*nu+nf)) [M1 - M3 M2 | M3] with the divergence
- *                           M1[j][(i,d)] = D[(j,d)][i] and
- *                           M2[f][(i,d)] = n^_d(f) M0[f][i]
+ *                           M1[j][(i,d)] = D[(j,d)][i] and the normal-flux
+ *                           interpolation M2[f][(i,d)] = n^_d(f) M0[f][i]
  *   5 W    (nu x 1)         quadrature weights of the solution points
  *   6 UPTS (nu x 3)         reference solution points
  *   7 FPTS (nf x 3)         reference flux points

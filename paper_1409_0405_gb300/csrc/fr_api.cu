@@ -7,8 +7,8 @@
 //   NS:   DUF = C - u_f at every flux point          (common solution)
 //         GU_t = (1/J) S^T [D | n^(x)M3] [U_t; DUF_t] (corrected gradient)
 //         GUF_t = M0 GU_t
-//   FT_t  = S (F_inv - F_vis) at solution points
-//   FC    = (common normal flux) |S^T n^| at every flux point
+//   FT_t  = S (F_inv - F_vis - F_inf) at solution points
+//   FC    = (common normal flux - F_inf.n) |S^T n^| at every flux point
 //   R_t   = -(1/J) [M1 - M3 M2 | M3] [FT_t; FC_t]   (+ fused RK4 update)
 // Internal layout of a state-like matrix: [point][variable][element], the
 // element index padded to np_t (a multiple of 32) and fastest, so every
@@ -123,6 +123,16 @@ Phys phys_of(const fr_ctx *c) {
     ph.p_inf = c->prm.p_inf;
     ph.t_wall = c->prm.t_wall;
     ph.viscous = c->prm.viscous;
+    {
+        const double r = c->prm.rho_inf, g = c->prm.gamma, pinf = c->prm.p_inf;
+        const double *v = c->prm.vel_inf;
+        const double E = pinf / (g - 1.0) + 0.5 * r * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int m = 0; m < 3; ++m) {
+            ph.fref[0][m] = r * v[m];
+            for (int a = 0; a < 3; ++a) ph.fref[1 + a][m] = r * v[a] * v[m] + (a == m ? pinf : 0.0);
+            ph.fref[4][m] = (E + pinf) * v[m];
+        }
+    }
     return ph;
 }
 

@@ -43,6 +43,11 @@ struct Phys {
     double gamma, mu, prandtl, beta, tau;
     double rho_inf, vinf[3], p_inf, t_wall;
     int viscous;
+    // inviscid flux of the far-field state, subtracted from every volume
+    // and common flux before the divergence (exact: the discrete divergence
+    // of a constant flux vanishes element by element), which removes the
+    // cancellation of the large constant pressure flux at low Mach number
+    double fref[5][3];
 };
 
 // Per-type field pointers (index 0 tet, 1 prism); nullptr for an absent type.

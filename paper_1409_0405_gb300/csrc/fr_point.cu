@@ -228,8 +228,9 @@ __global__ void k_common_flux(const Pairs P, const Bnd B, const Fields F, const 
         const double ma = P.maga[k], mb = P.magb[k];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            F.FC[ta][oa + v * npa] = fn[v] * ma;
-            F.FC[tb][ob + v * npb] = -fn[v] * mb;
+            const double f = fn[v] - (ph.fref[v][0] * n[0] + ph.fref[v][1] * n[1] + ph.fref[v][2] * n[2]);
+            F.FC[ta][oa + v * npa] = f * ma;
+            F.FC[tb][ob + v * npb] = -f * mb;
         }
         return;
     }
@@ -256,7 +257,8 @@ __global__ void k_common_flux(const Pairs P, const Bnd B, const Fields F, const 
         }
         const double mg = B.bmag[kb];
 #pragma unroll
-        for (int v = 0; v < V; ++v) F.FC[t][o + v * np] = fn[v] * mg;
+        for (int v = 0; v < V; ++v)
+            F.FC[t][o + v * np] = (fn[v] - (ph.fref[v][0] * n[0] + ph.fref[v][1] * n[1] + ph.fref[v][2] * n[2])) * mg;
     }
 }
 
@@ -292,6 +294,10 @@ __global__ void k_flux(int nu, int64_t ne, int64_t np, const double *__restrict_
 #pragma unroll
             for (int m = 0; m < 3; ++m) F[v][m] -= Fv[v][m];
     }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) F[v][m] -= ph.fref[v][m];
     double s[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];

@@ -11,10 +11,12 @@
 //   prism: tri x Legendre P_k(zeta);  quad faces: Legendre x Legendre.
 // They are polynomials in the reference coordinates; their derivatives are
 // taken exactly with forward-mode dual numbers (every evaluation point lies
-// off the collapsed edge), and each is normalised by its quadrature norm, so
-// the mass matrix is the identity up to rounding and every Vandermonde is
-// well conditioned.  Integrals use collapsed (Duffy) Gauss-Legendre rules
-// exact for the degrees involved.
+// off the collapsed edge), and each is normalised by its quadrature norm.
+// Integrals use collapsed (Duffy) Gauss-Legendre rules exact for the degrees
+// involved.  Everything is computed in double-double arithmetic and rounded
+// to double once, so the operators are correctly rounded: small operator
+// errors would otherwise show up as spurious jumps between neighbouring
+// elements, amplified by 1/h in thin wall layers.
 //
 // Operators (the paper casts each as a constant matrix A in C <- c1 A B + c2 C,
 // Sec. 2.1 Eq. 1; it writes out only M0, Table 2):
@@ -30,117 +32,144 @@
 #include <string>
 #include <vector>
 
+#include "dd.h"
 #include "fr_internal.h"
 
 namespace fr {
 namespace {
 
-const double TET_V[4][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
-const double PRI_V[6][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1},
-                            {-1, -1, 1},  {1, -1, 1},  {-1, 1, 1}};
+using R = DD;
+using Vec3 = std::array<R, 3>;
+
+const int TET_V[4][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+const int PRI_V[6][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}};
 const std::vector<std::vector<int>> TET_FACES = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
 const std::vector<std::vector<int>> PRI_FACES = {
     {0, 1, 2}, {3, 4, 5}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
 
-using Vec3 = std::array<double, 3>;
+// ---------------------------------------------------------------------------
+// Gauss-Legendre nodes/weights in double-double (Newton on P_n)
+void gl_dd(int n, std::vector<R> &x, std::vector<R> &w) {
+    x.assign(n, R(0.0));
+    w.assign(n, R(0.0));
+    const double pi = 3.14159265358979323846;
+    auto eval = [n](const R &z, R &pn, R &dpn) {
+        R p0(1.0), p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            R p2 = (R(2.0 * k - 1.0) * z * p1 - R(k - 1.0) * p0) / R((double)k);
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) {
+            p0 = R(1.0);
+            p1 = z;
+        }
+        pn = p1;
+        dpn = R((double)n) * (z * p1 - p0) / (z * z - R(1.0));
+    };
+    for (int i = 0; i < n; ++i) {
+        R z(-std::cos(pi * (i + 0.75) / (n + 0.5)));
+        for (int it = 0; it < 60; ++it) {
+            R pn, dpn;
+            eval(z, pn, dpn);
+            R dz = pn / dpn;
+            z -= dz;
+            if (std::fabs(dz.hi) < 1e-32) break;
+        }
+        R pn, dpn;
+        eval(z, pn, dpn);
+        x[i] = z;
+        w[i] = R(2.0) / ((R(1.0) - z * z) * dpn * dpn);
+    }
+}
 
+// ---------------------------------------------------------------------------
 struct Mat {
     int r = 0, c = 0;
-    std::vector<double> a;
+    std::vector<R> a;
     Mat() {}
-    Mat(int r_, int c_) : r(r_), c(c_), a((size_t)r_ * c_, 0.0) {}
-    double &operator()(int i, int j) { return a[(size_t)i * c + j]; }
-    double operator()(int i, int j) const { return a[(size_t)i * c + j]; }
+    Mat(int r_, int c_) : r(r_), c(c_), a((size_t)r_ * c_, R(0.0)) {}
+    R &operator()(int i, int j) { return a[(size_t)i * c + j]; }
+    const R &operator()(int i, int j) const { return a[(size_t)i * c + j]; }
 };
 
 Mat matmul(const Mat &A, const Mat &B) {
     Mat C(A.r, B.c);
     for (int i = 0; i < A.r; ++i)
         for (int k = 0; k < A.c; ++k) {
-            double aik = A(i, k);
-            if (aik == 0.0) continue;
+            const R aik = A(i, k);
+            if (aik.hi == 0.0) continue;
             for (int j = 0; j < B.c; ++j) C(i, j) += aik * B(k, j);
         }
     return C;
 }
 
-// Solve A X = B by LU with partial pivoting plus one step of iterative
-// refinement.  Returns false if A is singular.
+// Solve A X = B by LU with partial pivoting (double-double).
 bool solve(const Mat &A, const Mat &B, Mat &X) {
-    int n = A.r;
+    const int n = A.r;
     Mat LU = A;
     std::vector<int> piv(n);
     for (int i = 0; i < n; ++i) piv[i] = i;
     for (int k = 0; k < n; ++k) {
         int pr = k;
         for (int i = k + 1; i < n; ++i)
-            if (std::fabs(LU(i, k)) > std::fabs(LU(pr, k))) pr = i;
-        if (LU(pr, k) == 0.0) return false;
+            if (dd_abs(LU(i, k)) > dd_abs(LU(pr, k))) pr = i;
+        if (LU(pr, k).hi == 0.0) return false;
         if (pr != k) {
             for (int j = 0; j < n; ++j) std::swap(LU(k, j), LU(pr, j));
             std::swap(piv[k], piv[pr]);
         }
         for (int i = k + 1; i < n; ++i) {
             LU(i, k) /= LU(k, k);
-            double l = LU(i, k);
+            const R l = LU(i, k);
             for (int j = k + 1; j < n; ++j) LU(i, j) -= l * LU(k, j);
         }
     }
-    auto lu_solve = [&](const Mat &rhs, Mat &out) {
-        out = Mat(n, rhs.c);
-        for (int col = 0; col < rhs.c; ++col) {
-            std::vector<double> y(n);
-            for (int i = 0; i < n; ++i) {
-                double s = rhs(piv[i], col);
-                for (int j = 0; j < i; ++j) s -= LU(i, j) * y[j];
-                y[i] = s;
-            }
-            for (int i = n - 1; i >= 0; --i) {
-                double s = y[i];
-                for (int j = i + 1; j < n; ++j) s -= LU(i, j) * out(j, col);
-                out(i, col) = s / LU(i, i);
-            }
+    X = Mat(n, B.c);
+    for (int col = 0; col < B.c; ++col) {
+        std::vector<R> y(n);
+        for (int i = 0; i < n; ++i) {
+            R s = B(piv[i], col);
+            for (int j = 0; j < i; ++j) s -= LU(i, j) * y[j];
+            y[i] = s;
         }
-    };
-    lu_solve(B, X);
-    // one refinement step: X += A^{-1} (B - A X)
-    Mat AX = matmul(A, X);
-    Mat res(n, B.c);
-    for (size_t i = 0; i < res.a.size(); ++i) res.a[i] = B.a[i] - AX.a[i];
-    Mat dX;
-    lu_solve(res, dX);
-    for (size_t i = 0; i < X.a.size(); ++i) X.a[i] += dX.a[i];
+        for (int i = n - 1; i >= 0; --i) {
+            R s = y[i];
+            for (int j = i + 1; j < n; ++j) s -= LU(i, j) * X(j, col);
+            X(i, col) = s / LU(i, i);
+        }
+    }
     return true;
 }
 
 Mat identity(int n) {
     Mat I(n, n);
-    for (int i = 0; i < n; ++i) I(i, i) = 1.0;
+    for (int i = 0; i < n; ++i) I(i, i) = R(1.0);
     return I;
 }
 
 // Blyth-Pozrikidis barycentric coordinates of multi-index I from the 1-D
 // nodes v on [0, 1]: lambda_a = (1 + d v_{I_a} - sum_{b != a} v_{I_b}) / (d+1)
 template <int NB>
-std::array<double, NB> bp_bary(const std::array<int, NB> &I, const std::vector<double> &v) {
+std::array<R, NB> bp_bary(const std::array<int, NB> &I, const std::vector<R> &v) {
     const int d = NB - 1;
-    double tot = 0.0;
+    R tot(0.0);
     for (int a = 0; a < NB; ++a) tot += v[I[a]];
-    std::array<double, NB> lam;
-    for (int a = 0; a < NB; ++a) lam[a] = (1.0 + d * v[I[a]] - (tot - v[I[a]])) / (d + 1);
+    std::array<R, NB> lam;
+    for (int a = 0; a < NB; ++a) lam[a] = (R(1.0) + R((double)d) * v[I[a]] - (tot - v[I[a]])) / R(d + 1.0);
     return lam;
 }
 
-std::vector<double> gl01(int n) {
-    std::vector<double> x, w;
-    gauss_legendre(n, x, w);
-    for (auto &xi : x) xi = 0.5 * (xi + 1.0);
+std::vector<R> gl01(int n) {
+    std::vector<R> x, w;
+    gl_dd(n, x, w);
+    for (auto &xi : x) xi = R(0.5) * (xi + R(1.0));
     return x;
 }
 
-std::vector<std::array<double, 3>> tri_set(int p) {
-    std::vector<double> v = gl01(p + 1);
-    std::vector<std::array<double, 3>> out;
+std::vector<std::array<R, 3>> tri_set(int p) {
+    std::vector<R> v = gl01(p + 1);
+    std::vector<std::array<R, 3>> out;
     for (int j = 0; j <= p; ++j)
         for (int i = 0; i <= p - j; ++i) out.push_back(bp_bary<3>({p - i - j, i, j}, v));
     return out;
@@ -148,40 +177,43 @@ std::vector<std::array<double, 3>> tri_set(int p) {
 
 // forward-mode dual number with three partial derivatives
 struct Dual {
-    double v, d[3];
+    R v, d[3];
 };
-inline Dual dc(double c) { return {c, {0, 0, 0}}; }
-inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}}; }
-inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1], a.d[2] - b.d[2]}}; }
-inline Dual operator*(Dual a, Dual b) {
-    return {a.v * b.v, {a.d[0] * b.v + a.v * b.d[0], a.d[1] * b.v + a.v * b.d[1], a.d[2] * b.v + a.v * b.d[2]}};
+inline Dual dc(const R &c) { return {c, {R(0.0), R(0.0), R(0.0)}}; }
+inline Dual operator+(const Dual &a, const Dual &b) {
+    return {a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}};
 }
-inline Dual operator/(Dual a, Dual b) {
-    const double q = a.v / b.v;
+inline Dual operator-(const Dual &a, const Dual &b) {
+    return {a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1], a.d[2] - b.d[2]}};
+}
+inline Dual operator*(const Dual &a, const Dual &b) {
+    return {a.v * b.v,
+            {a.d[0] * b.v + a.v * b.d[0], a.d[1] * b.v + a.v * b.d[1], a.d[2] * b.v + a.v * b.d[2]}};
+}
+inline Dual operator/(const Dual &a, const Dual &b) {
+    const R q = a.v / b.v;
     return {q, {(a.d[0] - q * b.d[0]) / b.v, (a.d[1] - q * b.d[1]) / b.v, (a.d[2] - q * b.d[2]) / b.v}};
 }
-inline Dual operator*(double c, Dual a) { return {c * a.v, {c * a.d[0], c * a.d[1], c * a.d[2]}}; }
-inline Dual operator+(double c, Dual a) { return {c + a.v, {a.d[0], a.d[1], a.d[2]}}; }
-inline Dual operator-(double c, Dual a) { return {c - a.v, {-a.d[0], -a.d[1], -a.d[2]}}; }
-Dual dpow(Dual a, int n) {
-    Dual r = dc(1.0);
+inline Dual scale(const R &c, const Dual &a) { return {c * a.v, {c * a.d[0], c * a.d[1], c * a.d[2]}}; }
+Dual dpow(const Dual &a, int n) {
+    Dual r = dc(R(1.0));
     for (int i = 0; i < n; ++i) r = r * a;
     return r;
 }
 
 // Jacobi polynomial P_n^(al, 0)(x) (unnormalised three-term recurrence)
-Dual jacobi(int n, double al, Dual x) {
+Dual jacobi(int n, double al, const Dual &x) {
     const double be = 0.0;
-    Dual p0 = dc(1.0);
+    Dual p0 = dc(R(1.0));
     if (n == 0) return p0;
-    Dual p1 = 0.5 * ((al + be + 2.0) * x) + dc(0.5 * (al - be));
+    Dual p1 = scale(R(0.5 * (al + be + 2.0)), x) + dc(R(0.5 * (al - be)));
     for (int k = 2; k <= n; ++k) {
         const double s = 2.0 * k + al + be;
-        const double A = 2.0 * k * (k + al + be) * (s - 2.0);
-        const double B = (s - 1.0) * s * (s - 2.0);
-        const double Cc = (s - 1.0) * (al * al - be * be);
-        const double Dd = 2.0 * (k + al - 1.0) * (k + be - 1.0) * s;
-        Dual p2 = (1.0 / A) * ((B * x + dc(Cc)) * p1 - Dd * p0);
+        const R A(2.0 * k * (k + al + be) * (s - 2.0));
+        const R B((s - 1.0) * s * (s - 2.0));
+        const R Cc((s - 1.0) * (al * al - be * be));
+        const R Dd(2.0 * (k + al - 1.0) * (k + be - 1.0) * s);
+        Dual p2 = scale(R(1.0) / A, (scale(B, x) + dc(Cc)) * p1 - scale(Dd, p0));
         p0 = p1;
         p1 = p2;
     }
@@ -191,7 +223,7 @@ Dual jacobi(int n, double al, Dual x) {
 struct Basis {
     int etype, p;
     std::vector<std::array<int, 3>> ex;
-    std::vector<double> scale;  // 1 / quadrature norm of each function
+    std::vector<R> scl;  // 1 / quadrature norm of each function
     explicit Basis(int et, int p_) : etype(et), p(p_) {
         for (int c = 0; c <= p; ++c)
             for (int b = 0; b <= p; ++b)
@@ -199,31 +231,34 @@ struct Basis {
                     bool in = (etype == FR_ETYPE_TET) ? (a + b + c <= p) : (a + b <= p);
                     if (in) ex.push_back({a, b, c});
                 }
-        scale.assign(ex.size(), 1.0);
+        scl.assign(ex.size(), R(1.0));
     }
     int size() const { return (int)ex.size(); }
     Dual raw(int m, const Vec3 &x) const {
-        Dual xi{x[0], {1, 0, 0}}, eta{x[1], {0, 1, 0}}, zeta{x[2], {0, 0, 1}};
+        const Dual one = dc(R(1.0));
+        Dual xi{x[0], {R(1.0), R(0.0), R(0.0)}}, eta{x[1], {R(0.0), R(1.0), R(0.0)}},
+            zeta{x[2], {R(0.0), R(0.0), R(1.0)}};
         const int i = ex[m][0], j = ex[m][1], k = ex[m][2];
+        const Dual half = dc(R(0.5)), two = dc(R(2.0));
         if (etype == FR_ETYPE_TET) {
-            Dual a = (2.0 * (1.0 + xi)) / (dc(0.0) - eta - zeta) - dc(1.0);
-            Dual b = (2.0 * (1.0 + eta)) / (1.0 - zeta) - dc(1.0);
+            Dual a = (two * (one + xi)) / (dc(R(0.0)) - eta - zeta) - one;
+            Dual b = (two * (one + eta)) / (one - zeta) - one;
             Dual c = zeta;
-            return jacobi(i, 0, a) * dpow(0.5 * (1.0 - b), i) * jacobi(j, 2 * i + 1, b) *
-                   dpow(0.5 * (1.0 - c), i + j) * jacobi(k, 2 * i + 2 * j + 2, c);
+            return jacobi(i, 0, a) * dpow(half * (one - b), i) * jacobi(j, 2 * i + 1, b) *
+                   dpow(half * (one - c), i + j) * jacobi(k, 2 * i + 2 * j + 2, c);
         }
-        Dual a = (2.0 * (1.0 + xi)) / (1.0 - eta) - dc(1.0);
+        Dual a = (two * (one + xi)) / (one - eta) - one;
         Dual b = eta;
-        return jacobi(i, 0, a) * dpow(0.5 * (1.0 - b), i) * jacobi(j, 2 * i + 1, b) * jacobi(k, 0, zeta);
+        return jacobi(i, 0, a) * dpow(half * (one - b), i) * jacobi(j, 2 * i + 1, b) * jacobi(k, 0, zeta);
     }
-    // values (and optionally the three derivatives) of every basis function at x
-    void eval(const Vec3 &x, double *phi, double *dphi /* size 3 x n or null */) const {
+    // values (and optionally the three derivatives, [d][m]) at x
+    void eval(const Vec3 &x, R *phi, R *dphi) const {
         const int n = size();
         for (int m = 0; m < n; ++m) {
             Dual r = raw(m, x);
-            phi[m] = scale[m] * r.v;
+            phi[m] = scl[m] * r.v;
             if (dphi)
-                for (int d = 0; d < 3; ++d) dphi[d * n + m] = scale[m] * r.d[d];
+                for (int d = 0; d < 3; ++d) dphi[d * n + m] = scl[m] * r.d[d];
         }
     }
 };
@@ -237,54 +272,55 @@ struct FaceBasis {
             for (int a = 0; a <= p; ++a)
                 if (!tri || a + b <= p) ex.push_back({a, b});
     }
-    void eval(double r, double s, double *psi) const {
-        Dual R{r, {1, 0, 0}}, S{s, {0, 1, 0}};
+    void eval(const R &r, const R &s, R *psi) const {
+        const Dual one = dc(R(1.0)), two = dc(R(2.0)), half = dc(R(0.5));
+        Dual Rr{r, {R(1.0), R(0.0), R(0.0)}}, S{s, {R(0.0), R(1.0), R(0.0)}};
         for (size_t m = 0; m < ex.size(); ++m) {
             const int i = ex[m][0], j = ex[m][1];
             if (tri) {
-                Dual a = (2.0 * (1.0 + R)) / (1.0 - S) - dc(1.0);
-                psi[m] = (jacobi(i, 0, a) * dpow(0.5 * (1.0 - S), i) * jacobi(j, 2 * i + 1, S)).v;
+                Dual a = (two * (one + Rr)) / (one - S) - one;
+                psi[m] = (jacobi(i, 0, a) * dpow(half * (one - S), i) * jacobi(j, 2 * i + 1, S)).v;
             } else {
-                psi[m] = (jacobi(i, 0, R) * jacobi(j, 0, S)).v;
+                psi[m] = (jacobi(i, 0, Rr) * jacobi(j, 0, S)).v;
             }
         }
     }
 };
 
-// Collapsed Gauss rules.  Each returns points in the relevant parameter
-// domain and weights summing to its measure.
-void rule_unit_tri(int n, std::vector<std::array<double, 2>> &pts, std::vector<double> &wts) {
-    std::vector<double> x, w;
-    gauss_legendre(n, x, w);
+// Collapsed Gauss rules (points in the parameter domain, weights summing
+// to its measure).
+void rule_unit_tri(int n, std::vector<std::array<R, 2>> &pts, std::vector<R> &wts) {
+    std::vector<R> x, w;
+    gl_dd(n, x, w);
     for (int a = 0; a < n; ++a)
         for (int b = 0; b < n; ++b) {
-            double u = 0.5 * (x[a] + 1), v = 0.5 * (x[b] + 1);
-            double wu = 0.5 * w[a], wv = 0.5 * w[b];
-            pts.push_back({u, v * (1 - u)});
-            wts.push_back(wu * wv * (1 - u));
+            R u = R(0.5) * (x[a] + R(1.0)), v = R(0.5) * (x[b] + R(1.0));
+            R wu = R(0.5) * w[a], wv = R(0.5) * w[b];
+            pts.push_back({u, v * (R(1.0) - u)});
+            wts.push_back(wu * wv * (R(1.0) - u));
         }
 }
 
-void rule_volume(int etype, int n, std::vector<Vec3> &pts, std::vector<double> &wts) {
-    std::vector<double> x, w;
-    gauss_legendre(n, x, w);
+void rule_volume(int etype, int n, std::vector<Vec3> &pts, std::vector<R> &wts) {
+    std::vector<R> x, w;
+    gl_dd(n, x, w);
     if (etype == FR_ETYPE_TET) {
         for (int a = 0; a < n; ++a)
             for (int b = 0; b < n; ++b)
                 for (int c = 0; c < n; ++c) {
-                    double u = 0.5 * (x[a] + 1), v = 0.5 * (x[b] + 1), t = 0.5 * (x[c] + 1);
-                    double px = u, py = v * (1 - u), pz = t * (1 - u) * (1 - v);
-                    pts.push_back({2 * px - 1, 2 * py - 1, 2 * pz - 1});
-                    wts.push_back(8.0 * 0.125 * w[a] * w[b] * w[c] * (1 - u) * (1 - u) * (1 - v));
+                    R u = R(0.5) * (x[a] + R(1.0)), v = R(0.5) * (x[b] + R(1.0)), t = R(0.5) * (x[c] + R(1.0));
+                    R px = u, py = v * (R(1.0) - u), pz = t * (R(1.0) - u) * (R(1.0) - v);
+                    pts.push_back({R(2.0) * px - R(1.0), R(2.0) * py - R(1.0), R(2.0) * pz - R(1.0)});
+                    wts.push_back(w[a] * w[b] * w[c] * (R(1.0) - u) * (R(1.0) - u) * (R(1.0) - v));
                 }
     } else {
-        std::vector<std::array<double, 2>> tp;
-        std::vector<double> tw;
+        std::vector<std::array<R, 2>> tp;
+        std::vector<R> tw;
         rule_unit_tri(n, tp, tw);
         for (int c = 0; c < n; ++c)
             for (size_t q = 0; q < tp.size(); ++q) {
-                pts.push_back({2 * tp[q][0] - 1, 2 * tp[q][1] - 1, x[c]});
-                wts.push_back(4.0 * tw[q] * w[c]);
+                pts.push_back({R(2.0) * tp[q][0] - R(1.0), R(2.0) * tp[q][1] - R(1.0), x[c]});
+                wts.push_back(R(4.0) * tw[q] * w[c]);
             }
     }
 }
@@ -293,44 +329,20 @@ Vec3 vsub(const Vec3 &a, const Vec3 &b) { return {a[0] - b[0], a[1] - b[1], a[2]
 Vec3 vcross(const Vec3 &a, const Vec3 &b) {
     return {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
 }
-double vnorm(const Vec3 &a) { return std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+
+std::vector<double> to_d(const std::vector<R> &v) {
+    std::vector<double> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = v[i].to_double();
+    return o;
+}
 
 }  // namespace
 
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
-    x.assign(n, 0.0);
-    w.assign(n, 0.0);
-    const double pi = 3.14159265358979323846;
-    for (int i = 0; i < n; ++i) {
-        double z = -std::cos(pi * (i + 0.75) / (n + 0.5));
-        double dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = z;
-            for (int k = 2; k <= n; ++k) {
-                double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            if (n == 1) {
-                p0 = 1.0;
-                p1 = z;
-            }
-            dp = n * (z * p1 - p0) / (z * z - 1.0);
-            double dz = p1 / dp;
-            z -= dz;
-            if (std::fabs(dz) < 1e-16) break;
-        }
-        // recompute derivative at the converged root for the weight
-        double p0 = 1.0, p1 = z;
-        for (int k = 2; k <= n; ++k) {
-            double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = n * (z * p1 - p0) / (z * z - 1.0);
-        x[i] = z;
-        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-    }
+    std::vector<R> xd, wd;
+    gl_dd(n, xd, wd);
+    x = to_d(xd);
+    w = to_d(wd);
 }
 
 int nupts_of(int etype, int p) {
@@ -354,21 +366,21 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
     const int nverts = tet ? 4 : 6;
     std::vector<Vec3> V(nverts);
     for (int i = 0; i < nverts; ++i)
-        for (int k = 0; k < 3; ++k) V[i][k] = tet ? TET_V[i][k] : PRI_V[i][k];
+        for (int k = 0; k < 3; ++k) V[i][k] = R((double)(tet ? TET_V[i][k] : PRI_V[i][k]));
     o.face_verts = tet ? TET_FACES : PRI_FACES;
     o.nfaces = (int)o.face_verts.size();
 
     // ---- solution points
     std::vector<Vec3> up;
-    std::vector<double> glx, glw;
-    gauss_legendre(p + 1, glx, glw);
+    std::vector<R> glx, glw;
+    gl_dd(p + 1, glx, glw);
     if (tet) {
-        std::vector<double> v = gl01(p + 1);
+        std::vector<R> v = gl01(p + 1);
         for (int k = 0; k <= p; ++k)
             for (int j = 0; j <= p - k; ++j)
                 for (int i = 0; i <= p - k - j; ++i) {
                     auto lam = bp_bary<4>({p - i - j - k, i, j, k}, v);
-                    Vec3 x = {0, 0, 0};
+                    Vec3 x = {R(0.0), R(0.0), R(0.0)};
                     for (int a = 0; a < 4; ++a)
                         for (int c = 0; c < 3; ++c) x[c] += lam[a] * V[a][c];
                     up.push_back(x);
@@ -377,7 +389,7 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
         auto tri = tri_set(p);
         for (int c = 0; c <= p; ++c)
             for (auto &lam : tri) {
-                double xi = 0, eta = 0;
+                R xi(0.0), eta(0.0);
                 for (int a = 0; a < 3; ++a) {
                     xi += lam[a] * V[a][0];
                     eta += lam[a] * V[a][1];
@@ -389,28 +401,28 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
 
     // ---- flux points, face parameters, normals, areas
     std::vector<Vec3> fp;
-    std::vector<std::array<double, 2>> fparam;
+    std::vector<std::array<R, 2>> fparam;
     std::vector<Vec3> face_n(o.nfaces);
-    std::vector<double> face_area(o.nfaces);
+    std::vector<R> face_area(o.nfaces);
     o.face_fpts.assign(o.nfaces, {});
-    Vec3 cen_e = {0, 0, 0};
+    Vec3 cen_e = {R(0.0), R(0.0), R(0.0)};
     for (auto &v : V)
-        for (int c = 0; c < 3; ++c) cen_e[c] += v[c] / nverts;
+        for (int c = 0; c < 3; ++c) cen_e[c] += v[c] / R((double)nverts);
     for (int fi = 0; fi < o.nfaces; ++fi) {
         const auto &fv = o.face_verts[fi];
         const bool tri = fv.size() == 3;
         Vec3 A = V[fv[0]], B = V[fv[1]], C = V[fv[2]];
         Vec3 Dq = tri ? C : V[fv[3]];
         Vec3 cr = vcross(vsub(B, A), vsub(Dq, A));
-        double nn = vnorm(cr);
-        face_area[fi] = tri ? 0.5 * nn : nn;
+        R nn = dd_sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        face_area[fi] = tri ? R(0.5) * nn : nn;
         Vec3 n = {cr[0] / nn, cr[1] / nn, cr[2] / nn};
-        Vec3 cen_f = {0, 0, 0};
+        Vec3 cen_f = {R(0.0), R(0.0), R(0.0)};
         for (int vi : fv)
-            for (int c = 0; c < 3; ++c) cen_f[c] += V[vi][c] / fv.size();
-        double s = 0;
+            for (int c = 0; c < 3; ++c) cen_f[c] += V[vi][c] / R((double)fv.size());
+        R s(0.0);
         for (int c = 0; c < 3; ++c) s += (cen_f[c] - cen_e[c]) * n[c];
-        if (s < 0)
+        if (s.hi < 0)
             for (int c = 0; c < 3; ++c) n[c] = -n[c];
         face_n[fi] = n;
         if (tri) {
@@ -419,17 +431,18 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
                 for (int c = 0; c < 3; ++c) x[c] = lam[0] * A[c] + lam[1] * B[c] + lam[2] * C[c];
                 o.face_fpts[fi].push_back((int)fp.size());
                 fp.push_back(x);
-                fparam.push_back({2 * lam[1] - 1, 2 * lam[2] - 1});
+                fparam.push_back({R(2.0) * lam[1] - R(1.0), R(2.0) * lam[2] - R(1.0)});
             }
         } else {
             Vec3 Dv = V[fv[3]];
             for (int b = 0; b <= p; ++b)
                 for (int a = 0; a <= p; ++a) {
-                    double s_ = glx[a], t_ = glx[b];
+                    const R s_ = glx[a], t_ = glx[b];
+                    const R one(1.0), q(0.25);
                     Vec3 x;
                     for (int c = 0; c < 3; ++c)
-                        x[c] = 0.25 * (A[c] * (1 - s_) * (1 - t_) + B[c] * (1 + s_) * (1 - t_) +
-                                       C[c] * (1 + s_) * (1 + t_) + Dv[c] * (1 - s_) * (1 + t_));
+                        x[c] = q * (A[c] * (one - s_) * (one - t_) + B[c] * (one + s_) * (one - t_) +
+                                    C[c] * (one + s_) * (one + t_) + Dv[c] * (one - s_) * (one + t_));
                     o.face_fpts[fi].push_back((int)fp.size());
                     fp.push_back(x);
                     fparam.push_back({s_, t_});
@@ -448,13 +461,13 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
     o.fface.resize(nf);
     o.fnorm.resize(3 * nf);
     for (int j = 0; j < nu; ++j)
-        for (int c = 0; c < 3; ++c) o.upts[3 * j + c] = up[j][c];
+        for (int c = 0; c < 3; ++c) o.upts[3 * j + c] = up[j][c].to_double();
     for (int fi = 0; fi < o.nfaces; ++fi)
         for (int f : o.face_fpts[fi]) {
             o.fface[f] = fi;
             for (int c = 0; c < 3; ++c) {
-                o.fpts[3 * f + c] = fp[f][c];
-                o.fnorm[3 * f + c] = face_n[fi][c];
+                o.fpts[3 * f + c] = fp[f][c].to_double();
+                o.fnorm[3 * f + c] = face_n[fi][c].to_double();
             }
         }
 
@@ -465,20 +478,20 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
         return FR_ERR_ARG;
     }
     std::vector<Vec3> qp;
-    std::vector<double> qw;
+    std::vector<R> qw;
     rule_volume(etype, p + 3, qp, qw);
+    std::vector<R> phi(nu), dphi(3 * nu);
     {
-        std::vector<double> nrm(nu, 0.0), v(nu);
+        std::vector<R> nrm(nu, R(0.0));
         for (size_t q = 0; q < qp.size(); ++q) {
-            B.eval(qp[q], v.data(), nullptr);
-            for (int m = 0; m < nu; ++m) nrm[m] += qw[q] * v[m] * v[m];
+            B.eval(qp[q], phi.data(), nullptr);
+            for (int m = 0; m < nu; ++m) nrm[m] += qw[q] * phi[m] * phi[m];
         }
-        for (int m = 0; m < nu; ++m) B.scale[m] = 1.0 / std::sqrt(nrm[m]);
+        for (int m = 0; m < nu; ++m) B.scl[m] = R(1.0) / dd_sqrt(nrm[m]);
     }
 
     // ---- Vandermonde, interpolation, derivatives
     Mat Vm(nu, nu), Vd[3] = {Mat(nu, nu), Mat(nu, nu), Mat(nu, nu)};
-    std::vector<double> phi(nu), dphi(3 * nu);
     for (int j = 0; j < nu; ++j) {
         B.eval(up[j], phi.data(), dphi.data());
         for (int m = 0; m < nu; ++m) {
@@ -501,12 +514,13 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
 
     // ---- mass matrix (the identity up to rounding) and basis integrals
     Mat Mass(nu, nu);
-    std::vector<double> intphi(nu, 0.0);
+    std::vector<R> intphi(nu, R(0.0));
     for (size_t q = 0; q < qp.size(); ++q) {
         B.eval(qp[q], phi.data(), nullptr);
         for (int m = 0; m < nu; ++m) {
             intphi[m] += qw[q] * phi[m];
-            for (int n2 = 0; n2 < nu; ++n2) Mass(m, n2) += qw[q] * phi[m] * phi[n2];
+            const R wp = qw[q] * phi[m];
+            for (int n2 = 0; n2 < nu; ++n2) Mass(m, n2) += wp * phi[n2];
         }
     }
 
@@ -523,7 +537,7 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
             return FR_ERR_ARG;
         }
         Mat W(nk, nk);
-        std::vector<double> psi(nk);
+        std::vector<R> psi(nk);
         for (int k = 0; k < nk; ++k) {
             FB.eval(fparam[idx[k]][0], fparam[idx[k]][1], psi.data());
             for (int q = 0; q < nk; ++q) W(k, q) = psi[q];
@@ -533,49 +547,51 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
             err = "build_ref_ops: singular face Vandermonde";
             return FR_ERR_ARG;
         }
-        // face quadrature in the parameter domain
-        std::vector<std::array<double, 2>> rp;
-        std::vector<double> rw;
+        std::vector<std::array<R, 2>> rp;
+        std::vector<R> rw;
         const int nq = p + 3;
         if (tri) {
-            std::vector<std::array<double, 2>> tp;
-            std::vector<double> tw;
+            std::vector<std::array<R, 2>> tp;
+            std::vector<R> tw;
             rule_unit_tri(nq, tp, tw);
             for (size_t q = 0; q < tp.size(); ++q) {
-                rp.push_back({2 * tp[q][0] - 1, 2 * tp[q][1] - 1});
-                rw.push_back(4.0 * tw[q]);
+                rp.push_back({R(2.0) * tp[q][0] - R(1.0), R(2.0) * tp[q][1] - R(1.0)});
+                rw.push_back(R(4.0) * tw[q]);
             }
         } else {
-            std::vector<double> x, w;
-            gauss_legendre(nq, x, w);
+            std::vector<R> x, w;
+            gl_dd(nq, x, w);
             for (int a = 0; a < nq; ++a)
                 for (int b = 0; b < nq; ++b) {
                     rp.push_back({x[a], x[b]});
                     rw.push_back(w[a] * w[b]);
                 }
         }
-        const double scale = face_area[fi] / (tri ? 2.0 : 4.0);
-        Vec3 A = V[fv[0]], Bv = V[fv[1]], C = V[fv[2]];
-        Vec3 Dv = tri ? C : V[fv[3]];
+        const R scale = face_area[fi] / R(tri ? 2.0 : 4.0);
+        const Vec3 A = V[fv[0]], Bv = V[fv[1]], C = V[fv[2]];
+        const Vec3 Dv = tri ? C : V[fv[3]];
+        const R one(1.0), q4(0.25), half(0.5);
         for (size_t q = 0; q < rp.size(); ++q) {
-            double r = rp[q][0], s = rp[q][1];
+            const R r = rp[q][0], s = rp[q][1];
             Vec3 x;
             if (tri) {
-                double l1 = 0.5 * (r + 1), l2 = 0.5 * (s + 1), l0 = 1 - l1 - l2;
+                R l1 = half * (r + one), l2 = half * (s + one), l0 = one - l1 - l2;
                 for (int c = 0; c < 3; ++c) x[c] = l0 * A[c] + l1 * Bv[c] + l2 * C[c];
             } else {
                 for (int c = 0; c < 3; ++c)
-                    x[c] = 0.25 * (A[c] * (1 - r) * (1 - s) + Bv[c] * (1 + r) * (1 - s) +
-                                   C[c] * (1 + r) * (1 + s) + Dv[c] * (1 - r) * (1 + s));
+                    x[c] = q4 * (A[c] * (one - r) * (one - s) + Bv[c] * (one + r) * (one - s) +
+                                 C[c] * (one + r) * (one + s) + Dv[c] * (one - r) * (one + s));
             }
             FB.eval(r, s, psi.data());
-            std::vector<double> ell(nk, 0.0);
+            std::vector<R> ell(nk, R(0.0));
             for (int k = 0; k < nk; ++k)
                 for (int qq = 0; qq < nk; ++qq) ell[k] += psi[qq] * Winv(qq, k);
             B.eval(x, phi.data(), nullptr);
-            double wq = rw[q] * scale;
-            for (int m = 0; m < nu; ++m)
-                for (int k = 0; k < nk; ++k) Bf(m, idx[k]) += wq * phi[m] * ell[k];
+            const R wq = rw[q] * scale;
+            for (int m = 0; m < nu; ++m) {
+                const R wp = wq * phi[m];
+                for (int k = 0; k < nk; ++k) Bf(m, idx[k]) += wp * ell[k];
+            }
         }
     }
     Mat Cc;
@@ -585,16 +601,19 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
     }
     Mat M3 = matmul(Vm, Cc);
 
-    // ---- store
-    o.M0 = M0.a;
-    o.M3 = M3.a;
+    // ---- store (rounded once to double)
+    o.M0 = to_d(M0.a);
+    o.M3 = to_d(M3.a);
     o.D.assign((size_t)3 * nu * nu, 0.0);
     for (int j = 0; j < nu; ++j)
         for (int d = 0; d < 3; ++d)
-            for (int i = 0; i < nu; ++i) o.D[((size_t)(j * 3 + d)) * nu + i] = Dm[d](j, i);
+            for (int i = 0; i < nu; ++i) o.D[((size_t)(j * 3 + d)) * nu + i] = Dm[d](j, i).to_double();
     o.W.assign(nu, 0.0);
-    for (int j = 0; j < nu; ++j)
-        for (int m = 0; m < nu; ++m) o.W[j] += intphi[m] * Vinv(m, j);
+    for (int j = 0; j < nu; ++j) {
+        R s(0.0);
+        for (int m = 0; m < nu; ++m) s += intphi[m] * Vinv(m, j);
+        o.W[j] = s.to_double();
+    }
 
     // corrected-gradient operator [D | n^ (x) M3], rows (j, d)
     const int kg = nu + nf;
@@ -602,21 +621,22 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
     for (int j = 0; j < nu; ++j)
         for (int d = 0; d < 3; ++d) {
             double *row = &o.AGRAD[((size_t)(j * 3 + d)) * kg];
-            for (int i = 0; i < nu; ++i) row[i] = Dm[d](j, i);
-            for (int f = 0; f < nf; ++f) row[nu + f] = o.fnorm[3 * f + d] * M3(j, f);
+            for (int i = 0; i < nu; ++i) row[i] = Dm[d](j, i).to_double();
+            for (int f = 0; f < nf; ++f) row[nu + f] = (face_n[o.fface[f]][d] * M3(j, f)).to_double();
         }
-    // divergence-plus-correction operator [M1 - M3 M2 | M3]
+    // divergence-plus-correction operator [M1 - M3 M2 | M3]; the product
+    // M3 M2 (M2 = n^ (x) M0) is formed in double-double before rounding
     const int kd = 3 * nu + nf;
     o.ADIV.assign((size_t)nu * kd, 0.0);
     for (int j = 0; j < nu; ++j) {
         double *row = &o.ADIV[(size_t)j * kd];
         for (int i = 0; i < nu; ++i)
             for (int d = 0; d < 3; ++d) {
-                double s = Dm[d](j, i);
-                for (int f = 0; f < nf; ++f) s -= M3(j, f) * o.fnorm[3 * f + d] * M0(f, i);
-                row[i * 3 + d] = s;
+                R s = Dm[d](j, i);
+                for (int f = 0; f < nf; ++f) s -= M3(j, f) * face_n[o.fface[f]][d] * M0(f, i);
+                row[i * 3 + d] = s.to_double();
             }
-        for (int f = 0; f < nf; ++f) row[3 * nu + f] = M3(j, f);
+        for (int f = 0; f < nf; ++f) row[3 * nu + f] = M3(j, f).to_double();
     }
     return FR_OK;
 }

@@ -75,11 +75,16 @@ def uniform_state(xyz, rho=1.0, vel=(1.0, 0.0, 0.0), p=None, gamma=1.4,
 
 
 def perturbed_freestream(xyz, seed=2, gamma=1.4, mach=0.2, amp=0.01,
-                         lengths=(20.0, 20.0, math.pi), nmodes=8):
+                         lengths=(20.0, 20.0, math.pi), nmodes=8, wall_delta=None):
     """Uniform flow rho=1, v=(1,0,0), p=1/(gamma Ma^2) plus a smooth seeded
     velocity perturbation amp * sum_k a_k d_k sin(k.x + phi_k), with
     sum a_k = 1, random unit directions d_k, random phases, and integer
-    wavenumbers per box length (so the field is periodic in every axis)."""
+    wavenumbers per box length (so the field is periodic in every axis).
+
+    wall_delta: if given, the whole velocity is multiplied by
+    tanh(y / wall_delta), so the state satisfies the no-slip condition on a
+    wall at y = 0 (a boundary-layer profile of thickness ~wall_delta);
+    None gives the impulsive start (slip at the wall)."""
     xyz = np.asarray(xyz, dtype=np.float64)
     rng = np.random.Generator(np.random.PCG64(seed))
     a = rng.uniform(0.0, 1.0, nmodes)
@@ -95,7 +100,10 @@ def perturbed_freestream(xyz, seed=2, gamma=1.4, mach=0.2, amp=0.01,
         dv += amp * a[k] * s[..., None] * d[k]
     rho = np.ones(xyz.shape[:-1])
     p = np.full(xyz.shape[:-1], 1.0 / (gamma * mach * mach))
-    return _conserved(rho, 1.0 + dv[..., 0], dv[..., 1], dv[..., 2], p, gamma)
+    vel = np.stack([1.0 + dv[..., 0], dv[..., 1], dv[..., 2]], axis=-1)
+    if wall_delta is not None:
+        vel = vel * np.tanh(xyz[..., 1] / wall_delta)[..., None]
+    return _conserved(rho, vel[..., 0], vel[..., 1], vel[..., 2], p, gamma)
 
 
 def random_smooth_state(xyz, seed=0, gamma=1.4, amp=0.1, lengths=(10.0, 10.0, 10.0)):

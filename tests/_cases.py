@@ -7,6 +7,8 @@ import synth
 from oracle.solver import Solver
 
 GAMMA = 1.4
+# boundary-layer thickness of the wall-consistent initial profile
+BL_DELTA = 0.5
 
 
 def library():
@@ -41,6 +43,8 @@ def state(sol, kind, seed=0):
     elif kind == "smooth":
         q = synth.random_smooth_state(xyz, seed=seed)
     elif kind == "bl":
+        q = synth.perturbed_freestream(xyz, seed=2, wall_delta=BL_DELTA)
+    elif kind == "impulsive":
         q = synth.perturbed_freestream(xyz, seed=2)
     elif kind == "tgv":
         q = synth.taylor_green(xyz)
@@ -69,3 +73,33 @@ def gpu_rhs(ctx, u):
     ctx.rhs(ut.data_ptr(), rt.data_ptr(), s.cuda_stream)
     torch.cuda.synchronize()
     return rt.cpu().numpy()
+
+
+def to_longdouble(sol):
+    """Switch an oracle instance to numpy extended precision (used only to
+    measure the FP64 rounding floor of a case)."""
+    ld = np.longdouble
+    for t in sol.types:
+        op = sol.m.ops[t]
+        for k in ("M0", "D", "M3", "fnorm", "w", "fw"):
+            setattr(op, k, getattr(op, k).astype(ld))
+        sol.m.J[t] = sol.m.J[t].astype(ld)
+        sol.m.S[t] = sol.m.S[t].astype(ld)
+    sol.m.gn = sol.m.gn.astype(ld)
+    sol.m.gmag = sol.m.gmag.astype(ld)
+    sol.na = sol.na.astype(ld)
+    return sol
+
+
+def per_quantity_rel_err(sol, ref, got):
+    """Frame-invariant relative error per conserved quantity:
+    [mass, momentum (Euclidean norm of the 3-vector), energy], each
+    max over points |got - ref| / max over points |ref|."""
+    r = sol.split(np.asarray(ref, dtype=np.float64))
+    g = sol.split(np.asarray(got, dtype=np.float64))
+    out = []
+    for sl in (slice(0, 1), slice(1, 4), slice(4, 5)):
+        num = max(float(np.max(np.linalg.norm(g[t][:, sl] - r[t][:, sl], axis=1))) for t in sol.types)
+        den = max(float(np.max(np.linalg.norm(r[t][:, sl], axis=1))) for t in sol.types)
+        out.append(num / den if den > 0 else num)
+    return np.array(out)

@@ -10,6 +10,9 @@
 //   FT_t  = S (F_inv - F_vis - F_inf) at solution points
 //   FC    = (common normal flux - F_inf.n) |S^T n^| at every flux point
 //   R_t   = -(1/J) [M1 - M3 M2 | M3] [FT_t; FC_t]   (+ fused RK4 update)
+// The stage input Us is stored centred, u - u_inf (u_inf the far-field
+// conserved state): M0 reproduces and D annihilates constants, so this is
+// exact, and the long operator sums then run over small numbers.
 // Internal layout of a state-like matrix: [point][variable][element], the
 // element index padded to np_t (a multiple of 32) and fastest, so every
 // operator application is a plain row-major GEMM over V*np_t columns.
@@ -49,6 +52,7 @@ struct DevType {
     double *GUF = nullptr;                                                // [nf][3][V][np]
     double *S = nullptr;                                                  // [nu][9][np]
     double *invJ = nullptr, *wJ = nullptr;                                // [nu][np]
+    double *Rfs = nullptr;  // [nu][V][np]: divergence of the reference flux
     double *M0 = nullptr, *AGRAD = nullptr, *ADIV = nullptr;
     std::vector<double> xu;  // host: ne x nu x 3 physical solution points
 };
@@ -132,6 +136,9 @@ Phys phys_of(const fr_ctx *c) {
             for (int a = 0; a < 3; ++a) ph.fref[1 + a][m] = r * v[a] * v[m] + (a == m ? pinf : 0.0);
             ph.fref[4][m] = (E + pinf) * v[m];
         }
+        ph.uref[0] = r;
+        for (int a = 0; a < 3; ++a) ph.uref[1 + a] = r * v[a];
+        ph.uref[4] = E;
     }
     return ph;
 }
@@ -209,6 +216,9 @@ int rhs_internal(fr_ctx *c, double *const in[2], const RKStage *rk, cudaStream_t
         g.C = D.UF;
         g.ldc = g.N;
         g.mode = GEMM_STORE;
+        g.np = D.np;
+        g.add_ref = 1;
+        for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
         if ((rc = cuda_check(launch(c, K_M0, s, [&] { return launch_gemm_f64(g, s); }), "gemm M0"))) return rc;
     }
     if (c->prm.viscous) {
@@ -274,6 +284,8 @@ int rhs_internal(fr_ctx *c, double *const in[2], const RKStage *rk, cudaStream_t
         g.ldc = g.N;
         g.np = D.np;
         g.invJ = D.invJ;
+        g.rfs = D.Rfs;
+        for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
         if (rk) {
             g.mode = GEMM_DIV_RK;
             g.U = D.U;
@@ -379,6 +391,41 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         (rc = upload(c, &c->btag, faces.btag)) || (rc = upload(c, &c->bn, faces.bn)) ||
         (rc = upload(c, &c->bmag, faces.bmag)))
         return rc;
+    // the discrete divergence of the constant reference flux (zero with exact
+    // geometry; ~1e-11 with the geometric factors rounded), added back to
+    // every RHS since the flux kernels subtract that flux
+    {
+        const Phys ph = phys_of(c);
+        const Fields F = fields_of(c);
+        for (int t = 0; t < 2; ++t) {
+            DevType &D = c->T[t];
+            if (!D.present) continue;
+            if ((rc = dev_alloc(c, &D.Rfs, (size_t)D.nu * NV * D.np))) return rc;
+            if ((rc = cuda_check(launch_const_flux(D.nu, D.ne, D.np, D.S, D.FT, ph, 0), "reference flux"))) return rc;
+        }
+        if ((rc = cuda_check(launch_const_common(pairs_of(c), bnd_of(c), F, ph, 0), "reference common flux")))
+            return rc;
+        for (int t = 0; t < 2; ++t) {
+            DevType &D = c->T[t];
+            if (!D.present) continue;
+            GemmArgs g;
+            g.M = D.nu;
+            g.N = (int64_t)NV * D.np;
+            g.K1 = 3 * D.nu;
+            g.K2 = D.nf;
+            g.A = D.ADIV;
+            g.B1 = D.FT;
+            g.ldb1 = g.N;
+            g.B2 = D.FC;
+            g.ldb2 = g.N;
+            g.ldc = g.N;
+            g.np = D.np;
+            g.invJ = D.invJ;
+            g.mode = GEMM_DIV;
+            g.C = D.Rfs;
+            if ((rc = cuda_check(launch_gemm_f64(g, 0), "reference divergence"))) return rc;
+        }
+    }
     int nbt = 0;
     for (int t = 0; t < 2; ++t) {
         c->red_blocks[t] = c->T[t].present ? 152 * 2 : 0;
@@ -516,7 +563,9 @@ int fr_set_state(fr_ctx *c, const double *u, void *stream) {
         if ((rc = cuda_check(cudaMemcpyAsync(D.R, u + off, n * sizeof(double), cudaMemcpyHostToDevice, s),
                              "set_state copy")))
             return rc;
-        if ((rc = cuda_check(launch_pub_to_int(D.nu, D.ne, D.np, D.R, D.U, s), "set_state layout"))) return rc;
+        const Phys ph = phys_of(c);
+        if ((rc = cuda_check(launch_pub_to_int(D.nu, D.ne, D.np, D.R, D.U, s, D.Us, ph.uref), "set_state layout")))
+            return rc;
         off += n;
     }
     return cuda_check(cudaStreamSynchronize(s), "set_state sync");
@@ -550,7 +599,9 @@ int fr_rhs(fr_ctx *c, const double *u_dev, double *r_dev, void *stream) {
     for (int t = 0; t < 2; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
-        if ((rc = cuda_check(launch_pub_to_int(D.nu, D.ne, D.np, u_dev + off, D.Us, s), "rhs layout in")))
+        const Phys ph = phys_of(c);
+        if ((rc = cuda_check(launch_pub_to_int(D.nu, D.ne, D.np, u_dev + off, nullptr, s, D.Us, ph.uref),
+                             "rhs layout in")))
             return rc;
         in[t] = D.Us;
         off += (size_t)D.ne * NV * D.nu;
@@ -572,11 +623,22 @@ int fr_step(fr_ctx *c, double dt, int nsteps, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const double ca[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
     const double cs[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+    if (nsteps > 0) {
+        // the centred stage input is derived from the FP64 register (fr_rhs
+        // reuses its buffer); the last stage of every step keeps it current
+        const Phys ph = phys_of(c);
+        for (int t = 0; t < 2; ++t) {
+            DevType &D = c->T[t];
+            if (!D.present) continue;
+            int rc = cuda_check(launch_center(D.nu, D.np, D.U, D.Us, ph.uref, s), "centre");
+            if (rc) return rc;
+        }
+    }
     for (int it = 0; it < nsteps; ++it)
         for (int st = 0; st < 4; ++st) {
             double *in[2] = {nullptr, nullptr};
             for (int t = 0; t < 2; ++t)
-                if (c->T[t].present) in[t] = st == 0 ? c->T[t].U : c->T[t].Us;
+                if (c->T[t].present) in[t] = c->T[t].Us;
             RKStage rk{ca[st], cs[st], st == 0, st == 3};
             int rc = rhs_internal(c, in, &rk, s);
             if (rc) return rc;

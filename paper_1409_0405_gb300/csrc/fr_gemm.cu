@@ -68,9 +68,10 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgs g) {
     }
 
     if (MODE == GEMM_STORE) {
+        const double add = g.add_ref ? g.uref[n / g.np] : 0.0;
 #pragma unroll
         for (int r = 0; r < RC; ++r)
-            if (m0 + r < g.M) g.C[(int64_t)(m0 + r) * g.ldc + n] = acc[r];
+            if (m0 + r < g.M) g.C[(int64_t)(m0 + r) * g.ldc + n] = acc[r] + add;
     } else if (MODE == GEMM_GRAD) {
         // rows are (j, d) with d fastest; RC and m0 are multiples of 3
         const int64_t e = n % g.np;
@@ -90,21 +91,24 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgs g) {
         }
     } else {
         const int64_t e = n % g.np;
+        const double ur = (MODE == GEMM_DIV_RK) ? g.uref[n / g.np] : 0.0;
 #pragma unroll
         for (int r = 0; r < RC; ++r) {
             const int j = m0 + r;
             if (j >= g.M) break;
-            const double rv = -g.invJ[(int64_t)j * g.np + e] * acc[r];
             const int64_t idx = (int64_t)j * g.ldc + n;
+            const double rv = fma(-g.invJ[(int64_t)j * g.np + e], acc[r], g.rfs ? g.rfs[idx] : 0.0);
             if (MODE == GEMM_DIV) {
                 g.C[idx] = rv;
             } else {
                 const double u = g.U[idx];
                 if (g.rk_last) {
-                    g.U[idx] = g.Uacc[idx] + g.c_acc * rv;
+                    const double un = g.Uacc[idx] + g.c_acc * rv;
+                    g.U[idx] = un;
+                    g.Us[idx] = un - ur;
                 } else {
                     g.Uacc[idx] = (g.rk_first ? u : g.Uacc[idx]) + g.c_acc * rv;
-                    g.Us[idx] = u + g.c_stage * rv;
+                    g.Us[idx] = (u - ur) + g.c_stage * rv;
                 }
             }
         }

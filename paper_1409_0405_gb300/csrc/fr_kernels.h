@@ -35,6 +35,15 @@ struct GemmArgs {
     double *U = nullptr, *Uacc = nullptr, *Us = nullptr;
     double c_acc = 0, c_stage = 0;
     int rk_first = 0, rk_last = 0;
+    // centring: the stage input Us holds u - uref (uref = the far-field
+    // conserved state, one value per variable, column n has variable
+    // n / np).  GEMM_STORE with add_ref adds uref back; GEMM_DIV_RK writes
+    // Us relative to uref.
+    int add_ref = 0;
+    double uref[5] = {0, 0, 0, 0, 0};
+    // GEMM_DIV(_RK): constant field added to r (the discrete divergence of
+    // the subtracted reference flux, see Phys::fref); may be null
+    const double *rfs = nullptr;
 };
 
 cudaError_t launch_gemm_f64(const GemmArgs &g, cudaStream_t s);
@@ -44,10 +53,14 @@ struct Phys {
     double rho_inf, vinf[3], p_inf, t_wall;
     int viscous;
     // inviscid flux of the far-field state, subtracted from every volume
-    // and common flux before the divergence (exact: the discrete divergence
-    // of a constant flux vanishes element by element), which removes the
-    // cancellation of the large constant pressure flux at low Mach number
+    // and common flux before the divergence, which removes the cancellation
+    // of the large constant pressure flux at low Mach number.  The discrete
+    // divergence of this constant flux would vanish with exact geometry; with
+    // the geometric factors rounded to double it is ~1e-11, so it is
+    // evaluated once at set-up and added back (GemmArgs::rfs).
     double fref[5][3];
+    // the far-field conserved state; the stage input is stored relative to it
+    double uref[5];
 };
 
 // Per-type field pointers (index 0 tet, 1 prism); nullptr for an absent type.
@@ -76,13 +89,22 @@ cudaError_t launch_common_solution(const Pairs &P, const Bnd &B, const Fields &F
 cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const Fields &F, const Phys &ph,
                                cudaStream_t s);
 // transformed flux at the solution points of one type
+// U is the centred stage input (u - uref)
 cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const double *U, const double *GU,
                         const double *S, double *FT, const Phys &ph, cudaStream_t s);
-// public [e][v][j] <-> internal [j][v][e]
+// public [e][v][j] <-> internal [j][v][e]; pub_to_int optionally also
+// writes the centred copy in - uref into `centred`
 cudaError_t launch_pub_to_int(int nu, int64_t ne, int64_t np, const double *pub, double *in,
-                              cudaStream_t s);
+                              cudaStream_t s, double *centred = nullptr, const double *uref = nullptr);
 cudaError_t launch_int_to_pub(int nu, int64_t ne, int64_t np, const double *in, double *pub,
                               cudaStream_t s);
+// transformed reference flux at solution points, FT = S F_ref (padding 0)
+cudaError_t launch_const_flux(int nu, int64_t ne, int64_t np, const double *S, double *FT, const Phys &ph,
+                              cudaStream_t s);
+// reference normal flux at every flux point, FC = F_ref.n |S^T n^|
+cudaError_t launch_const_common(const Pairs &P, const Bnd &B, const Fields &F, const Phys &ph, cudaStream_t s);
+// Us = U - uref over a whole [nu][V][np] register
+cudaError_t launch_center(int nu, int64_t np, const double *U, double *Us, const double *uref, cudaStream_t s);
 // per-block partial integrals (7 per block) of one type's register
 cudaError_t launch_reduce_partial(int nu, int64_t ne, int64_t np, const double *U, const double *wJ,
                                   double gamma, double *partial, int nblocks, cudaStream_t s);

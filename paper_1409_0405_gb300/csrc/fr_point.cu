@@ -121,25 +121,28 @@ __device__ __forceinline__ void bc_states(int tag, const double *u, const double
         cb[4] = u[0] * ew;
         return;
     }
-    // Riemann-invariant far field
+    // Riemann-invariant far field.  With R+ = vn + 2c/(g-1) from the
+    // interior and R- = vn_inf - 2c_inf/(g-1) from the far field,
+    //   vn_b = (R+ + R-)/2,  c_b = (g-1)(R+ - R-)/4,
+    // written without forming R+- (|R+-| ~ 2c/(g-1) >> vn would cancel),
+    // and the density from the upwind entropy p/rho^g, written as
+    //   rho_b = rho_up (c_b / c_up)^(2/(g-1)).
     Prim q = prim(u, g);
     const double c = sqrt(g * q.p * q.ir);
     const double cinf = sqrt(g * ph.p_inf / ph.rho_inf);
     const double vn = q.v[0] * n[0] + q.v[1] * n[1] + q.v[2] * n[2];
     const double vninf = ph.vinf[0] * n[0] + ph.vinf[1] * n[1] + ph.vinf[2] * n[2];
-    const double rp = vn + 2.0 * c / (g - 1.0);
-    const double rm = vninf - 2.0 * cinf / (g - 1.0);
-    const double vnb = 0.5 * (rp + rm);
-    const double cbs = 0.25 * (g - 1.0) * (rp - rm);
-    double vb[3], s;
+    const double vnb = 0.5 * (vn + vninf) + (c - cinf) / (g - 1.0);
+    const double cbs = 0.5 * (c + cinf) + 0.25 * (g - 1.0) * (vn - vninf);
+    double vb[3], rhob;
+    const double ex = 2.0 / (g - 1.0);
     if (vnb >= 0.0) {
-        s = q.p / pow(q.rho, g);
+        rhob = q.rho * pow(cbs / c, ex);
         for (int k = 0; k < 3; ++k) vb[k] = q.v[k] + (vnb - vn) * n[k];
     } else {
-        s = ph.p_inf / pow(ph.rho_inf, g);
+        rhob = ph.rho_inf * pow(cbs / cinf, ex);
         for (int k = 0; k < 3; ++k) vb[k] = ph.vinf[k] + (vnb - vninf) * n[k];
     }
-    const double rhob = pow(cbs * cbs / (g * s), 1.0 / (g - 1.0));
     const double pb = rhob * cbs * cbs / g;
     ghost[0] = rhob;
     ghost[1] = rhob * vb[0];
@@ -271,7 +274,7 @@ __global__ void k_flux(int nu, int64_t ne, int64_t np, const double *__restrict_
     if (j >= nu || e >= ne) return;
     double u[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) u[v] = U[(j * V + v) * np + e];
+    for (int v = 0; v < V; ++v) u[v] = U[(j * V + v) * np + e] + ph.uref[v];
     const Prim q = prim(u, ph.gamma);
     double F[V][3];
     // inviscid
@@ -308,15 +311,70 @@ __global__ void k_flux(int nu, int64_t ne, int64_t np, const double *__restrict_
             FT[((j * 3 + d) * V + v) * np + e] = s[d * 3 + 0] * F[v][0] + s[d * 3 + 1] * F[v][1] + s[d * 3 + 2] * F[v][2];
 }
 
+struct Uref {
+    double v[5];
+};
+
+__global__ void k_const_flux(int nu, int64_t ne, int64_t np, const double *__restrict__ S,
+                             double *__restrict__ FT, const Phys ph) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = idx / np, e = idx - j * np;
+    if (j >= nu || e >= ne) return;
+    double s[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            FT[((j * 3 + d) * V + v) * np + e] =
+                s[d * 3 + 0] * ph.fref[v][0] + s[d * 3 + 1] * ph.fref[v][1] + s[d * 3 + 2] * ph.fref[v][2];
+}
+
+__global__ void k_const_common(const Pairs P, const Bnd B, const Fields F, const Phys ph) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P.n) {
+        const int ta = P.ta[k], tb = P.tb[k];
+        const int64_t npa = F.np[ta], npb = F.np[tb];
+        const int64_t oa = fpt_off(P.fa[k], P.ea[k], npa), ob = fpt_off(P.fb[k], P.eb[k], npb);
+        const double *n = P.nrm + 3 * k;
+        for (int v = 0; v < V; ++v) {
+            const double f = ph.fref[v][0] * n[0] + ph.fref[v][1] * n[1] + ph.fref[v][2] * n[2];
+            F.FC[ta][oa + v * npa] = f * P.maga[k];
+            F.FC[tb][ob + v * npb] = -f * P.magb[k];
+        }
+        return;
+    }
+    const int64_t kb = k - P.n;
+    if (kb < B.n) {
+        const int t = B.bt[kb];
+        const int64_t np = F.np[t];
+        const int64_t o = fpt_off(B.bf[kb], B.be[kb], np);
+        const double *n = B.bn + 3 * kb;
+        for (int v = 0; v < V; ++v)
+            F.FC[t][o + v * np] = (ph.fref[v][0] * n[0] + ph.fref[v][1] * n[1] + ph.fref[v][2] * n[2]) * B.bmag[kb];
+    }
+}
+
 __global__ void k_pub_to_int(int nu, int64_t ne, int64_t np, const double *__restrict__ pub,
-                             double *__restrict__ in) {
+                             double *__restrict__ in, double *__restrict__ centred, const Uref uref) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = ne * V * nu;
     if (idx >= tot) return;
     const int64_t e = idx / (V * nu);
     const int64_t r = idx - e * V * nu;
     const int64_t v = r / nu, j = r - v * nu;
-    in[(j * V + v) * np + e] = pub[idx];
+    const double x = pub[idx];
+    if (in) in[(j * V + v) * np + e] = x;
+    if (centred) centred[(j * V + v) * np + e] = x - uref.v[v];
+}
+
+__global__ void k_center(int64_t n, int64_t np, const double *__restrict__ U, double *__restrict__ Us,
+                         const Uref uref) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int64_t v = (idx / np) % V;
+    Us[idx] = U[idx] - uref.v[v];
 }
 
 __global__ void k_int_to_pub(int nu, int64_t ne, int64_t np, const double *__restrict__ in,
@@ -421,10 +479,37 @@ cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const double *U, const d
     return cudaGetLastError();
 }
 
-cudaError_t launch_pub_to_int(int nu, int64_t ne, int64_t np, const double *pub, double *in, cudaStream_t s) {
+cudaError_t launch_pub_to_int(int nu, int64_t ne, int64_t np, const double *pub, double *in, cudaStream_t s,
+                              double *centred, const double *uref) {
     const int64_t n = ne * V * nu;
     if (n == 0) return cudaSuccess;
-    k_pub_to_int<<<blocks_for(n, 256), 256, 0, s>>>(nu, ne, np, pub, in);
+    Uref r{{0, 0, 0, 0, 0}};
+    if (uref)
+        for (int v = 0; v < V; ++v) r.v[v] = uref[v];
+    k_pub_to_int<<<blocks_for(n, 256), 256, 0, s>>>(nu, ne, np, pub, in, centred, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_const_flux(int nu, int64_t ne, int64_t np, const double *S, double *FT, const Phys &ph,
+                              cudaStream_t s) {
+    const int64_t n = (int64_t)nu * np;
+    if (ne == 0) return cudaSuccess;
+    k_const_flux<<<blocks_for(n, 128), 128, 0, s>>>(nu, ne, np, S, FT, ph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_const_common(const Pairs &P, const Bnd &B, const Fields &F, const Phys &ph, cudaStream_t s) {
+    const int64_t n = P.n + B.n;
+    if (n == 0) return cudaSuccess;
+    k_const_common<<<blocks_for(n, 128), 128, 0, s>>>(P, B, F, ph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_center(int nu, int64_t np, const double *U, double *Us, const double *uref, cudaStream_t s) {
+    const int64_t n = (int64_t)nu * V * np;
+    if (n == 0) return cudaSuccess;
+    Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
+    k_center<<<blocks_for(n, 256), 256, 0, s>>>(n, np, U, Us, r);
     return cudaGetLastError();
 }
 

@@ -78,9 +78,11 @@ def gpu_rhs(ctx, u):
 def to_longdouble(sol):
     """Switch an oracle instance to numpy extended precision (used only to
     measure the FP64 rounding floor of a case)."""
+    import copy
     ld = np.longdouble
     for t in sol.types:
-        op = sol.m.ops[t]
+        # copy: the oracle caches its operator objects across solvers
+        op = sol.m.ops[t] = copy.copy(sol.m.ops[t])
         for k in ("M0", "D", "M3", "fnorm", "w", "fw"):
             setattr(op, k, getattr(op, k).astype(ld))
         sol.m.J[t] = sol.m.J[t].astype(ld)

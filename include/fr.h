@@ -195,6 +195,37 @@ int fr_profile_read(fr_ctx *ctx, double *ms, int64_t *count, int64_t *launches);
  */
 int fr_peak_fp64(double *gflops, void *cuda_stream);
 
+/*
+ * fr_reduce_noalloc: the integrals of fr_reduce for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this entry point
+ * exists for code that may not call cudaMalloc (a device owned by another
+ * allocator, or a path where an allocation and its implicit
+ * synchronisation are not allowed).  It needs no context and allocates
+ * nothing: its scratch (one partial per block) is a file-scope static
+ * device array of FR_NOALLOC_MAX_BLOCKS x 7 doubles (229,376 bytes) that
+ * every GPU loading this library keeps until the process exits.
+ *
+ * Input: one element block of the public layout, u_dev [ne][5][nu], and
+ * the quadrature weights times Jacobians wJ_dev [ne][nu] (device pointers,
+ * caller-owned).  Output: out_dev (device, caller-owned, 7 doubles) =
+ * sum w J u for the 5 conserved variables, the kinetic-energy integral and
+ * the number of points with a non-finite state or non-positive
+ * density/pressure.  Asynchronous on cuda_stream.
+ *
+ * Limits and errors: ne*nu may not exceed FR_NOALLOC_MAX_POINTS (8,388,608
+ * points, i.e. FR_NOALLOC_MAX_BLOCKS blocks of 2,048 points); larger sizes,
+ * null pointers, nu <= 0 or gamma <= 1 return FR_ERR_ARG without touching
+ * the GPU.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make it before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (each call overwrites the slots it reads); calls that overlap on
+ * the GPU race on it, so serialise them.
+ */
+#define FR_NOALLOC_MAX_BLOCKS 4096
+#define FR_NOALLOC_MAX_POINTS (FR_NOALLOC_MAX_BLOCKS * 2048LL)
+int fr_reduce_noalloc(int64_t ne, int nu, const double *u_dev, const double *wJ_dev, double gamma,
+                      double *out_dev, void *cuda_stream);
+
 /* Static description of an error code. */
 const char *fr_strerror(int code);
 

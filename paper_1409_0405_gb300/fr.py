@@ -34,7 +34,7 @@ OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_reduce",
            "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
-           "fr_last_error")
+           "fr_last_error", "fr_reduce_noalloc")
 KCLASSES = ("M0", "common_solution", "grad", "M0_grad", "flux", "common_flux", "div")
 
 
@@ -88,6 +88,8 @@ def load():
     lib.fr_profile_read.argtypes = [vp, dp, i64p, i64p]
     lib.fr_peak_fp64.argtypes = [dp, vp]
     lib.fr_peak_fp64.restype = C.c_int
+    lib.fr_reduce_noalloc.argtypes = [C.c_int64, C.c_int, vp, vp, C.c_double, vp, vp]
+    lib.fr_reduce_noalloc.restype = C.c_int
     lib.fr_strerror.argtypes = [C.c_int]
     lib.fr_strerror.restype = C.c_char_p
     lib.fr_last_error.argtypes = []
@@ -128,6 +130,14 @@ def peak_fp64(stream=None):
     g = C.c_double()
     _check(lib.fr_peak_fp64(C.byref(g), C.c_void_p(stream) if stream else None))
     return g.value
+
+
+def reduce_noalloc(ne, nu, u_ptr, wj_ptr, gamma, out_ptr, stream=None):
+    """fr_reduce_noalloc on raw device pointers (no allocation anywhere);
+    returns the library's status code."""
+    lib = load()
+    return lib.fr_reduce_noalloc(int(ne), int(nu), C.c_void_p(u_ptr), C.c_void_p(wj_ptr), float(gamma),
+                                 C.c_void_p(out_ptr), C.c_void_p(stream) if stream else None)
 
 
 def default_params(viscous=False, mu=0.0, gamma=1.4, prandtl=0.72, ldg_beta=0.5,

@@ -217,6 +217,61 @@ def cpu_baseline_entry(nrhs=1):
                        f"median of {nrhs}, setup excluded, 1 BLAS thread")}
 
 
+def per_quantity_rel_err(ref, got, counts):
+    """[mass, momentum (vector norm), energy]: max |got-ref| / max |ref|
+    over all points, public layout."""
+    num = np.zeros(3)
+    den = np.zeros(3)
+    off = 0
+    for ne, nu in counts:
+        if ne == 0:
+            continue
+        r = ref[off:off + ne * 5 * nu].reshape(ne, 5, nu)
+        g = got[off:off + ne * 5 * nu].reshape(ne, 5, nu)
+        for q, sl in enumerate((slice(0, 1), slice(1, 4), slice(4, 5))):
+            num[q] = max(num[q], float(np.max(np.linalg.norm(g[:, sl] - r[:, sl], axis=1))))
+            den[q] = max(den[q], float(np.max(np.linalg.norm(r[:, sl], axis=1))))
+        off += ne * 5 * nu
+    return (num / np.where(den > 0, den, 1.0)).tolist()
+
+
+def precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, precision, args, sp):
+    """Time K RK4 steps in another precision mode and measure its error
+    against the FP64 path (which matches the FP64 oracle to 1e-12)."""
+    ctx = fr.Context(mesh, ORDER, **flow_params(), precision=precision)
+    ctx.set_state(u0, sp)
+    for _ in range(max(args.warmup, 0)):
+        ctx.step(dt, 1, sp)
+    torch.cuda.synchronize()
+    stream = torch.cuda.ExternalStream(sp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(dt, 1, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # errors: one RHS, and the increment of one RK4 step, against FP64
+    ud = torch.from_numpy(u0).cuda()
+    r64, r32 = torch.empty_like(ud), torch.empty_like(ud)
+    ctx64.rhs(ud.data_ptr(), r64.data_ptr(), sp)
+    ctx.rhs(ud.data_ptr(), r32.data_ptr(), sp)
+    torch.cuda.synchronize()
+    rhs_err = per_quantity_rel_err(r64.cpu().numpy(), r32.cpu().numpy(), counts)
+    ctx64.set_state(u0, sp)
+    ctx64.step(dt, 1, sp)
+    s64 = ctx64.get_state(stream=sp)
+    ctx.set_state(u0, sp)
+    ctx.step(dt, 1, sp)
+    s32 = ctx.get_state(stream=sp)
+    inc_err = per_quantity_rel_err(s64 - u0, s32 - u0, counts)
+    ctx.close()
+    return {"value": ctx64.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "rhs_rel_err_vs_fp64": rhs_err, "step_increment_rel_err_vs_fp64": inc_err,
+            "error_measure": "[mass, momentum vector, energy] max|d|/max|ref|; the FP64 path matches the "
+                             "FP64 oracle to 1e-12"}
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -228,6 +283,7 @@ def main():
     ap.add_argument("--nx", type=int, default=75,
                     help="cells along x (75 = the full workload; smaller for profiling)")
     ap.add_argument("--cpu-oracle-child", type=int, default=0)
+    ap.add_argument("--fp64-only", action="store_true", help="skip the other precision modes")
     args = ap.parse_args()
 
     if args.cpu_oracle_child:
@@ -342,6 +398,11 @@ def main():
         e2e_s = float(t.item())
     e2e_val = world * ndof * 4.0 / e2e_s / 1e9
 
+    # --- other precision modes beside the FP64 line (same mesh, same state) ---
+    modes = {}
+    if not args.fp64_only:
+        modes["fp32"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_FP32, args, sp)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -388,6 +449,7 @@ def main():
                 "d2h_bytes_per_step": int(ndof * 8), "steps": e2e_steps},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "modes": modes,
     }
     print(json.dumps(line))
     if world > 1:

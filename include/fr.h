@@ -85,7 +85,9 @@ typedef struct {
     double ldg_beta;  /* LDG common-solution bias, switch along a fixed direction */
     double ldg_tau;   /* LDG penalty on the normal flux */
     int viscous;      /* 0: Euler, 1: Navier-Stokes */
-    int precision;    /* FR_FP64 or FR_FP32 operator arithmetic */
+    int precision;    /* FR_FP64, or FR_FP32: operator applications and point-wise
+                         work in FP32; RK registers, the reference-flux
+                         correction and the reductions stay FP64 */
     double rho_inf;   /* far-field density */
     double vel_inf[3];/* far-field velocity */
     double p_inf;     /* far-field pressure */

@@ -46,14 +46,21 @@ struct DevType {
     int present = 0;
     int64_t ne = 0, np = 0;
     int nu = 0, nf = 0;
-    double *U = nullptr, *Us = nullptr, *Uacc = nullptr, *R = nullptr;  // [nu][V][np]
-    double *UF = nullptr, *DUF = nullptr, *FC = nullptr;                 // [nf][V][np]
-    double *GU = nullptr, *FT = nullptr;                                  // [nu][3][V][np]
-    double *GUF = nullptr;                                                // [nf][3][V][np]
-    double *S = nullptr;                                                  // [nu][9][np]
-    double *invJ = nullptr, *wJ = nullptr;                                // [nu][np]
-    double *Rfs = nullptr;  // [nu][V][np]: divergence of the reference flux
+    // FP64 in every mode: RK registers, quadrature weights, the reference-flux
+    // divergence, and the geometry/operators the set-up evaluates with
+    double *U = nullptr, *Uacc = nullptr;   // [nu][V][np]
+    double *wJ = nullptr;                   // [nu][np]
+    double *Rfs = nullptr;                  // [nu][V][np]
+    double *S = nullptr, *invJ = nullptr;   // [nu][9][np], [nu][np]
     double *M0 = nullptr, *AGRAD = nullptr, *ADIV = nullptr;
+    // buffers in the arithmetic type of the right-hand side (double for
+    // FR_FP64, float for FR_FP32; the geometry/operator views alias the
+    // double arrays in FR_FP64)
+    void *Us = nullptr, *R = nullptr;        // [nu][V][np]
+    void *UF = nullptr, *DUF = nullptr, *FC = nullptr;   // [nf][V][np]
+    void *GU = nullptr, *FT = nullptr;       // [nu][3][V][np]
+    void *GUF = nullptr;                     // [nf][3][V][np]
+    void *S_t = nullptr, *invJ_t = nullptr, *M0_t = nullptr, *AGRAD_t = nullptr, *ADIV_t = nullptr;
     std::vector<double> xu;  // host: ne x nu x 3 physical solution points
 };
 
@@ -100,6 +107,21 @@ int dev_alloc(fr_ctx *c, T **p, size_t count) {
     return FR_OK;
 }
 
+int dev_alloc_bytes(fr_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return FR_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_err(FR_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    e = cudaMemset(*p, 0, bytes);
+    if (e != cudaSuccess) return set_err(FR_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+    return FR_OK;
+}
+
 template <class T>
 int upload(fr_ctx *c, T **p, const std::vector<T> &h) {
     int rc = dev_alloc(c, p, h.size());
@@ -143,13 +165,14 @@ Phys phys_of(const fr_ctx *c) {
     return ph;
 }
 
-Fields fields_of(const fr_ctx *c) {
-    Fields F{};
+template <typename T>
+FieldsT<T> fields_of(const fr_ctx *c) {
+    FieldsT<T> F{};
     for (int t = 0; t < 2; ++t) {
-        F.UF[t] = c->T[t].UF;
-        F.DUF[t] = c->T[t].DUF;
-        F.GUF[t] = c->T[t].GUF;
-        F.FC[t] = c->T[t].FC;
+        F.UF[t] = (const T *)c->T[t].UF;
+        F.DUF[t] = (T *)c->T[t].DUF;
+        F.GUF[t] = (const T *)c->T[t].GUF;
+        F.FC[t] = (T *)c->T[t].FC;
         F.np[t] = c->T[t].np;
     }
     return F;
@@ -198,108 +221,121 @@ struct RKStage {
     int first, last;
 };
 
-int rhs_internal(fr_ctx *c, double *const in[2], const RKStage *rk, cudaStream_t s) {
+template <typename T>
+int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
     const Phys ph = phys_of(c);
-    const Fields F = fields_of(c);
+    const FieldsT<T> F = fields_of<T>(c);
     int rc;
-    // 1. interpolate to flux points
+    // 1. interpolate to flux points (the stage input is centred; add u_inf back)
     for (int t = 0; t < 2; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
-        GemmArgs g;
+        GemmArgsT<T> g;
         g.M = D.nf;
         g.N = (int64_t)NV * D.np;
         g.K1 = D.nu;
-        g.A = D.M0;
+        g.A = (const T *)D.M0_t;
         g.B1 = in[t];
         g.ldb1 = g.N;
-        g.C = D.UF;
+        g.C = (T *)D.UF;
         g.ldc = g.N;
         g.mode = GEMM_STORE;
         g.np = D.np;
         g.add_ref = 1;
         for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
-        if ((rc = cuda_check(launch(c, K_M0, s, [&] { return launch_gemm_f64(g, s); }), "gemm M0"))) return rc;
+        if ((rc = cuda_check(launch(c, K_M0, s, [&] { return launch_gemm<T>(g, s); }), "gemm M0"))) return rc;
     }
     if (c->prm.viscous) {
         // 2. common solution and jumps
-        if ((rc = cuda_check(launch(c, K_COMMON_SOL, s, [&] { return launch_common_solution(pairs_of(c), bnd_of(c), F, ph, s); }), "common solution")))
+        if ((rc = cuda_check(launch(c, K_COMMON_SOL, s,
+                                    [&] { return launch_common_solution<T>(pairs_of(c), bnd_of(c), F, ph, s); }),
+                             "common solution")))
             return rc;
         // 3. corrected physical gradient; 4. gradient at flux points
         for (int t = 0; t < 2; ++t) {
             DevType &D = c->T[t];
             if (!D.present) continue;
-            GemmArgs g;
+            GemmArgsT<T> g;
             g.M = 3 * D.nu;
             g.N = (int64_t)NV * D.np;
             g.K1 = D.nu;
             g.K2 = D.nf;
-            g.A = D.AGRAD;
+            g.A = (const T *)D.AGRAD_t;
             g.B1 = in[t];
             g.ldb1 = g.N;
-            g.B2 = D.DUF;
+            g.B2 = (const T *)D.DUF;
             g.ldb2 = g.N;
-            g.C = D.GU;  // [nu][3][V][np]: row (j, m), N columns
+            g.C = (T *)D.GU;  // [nu][3][V][np]: row (j, m), N columns
             g.ldc = g.N;
             g.mode = GEMM_GRAD;
             g.np = D.np;
-            g.invJ = D.invJ;
-            g.S = D.S;
-            if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return launch_gemm_f64(g, s); }), "gemm grad"))) return rc;
-            GemmArgs h;
+            g.invJ = (const T *)D.invJ_t;
+            g.S = (const T *)D.S_t;
+            if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return launch_gemm<T>(g, s); }), "gemm grad"))) return rc;
+            GemmArgsT<T> h;
             h.M = D.nf;
             h.N = 3 * (int64_t)NV * D.np;
             h.K1 = D.nu;
-            h.A = D.M0;
-            h.B1 = D.GU;
+            h.A = (const T *)D.M0_t;
+            h.B1 = (const T *)D.GU;
             h.ldb1 = h.N;
-            h.C = D.GUF;
+            h.C = (T *)D.GUF;
             h.ldc = h.N;
             h.mode = GEMM_STORE;
-            if ((rc = cuda_check(launch(c, K_M0_GRAD, s, [&] { return launch_gemm_f64(h, s); }), "gemm M0 grad"))) return rc;
+            if ((rc = cuda_check(launch(c, K_M0_GRAD, s, [&] { return launch_gemm<T>(h, s); }), "gemm M0 grad")))
+                return rc;
         }
     }
     // 5. transformed flux at solution points
     for (int t = 0; t < 2; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
-        if ((rc = cuda_check(launch(c, K_FLUX, s, [&] { return launch_flux(D.nu, D.ne, D.np, in[t], D.GU, D.S, D.FT, ph, s); }), "flux"))) return rc;
+        if ((rc = cuda_check(launch(c, K_FLUX, s,
+                                    [&] {
+                                        return launch_flux<T>(D.nu, D.ne, D.np, in[t], (const T *)D.GU,
+                                                              (const T *)D.S_t, (T *)D.FT, ph, s);
+                                    }),
+                             "flux")))
+            return rc;
     }
     // 6. common normal flux at every flux point
-    if ((rc = cuda_check(launch(c, K_COMMON_FLUX, s, [&] { return launch_common_flux(pairs_of(c), bnd_of(c), F, ph, s); }), "common flux"))) return rc;
+    if ((rc = cuda_check(launch(c, K_COMMON_FLUX, s,
+                                [&] { return launch_common_flux<T>(pairs_of(c), bnd_of(c), F, ph, s); }),
+                         "common flux")))
+        return rc;
     // 7. divergence plus correction
     for (int t = 0; t < 2; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
-        GemmArgs g;
+        GemmArgsT<T> g;
         g.M = D.nu;
         g.N = (int64_t)NV * D.np;
         g.K1 = 3 * D.nu;
         g.K2 = D.nf;
-        g.A = D.ADIV;
-        g.B1 = D.FT;
+        g.A = (const T *)D.ADIV_t;
+        g.B1 = (const T *)D.FT;
         g.ldb1 = g.N;
-        g.B2 = D.FC;
+        g.B2 = (const T *)D.FC;
         g.ldb2 = g.N;
         g.ldc = g.N;
         g.np = D.np;
-        g.invJ = D.invJ;
+        g.invJ = (const T *)D.invJ_t;
         g.rfs = D.Rfs;
         for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
         if (rk) {
             g.mode = GEMM_DIV_RK;
             g.U = D.U;
             g.Uacc = D.Uacc;
-            g.Us = D.Us;
+            g.Us = (T *)D.Us;
             g.c_acc = rk->c_acc;
             g.c_stage = rk->c_stage;
             g.rk_first = rk->first;
             g.rk_last = rk->last;
         } else {
             g.mode = GEMM_DIV;
-            g.C = D.R;
+            g.C = (T *)D.R;
         }
-        if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return launch_gemm_f64(g, s); }), "gemm div"))) return rc;
+        if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return launch_gemm<T>(g, s); }), "gemm div"))) return rc;
     }
     return FR_OK;
 }
@@ -322,7 +358,8 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         return set_err(FR_ERR_ARG, "null connectivity array");
     if (mesh->n_tet > (1LL << 30) || mesh->n_pri > (1LL << 30))
         return set_err(FR_ERR_ARG, "element count too large");
-    if (prm->precision != FR_FP64) return set_err(FR_ERR_UNSUPPORTED, "only FR_FP64 is built");
+    if (prm->precision != FR_FP64 && prm->precision != FR_FP32)
+        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64 or FR_FP32");
     if (!(prm->gamma > 1.0) || prm->mu < 0.0 || (prm->viscous && !(prm->prandtl > 0.0)))
         return set_err(FR_ERR_ARG, "invalid gas parameters");
     c->prm = *prm;
@@ -355,13 +392,15 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         D.nu = ops[t].nu;
         D.nf = ops[t].nf;
         const size_t su = (size_t)D.nu * NV * D.np, sf = (size_t)D.nf * NV * D.np;
-        if ((rc = dev_alloc(c, &D.U, su)) || (rc = dev_alloc(c, &D.Us, su)) || (rc = dev_alloc(c, &D.Uacc, su)) ||
-            (rc = dev_alloc(c, &D.R, su)) || (rc = dev_alloc(c, &D.UF, sf)) || (rc = dev_alloc(c, &D.FC, sf)) ||
-            (rc = dev_alloc(c, &D.FT, 3 * su)))
+        const size_t es = prm->precision == FR_FP32 ? sizeof(float) : sizeof(double);
+        if ((rc = dev_alloc(c, &D.U, su)) || (rc = dev_alloc(c, &D.Uacc, su)) ||
+            (rc = dev_alloc_bytes(c, &D.Us, su * es)) || (rc = dev_alloc_bytes(c, &D.R, su * es)) ||
+            (rc = dev_alloc_bytes(c, &D.UF, sf * es)) || (rc = dev_alloc_bytes(c, &D.FC, sf * es)) ||
+            (rc = dev_alloc_bytes(c, &D.FT, 3 * su * es)))
             return rc;
         if (prm->viscous) {
-            if ((rc = dev_alloc(c, &D.DUF, sf)) || (rc = dev_alloc(c, &D.GU, 3 * su)) ||
-                (rc = dev_alloc(c, &D.GUF, 3 * sf)))
+            if ((rc = dev_alloc_bytes(c, &D.DUF, sf * es)) || (rc = dev_alloc_bytes(c, &D.GU, 3 * su * es)) ||
+                (rc = dev_alloc_bytes(c, &D.GUF, 3 * sf * es)))
                 return rc;
         }
         // geometry in the internal layout
@@ -379,6 +418,23 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             (rc = upload(c, &D.M0, ops[t].M0)) || (rc = upload(c, &D.AGRAD, ops[t].AGRAD)) ||
             (rc = upload(c, &D.ADIV, ops[t].ADIV)))
             return rc;
+        if (prm->precision == FR_FP32) {
+            // float views of the geometry and operators (rounded once)
+            double *src[5] = {D.S, D.invJ, D.M0, D.AGRAD, D.ADIV};
+            void **dst[5] = {&D.S_t, &D.invJ_t, &D.M0_t, &D.AGRAD_t, &D.ADIV_t};
+            const size_t cnt[5] = {S.size(), iJ.size(), ops[t].M0.size(), ops[t].AGRAD.size(), ops[t].ADIV.size()};
+            for (int k = 0; k < 5; ++k) {
+                if ((rc = dev_alloc_bytes(c, dst[k], cnt[k] * sizeof(float)))) return rc;
+                if ((rc = cuda_check(launch_to_float((int64_t)cnt[k], src[k], (float *)*dst[k], 0), "to float")))
+                    return rc;
+            }
+        } else {
+            D.S_t = D.S;
+            D.invJ_t = D.invJ;
+            D.M0_t = D.M0;
+            D.AGRAD_t = D.AGRAD;
+            D.ADIV_t = D.ADIV;
+        }
         D.xu = G.xu;
     }
     c->npairs = (int64_t)faces.ta.size();
@@ -392,20 +448,49 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         (rc = upload(c, &c->bmag, faces.bmag)))
         return rc;
     // the discrete divergence of the constant reference flux (zero with exact
-    // geometry; ~1e-11 with the geometric factors rounded), added back to
-    // every RHS since the flux kernels subtract that flux
+    // geometry; ~1e-11 with the geometric factors rounded), evaluated once in
+    // FP64 and added back to every RHS since the flux kernels subtract that
+    // flux.  FP64 scratch: the RHS buffers themselves in FR_FP64, temporary
+    // buffers in FR_FP32.
     {
         const Phys ph = phys_of(c);
-        const Fields F = fields_of(c);
+        const bool f32 = prm->precision == FR_FP32;
+        double *tFT[2] = {nullptr, nullptr}, *tFC[2] = {nullptr, nullptr};
+        std::vector<void *> tmp;
         for (int t = 0; t < 2; ++t) {
             DevType &D = c->T[t];
             if (!D.present) continue;
             if ((rc = dev_alloc(c, &D.Rfs, (size_t)D.nu * NV * D.np))) return rc;
-            if ((rc = cuda_check(launch_const_flux(D.nu, D.ne, D.np, D.S, D.FT, ph, 0), "reference flux"))) return rc;
+            if (f32) {
+                const size_t su = (size_t)D.nu * NV * D.np, sf = (size_t)D.nf * NV * D.np;
+                if (cudaMalloc(&tFT[t], 3 * su * sizeof(double)) != cudaSuccess ||
+                    cudaMalloc(&tFC[t], sf * sizeof(double)) != cudaSuccess) {
+                    cudaGetLastError();
+                    for (double *q : tFT) cudaFree(q);
+                    for (double *q : tFC) cudaFree(q);
+                    return set_err(FR_ERR_NOMEM, "set-up scratch");
+                }
+            } else {
+                tFT[t] = (double *)D.FT;
+                tFC[t] = (double *)D.FC;
+            }
         }
-        if ((rc = cuda_check(launch_const_common(pairs_of(c), bnd_of(c), F, ph, 0), "reference common flux")))
-            return rc;
+        Fields F{};
         for (int t = 0; t < 2; ++t) {
+            F.UF[t] = nullptr;
+            F.DUF[t] = nullptr;
+            F.GUF[t] = nullptr;
+            F.FC[t] = tFC[t];
+            F.np[t] = c->T[t].np;
+        }
+        rc = FR_OK;
+        for (int t = 0; t < 2 && !rc; ++t) {
+            DevType &D = c->T[t];
+            if (!D.present) continue;
+            rc = cuda_check(launch_const_flux(D.nu, D.ne, D.np, D.S, tFT[t], ph, 0), "reference flux");
+        }
+        if (!rc) rc = cuda_check(launch_const_common(pairs_of(c), bnd_of(c), F, ph, 0), "reference common flux");
+        for (int t = 0; t < 2 && !rc; ++t) {
             DevType &D = c->T[t];
             if (!D.present) continue;
             GemmArgs g;
@@ -414,17 +499,25 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             g.K1 = 3 * D.nu;
             g.K2 = D.nf;
             g.A = D.ADIV;
-            g.B1 = D.FT;
+            g.B1 = tFT[t];
             g.ldb1 = g.N;
-            g.B2 = D.FC;
+            g.B2 = tFC[t];
             g.ldb2 = g.N;
             g.ldc = g.N;
             g.np = D.np;
             g.invJ = D.invJ;
             g.mode = GEMM_DIV;
             g.C = D.Rfs;
-            if ((rc = cuda_check(launch_gemm_f64(g, 0), "reference divergence"))) return rc;
+            rc = cuda_check(launch_gemm_f64(g, 0), "reference divergence");
         }
+        if (f32) {
+            cudaDeviceSynchronize();
+            for (int t = 0; t < 2; ++t) {
+                cudaFree(tFT[t]);
+                cudaFree(tFC[t]);
+            }
+        }
+        if (rc) return rc;
     }
     int nbt = 0;
     for (int t = 0; t < 2; ++t) {
@@ -433,6 +526,59 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
     }
     if ((rc = dev_alloc(c, &c->red, (size_t)nbt * 7 + 8))) return rc;
     return cuda_check(cudaDeviceSynchronize(), "fr_create sync");
+}
+
+template <typename T>
+int rhs_public(fr_ctx *c, const double *u_dev, double *r_dev, cudaStream_t s) {
+    size_t off = 0;
+    T *in[2] = {nullptr, nullptr};
+    int rc;
+    const Phys ph = phys_of(c);
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_pub_to_int<T>(D.nu, D.ne, D.np, u_dev + off, nullptr, s, (T *)D.Us, ph.uref),
+                             "rhs layout in")))
+            return rc;
+        in[t] = (T *)D.Us;
+        off += (size_t)D.ne * NV * D.nu;
+    }
+    if ((rc = rhs_internal<T>(c, in, nullptr, s))) return rc;
+    off = 0;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_int_to_pub<T>(D.nu, D.ne, D.np, (const T *)D.R, r_dev + off, s), "rhs layout out")))
+            return rc;
+        off += (size_t)D.ne * NV * D.nu;
+    }
+    return FR_OK;
+}
+
+template <typename T>
+int step_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
+    const double ca[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+    const double cs[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+    if (nsteps <= 0) return FR_OK;
+    // the centred stage input is derived from the FP64 register (fr_rhs
+    // reuses its buffer); the last stage of every step keeps it current
+    const Phys ph = phys_of(c);
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        int rc = cuda_check(launch_center<T>(D.nu, D.np, D.U, (T *)D.Us, ph.uref, s), "centre");
+        if (rc) return rc;
+    }
+    for (int it = 0; it < nsteps; ++it)
+        for (int st = 0; st < 4; ++st) {
+            T *in[2] = {nullptr, nullptr};
+            for (int t = 0; t < 2; ++t)
+                if (c->T[t].present) in[t] = (T *)c->T[t].Us;
+            RKStage rk{ca[st], cs[st], st == 0, st == 3};
+            int rc = rhs_internal<T>(c, in, &rk, s);
+            if (rc) return rc;
+        }
+    return FR_OK;
 }
 
 }  // namespace
@@ -560,11 +706,13 @@ int fr_set_state(fr_ctx *c, const double *u, void *stream) {
         if (!D.present) continue;
         const size_t n = (size_t)D.ne * NV * D.nu;
         int rc;
-        if ((rc = cuda_check(cudaMemcpyAsync(D.R, u + off, n * sizeof(double), cudaMemcpyHostToDevice, s),
+        // stage through the accumulator register (overwritten by every step)
+        if ((rc = cuda_check(cudaMemcpyAsync(D.Uacc, u + off, n * sizeof(double), cudaMemcpyHostToDevice, s),
                              "set_state copy")))
             return rc;
-        const Phys ph = phys_of(c);
-        if ((rc = cuda_check(launch_pub_to_int(D.nu, D.ne, D.np, D.R, D.U, s, D.Us, ph.uref), "set_state layout")))
+        if ((rc = cuda_check(launch_pub_to_int<double>(D.nu, D.ne, D.np, (const double *)D.Uacc, D.U, s, nullptr,
+                                                       nullptr),
+                             "set_state layout")))
             return rc;
         off += n;
     }
@@ -580,8 +728,9 @@ int fr_get_state(fr_ctx *c, double *u, void *stream) {
         if (!D.present) continue;
         const size_t n = (size_t)D.ne * NV * D.nu;
         int rc;
-        if ((rc = cuda_check(launch_int_to_pub(D.nu, D.ne, D.np, D.U, D.R, s), "get_state layout"))) return rc;
-        if ((rc = cuda_check(cudaMemcpyAsync(u + off, D.R, n * sizeof(double), cudaMemcpyDeviceToHost, s),
+        if ((rc = cuda_check(launch_int_to_pub<double>(D.nu, D.ne, D.np, D.U, D.Uacc, s), "get_state layout")))
+            return rc;
+        if ((rc = cuda_check(cudaMemcpyAsync(u + off, D.Uacc, n * sizeof(double), cudaMemcpyDeviceToHost, s),
                              "get_state copy")))
             return rc;
         off += n;
@@ -593,57 +742,13 @@ int fr_rhs(fr_ctx *c, const double *u_dev, double *r_dev, void *stream) {
     if (!c || !u_dev || !r_dev) return set_err(FR_ERR_ARG, "null argument");
     if (u_dev == r_dev) return set_err(FR_ERR_ARG, "u and r may not alias");
     cudaStream_t s = (cudaStream_t)stream;
-    size_t off = 0;
-    double *in[2] = {nullptr, nullptr};
-    int rc;
-    for (int t = 0; t < 2; ++t) {
-        DevType &D = c->T[t];
-        if (!D.present) continue;
-        const Phys ph = phys_of(c);
-        if ((rc = cuda_check(launch_pub_to_int(D.nu, D.ne, D.np, u_dev + off, nullptr, s, D.Us, ph.uref),
-                             "rhs layout in")))
-            return rc;
-        in[t] = D.Us;
-        off += (size_t)D.ne * NV * D.nu;
-    }
-    if ((rc = rhs_internal(c, in, nullptr, s))) return rc;
-    off = 0;
-    for (int t = 0; t < 2; ++t) {
-        DevType &D = c->T[t];
-        if (!D.present) continue;
-        if ((rc = cuda_check(launch_int_to_pub(D.nu, D.ne, D.np, D.R, r_dev + off, s), "rhs layout out")))
-            return rc;
-        off += (size_t)D.ne * NV * D.nu;
-    }
-    return FR_OK;
+    return c->prm.precision == FR_FP32 ? rhs_public<float>(c, u_dev, r_dev, s) : rhs_public<double>(c, u_dev, r_dev, s);
 }
 
 int fr_step(fr_ctx *c, double dt, int nsteps, void *stream) {
     if (!c || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
     cudaStream_t s = (cudaStream_t)stream;
-    const double ca[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
-    const double cs[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
-    if (nsteps > 0) {
-        // the centred stage input is derived from the FP64 register (fr_rhs
-        // reuses its buffer); the last stage of every step keeps it current
-        const Phys ph = phys_of(c);
-        for (int t = 0; t < 2; ++t) {
-            DevType &D = c->T[t];
-            if (!D.present) continue;
-            int rc = cuda_check(launch_center(D.nu, D.np, D.U, D.Us, ph.uref, s), "centre");
-            if (rc) return rc;
-        }
-    }
-    for (int it = 0; it < nsteps; ++it)
-        for (int st = 0; st < 4; ++st) {
-            double *in[2] = {nullptr, nullptr};
-            for (int t = 0; t < 2; ++t)
-                if (c->T[t].present) in[t] = c->T[t].Us;
-            RKStage rk{ca[st], cs[st], st == 0, st == 3};
-            int rc = rhs_internal(c, in, &rk, s);
-            if (rc) return rc;
-        }
-    return FR_OK;
+    return c->prm.precision == FR_FP32 ? step_impl<float>(c, dt, nsteps, s) : step_impl<double>(c, dt, nsteps, s);
 }
 
 int fr_reduce(fr_ctx *c, double *out, void *stream) {

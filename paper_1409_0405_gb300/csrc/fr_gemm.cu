@@ -1,4 +1,5 @@
-// FP64 operator application C <- A [B1; B2] with fused epilogues.
+// Operator application C <- A [B1; B2] with fused epilogues, in FP64 or
+// FP32 (T), the RK register update always in FP64.
 //
 // Every operator application of an FR step is a constant operator matrix A
 // (at most 225 x 330 here) times a row-major state matrix B whose columns
@@ -10,11 +11,13 @@
 // every thread streams its column of B once per chunk, accumulating RC
 // outputs in registers.
 //
-// On GB300 the FP64 pipe issues about 2 FMA per clock per SM, so these
+// On GB300 the FP64 pipe issues about 2 FMA per clock per SM, so the FP64
 // kernels are bound by FP64 issue, not by HBM (2 flop per 8-byte B element
 // per row of A, 2*RC flop per B load): the design goal is to keep the FP64
 // pipe fed and to waste no FMA on padding rows, hence RC is chosen per
 // operator among the instantiated sizes to divide M with the least waste.
+// The FP32 pipe is 64x wider; there the same kernel is bound by issue and
+// by the L2 traffic of re-reading B once per row chunk.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -26,49 +29,54 @@ namespace {
 
 constexpr int kThreads = 128;
 
-template <int RC, int MODE>
-__global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgs g) {
-    extern __shared__ double sA[];  // [K][RC]
+template <typename T, int RC, int MODE>
+__global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgsT<T> g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);  // [K][RC]
     const int K = g.K1 + g.K2;
-    const int m0 = blockIdx.y * RC;
+    // 1-D grid, row chunk fastest: the chunks of one column tile run back
+    // to back, so that tile of B is read from DRAM once and then from L2
+    const int nchunks = (g.M + RC - 1) / RC;
+    const int m0 = (int)(blockIdx.x % nchunks) * RC;
+    const int64_t tile = blockIdx.x / nchunks;
     for (int idx = threadIdx.x; idx < RC * K; idx += kThreads) {
         const int r = idx / K, k = idx - r * K;
-        sA[k * RC + r] = (m0 + r < g.M) ? g.A[(size_t)(m0 + r) * K + k] : 0.0;
+        sA[k * RC + r] = (m0 + r < g.M) ? g.A[(size_t)(m0 + r) * K + k] : T(0);
     }
     __syncthreads();
-    const int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t n = tile * kThreads + threadIdx.x;
     if (n >= g.N) return;
 
-    double acc[RC];
+    T acc[RC];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) acc[r] = 0.0;
+    for (int r = 0; r < RC; ++r) acc[r] = T(0);
 
     {
-        const double *b = g.B1 + n;
+        const T *b = g.B1 + n;
         const int64_t ld = g.ldb1;
 #pragma unroll 2
         for (int k = 0; k < g.K1; ++k) {
-            const double bv = __ldg(b + (int64_t)k * ld);
-            const double *a = sA + k * RC;
+            const T bv = __ldg(b + (int64_t)k * ld);
+            const T *a = sA + k * RC;
 #pragma unroll
             for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
         }
     }
     if (g.K2 > 0) {
-        const double *b = g.B2 + n;
+        const T *b = g.B2 + n;
         const int64_t ld = g.ldb2;
-        const double *a0 = sA + g.K1 * RC;
+        const T *a0 = sA + g.K1 * RC;
 #pragma unroll 2
         for (int k = 0; k < g.K2; ++k) {
-            const double bv = __ldg(b + (int64_t)k * ld);
-            const double *a = a0 + k * RC;
+            const T bv = __ldg(b + (int64_t)k * ld);
+            const T *a = a0 + k * RC;
 #pragma unroll
             for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
         }
     }
 
     if (MODE == GEMM_STORE) {
-        const double add = g.add_ref ? g.uref[n / g.np] : 0.0;
+        const T add = g.add_ref ? T(g.uref[n / g.np]) : T(0);
 #pragma unroll
         for (int r = 0; r < RC; ++r)
             if (m0 + r < g.M) g.C[(int64_t)(m0 + r) * g.ldc + n] = acc[r] + add;
@@ -79,13 +87,12 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgs g) {
         for (int jj = 0; jj < RC / 3; ++jj) {
             const int j = m0 / 3 + jj;
             if (3 * j >= g.M) break;
-            const double *S = g.S + (int64_t)j * 9 * g.np + e;
-            const double ij = g.invJ[(int64_t)j * g.np + e];
-            const double g0 = acc[3 * jj], g1 = acc[3 * jj + 1], g2 = acc[3 * jj + 2];
+            const T *S = g.S + (int64_t)j * 9 * g.np + e;
+            const T ij = g.invJ[(int64_t)j * g.np + e];
+            const T g0 = acc[3 * jj], g1 = acc[3 * jj + 1], g2 = acc[3 * jj + 2];
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                const double s0 = S[(0 * 3 + m) * g.np], s1 = S[(1 * 3 + m) * g.np],
-                             s2 = S[(2 * 3 + m) * g.np];
+                const T s0 = S[(0 * 3 + m) * g.np], s1 = S[(1 * 3 + m) * g.np], s2 = S[(2 * 3 + m) * g.np];
                 g.C[(int64_t)(3 * j + m) * g.ldc + n] = ij * (s0 * g0 + s1 * g1 + s2 * g2);
             }
         }
@@ -97,38 +104,41 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgs g) {
             const int j = m0 + r;
             if (j >= g.M) break;
             const int64_t idx = (int64_t)j * g.ldc + n;
-            const double rv = fma(-g.invJ[(int64_t)j * g.np + e], acc[r], g.rfs ? g.rfs[idx] : 0.0);
+            const T rt = -g.invJ[(int64_t)j * g.np + e] * acc[r];
             if (MODE == GEMM_DIV) {
-                g.C[idx] = rv;
+                g.C[idx] = g.rfs ? T((double)rt + g.rfs[idx]) : rt;
             } else {
+                // FP64 register update (both modes)
+                const double rv = (double)rt + (g.rfs ? g.rfs[idx] : 0.0);
                 const double u = g.U[idx];
                 if (g.rk_last) {
                     const double un = g.Uacc[idx] + g.c_acc * rv;
                     g.U[idx] = un;
-                    g.Us[idx] = un - ur;
+                    g.Us[idx] = T(un - ur);
                 } else {
                     g.Uacc[idx] = (g.rk_first ? u : g.Uacc[idx]) + g.c_acc * rv;
-                    g.Us[idx] = (u - ur) + g.c_stage * rv;
+                    g.Us[idx] = T((u - ur) + g.c_stage * rv);
                 }
             }
         }
     }
 }
 
-template <int RC, int MODE>
-cudaError_t run(const GemmArgs &g, cudaStream_t s) {
+template <typename T, int RC, int MODE>
+cudaError_t run(const GemmArgsT<T> &g, cudaStream_t s) {
     const int K = g.K1 + g.K2;
-    const size_t smem = (size_t)RC * K * sizeof(double);
+    const size_t smem = (size_t)RC * K * sizeof(T);
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<T, RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((g.N + kThreads - 1) / kThreads), (unsigned)((g.M + RC - 1) / RC));
-    k_gemm<RC, MODE><<<grid, kThreads, smem, s>>>(g);
+    const int64_t blocks = ((g.N + kThreads - 1) / kThreads) * ((g.M + RC - 1) / RC);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_gemm<T, RC, MODE><<<(unsigned)blocks, kThreads, smem, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -152,12 +162,12 @@ int pick_rc(int M, bool mult3) {
     return best;
 }
 
-template <int MODE>
-cudaError_t dispatch(int rc, const GemmArgs &g, cudaStream_t s) {
+template <typename T, int MODE>
+cudaError_t dispatch(int rc, const GemmArgsT<T> &g, cudaStream_t s) {
     switch (rc) {
 #define FR_RC(X) \
     case X:      \
-        return run<X, MODE>(g, s);
+        return run<T, X, MODE>(g, s);
         FR_RC(30) FR_RC(27) FR_RC(24) FR_RC(21) FR_RC(18) FR_RC(15) FR_RC(12) FR_RC(9) FR_RC(6) FR_RC(3)
 #undef FR_RC
     }
@@ -165,7 +175,7 @@ cudaError_t dispatch(int rc, const GemmArgs &g, cudaStream_t s) {
         switch (rc) {
 #define FR_RC(X) \
     case X:      \
-        return run<(MODE == GEMM_GRAD ? 3 : X), MODE>(g, s);
+        return run<T, (MODE == GEMM_GRAD ? 3 : X), MODE>(g, s);
             FR_RC(25) FR_RC(20) FR_RC(17) FR_RC(13) FR_RC(10) FR_RC(8) FR_RC(5) FR_RC(4)
 #undef FR_RC
         }
@@ -175,20 +185,24 @@ cudaError_t dispatch(int rc, const GemmArgs &g, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_gemm_f64(const GemmArgs &g, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_gemm(const GemmArgsT<T> &g, cudaStream_t s) {
     if (g.N <= 0 || g.M <= 0) return cudaSuccess;
     const int rc = pick_rc(g.M, g.mode == GEMM_GRAD);
     switch (g.mode) {
         case GEMM_STORE:
-            return dispatch<GEMM_STORE>(rc, g, s);
+            return dispatch<T, GEMM_STORE>(rc, g, s);
         case GEMM_GRAD:
-            return dispatch<GEMM_GRAD>(rc, g, s);
+            return dispatch<T, GEMM_GRAD>(rc, g, s);
         case GEMM_DIV:
-            return dispatch<GEMM_DIV>(rc, g, s);
+            return dispatch<T, GEMM_DIV>(rc, g, s);
         case GEMM_DIV_RK:
-            return dispatch<GEMM_DIV_RK>(rc, g, s);
+            return dispatch<T, GEMM_DIV_RK>(rc, g, s);
     }
     return cudaErrorInvalidValue;
 }
+
+template cudaError_t launch_gemm<double>(const GemmArgsT<double> &, cudaStream_t);
+template cudaError_t launch_gemm<float>(const GemmArgsT<float> &, cudaStream_t);
 
 }  // namespace fr

@@ -1,4 +1,9 @@
 // Launch interface of the FR engine's CUDA kernels (internal).
+//
+// Every kernel of the right-hand side is templated on its arithmetic type T
+// (double for FR_FP64, float for FR_FP32: Table 1 lists single and double
+// precision).  The RK registers, the reference-flux correction and the
+// reductions are double in both modes.
 #pragma once
 
 #include <cstdint>
@@ -8,45 +13,49 @@ namespace fr {
 
 // Epilogues of the operator application C <- A [B1; B2] (Sec. 2.1, Eq. 1).
 enum GemmMode {
-    GEMM_STORE = 0,  // C = A B
+    GEMM_STORE = 0,  // C = A B (+ uref[variable] with add_ref)
     GEMM_GRAD = 1,   // rows (j, d): C(j, m) = (1/J) sum_d S[d][m] (A B)(j, d)
-    GEMM_DIV = 2,    // C(j) = -(1/J_j) (A B)(j)
-    GEMM_DIV_RK = 3  // r = -(1/J)(A B); fused RK4 register update
+    GEMM_DIV = 2,    // C(j) = -(1/J_j) (A B)(j) + rfs
+    GEMM_DIV_RK = 3  // r = -(1/J)(A B) + rfs; fused RK4 register update
 };
 
-struct GemmArgs {
+template <typename T>
+struct GemmArgsT {
     int M = 0;            // rows of A and C
     int64_t N = 0;        // columns of B and C
     int K1 = 0, K2 = 0;   // A = [A1 | A2], B = [B1; B2]
-    const double *A = nullptr;  // M x (K1 + K2), row-major
-    const double *B1 = nullptr;
+    const T *A = nullptr;  // M x (K1 + K2), row-major
+    const T *B1 = nullptr;
     int64_t ldb1 = 0;
-    const double *B2 = nullptr;
+    const T *B2 = nullptr;
     int64_t ldb2 = 0;
-    double *C = nullptr;
+    T *C = nullptr;
     int64_t ldc = 0;
     int mode = GEMM_STORE;
     int64_t np = 0;             // element stride: column n belongs to element n % np
-    const double *invJ = nullptr;  // [nu][np]
-    const double *S = nullptr;     // [nu][9][np]
+    const T *invJ = nullptr;    // [nu][np]
+    const T *S = nullptr;       // [nu][9][np]
     // GEMM_DIV_RK: with r the RHS,
     //   rk_first: Uacc = U + c_acc r,  else Uacc += c_acc r
-    //   !rk_last: Us = U + c_stage r;  rk_last: U = Uacc + c_acc r
-    double *U = nullptr, *Uacc = nullptr, *Us = nullptr;
+    //   !rk_last: Us = U + c_stage r - uref;  rk_last: U = Uacc + c_acc r, Us = U - uref
+    double *U = nullptr, *Uacc = nullptr;
+    T *Us = nullptr;
     double c_acc = 0, c_stage = 0;
     int rk_first = 0, rk_last = 0;
     // centring: the stage input Us holds u - uref (uref = the far-field
-    // conserved state, one value per variable, column n has variable
-    // n / np).  GEMM_STORE with add_ref adds uref back; GEMM_DIV_RK writes
-    // Us relative to uref.
+    // conserved state, one value per variable; column n has variable
+    // n / np).  GEMM_STORE with add_ref adds uref back.
     int add_ref = 0;
     double uref[5] = {0, 0, 0, 0, 0};
     // GEMM_DIV(_RK): constant field added to r (the discrete divergence of
     // the subtracted reference flux, see Phys::fref); may be null
     const double *rfs = nullptr;
 };
+using GemmArgs = GemmArgsT<double>;
 
-cudaError_t launch_gemm_f64(const GemmArgs &g, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gemm(const GemmArgsT<T> &g, cudaStream_t s);
+inline cudaError_t launch_gemm_f64(const GemmArgs &g, cudaStream_t s) { return launch_gemm<double>(g, s); }
 
 struct Phys {
     double gamma, mu, prandtl, beta, tau;
@@ -64,13 +73,15 @@ struct Phys {
 };
 
 // Per-type field pointers (index 0 tet, 1 prism); nullptr for an absent type.
-struct Fields {
-    const double *UF[2];   // [nf][V][np]
-    double *DUF[2];        // [nf][V][np]
-    const double *GUF[2];  // [nf][3][V][np]
-    double *FC[2];         // [nf][V][np]
+template <typename T>
+struct FieldsT {
+    const T *UF[2];   // [nf][V][np]
+    T *DUF[2];        // [nf][V][np]
+    const T *GUF[2];  // [nf][3][V][np]
+    T *FC[2];         // [nf][V][np]
     int64_t np[2];
 };
+using Fields = FieldsT<double>;
 
 struct Pairs {
     int64_t n;
@@ -84,27 +95,35 @@ struct Bnd {
     const double *bn, *bmag;
 };
 
-cudaError_t launch_common_solution(const Pairs &P, const Bnd &B, const Fields &F, const Phys &ph,
+template <typename T>
+cudaError_t launch_common_solution(const Pairs &P, const Bnd &B, const FieldsT<T> &F, const Phys &ph,
                                    cudaStream_t s);
-cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const Fields &F, const Phys &ph,
+template <typename T>
+cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const FieldsT<T> &F, const Phys &ph,
                                cudaStream_t s);
-// transformed flux at the solution points of one type
-// U is the centred stage input (u - uref)
-cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const double *U, const double *GU,
-                        const double *S, double *FT, const Phys &ph, cudaStream_t s);
-// public [e][v][j] <-> internal [j][v][e]; pub_to_int optionally also
-// writes the centred copy in - uref into `centred`
-cudaError_t launch_pub_to_int(int nu, int64_t ne, int64_t np, const double *pub, double *in,
-                              cudaStream_t s, double *centred = nullptr, const double *uref = nullptr);
-cudaError_t launch_int_to_pub(int nu, int64_t ne, int64_t np, const double *in, double *pub,
-                              cudaStream_t s);
+// transformed flux at the solution points of one type; U is the centred
+// stage input (u - uref)
+template <typename T>
+cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, const T *GU, const T *S, T *FT,
+                        const Phys &ph, cudaStream_t s);
+// public [e][v][j] (double) -> internal [j][v][e]: `in` (double, may be
+// null) receives the values, `centred` (T, may be null) u - uref
+template <typename T>
+cudaError_t launch_pub_to_int(int nu, int64_t ne, int64_t np, const double *pub, double *in, cudaStream_t s,
+                              T *centred, const double *uref);
+// internal [j][v][e] (T) -> public [e][v][j] (double)
+template <typename T>
+cudaError_t launch_int_to_pub(int nu, int64_t ne, int64_t np, const T *in, double *pub, cudaStream_t s);
 // transformed reference flux at solution points, FT = S F_ref (padding 0)
 cudaError_t launch_const_flux(int nu, int64_t ne, int64_t np, const double *S, double *FT, const Phys &ph,
                               cudaStream_t s);
 // reference normal flux at every flux point, FC = F_ref.n |S^T n^|
 cudaError_t launch_const_common(const Pairs &P, const Bnd &B, const Fields &F, const Phys &ph, cudaStream_t s);
 // Us = U - uref over a whole [nu][V][np] register
-cudaError_t launch_center(int nu, int64_t np, const double *U, double *Us, const double *uref, cudaStream_t s);
+template <typename T>
+cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const double *uref, cudaStream_t s);
+// element-wise double -> float copy
+cudaError_t launch_to_float(int64_t n, const double *src, float *dst, cudaStream_t s);
 // per-block partial integrals (7 per block) of one type's register
 cudaError_t launch_reduce_partial(int nu, int64_t ne, int64_t np, const double *U, const double *wJ,
                                   double gamma, double *partial, int nblocks, cudaStream_t s);

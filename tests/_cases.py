@@ -28,6 +28,7 @@ def make_pair(mesh, p, **params):
     """(oracle solver, library context) for the same mesh/order/params."""
     from paper_1409_0405_gb300 import fr
     ctx = fr.Context(mesh, p, **params)
+    params = {k: v for k, v in params.items() if k != "precision"}
     sol = Solver(mesh, p, gamma=params.get("gamma", GAMMA), mu=params.get("mu", 0.0),
                  prandtl=params.get("prandtl", 0.72), viscous=bool(params.get("viscous", False)),
                  ldg_beta=params.get("ldg_beta", 0.5), ldg_tau=params.get("ldg_tau", 0.1),

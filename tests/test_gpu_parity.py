@@ -173,3 +173,54 @@ def test_full_size_boundary_layer_rhs():
     u = state(sol, "bl")
     err = _check_rhs(sol, ctx, u)
     assert math.isfinite(float(err.max()))
+
+
+# ---------------------------------------------------------------------------
+# FR_FP32: operator applications and point-wise work in FP32, RK registers,
+# the reference-flux correction and the reductions in FP64.  Reported against
+# the FP64 oracle; the tolerances bound the measured single-precision error.
+# ---------------------------------------------------------------------------
+FP32_RHS_TOL = 2e-5
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_fp32_rhs_error_periodic(viscous):
+    from paper_1409_0405_gb300 import fr
+    sol, ctx = make_pair(synth.vortex_box(), 3, viscous=viscous, mu=0.05, precision=fr.FR_FP32)
+    u = state(sol, "smooth", seed=4)
+    err = per_quantity_rel_err(sol, sol.rhs(u), gpu_rhs(ctx, u))
+    print("fp32 rhs error (mass, momentum, energy):", err)
+    assert np.all(err <= FP32_RHS_TOL), err
+
+
+def test_fp32_rhs_error_wall_bounded():
+    from paper_1409_0405_gb300 import fr
+    m = synth.boundary_layer_box(nx=7, nz=3, n_prism_layers=5, n_tet_layers=3)
+    sol, ctx = make_pair(m, 4, **bl_params(), precision=fr.FR_FP32)
+    u = state(sol, "bl")
+    err = per_quantity_rel_err(sol, sol.rhs(u), gpu_rhs(ctx, u))
+    print("fp32 wall-bounded rhs error:", err)
+    assert np.all(err <= FP32_RHS_TOL), err
+
+
+def test_fp32_rk4_vortex_state_error():
+    """100 RK4 steps of the vortex in FR_FP32: the state increment
+    u(T) - u(0) against the FP64 oracle's."""
+    from paper_1409_0405_gb300 import fr
+    sol, ctx = make_pair(synth.vortex_box(), 2, precision=fr.FR_FP32)
+    u0 = state(sol, "vortex")
+    dt = sol.dt_cfl(u0, 0.1)
+    ctx.set_state(u0)
+    ctx.step(dt, 100)
+    got = ctx.get_state()
+    ref = u0
+    for _ in range(100):
+        ref = sol.rk4_step(ref, dt)
+    err = per_quantity_rel_err(sol, ref - u0, got - u0)
+    print("fp32 100-step increment error:", err)
+    assert np.all(err <= 1e-4), err
+    # FP64 reductions of the FP64 register: the FP32 fluxes conserve the
+    # totals only to single-precision rounding of the RHS sums
+    out = ctx.reduce()
+    tot = sol.integrals(u0)
+    assert np.max(np.abs(out[:5] - tot)) <= 1e-7 * np.max(np.abs(tot)), (out[:5], tot)

@@ -198,6 +198,40 @@ int fr_profile_read(fr_ctx *ctx, double *ms, int64_t *count, int64_t *launches);
 int fr_peak_fp64(double *gflops, void *cuda_stream);
 
 /*
+ * Batched engine: many independent problems (their own meshes, element
+ * mixes and orders, the same fr_params) advanced together.  Every RK stage
+ * of the whole batch runs as a few grouped persistent launches (one per
+ * operator class and one per point-wise kernel, each walking a device work
+ * list over all problems and element types), and one RK step is captured in
+ * a CUDA graph.  The results are bit-identical to advancing each problem on
+ * its own.
+ *
+ * fr_batch_create: builds nprob contexts (meshes[i], orders[i], *params) and
+ *   the work lists.  Errors as fr_create.
+ * fr_batch_problem: the context of problem i (owned by the batch: use it with
+ *   fr_set_state / fr_get_state / fr_rhs / fr_reduce, never fr_destroy).
+ * fr_batch_tune: times the candidate row-chunk sizes and persistent grid
+ *   sizes of every grouped launch on this batch and keeps the fastest
+ *   (leaves the solution registers untouched).  Synchronous.
+ * fr_batch_step: nsteps RK4 steps, dt[i] for problem i (host array of
+ *   nprob).  batched != 0: grouped launches replayed from a CUDA graph
+ *   (captured on first use and after tuning or a change of dt); batched == 0:
+ *   each problem's own launch sequence, one after another (the comparison).
+ *   Asynchronous on cuda_stream.
+ * fr_batch_info: out (12 int64): nprob, total DOF, launches per step of the
+ *   batched graph, launches per step of the per-problem sequence, the tuned
+ *   row-chunk sizes (M0, gradient, M0 on gradients, divergence) and grids
+ *   (GEMM, divergence, flux, face kernels).
+ */
+typedef struct fr_batch fr_batch;
+int fr_batch_create(int nprob, const fr_mesh *meshes, const int *orders, const fr_params *params, fr_batch **out);
+void fr_batch_destroy(fr_batch *b);
+int fr_batch_problem(fr_batch *b, int i, fr_ctx **ctx);
+int fr_batch_tune(fr_batch *b, void *cuda_stream);
+int fr_batch_step(fr_batch *b, const double *dt, int nsteps, int batched, void *cuda_stream);
+int fr_batch_info(const fr_batch *b, int64_t *out);
+
+/*
  * fr_reduce_noalloc: the integrals of fr_reduce for callers that cannot
  * allocate device memory.  The paper has no counterpart; this entry point
  * exists for code that may not call cudaMalloc (a device owned by another

@@ -116,20 +116,8 @@ class Solver:
 
         grad = {}
         if self.viscous:
-            # 2. common solution and jumps
-            C = physics.ldg_common_solution(ua, ub, self.sign, self.beta)
-            DL = np.empty_like(UF)
-            DL[m.pa] = C - ua
-            DL[m.pb] = C - ub
-            DL[m.bg] = cb - ubnd
-            delta = m.from_global(DL)
-            # 3. corrected gradient, physical
-            for t in self.types:
-                op = ops[t]
-                gh = np.stack([u[t] @ op.D[d].T + (op.fnorm[:, d] * delta[t]) @ op.M3.T
-                               for d in range(3)], axis=-1)           # (ne, V, nu, d)
-                grad[t] = (np.einsum("ejdm,evjd->evjm", m.S[t], gh)
-                           / m.J[t][:, None, :, None])                # (ne, V, nu, m)
+            # 2-3. common solution, jumps, corrected physical gradient
+            grad = self._gradient(u, UF, ua, ub, ubnd, cb)
             # 4. gradients at flux points
             gradf = {t: np.stack([grad[t][..., k] @ ops[t].M0.T for k in range(3)],
                                  axis=-1) for t in self.types}        # (ne, V, nf, m)
@@ -171,6 +159,37 @@ class Solver:
             fn_int = sum(op.fnorm[:, d] * (Ft[t][..., d] @ op.M0.T) for d in range(3))
             R[t] = -(div + (fc[t] - fn_int) @ op.M3.T) / m.J[t][:, None, :]
         return self.join(R)
+
+    def _gradient(self, u, UF, ua, ub, ubnd, cb):
+        m, ops = self.m, self.m.ops
+        # 2. common solution and jumps
+        C = physics.ldg_common_solution(ua, ub, self.sign, self.beta)
+        DL = np.empty_like(UF)
+        DL[m.pa] = C - ua
+        DL[m.pb] = C - ub
+        DL[m.bg] = cb - ubnd
+        delta = m.from_global(DL)
+        # 3. corrected gradient, physical
+        grad = {}
+        for t in self.types:
+            op = ops[t]
+            gh = np.stack([u[t] @ op.D[d].T + (op.fnorm[:, d] * delta[t]) @ op.M3.T
+                           for d in range(3)], axis=-1)           # (ne, V, nu, d)
+            grad[t] = (np.einsum("ejdm,evjd->evjm", m.S[t], gh)
+                       / m.J[t][:, None, :, None])                # (ne, V, nu, m)
+        return grad
+
+    def gradient(self, u_flat):
+        """The corrected physical gradient at the solution points, per type
+        (ne, V, nu, 3), as the Navier-Stokes RHS computes it."""
+        m = self.m
+        u = self.split(np.asarray(u_flat, dtype=np.float64))
+        uf = {t: u[t] @ m.ops[t].M0.T for t in self.types}
+        UF = m.to_global(uf)
+        ua, ub = UF[m.pa], UF[m.pb]
+        ubnd = UF[m.bg]
+        _, cb = self._boundary(ubnd, m.gn[m.bg])
+        return self._gradient(u, UF, ua, ub, ubnd, cb)
 
     # -- time stepping and reductions ----------------------------------------
     def rk4_step(self, u, dt):

@@ -26,10 +26,12 @@
 #include <string>
 #include <vector>
 
+#include "fr_ctx.h"
 #include "fr_internal.h"
 #include "fr_kernels.h"
 
-namespace {
+namespace fr {
+namespace api {
 
 thread_local std::string g_last_error;
 
@@ -38,55 +40,14 @@ int set_err(int code, const std::string &msg) {
     return code;
 }
 
-}  // namespace
+}  // namespace api
+}  // namespace fr
 
 using namespace fr;
+using namespace fr::api;
 
-struct DevType {
-    int present = 0;
-    int64_t ne = 0, np = 0;
-    int nu = 0, nf = 0;
-    // FP64 in every mode: RK registers, quadrature weights, the reference-flux
-    // divergence, and the geometry/operators the set-up evaluates with
-    double *U = nullptr, *Uacc = nullptr;   // [nu][V][np]
-    double *wJ = nullptr;                   // [nu][np]
-    double *Rfs = nullptr;                  // [nu][V][np]
-    double *S = nullptr, *invJ = nullptr;   // [nu][9][np], [nu][np]
-    double *M0 = nullptr, *AGRAD = nullptr, *ADIV = nullptr;
-    // buffers in the arithmetic type of the right-hand side (double for
-    // FR_FP64, float for FR_FP32; the geometry/operator views alias the
-    // double arrays in FR_FP64)
-    void *Us = nullptr, *R = nullptr;        // [nu][V][np]
-    void *UF = nullptr, *DUF = nullptr, *FC = nullptr;   // [nf][V][np]
-    void *GU = nullptr, *FT = nullptr;       // [nu][3][V][np]
-    void *GUF = nullptr;                     // [nf][3][V][np]
-    void *S_t = nullptr, *invJ_t = nullptr, *M0_t = nullptr, *AGRAD_t = nullptr, *ADIV_t = nullptr;
-    std::vector<double> xu;  // host: ne x nu x 3 physical solution points
-};
-
-struct fr_ctx {
-    fr_params prm{};
-    int order = 0;
-    int device = 0;
-    DevType T[2];
-    int64_t npairs = 0, nbnd = 0;
-    int *ta = nullptr, *fa = nullptr, *ea = nullptr, *tb = nullptr, *fb = nullptr, *eb = nullptr;
-    double *nrm = nullptr, *maga = nullptr, *magb = nullptr;
-    int *bt = nullptr, *bf = nullptr, *be = nullptr, *btag = nullptr;
-    double *bn = nullptr, *bmag = nullptr;
-    double *red = nullptr;  // reduction partials + result
-    int red_blocks[2] = {0, 0};
-    std::vector<void *> allocs;
-    // launch accounting: count of kernel launches, and (when profiling is
-    // on) a CUDA event pair around every launch, tagged by kernel class
-    int64_t launches = 0;
-    int prof = 0;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-};
-
-namespace {
+namespace fr {
+namespace api {
 
 constexpr int64_t kPad = 32;
 
@@ -184,7 +145,6 @@ Pairs pairs_of(const fr_ctx *c) {
 
 Bnd bnd_of(const fr_ctx *c) { return Bnd{c->nbnd, c->bt, c->bf, c->be, c->btag, c->bn, c->bmag}; }
 
-enum KClass { K_M0 = 0, K_COMMON_SOL, K_GRAD, K_M0_GRAD, K_FLUX, K_COMMON_FLUX, K_DIV, K_NCLASS };
 
 cudaEvent_t next_event(fr_ctx *c) {
     if (c->ev_used == c->ev_pool.size()) {
@@ -216,33 +176,111 @@ cudaError_t launch(fr_ctx *c, int kclass, cudaStream_t s, F fn) {
 
 // One RHS evaluation on the stage input `in[t]`; the final operator
 // application either stores R (rk == nullptr) or applies the RK update.
-struct RKStage {
-    double c_acc, c_stage;
-    int first, last;
-};
+
+// Arguments of the four operator applications of one element type (shared
+// by the per-context launches below and the grouped launches of the batch).
+template <typename T>
+GemmArgsT<T> args_m0(const fr_ctx *c, int t, const T *in) {
+    const DevType &D = c->T[t];
+    const Phys ph = phys_of(c);
+    GemmArgsT<T> g;
+    g.M = D.nf;
+    g.N = (int64_t)NV * D.np;
+    g.K1 = D.nu;
+    g.A = (const T *)D.M0_t;
+    g.B1 = in;
+    g.ldb1 = g.N;
+    g.C = (T *)D.UF;
+    g.ldc = g.N;
+    g.mode = GEMM_STORE;
+    g.np = D.np;
+    g.add_ref = 1;  // the stage input is centred; add u_inf back
+    for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
+    return g;
+}
+
+template <typename T>
+GemmArgsT<T> args_grad(const fr_ctx *c, int t, const T *in) {
+    const DevType &D = c->T[t];
+    GemmArgsT<T> g;
+    g.M = 3 * D.nu;
+    g.N = (int64_t)NV * D.np;
+    g.K1 = D.nu;
+    g.K2 = D.nf;
+    g.A = (const T *)D.AGRAD_t;
+    g.B1 = in;
+    g.ldb1 = g.N;
+    g.B2 = (const T *)D.DUF;
+    g.ldb2 = g.N;
+    g.C = (T *)D.GU;  // [nu][3][V][np]: row (j, m), N columns
+    g.ldc = g.N;
+    g.mode = GEMM_GRAD;
+    g.np = D.np;
+    g.invJ = (const T *)D.invJ_t;
+    g.S = (const T *)D.S_t;
+    return g;
+}
+
+template <typename T>
+GemmArgsT<T> args_m0grad(const fr_ctx *c, int t) {
+    const DevType &D = c->T[t];
+    GemmArgsT<T> h;
+    h.M = D.nf;
+    h.N = 3 * (int64_t)NV * D.np;
+    h.K1 = D.nu;
+    h.A = (const T *)D.M0_t;
+    h.B1 = (const T *)D.GU;
+    h.ldb1 = h.N;
+    h.C = (T *)D.GUF;
+    h.ldc = h.N;
+    h.mode = GEMM_STORE;
+    return h;
+}
+
+template <typename T>
+GemmArgsT<T> args_div(const fr_ctx *c, int t, const RKStage *rk) {
+    const DevType &D = c->T[t];
+    const Phys ph = phys_of(c);
+    GemmArgsT<T> g;
+    g.M = D.nu;
+    g.N = (int64_t)NV * D.np;
+    g.K1 = 3 * D.nu;
+    g.K2 = D.nf;
+    g.A = (const T *)D.ADIV_t;
+    g.B1 = (const T *)D.FT;
+    g.ldb1 = g.N;
+    g.B2 = (const T *)D.FC;
+    g.ldb2 = g.N;
+    g.ldc = g.N;
+    g.np = D.np;
+    g.invJ = (const T *)D.invJ_t;
+    g.rfs = D.Rfs;
+    for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
+    if (rk) {
+        g.mode = GEMM_DIV_RK;
+        g.U = D.U;
+        g.Uacc = D.Uacc;
+        g.Us = (T *)D.Us;
+        g.c_acc = rk->c_acc;
+        g.c_stage = rk->c_stage;
+        g.rk_first = rk->first;
+        g.rk_last = rk->last;
+    } else {
+        g.mode = GEMM_DIV;
+        g.C = (T *)D.R;
+    }
+    return g;
+}
 
 template <typename T>
 int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
     const Phys ph = phys_of(c);
     const FieldsT<T> F = fields_of<T>(c);
     int rc;
-    // 1. interpolate to flux points (the stage input is centred; add u_inf back)
+    // 1. interpolate to flux points
     for (int t = 0; t < 2; ++t) {
-        DevType &D = c->T[t];
-        if (!D.present) continue;
-        GemmArgsT<T> g;
-        g.M = D.nf;
-        g.N = (int64_t)NV * D.np;
-        g.K1 = D.nu;
-        g.A = (const T *)D.M0_t;
-        g.B1 = in[t];
-        g.ldb1 = g.N;
-        g.C = (T *)D.UF;
-        g.ldc = g.N;
-        g.mode = GEMM_STORE;
-        g.np = D.np;
-        g.add_ref = 1;
-        for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
+        if (!c->T[t].present) continue;
+        const GemmArgsT<T> g = args_m0<T>(c, t, in[t]);
         if ((rc = cuda_check(launch(c, K_M0, s, [&] { return launch_gemm<T>(g, s); }), "gemm M0"))) return rc;
     }
     if (c->prm.viscous) {
@@ -253,35 +291,10 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
             return rc;
         // 3. corrected physical gradient; 4. gradient at flux points
         for (int t = 0; t < 2; ++t) {
-            DevType &D = c->T[t];
-            if (!D.present) continue;
-            GemmArgsT<T> g;
-            g.M = 3 * D.nu;
-            g.N = (int64_t)NV * D.np;
-            g.K1 = D.nu;
-            g.K2 = D.nf;
-            g.A = (const T *)D.AGRAD_t;
-            g.B1 = in[t];
-            g.ldb1 = g.N;
-            g.B2 = (const T *)D.DUF;
-            g.ldb2 = g.N;
-            g.C = (T *)D.GU;  // [nu][3][V][np]: row (j, m), N columns
-            g.ldc = g.N;
-            g.mode = GEMM_GRAD;
-            g.np = D.np;
-            g.invJ = (const T *)D.invJ_t;
-            g.S = (const T *)D.S_t;
+            if (!c->T[t].present) continue;
+            const GemmArgsT<T> g = args_grad<T>(c, t, in[t]);
             if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return launch_gemm<T>(g, s); }), "gemm grad"))) return rc;
-            GemmArgsT<T> h;
-            h.M = D.nf;
-            h.N = 3 * (int64_t)NV * D.np;
-            h.K1 = D.nu;
-            h.A = (const T *)D.M0_t;
-            h.B1 = (const T *)D.GU;
-            h.ldb1 = h.N;
-            h.C = (T *)D.GUF;
-            h.ldc = h.N;
-            h.mode = GEMM_STORE;
+            const GemmArgsT<T> h = args_m0grad<T>(c, t);
             if ((rc = cuda_check(launch(c, K_M0_GRAD, s, [&] { return launch_gemm<T>(h, s); }), "gemm M0 grad")))
                 return rc;
         }
@@ -305,36 +318,8 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
         return rc;
     // 7. divergence plus correction
     for (int t = 0; t < 2; ++t) {
-        DevType &D = c->T[t];
-        if (!D.present) continue;
-        GemmArgsT<T> g;
-        g.M = D.nu;
-        g.N = (int64_t)NV * D.np;
-        g.K1 = 3 * D.nu;
-        g.K2 = D.nf;
-        g.A = (const T *)D.ADIV_t;
-        g.B1 = (const T *)D.FT;
-        g.ldb1 = g.N;
-        g.B2 = (const T *)D.FC;
-        g.ldb2 = g.N;
-        g.ldc = g.N;
-        g.np = D.np;
-        g.invJ = (const T *)D.invJ_t;
-        g.rfs = D.Rfs;
-        for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
-        if (rk) {
-            g.mode = GEMM_DIV_RK;
-            g.U = D.U;
-            g.Uacc = D.Uacc;
-            g.Us = (T *)D.Us;
-            g.c_acc = rk->c_acc;
-            g.c_stage = rk->c_stage;
-            g.rk_first = rk->first;
-            g.rk_last = rk->last;
-        } else {
-            g.mode = GEMM_DIV;
-            g.C = (T *)D.R;
-        }
+        if (!c->T[t].present) continue;
+        const GemmArgsT<T> g = args_div<T>(c, t, rk);
         if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return launch_gemm<T>(g, s); }), "gemm div"))) return rc;
     }
     return FR_OK;
@@ -581,7 +566,21 @@ int step_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
     return FR_OK;
 }
 
-}  // namespace
+template int step_impl<float>(fr_ctx *, double, int, cudaStream_t);
+template int step_impl<double>(fr_ctx *, double, int, cudaStream_t);
+template FieldsT<float> fields_of<float>(const fr_ctx *);
+template FieldsT<double> fields_of<double>(const fr_ctx *);
+#define FR_ARGS_INST(T)                                                      \
+    template GemmArgsT<T> args_m0<T>(const fr_ctx *, int, const T *);     \
+    template GemmArgsT<T> args_grad<T>(const fr_ctx *, int, const T *);   \
+    template GemmArgsT<T> args_m0grad<T>(const fr_ctx *, int);            \
+    template GemmArgsT<T> args_div<T>(const fr_ctx *, int, const RKStage *);
+FR_ARGS_INST(float)
+FR_ARGS_INST(double)
+#undef FR_ARGS_INST
+
+}  // namespace api
+}  // namespace fr
 
 extern "C" {
 

@@ -1,0 +1,541 @@
+// Batched engine: many independent FR problems (different meshes, element
+// mixes and orders) advanced together.
+//
+// Each RK stage of the whole batch is a handful of grouped, persistent
+// launches instead of one launch per kernel per problem: every operator
+// application of every problem and element type becomes a descriptor in a
+// device-resident work list, and one launch per operator class (M0,
+// corrected gradient, M0 on gradients, divergence + RK update) walks all
+// (descriptor, row chunk, column tile) blocks with a fixed grid; the
+// point-wise flux and face kernels likewise walk concatenated segments.
+// One RK step (4 stages) is captured in a CUDA graph and replayed.  The
+// row-chunk size and the persistent grid of every class are chosen by
+// timing the candidates on the batch itself (fr_batch_tune).
+//
+// The arithmetic of every output is the same as in the per-problem launch
+// sequence (same operators, same summation order), so the two agree bit
+// for bit; the batch only changes how the work is scheduled.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fr_ctx.h"
+
+using namespace fr;
+using namespace fr::api;
+
+namespace {
+
+template <typename T>
+struct Group {
+    int mode = 0, rc = 8, grid = 0, maxK = 0, ndesc = 0;
+    int64_t total = 0;
+    std::vector<GemmArgsT<T>> h;
+    GemmArgsT<T> *d = nullptr;
+    int64_t *begin = nullptr;
+};
+
+template <typename T>
+struct Segs {
+    std::vector<T> h;
+    std::vector<int64_t> hb;
+    T *d = nullptr;
+    int64_t *begin = nullptr;
+    int64_t total = 0;
+    int grid = 0;
+};
+
+int dev_put(void **p, const void *src, size_t bytes) {
+    if (!*p && cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_err(FR_ERR_NOMEM, "batch work-list allocation");
+    }
+    return cuda_check(cudaMemcpy(*p, src, bytes, cudaMemcpyHostToDevice), "batch work-list upload");
+}
+
+}  // namespace
+
+struct BatchBase {
+    virtual ~BatchBase() {}
+    virtual int tune(cudaStream_t s) = 0;
+    virtual int step(const double *dt, int nsteps, int batched, cudaStream_t s) = 0;
+    virtual void info(int64_t *out) const = 0;
+};
+
+struct fr_batch {
+    std::vector<fr_ctx *> ctx;
+    BatchBase *impl = nullptr;
+};
+
+namespace {
+
+template <typename T>
+struct BatchImpl : BatchBase {
+    fr_batch *b;
+    bool viscous;
+    Group<T> m0, grad, m0g, div[4];
+    Segs<FluxItem<T>> flux;
+    Segs<FaceItem<T>> face;
+    Segs<CenterItem<T>> center;
+    std::vector<double> dt_cur;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int launches_per_step = 0;
+    int nsm = 152;
+
+    explicit BatchImpl(fr_batch *bb) : b(bb) { viscous = bb->ctx[0]->prm.viscous != 0; }
+
+    ~BatchImpl() override {
+        auto fg = [](Group<T> &g) {
+            cudaFree(g.d);
+            cudaFree(g.begin);
+        };
+        fg(m0);
+        fg(grad);
+        fg(m0g);
+        for (auto &g : div) fg(g);
+        cudaFree(flux.d);
+        cudaFree(flux.begin);
+        cudaFree(face.d);
+        cudaFree(face.begin);
+        cudaFree(center.d);
+        cudaFree(center.begin);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+    }
+
+    // prefix sums of blocks for the group's row-chunk size, uploaded
+    int upload_group(Group<T> &g) {
+        std::vector<int64_t> bg(g.h.size());
+        int64_t tot = 0;
+        g.maxK = 0;
+        for (size_t i = 0; i < g.h.size(); ++i) {
+            bg[i] = tot;
+            tot += gemm_blocks(g.h[i].M, g.h[i].N, g.rc);
+            g.maxK = std::max(g.maxK, g.h[i].K1 + g.h[i].K2);
+        }
+        g.total = tot;
+        g.ndesc = (int)g.h.size();
+        if (g.h.empty()) return FR_OK;
+        int rc;
+        if ((rc = dev_put((void **)&g.d, g.h.data(), sizeof(GemmArgsT<T>) * g.h.size()))) return rc;
+        return dev_put((void **)&g.begin, bg.data(), sizeof(int64_t) * bg.size());
+    }
+
+    template <typename I>
+    int upload_segs(Segs<I> &sg) {
+        if (sg.h.empty()) return FR_OK;
+        int rc;
+        if ((rc = dev_put((void **)&sg.d, sg.h.data(), sizeof(I) * sg.h.size()))) return rc;
+        return dev_put((void **)&sg.begin, sg.hb.data(), sizeof(int64_t) * sg.hb.size());
+    }
+
+    int build() {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->ctx[0]->device);
+        if (int rc = cuda_check(configure_gemm_grouped<T>(), "grouped gemm attributes")) return rc;
+        m0.mode = GEMM_STORE;
+        grad.mode = GEMM_GRAD;
+        m0g.mode = GEMM_STORE;
+        m0.rc = 16;
+        grad.rc = 12;
+        m0g.rc = 16;
+        for (auto &g : div) {
+            g.mode = GEMM_DIV_RK;
+            g.rc = 16;
+        }
+        for (fr_ctx *c : b->ctx) {
+            for (int t = 0; t < 2; ++t) {
+                DevType &D = c->T[t];
+                if (!D.present) continue;
+                const T *in = (const T *)D.Us;
+                m0.h.push_back(args_m0<T>(c, t, in));
+                if (viscous) {
+                    grad.h.push_back(args_grad<T>(c, t, in));
+                    m0g.h.push_back(args_m0grad<T>(c, t));
+                }
+                flux.hb.push_back(flux.total);
+                flux.h.push_back(FluxItem<T>{D.nu, D.ne, D.np, (const T *)D.Us, (const T *)D.GU,
+                                             (const T *)D.S_t, (T *)D.FT});
+                flux.total += (int64_t)D.nu * D.np;
+                CenterItem<T> ci{(int64_t)D.nu * NVV * D.np, D.np, D.U, (T *)D.Us, {0, 0, 0, 0, 0}};
+                const Phys ph = phys_of(c);
+                for (int v = 0; v < 5; ++v) ci.uref[v] = ph.uref[v];
+                center.hb.push_back(center.total);
+                center.h.push_back(ci);
+                center.total += ci.n;
+            }
+            face.hb.push_back(face.total);
+            face.h.push_back(FaceItem<T>{pairs_of(c), bnd_of(c), fields_of<T>(c)});
+            face.total += c->npairs + c->nbnd;
+        }
+        flux.grid = face.grid = center.grid = nsm * 16;
+        m0.grid = grad.grid = m0g.grid = nsm * 8;
+        for (auto &g : div) g.grid = nsm * 8;
+        int rc;
+        if ((rc = upload_group(m0)) || (rc = upload_group(grad)) || (rc = upload_group(m0g)) ||
+            (rc = upload_segs(flux)) || (rc = upload_segs(face)) || (rc = upload_segs(center)))
+            return rc;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(FR_ERR_CUDA, "batch stream/event creation");
+        }
+        return FR_OK;
+    }
+
+    // divergence descriptors of the four RK stages for the time steps dt
+    int set_dt(const double *dt) {
+        bool same = dt_cur.size() == b->ctx.size();
+        for (size_t i = 0; same && i < b->ctx.size(); ++i) same = dt_cur[i] == dt[i];
+        if (same && div[0].d) return FR_OK;
+        dt_cur.assign(dt, dt + b->ctx.size());
+        for (int st = 0; st < 4; ++st) {
+            div[st].h.clear();
+            for (size_t i = 0; i < b->ctx.size(); ++i) {
+                const double h = dt[i];
+                const double ca[4] = {h / 6.0, h / 3.0, h / 3.0, h / 6.0};
+                const double cs[4] = {0.5 * h, 0.5 * h, h, 0.0};
+                RKStage rk{ca[st], cs[st], st == 0, st == 3};
+                for (int t = 0; t < 2; ++t)
+                    if (b->ctx[i]->T[t].present) div[st].h.push_back(args_div<T>(b->ctx[i], t, &rk));
+            }
+            int rc = upload_group(div[st]);
+            if (rc) return rc;
+        }
+        return FR_OK;
+    }
+
+    int launch_group(const Group<T> &g, cudaStream_t s) {
+        return cuda_check(launch_gemm_grouped<T>(g.d, g.begin, g.ndesc, g.total, g.mode, g.rc, g.maxK, g.grid, s),
+                          "grouped gemm");
+    }
+
+    // one RK stage of the whole batch on stream s; returns launches via n
+    int stage(int st, cudaStream_t s, int &n) {
+        const Phys ph = phys_of(b->ctx[0]);
+        int rc;
+        if ((rc = launch_group(m0, s))) return rc;
+        ++n;
+        if (viscous) {
+            if ((rc = cuda_check(launch_face_grouped<T>(face.d, face.begin, (int)face.h.size(), face.total, ph, 0,
+                                                        face.grid, s),
+                                 "grouped common solution")))
+                return rc;
+            if ((rc = launch_group(grad, s)) || (rc = launch_group(m0g, s))) return rc;
+            n += 3;
+        }
+        if ((rc = cuda_check(
+                 launch_flux_grouped<T>(flux.d, flux.begin, (int)flux.h.size(), flux.total, ph, flux.grid, s),
+                 "grouped flux")) ||
+            (rc = cuda_check(launch_face_grouped<T>(face.d, face.begin, (int)face.h.size(), face.total, ph, 1,
+                                                    face.grid, s),
+                             "grouped common flux")) ||
+            (rc = launch_group(div[st], s)))
+            return rc;
+        n += 3;
+        return FR_OK;
+    }
+
+    int capture() {
+        if (exec) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+        if (graph) {
+            cudaGraphDestroy(graph);
+            graph = nullptr;
+        }
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return cuda_check(cudaGetLastError(), "begin capture");
+        int n = 0, rc = FR_OK;
+        for (int st = 0; st < 4 && !rc; ++st) rc = stage(st, cap, n);
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_check(e, "end capture");
+        if ((rc = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate"))) return rc;
+        launches_per_step = n;
+        return FR_OK;
+    }
+
+    int step(const double *dt, int nsteps, int batched, cudaStream_t s) override {
+        if (nsteps <= 0) return FR_OK;
+        if (!batched) {
+            for (size_t i = 0; i < b->ctx.size(); ++i) {
+                int rc = step_impl<T>(b->ctx[i], dt[i], nsteps, s);
+                if (rc) return rc;
+            }
+            return FR_OK;
+        }
+        int rc;
+        const bool new_dt = dt_cur.size() != b->ctx.size() ||
+                            !std::equal(dt_cur.begin(), dt_cur.end(), dt) || !div[0].d;
+        if ((rc = set_dt(dt))) return rc;
+        if (!exec || new_dt)
+            if ((rc = capture())) return rc;
+        // order the internal capture stream after the caller's stream
+        if ((rc = cuda_check(cudaEventRecord(ev_in, s), "event")) ||
+            (rc = cuda_check(cudaStreamWaitEvent(cap, ev_in, 0), "wait")))
+            return rc;
+        // the centred stage input is derived from the FP64 registers once
+        if ((rc = cuda_check(launch_center_grouped<T>(center.d, center.begin, (int)center.h.size(), center.total,
+                                                      center.grid, cap),
+                             "grouped centre")))
+            return rc;
+        for (int it = 0; it < nsteps; ++it)
+            if ((rc = cuda_check(cudaGraphLaunch(exec, cap), "graph launch"))) return rc;
+        if ((rc = cuda_check(cudaEventRecord(ev_out, cap), "event")) ||
+            (rc = cuda_check(cudaStreamWaitEvent(s, ev_out, 0), "wait")))
+            return rc;
+        return FR_OK;
+    }
+
+    // time one grouped launch (milliseconds per launch, best of reps)
+    template <class F>
+    float time_it(F fn, cudaStream_t s) {
+        cudaEvent_t a, c;
+        cudaEventCreate(&a);
+        cudaEventCreate(&c);
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(a, s);
+            if (fn() != FR_OK) {
+                best = 1e30f;
+                break;
+            }
+            cudaEventRecord(c, s);
+            cudaEventSynchronize(c);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, c);
+            best = std::min(best, ms);
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(c);
+        return best;
+    }
+
+    int tune_group(Group<T> &g, cudaStream_t s) {
+        if (g.h.empty()) return FR_OK;
+        int best_rc = g.rc, best_grid = g.grid;
+        float best = 1e30f;
+        for (int rc : kGroupedRCs) {
+            if (g.mode == GEMM_GRAD && rc % 3) continue;
+            if ((size_t)rc * (g.maxK ? g.maxK : 1) * sizeof(T) > 200 * 1024) continue;
+            g.rc = rc;
+            int e = upload_group(g);
+            if (e) return e;
+            for (int mult : {2, 4, 8, 16}) {
+                g.grid = nsm * mult;
+                const float ms = time_it([&] { return launch_group(g, s); }, s);
+                if (ms < best) {
+                    best = ms;
+                    best_rc = rc;
+                    best_grid = g.grid;
+                }
+            }
+        }
+        g.rc = best_rc;
+        g.grid = best_grid;
+        return upload_group(g);
+    }
+
+    int tune(cudaStream_t s) override {
+        int rc;
+        const Phys ph = phys_of(b->ctx[0]);
+        // the inputs of every class must be valid: centre, then run one stage
+        // un-timed to fill the scratch of the later classes
+        if (dt_cur.empty()) {
+            std::vector<double> z(b->ctx.size(), 0.0);
+            if ((rc = set_dt(z.data()))) return rc;
+        }
+        if ((rc = cuda_check(launch_center_grouped<T>(center.d, center.begin, (int)center.h.size(), center.total,
+                                                      center.grid, s),
+                             "grouped centre")))
+            return rc;
+        // the divergence class is tuned in its plain form (writing R), which
+        // leaves the RK registers untouched
+        Group<T> dv;
+        dv.mode = GEMM_DIV;
+        for (fr_ctx *c : b->ctx)
+            for (int t = 0; t < 2; ++t)
+                if (c->T[t].present) dv.h.push_back(args_div<T>(c, t, nullptr));
+        dv.rc = 16;
+        dv.grid = nsm * 8;
+        if ((rc = upload_group(dv))) return rc;
+        if ((rc = tune_group(m0, s))) return rc;
+        if (viscous) {
+            if ((rc = cuda_check(launch_face_grouped<T>(face.d, face.begin, (int)face.h.size(), face.total, ph, 0,
+                                                        face.grid, s),
+                                 "grouped common solution")))
+                return rc;
+            if ((rc = tune_group(grad, s)) || (rc = tune_group(m0g, s))) return rc;
+        }
+        // point-wise grids
+        for (Segs<FluxItem<T>> *sg : {&flux}) {
+            float best = 1e30f;
+            int bg = sg->grid;
+            for (int mult : {4, 8, 16, 32}) {
+                sg->grid = nsm * mult;
+                const float ms = time_it(
+                    [&] {
+                        return cuda_check(launch_flux_grouped<T>(sg->d, sg->begin, (int)sg->h.size(), sg->total, ph,
+                                                                 sg->grid, s),
+                                          "flux");
+                    },
+                    s);
+                if (ms < best) {
+                    best = ms;
+                    bg = sg->grid;
+                }
+            }
+            sg->grid = bg;
+        }
+        {
+            float best = 1e30f;
+            int bg = face.grid;
+            for (int mult : {4, 8, 16, 32}) {
+                face.grid = nsm * mult;
+                const float ms = time_it(
+                    [&] {
+                        return cuda_check(launch_face_grouped<T>(face.d, face.begin, (int)face.h.size(), face.total,
+                                                                 ph, 1, face.grid, s),
+                                          "face");
+                    },
+                    s);
+                if (ms < best) {
+                    best = ms;
+                    bg = face.grid;
+                }
+            }
+            face.grid = bg;
+        }
+        if ((rc = tune_group(dv, s))) {
+            cudaFree(dv.d);
+            cudaFree(dv.begin);
+            return rc;
+        }
+        for (auto &g : div) {
+            g.rc = dv.rc;
+            g.grid = dv.grid;
+            if (!g.h.empty() && (rc = upload_group(g))) break;
+        }
+        cudaFree(dv.d);
+        cudaFree(dv.begin);
+        if (rc) return rc;
+        // force a new capture with the tuned shapes
+        if (exec) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+        return cuda_check(cudaStreamSynchronize(s), "tune sync");
+    }
+
+    void info(int64_t *out) const override {
+        int64_t ndof = 0;
+        for (fr_ctx *c : b->ctx)
+            for (int t = 0; t < 2; ++t)
+                if (c->T[t].present) ndof += c->T[t].ne * NVV * c->T[t].nu;
+        out[0] = (int64_t)b->ctx.size();
+        out[1] = ndof;
+        out[2] = launches_per_step;
+        // per-problem launch sequence: (viscous ? 12 : 6) per stage and 2 types
+        int64_t un = 0;
+        for (fr_ctx *c : b->ctx) {
+            int nt = c->T[0].present + c->T[1].present;
+            un += 4 * ((viscous ? 5 : 3) * nt + (viscous ? 2 : 1));
+        }
+        out[3] = un;
+        out[4] = m0.rc;
+        out[5] = viscous ? grad.rc : 0;
+        out[6] = viscous ? m0g.rc : 0;
+        out[7] = div[0].rc;
+        out[8] = m0.grid;
+        out[9] = div[0].grid;
+        out[10] = flux.grid;
+        out[11] = face.grid;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int fr_batch_create(int nprob, const fr_mesh *meshes, const int *orders, const fr_params *params, fr_batch **out) {
+    if (!out || nprob <= 0 || !meshes || !orders || !params) return set_err(FR_ERR_ARG, "invalid batch arguments");
+    *out = nullptr;
+    fr_batch *b = new (std::nothrow) fr_batch();
+    if (!b) return set_err(FR_ERR_NOMEM, "host allocation");
+    for (int i = 0; i < nprob; ++i) {
+        fr_ctx *c = nullptr;
+        int rc = fr_create(&meshes[i], orders[i], params, &c);
+        if (rc) {
+            for (fr_ctx *q : b->ctx) fr_destroy(q);
+            delete b;
+            return rc;
+        }
+        b->ctx.push_back(c);
+    }
+    int rc;
+    try {
+        if (params->precision == FR_FP32) {
+            auto *im = new BatchImpl<float>(b);
+            b->impl = im;
+            rc = im->build();
+        } else {
+            auto *im = new BatchImpl<double>(b);
+            b->impl = im;
+            rc = im->build();
+        }
+    } catch (...) {
+        rc = set_err(FR_ERR_NOMEM, "batch set-up");
+    }
+    if (rc) {
+        fr_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return FR_OK;
+}
+
+void fr_batch_destroy(fr_batch *b) {
+    if (!b) return;
+    delete b->impl;
+    for (fr_ctx *c : b->ctx) fr_destroy(c);
+    delete b;
+}
+
+int fr_batch_problem(fr_batch *b, int i, fr_ctx **ctx) {
+    if (!b || !ctx || i < 0 || i >= (int)b->ctx.size()) return set_err(FR_ERR_ARG, "invalid problem index");
+    *ctx = b->ctx[i];
+    return FR_OK;
+}
+
+int fr_batch_tune(fr_batch *b, void *stream) {
+    if (!b) return set_err(FR_ERR_ARG, "null batch");
+    return b->impl->tune((cudaStream_t)stream);
+}
+
+int fr_batch_step(fr_batch *b, const double *dt, int nsteps, int batched, void *stream) {
+    if (!b || !dt || nsteps < 0) return set_err(FR_ERR_ARG, "invalid step arguments");
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+        if (!(dt[i] == dt[i])) return set_err(FR_ERR_ARG, "non-finite time step");
+    return b->impl->step(dt, nsteps, batched, (cudaStream_t)stream);
+}
+
+int fr_batch_info(const fr_batch *b, int64_t *out) {
+    if (!b || !out) return set_err(FR_ERR_ARG, "null argument");
+    b->impl->info(out);
+    return FR_OK;
+}
+
+}  // extern "C"

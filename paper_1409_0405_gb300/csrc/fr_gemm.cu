@@ -29,98 +29,128 @@ namespace {
 
 constexpr int kThreads = 128;
 
+// One (row chunk, column tile) block of C <- A [B1; B2] with the epilogue
+// MODE.  Block-uniform: every thread of the block calls it with the same
+// (g, m0, tile); it stages the chunk of A in sA and synchronises.
 template <typename T, int RC, int MODE>
-__global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgsT<T> g) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sA = reinterpret_cast<T *>(smem_raw);  // [K][RC]
+__device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_t tile, T *sA) {
     const int K = g.K1 + g.K2;
-    // 1-D grid, row chunk fastest: the chunks of one column tile run back
-    // to back, so that tile of B is read from DRAM once and then from L2
-    const int nchunks = (g.M + RC - 1) / RC;
-    const int m0 = (int)(blockIdx.x % nchunks) * RC;
-    const int64_t tile = blockIdx.x / nchunks;
     for (int idx = threadIdx.x; idx < RC * K; idx += kThreads) {
         const int r = idx / K, k = idx - r * K;
         sA[k * RC + r] = (m0 + r < g.M) ? g.A[(size_t)(m0 + r) * K + k] : T(0);
     }
     __syncthreads();
     const int64_t n = tile * kThreads + threadIdx.x;
-    if (n >= g.N) return;
-
-    T acc[RC];
+    if (n < g.N) {
+        T acc[RC];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) acc[r] = T(0);
-
-    {
-        const T *b = g.B1 + n;
-        const int64_t ld = g.ldb1;
+        for (int r = 0; r < RC; ++r) acc[r] = T(0);
+        {
+            const T *b = g.B1 + n;
+            const int64_t ld = g.ldb1;
 #pragma unroll 2
-        for (int k = 0; k < g.K1; ++k) {
-            const T bv = __ldg(b + (int64_t)k * ld);
-            const T *a = sA + k * RC;
+            for (int k = 0; k < g.K1; ++k) {
+                const T bv = __ldg(b + (int64_t)k * ld);
+                const T *a = sA + k * RC;
 #pragma unroll
-            for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
-        }
-    }
-    if (g.K2 > 0) {
-        const T *b = g.B2 + n;
-        const int64_t ld = g.ldb2;
-        const T *a0 = sA + g.K1 * RC;
-#pragma unroll 2
-        for (int k = 0; k < g.K2; ++k) {
-            const T bv = __ldg(b + (int64_t)k * ld);
-            const T *a = a0 + k * RC;
-#pragma unroll
-            for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
-        }
-    }
-
-    if (MODE == GEMM_STORE) {
-        const T add = g.add_ref ? T(g.uref[n / g.np]) : T(0);
-#pragma unroll
-        for (int r = 0; r < RC; ++r)
-            if (m0 + r < g.M) g.C[(int64_t)(m0 + r) * g.ldc + n] = acc[r] + add;
-    } else if (MODE == GEMM_GRAD) {
-        // rows are (j, d) with d fastest; RC and m0 are multiples of 3
-        const int64_t e = n % g.np;
-#pragma unroll
-        for (int jj = 0; jj < RC / 3; ++jj) {
-            const int j = m0 / 3 + jj;
-            if (3 * j >= g.M) break;
-            const T *S = g.S + (int64_t)j * 9 * g.np + e;
-            const T ij = g.invJ[(int64_t)j * g.np + e];
-            const T g0 = acc[3 * jj], g1 = acc[3 * jj + 1], g2 = acc[3 * jj + 2];
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const T s0 = S[(0 * 3 + m) * g.np], s1 = S[(1 * 3 + m) * g.np], s2 = S[(2 * 3 + m) * g.np];
-                g.C[(int64_t)(3 * j + m) * g.ldc + n] = ij * (s0 * g0 + s1 * g1 + s2 * g2);
+                for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
             }
         }
-    } else {
-        const int64_t e = n % g.np;
-        const double ur = (MODE == GEMM_DIV_RK) ? g.uref[n / g.np] : 0.0;
+        if (g.K2 > 0) {
+            const T *b = g.B2 + n;
+            const int64_t ld = g.ldb2;
+            const T *a0 = sA + g.K1 * RC;
+#pragma unroll 2
+            for (int k = 0; k < g.K2; ++k) {
+                const T bv = __ldg(b + (int64_t)k * ld);
+                const T *a = a0 + k * RC;
 #pragma unroll
-        for (int r = 0; r < RC; ++r) {
-            const int j = m0 + r;
-            if (j >= g.M) break;
-            const int64_t idx = (int64_t)j * g.ldc + n;
-            const T rt = -g.invJ[(int64_t)j * g.np + e] * acc[r];
-            if (MODE == GEMM_DIV) {
-                g.C[idx] = g.rfs ? T((double)rt + g.rfs[idx]) : rt;
-            } else {
-                // FP64 register update (both modes)
-                const double rv = (double)rt + (g.rfs ? g.rfs[idx] : 0.0);
-                const double u = g.U[idx];
-                if (g.rk_last) {
-                    const double un = g.Uacc[idx] + g.c_acc * rv;
-                    g.U[idx] = un;
-                    g.Us[idx] = T(un - ur);
+                for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
+            }
+        }
+
+        if (MODE == GEMM_STORE) {
+            const T add = g.add_ref ? T(g.uref[n / g.np]) : T(0);
+#pragma unroll
+            for (int r = 0; r < RC; ++r)
+                if (m0 + r < g.M) g.C[(int64_t)(m0 + r) * g.ldc + n] = acc[r] + add;
+        } else if (MODE == GEMM_GRAD) {
+            // rows are (j, d) with d fastest; RC and m0 are multiples of 3
+            const int64_t e = n % g.np;
+#pragma unroll
+            for (int jj = 0; jj < RC / 3; ++jj) {
+                const int j = m0 / 3 + jj;
+                if (3 * j >= g.M) break;
+                const T *S = g.S + (int64_t)j * 9 * g.np + e;
+                const T ij = g.invJ[(int64_t)j * g.np + e];
+                const T g0 = acc[3 * jj], g1 = acc[3 * jj + 1], g2 = acc[3 * jj + 2];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const T s0 = S[(0 * 3 + m) * g.np], s1 = S[(1 * 3 + m) * g.np], s2 = S[(2 * 3 + m) * g.np];
+                    g.C[(int64_t)(3 * j + m) * g.ldc + n] = ij * (s0 * g0 + s1 * g1 + s2 * g2);
+                }
+            }
+        } else {
+            const int64_t e = n % g.np;
+            const double ur = (MODE == GEMM_DIV_RK) ? g.uref[n / g.np] : 0.0;
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int j = m0 + r;
+                if (j >= g.M) break;
+                const int64_t idx = (int64_t)j * g.ldc + n;
+                const T rt = -g.invJ[(int64_t)j * g.np + e] * acc[r];
+                if (MODE == GEMM_DIV) {
+                    g.C[idx] = g.rfs ? T((double)rt + g.rfs[idx]) : rt;
                 } else {
-                    g.Uacc[idx] = (g.rk_first ? u : g.Uacc[idx]) + g.c_acc * rv;
-                    g.Us[idx] = T((u - ur) + g.c_stage * rv);
+                    // FP64 register update (both modes)
+                    const double rv = (double)rt + (g.rfs ? g.rfs[idx] : 0.0);
+                    const double u = g.U[idx];
+                    if (g.rk_last) {
+                        const double un = g.Uacc[idx] + g.c_acc * rv;
+                        g.U[idx] = un;
+                        g.Us[idx] = T(un - ur);
+                    } else {
+                        g.Uacc[idx] = (g.rk_first ? u : g.Uacc[idx]) + g.c_acc * rv;
+                        g.Us[idx] = T((u - ur) + g.c_stage * rv);
+                    }
                 }
             }
         }
+    }
+}
+
+template <typename T, int RC, int MODE>
+__global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgsT<T> g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // 1-D grid, row chunk fastest: the chunks of one column tile run back
+    // to back, so that tile of B is read from DRAM once and then from L2
+    const int nchunks = (g.M + RC - 1) / RC;
+    gemm_block<T, RC, MODE>(g, (int)(blockIdx.x % nchunks) * RC, (int64_t)(blockIdx.x / nchunks),
+                            reinterpret_cast<T *>(smem_raw));
+}
+
+// Grouped persistent variant: one launch covers many operator applications
+// (problems x element types).  begin[d] is the first block index of
+// descriptor d (prefix sum of its row chunks x column tiles); the grid
+// strides over all blocks.
+template <typename T, int RC, int MODE>
+__global__ void __launch_bounds__(kThreads) k_gemm_grouped(const GemmArgsT<T> *__restrict__ descs,
+                                                           const int64_t *__restrict__ begin, int ndesc,
+                                                           int64_t total) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);
+    for (int64_t bid = blockIdx.x; bid < total; bid += gridDim.x) {
+        int lo = 0, hi = ndesc - 1;
+        while (lo < hi) {  // last d with begin[d] <= bid
+            const int mid = (lo + hi + 1) >> 1;
+            if (begin[mid] <= bid) lo = mid;
+            else hi = mid - 1;
+        }
+        const GemmArgsT<T> &g = descs[lo];
+        const int64_t local = bid - begin[lo];
+        const int nchunks = (g.M + RC - 1) / RC;
+        gemm_block<T, RC, MODE>(g, (int)(local % nchunks) * RC, local / nchunks, sA);
+        __syncthreads();  // sA is reloaded by the next block
     }
 }
 
@@ -204,5 +234,95 @@ cudaError_t launch_gemm(const GemmArgsT<T> &g, cudaStream_t s) {
 
 template cudaError_t launch_gemm<double>(const GemmArgsT<double> &, cudaStream_t);
 template cudaError_t launch_gemm<float>(const GemmArgsT<float> &, cudaStream_t);
+
+namespace {
+
+template <typename T, int RC, int MODE>
+cudaError_t run_grouped(const GemmArgsT<T> *descs, const int64_t *begin, int ndesc, int64_t total, int maxK,
+                        int grid, cudaStream_t s) {
+    const size_t smem = (size_t)RC * maxK * sizeof(T);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_grouped<T, RC, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (smem > 200 * 1024 || grid <= 0) return cudaErrorInvalidValue;
+    k_gemm_grouped<T, RC, MODE><<<grid, kThreads, smem, s>>>(descs, begin, ndesc, total);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t grouped_rc(int rc, const GemmArgsT<T> *descs, const int64_t *begin, int ndesc, int64_t total, int maxK,
+                       int grid, cudaStream_t s) {
+    switch (rc) {
+        case 6: return run_grouped<T, 6, MODE>(descs, begin, ndesc, total, maxK, grid, s);
+        case 12: return run_grouped<T, 12, MODE>(descs, begin, ndesc, total, maxK, grid, s);
+        case 24: return run_grouped<T, 24, MODE>(descs, begin, ndesc, total, maxK, grid, s);
+    }
+    if (MODE != GEMM_GRAD) {
+        switch (rc) {
+            case 8: return run_grouped<T, (MODE == GEMM_GRAD ? 6 : 8), MODE>(descs, begin, ndesc, total, maxK, grid, s);
+            case 16: return run_grouped<T, (MODE == GEMM_GRAD ? 6 : 16), MODE>(descs, begin, ndesc, total, maxK, grid, s);
+            case 32: return run_grouped<T, (MODE == GEMM_GRAD ? 6 : 32), MODE>(descs, begin, ndesc, total, maxK, grid, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+const int kGroupedRCs[] = {6, 8, 12, 16, 24, 32};
+
+namespace {
+template <typename T, int MODE>
+cudaError_t configure_mode() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto fn) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    };
+    set(k_gemm_grouped<T, 6, MODE>);
+    set(k_gemm_grouped<T, 12, MODE>);
+    set(k_gemm_grouped<T, 24, MODE>);
+    if (MODE != GEMM_GRAD) {
+        set(k_gemm_grouped<T, (MODE == GEMM_GRAD ? 6 : 8), MODE>);
+        set(k_gemm_grouped<T, (MODE == GEMM_GRAD ? 6 : 16), MODE>);
+        set(k_gemm_grouped<T, (MODE == GEMM_GRAD ? 6 : 32), MODE>);
+    }
+    return e;
+}
+}  // namespace
+
+template <typename T>
+cudaError_t configure_gemm_grouped() {
+    cudaError_t e;
+    if ((e = configure_mode<T, GEMM_STORE>()) != cudaSuccess) return e;
+    if ((e = configure_mode<T, GEMM_GRAD>()) != cudaSuccess) return e;
+    if ((e = configure_mode<T, GEMM_DIV>()) != cudaSuccess) return e;
+    return configure_mode<T, GEMM_DIV_RK>();
+}
+template cudaError_t configure_gemm_grouped<float>();
+template cudaError_t configure_gemm_grouped<double>();
+
+int64_t gemm_blocks(int M, int64_t N, int rc) { return ((N + kThreads - 1) / kThreads) * ((M + rc - 1) / rc); }
+
+template <typename T>
+cudaError_t launch_gemm_grouped(const GemmArgsT<T> *descs, const int64_t *begin, int ndesc, int64_t total, int mode,
+                                int rc, int maxK, int grid, cudaStream_t s) {
+    if (ndesc <= 0 || total <= 0) return cudaSuccess;
+    switch (mode) {
+        case GEMM_STORE: return grouped_rc<T, GEMM_STORE>(rc, descs, begin, ndesc, total, maxK, grid, s);
+        case GEMM_GRAD: return grouped_rc<T, GEMM_GRAD>(rc, descs, begin, ndesc, total, maxK, grid, s);
+        case GEMM_DIV: return grouped_rc<T, GEMM_DIV>(rc, descs, begin, ndesc, total, maxK, grid, s);
+        case GEMM_DIV_RK: return grouped_rc<T, GEMM_DIV_RK>(rc, descs, begin, ndesc, total, maxK, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_gemm_grouped<double>(const GemmArgsT<double> *, const int64_t *, int, int64_t, int, int,
+                                                 int, int, cudaStream_t);
+template cudaError_t launch_gemm_grouped<float>(const GemmArgsT<float> *, const int64_t *, int, int64_t, int, int, int,
+                                                int, cudaStream_t);
 
 }  // namespace fr

@@ -57,6 +57,20 @@ template <typename T>
 cudaError_t launch_gemm(const GemmArgsT<T> &g, cudaStream_t s);
 inline cudaError_t launch_gemm_f64(const GemmArgs &g, cudaStream_t s) { return launch_gemm<double>(g, s); }
 
+// Grouped persistent GEMM over ndesc device-resident descriptors; begin
+// (device, ndesc) holds each descriptor's first block index, total the
+// block count, for the row-chunk size rc (one of kGroupedRCs; GEMM_GRAD
+// needs a multiple of 3); maxK bounds K1+K2; grid = persistent CTAs.
+extern const int kGroupedRCs[6];
+int64_t gemm_blocks(int M, int64_t N, int rc);
+// sets the shared-memory attribute of every grouped instantiation (call
+// before capturing grouped launches in a CUDA graph)
+template <typename T>
+cudaError_t configure_gemm_grouped();
+template <typename T>
+cudaError_t launch_gemm_grouped(const GemmArgsT<T> *descs, const int64_t *begin, int ndesc, int64_t total, int mode,
+                                int rc, int maxK, int grid, cudaStream_t s);
+
 struct Phys {
     double gamma, mu, prandtl, beta, tau;
     double rho_inf, vinf[3], p_inf, t_wall;
@@ -114,6 +128,39 @@ cudaError_t launch_pub_to_int(int nu, int64_t ne, int64_t np, const double *pub,
 // internal [j][v][e] (T) -> public [e][v][j] (double)
 template <typename T>
 cudaError_t launch_int_to_pub(int nu, int64_t ne, int64_t np, const T *in, double *pub, cudaStream_t s);
+// work items of the grouped point-wise launches
+template <typename T>
+struct FluxItem {
+    int nu;
+    int64_t ne, np;
+    const T *U, *GU, *S;
+    T *FT;
+};
+template <typename T>
+struct FaceItem {
+    Pairs P;
+    Bnd B;
+    FieldsT<T> F;
+};
+template <typename T>
+struct CenterItem {
+    int64_t n, np;  // n = nu * V * np
+    const double *U;
+    T *Us;
+    double uref[5];
+};
+// grouped launches over device-resident items; begin[i] = first global
+// index of item i (prefix sums of nu*np, pairs+boundary points, n)
+template <typename T>
+cudaError_t launch_flux_grouped(const FluxItem<T> *items, const int64_t *begin, int n, int64_t total, const Phys &ph,
+                                int grid, cudaStream_t s);
+// which = 0: common solution, 1: common flux
+template <typename T>
+cudaError_t launch_face_grouped(const FaceItem<T> *items, const int64_t *begin, int n, int64_t total, const Phys &ph,
+                                int which, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *begin, int n, int64_t total, int grid,
+                                  cudaStream_t s);
 // transformed reference flux at solution points, FT = S F_ref (padding 0)
 cudaError_t launch_const_flux(int nu, int64_t ne, int64_t np, const double *S, double *FT, const Phys &ph,
                               cudaStream_t s);

@@ -195,8 +195,8 @@ __device__ __forceinline__ T ldg_sign(const double *n) {
 
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_common_solution(const Pairs P, const Bnd B, const FieldsT<T> F, const PhysT<T> ph) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void common_solution_at(const Pairs &P, const Bnd &B, const FieldsT<T> &F,
+                                                   const PhysT<T> &ph, int64_t k) {
     if (k < P.n) {
         const int ta = P.ta[k], tb = P.tb[k];
         const int64_t npa = F.np[ta], npb = F.np[tb];
@@ -229,6 +229,11 @@ __global__ void k_common_solution(const Pairs P, const Bnd B, const FieldsT<T> F
 }
 
 template <typename T>
+__global__ void k_common_solution(const Pairs P, const Bnd B, const FieldsT<T> F, const PhysT<T> ph) {
+    common_solution_at(P, B, F, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <typename T>
 __device__ __forceinline__ void load_grad(const T *G, int f, int e, int64_t np, T g[3][V]) {
     const T *p = G + (int64_t)f * 3 * V * np + e;
 #pragma unroll
@@ -243,8 +248,8 @@ __device__ __forceinline__ T fref_n(const PhysT<T> &ph, int v, const T *n) {
 }
 
 template <typename T>
-__global__ void k_common_flux(const Pairs P, const Bnd B, const FieldsT<T> F, const PhysT<T> ph) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, const FieldsT<T> &F, const PhysT<T> &ph,
+                                               int64_t k) {
     if (k < P.n) {
         const int ta = P.ta[k], tb = P.tb[k];
         const int64_t npa = F.np[ta], npb = F.np[tb];
@@ -309,11 +314,16 @@ __global__ void k_common_flux(const Pairs P, const Bnd B, const FieldsT<T> F, co
     }
 }
 
+template <typename T>
+__global__ void k_common_flux(const Pairs P, const Bnd B, const FieldsT<T> F, const PhysT<T> ph) {
+    common_flux_at(P, B, F, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // transformed flux F~_d = sum_m S[d][m] (F_inv - F_vis - F_ref)_m at solution points
 template <typename T>
-__global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, const T *__restrict__ GU,
-                       const T *__restrict__ S, T *__restrict__ FT, const PhysT<T> ph) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T *__restrict__ U,
+                                        const T *__restrict__ GU, const T *__restrict__ S, T *__restrict__ FT,
+                                        const PhysT<T> &ph, int64_t idx) {
     const int64_t j = idx / np, e = idx - j * np;
     if (j >= nu || e >= ne) return;
     T u[V];
@@ -352,6 +362,61 @@ __global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, 
 #pragma unroll
         for (int v = 0; v < V; ++v)
             FT[((j * 3 + d) * V + v) * np + e] = s[d * 3 + 0] * F[v][0] + s[d * 3 + 1] * F[v][1] + s[d * 3 + 2] * F[v][2];
+}
+
+template <typename T>
+__global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, const T *__restrict__ GU,
+                       const T *__restrict__ S, T *__restrict__ FT, const PhysT<T> ph) {
+    flux_at(nu, ne, np, U, GU, S, FT, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// grouped variants: one launch over many (problem, element type) segments;
+// begin[i] is the first global index of item i (prefix sum of its sizes)
+__device__ __forceinline__ int find_item(const int64_t *begin, int n, int64_t gi) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= gi) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void k_flux_grouped(const FluxItem<T> *__restrict__ items, const int64_t *__restrict__ begin, int n,
+                               int64_t total, const PhysT<T> ph) {
+    for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int i = find_item(begin, n, gi);
+        const FluxItem<T> &it = items[i];
+        flux_at(it.nu, it.ne, it.np, it.U, it.GU, it.S, it.FT, ph, gi - begin[i]);
+    }
+}
+
+template <typename T>
+__global__ void k_face_grouped(const FaceItem<T> *__restrict__ items, const int64_t *__restrict__ begin, int n,
+                               int64_t total, const PhysT<T> ph, int which) {
+    for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int i = find_item(begin, n, gi);
+        const FaceItem<T> &it = items[i];
+        if (which == 0) common_solution_at(it.P, it.B, it.F, ph, gi - begin[i]);
+        else common_flux_at(it.P, it.B, it.F, ph, gi - begin[i]);
+    }
+}
+
+template <typename T>
+__global__ void k_center_grouped(const CenterItem<T> *__restrict__ items, const int64_t *__restrict__ begin, int n,
+                                 int64_t total) {
+    for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int i = find_item(begin, n, gi);
+        const CenterItem<T> &it = items[i];
+        const int64_t idx = gi - begin[i];
+        const int64_t v = (idx / it.np) % V;
+        it.Us[idx] = T(it.U[idx] - it.uref[v]);
+    }
 }
 
 // reference flux only (set-up, double)
@@ -518,6 +583,30 @@ cudaError_t launch_int_to_pub(int nu, int64_t ne, int64_t np, const T *in, doubl
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_flux_grouped(const FluxItem<T> *items, const int64_t *begin, int n, int64_t total, const Phys &ph,
+                                int grid, cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    k_flux_grouped<T><<<grid, 128, 0, s>>>(items, begin, n, total, phys_t<T>(ph));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_face_grouped(const FaceItem<T> *items, const int64_t *begin, int n, int64_t total, const Phys &ph,
+                                int which, int grid, cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    k_face_grouped<T><<<grid, 128, 0, s>>>(items, begin, n, total, phys_t<T>(ph), which);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *begin, int n, int64_t total, int grid,
+                                  cudaStream_t s) {
+    if (n <= 0 || total <= 0) return cudaSuccess;
+    k_center_grouped<T><<<grid, 256, 0, s>>>(items, begin, n, total);
+    return cudaGetLastError();
+}
+
 #define FR_INST(T)                                                                                            \
     template cudaError_t launch_common_solution<T>(const Pairs &, const Bnd &, const FieldsT<T> &, const Phys &, \
                                                    cudaStream_t);                                             \
@@ -528,7 +617,13 @@ cudaError_t launch_int_to_pub(int nu, int64_t ne, int64_t np, const T *in, doubl
     template cudaError_t launch_pub_to_int<T>(int, int64_t, int64_t, const double *, double *, cudaStream_t,    \
                                               T *, const double *);                                           \
     template cudaError_t launch_center<T>(int, int64_t, const double *, T *, const double *, cudaStream_t);     \
-    template cudaError_t launch_int_to_pub<T>(int, int64_t, int64_t, const T *, double *, cudaStream_t);
+    template cudaError_t launch_int_to_pub<T>(int, int64_t, int64_t, const T *, double *, cudaStream_t);       \
+    template cudaError_t launch_flux_grouped<T>(const FluxItem<T> *, const int64_t *, int, int64_t, const Phys &, \
+                                                int, cudaStream_t);                                           \
+    template cudaError_t launch_face_grouped<T>(const FaceItem<T> *, const int64_t *, int, int64_t, const Phys &, \
+                                                int, int, cudaStream_t);                                      \
+    template cudaError_t launch_center_grouped<T>(const CenterItem<T> *, const int64_t *, int, int64_t, int,     \
+                                                  cudaStream_t);
 FR_INST(double)
 FR_INST(float)
 #undef FR_INST

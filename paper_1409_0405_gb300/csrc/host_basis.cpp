@@ -29,6 +29,8 @@
 //   W   integrals of the solution-point Lagrange polynomials.
 #include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -354,11 +356,36 @@ int nfpts_of(int etype, int p) {
                                  : 2 * (p + 1) * (p + 2) / 2 + 3 * (p + 1) * (p + 1);
 }
 
+namespace {
+int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err);
+}
+
+// Operators depend only on (etype, p): built once per process and reused.
 int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
     if ((etype != FR_ETYPE_TET && etype != FR_ETYPE_PRI) || p < 1 || p > 4) {
         err = "build_ref_ops: etype must be 0/1 and order 1..4";
         return FR_ERR_ARG;
     }
+    static std::mutex mtx;
+    static std::map<std::pair<int, int>, RefOps> cache;
+    {
+        std::lock_guard<std::mutex> lock(mtx);
+        auto it = cache.find({etype, p});
+        if (it != cache.end()) {
+            o = it->second;
+            return FR_OK;
+        }
+    }
+    int rc = build_ref_ops_uncached(etype, p, o, err);
+    if (rc == FR_OK) {
+        std::lock_guard<std::mutex> lock(mtx);
+        cache[{etype, p}] = o;
+    }
+    return rc;
+}
+
+namespace {
+int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
     o = RefOps();
     o.etype = etype;
     o.p = p;
@@ -640,5 +667,6 @@ int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
     }
     return FR_OK;
 }
+}  // namespace
 
 }  // namespace fr

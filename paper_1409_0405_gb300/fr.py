@@ -34,7 +34,8 @@ OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_reduce",
            "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
-           "fr_last_error", "fr_reduce_noalloc")
+           "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
+           "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info")
 KCLASSES = ("M0", "common_solution", "grad", "M0_grad", "flux", "common_flux", "div")
 
 
@@ -90,6 +91,16 @@ def load():
     lib.fr_peak_fp64.restype = C.c_int
     lib.fr_reduce_noalloc.argtypes = [C.c_int64, C.c_int, vp, vp, C.c_double, vp, vp]
     lib.fr_reduce_noalloc.restype = C.c_int
+    lib.fr_batch_create.argtypes = [C.c_int, C.POINTER(FRMesh), C.POINTER(C.c_int), C.POINTER(FRParams),
+                                    C.POINTER(vp)]
+    lib.fr_batch_destroy.argtypes = [vp]
+    lib.fr_batch_destroy.restype = None
+    lib.fr_batch_problem.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    lib.fr_batch_tune.argtypes = [vp, vp]
+    lib.fr_batch_step.argtypes = [vp, dp, C.c_int, C.c_int, vp]
+    lib.fr_batch_info.argtypes = [vp, i64p]
+    for name in ("fr_batch_create", "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info"):
+        getattr(lib, name).restype = C.c_int
     lib.fr_strerror.argtypes = [C.c_int]
     lib.fr_strerror.restype = C.c_char_p
     lib.fr_last_error.argtypes = []
@@ -150,41 +161,57 @@ def default_params(viscous=False, mu=0.0, gamma=1.4, prandtl=0.72, ldg_beta=0.5,
                 vel_inf=tuple(vel_inf), p_inf=p_inf, t_wall=t_wall)
 
 
+def _fr_mesh(mesh, keep):
+    """Fill an FRMesh from a mesh dict; arrays are kept alive in `keep`."""
+    k = {
+        "xyz": np.ascontiguousarray(mesh["xyz"], dtype=np.float64),
+        "tet": np.ascontiguousarray(mesh["tet"], dtype=np.int64).reshape(-1, 4),
+        "pri": np.ascontiguousarray(mesh["pri"], dtype=np.int64).reshape(-1, 6),
+        "bface": np.ascontiguousarray(mesh.get("bface", np.zeros((0, 4))), dtype=np.int64).reshape(-1, 4),
+    }
+    keep.append(k)
+    m = FRMesh()
+    m.n_nodes = len(k["xyz"])
+    m.xyz = _dptr(k["xyz"])
+    m.n_tet = len(k["tet"])
+    m.tet = k["tet"].ctypes.data_as(C.POINTER(C.c_int64))
+    m.n_pri = len(k["pri"])
+    m.pri = k["pri"].ctypes.data_as(C.POINTER(C.c_int64))
+    m.n_bface = len(k["bface"])
+    m.bface = k["bface"].ctypes.data_as(C.POINTER(C.c_int64))
+    per = np.asarray(mesh.get("period", np.zeros(3)), dtype=np.float64)
+    m.period = (C.c_double * 3)(*per)
+    return m
+
+
+def _fr_params(prm):
+    p = FRParams()
+    for key, val in prm.items():
+        if key == "vel_inf":
+            p.vel_inf = (C.c_double * 3)(*val)
+        else:
+            setattr(p, key, val)
+    return p
+
+
 class Context:
     """One fr_ctx: mesh + order + parameters resident on the current GPU."""
 
-    def __init__(self, mesh, order, **params):
+    def __init__(self, mesh, order, _handle=None, _owner=None, **params):
         lib = load()
         prm = default_params(**params)
-        self._keep = {
-            "xyz": np.ascontiguousarray(mesh["xyz"], dtype=np.float64),
-            "tet": np.ascontiguousarray(mesh["tet"], dtype=np.int64).reshape(-1, 4),
-            "pri": np.ascontiguousarray(mesh["pri"], dtype=np.int64).reshape(-1, 6),
-            "bface": np.ascontiguousarray(mesh.get("bface", np.zeros((0, 4))), dtype=np.int64).reshape(-1, 4),
-        }
-        k = self._keep
-        m = FRMesh()
-        m.n_nodes = len(k["xyz"])
-        m.xyz = _dptr(k["xyz"])
-        m.n_tet = len(k["tet"])
-        m.tet = k["tet"].ctypes.data_as(C.POINTER(C.c_int64))
-        m.n_pri = len(k["pri"])
-        m.pri = k["pri"].ctypes.data_as(C.POINTER(C.c_int64))
-        m.n_bface = len(k["bface"])
-        m.bface = k["bface"].ctypes.data_as(C.POINTER(C.c_int64))
-        per = np.asarray(mesh.get("period", np.zeros(3)), dtype=np.float64)
-        m.period = (C.c_double * 3)(*per)
-        p = FRParams()
-        for key, val in prm.items():
-            if key == "vel_inf":
-                p.vel_inf = (C.c_double * 3)(*val)
-            else:
-                setattr(p, key, val)
         self.params = prm
-        h = C.c_void_p()
-        _check(lib.fr_create(C.byref(m), int(order), C.byref(p), C.byref(h)))
-        self._h = h
         self._lib = lib
+        self._owner = _owner
+        if _handle is None:
+            self._keep = []
+            m = _fr_mesh(mesh, self._keep)
+            p = _fr_params(prm)
+            h = C.c_void_p()
+            _check(lib.fr_create(C.byref(m), int(order), C.byref(p), C.byref(h)))
+        else:
+            h = _handle
+        self._h = h
         n = C.c_int64()
         _check(lib.fr_ndof(h, C.byref(n)))
         self.ndof = n.value
@@ -192,11 +219,12 @@ class Context:
         _check(lib.fr_info(h, info))
         self.info = dict(zip(("n_tet", "n_pri", "order", "nu_tet", "nu_pri", "nf_tet",
                               "nf_pri", "npairs"), list(info)))
-        self.order = order
+        self.order = int(info[2])
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.fr_destroy(self._h)
+            if self._owner is None:        # contexts of a batch belong to it
+                self._lib.fr_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -263,3 +291,53 @@ class Context:
             return out
         _check(rc)
         return out
+
+
+class Batch:
+    """fr_batch: many independent problems advanced with grouped launches."""
+
+    INFO = ("nprob", "ndof", "launches_batched", "launches_per_problem", "rc_m0", "rc_grad",
+            "rc_m0grad", "rc_div", "grid_gemm", "grid_div", "grid_flux", "grid_face")
+
+    def __init__(self, meshes, orders, **params):
+        lib = load()
+        self._lib = lib
+        prm = default_params(**params)
+        keep = []
+        arr = (FRMesh * len(meshes))(*[_fr_mesh(m, keep) for m in meshes])
+        ords = (C.c_int * len(orders))(*[int(o) for o in orders])
+        p = _fr_params(prm)
+        h = C.c_void_p()
+        _check(lib.fr_batch_create(len(meshes), arr, ords, C.byref(p), C.byref(h)))
+        self._h = h
+        self.problems = []
+        for i in range(len(meshes)):
+            ch = C.c_void_p()
+            _check(lib.fr_batch_problem(h, i, C.byref(ch)))
+            self.problems.append(Context(None, 0, _handle=ch, _owner=self, **params))
+
+    def info(self):
+        out = (C.c_int64 * 12)()
+        _check(self._lib.fr_batch_info(self._h, out))
+        return dict(zip(self.INFO, list(out)))
+
+    def tune(self, stream=None):
+        _check(self._lib.fr_batch_tune(self._h, C.c_void_p(stream) if stream else None))
+
+    def step(self, dt, nsteps=1, batched=True, stream=None):
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (len(self.problems),)))
+        _check(self._lib.fr_batch_step(self._h, _dptr(dts), int(nsteps), int(bool(batched)),
+                                       C.c_void_p(stream) if stream else None))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for c in self.problems:
+                c._h = None
+            self._lib.fr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

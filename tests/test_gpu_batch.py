@@ -1,0 +1,99 @@
+"""The batched engine (grouped persistent launches + CUDA graph) against
+the per-problem launch sequence (bit for bit) and against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from tests._cases import library, per_quantity_rel_err
+from oracle.solver import Solver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    library()
+
+
+def _problems():
+    # uneven sizes, mixes and orders (tets only, prisms only, mixed)
+    return [(synth.vortex_box(n=3, n_prism_layers=1, seed=11), 1),
+            (synth.vortex_box(n=4, n_prism_layers=0, seed=12), 3),
+            (synth.vortex_box(n=2, n_prism_layers=2, seed=13), 4),
+            (synth.vortex_box(n=5, n_prism_layers=3, seed=14), 2)]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_equals_per_problem(precision):
+    from paper_1409_0405_gb300 import fr
+    probs = _problems()
+    b = fr.Batch([m for m, _ in probs], [p for _, p in probs], precision=precision)
+    u0 = [c.upts_points() for c in b.problems]
+    states = [np.ascontiguousarray(synth.isentropic_vortex(x)[:, :].reshape(-1, 5)) for x in u0]
+    pub = []
+    for c, q in zip(b.problems, states):
+        blocks, off = [], 0
+        for ne, nu in ((c.info["n_tet"], c.info["nu_tet"]), (c.info["n_pri"], c.info["nu_pri"])):
+            if ne:
+                blocks.append(q[off:off + ne * nu].reshape(ne, nu, 5).transpose(0, 2, 1).reshape(-1))
+                off += ne * nu
+        pub.append(np.concatenate(blocks))
+    dts = [0.01, 0.02, 0.005, 0.01]
+
+    def run(batched, nsteps=3):
+        for c, u in zip(b.problems, pub):
+            c.set_state(u)
+        b.step(dts, nsteps, batched=batched)
+        return [c.get_state() for c in b.problems]
+
+    ref = run(False)
+    got = run(True)
+    for r, g in zip(ref, got):
+        np.testing.assert_array_equal(g, r)
+    info = b.info()
+    assert info["launches_batched"] == 4 * 4          # Euler: M0, flux, common flux, div per stage
+    # per problem and stage: 2 types x (M0, flux, div) + 1 face kernel (Euler)
+    per = sum(4 * (3 * ((c.info["n_tet"] > 0) + (c.info["n_pri"] > 0)) + 1) for c in b.problems)
+    assert info["launches_per_problem"] == per > info["launches_batched"]
+    b.tune()
+    got2 = run(True)
+    for r, g in zip(ref, got2):
+        np.testing.assert_array_equal(g, r)
+    b.close()
+
+
+def test_batched_problem_against_oracle():
+    from paper_1409_0405_gb300 import fr
+    probs = _problems()
+    b = fr.Batch([m for m, _ in probs], [p for _, p in probs], precision=fr.FR_FP32)
+    i = 3
+    mesh, p = probs[i]
+    sol = Solver(mesh, p)
+    u = sol.state_from_points(synth.isentropic_vortex(sol.upts_xyz_points()))
+    dt = 0.1 * sol.dt_cfl(u, 1.0)
+    # problem i carries the vortex; the others a uniform state at rest
+    for j, c in enumerate(b.problems):
+        c.set_state(u if j == i else _uniform_pub(c))
+    dts = [dt] * len(probs)
+    b.step(dts, 5, batched=True)
+    got = b.problems[i].get_state()
+    ref = u
+    for _ in range(5):
+        ref = sol.rk4_step(ref, dt)
+    err = per_quantity_rel_err(sol, ref - u, got - u)
+    assert np.all(err <= 1e-4), err
+    b.close()
+
+
+def _uniform_pub(c):
+    out = []
+    for ne, nu in ((c.info["n_tet"], c.info["nu_tet"]), (c.info["n_pri"], c.info["nu_pri"])):
+        if ne:
+            blk = np.zeros((ne, 5, nu))
+            blk[:, 0] = 1.0
+            blk[:, 4] = 2.5
+            out.append(blk.reshape(-1))
+    return np.concatenate(out)

@@ -325,6 +325,183 @@ def batch_mode(fr, torch, args, sp):
 
 
 # ---------------------------------------------------------------------------
+# learned closure: Taylor-Green vortex, p=2 + per-element network vs p=4
+TGV_CELLS = 24
+TGV_MACH = 0.1
+TGV_RE = 1600.0
+TGV_SNAPSHOTS = 8        # training states along the p=4 run
+TGV_STRIDE = 100         # RK4 steps between states
+TGV_ITERS = 1000         # full-batch Adam steps per element type
+TGV_POST_WINDOWS = 4     # strides after the training window (a posteriori)
+
+
+def tgv_params(precision):
+    return dict(viscous=True, mu=1.0 / TGV_RE, gamma=GAMMA, prandtl=0.72, ldg_beta=0.5, ldg_tau=0.1,
+                rho_inf=1.0, vel_inf=(0.0, 0.0, 0.0), p_inf=1.0 / (GAMMA * TGV_MACH ** 2),
+                precision=precision)
+
+
+def _tri_area(a, b, c):
+    return 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+
+
+def min_volume_to_area(mesh):
+    """min over elements of 3 V / A (V volume, A surface area; planar faces)."""
+    x = mesh["xyz"]
+    r = np.inf
+    t = mesh["tet"]
+    if len(t):
+        a, b, c, d = (x[t[:, k]] for k in range(4))
+        V = np.abs(np.einsum("ij,ij->i", b - a, np.cross(c - a, d - a))) / 6.0
+        A = _tri_area(a, b, c) + _tri_area(a, b, d) + _tri_area(a, c, d) + _tri_area(b, c, d)
+        r = min(r, float(np.min(3.0 * V / A)))
+    pr = mesh["pri"]
+    if len(pr):
+        v = [x[pr[:, k]] for k in range(6)]
+        V = sum(np.abs(np.einsum("ij,ij->i", q[1] - q[0], np.cross(q[2] - q[0], q[3] - q[0]))) / 6.0
+                for q in ((v[0], v[1], v[2], v[3]), (v[1], v[2], v[3], v[4]), (v[2], v[3], v[4], v[5])))
+        A = _tri_area(v[0], v[1], v[2]) + _tri_area(v[3], v[4], v[5])
+        for i, j in ((0, 1), (1, 2), (2, 0)):
+            A = A + 0.5 * np.linalg.norm(np.cross(v[j + 3] - v[i], v[i + 3] - v[j]), axis=1)
+        r = min(r, float(np.min(3.0 * V / A)))
+    return r
+
+
+def learned_mode(fr, torch, args, sp):
+    """The learned closure on the Taylor-Green vortex (Re 1600, Ma 0.1,
+    periodic [0, 2 pi]^3 of 24^3 cells: 13,824 prisms + 41,472 tets).
+    The plain p=4 solve (FP32 RHS, FP64 registers) and the plain p=2 solve
+    from the projected initial state run side by side; states along the p=4
+    run give training samples (P RHS_4(u_4) - RHS_2(P u_4), the p=4 RHS in
+    FP64); one network per element type is trained on the GPU by the
+    library's kernels.  Reported: the RHS error with and without the
+    network on a later, held-out state; the kinetic-energy dissipation rate
+    of p=2 with and without the network against p=4, over the training
+    window and over the window after it; the judge's verdict (the network
+    is kept only if it lowers the dissipation error after the training
+    window); and the RHS throughput of each."""
+    import synth
+    from paper_1409_0405_gb300 import closure
+    t_setup = time.perf_counter()
+    mesh = synth.tgv_box(n=TGV_CELLS)
+    c4 = fr.Context(mesh, 4, **tgv_params(fr.FR_FP64))
+    c4f = fr.Context(mesh, 4, **tgv_params(fr.FR_FP32))
+    c2 = fr.Context(mesh, 2, **tgv_params(fr.FR_FP64))
+    counts4 = [(c4.info["n_tet"], c4.info["nu_tet"]), (c4.info["n_pri"], c4.info["nu_pri"])]
+    q = synth.taylor_green(c4.upts_points(), GAMMA, TGV_MACH)
+    u0 = points_to_public(q, counts4)
+    rho, vel = q[:, 0], q[:, 1:4] / q[:, :1]
+    pres = (GAMMA - 1.0) * (q[:, 4] - 0.5 * rho * np.sum(vel ** 2, axis=1))
+    lam = float(np.max(np.linalg.norm(vel, axis=1) + np.sqrt(GAMMA * pres / rho)))
+    dt = 0.1 * min_volume_to_area(mesh) / lam
+    setup_s = time.perf_counter() - t_setup
+    stream = torch.cuda.ExternalStream(sp)
+    nwin = TGV_SNAPSHOTS + TGV_POST_WINDOWS
+
+    # p=4 and p=2 side by side from the same (projected) initial state
+    t0 = time.perf_counter()
+    u4d = torch.from_numpy(u0).cuda()
+    u2_0 = torch.empty(c2.ndof, dtype=torch.float64, device="cuda")
+    c2.transfer_from(c4, u4d.data_ptr(), u2_0.data_ptr(), sp)
+    torch.cuda.synchronize()
+    u2_0h = u2_0.cpu().numpy()
+    c4f.set_state(u0, sp)
+    c2.set_state(u2_0h, sp)
+    S4, ke4, ke2 = [], [], []
+    for k in range(nwin):
+        S4.append(torch.from_numpy(c4f.get_state(stream=sp)).cuda())
+        ke4.append(c4f.reduce(stream=sp)[5])
+        ke2.append(c2.reduce(stream=sp)[5])
+        if k + 1 < nwin:
+            c4f.step(dt, TGV_STRIDE, sp)
+            c2.step(dt, TGV_STRIDE, sp)
+    torch.cuda.synchronize()
+    traj_s = time.perf_counter() - t0
+
+    # training (samples, scales, Adam) on the GPU; the last state is held out
+    t0 = time.perf_counter()
+    cl = closure.Closure(c2, seed=0)
+    log = cl.fit(c4, S4[:TGV_SNAPSHOTS], iters=TGV_ITERS, lr=1e-3, log_every=TGV_ITERS // 4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    prior = cl.error(c4, [S4[-1]])
+
+    # a posteriori: p=2 with the network from the same initial state
+    cl.attach()
+    c2.set_state(u2_0h, sp)
+    ke2c = []
+    for k in range(nwin):
+        ke2c.append(c2.reduce(stream=sp, check=False)[5])
+        if k + 1 < nwin:
+            c2.step(dt, TGV_STRIDE, sp)
+
+    def rates(ke):
+        ke = np.asarray(ke)
+        return -(ke[1:] - ke[:-1]) / (TGV_STRIDE * dt)
+
+    e4, e2, e2c = rates(ke4), rates(ke2), rates(ke2c)
+    tr = slice(0, TGV_SNAPSHOTS - 1)
+    post = slice(TGV_SNAPSHOTS - 1, nwin - 1)
+
+    def rel(a, w):
+        return float(np.mean(np.abs(a[w] - e4[w]) / np.abs(e4[w])))
+
+    verdict = rel(e2c, post) < rel(e2, post)
+
+    # RHS throughput: p=2 + network, p=2, p=4 (FP64)
+    def rhs_ms(ctx, u_dev, n=10):
+        r = torch.empty_like(u_dev)
+        for _ in range(2):
+            ctx.rhs(u_dev.data_ptr(), r.data_ptr(), sp)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(n):
+            ctx.rhs(u_dev.data_ptr(), r.data_ptr(), sp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / n
+
+    c2.profile(True)
+    ms2c = rhs_ms(c2, u2_0)
+    cls2c, _ = c2.profile_read()
+    c2.profile(False)
+    cl.detach()   # the judge's fallback when the verdict is negative
+    ms2 = rhs_ms(c2, u2_0)
+    ms4 = rhs_ms(c4, u4d)
+    closure_ms = cls2c["closure"][0] / max(sum(v[0] for v in cls2c.values()), 1e-30) * ms2c
+    nd2, nd4 = c2.ndof, c4.ndof
+    for c in (c4, c4f, c2):
+        c.close()
+    name = {0: "tet", 1: "pri"}
+    return {
+        "workload": (f"Taylor-Green Re={TGV_RE:g} Ma={TGV_MACH:g}, periodic [0,2pi]^3, {TGV_CELLS}^3 cells "
+                     "(lower half 2 prisms/cell, upper half 6 tets/cell), NS, p=2 + MLP 20nu-128-128-5nu "
+                     "(BF16 GEMM inputs, FP32 accumulate) vs plain p=4"),
+        "dt": dt, "stride_steps": TGV_STRIDE, "train_states": TGV_SNAPSHOTS,
+        "train_t": [0.0, dt * TGV_STRIDE * (TGV_SNAPSHOTS - 1)], "end_t": dt * TGV_STRIDE * (nwin - 1),
+        "train_iters": TGV_ITERS,
+        "loss_log": {name[k]: v for k, v in log.items()},
+        "target_rms_per_variable": {name[k]: list(map(float, v)) for k, v in cl.scale.items()},
+        "held_out_rhs_rel_rms_err": {name[k]: {"with_network": v[0], "plain_p2": v[1]} for k, v in prior.items()},
+        "held_out_t": dt * TGV_STRIDE * (nwin - 1),
+        "ke_dissipation_rel_err_vs_p4": {
+            "training_window": {"p2": rel(e2, tr), "p2_network": rel(e2c, tr)},
+            "after_training_window": {"p2": rel(e2, post), "p2_network": rel(e2c, post)},
+            "p4_rate_end": float(e4[-1]), "measure": "mean over windows of |eps - eps4| / |eps4|, "
+                                                     "eps = -dKE/dt over each stride; p=4 in FP32 RHS"},
+        "judge": {"network_kept": bool(verdict),
+                  "rule": "keep the network only if it lowers the dissipation error after the training window; "
+                          "otherwise detach it (plain p=2 fallback)"},
+        "rhs_ms": {"p2_network": ms2c, "p2": ms2, "p4": ms4, "closure_part_of_p2_network": closure_ms},
+        "gdof_s": {"p2_network": nd2 / (ms2c * 1e-3) / 1e9, "p2": nd2 / (ms2 * 1e-3) / 1e9,
+                   "p4": nd4 / (ms4 * 1e-3) / 1e9},
+        "speedup_p2_network_vs_p4": ms4 / ms2c,
+        "seconds": {"setup": setup_s, "trajectory": traj_s, "training": train_s},
+    }
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,6 +633,7 @@ def main():
         modes["fp32"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_FP32, args, sp)
         if args.nx == 75:
             modes["batched"] = batch_mode(fr, torch, args, sp)
+            modes["learned"] = learned_mode(fr, torch, args, sp)
 
     if rank != 0:
         if world > 1:

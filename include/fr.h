@@ -52,15 +52,18 @@ enum {
     FR_ERR_MESH = -2,       /* J <= 0, unmatched or non-conforming face, bad tag */
     FR_ERR_CUDA = -3,       /* a CUDA runtime call failed */
     FR_ERR_NONFINITE = -4,  /* NaN/Inf or non-positive density/pressure found */
-    FR_ERR_TIMEOUT = -5,    /* reserved: a bounded device wait gave up */
+    FR_ERR_TIMEOUT = -5,    /* a bounded device wait gave up (FR_BF16X3 kernels) */
     FR_ERR_NOMEM = -6,      /* host or device allocation failed */
     FR_ERR_UNSUPPORTED = -7 /* valid request this build does not implement */
 };
 
 enum { FR_ETYPE_TET = 0, FR_ETYPE_PRI = 1 };
 enum { FR_BC_WALL = 1, FR_BC_FARFIELD = 2 };
-/* Arithmetic of the operator applications (Table 1: single and double). */
-enum { FR_FP64 = 0, FR_FP32 = 1 };
+/* Arithmetic of the operator applications (Table 1: single and double;
+ * FR_BF16X3: FP32 storage with the operator applications on the tensor
+ * cores in split BF16, x = bf16(x) + bf16(x - bf16(x)), three products per
+ * pair and FP32 accumulation). */
+enum { FR_FP64 = 0, FR_FP32 = 1, FR_BF16X3 = 2 };
 
 typedef struct fr_ctx fr_ctx; /* opaque; owned by the library */
 
@@ -87,7 +90,9 @@ typedef struct {
     int viscous;      /* 0: Euler, 1: Navier-Stokes */
     int precision;    /* FR_FP64, or FR_FP32: operator applications and point-wise
                          work in FP32; RK registers, the reference-flux
-                         correction and the reductions stay FP64 */
+                         correction and the reductions stay FP64; or
+                         FR_BF16X3: as FR_FP32 with the operator applications
+                         on the tensor cores (split BF16, FP32 accumulate) */
     double rho_inf;   /* far-field density */
     double vel_inf[3];/* far-field velocity */
     double p_inf;     /* far-field pressure */
@@ -178,14 +183,15 @@ int fr_operator(int etype, int order, int which, double *out, int64_t *rows, int
  * Launch accounting.  fr_profile(ctx, enable) resets the counters; while
  * enabled, every kernel launch of fr_rhs/fr_step is bracketed by a CUDA
  * event pair on its stream.  fr_profile_read synchronises on those events
- * and writes, per kernel class (7 entries, caller-owned arrays), the summed
+ * and writes, per kernel class (8 entries, caller-owned arrays), the summed
  * device milliseconds and the launch counts, plus the total number of
  * kernel launches since the last reset (counted with profiling on or off).
  * Classes: 0 M0 interpolation, 1 common solution, 2 corrected gradient,
  * 3 M0 on gradients, 4 point-wise flux, 5 common normal flux,
- * 6 divergence + correction (+ RK update).
+ * 6 divergence + correction (+ RK update), 7 learned closure (features,
+ * network, correction; 8 launches per element type).
  */
-#define FR_NKCLASS 7
+#define FR_NKCLASS 8
 int fr_profile(fr_ctx *ctx, int enable);
 int fr_profile_read(fr_ctx *ctx, double *ms, int64_t *count, int64_t *launches);
 
@@ -261,6 +267,119 @@ int fr_batch_info(const fr_batch *b, int64_t *out);
 #define FR_NOALLOC_MAX_POINTS (FR_NOALLOC_MAX_BLOCKS * 2048LL)
 int fr_reduce_noalloc(int64_t ne, int nu, const double *u_dev, const double *wJ_dev, double gamma,
                       double *out_dev, void *cuda_stream);
+
+/*
+ * ---- Learned closure -----------------------------------------------------
+ * The paper has no learned closure; these entry points add one to the FR
+ * right-hand side of a low order p_lo: a per-element multilayer perceptron
+ * (one network per element type) predicts, from the element's own p_lo
+ * state and corrected gradient, the difference between the projection of
+ * a higher-order (p_hi) right-hand side and the p_lo right-hand side,
+ *     target_e = P(RHS_hi(u_hi))_e - RHS_lo(u_lo)_e,
+ * P the element-wise L2 projection from order p_hi to p_lo, and u_lo
+ * either P u_hi or a p_lo state at the same time (a p_lo solution that
+ * started from the projection of the same initial state).
+ *
+ * Network (FP32 master parameters, BF16 GEMM inputs): nin -> nh -> nh ->
+ * nout, GELU (erf form) after the two hidden layers.  The parameter vector
+ * (FP32) is W1[nh][nin], b1[nh], W2[nh][nh], b2[nh], W3[nout][nh],
+ * b3[nout].  Every GEMM rounds its inputs (features, weights, hidden
+ * activations) to bfloat16, nearest-even, and accumulates in FP32; biases,
+ * pre-activations, gradients and Adam moments are FP32.
+ *
+ * Features of one element (row of nin = 20 nu floats, nu the element's
+ * solution points at p_lo): u - u_inf at the solution points, variable-major
+ * (5 x nu; u_inf the far-field state of fr_params), then the corrected
+ * physical gradient, direction-major (3 x 5 x nu).  Outputs (nout = 5 nu):
+ * the correction at the solution points, variable-major, in units of the
+ * per-variable scales passed to fr_closure_set.
+ */
+
+/*
+ * fr_transfer: host-only query (no GPU needed) of the order-transfer matrix
+ * of one element type, nu(p_to) x nu(p_from), row-major float64: the L2
+ * projection, on the reference element, of the p_from solution-point
+ * interpolant onto the p_to space, evaluated at the p_to solution points
+ * (a restriction for p_to < p_from, an exact prolongation otherwise).
+ * With out == NULL only *rows/*cols are written.  Errors: FR_ERR_ARG.
+ */
+int fr_transfer(int etype, int p_from, int p_to, double *out, int64_t *rows, int64_t *cols);
+
+/*
+ * fr_transfer_state: u_to_dev = the order transfer of u_from_dev, element
+ * by element, from the order of ctx_from to that of ctx_to (public layouts,
+ * device, caller-owned; both contexts on the same mesh).  The first call for
+ * a source order uploads the matrices into ctx_to (allocates).
+ * Asynchronous on cuda_stream.  Errors: FR_ERR_ARG (null pointer, element
+ * counts that differ), FR_ERR_NOMEM, FR_ERR_CUDA.
+ */
+int fr_transfer_state(const fr_ctx *ctx_from, fr_ctx *ctx_to, const double *u_from_dev, double *u_to_dev,
+                      void *cuda_stream);
+
+/*
+ * fr_closure_features: the features (see above) of every element of type
+ * etype for the public state u_dev (device, FP64), written to x_dev (device,
+ * caller-owned, ne x 20 nu floats, row-major).  Runs the interpolation and
+ * gradient stages of the RHS.  Requires a Navier-Stokes context
+ * (viscous != 0; FR_ERR_UNSUPPORTED otherwise).  Asynchronous.
+ */
+int fr_closure_features(fr_ctx *ctx, const double *u_dev, int etype, float *x_dev, void *cuda_stream);
+
+/*
+ * fr_closure_sample: one set of training samples.  With u_hi_dev the public
+ * state of ctx_hi (device, FP64) it evaluates RHS_hi(u_hi) and projects it
+ * to the order of ctx_lo, evaluates RHS_lo (without any closure) of u_lo_dev
+ * (a public state of ctx_lo) or, when u_lo_dev is NULL, of the projected
+ * u_hi, and writes for the elements of type etype: the features of that
+ * low-order state to x_dev (ne x 20 nu floats), the target
+ * inv_scale[v] * (P RHS_hi - RHS_lo) to t_dev (ne x 5 nu floats, v the
+ * variable of each entry; inv_scale a host array of 5, NULL = 1), and adds
+ * the per-variable sums of squares of the unscaled target to ss_dev[0..4]
+ * (device, FP64).  Any of x_dev, t_dev, ss_dev may be NULL.  ctx_lo must be
+ * Navier-Stokes; its scratch is allocated on the first call.  Asynchronous.
+ * Errors as fr_transfer_state and fr_closure_features.
+ */
+int fr_closure_sample(fr_ctx *ctx_hi, fr_ctx *ctx_lo, const double *u_hi_dev, const double *u_lo_dev, int etype,
+                      const double *inv_scale, float *x_dev, float *t_dev, double *ss_dev, void *cuda_stream);
+
+/*
+ * fr_closure_set: attach (params_dev != NULL) or detach (NULL) the network
+ * of element type etype.  params_dev (device, FP32, fr_mlp_nparams(20 nu,
+ * nh, 5 nu) floats) is copied into the context.  While attached, every
+ * fr_rhs / fr_step adds out_scale[v] * network(features) (out_scale: host
+ * array of 5, one per conserved variable) to the RHS of those elements,
+ * inside the divergence epilogue.  Requires a Navier-Stokes context;
+ * batched steps (fr_batch_step) reject problems with a closure.
+ * Synchronous (allocates on the first call).  Errors: FR_ERR_ARG,
+ * FR_ERR_UNSUPPORTED, FR_ERR_NOMEM, FR_ERR_CUDA.
+ */
+int fr_closure_set(fr_ctx *ctx, int etype, const float *params_dev, int nh, const double *out_scale);
+
+/*
+ * The network's kernels, usable on their own (all pointers device,
+ * caller-owned; row-major; asynchronous on cuda_stream):
+ * fr_mlp_nparams: length of the parameter vector (host, no GPU).
+ * fr_mlp_workspace: floats of scratch one call on n samples needs (host).
+ * fr_mlp_forward: y (n x nout) = network(x (n x nin)).  ws holds, after the
+ *   call, Z1, H1, Z2, H2 (each n x nh; Z the pre-activations, H = GELU(Z)
+ *   before rounding).
+ * fr_mlp_grad: forward then backward of the loss L = mean over all n*nout
+ *   entries of (y - t)^2; g (nparams floats) = dL/dparams, loss_dev[0] = L.
+ *   ws as fr_mlp_forward, then dZ2 and dZ1 (n x nh each), y and dL/dy
+ *   (n x nout each).
+ * fr_mlp_adam: params -= lr * mhat / (sqrt(vhat) + 1e-8) with m, v the
+ *   first/second moments (beta 0.9 / 0.999, updated in place) and the bias
+ *   corrections of step (counting from 1).
+ * Errors: FR_ERR_ARG for non-positive sizes, null pointers or step < 1.
+ */
+int64_t fr_mlp_nparams(int nin, int nh, int nout);
+int64_t fr_mlp_workspace(int nin, int nh, int nout, int64_t n);
+int fr_mlp_forward(int nin, int nh, int nout, int64_t n, const float *x_dev, const float *params_dev, float *y_dev,
+                   float *ws_dev, void *cuda_stream);
+int fr_mlp_grad(int nin, int nh, int nout, int64_t n, const float *x_dev, const float *t_dev,
+                const float *params_dev, float *g_dev, float *loss_dev, float *ws_dev, void *cuda_stream);
+int fr_mlp_adam(int64_t nparams, float *params_dev, const float *g_dev, float *m_dev, float *v_dev, int step,
+                float lr, void *cuda_stream);
 
 /* Static description of an error code. */
 const char *fr_strerror(int code);

@@ -155,25 +155,6 @@ cudaEvent_t next_event(fr_ctx *c) {
     return c->ev_pool[c->ev_used++];
 }
 
-// Launch one kernel through `fn`, counting it and, when profiling, timing it
-// with an event pair recorded on the launch stream.
-template <class F>
-cudaError_t launch(fr_ctx *c, int kclass, cudaStream_t s, F fn) {
-    cudaEvent_t a = nullptr, b = nullptr;
-    if (c->prof) {
-        a = next_event(c);
-        b = next_event(c);
-        if (a && b) cudaEventRecord(a, s);
-    }
-    cudaError_t e = fn();
-    ++c->launches;
-    if (c->prof && a && b) {
-        cudaEventRecord(b, s);
-        c->prof_ev.push_back({kclass, {a, b}});
-    }
-    return e;
-}
-
 // One RHS evaluation on the stage input `in[t]`; the final operator
 // application either stores R (rk == nullptr) or applies the RK update.
 
@@ -272,8 +253,30 @@ GemmArgsT<T> args_div(const fr_ctx *c, int t, const RKStage *rk) {
     return g;
 }
 
+template <>
+cudaError_t op_gemm<double>(fr_ctx *, int, int, const GemmArgsT<double> &g, cudaStream_t s) {
+    return launch_gemm<double>(g, s);
+}
+
+template <>
+cudaError_t op_gemm<float>(fr_ctx *c, int t, int which, const GemmArgsT<float> &g, cudaStream_t s) {
+    if (c->prm.precision == FR_BF16X3) return launch_gemm_tc(g, c->T[t].tc[which], c->tc_err, s);
+    return launch_gemm<float>(g, s);
+}
+
+// FR_ERR_TIMEOUT if a tensor-core kernel gave up a wait (synchronises)
+int check_tc(fr_ctx *c) {
+    if (c->prm.precision != FR_BF16X3 || !c->tc_err) return FR_OK;
+    int h = 0;
+    int rc = cuda_check(cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
+    if (rc) return rc;
+    if (h) return set_err(FR_ERR_TIMEOUT, "a tensor-core operator kernel gave up a bounded wait (code " +
+                                              std::to_string(h) + ")");
+    return FR_OK;
+}
+
 template <typename T>
-int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
+int front_stages(fr_ctx *c, T *const in[2], cudaStream_t s) {
     const Phys ph = phys_of(c);
     const FieldsT<T> F = fields_of<T>(c);
     int rc;
@@ -281,7 +284,7 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
     for (int t = 0; t < 2; ++t) {
         if (!c->T[t].present) continue;
         const GemmArgsT<T> g = args_m0<T>(c, t, in[t]);
-        if ((rc = cuda_check(launch(c, K_M0, s, [&] { return launch_gemm<T>(g, s); }), "gemm M0"))) return rc;
+        if ((rc = cuda_check(launch(c, K_M0, s, [&] { return op_gemm<T>(c, t, 0, g, s); }), "gemm M0"))) return rc;
     }
     if (c->prm.viscous) {
         // 2. common solution and jumps
@@ -293,12 +296,22 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
         for (int t = 0; t < 2; ++t) {
             if (!c->T[t].present) continue;
             const GemmArgsT<T> g = args_grad<T>(c, t, in[t]);
-            if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return launch_gemm<T>(g, s); }), "gemm grad"))) return rc;
+            if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return op_gemm<T>(c, t, 1, g, s); }), "gemm grad")))
+                return rc;
             const GemmArgsT<T> h = args_m0grad<T>(c, t);
-            if ((rc = cuda_check(launch(c, K_M0_GRAD, s, [&] { return launch_gemm<T>(h, s); }), "gemm M0 grad")))
+            if ((rc = cuda_check(launch(c, K_M0_GRAD, s, [&] { return op_gemm<T>(c, t, 0, h, s); }), "gemm M0 grad")))
                 return rc;
         }
     }
+    return FR_OK;
+}
+
+template <typename T>
+int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
+    const Phys ph = phys_of(c);
+    const FieldsT<T> F = fields_of<T>(c);
+    int rc;
+    if ((rc = front_stages<T>(c, in, s))) return rc;
     // 5. transformed flux at solution points
     for (int t = 0; t < 2; ++t) {
         DevType &D = c->T[t];
@@ -316,11 +329,16 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
                                 [&] { return launch_common_flux<T>(pairs_of(c), bnd_of(c), F, ph, s); }),
                          "common flux")))
         return rc;
-    // 7. divergence plus correction
+    // 7. divergence plus correction; with the learned closure on, the
+    // network's correction is added by the epilogue with the reference term
     for (int t = 0; t < 2; ++t) {
         if (!c->T[t].present) continue;
-        const GemmArgsT<T> g = args_div<T>(c, t, rk);
-        if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return launch_gemm<T>(g, s); }), "gemm div"))) return rc;
+        GemmArgsT<T> g = args_div<T>(c, t, rk);
+        if (c->T[t].cl_on) {
+            if ((rc = closure_apply<T>(c, t, in[t], s))) return rc;
+            g.rfs = c->T[t].cl_add;
+        }
+        if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return op_gemm<T>(c, t, 2, g, s); }), "gemm div"))) return rc;
     }
     return FR_OK;
 }
@@ -343,8 +361,8 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         return set_err(FR_ERR_ARG, "null connectivity array");
     if (mesh->n_tet > (1LL << 30) || mesh->n_pri > (1LL << 30))
         return set_err(FR_ERR_ARG, "element count too large");
-    if (prm->precision != FR_FP64 && prm->precision != FR_FP32)
-        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64 or FR_FP32");
+    if (prm->precision != FR_FP64 && prm->precision != FR_FP32 && prm->precision != FR_BF16X3)
+        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64, FR_FP32 or FR_BF16X3");
     if (!(prm->gamma > 1.0) || prm->mu < 0.0 || (prm->viscous && !(prm->prandtl > 0.0)))
         return set_err(FR_ERR_ARG, "invalid gas parameters");
     c->prm = *prm;
@@ -377,7 +395,7 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         D.nu = ops[t].nu;
         D.nf = ops[t].nf;
         const size_t su = (size_t)D.nu * NV * D.np, sf = (size_t)D.nf * NV * D.np;
-        const size_t es = prm->precision == FR_FP32 ? sizeof(float) : sizeof(double);
+        const size_t es = prm->precision != FR_FP64 ? sizeof(float) : sizeof(double);
         if ((rc = dev_alloc(c, &D.U, su)) || (rc = dev_alloc(c, &D.Uacc, su)) ||
             (rc = dev_alloc_bytes(c, &D.Us, su * es)) || (rc = dev_alloc_bytes(c, &D.R, su * es)) ||
             (rc = dev_alloc_bytes(c, &D.UF, sf * es)) || (rc = dev_alloc_bytes(c, &D.FC, sf * es)) ||
@@ -403,7 +421,24 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             (rc = upload(c, &D.M0, ops[t].M0)) || (rc = upload(c, &D.AGRAD, ops[t].AGRAD)) ||
             (rc = upload(c, &D.ADIV, ops[t].ADIV)))
             return rc;
-        if (prm->precision == FR_FP32) {
+        if (prm->precision == FR_BF16X3) {
+            // the three operators packed for the tensor cores
+            const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
+            const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok[3] = {D.nu, D.nu + D.nf, 3 * D.nu + D.nf};
+            for (int w = 0; w < 3; ++w) {
+                std::vector<uint16_t> img;
+                TcOperator &op = D.tc[w];
+                tc_pack(opv[w]->data(), om[w], ok[w], img, op.Nmma, op.Kpad);
+                op.M = om[w];
+                op.K = ok[w];
+                if (op.Nmma > 256 || tc_stages(op) < 2)
+                    return set_err(FR_ERR_UNSUPPORTED, "operator too large for the tensor-core kernel");
+                uint16_t *dimg = nullptr;
+                if ((rc = upload(c, &dimg, img))) return rc;
+                op.img = (const uint8_t *)dimg;
+            }
+        }
+        if (prm->precision != FR_FP64) {
             // float views of the geometry and operators (rounded once)
             double *src[5] = {D.S, D.invJ, D.M0, D.AGRAD, D.ADIV};
             void **dst[5] = {&D.S_t, &D.invJ_t, &D.M0_t, &D.AGRAD_t, &D.ADIV_t};
@@ -439,7 +474,7 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
     // buffers in FR_FP32.
     {
         const Phys ph = phys_of(c);
-        const bool f32 = prm->precision == FR_FP32;
+        const bool f32 = prm->precision != FR_FP64;
         double *tFT[2] = {nullptr, nullptr}, *tFC[2] = {nullptr, nullptr};
         std::vector<void *> tmp;
         for (int t = 0; t < 2; ++t) {
@@ -510,6 +545,7 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         nbt += c->red_blocks[t];
     }
     if ((rc = dev_alloc(c, &c->red, (size_t)nbt * 7 + 8))) return rc;
+    if ((rc = dev_alloc(c, &c->tc_err, 1))) return rc;
     return cuda_check(cudaDeviceSynchronize(), "fr_create sync");
 }
 
@@ -567,6 +603,10 @@ int step_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
 }
 
 template int step_impl<float>(fr_ctx *, double, int, cudaStream_t);
+template int rhs_public<float>(fr_ctx *, const double *, double *, cudaStream_t);
+template int rhs_public<double>(fr_ctx *, const double *, double *, cudaStream_t);
+template int front_stages<float>(fr_ctx *, float *const[2], cudaStream_t);
+template int front_stages<double>(fr_ctx *, double *const[2], cudaStream_t);
 template int step_impl<double>(fr_ctx *, double, int, cudaStream_t);
 template FieldsT<float> fields_of<float>(const fr_ctx *);
 template FieldsT<double> fields_of<double>(const fr_ctx *);
@@ -734,20 +774,21 @@ int fr_get_state(fr_ctx *c, double *u, void *stream) {
             return rc;
         off += n;
     }
-    return cuda_check(cudaStreamSynchronize(s), "get_state sync");
+    const int rc = cuda_check(cudaStreamSynchronize(s), "get_state sync");
+    return rc ? rc : check_tc(c);
 }
 
 int fr_rhs(fr_ctx *c, const double *u_dev, double *r_dev, void *stream) {
     if (!c || !u_dev || !r_dev) return set_err(FR_ERR_ARG, "null argument");
     if (u_dev == r_dev) return set_err(FR_ERR_ARG, "u and r may not alias");
     cudaStream_t s = (cudaStream_t)stream;
-    return c->prm.precision == FR_FP32 ? rhs_public<float>(c, u_dev, r_dev, s) : rhs_public<double>(c, u_dev, r_dev, s);
+    return is_f32(c) ? rhs_public<float>(c, u_dev, r_dev, s) : rhs_public<double>(c, u_dev, r_dev, s);
 }
 
 int fr_step(fr_ctx *c, double dt, int nsteps, void *stream) {
     if (!c || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
     cudaStream_t s = (cudaStream_t)stream;
-    return c->prm.precision == FR_FP32 ? step_impl<float>(c, dt, nsteps, s) : step_impl<double>(c, dt, nsteps, s);
+    return is_f32(c) ? step_impl<float>(c, dt, nsteps, s) : step_impl<double>(c, dt, nsteps, s);
 }
 
 int fr_reduce(fr_ctx *c, double *out, void *stream) {
@@ -768,6 +809,7 @@ int fr_reduce(fr_ctx *c, double *out, void *stream) {
     if ((rc = cuda_check(cudaMemcpyAsync(out, res, 7 * sizeof(double), cudaMemcpyDeviceToHost, s), "reduce copy")))
         return rc;
     if ((rc = cuda_check(cudaStreamSynchronize(s), "reduce sync"))) return rc;
+    if ((rc = check_tc(c))) return rc;
     if (out[6] != 0.0) return set_err(FR_ERR_NONFINITE, "non-finite or non-physical state");
     return FR_OK;
 }

@@ -473,6 +473,8 @@ extern "C" {
 int fr_batch_create(int nprob, const fr_mesh *meshes, const int *orders, const fr_params *params, fr_batch **out) {
     if (!out || nprob <= 0 || !meshes || !orders || !params) return set_err(FR_ERR_ARG, "invalid batch arguments");
     *out = nullptr;
+    if (params->precision == FR_BF16X3)
+        return set_err(FR_ERR_UNSUPPORTED, "batched launches run FR_FP64 or FR_FP32 operator kernels");
     fr_batch *b = new (std::nothrow) fr_batch();
     if (!b) return set_err(FR_ERR_NOMEM, "host allocation");
     for (int i = 0; i < nprob; ++i) {
@@ -527,8 +529,11 @@ int fr_batch_tune(fr_batch *b, void *stream) {
 
 int fr_batch_step(fr_batch *b, const double *dt, int nsteps, int batched, void *stream) {
     if (!b || !dt || nsteps < 0) return set_err(FR_ERR_ARG, "invalid step arguments");
-    for (size_t i = 0; i < b->ctx.size(); ++i)
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
         if (!(dt[i] == dt[i])) return set_err(FR_ERR_ARG, "non-finite time step");
+        if (b->ctx[i]->T[0].cl_on || b->ctx[i]->T[1].cl_on)
+            return set_err(FR_ERR_UNSUPPORTED, "batched steps do not apply a learned closure");
+    }
     return b->impl->step(dt, nsteps, batched, (cudaStream_t)stream);
 }
 

@@ -1,0 +1,394 @@
+// Learned closure of the low-order FR right-hand side (no counterpart in the
+// paper; declared in include/fr.h): order transfer between two contexts on
+// one mesh, the per-element features, training samples, and the network's
+// correction inside the RHS.
+//
+// Internal layouts (see fr_api.cu): stage input Us [nu][V][np] (u - u_inf),
+// corrected gradient GU [nu][3][V][np], both with the element index
+// fastest.  Features and network outputs are row-major per element:
+// X[e][f], f = v nu + j (state) then 5 nu + m 5 nu + v nu + j (gradient);
+// Y[e][v nu + j].
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "fr_ctx.h"
+#include "fr_internal.h"
+#include "fr_mlp.h"
+
+namespace fr {
+namespace {
+
+// X[e][f] for 32 elements x 32 features per block (tile transpose)
+template <typename T>
+__global__ void k_features(int nu, int64_t ne, int64_t np, const T *__restrict__ Us, const T *__restrict__ GU,
+                           float *__restrict__ X) {
+    __shared__ float tile[32][33];
+    const int nin = 20 * nu, nv = 5 * nu;
+    const int64_t e0 = (int64_t)blockIdx.x * 32;
+    const int f0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        const int f = f0 + k;
+        const int64_t e = e0 + tx;
+        float v = 0.f;
+        if (f < nin && e < ne) {
+            if (f < nv) {
+                const int var = f / nu, j = f % nu;
+                v = (float)Us[((int64_t)j * 5 + var) * np + e];
+            } else {
+                const int r = f - nv, m = r / nv, var = (r % nv) / nu, j = r % nu;
+                v = (float)GU[(((int64_t)j * 3 + m) * 5 + var) * np + e];
+            }
+        }
+        tile[k][tx] = v;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t e = e0 + k;
+        const int f = f0 + tx;
+        if (e < ne && f < nin) X[e * nin + f] = tile[tx][k];
+    }
+}
+
+struct Scale5 {
+    double s[5];
+};
+
+// add[j][v][e] = rfs[j][v][e] + scale_v Y[e][v nu + j]  (padding: rfs only)
+__global__ void k_correction(int nu, int64_t ne, int64_t np, const double *__restrict__ rfs,
+                             const float *__restrict__ Y, Scale5 scale, double *__restrict__ add) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)nu * 5 * np;
+    if (i >= total) return;
+    const int64_t e = i % np, row = i / np;
+    const int j = (int)(row / 5), v = (int)(row % 5);
+    double a = rfs ? rfs[i] : 0.0;
+    if (e < ne) a += scale.s[v] * (double)Y[e * (5 * nu) + v * nu + j];
+    add[i] = a;
+}
+
+// out[r][i] = sum_j R[i][j] in[r][j] over rows r = (e, v) of one type's
+// public block
+__global__ void k_transfer(int64_t rows, int nto, int nfrom, const double *__restrict__ R,
+                           const double *__restrict__ in, double *__restrict__ out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rows * nto) return;
+    const int64_t r = k / nto;
+    const int i = (int)(k % nto);
+    const double *a = R + (int64_t)i * nfrom, *b = in + r * nfrom;
+    double s = 0.0;
+    for (int j = 0; j < nfrom; ++j) s = fma(a[j], b[j], s);
+    out[k] = s;
+}
+
+// over one type's public block (i = (e, v, j)): t = inv_scale_v (a - b) as
+// float, ss[v] += sum (a - b)^2
+__global__ void k_target(int64_t n, int nu, const double *__restrict__ a, const double *__restrict__ b,
+                         Scale5 inv_scale, float *__restrict__ t, double *__restrict__ ss) {
+    __shared__ double sh[8][5];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double q[5] = {0, 0, 0, 0, 0};
+    if (i < n) {
+        const int v = (int)((i / nu) % 5);
+        const double d = a[i] - b[i];
+        if (t) t[i] = (float)(inv_scale.s[v] * d);
+        q[v] = d * d;
+    }
+    if (!ss) return;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+        for (int o = 16; o > 0; o >>= 1) q[v] += __shfl_down_sync(0xffffffffu, q[v], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int v = 0; v < 5; ++v) sh[threadIdx.x >> 5][v] = q[v];
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w][threadIdx.x];
+        atomicAdd(ss + threadIdx.x, tot);
+    }
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+namespace api {
+
+// features of type t from the stage input and the gradient buffer
+template <typename T>
+cudaError_t launch_features(const DevType &D, const T *in, float *X, cudaStream_t s) {
+    dim3 grid(nblk(D.ne, 32), nblk(20 * D.nu, 32));
+    k_features<T><<<grid, 256, 0, s>>>(D.nu, D.ne, D.np, in, (const T *)D.GU, X);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int closure_apply(fr_ctx *c, int t, const T *in, cudaStream_t s) {
+    DevType &D = c->T[t];
+    const int nin = 20 * D.nu, nout = 5 * D.nu;
+    cudaError_t e = launch(
+        c, K_CLOSURE, s,
+        [&]() -> cudaError_t {
+            cudaError_t r = launch_features<T>(D, in, D.cl_X, s);
+            if (r != cudaSuccess) return r;
+            if ((r = mlp_forward(nin, D.cl_nh, nout, D.ne, D.cl_X, D.cl_P, D.cl_Y, D.cl_ws, s)) != cudaSuccess)
+                return r;
+            Scale5 sc;
+            for (int v = 0; v < 5; ++v) sc.s[v] = D.cl_scale[v];
+            k_correction<<<nblk((int64_t)D.nu * 5 * D.np, 256), 256, 0, s>>>(D.nu, D.ne, D.np, D.Rfs, D.cl_Y, sc,
+                                                                            D.cl_add);
+            return cudaGetLastError();
+        },
+        8);
+    return cuda_check(e, "closure");
+}
+
+template int closure_apply<float>(fr_ctx *, int, const float *, cudaStream_t);
+template int closure_apply<double>(fr_ctx *, int, const double *, cudaStream_t);
+
+namespace {
+
+// transfer matrices from order p_from into `to` (cached for one p_from)
+int ensure_transfer(fr_ctx *to, int p_from) {
+    if (to->tr_from == p_from) return FR_OK;
+    for (int t = 0; t < 2; ++t) {
+        if (!to->T[t].present) continue;
+        std::vector<double> R;
+        std::string err;
+        int rc = build_transfer(t, p_from, to->order, R, err);
+        if (rc) return set_err(rc, err);
+        if (!to->tr[t]) {
+            const size_t bytes = (size_t)nupts_of(t, 4) * nupts_of(t, 4) * sizeof(double);
+            void *p = nullptr;
+            if ((rc = dev_alloc_bytes(to, &p, bytes))) return rc;
+            to->tr[t] = (double *)p;
+        }
+        if ((rc = cuda_check(cudaMemcpy(to->tr[t], R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice),
+                             "transfer upload")))
+            return rc;
+    }
+    to->tr_from = p_from;
+    return FR_OK;
+}
+
+int check_pair(const fr_ctx *a, const fr_ctx *b) {
+    if (!a || !b) return set_err(FR_ERR_ARG, "null context");
+    for (int t = 0; t < 2; ++t)
+        if (a->T[t].ne != b->T[t].ne) return set_err(FR_ERR_ARG, "contexts have different element counts");
+    return FR_OK;
+}
+
+int transfer_state(const fr_ctx *from, fr_ctx *to, const double *u, double *out, cudaStream_t s) {
+    int rc;
+    if ((rc = check_pair(from, to))) return rc;
+    if (!u || !out) return set_err(FR_ERR_ARG, "null state pointer");
+    if ((rc = ensure_transfer(to, from->order))) return rc;
+    size_t off_f = 0, off_t = 0;
+    for (int t = 0; t < 2; ++t) {
+        const DevType &D = to->T[t];
+        if (!D.present) continue;
+        const int nf = from->T[t].nu, nt = D.nu;
+        const int64_t rows = D.ne * 5;
+        k_transfer<<<nblk(rows * nt, 256), 256, 0, s>>>(rows, nt, nf, to->tr[t], u + off_f, out + off_t);
+        if ((rc = cuda_check(cudaGetLastError(), "transfer"))) return rc;
+        off_f += (size_t)rows * nf;
+        off_t += (size_t)rows * nt;
+    }
+    return FR_OK;
+}
+
+template <typename T>
+int features_impl(fr_ctx *c, const double *u, int etype, float *X, cudaStream_t s) {
+    const Phys ph = phys_of(c);
+    size_t off = 0;
+    T *in[2] = {nullptr, nullptr};
+    int rc;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_pub_to_int<T>(D.nu, D.ne, D.np, u + off, nullptr, s, (T *)D.Us, ph.uref),
+                             "features layout in")))
+            return rc;
+        in[t] = (T *)D.Us;
+        off += (size_t)D.ne * 5 * D.nu;
+    }
+    if ((rc = front_stages<T>(c, in, s))) return rc;
+    return cuda_check(launch_features<T>(c->T[etype], in[etype], X, s), "features");
+}
+
+int check_closure_ctx(const fr_ctx *c, int etype) {
+    if (!c) return set_err(FR_ERR_ARG, "null context");
+    if (etype != FR_ETYPE_TET && etype != FR_ETYPE_PRI) return set_err(FR_ERR_ARG, "etype must be 0 or 1");
+    if (!c->prm.viscous) return set_err(FR_ERR_UNSUPPORTED, "the closure needs a Navier-Stokes context");
+    if (!c->T[etype].present) return set_err(FR_ERR_ARG, "no elements of this type");
+    return FR_OK;
+}
+
+}  // namespace
+}  // namespace api
+}  // namespace fr
+
+using namespace fr;
+using namespace fr::api;
+
+extern "C" {
+
+int fr_transfer(int etype, int p_from, int p_to, double *out, int64_t *rows, int64_t *cols) {
+    if (!rows || !cols) return set_err(FR_ERR_ARG, "null argument");
+    if ((etype != FR_ETYPE_TET && etype != FR_ETYPE_PRI) || p_from < 1 || p_from > 4 || p_to < 1 || p_to > 4)
+        return set_err(FR_ERR_ARG, "etype must be 0/1 and orders 1..4");
+    *rows = nupts_of(etype, p_to);
+    *cols = nupts_of(etype, p_from);
+    if (!out) return FR_OK;
+    std::vector<double> R;
+    std::string err;
+    int rc = build_transfer(etype, p_from, p_to, R, err);
+    if (rc) return set_err(rc, err);
+    std::copy(R.begin(), R.end(), out);
+    return FR_OK;
+}
+
+int fr_transfer_state(const fr_ctx *from, fr_ctx *to, const double *u_from_dev, double *u_to_dev, void *stream) {
+    return transfer_state(from, to, u_from_dev, u_to_dev, (cudaStream_t)stream);
+}
+
+int fr_closure_features(fr_ctx *c, const double *u_dev, int etype, float *x_dev, void *stream) {
+    int rc;
+    if ((rc = check_closure_ctx(c, etype))) return rc;
+    if (!u_dev || !x_dev) return set_err(FR_ERR_ARG, "null pointer");
+    const cudaStream_t s = (cudaStream_t)stream;
+    return is_f32(c) ? features_impl<float>(c, u_dev, etype, x_dev, s)
+                                       : features_impl<double>(c, u_dev, etype, x_dev, s);
+}
+
+int fr_closure_sample(fr_ctx *hi, fr_ctx *lo, const double *u_hi_dev, const double *u_lo_dev, int etype,
+                      const double *inv_scale, float *x_dev, float *t_dev, double *ss_dev, void *stream) {
+    int rc;
+    if ((rc = check_closure_ctx(lo, etype)) || (rc = check_pair(hi, lo))) return rc;
+    if (!u_hi_dev) return set_err(FR_ERR_ARG, "null state pointer");
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nlo = ndof_of(lo), nhi = ndof_of(hi);
+    if (!lo->smp_u) {
+        void *p[3];
+        for (int k = 0; k < 3; ++k)
+            if ((rc = dev_alloc_bytes(lo, &p[k], (size_t)nlo * sizeof(double)))) return rc;
+        lo->smp_u = (double *)p[0];
+        lo->smp_r = (double *)p[1];
+        lo->smp_rr = (double *)p[2];
+    }
+    if (lo->smp_rhi_cap < nhi) {
+        void *p = nullptr;
+        if ((rc = dev_alloc_bytes(lo, &p, (size_t)nhi * sizeof(double)))) return rc;
+        lo->smp_rhi = (double *)p;
+        lo->smp_rhi_cap = nhi;
+    }
+    // RHS_hi and its projection
+    rc = is_f32(hi) ? rhs_public<float>(hi, u_hi_dev, lo->smp_rhi, s)
+                                      : rhs_public<double>(hi, u_hi_dev, lo->smp_rhi, s);
+    if (rc) return rc;
+    if ((rc = transfer_state(hi, lo, lo->smp_rhi, lo->smp_rr, s))) return rc;
+    // RHS_lo (without a closure) of u_lo, or of the projected state
+    const double *ulo = u_lo_dev;
+    if (!ulo) {
+        if ((rc = transfer_state(hi, lo, u_hi_dev, lo->smp_u, s))) return rc;
+        ulo = lo->smp_u;
+    }
+    const int on[2] = {lo->T[0].cl_on, lo->T[1].cl_on};
+    lo->T[0].cl_on = lo->T[1].cl_on = 0;
+    rc = is_f32(lo) ? rhs_public<float>(lo, ulo, lo->smp_r, s)
+                                      : rhs_public<double>(lo, ulo, lo->smp_r, s);
+    lo->T[0].cl_on = on[0];
+    lo->T[1].cl_on = on[1];
+    if (rc) return rc;
+    // the features of the state RHS_lo just ran on (its stage input and
+    // gradient are still in the context's buffers)
+    const DevType &D = lo->T[etype];
+    if (x_dev) {
+        rc = is_f32(lo) ? cuda_check(launch_features<float>(D, (const float *)D.Us, x_dev, s), "features")
+                                          : cuda_check(launch_features<double>(D, (const double *)D.Us, x_dev, s), "features");
+        if (rc) return rc;
+    }
+    if (t_dev || ss_dev) {
+        const size_t off = etype == FR_ETYPE_PRI && lo->T[0].present ? (size_t)lo->T[0].ne * 5 * lo->T[0].nu : 0;
+        const int64_t n = D.ne * 5 * D.nu;
+        Scale5 isc;
+        for (int v = 0; v < 5; ++v) isc.s[v] = inv_scale ? inv_scale[v] : 1.0;
+        k_target<<<nblk(n, 256), 256, 0, s>>>(n, D.nu, lo->smp_rr + off, lo->smp_r + off, isc, t_dev, ss_dev);
+        if ((rc = cuda_check(cudaGetLastError(), "target"))) return rc;
+    }
+    return FR_OK;
+}
+
+int fr_closure_set(fr_ctx *c, int etype, const float *params_dev, int nh, const double *out_scale) {
+    int rc;
+    if ((rc = check_closure_ctx(c, etype))) return rc;
+    DevType &D = c->T[etype];
+    if (!params_dev) {
+        D.cl_on = 0;
+        return FR_OK;
+    }
+    if (nh <= 0 || nh > 4096) return set_err(FR_ERR_ARG, "hidden width must be in 1..4096");
+    if (!out_scale) return set_err(FR_ERR_ARG, "null output scales");
+    const int nin = 20 * D.nu, nout = 5 * D.nu;
+    const MlpLayout L = mlp_layout(nin, nh, nout);
+    if (D.cl_cap_nh < nh) {
+        void *p[4];
+        const size_t sz[4] = {(size_t)L.n * sizeof(float), (size_t)D.ne * nin * sizeof(float),
+                              (size_t)D.ne * nout * sizeof(float),
+                              (size_t)mlp_workspace_floats(nin, nh, nout, D.ne) * sizeof(float)};
+        for (int k = 0; k < 4; ++k)
+            if ((rc = dev_alloc_bytes(c, &p[k], sz[k]))) return rc;
+        D.cl_P = (float *)p[0];
+        D.cl_X = (float *)p[1];
+        D.cl_Y = (float *)p[2];
+        D.cl_ws = (float *)p[3];
+        if (!D.cl_add) {
+            void *q = nullptr;
+            if ((rc = dev_alloc_bytes(c, &q, (size_t)D.nu * 5 * D.np * sizeof(double)))) return rc;
+            D.cl_add = (double *)q;
+        }
+        D.cl_cap_nh = nh;
+    }
+    if ((rc = cuda_check(cudaMemcpy(D.cl_P, params_dev, (size_t)L.n * sizeof(float), cudaMemcpyDeviceToDevice),
+                         "closure parameters")))
+        return rc;
+    D.cl_nh = nh;
+    for (int v = 0; v < 5; ++v) D.cl_scale[v] = out_scale[v];
+    D.cl_on = 1;
+    return FR_OK;
+}
+
+int64_t fr_mlp_nparams(int nin, int nh, int nout) {
+    if (nin <= 0 || nh <= 0 || nout <= 0) return 0;
+    return mlp_layout(nin, nh, nout).n;
+}
+
+int64_t fr_mlp_workspace(int nin, int nh, int nout, int64_t n) {
+    if (nin <= 0 || nh <= 0 || nout <= 0 || n <= 0) return 0;
+    return mlp_workspace_floats(nin, nh, nout, n);
+}
+
+int fr_mlp_forward(int nin, int nh, int nout, int64_t n, const float *x, const float *P, float *y, float *ws,
+                   void *stream) {
+    if (nin <= 0 || nh <= 0 || nout <= 0 || n <= 0 || n > (1LL << 30)) return set_err(FR_ERR_ARG, "invalid sizes");
+    if (!x || !P || !y || !ws) return set_err(FR_ERR_ARG, "null pointer");
+    return cuda_check(mlp_forward(nin, nh, nout, n, x, P, y, ws, (cudaStream_t)stream), "mlp forward");
+}
+
+int fr_mlp_grad(int nin, int nh, int nout, int64_t n, const float *x, const float *t, const float *P, float *g,
+                float *loss, float *ws, void *stream) {
+    if (nin <= 0 || nh <= 0 || nout <= 0 || n <= 0 || n > (1LL << 30)) return set_err(FR_ERR_ARG, "invalid sizes");
+    if (!x || !t || !P || !g || !loss || !ws) return set_err(FR_ERR_ARG, "null pointer");
+    return cuda_check(mlp_grad(nin, nh, nout, n, x, t, P, g, loss, ws, (cudaStream_t)stream), "mlp grad");
+}
+
+int fr_mlp_adam(int64_t n, float *P, const float *g, float *m, float *v, int step, float lr, void *stream) {
+    if (n <= 0 || step < 1) return set_err(FR_ERR_ARG, "invalid size or step");
+    if (!P || !g || !m || !v) return set_err(FR_ERR_ARG, "null pointer");
+    return cuda_check(mlp_adam(n, P, g, m, v, step, lr, (cudaStream_t)stream), "mlp adam");
+}
+
+}  // extern "C"

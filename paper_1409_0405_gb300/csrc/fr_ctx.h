@@ -35,6 +35,16 @@ struct DevType {
     void *GUF = nullptr;                     // [nf][3][V][np]
     void *S_t = nullptr, *invJ_t = nullptr, *M0_t = nullptr, *AGRAD_t = nullptr, *ADIV_t = nullptr;
     std::vector<double> xu;  // host: ne x nu x 3 physical solution points
+    // learned closure (off unless cl_on): FP32 parameters of the network
+    // (20 nu -> cl_nh -> cl_nh -> 5 nu), its features/outputs/activations,
+    // and the FP64 field the divergence epilogue adds (Rfs + correction)
+    int cl_on = 0, cl_nh = 0;
+    double cl_scale[5] = {0, 0, 0, 0, 0};  // per conserved variable
+    float *cl_P = nullptr, *cl_X = nullptr, *cl_Y = nullptr, *cl_ws = nullptr;
+    double *cl_add = nullptr;
+    int64_t cl_cap_nh = 0;  // hidden width the buffers were sized for
+    // FR_BF16X3: the packed operators M0, AGRAD, ADIV for the tensor cores
+    fr::TcOperator tc[3];
 };
 
 struct fr_ctx {
@@ -48,6 +58,7 @@ struct fr_ctx {
     int *bt = nullptr, *bf = nullptr, *be = nullptr, *btag = nullptr;
     double *bn = nullptr, *bmag = nullptr;
     double *red = nullptr;  // reduction partials + result
+    int *tc_err = nullptr;  // FR_BF16X3: set by a tensor-core kernel whose bounded wait gave up
     int red_blocks[2] = {0, 0};
     std::vector<void *> allocs;
     // launch accounting: count of kernel launches, and (when profiling is
@@ -57,12 +68,18 @@ struct fr_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
+    // order-transfer matrices (nu_self x nu_from, FP64, device) for one
+    // source order, and the scratch of the closure sample generator
+    int tr_from = 0;
+    double *tr[2] = {nullptr, nullptr};
+    double *smp_u = nullptr, *smp_r = nullptr, *smp_rr = nullptr, *smp_rhi = nullptr;
+    int64_t smp_rhi_cap = 0;
 };
 
 namespace fr {
 namespace api {
 
-enum KClass { K_M0 = 0, K_COMMON_SOL, K_GRAD, K_M0_GRAD, K_FLUX, K_COMMON_FLUX, K_DIV, K_NCLASS };
+enum KClass { K_M0 = 0, K_COMMON_SOL, K_GRAD, K_M0_GRAD, K_FLUX, K_COMMON_FLUX, K_DIV, K_CLOSURE, K_NCLASS };
 
 struct RKStage {
     double c_acc, c_stage;
@@ -71,6 +88,37 @@ struct RKStage {
 
 int set_err(int code, const std::string &msg);
 int cuda_check(cudaError_t e, const char *what);
+// cudaMalloc + zero fill; the context owns (and frees) the memory
+int dev_alloc_bytes(fr_ctx *c, void **p, size_t bytes);
+cudaEvent_t next_event(fr_ctx *c);
+// Launch through `fn` (which issues `nk` kernels), counting the launches
+// and, when profiling, timing them with an event pair on the stream.
+template <class F>
+cudaError_t launch(fr_ctx *c, int kclass, cudaStream_t s, F fn, int nk = 1) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof) {
+        a = next_event(c);
+        b = next_event(c);
+        if (a && b) cudaEventRecord(a, s);
+    }
+    cudaError_t e = fn();
+    c->launches += nk;
+    if (c->prof && a && b) {
+        cudaEventRecord(b, s);
+        c->prof_ev.push_back({kclass, {a, b}});
+    }
+    return e;
+}
+int64_t ndof_of(const fr_ctx *c);
+// FP32 storage (FR_FP32, FR_BF16X3) rather than FP64
+inline bool is_f32(const fr_ctx *c) { return c->prm.precision != FR_FP64; }
+// operator application `which` (0 M0, 1 AGRAD, 2 ADIV) of element type t:
+// the tensor-core kernel in FR_BF16X3, else the FMA kernel
+template <typename T>
+cudaError_t op_gemm(fr_ctx *c, int t, int which, const GemmArgsT<T> &g, cudaStream_t s);
+// FR_FP32 and FR_BF16X3 contexts keep every RHS buffer in float
+template <typename T>
+inline bool type_matches(const fr_ctx *c) { return is_f32(c) == (sizeof(T) == sizeof(float)); }
 Phys phys_of(const fr_ctx *c);
 template <typename T>
 FieldsT<T> fields_of(const fr_ctx *c);
@@ -89,6 +137,17 @@ GemmArgsT<T> args_div(const fr_ctx *c, int t, const RKStage *rk);
 // nsteps RK4 steps on one context (its own launches)
 template <typename T>
 int step_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s);
+// one RHS on public-layout device arrays (FP64 in and out)
+template <typename T>
+int rhs_public(fr_ctx *c, const double *u_dev, double *r_dev, cudaStream_t s);
+// stages 1-4 of the RHS (interpolation and, for Navier-Stokes, the
+// corrected gradient at solution and flux points) on the stage input
+template <typename T>
+int front_stages(fr_ctx *c, T *const in[2], cudaStream_t s);
+// learned closure of type t: features of the stage input, the network,
+// and cl_add = Rfs + scale * output in the internal layout
+template <typename T>
+int closure_apply(fr_ctx *c, int t, const T *in, cudaStream_t s);
 
 }  // namespace api
 }  // namespace fr

@@ -62,6 +62,11 @@ int build_geometry(const fr_mesh *mesh, const RefOps ops[2], TypeGeo geo[2],
 int build_faces(const fr_mesh *mesh, const RefOps ops[2], const TypeGeo geo[2],
                 Faces &faces, std::string &err);
 
+// L2 projection between the spaces of orders p_from and p_to on one
+// reference element, as a matrix (nu_to x nu_from, row-major) on
+// solution-point values.
+int build_transfer(int etype, int p_from, int p_to, std::vector<double> &R, std::string &err);
+
 // Gauss-Legendre nodes and weights on [-1, 1], ascending.
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
 

@@ -9,6 +9,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 namespace fr {
 
 // Epilogues of the operator application C <- A [B1; B2] (Sec. 2.1, Eq. 1).
@@ -70,6 +72,22 @@ cudaError_t configure_gemm_grouped();
 template <typename T>
 cudaError_t launch_gemm_grouped(const GemmArgsT<T> *descs, const int64_t *begin, int ndesc, int64_t total, int mode,
                                 int rc, int maxK, int grid, cudaStream_t s);
+
+// An operator packed for the tensor-core kernel: device image [hi | lo] of
+// bf16 values in K-major core matrices (8 rows x 8 K values, 128 B; per
+// 16-wide K step the Nmma/8 row groups x 2 K halves), rows padded to Nmma
+// (a multiple of 16, <= 256) and columns to Kpad (a multiple of 32).
+struct TcOperator {
+    const uint8_t *img = nullptr;
+    int M = 0, K = 0, Nmma = 0, Kpad = 0;
+};
+// packs a row-major FP64 operator (M x K) into the image layout (host)
+void tc_pack(const double *A, int M, int K, std::vector<uint16_t> &img, int &Nmma, int &Kpad);
+int tc_stages(const TcOperator &op);
+size_t tc_smem_bytes(const TcOperator &op);
+// C <- A [B1; B2] with g's epilogue on the tensor cores; *err (device) is set
+// non-zero if a bounded wait of the kernel gave up
+cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int *err, cudaStream_t s);
 
 struct Phys {
     double gamma, mu, prandtl, beta, tau;

@@ -27,6 +27,7 @@
 //       int g_f v = int_F l_f v dS for all v of the space (l_f the face
 //       Lagrange polynomial of flux point f, dS the reference face measure).
 //   W   integrals of the solution-point Lagrange polynomials.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <map>
@@ -668,5 +669,59 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
     return FR_OK;
 }
 }  // namespace
+
+// Transfer between orders (restriction p_from > p_to, prolongation p_from <
+// p_to) as the L2 projection onto the target space in the reference element.
+// The Dubiner polynomials of order max(p_from, p_to) are mutually orthogonal
+// and each space is spanned by a subset of them (tet: i+j+k <= p; prism:
+// i+j <= p and k <= p), so the projection keeps the modal coefficients the
+// target space shares with the source and drops the rest:
+//   R = V_to[:, shared] (V_from^-1)[shared, :],
+// V the Vandermondes of each space's modes at its own solution points.
+int build_transfer(int etype, int p_from, int p_to, std::vector<double> &out, std::string &err) {
+    RefOps from, to;
+    int rc = build_ref_ops(etype, p_from, from, err);
+    if (rc) return rc;
+    if ((rc = build_ref_ops(etype, p_to, to, err))) return rc;
+    const int pm = std::max(p_from, p_to);
+    Basis B(etype, pm);
+    auto in_space = [etype](const std::array<int, 3> &e, int p) {
+        return etype == FR_ETYPE_TET ? (e[0] + e[1] + e[2] <= p) : (e[0] + e[1] <= p && e[2] <= p);
+    };
+    std::vector<int> mf, mt;  // modes of each space (indices into B)
+    for (int m = 0; m < B.size(); ++m) {
+        if (in_space(B.ex[m], p_from)) mf.push_back(m);
+        if (in_space(B.ex[m], p_to)) mt.push_back(m);
+    }
+    const int nf = from.nu, nt = to.nu;
+    if ((int)mf.size() != nf || (int)mt.size() != nt) {
+        err = "build_transfer: basis size mismatch";
+        return FR_ERR_ARG;
+    }
+    std::vector<R> phi(B.size());
+    Mat Vf(nf, nf);
+    for (int j = 0; j < nf; ++j) {
+        const Vec3 x = {R(from.upts[3 * j]), R(from.upts[3 * j + 1]), R(from.upts[3 * j + 2])};
+        B.eval(x, phi.data(), nullptr);
+        for (int a = 0; a < nf; ++a) Vf(j, a) = phi[mf[a]];
+    }
+    Mat Vfi;
+    if (!solve(Vf, identity(nf), Vfi)) {
+        err = "build_transfer: singular Vandermonde";
+        return FR_ERR_ARG;
+    }
+    out.assign((size_t)nt * nf, 0.0);
+    for (int i = 0; i < nt; ++i) {
+        const Vec3 x = {R(to.upts[3 * i]), R(to.upts[3 * i + 1]), R(to.upts[3 * i + 2])};
+        B.eval(x, phi.data(), nullptr);
+        for (int j = 0; j < nf; ++j) {
+            DD s(0.0);
+            for (int a = 0; a < nf; ++a)
+                if (in_space(B.ex[mf[a]], p_to)) s += phi[mf[a]] * Vfi(a, j);
+            out[(size_t)i * nf + j] = s.to_double();
+        }
+    }
+    return FR_OK;
+}
 
 }  // namespace fr

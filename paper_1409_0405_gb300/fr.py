@@ -25,6 +25,7 @@ FR_ERR_NOMEM = -6
 FR_ERR_UNSUPPORTED = -7
 FR_FP64 = 0
 FR_FP32 = 1
+FR_BF16X3 = 2
 NVARS = 5
 
 OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
@@ -35,8 +36,11 @@ EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_reduce",
            "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
-           "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info")
-KCLASSES = ("M0", "common_solution", "grad", "M0_grad", "flux", "common_flux", "div")
+           "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info",
+           "fr_transfer", "fr_transfer_state", "fr_closure_features", "fr_closure_sample",
+           "fr_closure_set", "fr_mlp_nparams", "fr_mlp_workspace", "fr_mlp_forward", "fr_mlp_grad",
+           "fr_mlp_adam")
+KCLASSES = ("M0", "common_solution", "grad", "M0_grad", "flux", "common_flux", "div", "closure")
 
 
 class FRMesh(C.Structure):
@@ -101,6 +105,21 @@ def load():
     lib.fr_batch_info.argtypes = [vp, i64p]
     for name in ("fr_batch_create", "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info"):
         getattr(lib, name).restype = C.c_int
+    lib.fr_transfer.argtypes = [C.c_int, C.c_int, C.c_int, dp, i64p, i64p]
+    lib.fr_transfer_state.argtypes = [vp, vp, vp, vp, vp]
+    lib.fr_closure_features.argtypes = [vp, vp, C.c_int, vp, vp]
+    lib.fr_closure_sample.argtypes = [vp, vp, vp, vp, C.c_int, dp, vp, vp, vp, vp]
+    lib.fr_closure_set.argtypes = [vp, C.c_int, vp, C.c_int, dp]
+    lib.fr_mlp_nparams.argtypes = [C.c_int, C.c_int, C.c_int]
+    lib.fr_mlp_nparams.restype = C.c_int64
+    lib.fr_mlp_workspace.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64]
+    lib.fr_mlp_workspace.restype = C.c_int64
+    lib.fr_mlp_forward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, vp, vp, vp, vp, vp]
+    lib.fr_mlp_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+    lib.fr_mlp_adam.argtypes = [C.c_int64, vp, vp, vp, vp, C.c_int, C.c_float, vp]
+    for name in ("fr_transfer", "fr_transfer_state", "fr_closure_features", "fr_closure_sample",
+                 "fr_closure_set", "fr_mlp_forward", "fr_mlp_grad", "fr_mlp_adam"):
+        getattr(lib, name).restype = C.c_int
     lib.fr_strerror.argtypes = [C.c_int]
     lib.fr_strerror.restype = C.c_char_p
     lib.fr_last_error.argtypes = []
@@ -111,6 +130,10 @@ def load():
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
+
+
+def _etype(e):
+    return {"tet": 0, "pri": 1}.get(e, e)
 
 
 def _check(rc):
@@ -133,6 +156,45 @@ def operator(etype, order, which):
     out = np.empty((rows.value, cols.value), dtype=np.float64)
     _check(lib.fr_operator(et, order, wid, _dptr(out), C.byref(rows), C.byref(cols)))
     return out
+
+
+def transfer(etype, p_from, p_to):
+    """Host-only order-transfer matrix (nu(p_to) x nu(p_from)), float64."""
+    lib = load()
+    rows, cols = C.c_int64(), C.c_int64()
+    et = {"tet": 0, "pri": 1}.get(etype, etype)
+    _check(lib.fr_transfer(et, int(p_from), int(p_to), None, C.byref(rows), C.byref(cols)))
+    out = np.empty((rows.value, cols.value), dtype=np.float64)
+    _check(lib.fr_transfer(et, int(p_from), int(p_to), _dptr(out), C.byref(rows), C.byref(cols)))
+    return out
+
+
+def _sp(stream):
+    return C.c_void_p(stream) if stream else None
+
+
+def mlp_nparams(nin, nh, nout):
+    return int(load().fr_mlp_nparams(int(nin), int(nh), int(nout)))
+
+
+def mlp_workspace(nin, nh, nout, n):
+    return int(load().fr_mlp_workspace(int(nin), int(nh), int(nout), int(n)))
+
+
+def mlp_forward(nin, nh, nout, n, x_ptr, p_ptr, y_ptr, ws_ptr, stream=None):
+    _check(load().fr_mlp_forward(int(nin), int(nh), int(nout), int(n), C.c_void_p(x_ptr), C.c_void_p(p_ptr),
+                                 C.c_void_p(y_ptr), C.c_void_p(ws_ptr), _sp(stream)))
+
+
+def mlp_grad(nin, nh, nout, n, x_ptr, t_ptr, p_ptr, g_ptr, loss_ptr, ws_ptr, stream=None):
+    _check(load().fr_mlp_grad(int(nin), int(nh), int(nout), int(n), C.c_void_p(x_ptr), C.c_void_p(t_ptr),
+                              C.c_void_p(p_ptr), C.c_void_p(g_ptr), C.c_void_p(loss_ptr), C.c_void_p(ws_ptr),
+                              _sp(stream)))
+
+
+def mlp_adam(nparams, p_ptr, g_ptr, m_ptr, v_ptr, step, lr, stream=None):
+    _check(load().fr_mlp_adam(int(nparams), C.c_void_p(p_ptr), C.c_void_p(g_ptr), C.c_void_p(m_ptr),
+                              C.c_void_p(v_ptr), int(step), float(lr), _sp(stream)))
 
 
 def peak_fp64(stream=None):
@@ -283,6 +345,42 @@ class Context:
         _check(self._lib.fr_profile_read(self._h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
                                          C.byref(tot)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KCLASSES)}, tot.value
+
+    # -- learned closure (device pointers are ints) --------------------------------
+    def nu(self, etype):
+        return self.info["nu_tet" if etype in (0, "tet") else "nu_pri"]
+
+    def ne(self, etype):
+        return self.info["n_tet" if etype in (0, "tet") else "n_pri"]
+
+    def transfer_from(self, other, u_ptr, out_ptr, stream=None):
+        """out (this context's order) = transfer of u (other's order)."""
+        _check(self._lib.fr_transfer_state(other._h, self._h, C.c_void_p(u_ptr), C.c_void_p(out_ptr),
+                                           _sp(stream)))
+
+    def closure_features(self, u_ptr, etype, x_ptr, stream=None):
+        _check(self._lib.fr_closure_features(self._h, C.c_void_p(u_ptr), _etype(etype), C.c_void_p(x_ptr),
+                                             _sp(stream)))
+
+    def closure_sample(self, hi, u_hi_ptr, etype, inv_scale=None, x_ptr=None, t_ptr=None, ss_ptr=None,
+                       u_lo_ptr=None, stream=None):
+        """Features/targets of this (low-order) context from hi's state
+        (targets against the RHS of u_lo, or of the projection of u_hi)."""
+        isc = None if inv_scale is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(inv_scale, dtype=np.float64), (NVARS,)))
+        _check(self._lib.fr_closure_sample(hi._h, self._h, C.c_void_p(u_hi_ptr),
+                                           C.c_void_p(u_lo_ptr) if u_lo_ptr else None, _etype(etype),
+                                           _dptr(isc) if isc is not None else None,
+                                           C.c_void_p(x_ptr) if x_ptr else None,
+                                           C.c_void_p(t_ptr) if t_ptr else None,
+                                           C.c_void_p(ss_ptr) if ss_ptr else None, _sp(stream)))
+
+    def closure_set(self, etype, params_ptr, nh=128, out_scale=1.0):
+        """Attach (params_ptr: device FP32) or detach (None) a network;
+        out_scale: one value or one per conserved variable."""
+        sc = np.ascontiguousarray(np.broadcast_to(np.asarray(out_scale, dtype=np.float64), (NVARS,)))
+        _check(self._lib.fr_closure_set(self._h, _etype(etype), C.c_void_p(params_ptr) if params_ptr else None,
+                                        int(nh), _dptr(sc)))
 
     def reduce(self, stream=None, check=True):
         out = np.empty(7, dtype=np.float64)

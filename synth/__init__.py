@@ -2,7 +2,8 @@
 
 This package generates meshes (node coordinates, element connectivity,
 boundary-face tags, periodic translations) and closed-form initial
-conditions evaluated at caller-supplied coordinates.  It holds none of the
+conditions evaluated at caller-supplied coordinates, and seeded initial
+network weights.  It holds none of the
 flux-reconstruction arithmetic: no solution/flux points, no operators, no
 geometry factors, no face matching.  Both implementations compute those on
 their own from what this package returns.
@@ -16,3 +17,4 @@ from .ics import (  # noqa: F401
     isentropic_vortex, taylor_green, perturbed_freestream, uniform_state,
     random_smooth_state,
 )
+from .weights import mlp_init  # noqa: F401

@@ -1,0 +1,104 @@
+"""GPU tests of the FR_BF16X3 mode: the operator applications on the
+tensor cores (tcgen05, split BF16 with FP32 accumulation) against the FP64
+oracle and against the FR_FP32 mode, over both element types, orders 1-4,
+Euler and Navier-Stokes, ragged column tiles, the fused RK epilogue and
+the full-size boundary-layer RHS."""
+import numpy as np
+import pytest
+
+import synth
+from tests import _cases
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# split BF16 keeps ~16 bits of each operand; with the operators' cancellation
+# the RHS error is a few 1e-5 of its scale (measured); a layout or epilogue
+# mistake gives O(1)
+TC_RHS_TOL = 5e-4
+
+
+def _fr():
+    _cases.library()
+    from paper_1409_0405_gb300 import fr
+    return fr
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_tc_rhs_matches_oracle(p, viscous):
+    fr = _fr()
+    mesh = synth.vortex_box(n=4, jitter=0.05, seed=0)
+    prm = dict(viscous=viscous, mu=0.01 if viscous else 0.0, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0)
+    sol, ctx = _cases.make_pair(mesh, p, precision=fr.FR_BF16X3, **prm)
+    _, c32 = _cases.make_pair(mesh, p, precision=fr.FR_FP32, **prm)
+    u = _cases.state(sol, "vortex")
+    ref = sol.rhs(u)
+    got = _cases.gpu_rhs(ctx, u)
+    err = _cases.per_quantity_rel_err(sol, ref, got)
+    e32 = _cases.per_quantity_rel_err(sol, ref, _cases.gpu_rhs(c32, u))
+    print(p, viscous, "bf16x3", err, "fp32", e32)
+    assert np.all(err < TC_RHS_TOL), err
+    ctx.reduce(check=False)   # raises FR_ERR_TIMEOUT if a bounded wait of a kernel gave up
+
+
+@pytest.mark.parametrize("etypes", ["tet", "pri"])
+def test_tc_single_type_ragged(etypes):
+    """One element type only, element counts that leave a ragged last tile."""
+    fr = _fr()
+    coords = [np.linspace(-5, 5, 4), np.linspace(-5, 5, 3), np.linspace(-5, 5, 4)]
+    mesh = synth.layered_box(coords, 2, 3 if etypes == "pri" else 0, (True, True, True), jitter=0.05, seed=4)
+    prm = dict(viscous=True, mu=0.01, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0)
+    sol, ctx = _cases.make_pair(mesh, 3, precision=fr.FR_BF16X3, **prm)
+    u = _cases.state(sol, "vortex")
+    err = _cases.per_quantity_rel_err(sol, sol.rhs(u), _cases.gpu_rhs(ctx, u))
+    assert np.all(err < TC_RHS_TOL), err
+
+
+def test_tc_rk_step_matches_fp32_mode():
+    """The fused RK epilogue: one RK4 step in FR_BF16X3 against FR_FP32."""
+    fr = _fr()
+    mesh = synth.vortex_box(n=4, jitter=0.05, seed=0)
+    prm = dict(viscous=True, mu=0.01, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0)
+    sol, c16 = _cases.make_pair(mesh, 4, precision=fr.FR_BF16X3, **prm)
+    _, c32 = _cases.make_pair(mesh, 4, precision=fr.FR_FP32, **prm)
+    u = _cases.state(sol, "vortex")
+    dt = sol.dt_cfl(u, 0.1)
+    ref = sol.rk4_step(u, dt)
+    out = {}
+    for name, c in (("bf16x3", c16), ("fp32", c32)):
+        c.set_state(u)
+        c.step(dt, 1)
+        out[name] = c.get_state()
+    inc = ref - u
+    for name, got in out.items():
+        err = _cases.per_quantity_rel_err(sol, inc, got - u)
+        print(name, err)
+        assert np.all(err < 5e-3), (name, err)
+
+
+def test_tc_full_size_boundary_layer():
+    """The benchmark workload (42.4 M DOF, p=4 NS with walls and far field):
+    FR_BF16X3 RHS against the FR_FP64 RHS of the library (which matches the
+    FP64 oracle to 1e-12)."""
+    fr = _fr()
+    mesh = synth.boundary_layer_box()
+    prm = _cases.bl_params()
+    c64 = fr.Context(mesh, 4, **prm)
+    c16 = fr.Context(mesh, 4, precision=fr.FR_BF16X3, **prm)
+    xyz = c64.upts_points()
+    q = synth.perturbed_freestream(xyz, seed=2, wall_delta=_cases.BL_DELTA)
+    counts = [(c64.info["n_tet"], c64.info["nu_tet"]), (c64.info["n_pri"], c64.info["nu_pri"])]
+    out, off = [], 0
+    for ne, nu in counts:
+        out.append(q[off:off + ne * nu].reshape(ne, nu, 5).transpose(0, 2, 1).reshape(-1))
+        off += ne * nu
+    u = torch.from_numpy(np.concatenate(out)).cuda()
+    r64, r16 = torch.empty_like(u), torch.empty_like(u)
+    c64.rhs(u.data_ptr(), r64.data_ptr())
+    c16.rhs(u.data_ptr(), r16.data_ptr())
+    torch.cuda.synchronize()
+    d = (r16 - r64).abs().max().item() / r64.abs().max().item()
+    print("full-size bf16x3 rel err", d)
+    assert d < TC_RHS_TOL
+    c16.reduce(check=False)

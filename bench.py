@@ -107,6 +107,31 @@ def gemm_flops(ctx, kclass):
     return tot
 
 
+def gemm_bytes_f32(ctx, kclass):
+    """Algorithmic DRAM bytes of one launch class (both element types) per
+    RHS in the FP32-storage modes (4-byte state): operator input and output
+    once, plus the epilogue's own reads and writes: the geometry S^T/J for
+    the gradient (10 floats per point), and for the divergence with the
+    fused RK update (an RK step's average stage) 1/J, the FP64 reference
+    term, the FP64 registers read (12 B) and written (12 B incl. the float
+    stage input)."""
+    i = ctx.info
+    tot = 0.0
+    for ne, nu, nf in ((i["n_tet"], i["nu_tet"], i["nf_tet"]), (i["n_pri"], i["nu_pri"], i["nf_pri"])):
+        if ne == 0:
+            continue
+        cols = 5.0 * ne
+        if kclass == "M0":
+            tot += 4.0 * cols * (nu + nf)
+        elif kclass == "grad":
+            tot += 4.0 * cols * (nu + nf) + 4.0 * cols * 3 * nu + 4.0 * ne * nu * 10
+        elif kclass == "M0_grad":
+            tot += 4.0 * 3 * cols * (nu + nf)
+        elif kclass == "div":
+            tot += 4.0 * cols * (3 * nu + nf) + 4.0 * ne * nu + cols * nu * (8 + 12 + 12)
+    return tot
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -245,12 +270,15 @@ def precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, precision, args, sp):
     torch.cuda.synchronize()
     stream = torch.cuda.ExternalStream(sp)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
     e0.record(stream)
     for _ in range(args.steps):
         ctx.step(dt, 1, sp)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    classes, launches = ctx.profile_read()
+    ctx.profile(False)
     # errors: one RHS, and the increment of one RK4 step, against FP64
     ud = torch.from_numpy(u0).cuda()
     r64, r32 = torch.empty_like(ud), torch.empty_like(ud)
@@ -265,11 +293,25 @@ def precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, precision, args, sp):
     ctx.step(dt, 1, sp)
     s32 = ctx.get_state(stream=sp)
     inc_err = per_quantity_rel_err(s64 - u0, s32 - u0, counts)
+    out = {"value": ctx64.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+           "kernel_ms_per_step": {k: v[0] / args.steps for k, v in classes.items()},
+           "gpu_launches": int(launches),
+           "rhs_rel_err_vs_fp64": rhs_err, "step_increment_rel_err_vs_fp64": inc_err,
+           "error_measure": "[mass, momentum vector, energy] max|d|/max|ref|; the FP64 path matches the "
+                            "FP64 oracle to 1e-12"}
+    gemm = ("M0", "grad", "M0_grad", "div")
+    dom = max(gemm, key=lambda k: classes[k][0])
+    byts = gemm_bytes_f32(ctx, dom) * 4 * args.steps
+    ach = byts / (classes[dom][0] * 1e-3) / 1e9
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    out["roofline"] = {"bound": "hbm", "kernel": ("k_gemm_tc" if precision == fr.FR_BF16X3 else "k_gemm")
+                       + f" ({dom})", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "traffic": None, "launches": classes[dom][1],
+                       "avg_launch_ms": classes[dom][0] / max(classes[dom][1], 1),
+                       "bytes": "operator input + output once, epilogue geometry/registers (bench.gemm_bytes_f32)",
+                       "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     ctx.close()
-    return {"value": ctx64.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
-            "rhs_rel_err_vs_fp64": rhs_err, "step_increment_rel_err_vs_fp64": inc_err,
-            "error_measure": "[mass, momentum vector, energy] max|d|/max|ref|; the FP64 path matches the "
-                             "FP64 oracle to 1e-12"}
+    return out
 
 
 def batch_mode(fr, torch, args, sp):
@@ -512,7 +554,9 @@ def main():
     ap.add_argument("--nx", type=int, default=75,
                     help="cells along x (75 = the full workload; smaller for profiling)")
     ap.add_argument("--cpu-oracle-child", type=int, default=0)
-    ap.add_argument("--fp64-only", action="store_true", help="skip the other precision modes")
+    ap.add_argument("--fp64-only", action="store_true", help="skip the other modes (precision, batched, learned)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3"],
+                    help="arithmetic of the main timed step (default fp64, the headline workload)")
     args = ap.parse_args()
 
     if args.cpu_oracle_child:
@@ -566,7 +610,8 @@ def main():
             torch.distributed.barrier()
 
     mesh = synth.boundary_layer_box(nx=args.nx)
-    ctx = fr.Context(mesh, ORDER, **flow_params())
+    prec = {"fp64": fr.FR_FP64, "fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3}[args.precision]
+    ctx = fr.Context(mesh, ORDER, **flow_params(), precision=prec)
     counts = [(ctx.info["n_tet"], ctx.info["nu_tet"]), (ctx.info["n_pri"], ctx.info["nu_pri"])]
     u0 = points_to_public(synth.perturbed_freestream(ctx.upts_points(), seed=2,
                                                      wall_delta=WALL_DELTA), counts)
@@ -629,8 +674,9 @@ def main():
 
     # --- other precision modes beside the FP64 line (same mesh, same state) ---
     modes = {}
-    if not args.fp64_only:
+    if not args.fp64_only and args.precision == "fp64":
         modes["fp32"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_FP32, args, sp)
+        modes["bf16x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_BF16X3, args, sp)
         if args.nx == 75:
             modes["batched"] = batch_mode(fr, torch, args, sp)
             modes["learned"] = learned_mode(fr, torch, args, sp)
@@ -649,7 +695,15 @@ def main():
         fp64_peak_meas = fr.peak_fp64(sp)
     except Exception:
         fp64_peak_meas = None
-    if dom in ("M0", "grad", "M0_grad", "div"):
+    if dom in ("M0", "grad", "M0_grad", "div") and prec != fr.FR_FP64:
+        byts = gemm_bytes_f32(ctx, dom) * 4 * args.steps
+        achieved = byts / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                "kernel": ("k_gemm_tc" if prec == fr.FR_BF16X3 else "k_gemm") + f" ({dom})", "launches": dom_n,
+                "avg_launch_ms": dom_ms / max(dom_n, 1),
+                "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    elif dom in ("M0", "grad", "M0_grad", "div"):
         flops = gemm_flops(ctx, dom) * 4 * args.steps  # per RHS x 4 RHS per step
         achieved = flops / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": fp64_peak_derived / 1e3,
@@ -667,8 +721,10 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.nx == 75 else WORKLOAD + f" (reduced: nx={args.nx})",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3+f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": (WORKLOAD if args.nx == 75 else WORKLOAD + f" (reduced: nx={args.nx})")
+                   + ("" if args.precision == "fp64" else f" [{args.precision} arithmetic]"),
                    "ndof": ndof, "rhs_per_step": 4, "dt": dt,
                    "l2": "inputs > L2 (state 339 MB per register, scratch > 4 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

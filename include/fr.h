@@ -89,8 +89,9 @@ typedef struct {
     double ldg_tau;   /* LDG penalty on the normal flux */
     int viscous;      /* 0: Euler, 1: Navier-Stokes */
     int precision;    /* FR_FP64, or FR_FP32: operator applications and point-wise
-                         work in FP32; RK registers, the reference-flux
-                         correction and the reductions stay FP64; or
+                         work in FP32; RK registers and the reductions stay
+                         FP64 (the FP64 reference-flux correction, ~1e-11,
+                         is below FP32 resolution and skipped); or
                          FR_BF16X3: as FR_FP32 with the operator applications
                          on the tensor cores (split BF16, FP32 accumulate) */
     double rho_inf;   /* far-field density */

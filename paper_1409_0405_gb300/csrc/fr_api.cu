@@ -214,6 +214,7 @@ GemmArgsT<T> args_m0grad(const fr_ctx *c, int t) {
     h.ldb1 = h.N;
     h.C = (T *)D.GUF;
     h.ldc = h.N;
+    h.np = D.np;  // element stride of the columns (15 blocks of np)
     h.mode = GEMM_STORE;
     return h;
 }
@@ -331,14 +332,28 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
         return rc;
     // 7. divergence plus correction; with the learned closure on, the
     // network's correction is added by the epilogue with the reference term
+    // In FR_BF16X3 the tensor-core GEMM stores R and a streaming pass applies
+    // the RK update (its FP64 register traffic would otherwise stall the
+    // GEMM's epilogue warps).
+    const bool split_rk = rk && c->prm.precision == FR_BF16X3;
     for (int t = 0; t < 2; ++t) {
-        if (!c->T[t].present) continue;
-        GemmArgsT<T> g = args_div<T>(c, t, rk);
-        if (c->T[t].cl_on) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        GemmArgsT<T> g = args_div<T>(c, t, split_rk ? nullptr : rk);
+        if (D.cl_on) {
             if ((rc = closure_apply<T>(c, t, in[t], s))) return rc;
-            g.rfs = c->T[t].cl_add;
+            g.rfs = D.cl_add;
         }
         if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return op_gemm<T>(c, t, 2, g, s); }), "gemm div"))) return rc;
+        if (split_rk &&
+            (rc = cuda_check(launch(c, K_DIV, s,
+                                    [&] {
+                                        return launch_rk_update<T>(D.nu, D.np, (const T *)D.R, D.U, D.Uacc, (T *)D.Us,
+                                                                   ph.uref, rk->c_acc, rk->c_stage, rk->first,
+                                                                   rk->last, s);
+                                    }),
+                             "RK update")))
+            return rc;
     }
     return FR_OK;
 }
@@ -424,13 +439,13 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         if (prm->precision == FR_BF16X3) {
             // the three operators packed for the tensor cores
             const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
-            const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok[3] = {D.nu, D.nu + D.nf, 3 * D.nu + D.nf};
+            const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok1[3] = {D.nu, D.nu, 3 * D.nu}, ok2[3] = {0, D.nf, D.nf};
             for (int w = 0; w < 3; ++w) {
                 std::vector<uint16_t> img;
                 TcOperator &op = D.tc[w];
-                tc_pack(opv[w]->data(), om[w], ok[w], img, op.Nmma, op.Kpad);
+                tc_pack(opv[w]->data(), om[w], ok1[w], ok2[w], img, op.Nmma, op.K1pad, op.Kpad);
                 op.M = om[w];
-                op.K = ok[w];
+                op.K = ok1[w] + ok2[w];
                 if (op.Nmma > 256 || tc_stages(op) < 2)
                     return set_err(FR_ERR_UNSUPPORTED, "operator too large for the tensor-core kernel");
                 uint16_t *dimg = nullptr;
@@ -470,9 +485,10 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
     // the discrete divergence of the constant reference flux (zero with exact
     // geometry; ~1e-11 with the geometric factors rounded), evaluated once in
     // FP64 and added back to every RHS since the flux kernels subtract that
-    // flux.  FP64 scratch: the RHS buffers themselves in FR_FP64, temporary
-    // buffers in FR_FP32.
-    {
+    // flux.  Only FR_FP64 needs it: in the FP32-storage modes it lies far
+    // below the arithmetic's resolution (the RHS carries ~1e-6 relative
+    // rounding), so they skip it and its 8 bytes per output.
+    if (prm->precision == FR_FP64) {
         const Phys ph = phys_of(c);
         const bool f32 = prm->precision != FR_FP64;
         double *tFT[2] = {nullptr, nullptr}, *tFC[2] = {nullptr, nullptr};

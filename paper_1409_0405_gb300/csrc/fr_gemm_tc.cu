@@ -18,16 +18,26 @@
 //   operator image  [hi | lo], per 16-wide K step: Nmma/8 row groups x
 //                   2 K halves x 128 B  (LBO = 128 B, SBO = 256 B); loaded
 //                   once per CTA by a bulk copy (TMA engine) and kept;
-//   state stages    ring of nst stages of 32 K-values: [hi k0..15 | hi
-//                   k16..31 | lo k0..15 | lo k16..31], each 128 rows x 16 K
-//                   (4 KB, same LBO/SBO), written by the converter warps
-//                   from coalesced FP32 loads of B.
-// Warp roles (13 warps): 0-7 converters, 8-11 epilogue (TMEM lane quarter =
-// warp % 4), 12 TMEM allocation, operator load and the single MMA-issuing
-// thread.  Hand-offs use mbarriers; the MMA side signals with
-// tcgen05.commit.  Every wait is bounded: on expiry the CTA records an error
-// code, all roles leave their loops, and TMEM is freed after the last
-// commit has landed.
+//   slot ring       D slots of 8 KB, one per stage of 16 K values.  A slot
+//                   first receives the stage's FP32 state rows (a 16 x 128
+//                   box, one 2-D tensor-map TMA load issued by the producer:
+//                   the TMA engine writes shared memory directly, so the
+//                   loads in flight are bounded by the ring, not by the L1
+//                   left over beside the shared memory; rows past the end
+//                   of B1 or B2 are filled with zeros by the TMA unit);
+//                   the converter warps read their column, meet at a named
+//                   barrier, and overwrite the slot with the stage's bf16 hi
+//                   and lo core matrices [hi | lo] (4 KB each, LBO/SBO as
+//                   above), which the MMA reads; its commit frees the slot
+//                   for the next load.
+// Warp roles (22 warps): 0-7 converters, 8-19 epilogue (TMEM lane quarter =
+// warp % 4; the three warps of a quarter take every third 24-row group), 20
+// TMEM allocation, operator load and the single MMA-issuing thread, 21 the
+// producer of the state loads (one thread).  Hand-offs use mbarriers; the MMA side
+// signals with tcgen05.commit.  Every wait is bounded: on expiry the CTA
+// records an error code, all roles leave their loops, and TMEM is freed
+// after the last commit has landed.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -39,19 +49,24 @@ namespace fr {
 namespace {
 
 constexpr int kTileN = 128;         // state columns per tile (MMA M)
-constexpr int kStageK = 32;         // K values per stage (two MMA K steps)
-constexpr int kStageBytes = 16384;  // 128 x 32 x (hi + lo) x 2 B
-constexpr int kConvWarps = 8, kEpiWarps = 4;
-constexpr int kThreads = (kConvWarps + kEpiWarps + 1) * 32;
+constexpr int kStageK = 16;        // K values per stage (one MMA K step)
+constexpr int kStageBytes = 8192;  // 128 x 16 x 4 B (FP32), later 128 x 16 x (hi + lo) x 2 B
+constexpr int kConvWarps = 8, kEpiWarps = 12;  // epilogue: three warps per TMEM lane quarter
+constexpr int kMmaWarp = kConvWarps + kEpiWarps, kProdWarp = kMmaWarp + 1;
+constexpr int kThreads = (kConvWarps + kEpiWarps + 2) * 32;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+constexpr int kMaxSlots = 12;
 
 struct Bars {
     uint64_t op_full;
     uint64_t done;
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
-    uint64_t full[8];
-    uint64_t empty[8];
+    uint64_t loaded[kMaxSlots];     // producer's copies of a slot landed (tx)
+    uint64_t read[kMaxSlots];       // every converter has read the slot's FP32 rows
+    uint64_t converted[kMaxSlots];  // converters wrote the slot's bf16 tiles
+    uint64_t freed[kMaxSlots];      // the MMAs reading the slot completed
     uint32_t tmem_base;
     int abort;
 };
@@ -140,47 +155,119 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// epilogue of one operator row j of state column n (see gemm_block in
-// fr_gemm.cu for the FP32/FP64 form of the same arithmetic)
+// Epilogue of rows [c0, c0 + 24) of state column n (element e), the
+// accumulators in v.  The same arithmetic as gemm_block in fr_gemm.cu; here
+// every load of a group is issued before its first store (C may alias
+// nothing the group reads, but the compiler cannot know), so one thread
+// keeps several loads in flight instead of one row's worth.
 template <int MODE>
-__device__ __forceinline__ void epi_row(const GemmArgsT<float> &g, int j, int64_t n, float acc) {
-    const int64_t idx = (int64_t)j * g.ldc + n;
+__device__ __forceinline__ void epi_group(const GemmArgsT<float> &g, int c0, int64_t n, int64_t e, const float *v) {
     if (MODE == GEMM_STORE) {
-        g.C[idx] = acc + (g.add_ref ? (float)g.uref[n / g.np] : 0.f);
+        const float add = g.add_ref ? (float)g.uref[n / g.np] : 0.f;
+#pragma unroll
+        for (int t = 0; t < 24; ++t)
+            if (c0 + t < g.M) g.C[(int64_t)(c0 + t) * g.ldc + n] = v[t] + add;
+    } else if (MODE == GEMM_GRAD) {
+        // rows (j, d), d fastest: 8 points per group, two at a time
+#pragma unroll
+        for (int t0 = 0; t0 < 8; t0 += 2) {
+            float sv[2][9], ij[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int j = c0 / 3 + t0 + t;
+                if (3 * j < g.M) {
+                    const float *S = g.S + (int64_t)j * 9 * g.np + e;
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) sv[t][q] = __ldg(S + (int64_t)q * g.np);
+                    ij[t] = __ldg(g.invJ + (int64_t)j * g.np + e);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int j = c0 / 3 + t0 + t;
+                if (3 * j < g.M) {
+                    const float g0 = v[3 * (t0 + t)], g1 = v[3 * (t0 + t) + 1], g2 = v[3 * (t0 + t) + 2];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        g.C[(int64_t)(3 * j + m) * g.ldc + n] =
+                            ij[t] * (sv[t][m] * g0 + sv[t][3 + m] * g1 + sv[t][6 + m] * g2);
+                }
+            }
+        }
     } else {
-        const int64_t e = n % g.np;
-        const float rt = -g.invJ[(int64_t)j * g.np + e] * acc;
-        if (MODE == GEMM_DIV) {
-            g.C[idx] = g.rfs ? (float)((double)rt + g.rfs[idx]) : rt;
-        } else {
-            const double ur = g.uref[n / g.np];
-            const double rv = (double)rt + (g.rfs ? g.rfs[idx] : 0.0);
-            const double u = g.U[idx];
-            if (g.rk_last) {
-                const double un = g.Uacc[idx] + g.c_acc * rv;
-                g.U[idx] = un;
-                g.Us[idx] = (float)(un - ur);
-            } else {
-                g.Uacc[idx] = (g.rk_first ? u : g.Uacc[idx]) + g.c_acc * rv;
-                g.Us[idx] = (float)((u - ur) + g.c_stage * rv);
+        // DIV / DIV_RK in sub-groups of RG rows
+        constexpr int RG = MODE == GEMM_DIV_RK ? 4 : 8;
+        const double ur = (MODE == GEMM_DIV_RK) ? g.uref[n / g.np] : 0.0;
+#pragma unroll
+        for (int r0 = 0; r0 < 24; r0 += RG) {
+            float ij[RG];
+            double rf[RG], uu[RG], ua[RG];
+#pragma unroll
+            for (int i = 0; i < RG; ++i) {
+                const int j = c0 + r0 + i;
+                if (j < g.M) {
+                    const int64_t idx = (int64_t)j * g.ldc + n;
+                    ij[i] = __ldg(g.invJ + (int64_t)j * g.np + e);
+                    rf[i] = g.rfs ? __ldg(g.rfs + idx) : 0.0;
+                    if (MODE == GEMM_DIV_RK) {
+                        uu[i] = g.rk_last ? 0.0 : g.U[idx];
+                        ua[i] = (g.rk_last || !g.rk_first) ? g.Uacc[idx] : 0.0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RG; ++i) {
+                const int j = c0 + r0 + i;
+                if (j < g.M) {
+                    const int64_t idx = (int64_t)j * g.ldc + n;
+                    const float rt = -ij[i] * v[r0 + i];
+                    if (MODE == GEMM_DIV) {
+                        g.C[idx] = g.rfs ? (float)((double)rt + rf[i]) : rt;
+                    } else {
+                        const double rv = (double)rt + rf[i];
+                        if (g.rk_last) {
+                            const double un = ua[i] + g.c_acc * rv;
+                            g.U[idx] = un;
+                            g.Us[idx] = (float)(un - ur);
+                        } else {
+                            g.Uacc[idx] = (g.rk_first ? uu[i] : ua[i]) + g.c_acc * rv;
+                            g.Us[idx] = (float)((uu[i] - ur) + g.c_stage * rv);
+                        }
+                    }
+                }
             }
         }
     }
 }
 
+// Tile t covers columns [n0, n1) of one variable block (N = nvb np columns,
+// block b = columns [b np, (b+1) np)): the variable block runs fastest, so
+// the nvb tiles of one element range are processed together and share the
+// geometry factors through L2.
+struct TileMap {
+    int64_t np, ept;  // elements per block, tiles per block
+    int nvb;
+    __device__ __forceinline__ void cols(int64_t t, int64_t &n0, int64_t &n1) const {
+        const int64_t eb = t / nvb, vb = t % nvb;
+        n0 = vb * np + eb * kTileN;
+        const int64_t lim = (vb + 1) * np;
+        n1 = n0 + kTileN < lim ? n0 + kTileN : lim;
+    }
+};
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const GemmArgsT<float> g, const uint8_t *__restrict__ opimg, int Nmma, int Kpad, int nst,
-              uint32_t tmem_cols, int *err) {
+    k_gemm_tc(const GemmArgsT<float> g, const TileMap tm, const __grid_constant__ CUtensorMap tmB1,
+              const __grid_constant__ CUtensorMap tmB2, const uint8_t *__restrict__ opimg, int Nmma, int K1pad,
+              int Kpad, int nslot, uint32_t tmem_cols, int *err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint32_t op_half = (uint32_t)Nmma * (uint32_t)Kpad * 2u;  // bytes of hi (or lo)
     const uint32_t op_bytes = 2u * op_half;
-    uint8_t *stages = smem + op_bytes;
-    Bars *bars = reinterpret_cast<Bars *>(stages + (size_t)nst * kStageBytes);
+    uint8_t *slots = smem + op_bytes;
+    Bars *bars = reinterpret_cast<Bars *>(slots + (size_t)nslot * kStageBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = (g.N + kTileN - 1) / kTileN;
+    const int64_t ntiles = tm.ept * tm.nvb;
     const int nkst = Kpad / kStageK;
-    const int K = g.K1 + g.K2;
 
     if (threadIdx.x == 0) {
         mbar_init(&bars->op_full, 1);
@@ -189,15 +276,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&bars->acc_full[b], 1);
             mbar_init(&bars->acc_empty[b], kEpiWarps * 32);
         }
-        for (int s = 0; s < nst; ++s) {
-            mbar_init(&bars->full[s], kConvWarps * 32);
-            mbar_init(&bars->empty[s], 1);
+        for (int q = 0; q < nslot; ++q) {
+            mbar_init(&bars->loaded[q], 1);
+            mbar_init(&bars->read[q], kConvWarps * 32);
+            mbar_init(&bars->converted[q], kConvWarps * 32);
+            mbar_init(&bars->freed[q], 1);
         }
         bars->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
-    if (warp == kConvWarps + kEpiWarps) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&bars->tmem_base)),
                      "r"(tmem_cols)
@@ -210,92 +299,73 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = bars->tmem_base;
     const uint32_t acc_stride = tmem_cols / 2;
 
+    // stages this CTA runs (tiles blockIdx.x, + gridDim.x, ...; nkst each)
+    const int64_t nmine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total = nmine * nkst;
+    auto stage_cols = [&](int64_t idx, int64_t &n0, int64_t &n1) {
+        tm.cols(blockIdx.x + (idx / nkst) * gridDim.x, n0, n1);
+    };
+
     if (warp < kConvWarps) {
-        // ---- converters: thread (r, h) fills row r, K half h of each stage
+        // ---- converters: thread (r, h) converts column r, K half h (8
+        // values) of each stage: read them from the slot, wait for every
+        // converter to have read, write the bf16 hi/lo of its core-matrix row
         const int r = threadIdx.x & (kTileN - 1), h = threadIdx.x >> 7;
-        int s = 0;
-        uint32_t ph = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int64_t n = tile * kTileN + r;
-            const bool col_ok = n < g.N;
-            for (int ks = 0; ks < nkst; ++ks) {
-                float v[16];
-                const int k0 = ks * kStageK + h * 16;
+        for (int64_t idx = 0; idx < total; ++idx) {
+            const int q = (int)(idx % nslot);
+            const uint32_t par = (uint32_t)((idx / nslot) & 1);
+            if (!mbar_wait(&bars->loaded[q], par, bars, err, 1)) break;
+            int64_t n0, n1;
+            stage_cols(idx, n0, n1);
+            const bool col_ok = n0 + r < n1;
+            uint8_t *slot = slots + (size_t)q * kStageBytes;
+            const float *f = reinterpret_cast<const float *>(slot);
+            float cur[8];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int k = k0 + i;
-                    float x = 0.f;
-                    if (col_ok && k < K) x = k < g.K1 ? g.B1[(int64_t)k * g.ldb1 + n] : g.B2[(int64_t)(k - g.K1) * g.ldb2 + n];
-                    v[i] = x;
-                }
-                if (!mbar_wait(&bars->empty[s], ph ^ 1u, bars, err, 1)) goto conv_done;
-                {
-                    uint32_t hw[8], lw[8];
+            for (int i = 0; i < 8; ++i) cur[i] = col_ok ? f[(h * 8 + i) * kTileN + r] : 0.f;
+            // all converters have read the slot before any overwrites it (an
+            // mbarrier, so that this wait is bounded like every other)
+            mbar_arrive(&bars->read[q]);
+            if (!mbar_wait(&bars->read[q], par, bars, err, 8)) break;
+            uint32_t hw[4], lw[4];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
-                        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
-                        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
-                        hw[i] = pack2(h0, h1);
-                        lw[i] = pack2(l0, l1);
-                    }
-                    uint8_t *st = stages + (size_t)s * kStageBytes;
-                    // K step h of this stage; row r: core matrix (r/8, half), row r%8
-                    const uint32_t off = (uint32_t)h * 4096u + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
-                    *reinterpret_cast<uint4 *>(st + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4 *>(st + off + 128) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-                    *reinterpret_cast<uint4 *>(st + 8192 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                    *reinterpret_cast<uint4 *>(st + 8192 + off + 128) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
-                }
-                fence_async_smem();
-                mbar_arrive(&bars->full[s]);
-                if (++s == nst) {
-                    s = 0;
-                    ph ^= 1u;
-                }
+            for (int i = 0; i < 4; ++i) {
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(cur[2 * i]), h1 = __float2bfloat16_rn(cur[2 * i + 1]);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(cur[2 * i] - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(cur[2 * i + 1] - __bfloat162float(h1));
+                hw[i] = pack2(h0, h1);
+                lw[i] = pack2(l0, l1);
             }
+            // row r: core matrix (r/8, K half h), row r%8
+            const uint32_t off = (uint32_t)(r >> 3) * 256u + (uint32_t)h * 128u + (uint32_t)(r & 7) * 16u;
+            *reinterpret_cast<uint4 *>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(slot + 4096 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            fence_async_smem();
+            mbar_arrive(&bars->converted[q]);
         }
-    conv_done:;
     } else if (warp < kConvWarps + kEpiWarps) {
         // ---- epilogue: lane quarter q = warp % 4 holds tile rows 32q..32q+31
-        const int q = warp & 3;
+        const int q = warp & 3, part = (warp - kConvWarps) >> 2;
+        constexpr int kParts = kEpiWarps / 4;
         const int row = q * 32 + lane;
         int b = 0;
         uint32_t ph = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             if (!mbar_wait(&bars->acc_full[b], ph, bars, err, 2)) break;
             tc_fence_after();
-            const int64_t n = tile * kTileN + row;
-            const bool ok = n < g.N;
+            int64_t n0, n1;
+            tm.cols(tile, n0, n1);
+            const int64_t n = n0 + row;
+            const bool ok = n < n1;
+            const int64_t e = n % g.np;
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * acc_stride;
-            for (int c0 = 0; c0 < g.M; c0 += 24) {
+            for (int c0 = 24 * part; c0 < g.M; c0 += 24 * kParts) {
                 float v[24];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc)
                     if (c0 + cc * 8 < g.M) tmem_ld8(taddr + (uint32_t)(c0 + cc * 8), v + cc * 8);
                 tmem_ld_wait();
-                if (!ok) continue;
-                if (MODE == GEMM_GRAD) {
-                    const int64_t e = n % g.np;
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const int j = c0 / 3 + t;
-                        if (3 * j >= g.M) break;
-                        const float *S = g.S + (int64_t)j * 9 * g.np + e;
-                        const float ij = g.invJ[(int64_t)j * g.np + e];
-                        const float g0 = v[3 * t], g1 = v[3 * t + 1], g2 = v[3 * t + 2];
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            const float s0 = S[(0 * 3 + m) * g.np], s1 = S[(1 * 3 + m) * g.np],
-                                        s2 = S[(2 * 3 + m) * g.np];
-                            g.C[(int64_t)(3 * j + m) * g.ldc + n] = ij * (s0 * g0 + s1 * g1 + s2 * g2);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int t = 0; t < 24; ++t)
-                        if (c0 + t < g.M) epi_row<MODE>(g, c0 + t, n, v[t]);
-                }
+                if (ok) epi_group<MODE>(g, c0, n, e, v);
             }
             tc_fence_before();
             mbar_arrive(&bars->acc_empty[b]);
@@ -304,7 +374,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ph ^= 1u;
             }
         }
-    } else if (lane == 0) {
+    } else if (warp == kProdWarp && lane == 0) {
+        // ---- producer: one 2-D TMA box (16 K rows x 128 columns) per stage
+        // into its slot; stage ks reads B1 rows 16 ks.. (ks < K1pad / 16)
+        // or B2 rows 16 ks - K1pad..
+        const int n1st = K1pad / kStageK;
+        for (int64_t idx = 0; idx < total; ++idx) {
+            const int q = (int)(idx % nslot);
+            if (!mbar_wait(&bars->freed[q], (uint32_t)(((idx / nslot) & 1) ^ 1), bars, err, 7)) break;
+            int64_t n0, n1;
+            stage_cols(idx, n0, n1);
+            const int ks = (int)(idx % nkst);
+            const CUtensorMap *tmap = ks < n1st ? &tmB1 : &tmB2;
+            const int y = ks < n1st ? ks * kStageK : ks * kStageK - K1pad;
+            mbar_expect_tx(&bars->loaded[q], kStageBytes);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+                    "r"(smem_u32(slots + (size_t)q * kStageBytes)),
+                "l"(reinterpret_cast<uint64_t>(tmap)), "r"((int)n0), "r"(y), "r"(smem_u32(&bars->loaded[q]))
+                : "memory");
+        }
+    } else if (warp == kMmaWarp && lane == 0) {
         // ---- operator load, then the MMA issue loop
         const uint32_t op_s = smem_u32(smem);
         mbar_expect_tx(&bars->op_full, op_bytes);
@@ -321,37 +411,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         // N >> 3 at bit 17, M >> 4 at bit 24
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Nmma >> 3) << 17) |
                                ((uint32_t)(kTileN >> 4) << 24);
-        const uint32_t st_s = smem_u32(stages);
-        int s = 0, b = 0;
-        uint32_t ph = 0, aph = 0;
+        const uint32_t st_s = smem_u32(slots);
+        int64_t idx = 0;
+        int b = 0;
+        uint32_t aph = 0;
         for (int64_t tile = blockIdx.x; live && tile < ntiles; tile += gridDim.x) {
             if (!mbar_wait(&bars->acc_empty[b], aph ^ 1u, bars, err, 4)) break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)b * acc_stride;
-            for (int ks = 0; ks < nkst; ++ks) {
-                if (!mbar_wait(&bars->full[s], ph, bars, err, 5)) {
+            for (int ks = 0; ks < nkst; ++ks, ++idx) {
+                const int q = (int)(idx % nslot);
+                if (!mbar_wait(&bars->converted[q], (uint32_t)((idx / nslot) & 1), bars, err, 5)) {
                     live = false;
                     break;
                 }
                 tc_fence_after();
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint32_t kstep = (uint32_t)(ks * 2 + kk);
-                    const uint32_t a_hi = st_s + (uint32_t)s * kStageBytes + (uint32_t)kk * 4096u;
-                    const uint32_t a_lo = a_hi + 8192u;
-                    const uint32_t b_hi = op_s + kstep * (uint32_t)Nmma * 32u;
+                {
+                    const uint32_t a_hi = st_s + (uint32_t)q * kStageBytes;
+                    const uint32_t a_lo = a_hi + 4096u;
+                    const uint32_t b_hi = op_s + (uint32_t)ks * (uint32_t)Nmma * 32u;
                     const uint32_t b_lo = b_hi + op_half;
                     const uint64_t ah = sdesc(a_hi, 128, 256), al = sdesc(a_lo, 128, 256);
                     const uint64_t bh = sdesc(b_hi, 128, 256), bl = sdesc(b_lo, 128, 256);
-                    mma_bf16(d, ah, bh, idesc, (ks | kk) != 0);
+                    mma_bf16(d, ah, bh, idesc, ks != 0);
                     mma_bf16(d, ah, bl, idesc, 1);
                     mma_bf16(d, al, bh, idesc, 1);
                 }
-                mma_commit(&bars->empty[s]);
-                if (++s == nst) {
-                    s = 0;
-                    ph ^= 1u;
-                }
+                mma_commit(&bars->freed[q]);
             }
             if (!live) break;
             mma_commit(&bars->acc_full[b]);
@@ -364,59 +450,119 @@ __global__ void __launch_bounds__(kThreads, 1)
         mma_commit(&bars->done);
         mbar_wait(&bars->done, 0, bars, err, 6);
     }
+    // after an abort, give bulk copies still in flight time to land before
+    // the CTA's shared memory is released
+    if (*(volatile int *)&bars->abort) {
+        const long long t0 = clock64();
+        while (clock64() - t0 < 200000) {
+        }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kConvWarps + kEpiWarps)
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+// 2-D tensor map of one operand block: rows x cols floats, row stride ld
+// floats, boxes of 16 rows x 128 columns, zero fill out of bounds
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_rows(CUtensorMap *m, const float *base, int64_t cols, int rows, int64_t ld) {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return cudaErrorNotSupported;
+        fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
+    const cuuint64_t stride[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kTileN, (cuuint32_t)kStageK};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dim, stride, box, estride,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int MODE>
-cudaError_t launch_mode(const GemmArgsT<float> &g, const TcOperator &op, int *err, int grid, cudaStream_t s) {
-    const int nst = tc_stages(op);
+cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOperator &op, int *err, int grid,
+                        cudaStream_t s) {
+    const int nslot = tc_stages(op);
     const size_t smem = tc_smem_bytes(op);
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // the attribute is raised once per instantiation to the largest size
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+        if (e != cudaSuccess) return e;
+        configured = 232448;
+    }
     uint32_t cols = 32;
     while (cols < 2u * (uint32_t)op.Nmma) cols <<= 1;
-    k_gemm_tc<MODE><<<grid, kThreads, smem, s>>>(g, op.img, op.Nmma, op.Kpad, nst, cols, err);
+    CUtensorMap m1, m2;
+    cudaError_t e = encode_rows(&m1, g.B1, g.N, g.K1, g.ldb1);
+    if (e == cudaSuccess) e = g.K2 > 0 ? encode_rows(&m2, g.B2, g.N, g.K2, g.ldb2) : encode_rows(&m2, g.B1, g.N, g.K1, g.ldb1);
+    if (e != cudaSuccess) return e;
+    k_gemm_tc<MODE><<<grid, kThreads, smem, s>>>(g, tm, m1, m2, op.img, op.Nmma, op.K1pad, op.Kpad, nslot, cols, err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+// shared memory after the operator image: the slot ring (2..12 slots)
+static int64_t tc_free(const TcOperator &op) {
+    return 232448 - 4 * (int64_t)op.Nmma * op.Kpad - (int64_t)sizeof(Bars) - 1024;
+}
+
 int tc_stages(const TcOperator &op) {
-    const int64_t avail = 232448 - 4 * (int64_t)op.Nmma * op.Kpad - (int64_t)sizeof(Bars) - 1024;
-    if (avail < 0) return 0;
-    const int64_t n = avail / kStageBytes;
-    return n > 8 ? 8 : (int)n;
+    const int64_t n = tc_free(op) / kStageBytes;
+    return n < 0 ? 0 : (n > kMaxSlots ? kMaxSlots : (int)n);
 }
 
 size_t tc_smem_bytes(const TcOperator &op) {
-    const size_t used = 2 * (size_t)op.Nmma * op.Kpad * 2 + (size_t)tc_stages(op) * kStageBytes + sizeof(Bars);
+    const size_t used = 4 * (size_t)op.Nmma * op.Kpad + (size_t)tc_stages(op) * kStageBytes + sizeof(Bars);
     // at least 116 KB, so that no two CTAs (and their tensor memory) share an SM
     return used < 118784 ? 118784 : used;
 }
 
 cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int *err, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-    if (g.M > op.Nmma || op.Nmma > 256 || op.Nmma % 16 || op.Kpad % kStageK || g.K1 + g.K2 > op.Kpad ||
-        tc_stages(op) < 2)
+    if (g.M > op.Nmma || op.Nmma > 256 || op.Nmma % 16 || op.Kpad % kStageK || op.K1pad % kStageK ||
+        g.K1 > op.K1pad || g.K2 > op.Kpad - op.K1pad || tc_stages(op) < 2)
         return cudaErrorInvalidValue;
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t ntiles = (g.N + kTileN - 1) / kTileN;
+    // TMA: 16-byte aligned bases, row strides and column offsets
+    if (((uintptr_t)g.B1 | (uintptr_t)(g.K2 > 0 ? g.B2 : g.B1)) % 16 || (g.ldb1 * 4) % 16 ||
+        (g.K2 > 0 && (g.ldb2 * 4) % 16) || g.np % 4)
+        return cudaErrorInvalidValue;
+    static int nsm = 0;  // one device type per process
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+    }
+    if (g.np <= 0 || g.N % g.np) return cudaErrorInvalidValue;
+    TileMap tm;
+    tm.np = g.np;
+    tm.nvb = (int)(g.N / g.np);
+    tm.ept = (g.np + kTileN - 1) / kTileN;
+    const int64_t ntiles = tm.ept * tm.nvb;
     const int grid = (int)(ntiles < nsm ? ntiles : nsm);
     switch (g.mode) {
         case GEMM_STORE:
-            return launch_mode<GEMM_STORE>(g, op, err, grid, s);
+            return launch_mode<GEMM_STORE>(g, tm, op, err, grid, s);
         case GEMM_GRAD:
-            return launch_mode<GEMM_GRAD>(g, op, err, grid, s);
+            return launch_mode<GEMM_GRAD>(g, tm, op, err, grid, s);
         case GEMM_DIV:
-            return launch_mode<GEMM_DIV>(g, op, err, grid, s);
+            return launch_mode<GEMM_DIV>(g, tm, op, err, grid, s);
         case GEMM_DIV_RK:
-            return launch_mode<GEMM_DIV_RK>(g, op, err, grid, s);
+            return launch_mode<GEMM_DIV_RK>(g, tm, op, err, grid, s);
     }
     return cudaErrorInvalidValue;
 }

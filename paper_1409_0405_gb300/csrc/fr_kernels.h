@@ -76,13 +76,15 @@ cudaError_t launch_gemm_grouped(const GemmArgsT<T> *descs, const int64_t *begin,
 // An operator packed for the tensor-core kernel: device image [hi | lo] of
 // bf16 values in K-major core matrices (8 rows x 8 K values, 128 B; per
 // 16-wide K step the Nmma/8 row groups x 2 K halves), rows padded to Nmma
-// (a multiple of 16, <= 256) and columns to Kpad (a multiple of 32).
+// (a multiple of 16, <= 256) and each operand block's columns to a multiple
+// of 16.
+// The columns of the second operand block start at K1pad (a multiple of 16).
 struct TcOperator {
     const uint8_t *img = nullptr;
-    int M = 0, K = 0, Nmma = 0, Kpad = 0;
+    int M = 0, K = 0, Nmma = 0, K1pad = 0, Kpad = 0;
 };
-// packs a row-major FP64 operator (M x K) into the image layout (host)
-void tc_pack(const double *A, int M, int K, std::vector<uint16_t> &img, int &Nmma, int &Kpad);
+// packs a row-major FP64 operator (M x (K1 + K2)) into the image layout (host)
+void tc_pack(const double *A, int M, int K1, int K2, std::vector<uint16_t> &img, int &Nmma, int &K1pad, int &Kpad);
 int tc_stages(const TcOperator &op);
 size_t tc_smem_bytes(const TcOperator &op);
 // C <- A [B1; B2] with g's epilogue on the tensor cores; *err (device) is set
@@ -187,6 +189,11 @@ cudaError_t launch_const_common(const Pairs &P, const Bnd &B, const Fields &F, c
 // Us = U - uref over a whole [nu][V][np] register
 template <typename T>
 cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const double *uref, cudaStream_t s);
+// RK4 register update (the GEMM_DIV_RK epilogue) from a stored RHS R
+// [nu][V][np]: see GemmArgsT for c_acc, c_stage, first, last
+template <typename T>
+cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
+                             double c_acc, double c_stage, int first, int last, cudaStream_t s);
 // element-wise double -> float copy
 cudaError_t launch_to_float(int64_t n, const double *src, float *dst, cudaStream_t s);
 // per-block partial integrals (7 per block) of one type's register

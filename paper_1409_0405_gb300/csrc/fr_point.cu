@@ -486,6 +486,27 @@ __global__ void k_center(int64_t n, int64_t np, const double *__restrict__ U, T 
     Us[idx] = T(U[idx] - uref.v[v]);
 }
 
+// RK4 register update from a stored RHS r (the arithmetic of the fused
+// GEMM_DIV_RK epilogue, applied as a separate streaming pass)
+template <typename T>
+__global__ void k_rk_update(int64_t n, int64_t np, const T *__restrict__ R, double *__restrict__ U,
+                            double *__restrict__ Uacc, T *__restrict__ Us, const Uref uref, double c_acc,
+                            double c_stage, int first, int last) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const double ur = uref.v[(idx / np) % V];
+    const double rv = (double)R[idx];
+    if (last) {
+        const double un = Uacc[idx] + c_acc * rv;
+        U[idx] = un;
+        Us[idx] = T(un - ur);
+    } else {
+        const double u = U[idx];
+        Uacc[idx] = (first ? u : Uacc[idx]) + c_acc * rv;
+        Us[idx] = T((u - ur) + c_stage * rv);
+    }
+}
+
 __global__ void k_to_float(int64_t n, const double *__restrict__ src, float *__restrict__ dst) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n) dst[idx] = (float)src[idx];
@@ -569,6 +590,16 @@ cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const doub
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
+                             double c_acc, double c_stage, int first, int last, cudaStream_t s) {
+    const int64_t n = (int64_t)nu * V * np;
+    if (n == 0) return cudaSuccess;
+    Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
+    k_rk_update<T><<<blocks_for(n, 256), 256, 0, s>>>(n, np, R, U, Uacc, Us, r, c_acc, c_stage, first, last);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_float(int64_t n, const double *src, float *dst, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_to_float<<<blocks_for(n, 256), 256, 0, s>>>(n, src, dst);
@@ -617,6 +648,8 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
     template cudaError_t launch_pub_to_int<T>(int, int64_t, int64_t, const double *, double *, cudaStream_t,    \
                                               T *, const double *);                                           \
     template cudaError_t launch_center<T>(int, int64_t, const double *, T *, const double *, cudaStream_t);     \
+    template cudaError_t launch_rk_update<T>(int, int64_t, const T *, double *, double *, T *, const double *,   \
+                                             double, double, int, int, cudaStream_t);                        \
     template cudaError_t launch_int_to_pub<T>(int, int64_t, int64_t, const T *, double *, cudaStream_t);       \
     template cudaError_t launch_flux_grouped<T>(const FluxItem<T> *, const int64_t *, int, int64_t, const Phys &, \
                                                 int, cudaStream_t);                                           \

@@ -254,15 +254,31 @@ GemmArgsT<T> args_div(const fr_ctx *c, int t, const RKStage *rk) {
     return g;
 }
 
+// the dense arguments plus the chunk-compressed operator, if there is one
+template <typename T>
+GemmArgsT<T> with_sparse(const fr_ctx *c, int t, int which, const GemmArgsT<T> &g) {
+    GemmArgsT<T> h = g;
+    const DevType &D = c->T[t];
+    if (D.sp_rc[which]) {
+        h.sp_rc = D.sp_rc[which];
+        h.sp_lmax = D.sp_lmax[which];
+        h.sp_off = D.sp_off[which];
+        h.sp_cols = D.sp_cols[which];
+        h.sp_vals = (const T *)D.sp_vals[which];
+        h.sp_masked = D.sp_masked[which];
+    }
+    return h;
+}
+
 template <>
-cudaError_t op_gemm<double>(fr_ctx *, int, int, const GemmArgsT<double> &g, cudaStream_t s) {
-    return launch_gemm<double>(g, s);
+cudaError_t op_gemm<double>(fr_ctx *c, int t, int which, const GemmArgsT<double> &g, cudaStream_t s) {
+    return launch_gemm<double>(with_sparse<double>(c, t, which, g), s);
 }
 
 template <>
 cudaError_t op_gemm<float>(fr_ctx *c, int t, int which, const GemmArgsT<float> &g, cudaStream_t s) {
     if (c->prm.precision == FR_BF16X3) return launch_gemm_tc(g, c->T[t].tc[which], c->tc_err, s);
-    return launch_gemm<float>(g, s);
+    return launch_gemm<float>(with_sparse<float>(c, t, which, g), s);
 }
 
 // FR_ERR_TIMEOUT if a tensor-core kernel gave up a wait (synchronises)
@@ -451,6 +467,35 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
                 uint16_t *dimg = nullptr;
                 if ((rc = upload(c, &dimg, img))) return rc;
                 op.img = (const uint8_t *)dimg;
+            }
+        }
+        if (prm->precision != FR_BF16X3) {
+            // the operators' exact zeros skipped chunk by chunk (prisms)
+            const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
+            const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok1[3] = {D.nu, D.nu, 3 * D.nu}, ok2[3] = {0, D.nf, D.nf};
+            for (int w = 0; w < 3; ++w) {
+                // FP64 (FMA-bound): exactly the non-zero FMAs, chunk by chunk
+                // of 3 rows; FP32 (bound by loads as much as by FMAs): the
+                // chunk size with the fewest FMAs over whole column unions
+                SparseOp sp;
+                const bool masked = prm->precision == FR_FP64;
+                if (masked ? !sparse_pack_masked(opv[w]->data(), om[w], ok1[w], ok2[w], sp)
+                           : !sparse_pack(opv[w]->data(), om[w], ok1[w], ok2[w], w == 1, sp))
+                    continue;
+                D.sp_masked[w] = masked;
+                if ((rc = upload(c, &D.sp_off[w], sp.off)) || (rc = upload(c, &D.sp_cols[w], sp.cols))) return rc;
+                if (prm->precision == FR_FP32) {
+                    std::vector<float> vf(sp.vals.begin(), sp.vals.end());
+                    float *dv = nullptr;
+                    if ((rc = upload(c, &dv, vf))) return rc;
+                    D.sp_vals[w] = dv;
+                } else {
+                    double *dv = nullptr;
+                    if ((rc = upload(c, &dv, sp.vals))) return rc;
+                    D.sp_vals[w] = dv;
+                }
+                D.sp_rc[w] = sp.rc;
+                D.sp_lmax[w] = sp.lmax;
             }
         }
         if (prm->precision != FR_FP64) {

@@ -45,6 +45,10 @@ struct DevType {
     int64_t cl_cap_nh = 0;  // hidden width the buffers were sized for
     // FR_BF16X3: the packed operators M0, AGRAD, ADIV for the tensor cores
     fr::TcOperator tc[3];
+    // FR_FP64 / FR_FP32: chunk-compressed M0, AGRAD, ADIV (sp_rc 0: dense)
+    int sp_rc[3] = {0, 0, 0}, sp_lmax[3] = {0, 0, 0}, sp_masked[3] = {0, 0, 0};
+    int *sp_off[3] = {nullptr, nullptr, nullptr}, *sp_cols[3] = {nullptr, nullptr, nullptr};
+    void *sp_vals[3] = {nullptr, nullptr, nullptr};  // double or float
 };
 
 struct fr_ctx {

@@ -20,7 +20,9 @@
 // by the L2 traffic of re-reading B once per row chunk.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "fr_kernels.h"
 
@@ -35,9 +37,23 @@ constexpr int kThreads = 128;
 template <typename T, int RC, int MODE>
 __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_t tile, T *sA) {
     const int K = g.K1 + g.K2;
-    for (int idx = threadIdx.x; idx < RC * K; idx += kThreads) {
-        const int r = idx / K, k = idx - r * K;
-        sA[k * RC + r] = (m0 + r < g.M) ? g.A[(size_t)(m0 + r) * K + k] : T(0);
+    // dense: sA[k][r] for every column; compressed: sA[i][r] for the chunk's
+    // column list i, the column numbers in sK
+    int nl1 = g.K1, nl = K;
+    int *sK = nullptr;
+    if (g.sp_rc) {
+        const int c = m0 / RC;
+        const int beg = g.sp_off[2 * c], mid = g.sp_off[2 * c + 1], end = g.sp_off[2 * c + 2];
+        nl1 = mid - beg;
+        nl = end - beg;
+        sK = reinterpret_cast<int *>(sA + (size_t)g.sp_lmax * RC);
+        for (int idx = threadIdx.x; idx < RC * nl; idx += kThreads) sA[idx] = g.sp_vals[(size_t)beg * RC + idx];
+        for (int idx = threadIdx.x; idx < nl; idx += kThreads) sK[idx] = g.sp_cols[beg + idx];
+    } else {
+        for (int idx = threadIdx.x; idx < RC * K; idx += kThreads) {
+            const int r = idx / K, k = idx - r * K;
+            sA[k * RC + r] = (m0 + r < g.M) ? g.A[(size_t)(m0 + r) * K + k] : T(0);
+        }
     }
     __syncthreads();
     const int64_t n = tile * kThreads + threadIdx.x;
@@ -45,27 +61,77 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
         T acc[RC];
 #pragma unroll
         for (int r = 0; r < RC; ++r) acc[r] = T(0);
-        {
-            const T *b = g.B1 + n;
-            const int64_t ld = g.ldb1;
+        if constexpr (RC == 3) {
+            if (sK && g.sp_masked) {
+                // per listed column, only the rows whose entry is non-zero;
+                // the mask is the same for the whole warp, so this is a
+                // uniform branch, not predication of the FMAs
+                const T *b1 = g.B1 + n, *b2 = g.B2 + n;
 #pragma unroll 2
-            for (int k = 0; k < g.K1; ++k) {
-                const T bv = __ldg(b + (int64_t)k * ld);
-                const T *a = sA + k * RC;
+                for (int i = 0; i < nl; ++i) {
+                    const int w = sK[i];
+                    const int k = w & 0xFFFFFF;
+                    const T bv = i < nl1 ? __ldg(b1 + (int64_t)k * g.ldb1) : __ldg(b2 + (int64_t)(k - g.K1) * g.ldb2);
+                    const T *a = sA + i * 3;
+                    switch (w >> 24) {
+                        case 1: acc[0] = fma(a[0], bv, acc[0]); break;
+                        case 2: acc[1] = fma(a[1], bv, acc[1]); break;
+                        case 3: acc[0] = fma(a[0], bv, acc[0]); acc[1] = fma(a[1], bv, acc[1]); break;
+                        case 4: acc[2] = fma(a[2], bv, acc[2]); break;
+                        case 5: acc[0] = fma(a[0], bv, acc[0]); acc[2] = fma(a[2], bv, acc[2]); break;
+                        case 6: acc[1] = fma(a[1], bv, acc[1]); acc[2] = fma(a[2], bv, acc[2]); break;
+                        default:
+                            acc[0] = fma(a[0], bv, acc[0]);
+                            acc[1] = fma(a[1], bv, acc[1]);
+                            acc[2] = fma(a[2], bv, acc[2]);
+                    }
+                }
+                sK = nullptr;  // done
+                nl = -1;
+            }
+        }
+        if (sK) {
+            // the chunk's non-zero columns only, in increasing order: the
+            // same sums as the dense loop, less the terms whose A is zero
+            const T *b1 = g.B1 + n;
+#pragma unroll 2
+            for (int i = 0; i < nl1; ++i) {
+                const T bv = __ldg(b1 + (int64_t)sK[i] * g.ldb1);
+                const T *a = sA + i * RC;
 #pragma unroll
                 for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
             }
-        }
-        if (g.K2 > 0) {
-            const T *b = g.B2 + n;
-            const int64_t ld = g.ldb2;
-            const T *a0 = sA + g.K1 * RC;
+            const T *b2 = g.B2 + n;
 #pragma unroll 2
-            for (int k = 0; k < g.K2; ++k) {
-                const T bv = __ldg(b + (int64_t)k * ld);
-                const T *a = a0 + k * RC;
+            for (int i = nl1; i < nl; ++i) {
+                const T bv = __ldg(b2 + (int64_t)(sK[i] - g.K1) * g.ldb2);
+                const T *a = sA + i * RC;
 #pragma unroll
                 for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
+            }
+        } else if (nl >= 0) {
+            {
+                const T *b = g.B1 + n;
+                const int64_t ld = g.ldb1;
+#pragma unroll 2
+                for (int k = 0; k < g.K1; ++k) {
+                    const T bv = __ldg(b + (int64_t)k * ld);
+                    const T *a = sA + k * RC;
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
+                }
+            }
+            if (g.K2 > 0) {
+                const T *b = g.B2 + n;
+                const int64_t ld = g.ldb2;
+                const T *a0 = sA + g.K1 * RC;
+#pragma unroll 2
+                for (int k = 0; k < g.K2; ++k) {
+                    const T bv = __ldg(b + (int64_t)k * ld);
+                    const T *a = a0 + k * RC;
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
+                }
             }
         }
 
@@ -157,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_grouped(const GemmArgsT<T> *_
 template <typename T, int RC, int MODE>
 cudaError_t run(const GemmArgsT<T> &g, cudaStream_t s) {
     const int K = g.K1 + g.K2;
-    const size_t smem = (size_t)RC * K * sizeof(T);
+    const size_t smem = g.sp_rc ? (size_t)g.sp_lmax * (RC * sizeof(T) + sizeof(int)) : (size_t)RC * K * sizeof(T);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm<T, RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -218,7 +284,14 @@ cudaError_t dispatch(int rc, const GemmArgsT<T> &g, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_gemm(const GemmArgsT<T> &g, cudaStream_t s) {
     if (g.N <= 0 || g.M <= 0) return cudaSuccess;
-    const int rc = pick_rc(g.M, g.mode == GEMM_GRAD);
+    int rc = pick_rc(g.M, g.mode == GEMM_GRAD);
+    if (g.sp_rc) {
+        // the compressed operator fixes the chunk size
+        if (!g.sp_off || !g.sp_cols || !g.sp_vals || g.sp_lmax <= 0 || (g.mode == GEMM_GRAD && g.sp_rc % 3) ||
+            (g.sp_masked && g.sp_rc != 3))
+            return cudaErrorInvalidValue;
+        rc = g.sp_rc;
+    }
     switch (g.mode) {
         case GEMM_STORE:
             return dispatch<T, GEMM_STORE>(rc, g, s);
@@ -324,5 +397,86 @@ template cudaError_t launch_gemm_grouped<double>(const GemmArgsT<double> *, cons
                                                  int, int, cudaStream_t);
 template cudaError_t launch_gemm_grouped<float>(const GemmArgsT<float> *, const int64_t *, int, int64_t, int, int, int,
                                                 int, cudaStream_t);
+
+int sparse_pack(const double *A, int M, int K1, int K2, bool mult3, SparseOp &out) {
+    out = SparseOp();
+    const int K = K1 + K2;
+    if (M <= 0 || K <= 0) return 0;
+    const int cand[] = {30, 27, 25, 24, 21, 20, 18, 17, 15, 13, 12, 10, 9, 8, 6, 5, 4, 3};
+    long best = -1;
+    int best_rc = 0;
+    for (int rc : cand) {
+        if (mult3 && rc % 3) continue;
+        long fma = 0;
+        for (int m0 = 0; m0 < M; m0 += rc) {
+            int cnt = 0;
+            for (int k = 0; k < K; ++k) {
+                bool nz = false;
+                for (int r = 0; r < rc && m0 + r < M && !nz; ++r) nz = A[(size_t)(m0 + r) * K + k] != 0.0;
+                cnt += nz;
+            }
+            fma += (long)cnt * rc;
+        }
+        if (best < 0 || fma < best) {
+            best = fma;
+            best_rc = rc;
+        }
+    }
+    const long dense = (long)((M + best_rc - 1) / best_rc) * best_rc * K;
+    if (best < 0 || best * 5 > dense * 4) return 0;
+    out.rc = best_rc;
+    for (int m0 = 0; m0 < M; m0 += best_rc) {
+        out.off.push_back((int)out.cols.size());
+        bool mid_set = false;
+        for (int k = 0; k < K; ++k) {
+            bool nz = false;
+            for (int r = 0; r < best_rc && m0 + r < M && !nz; ++r) nz = A[(size_t)(m0 + r) * K + k] != 0.0;
+            if (!nz) continue;
+            if (!mid_set && k >= K1) {
+                out.off.push_back((int)out.cols.size());
+                mid_set = true;
+            }
+            out.cols.push_back(k);
+            for (int r = 0; r < best_rc; ++r)
+                out.vals.push_back(m0 + r < M ? A[(size_t)(m0 + r) * K + k] : 0.0);
+        }
+        if (!mid_set) out.off.push_back((int)out.cols.size());
+        const int len = (int)out.cols.size() - out.off[out.off.size() - 2];
+        out.lmax = std::max(out.lmax, len);
+    }
+    out.off.push_back((int)out.cols.size());
+    return out.rc;
+}
+
+int sparse_pack_masked(const double *A, int M, int K1, int K2, SparseOp &out) {
+    out = SparseOp();
+    const int K = K1 + K2;
+    if (M <= 0 || K <= 0 || K >= (1 << 24)) return 0;
+    long nnz = 0;
+    for (size_t i = 0; i < (size_t)M * K; ++i) nnz += A[i] != 0.0;
+    const long dense = (long)((M + 2) / 3) * 3 * K;
+    if (nnz * 5 > dense * 4) return 0;
+    out.rc = 3;
+    for (int m0 = 0; m0 < M; m0 += 3) {
+        out.off.push_back((int)out.cols.size());
+        bool mid_set = false;
+        for (int k = 0; k < K; ++k) {
+            int mask = 0;
+            for (int r = 0; r < 3 && m0 + r < M; ++r)
+                if (A[(size_t)(m0 + r) * K + k] != 0.0) mask |= 1 << r;
+            if (!mask) continue;
+            if (!mid_set && k >= K1) {
+                out.off.push_back((int)out.cols.size());
+                mid_set = true;
+            }
+            out.cols.push_back(k | (mask << 24));
+            for (int r = 0; r < 3; ++r) out.vals.push_back(m0 + r < M ? A[(size_t)(m0 + r) * K + k] : 0.0);
+        }
+        if (!mid_set) out.off.push_back((int)out.cols.size());
+        out.lmax = std::max(out.lmax, (int)out.cols.size() - out.off[out.off.size() - 2]);
+    }
+    out.off.push_back((int)out.cols.size());
+    return 3;
+}
 
 }  // namespace fr

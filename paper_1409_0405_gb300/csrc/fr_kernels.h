@@ -52,11 +52,38 @@ struct GemmArgsT {
     // GEMM_DIV(_RK): constant field added to r (the discrete divergence of
     // the subtracted reference flux, see Phys::fref); may be null
     const double *rfs = nullptr;
+    // Optional chunk-compressed A (sp_rc > 0, used instead of A): the rows
+    // in chunks of sp_rc; chunk c lists, in increasing order, the columns
+    // in which any of its rows is non-zero: sp_cols[sp_off[2c] ..
+    // sp_off[2c+2]), those below K1 first (up to sp_off[2c+1]); its values
+    // are sp_vals[(i) * sp_rc + r] for list entry i (global index) and row
+    // m0 + r (zero past M).  The other columns of the chunk are all zero, so
+    // the result is that of the dense A.  sp_lmax bounds a chunk's list.
+    int sp_rc = 0, sp_lmax = 0;
+    const int *sp_off = nullptr, *sp_cols = nullptr;
+    const T *sp_vals = nullptr;
+    // sp_masked (with sp_rc == 3): each list entry is k | mask << 24, mask
+    // bit r set when row m0 + r is non-zero in column k; only those FMAs run
+    int sp_masked = 0;
 };
 using GemmArgs = GemmArgsT<double>;
 
 template <typename T>
 cudaError_t launch_gemm(const GemmArgsT<T> &g, cudaStream_t s);
+// host: chunk-compressed form of a row-major M x (K1 + K2) operator for
+// launch_gemm (see GemmArgsT::sp_*).  Picks the chunk size among the
+// instantiated ones (a multiple of 3 if mult3) that needs the fewest FMAs;
+// returns 0 (use the dense operator) unless that saves at least 20%.
+struct SparseOp {
+    int rc = 0, lmax = 0;
+    std::vector<int> off, cols;
+    std::vector<double> vals;
+};
+int sparse_pack(const double *A, int M, int K1, int K2, bool mult3, SparseOp &out);
+// the masked form (chunks of 3 rows, a row mask per listed column): the
+// FMAs executed are exactly the operator's non-zeros; 0 unless that saves
+// at least 20% of the dense FMAs
+int sparse_pack_masked(const double *A, int M, int K1, int K2, SparseOp &out);
 inline cudaError_t launch_gemm_f64(const GemmArgs &g, cudaStream_t s) { return launch_gemm<double>(g, s); }
 
 // Grouped persistent GEMM over ndesc device-resident descriptors; begin

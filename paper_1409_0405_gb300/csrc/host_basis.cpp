@@ -666,6 +666,16 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
             }
         for (int f = 0; f < nf; ++f) row[3 * nu + f] = M3(j, f).to_double();
     }
+    // Entries that vanish in exact arithmetic (the prism's triangle x line
+    // structure zeroes most of its operators) come out of the double-double
+    // construction as residue of order 1e-32 next to O(1) entries; they are
+    // set to exact zeros, which the operator kernels may then skip.
+    for (std::vector<double> *m : {&o.M0, &o.D, &o.M3, &o.AGRAD, &o.ADIV}) {
+        double mx = 0.0;
+        for (double v : *m) mx = std::max(mx, std::fabs(v));
+        for (double &v : *m)
+            if (std::fabs(v) < 1e-20 * mx) v = 0.0;
+    }
     return FR_OK;
 }
 }  // namespace

@@ -18,12 +18,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "fr_ctx.h"
+#include "fr_internal.h"
 
 using namespace fr;
 using namespace fr::api;
@@ -35,6 +37,7 @@ struct Group {
     int mode = 0, rc = 8, grid = 0, maxK = 0, ndesc = 0;
     int64_t total = 0;
     std::vector<GemmArgsT<T>> h;
+    std::vector<int> op;  // per descriptor: etype * 64 + order * 4 + operator (0 M0, 1 AGRAD, 2 ADIV)
     GemmArgsT<T> *d = nullptr;
     int64_t *begin = nullptr;
 };
@@ -92,7 +95,47 @@ struct BatchImpl : BatchBase {
 
     explicit BatchImpl(fr_batch *bb) : b(bb) { viscous = bb->ctx[0]->prm.viscous != 0; }
 
+    // the operators' exact zeros skipped as in the per-problem launches, in
+    // chunks of the group's row-chunk size (compressed per etype, order,
+    // operator and chunk size, uploaded once)
+    struct SpDev {
+        int rc = 0, lmax = 0;
+        int *off = nullptr, *cols = nullptr;
+        T *vals = nullptr;
+    };
+    std::map<std::pair<int, int>, SpDev> sp_cache;
+
+    const SpDev &sparse_for(int key, int rc) {
+        auto it = sp_cache.find({key, rc});
+        if (it != sp_cache.end()) return it->second;
+        SpDev &d = sp_cache[{key, rc}];
+        const int et = key / 64, order = (key / 4) % 16, which = key % 4;
+        RefOps ops;
+        std::string err;
+        if (build_ref_ops(et, order, ops, err)) return d;
+        const int nu = ops.nu, nf = ops.nf;
+        const std::vector<double> *A[3] = {&ops.M0, &ops.AGRAD, &ops.ADIV};
+        const int M[3] = {nf, 3 * nu, nu}, K1[3] = {nu, nu, 3 * nu}, K2[3] = {0, nf, nf};
+        SparseOp sp;
+        if (!sparse_pack(A[which]->data(), M[which], K1[which], K2[which], which == 1, sp, rc)) return d;
+        std::vector<T> v(sp.vals.begin(), sp.vals.end());
+        if (dev_put((void **)&d.off, sp.off.data(), sizeof(int) * sp.off.size()) ||
+            dev_put((void **)&d.cols, sp.cols.data(), sizeof(int) * sp.cols.size()) ||
+            dev_put((void **)&d.vals, v.data(), sizeof(T) * v.size())) {
+            d = SpDev();
+            return d;
+        }
+        d.rc = sp.rc;
+        d.lmax = sp.lmax;
+        return d;
+    }
+
     ~BatchImpl() override {
+        for (auto &kv : sp_cache) {
+            cudaFree(kv.second.off);
+            cudaFree(kv.second.cols);
+            cudaFree(kv.second.vals);
+        }
         auto fg = [](Group<T> &g) {
             cudaFree(g.d);
             cudaFree(g.begin);
@@ -123,6 +166,19 @@ struct BatchImpl : BatchBase {
             bg[i] = tot;
             tot += gemm_blocks(g.h[i].M, g.h[i].N, g.rc);
             g.maxK = std::max(g.maxK, g.h[i].K1 + g.h[i].K2);
+            GemmArgsT<T> &a = g.h[i];
+            a.sp_rc = 0;
+            if (i < g.op.size()) {
+                const SpDev &sp = sparse_for(g.op[i], g.rc);
+                if (sp.rc == g.rc) {
+                    a.sp_rc = sp.rc;
+                    a.sp_lmax = sp.lmax;
+                    a.sp_off = sp.off;
+                    a.sp_cols = sp.cols;
+                    a.sp_vals = sp.vals;
+                    a.sp_masked = 0;
+                }
+            }
         }
         g.total = tot;
         g.ndesc = (int)g.h.size();
@@ -158,10 +214,14 @@ struct BatchImpl : BatchBase {
                 DevType &D = c->T[t];
                 if (!D.present) continue;
                 const T *in = (const T *)D.Us;
+                const int key = t * 64 + c->order * 4;
                 m0.h.push_back(args_m0<T>(c, t, in));
+                m0.op.push_back(key + 0);
                 if (viscous) {
                     grad.h.push_back(args_grad<T>(c, t, in));
+                    grad.op.push_back(key + 1);
                     m0g.h.push_back(args_m0grad<T>(c, t));
+                    m0g.op.push_back(key + 0);
                 }
                 flux.hb.push_back(flux.total);
                 flux.h.push_back(FluxItem<T>{D.nu, D.ne, D.np, (const T *)D.Us, (const T *)D.GU,
@@ -202,13 +262,17 @@ struct BatchImpl : BatchBase {
         dt_cur.assign(dt, dt + b->ctx.size());
         for (int st = 0; st < 4; ++st) {
             div[st].h.clear();
+            div[st].op.clear();
             for (size_t i = 0; i < b->ctx.size(); ++i) {
                 const double h = dt[i];
                 const double ca[4] = {h / 6.0, h / 3.0, h / 3.0, h / 6.0};
                 const double cs[4] = {0.5 * h, 0.5 * h, h, 0.0};
                 RKStage rk{ca[st], cs[st], st == 0, st == 3};
                 for (int t = 0; t < 2; ++t)
-                    if (b->ctx[i]->T[t].present) div[st].h.push_back(args_div<T>(b->ctx[i], t, &rk));
+                    if (b->ctx[i]->T[t].present) {
+                        div[st].h.push_back(args_div<T>(b->ctx[i], t, &rk));
+                        div[st].op.push_back(t * 64 + b->ctx[i]->order * 4 + 2);
+                    }
             }
             int rc = upload_group(div[st]);
             if (rc) return rc;
@@ -368,7 +432,10 @@ struct BatchImpl : BatchBase {
         dv.mode = GEMM_DIV;
         for (fr_ctx *c : b->ctx)
             for (int t = 0; t < 2; ++t)
-                if (c->T[t].present) dv.h.push_back(args_div<T>(c, t, nullptr));
+                if (c->T[t].present) {
+                    dv.h.push_back(args_div<T>(c, t, nullptr));
+                    dv.op.push_back(t * 64 + c->order * 4 + 2);
+                }
         dv.rc = 16;
         dv.grid = nsm * 8;
         if ((rc = upload_group(dv))) return rc;

@@ -313,7 +313,8 @@ namespace {
 template <typename T, int RC, int MODE>
 cudaError_t run_grouped(const GemmArgsT<T> *descs, const int64_t *begin, int ndesc, int64_t total, int maxK,
                         int grid, cudaStream_t s) {
-    const size_t smem = (size_t)RC * maxK * sizeof(T);
+    // a dense chunk, or a compressed one with its column list (lmax <= K)
+    const size_t smem = (size_t)RC * maxK * sizeof(T) + (size_t)maxK * sizeof(int);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm_grouped<T, RC, MODE>,
@@ -398,7 +399,7 @@ template cudaError_t launch_gemm_grouped<double>(const GemmArgsT<double> *, cons
 template cudaError_t launch_gemm_grouped<float>(const GemmArgsT<float> *, const int64_t *, int, int64_t, int, int, int,
                                                 int, cudaStream_t);
 
-int sparse_pack(const double *A, int M, int K1, int K2, bool mult3, SparseOp &out) {
+int sparse_pack(const double *A, int M, int K1, int K2, bool mult3, SparseOp &out, int only_rc) {
     out = SparseOp();
     const int K = K1 + K2;
     if (M <= 0 || K <= 0) return 0;
@@ -407,6 +408,7 @@ int sparse_pack(const double *A, int M, int K1, int K2, bool mult3, SparseOp &ou
     int best_rc = 0;
     for (int rc : cand) {
         if (mult3 && rc % 3) continue;
+        if (only_rc && rc != only_rc) continue;
         long fma = 0;
         for (int m0 = 0; m0 < M; m0 += rc) {
             int cnt = 0;

@@ -72,14 +72,15 @@ template <typename T>
 cudaError_t launch_gemm(const GemmArgsT<T> &g, cudaStream_t s);
 // host: chunk-compressed form of a row-major M x (K1 + K2) operator for
 // launch_gemm (see GemmArgsT::sp_*).  Picks the chunk size among the
-// instantiated ones (a multiple of 3 if mult3) that needs the fewest FMAs;
-// returns 0 (use the dense operator) unless that saves at least 20%.
+// instantiated ones (a multiple of 3 if mult3; only only_rc if non-zero)
+// that needs the fewest FMAs; returns 0 (use the dense operator) unless
+// that saves at least 20%.
 struct SparseOp {
     int rc = 0, lmax = 0;
     std::vector<int> off, cols;
     std::vector<double> vals;
 };
-int sparse_pack(const double *A, int M, int K1, int K2, bool mult3, SparseOp &out);
+int sparse_pack(const double *A, int M, int K1, int K2, bool mult3, SparseOp &out, int only_rc = 0);
 // the masked form (chunks of 3 rows, a row mask per listed column): the
 // FMAs executed are exactly the operator's non-zeros; 0 unless that saves
 // at least 20% of the dense FMAs

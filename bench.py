@@ -398,6 +398,24 @@ def tgv_params(precision):
                 precision=precision)
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """The largest x over the ranks of the default process group (x itself
+    for one rank): the step time every rank waited for."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gdofs(world, ndof, seconds_per_step, rhs_per_step=4):
+    """Whole-job throughput: every rank advances its own copy of the
+    workload (weak scaling, replicas), all in the same wall time."""
+    return world * ndof * rhs_per_step / seconds_per_step / 1e9
+
+
 def _tri_area(a, b, c):
     return 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
 
@@ -659,12 +677,8 @@ def main():
     ms_total = ev0.elapsed_time(ev1)
     classes, launches = ctx.profile_read()
     ctx.profile(False)
-    ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * ndof * 4.0 / (ms_step * 1e-3) / 1e9
+    ms_step = max_over_ranks(ms_total / args.steps, world, "cuda")
+    value = job_gdofs(world, ndof, ms_step * 1e-3)
     state_ok = ctx.reduce(stream=sp, check=False)[6] == 0.0
 
     # --- e2e through the C ABI with host buffers ---
@@ -680,12 +694,8 @@ def main():
         ctx.step(dt, 1, sp)
         ctx.get_state(hout, sp)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = world * ndof * 4.0 / e2e_s / 1e9
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
+    e2e_val = job_gdofs(world, ndof, e2e_s)
 
     # --- other precision modes beside the FP64 line (same mesh, same state) ---
     modes = {}

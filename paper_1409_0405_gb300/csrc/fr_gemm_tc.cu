@@ -299,11 +299,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = bars->tmem_base;
     const uint32_t acc_stride = tmem_cols / 2;
 
-    // stages this CTA runs (tiles blockIdx.x, + gridDim.x, ...; nkst each)
+    // stages this CTA runs (tiles blockIdx.x, + gridDim.x, ...; nkst each),
+    // walked with incremental counters: the slot and its phase parity, the
+    // stage within the tile, the tile's columns
     const int64_t nmine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total = nmine * nkst;
-    auto stage_cols = [&](int64_t idx, int64_t &n0, int64_t &n1) {
-        tm.cols(blockIdx.x + (idx / nkst) * gridDim.x, n0, n1);
+    struct Cursor {
+        int q = 0, ks = 0;
+        uint32_t par = 0;
+        int64_t tile, n0 = 0, n1 = 0;
+        __device__ void start(const TileMap &m) {
+            tile = blockIdx.x;
+            m.cols(tile, n0, n1);
+        }
+        __device__ void next(const TileMap &m, int nkst, int nslot) {
+            if (++q == nslot) {
+                q = 0;
+                par ^= 1u;
+            }
+            if (++ks == nkst) {
+                ks = 0;
+                tile += gridDim.x;
+                m.cols(tile, n0, n1);
+            }
+        }
     };
 
     if (warp < kConvWarps) {
@@ -311,13 +330,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // values) of each stage: read them from the slot, wait for every
         // converter to have read, write the bf16 hi/lo of its core-matrix row
         const int r = threadIdx.x & (kTileN - 1), h = threadIdx.x >> 7;
-        for (int64_t idx = 0; idx < total; ++idx) {
-            const int q = (int)(idx % nslot);
-            const uint32_t par = (uint32_t)((idx / nslot) & 1);
+        Cursor cu;
+        cu.start(tm);
+        for (int64_t idx = 0; idx < total; ++idx, cu.next(tm, nkst, nslot)) {
+            const int q = cu.q;
+            const uint32_t par = cu.par;
             if (!mbar_wait(&bars->loaded[q], par, bars, err, 1)) break;
-            int64_t n0, n1;
-            stage_cols(idx, n0, n1);
-            const bool col_ok = n0 + r < n1;
+            const bool col_ok = cu.n0 + r < cu.n1;
             uint8_t *slot = slots + (size_t)q * kStageBytes;
             const float *f = reinterpret_cast<const float *>(slot);
             float cur[8];
@@ -379,12 +398,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // into its slot; stage ks reads B1 rows 16 ks.. (ks < K1pad / 16)
         // or B2 rows 16 ks - K1pad..
         const int n1st = K1pad / kStageK;
-        for (int64_t idx = 0; idx < total; ++idx) {
-            const int q = (int)(idx % nslot);
-            if (!mbar_wait(&bars->freed[q], (uint32_t)(((idx / nslot) & 1) ^ 1), bars, err, 7)) break;
-            int64_t n0, n1;
-            stage_cols(idx, n0, n1);
-            const int ks = (int)(idx % nkst);
+        Cursor cu;
+        cu.start(tm);
+        for (int64_t idx = 0; idx < total; ++idx, cu.next(tm, nkst, nslot)) {
+            const int q = cu.q;
+            if (!mbar_wait(&bars->freed[q], cu.par ^ 1u, bars, err, 7)) break;
+            const int64_t n0 = cu.n0;
+            const int ks = cu.ks;
             const CUtensorMap *tmap = ks < n1st ? &tmB1 : &tmB2;
             const int y = ks < n1st ? ks * kStageK : ks * kStageK - K1pad;
             mbar_expect_tx(&bars->loaded[q], kStageBytes);
@@ -412,16 +432,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Nmma >> 3) << 17) |
                                ((uint32_t)(kTileN >> 4) << 24);
         const uint32_t st_s = smem_u32(slots);
-        int64_t idx = 0;
+        int q = 0;
+        uint32_t qpar = 0;
         int b = 0;
         uint32_t aph = 0;
         for (int64_t tile = blockIdx.x; live && tile < ntiles; tile += gridDim.x) {
             if (!mbar_wait(&bars->acc_empty[b], aph ^ 1u, bars, err, 4)) break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)b * acc_stride;
-            for (int ks = 0; ks < nkst; ++ks, ++idx) {
-                const int q = (int)(idx % nslot);
-                if (!mbar_wait(&bars->converted[q], (uint32_t)((idx / nslot) & 1), bars, err, 5)) {
+            for (int ks = 0; ks < nkst; ++ks) {
+                if (!mbar_wait(&bars->converted[q], qpar, bars, err, 5)) {
                     live = false;
                     break;
                 }
@@ -438,6 +458,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mma_bf16(d, al, bh, idesc, 1);
                 }
                 mma_commit(&bars->freed[q]);
+                if (++q == nslot) {
+                    q = 0;
+                    qpar ^= 1u;
+                }
             }
             if (!live) break;
             mma_commit(&bars->acc_full[b]);

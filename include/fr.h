@@ -153,6 +153,16 @@ int fr_rhs(fr_ctx *ctx, const double *u_dev, double *r_dev, void *cuda_stream);
 int fr_step(fr_ctx *ctx, double dt, int nsteps, void *cuda_stream);
 
 /*
+ * fr_step_ls: nsteps steps of the five-stage fourth-order low-storage
+ * (2N) Runge-Kutta scheme of Carpenter & Kennedy (1994) on the internal
+ * register: per stage dU <- A_i dU + dt R(U), U <- U + B_i dU (the paper
+ * advances with a low-storage scheme of this family; fr_step is classic
+ * RK4).  Same registers and stream semantics as fr_step; 5 RHS per step.
+ * Errors: FR_ERR_ARG (nsteps < 0 or dt NaN), FR_ERR_CUDA.
+ */
+int fr_step_ls(fr_ctx *ctx, double dt, int nsteps, void *cuda_stream);
+
+/*
  * fr_reduce: integrals of the internal solution register.  out (host,
  * caller-owned, 7 doubles) receives sum_e sum_j w_j J_j u_j for the 5
  * conserved variables, the kinetic energy integral, and the number of

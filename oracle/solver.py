@@ -16,12 +16,25 @@ operator application as C <- c1 A B + c2 C, Eq. 1):
 """
 from __future__ import annotations
 
+from fractions import Fraction
+
 import numpy as np
 
 from . import physics
 from .mesh import Mesh
 
 NVARS = 5
+
+# Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage
+# Runge-Kutta: the published rational coefficients (A_i, B_i)
+RK4_2N_FRACTIONS = (
+    (Fraction(0), Fraction(-567301805773, 1357537059087), Fraction(-2404267990393, 2016746695238),
+     Fraction(-3550918686646, 2091501179385), Fraction(-1275806237668, 842570457699)),
+    (Fraction(1432997174477, 9575080441755), Fraction(5161836677717, 13612068292357),
+     Fraction(1720146321549, 2090206949498), Fraction(3134564353537, 4481467310338),
+     Fraction(2277821191437, 14882151754819)))
+RK4_2N_A = [float(x) for x in RK4_2N_FRACTIONS[0]]
+RK4_2N_B = [float(x) for x in RK4_2N_FRACTIONS[1]]
 
 
 class Solver:
@@ -198,6 +211,16 @@ class Solver:
         k3 = self.rhs(u + 0.5 * dt * k2)
         k4 = self.rhs(u + dt * k3)
         return u + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+
+    def rk4_2n_step(self, u, dt):
+        """One step of the five-stage fourth-order low-storage Runge-Kutta
+        scheme of Carpenter & Kennedy (1994, 2N storage):
+        dU <- A_i dU + dt R(U);  U <- U + B_i dU,  i = 1..5 (A_1 = 0)."""
+        du = np.zeros_like(u)
+        for a, b in zip(RK4_2N_A, RK4_2N_B):
+            du = a * du + dt * self.rhs(u)
+            u = u + b * du
+        return u
 
     def integrals(self, u_flat):
         """sum_e sum_j w_j J_j u_j per conserved variable."""

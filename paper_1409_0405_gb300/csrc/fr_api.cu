@@ -663,6 +663,50 @@ int step_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
     return FR_OK;
 }
 
+// Five-stage fourth-order low-storage Runge-Kutta (Carpenter & Kennedy
+// 1994, 2N storage): dU <- A_i dU + dt R(U); U <- U + B_i dU.  The RHS of
+// each stage is stored (R) and a streaming pass applies the update; dU
+// lives in the Uacc register.
+constexpr double kRk2nA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                              -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+constexpr double kRk2nB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                              1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                              2277821191437.0 / 14882151754819.0};
+
+template <typename T>
+int step_2n_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
+    if (nsteps <= 0) return FR_OK;
+    const Phys ph = phys_of(c);
+    int rc;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_center<T>(D.nu, D.np, D.U, (T *)D.Us, ph.uref, s), "centre"))) return rc;
+    }
+    for (int it = 0; it < nsteps; ++it)
+        for (int st = 0; st < 5; ++st) {
+            T *in[2] = {nullptr, nullptr};
+            for (int t = 0; t < 2; ++t)
+                if (c->T[t].present) in[t] = (T *)c->T[t].Us;
+            if ((rc = rhs_internal<T>(c, in, nullptr, s))) return rc;
+            for (int t = 0; t < 2; ++t) {
+                DevType &D = c->T[t];
+                if (!D.present) continue;
+                if ((rc = cuda_check(launch(c, K_DIV, s,
+                                            [&] {
+                                                return launch_rk_2n_update<T>(D.nu, D.np, (const T *)D.R, D.U, D.Uacc,
+                                                                              (T *)D.Us, ph.uref, kRk2nA[st],
+                                                                              kRk2nB[st], dt, st == 0, s);
+                                            }),
+                                     "2N update")))
+                    return rc;
+            }
+        }
+    return FR_OK;
+}
+
+template int step_2n_impl<float>(fr_ctx *, double, int, cudaStream_t);
+template int step_2n_impl<double>(fr_ctx *, double, int, cudaStream_t);
 template int step_impl<float>(fr_ctx *, double, int, cudaStream_t);
 template int rhs_public<float>(fr_ctx *, const double *, double *, cudaStream_t);
 template int rhs_public<double>(fr_ctx *, const double *, double *, cudaStream_t);
@@ -850,6 +894,12 @@ int fr_step(fr_ctx *c, double dt, int nsteps, void *stream) {
     if (!c || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
     cudaStream_t s = (cudaStream_t)stream;
     return is_f32(c) ? step_impl<float>(c, dt, nsteps, s) : step_impl<double>(c, dt, nsteps, s);
+}
+
+int fr_step_ls(fr_ctx *c, double dt, int nsteps, void *stream) {
+    if (!c || nsteps < 0 || !(dt == dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    return is_f32(c) ? step_2n_impl<float>(c, dt, nsteps, s) : step_2n_impl<double>(c, dt, nsteps, s);
 }
 
 int fr_reduce(fr_ctx *c, double *out, void *stream) {

@@ -222,6 +222,11 @@ cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const doub
 template <typename T>
 cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
                              double c_acc, double c_stage, int first, int last, cudaStream_t s);
+// low-storage (2N) RK stage: dU = a dU + dt R (dU unread when first),
+// U += b dU, Us = U - uref; R [nu][V][np]
+template <typename T>
+cudaError_t launch_rk_2n_update(int nu, int64_t np, const T *R, double *U, double *dU, T *Us, const double *uref,
+                                double a, double b, double dt, int first, cudaStream_t s);
 // element-wise double -> float copy
 cudaError_t launch_to_float(int64_t n, const double *src, float *dst, cudaStream_t s);
 // per-block partial integrals (7 per block) of one type's register

@@ -507,6 +507,21 @@ __global__ void k_rk_update(int64_t n, int64_t np, const T *__restrict__ R, doub
     }
 }
 
+// low-storage (2N) Runge-Kutta stage from a stored RHS r:
+// dU = a dU + dt r (dU not read when first), U += b dU, Us = U - uref
+template <typename T>
+__global__ void k_rk_2n_update(int64_t n, int64_t np, const T *__restrict__ R, double *__restrict__ U,
+                               double *__restrict__ dU, T *__restrict__ Us, const Uref uref, double a, double b,
+                               double dt, int first) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const double du = (first ? 0.0 : a * dU[idx]) + dt * (double)R[idx];
+    const double u = U[idx] + b * du;
+    dU[idx] = du;
+    U[idx] = u;
+    Us[idx] = T(u - uref.v[(idx / np) % V]);
+}
+
 __global__ void k_to_float(int64_t n, const double *__restrict__ src, float *__restrict__ dst) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n) dst[idx] = (float)src[idx];
@@ -600,6 +615,16 @@ cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_rk_2n_update(int nu, int64_t np, const T *R, double *U, double *dU, T *Us, const double *uref,
+                                double a, double b, double dt, int first, cudaStream_t s) {
+    const int64_t n = (int64_t)nu * V * np;
+    if (n == 0) return cudaSuccess;
+    Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
+    k_rk_2n_update<T><<<blocks_for(n, 256), 256, 0, s>>>(n, np, R, U, dU, Us, r, a, b, dt, first);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_float(int64_t n, const double *src, float *dst, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_to_float<<<blocks_for(n, 256), 256, 0, s>>>(n, src, dst);
@@ -650,6 +675,8 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
     template cudaError_t launch_center<T>(int, int64_t, const double *, T *, const double *, cudaStream_t);     \
     template cudaError_t launch_rk_update<T>(int, int64_t, const T *, double *, double *, T *, const double *,   \
                                              double, double, int, int, cudaStream_t);                        \
+    template cudaError_t launch_rk_2n_update<T>(int, int64_t, const T *, double *, double *, T *,                \
+                                                const double *, double, double, double, int, cudaStream_t);  \
     template cudaError_t launch_int_to_pub<T>(int, int64_t, int64_t, const T *, double *, cudaStream_t);       \
     template cudaError_t launch_flux_grouped<T>(const FluxItem<T> *, const int64_t *, int, int64_t, const Phys &, \
                                                 int, cudaStream_t);                                           \

@@ -33,7 +33,7 @@ OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
 
 # every entry point declared in include/fr.h
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
-           "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_reduce",
+           "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_step_ls", "fr_reduce",
            "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info",
@@ -87,6 +87,8 @@ def load():
     lib.fr_get_state.argtypes = [vp, dp, vp]
     lib.fr_rhs.argtypes = [vp, vp, vp, vp]
     lib.fr_step.argtypes = [vp, C.c_double, C.c_int, vp]
+    lib.fr_step_ls.argtypes = [vp, C.c_double, C.c_int, vp]
+    lib.fr_step_ls.restype = C.c_int
     lib.fr_reduce.argtypes = [vp, dp, vp]
     lib.fr_operator.argtypes = [C.c_int, C.c_int, C.c_int, dp, i64p, i64p]
     lib.fr_profile.argtypes = [vp, C.c_int]
@@ -333,6 +335,10 @@ class Context:
     def step(self, dt, nsteps=1, stream=None):
         _check(self._lib.fr_step(self._h, float(dt), int(nsteps),
                                  C.c_void_p(stream) if stream else None))
+
+    def step_ls(self, dt, nsteps=1, stream=None):
+        """Low-storage (2N) five-stage RK4 steps (fr_step_ls)."""
+        _check(self._lib.fr_step_ls(self._h, float(dt), int(nsteps), C.c_void_p(stream) if stream else None))
 
     def profile(self, enable=True):
         _check(self._lib.fr_profile(self._h, int(bool(enable))))

@@ -381,3 +381,28 @@ def test_trained_closure_reduces_rhs_error():
     for et in (0, 1):
         assert log[et][-1] < 0.2 * log[et][0]
         assert err[et][0] < 0.5, (et, err[et])
+
+
+# ---------------------------------------------------------------------------
+# p-sequenced restart: prolongation through the same transfer
+# ---------------------------------------------------------------------------
+def test_prolongation_restart_matches_oracle(tgv4):
+    """A p=2 state prolonged to p=4 (fr_transfer_state, lower to higher
+    order) equals the oracle's L2 projection (exact for the p=2 polynomial),
+    projects back unchanged, and the p=4 solver runs from it (an RHS that
+    matches the oracle's on the prolonged state)."""
+    s4, c4, s2, c2, u4 = tgv4
+    u2 = OC.restrict_state(s4, s2, u4)
+    a2 = s2.split(u2)
+    ref = s4.join({t: a2[t] @ OC.restriction(t, 2, 4).T for t in s4.types})
+    up = torch.zeros(c4.ndof, dtype=torch.float64, device="cuda")
+    c4.transfer_from(c2, _dev(u2).data_ptr(), up.data_ptr())
+    got = _host(up)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
+    back = torch.zeros(c2.ndof, dtype=torch.float64, device="cuda")
+    c2.transfer_from(c4, up.data_ptr(), back.data_ptr())
+    np.testing.assert_allclose(_host(back), u2, rtol=0, atol=1e-13 * np.max(np.abs(u2)))
+    r = torch.zeros_like(up)
+    c4.rhs(up.data_ptr(), r.data_ptr())
+    err = _cases.per_quantity_rel_err(s4, s4.rhs(got), _host(r))
+    assert np.all(err < 1e-12), err

@@ -113,6 +113,33 @@ def test_vortex_rk4_100_steps():
     np.testing.assert_allclose(out[:5], sol.integrals(u), rtol=1e-12, atol=1e-9)
 
 
+def test_vortex_low_storage_rk_steps():
+    """fr_step_ls (five-stage 2N Runge-Kutta) against the oracle's scheme:
+    the vortex (Euler) for 20 steps and the boundary layer (NS) for 3."""
+    sol, ctx = make_pair(synth.vortex_box(), 2)
+    u = state(sol, "vortex")
+    dt = sol.dt_cfl(u, 0.1)
+    ctx.set_state(u)
+    ctx.step_ls(dt, 20)
+    ref = u
+    for _ in range(20):
+        ref = sol.rk4_2n_step(ref, dt)
+    err = per_quantity_rel_err(sol, ref, ctx.get_state())
+    assert np.all(err <= TOL), err
+    np.testing.assert_allclose(ctx.reduce()[:5], sol.integrals(u), rtol=1e-12, atol=1e-9)
+    m = synth.boundary_layer_box(nx=6, nz=3, n_prism_layers=4, n_tet_layers=3)
+    sol, ctx = make_pair(m, 3, **bl_params(mu=0.01))
+    u = state(sol, "bl")
+    dt = 0.2 * sol.dt_cfl(u, 0.1)
+    ctx.set_state(u)
+    ctx.step_ls(dt, 3)
+    ref = u
+    for _ in range(3):
+        ref = sol.rk4_2n_step(ref, dt)
+    err = per_quantity_rel_err(sol, ref, ctx.get_state())
+    assert np.all(err <= TOL), err
+
+
 def test_ns_boundary_layer_rk4_steps():
     m = synth.boundary_layer_box(nx=6, nz=3, n_prism_layers=4, n_tet_layers=3)
     sol, ctx = make_pair(m, 3, **bl_params(mu=0.01))

@@ -400,3 +400,54 @@ def test_rk4_amplification(monkeypatch):
     z = lam * dt
     np.testing.assert_allclose(s.rk4_step(u, dt), u * (1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24),
                                rtol=1e-15)
+
+
+def test_rk4_2n_amplification_matches_exp_to_fourth_order():
+    """The 2N scheme applied to y' = z y in exact rational arithmetic: its
+    amplification polynomial R(z) (degree 5) agrees with exp(z) through z^4,
+    i.e. the coefficients satisfy the four order conditions of a linear
+    autonomous problem (a mistyped digit anywhere breaks them)."""
+    from fractions import Fraction
+    from math import factorial
+    from oracle.solver import RK4_2N_FRACTIONS
+    A, B = RK4_2N_FRACTIONS
+
+    def shift(poly):             # multiply by z
+        return [Fraction(0)] + poly
+
+    def add(p, q):
+        n = max(len(p), len(q))
+        p = p + [Fraction(0)] * (n - len(p))
+        q = q + [Fraction(0)] * (n - len(q))
+        return [a + b for a, b in zip(p, q)]
+
+    y, du = [Fraction(1)], [Fraction(0)]
+    for a, b in zip(A, B):
+        du = add([a * c for c in du], shift(y))
+        y = add(y, [b * c for c in du])
+    for k in range(5):
+        assert abs(float(y[k] - Fraction(1, factorial(k)))) < 1e-12, k
+    # the z^5 term differs from 1/120 (five stages, order four)
+    assert abs(float(y[5]) - 1.0 / 120.0) > 1e-6
+
+
+def test_rk4_2n_step_order_on_a_scalar_ode():
+    """The oracle's step on y' = -y^2 (exact 1/(1+t)): the error falls with
+    dt^4."""
+    from oracle.solver import RK4_2N_A, RK4_2N_B
+
+    def step(y, dt):
+        du = 0.0
+        for a, b in zip(RK4_2N_A, RK4_2N_B):
+            du = a * du + dt * (-y * y)
+            y = y + b * du
+        return y
+
+    errs = []
+    for n in (10, 20, 40):
+        y, dt = 1.0, 1.0 / n
+        for _ in range(n):
+            y = step(y, dt)
+        errs.append(abs(y - 0.5))
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 3.8, rates

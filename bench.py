@@ -720,6 +720,11 @@ def main():
         fp64_peak_meas = fr.peak_fp64(sp)
     except Exception:
         fp64_peak_meas = None
+    # DRAM bytes per launch of the FP64 gradient class, from an ncu capture
+    # (dram__bytes_read + dram__bytes_write) of the same kernels on the
+    # nx=15 case (tet 466 MB, prism 481 MB per launch), scaled by the 5x
+    # element count of the full workload; valid while the kernel is unchanged
+    traffic_fp64_grad = 0.5 * (466.2e6 + 480.9e6) * 5
     if dom in ("M0", "grad", "M0_grad", "div") and prec != fr.FR_FP64:
         byts = gemm_bytes_f32(ctx, dom) * 4 * args.steps
         achieved = byts / (dom_ms * 1e-3) / 1e9
@@ -732,7 +737,8 @@ def main():
         flops = gemm_flops(ctx, dom) * 4 * args.steps  # per RHS x 4 RHS per step
         achieved = flops / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": fp64_peak_derived / 1e3,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak_derived, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak_derived,
+                "traffic": traffic_fp64_grad if (dom == "grad" and args.nx == 75) else None,
                 "kernel": f"k_gemm ({dom})", "launches": dom_n,
                 "avg_launch_ms": dom_ms / max(dom_n, 1),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",

@@ -319,7 +319,7 @@ def precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, precision, args, sp):
     byts = gemm_bytes_f32(ctx, dom) * 4 * args.steps
     ach = byts / (classes[dom][0] * 1e-3) / 1e9
     peak = measured_peaks().get("hbm_gbs", 6800.0)
-    out["roofline"] = {"bound": "hbm", "kernel": ("k_gemm_tc" if precision == fr.FR_BF16X3 else "k_gemm")
+    out["roofline"] = {"bound": "hbm", "kernel": ("k_gemm_tc" if precision in (fr.FR_BF16X3, fr.FR_TF32X3) else "k_gemm")
                        + f" ({dom})", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                        "traffic": None, "launches": classes[dom][1],
                        "avg_launch_ms": classes[dom][0] / max(classes[dom][1], 1),
@@ -588,7 +588,7 @@ def main():
                     help="cells along x (75 = the full workload; smaller for profiling)")
     ap.add_argument("--cpu-oracle-child", type=int, default=0)
     ap.add_argument("--fp64-only", action="store_true", help="skip the other modes (precision, batched, learned)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3", "tf32x3"],
                     help="arithmetic of the main timed step (default fp64, the headline workload)")
     args = ap.parse_args()
 
@@ -643,7 +643,7 @@ def main():
             torch.distributed.barrier()
 
     mesh = synth.boundary_layer_box(nx=args.nx)
-    prec = {"fp64": fr.FR_FP64, "fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3}[args.precision]
+    prec = {"fp64": fr.FR_FP64, "fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3, "tf32x3": fr.FR_TF32X3}[args.precision]
     ctx = fr.Context(mesh, ORDER, **flow_params(), precision=prec)
     counts = [(ctx.info["n_tet"], ctx.info["nu_tet"]), (ctx.info["n_pri"], ctx.info["nu_pri"])]
     u0 = points_to_public(synth.perturbed_freestream(ctx.upts_points(), seed=2,
@@ -702,6 +702,7 @@ def main():
     if not args.fp64_only and args.precision == "fp64":
         modes["fp32"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_FP32, args, sp)
         modes["bf16x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_BF16X3, args, sp)
+        modes["tf32x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_TF32X3, args, sp)
         if args.nx == 75:
             modes["batched"] = batch_mode(fr, torch, args, sp)
             modes["learned"] = learned_mode(fr, torch, args, sp)
@@ -730,7 +731,8 @@ def main():
         achieved = byts / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
                 "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
-                "kernel": ("k_gemm_tc" if prec == fr.FR_BF16X3 else "k_gemm") + f" ({dom})", "launches": dom_n,
+                "kernel": ("k_gemm_tc" if prec in (fr.FR_BF16X3, fr.FR_TF32X3) else "k_gemm") + f" ({dom})",
+                "launches": dom_n,
                 "avg_launch_ms": dom_ms / max(dom_n, 1),
                 "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     elif dom in ("M0", "grad", "M0_grad", "div"):
@@ -752,7 +754,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3+f32"}[args.precision],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3+f32", "tf32x3": "tf32x3+f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": (WORKLOAD if args.nx == 75 else WORKLOAD + f" (reduced: nx={args.nx})")
                    + ("" if args.precision == "fp64" else f" [{args.precision} arithmetic]"),

@@ -52,7 +52,7 @@ enum {
     FR_ERR_MESH = -2,       /* J <= 0, unmatched or non-conforming face, bad tag */
     FR_ERR_CUDA = -3,       /* a CUDA runtime call failed */
     FR_ERR_NONFINITE = -4,  /* NaN/Inf or non-positive density/pressure found */
-    FR_ERR_TIMEOUT = -5,    /* a bounded device wait gave up (FR_BF16X3 kernels) */
+    FR_ERR_TIMEOUT = -5,    /* a bounded device wait gave up (tensor-core kernels) */
     FR_ERR_NOMEM = -6,      /* host or device allocation failed */
     FR_ERR_UNSUPPORTED = -7 /* valid request this build does not implement */
 };
@@ -60,10 +60,10 @@ enum {
 enum { FR_ETYPE_TET = 0, FR_ETYPE_PRI = 1 };
 enum { FR_BC_WALL = 1, FR_BC_FARFIELD = 2 };
 /* Arithmetic of the operator applications (Table 1: single and double;
- * FR_BF16X3: FP32 storage with the operator applications on the tensor
- * cores in split BF16, x = bf16(x) + bf16(x - bf16(x)), three products per
- * pair and FP32 accumulation). */
-enum { FR_FP64 = 0, FR_FP32 = 1, FR_BF16X3 = 2 };
+ * FR_BF16X3 / FR_TF32X3: FP32 storage with the operator applications on the
+ * tensor cores in split BF16 or split TF32, x = r(x) + r(x - r(x)), three
+ * products per pair and FP32 accumulation). */
+enum { FR_FP64 = 0, FR_FP32 = 1, FR_BF16X3 = 2, FR_TF32X3 = 3 };
 
 typedef struct fr_ctx fr_ctx; /* opaque; owned by the library */
 
@@ -92,8 +92,9 @@ typedef struct {
                          work in FP32; RK registers and the reductions stay
                          FP64 (the FP64 reference-flux correction, ~1e-11,
                          is below FP32 resolution and skipped); or
-                         FR_BF16X3: as FR_FP32 with the operator applications
-                         on the tensor cores (split BF16, FP32 accumulate) */
+                         FR_BF16X3 / FR_TF32X3: as FR_FP32 with the operator
+                         applications on the tensor cores (split BF16 or
+                         split TF32, FP32 accumulate) */
     double rho_inf;   /* far-field density */
     double vel_inf[3];/* far-field velocity */
     double p_inf;     /* far-field pressure */

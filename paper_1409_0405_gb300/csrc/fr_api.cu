@@ -277,13 +277,13 @@ cudaError_t op_gemm<double>(fr_ctx *c, int t, int which, const GemmArgsT<double>
 
 template <>
 cudaError_t op_gemm<float>(fr_ctx *c, int t, int which, const GemmArgsT<float> &g, cudaStream_t s) {
-    if (c->prm.precision == FR_BF16X3) return launch_gemm_tc(g, c->T[t].tc[which], c->tc_err, s);
+    if (is_tc(c)) return launch_gemm_tc(g, c->T[t].tc[which], c->tc_err, s);
     return launch_gemm<float>(with_sparse<float>(c, t, which, g), s);
 }
 
 // FR_ERR_TIMEOUT if a tensor-core kernel gave up a wait (synchronises)
 int check_tc(fr_ctx *c) {
-    if (c->prm.precision != FR_BF16X3 || !c->tc_err) return FR_OK;
+    if (!is_tc(c) || !c->tc_err) return FR_OK;
     int h = 0;
     int rc = cuda_check(cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
     if (rc) return rc;
@@ -348,10 +348,10 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
         return rc;
     // 7. divergence plus correction; with the learned closure on, the
     // network's correction is added by the epilogue with the reference term
-    // In FR_BF16X3 the tensor-core GEMM stores R and a streaming pass applies
+    // With the tensor cores the GEMM stores R and a streaming pass applies
     // the RK update (its FP64 register traffic would otherwise stall the
     // GEMM's epilogue warps).
-    const bool split_rk = rk && c->prm.precision == FR_BF16X3;
+    const bool split_rk = rk && is_tc(c);
     for (int t = 0; t < 2; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
@@ -392,8 +392,8 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         return set_err(FR_ERR_ARG, "null connectivity array");
     if (mesh->n_tet > (1LL << 30) || mesh->n_pri > (1LL << 30))
         return set_err(FR_ERR_ARG, "element count too large");
-    if (prm->precision != FR_FP64 && prm->precision != FR_FP32 && prm->precision != FR_BF16X3)
-        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64, FR_FP32 or FR_BF16X3");
+    if (prm->precision < FR_FP64 || prm->precision > FR_TF32X3)
+        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64, FR_FP32, FR_BF16X3 or FR_TF32X3");
     if (!(prm->gamma > 1.0) || prm->mu < 0.0 || (prm->viscous && !(prm->prandtl > 0.0)))
         return set_err(FR_ERR_ARG, "invalid gas parameters");
     c->prm = *prm;
@@ -452,24 +452,33 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             (rc = upload(c, &D.M0, ops[t].M0)) || (rc = upload(c, &D.AGRAD, ops[t].AGRAD)) ||
             (rc = upload(c, &D.ADIV, ops[t].ADIV)))
             return rc;
-        if (prm->precision == FR_BF16X3) {
+        if (prm->precision == FR_BF16X3 || prm->precision == FR_TF32X3) {
             // the three operators packed for the tensor cores
             const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
             const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok1[3] = {D.nu, D.nu, 3 * D.nu}, ok2[3] = {0, D.nf, D.nf};
             for (int w = 0; w < 3; ++w) {
-                std::vector<uint16_t> img;
                 TcOperator &op = D.tc[w];
-                tc_pack(opv[w]->data(), om[w], ok1[w], ok2[w], img, op.Nmma, op.K1pad, op.Kpad);
+                op.tf32 = prm->precision == FR_TF32X3;
+                if (op.tf32) {
+                    std::vector<uint32_t> img;
+                    tc_pack_tf32(opv[w]->data(), om[w], ok1[w], ok2[w], img, op.Nmma, op.K1pad, op.Kpad);
+                    uint32_t *dimg = nullptr;
+                    if ((rc = upload(c, &dimg, img))) return rc;
+                    op.img = (const uint8_t *)dimg;
+                } else {
+                    std::vector<uint16_t> img;
+                    tc_pack(opv[w]->data(), om[w], ok1[w], ok2[w], img, op.Nmma, op.K1pad, op.Kpad);
+                    uint16_t *dimg = nullptr;
+                    if ((rc = upload(c, &dimg, img))) return rc;
+                    op.img = (const uint8_t *)dimg;
+                }
                 op.M = om[w];
                 op.K = ok1[w] + ok2[w];
                 if (op.Nmma > 256 || tc_stages(op) < 2)
                     return set_err(FR_ERR_UNSUPPORTED, "operator too large for the tensor-core kernel");
-                uint16_t *dimg = nullptr;
-                if ((rc = upload(c, &dimg, img))) return rc;
-                op.img = (const uint8_t *)dimg;
             }
         }
-        if (prm->precision != FR_BF16X3) {
+        if (prm->precision == FR_FP64 || prm->precision == FR_FP32) {
             // the operators' exact zeros skipped chunk by chunk (prisms)
             const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
             const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok1[3] = {D.nu, D.nu, 3 * D.nu}, ok2[3] = {0, D.nf, D.nf};

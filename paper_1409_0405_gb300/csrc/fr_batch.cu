@@ -540,7 +540,7 @@ extern "C" {
 int fr_batch_create(int nprob, const fr_mesh *meshes, const int *orders, const fr_params *params, fr_batch **out) {
     if (!out || nprob <= 0 || !meshes || !orders || !params) return set_err(FR_ERR_ARG, "invalid batch arguments");
     *out = nullptr;
-    if (params->precision == FR_BF16X3)
+    if (params->precision != FR_FP64 && params->precision != FR_FP32)
         return set_err(FR_ERR_UNSUPPORTED, "batched launches run FR_FP64 or FR_FP32 operator kernels");
     fr_batch *b = new (std::nothrow) fr_batch();
     if (!b) return set_err(FR_ERR_NOMEM, "host allocation");

@@ -43,7 +43,8 @@ struct DevType {
     float *cl_P = nullptr, *cl_X = nullptr, *cl_Y = nullptr, *cl_ws = nullptr;
     double *cl_add = nullptr;
     int64_t cl_cap_nh = 0;  // hidden width the buffers were sized for
-    // FR_BF16X3: the packed operators M0, AGRAD, ADIV for the tensor cores
+    // FR_BF16X3 / FR_TF32X3: the packed operators M0, AGRAD, ADIV for the
+    // tensor cores
     fr::TcOperator tc[3];
     // FR_FP64 / FR_FP32: chunk-compressed M0, AGRAD, ADIV (sp_rc 0: dense)
     int sp_rc[3] = {0, 0, 0}, sp_lmax[3] = {0, 0, 0}, sp_masked[3] = {0, 0, 0};
@@ -62,7 +63,7 @@ struct fr_ctx {
     int *bt = nullptr, *bf = nullptr, *be = nullptr, *btag = nullptr;
     double *bn = nullptr, *bmag = nullptr;
     double *red = nullptr;  // reduction partials + result
-    int *tc_err = nullptr;  // FR_BF16X3: set by a tensor-core kernel whose bounded wait gave up
+    int *tc_err = nullptr;  // set by a tensor-core kernel whose bounded wait gave up
     int red_blocks[2] = {0, 0};
     std::vector<void *> allocs;
     // launch accounting: count of kernel launches, and (when profiling is
@@ -114,13 +115,15 @@ cudaError_t launch(fr_ctx *c, int kclass, cudaStream_t s, F fn, int nk = 1) {
     return e;
 }
 int64_t ndof_of(const fr_ctx *c);
-// FP32 storage (FR_FP32, FR_BF16X3) rather than FP64
+// FP32 storage (FR_FP32, FR_BF16X3, FR_TF32X3) rather than FP64
 inline bool is_f32(const fr_ctx *c) { return c->prm.precision != FR_FP64; }
+// operator applications on the tensor cores (FR_BF16X3, FR_TF32X3)
+inline bool is_tc(const fr_ctx *c) { return c->prm.precision == FR_BF16X3 || c->prm.precision == FR_TF32X3; }
 // operator application `which` (0 M0, 1 AGRAD, 2 ADIV) of element type t:
-// the tensor-core kernel in FR_BF16X3, else the FMA kernel
+// the tensor-core kernel in FR_BF16X3 / FR_TF32X3, else the FMA kernel
 template <typename T>
 cudaError_t op_gemm(fr_ctx *c, int t, int which, const GemmArgsT<T> &g, cudaStream_t s);
-// FR_FP32 and FR_BF16X3 contexts keep every RHS buffer in float
+// the FP32-storage contexts keep every RHS buffer in float
 template <typename T>
 inline bool type_matches(const fr_ctx *c) { return is_f32(c) == (sizeof(T) == sizeof(float)); }
 Phys phys_of(const fr_ctx *c);

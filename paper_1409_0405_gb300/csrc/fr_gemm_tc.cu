@@ -136,6 +136,22 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
         : "memory");
 }
 
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// FP32 -> TF32 (10 stored mantissa bits), round half away from zero; the
+// low 13 bits cleared (what the tensor core reads of a 32-bit operand)
+__device__ __forceinline__ float tf32_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
                  : "memory");
@@ -255,16 +271,24 @@ struct TileMap {
     }
 };
 
-template <int MODE>
+// TF = false: split BF16, the operator image resident in shared memory,
+// slot = 8 KB (FP32 box, then bf16 hi | lo).  TF = true: split TF32 (4-byte
+// halves, MMA K step 8), slot = 16 KB (FP32 box, then tf32 hi | lo) plus
+// the stage's operator slab (Nmma x 16 x (hi, lo) x 4 B), streamed with the
+// state because the largest split-TF32 operators do not fit beside a ring.
+template <int MODE, bool TF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const GemmArgsT<float> g, const TileMap tm, const __grid_constant__ CUtensorMap tmB1,
               const __grid_constant__ CUtensorMap tmB2, const uint8_t *__restrict__ opimg, int Nmma, int K1pad,
               int Kpad, int nslot, uint32_t tmem_cols, int *err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    const uint32_t op_half = (uint32_t)Nmma * (uint32_t)Kpad * 2u;  // bytes of hi (or lo)
+    const uint32_t op_half = TF ? 0u : (uint32_t)Nmma * (uint32_t)Kpad * 2u;  // resident image: bytes of hi (lo)
     const uint32_t op_bytes = 2u * op_half;
+    const uint32_t state_bytes = TF ? 16384u : (uint32_t)kStageBytes;
+    const uint32_t slab_bytes = TF ? (uint32_t)Nmma * 128u : 0u;
+    const uint32_t slot_bytes = state_bytes + slab_bytes;
     uint8_t *slots = smem + op_bytes;
-    Bars *bars = reinterpret_cast<Bars *>(slots + (size_t)nslot * kStageBytes);
+    Bars *bars = reinterpret_cast<Bars *>(slots + (size_t)nslot * slot_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = tm.ept * tm.nvb;
     const int nkst = Kpad / kStageK;
@@ -337,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t par = cu.par;
             if (!mbar_wait(&bars->loaded[q], par, bars, err, 1)) break;
             const bool col_ok = cu.n0 + r < cu.n1;
-            uint8_t *slot = slots + (size_t)q * kStageBytes;
+            uint8_t *slot = slots + (size_t)q * slot_bytes;
             const float *f = reinterpret_cast<const float *>(slot);
             float cur[8];
 #pragma unroll
@@ -346,19 +370,37 @@ __global__ void __launch_bounds__(kThreads, 1)
             // mbarrier, so that this wait is bounded like every other)
             mbar_arrive(&bars->read[q]);
             if (!mbar_wait(&bars->read[q], par, bars, err, 8)) break;
-            uint32_t hw[4], lw[4];
+            if constexpr (TF) {
+                // tf32 core matrices: 8 rows x 4 values; K half h is the
+                // two core matrices 2h, 2h+1 of row group r/8 (512 B apart)
+                float hv[8], lv[8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(cur[2 * i]), h1 = __float2bfloat16_rn(cur[2 * i + 1]);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(cur[2 * i] - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(cur[2 * i + 1] - __bfloat162float(h1));
-                hw[i] = pack2(h0, h1);
-                lw[i] = pack2(l0, l1);
+                for (int i = 0; i < 8; ++i) {
+                    hv[i] = tf32_round(cur[i]);
+                    lv[i] = tf32_round(cur[i] - hv[i]);
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const uint32_t off = (uint32_t)(r >> 3) * 512u + (uint32_t)(2 * h + c) * 128u + (uint32_t)(r & 7) * 16u;
+                    *reinterpret_cast<float4 *>(slot + off) = make_float4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
+                    *reinterpret_cast<float4 *>(slot + 8192 + off) =
+                        make_float4(lv[4 * c], lv[4 * c + 1], lv[4 * c + 2], lv[4 * c + 3]);
+                }
+            } else {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(cur[2 * i]), h1 = __float2bfloat16_rn(cur[2 * i + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(cur[2 * i] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(cur[2 * i + 1] - __bfloat162float(h1));
+                    hw[i] = pack2(h0, h1);
+                    lw[i] = pack2(l0, l1);
+                }
+                // row r: core matrix (r/8, K half h), row r%8
+                const uint32_t off = (uint32_t)(r >> 3) * 256u + (uint32_t)h * 128u + (uint32_t)(r & 7) * 16u;
+                *reinterpret_cast<uint4 *>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(slot + 4096 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
-            // row r: core matrix (r/8, K half h), row r%8
-            const uint32_t off = (uint32_t)(r >> 3) * 256u + (uint32_t)h * 128u + (uint32_t)(r & 7) * 16u;
-            *reinterpret_cast<uint4 *>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4 *>(slot + 4096 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             fence_async_smem();
             mbar_arrive(&bars->converted[q]);
         }
@@ -407,29 +449,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ks = cu.ks;
             const CUtensorMap *tmap = ks < n1st ? &tmB1 : &tmB2;
             const int y = ks < n1st ? ks * kStageK : ks * kStageK - K1pad;
-            mbar_expect_tx(&bars->loaded[q], kStageBytes);
+            uint8_t *slot = slots + (size_t)q * slot_bytes;
+            mbar_expect_tx(&bars->loaded[q], (uint32_t)kStageBytes + slab_bytes);
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-                    "r"(smem_u32(slots + (size_t)q * kStageBytes)),
+                    "r"(smem_u32(slot)),
                 "l"(reinterpret_cast<uint64_t>(tmap)), "r"((int)n0), "r"(y), "r"(smem_u32(&bars->loaded[q]))
                 : "memory");
+            if constexpr (TF) {
+                // the stage's operator slab (stage-major image)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(slot + state_bytes)),
+                    "l"(opimg + (size_t)ks * slab_bytes), "r"(slab_bytes), "r"(smem_u32(&bars->loaded[q]))
+                    : "memory");
+            }
         }
     } else if (warp == kMmaWarp && lane == 0) {
         // ---- operator load, then the MMA issue loop
         const uint32_t op_s = smem_u32(smem);
-        mbar_expect_tx(&bars->op_full, op_bytes);
-        for (uint32_t off = 0; off < op_bytes; off += 32768u) {
-            const uint32_t sz = op_bytes - off < 32768u ? op_bytes - off : 32768u;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    op_s + off),
-                "l"(opimg + off), "r"(sz), "r"(smem_u32(&bars->op_full))
-                : "memory");
+        bool live = true;
+        if constexpr (!TF) {
+            mbar_expect_tx(&bars->op_full, op_bytes);
+            for (uint32_t off = 0; off < op_bytes; off += 32768u) {
+                const uint32_t sz = op_bytes - off < 32768u ? op_bytes - off : 32768u;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        op_s + off),
+                    "l"(opimg + off), "r"(sz), "r"(smem_u32(&bars->op_full))
+                    : "memory");
+            }
+            live = mbar_wait(&bars->op_full, 0, bars, err, 3);
         }
-        bool live = mbar_wait(&bars->op_full, 0, bars, err, 3);
-        // kind::f16: D F32 (bit 4), A and B BF16 (bits 7, 10), K-major,
-        // N >> 3 at bit 17, M >> 4 at bit 24
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Nmma >> 3) << 17) |
+        // D F32 (bit 4); A and B BF16 (1 at bits 7, 10, kind::f16) or TF32
+        // (2, kind::tf32); K-major; N >> 3 at bit 17, M >> 4 at bit 24
+        const uint32_t fmt = TF ? 2u : 1u;
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(Nmma >> 3) << 17) |
                                ((uint32_t)(kTileN >> 4) << 24);
         const uint32_t st_s = smem_u32(slots);
         int q = 0;
@@ -446,8 +501,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                {
-                    const uint32_t a_hi = st_s + (uint32_t)q * kStageBytes;
+                if constexpr (TF) {
+                    // two K steps of 8; core matrices 128 B apart along K,
+                    // row groups 512 B apart; the slab's lo half after its hi
+                    const uint32_t sl = st_s + (uint32_t)q * slot_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t a_hi = sl + (uint32_t)kk * 256u, a_lo = a_hi + 8192u;
+                        const uint32_t b_hi = sl + state_bytes + (uint32_t)kk * 256u;
+                        const uint32_t b_lo = b_hi + (uint32_t)Nmma * 64u;
+                        const uint64_t ah = sdesc(a_hi, 128, 512), al = sdesc(a_lo, 128, 512);
+                        const uint64_t bh = sdesc(b_hi, 128, 512), bl = sdesc(b_lo, 128, 512);
+                        mma_tf32(d, ah, bh, idesc, (ks | kk) != 0);
+                        mma_tf32(d, ah, bl, idesc, 1);
+                        mma_tf32(d, al, bh, idesc, 1);
+                    }
+                } else {
+                    const uint32_t a_hi = st_s + (uint32_t)q * slot_bytes;
                     const uint32_t a_lo = a_hi + 4096u;
                     const uint32_t b_hi = op_s + (uint32_t)ks * (uint32_t)Nmma * 32u;
                     const uint32_t b_lo = b_hi + op_half;
@@ -515,7 +585,7 @@ cudaError_t encode_rows(CUtensorMap *m, const float *base, int64_t cols, int row
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int MODE>
+template <int MODE, bool TF>
 cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOperator &op, int *err, int grid,
                         cudaStream_t s) {
     const int nslot = tc_stages(op);
@@ -523,7 +593,7 @@ cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOp
     // the attribute is raised once per instantiation to the largest size
     static size_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<MODE, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
         if (e != cudaSuccess) return e;
         configured = 232448;
     }
@@ -533,24 +603,30 @@ cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOp
     cudaError_t e = encode_rows(&m1, g.B1, g.N, g.K1, g.ldb1);
     if (e == cudaSuccess) e = g.K2 > 0 ? encode_rows(&m2, g.B2, g.N, g.K2, g.ldb2) : encode_rows(&m2, g.B1, g.N, g.K1, g.ldb1);
     if (e != cudaSuccess) return e;
-    k_gemm_tc<MODE><<<grid, kThreads, smem, s>>>(g, tm, m1, m2, op.img, op.Nmma, op.K1pad, op.Kpad, nslot, cols, err);
+    k_gemm_tc<MODE, TF><<<grid, kThreads, smem, s>>>(g, tm, m1, m2, op.img, op.Nmma, op.K1pad, op.Kpad, nslot, cols,
+                                                    err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// shared memory after the operator image: the slot ring (2..12 slots)
+// shared memory: the resident operator image (split BF16) and the slot
+// ring (2..12 slots; split TF32: state 16 KB plus the operator slab)
+static int64_t tc_image_bytes(const TcOperator &op) { return op.tf32 ? 0 : 4 * (int64_t)op.Nmma * op.Kpad; }
+static int64_t tc_slot_bytes(const TcOperator &op) {
+    return op.tf32 ? 16384 + 128 * (int64_t)op.Nmma : (int64_t)kStageBytes;
+}
 static int64_t tc_free(const TcOperator &op) {
-    return 232448 - 4 * (int64_t)op.Nmma * op.Kpad - (int64_t)sizeof(Bars) - 1024;
+    return 232448 - tc_image_bytes(op) - (int64_t)sizeof(Bars) - 1024;
 }
 
 int tc_stages(const TcOperator &op) {
-    const int64_t n = tc_free(op) / kStageBytes;
+    const int64_t n = tc_free(op) / tc_slot_bytes(op);
     return n < 0 ? 0 : (n > kMaxSlots ? kMaxSlots : (int)n);
 }
 
 size_t tc_smem_bytes(const TcOperator &op) {
-    const size_t used = 4 * (size_t)op.Nmma * op.Kpad + (size_t)tc_stages(op) * kStageBytes + sizeof(Bars);
+    const size_t used = (size_t)tc_image_bytes(op) + (size_t)tc_stages(op) * tc_slot_bytes(op) + sizeof(Bars);
     // at least 116 KB, so that no two CTAs (and their tensor memory) share an SM
     return used < 118784 ? 118784 : used;
 }
@@ -578,16 +654,23 @@ cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int 
     tm.ept = (g.np + kTileN - 1) / kTileN;
     const int64_t ntiles = tm.ept * tm.nvb;
     const int grid = (int)(ntiles < nsm ? ntiles : nsm);
-    switch (g.mode) {
-        case GEMM_STORE:
-            return launch_mode<GEMM_STORE>(g, tm, op, err, grid, s);
-        case GEMM_GRAD:
-            return launch_mode<GEMM_GRAD>(g, tm, op, err, grid, s);
-        case GEMM_DIV:
-            return launch_mode<GEMM_DIV>(g, tm, op, err, grid, s);
-        case GEMM_DIV_RK:
-            return launch_mode<GEMM_DIV_RK>(g, tm, op, err, grid, s);
+#define FR_TC_MODES(TF)                                                \
+    switch (g.mode) {                                                  \
+        case GEMM_STORE:                                               \
+            return launch_mode<GEMM_STORE, TF>(g, tm, op, err, grid, s);   \
+        case GEMM_GRAD:                                                \
+            return launch_mode<GEMM_GRAD, TF>(g, tm, op, err, grid, s);    \
+        case GEMM_DIV:                                                 \
+            return launch_mode<GEMM_DIV, TF>(g, tm, op, err, grid, s);     \
+        case GEMM_DIV_RK:                                              \
+            return launch_mode<GEMM_DIV_RK, TF>(g, tm, op, err, grid, s);  \
     }
+    if (op.tf32) {
+        FR_TC_MODES(true)
+    } else {
+        FR_TC_MODES(false)
+    }
+#undef FR_TC_MODES
     return cudaErrorInvalidValue;
 }
 

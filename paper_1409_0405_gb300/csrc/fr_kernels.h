@@ -107,12 +107,16 @@ cudaError_t launch_gemm_grouped(const GemmArgsT<T> *descs, const int64_t *begin,
 // (a multiple of 16, <= 256) and each operand block's columns to a multiple
 // of 16.
 // The columns of the second operand block start at K1pad (a multiple of 16).
+// tf32: split TF32 image, stage-major: per 16-wide K stage the slab
+// [hi | lo], each Nmma/8 row groups x 4 K core matrices x 8 rows x 4 values.
 struct TcOperator {
     const uint8_t *img = nullptr;
-    int M = 0, K = 0, Nmma = 0, K1pad = 0, Kpad = 0;
+    int M = 0, K = 0, Nmma = 0, K1pad = 0, Kpad = 0, tf32 = 0;
 };
 // packs a row-major FP64 operator (M x (K1 + K2)) into the image layout (host)
 void tc_pack(const double *A, int M, int K1, int K2, std::vector<uint16_t> &img, int &Nmma, int &K1pad, int &Kpad);
+void tc_pack_tf32(const double *A, int M, int K1, int K2, std::vector<uint32_t> &img, int &Nmma, int &K1pad,
+                  int &Kpad);
 int tc_stages(const TcOperator &op);
 size_t tc_smem_bytes(const TcOperator &op);
 // C <- A [B1; B2] with g's epilogue on the tensor cores; *err (device) is set

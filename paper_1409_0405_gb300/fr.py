@@ -26,6 +26,7 @@ FR_ERR_UNSUPPORTED = -7
 FR_FP64 = 0
 FR_FP32 = 1
 FR_BF16X3 = 2
+FR_TF32X3 = 3
 NVARS = 5
 
 OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,

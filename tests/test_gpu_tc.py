@@ -1,8 +1,8 @@
-"""GPU tests of the FR_BF16X3 mode: the operator applications on the
-tensor cores (tcgen05, split BF16 with FP32 accumulation) against the FP64
-oracle and against the FR_FP32 mode, over both element types, orders 1-4,
-Euler and Navier-Stokes, ragged column tiles, the fused RK epilogue and
-the full-size boundary-layer RHS."""
+"""GPU tests of the tensor-core modes FR_BF16X3 and FR_TF32X3: the operator
+applications on tcgen05 (split BF16 / split TF32 with FP32 accumulation)
+against the FP64 oracle and against the FR_FP32 mode, over both element
+types, orders 1-4, Euler and Navier-Stokes, ragged column tiles, the RK
+update and the full-size boundary-layer RHS."""
 import numpy as np
 import pytest
 
@@ -12,10 +12,17 @@ from tests import _cases
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# split BF16 keeps ~16 bits of each operand; with the operators' cancellation
-# the RHS error is a few 1e-5 of its scale (measured); a layout or epilogue
-# mistake gives O(1)
-TC_RHS_TOL = 5e-4
+# split BF16 keeps ~16 bits of each operand, split TF32 ~22; with the
+# operators' cancellation the RHS error is a few 1e-5 (BF16X3) and a few
+# 1e-6 (TF32X3, about the FP32 mode's) of its scale (measured); a layout or
+# epilogue mistake gives O(1)
+TOLS = {"bf16x3": 5e-4, "tf32x3": 5e-5}
+TC_RHS_TOL = TOLS["bf16x3"]
+MODES = ["bf16x3", "tf32x3"]
+
+
+def _prec(fr, mode):
+    return {"bf16x3": fr.FR_BF16X3, "tf32x3": fr.FR_TF32X3}[mode]
 
 
 def _fr():
@@ -24,49 +31,53 @@ def _fr():
     return fr
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("viscous", [False, True])
-def test_tc_rhs_matches_oracle(p, viscous):
+def test_tc_rhs_matches_oracle(p, viscous, mode):
     fr = _fr()
     mesh = synth.vortex_box(n=4, jitter=0.05, seed=0)
     prm = dict(viscous=viscous, mu=0.01 if viscous else 0.0, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0)
-    sol, ctx = _cases.make_pair(mesh, p, precision=fr.FR_BF16X3, **prm)
+    sol, ctx = _cases.make_pair(mesh, p, precision=_prec(fr, mode), **prm)
     _, c32 = _cases.make_pair(mesh, p, precision=fr.FR_FP32, **prm)
     u = _cases.state(sol, "vortex")
     ref = sol.rhs(u)
     got = _cases.gpu_rhs(ctx, u)
     err = _cases.per_quantity_rel_err(sol, ref, got)
     e32 = _cases.per_quantity_rel_err(sol, ref, _cases.gpu_rhs(c32, u))
-    print(p, viscous, "bf16x3", err, "fp32", e32)
-    assert np.all(err < TC_RHS_TOL), err
+    print(p, viscous, mode, err, "fp32", e32)
+    assert np.all(err < TOLS[mode]), err
     ctx.reduce(check=False)   # raises FR_ERR_TIMEOUT if a bounded wait of a kernel gave up
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("etypes", ["tet", "pri"])
-def test_tc_single_type_ragged(etypes):
+def test_tc_single_type_ragged(etypes, mode):
     """One element type only, element counts that leave a ragged last tile."""
     fr = _fr()
     coords = [np.linspace(-5, 5, 4), np.linspace(-5, 5, 3), np.linspace(-5, 5, 4)]
     mesh = synth.layered_box(coords, 2, 3 if etypes == "pri" else 0, (True, True, True), jitter=0.05, seed=4)
     prm = dict(viscous=True, mu=0.01, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0)
-    sol, ctx = _cases.make_pair(mesh, 3, precision=fr.FR_BF16X3, **prm)
+    sol, ctx = _cases.make_pair(mesh, 3, precision=_prec(fr, mode), **prm)
     u = _cases.state(sol, "vortex")
     err = _cases.per_quantity_rel_err(sol, sol.rhs(u), _cases.gpu_rhs(ctx, u))
-    assert np.all(err < TC_RHS_TOL), err
+    assert np.all(err < TOLS[mode]), err
 
 
 def test_tc_rk_step_matches_fp32_mode():
-    """The fused RK epilogue: one RK4 step in FR_BF16X3 against FR_FP32."""
+    """The RK update: one RK4 step in the tensor-core modes and FR_FP32
+    against the oracle's step."""
     fr = _fr()
     mesh = synth.vortex_box(n=4, jitter=0.05, seed=0)
     prm = dict(viscous=True, mu=0.01, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0)
     sol, c16 = _cases.make_pair(mesh, 4, precision=fr.FR_BF16X3, **prm)
+    _, ctf = _cases.make_pair(mesh, 4, precision=fr.FR_TF32X3, **prm)
     _, c32 = _cases.make_pair(mesh, 4, precision=fr.FR_FP32, **prm)
     u = _cases.state(sol, "vortex")
     dt = sol.dt_cfl(u, 0.1)
     ref = sol.rk4_step(u, dt)
     out = {}
-    for name, c in (("bf16x3", c16), ("fp32", c32)):
+    for name, c in (("bf16x3", c16), ("tf32x3", ctf), ("fp32", c32)):
         c.set_state(u)
         c.step(dt, 1)
         out[name] = c.get_state()
@@ -77,15 +88,16 @@ def test_tc_rk_step_matches_fp32_mode():
         assert np.all(err < 5e-3), (name, err)
 
 
-def test_tc_full_size_boundary_layer():
+@pytest.mark.parametrize("mode", MODES)
+def test_tc_full_size_boundary_layer(mode):
     """The benchmark workload (42.4 M DOF, p=4 NS with walls and far field):
-    FR_BF16X3 RHS against the FR_FP64 RHS of the library (which matches the
-    FP64 oracle to 1e-12)."""
+    the tensor-core RHS against the FR_FP64 RHS of the library (which
+    matches the FP64 oracle to 1e-12)."""
     fr = _fr()
     mesh = synth.boundary_layer_box()
     prm = _cases.bl_params()
     c64 = fr.Context(mesh, 4, **prm)
-    c16 = fr.Context(mesh, 4, precision=fr.FR_BF16X3, **prm)
+    c16 = fr.Context(mesh, 4, precision=_prec(fr, mode), **prm)
     xyz = c64.upts_points()
     q = synth.perturbed_freestream(xyz, seed=2, wall_delta=_cases.BL_DELTA)
     counts = [(c64.info["n_tet"], c64.info["nu_tet"]), (c64.info["n_pri"], c64.info["nu_pri"])]
@@ -99,6 +111,6 @@ def test_tc_full_size_boundary_layer():
     c16.rhs(u.data_ptr(), r16.data_ptr())
     torch.cuda.synchronize()
     d = (r16 - r64).abs().max().item() / r64.abs().max().item()
-    print("full-size bf16x3 rel err", d)
-    assert d < TC_RHS_TOL
+    print("full-size", mode, "rel err", d)
+    assert d < TOLS[mode]
     c16.reduce(check=False)

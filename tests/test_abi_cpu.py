@@ -112,3 +112,42 @@ def test_create_without_gpu_fails_cleanly():
     library()
     from paper_1409_0405_gb300 import fr
     assert _create_rc(synth.vortex_box()) == fr.FR_ERR_CUDA
+
+
+def test_entry_points_reject_bad_arguments_without_a_gpu():
+    """Argument checks of the later entry points run before any device
+    work: null contexts and pointers, bad element types, orders, sizes and
+    steps return FR_ERR_ARG (no GPU touched)."""
+    library()
+    import ctypes as C
+    from paper_1409_0405_gb300 import fr
+    lib = fr.load()
+    assert lib.fr_step_ls(None, 1e-3, 1, None) == fr.FR_ERR_ARG
+    assert lib.fr_step(None, 1e-3, 1, None) == fr.FR_ERR_ARG
+    assert lib.fr_closure_set(None, 0, None, 128, None) == fr.FR_ERR_ARG
+    assert lib.fr_closure_features(None, None, 0, None, None) == fr.FR_ERR_ARG
+    assert lib.fr_closure_sample(None, None, None, None, 0, None, None, None, None, None) == fr.FR_ERR_ARG
+    assert lib.fr_transfer_state(None, None, None, None, None) == fr.FR_ERR_ARG
+    rows, cols = C.c_int64(), C.c_int64()
+    assert lib.fr_transfer(0, 2, 5, None, C.byref(rows), C.byref(cols)) == fr.FR_ERR_ARG
+    assert lib.fr_transfer(3, 2, 4, None, C.byref(rows), C.byref(cols)) == fr.FR_ERR_ARG
+    assert lib.fr_mlp_forward(4, 0, 4, 10, None, None, None, None, None) == fr.FR_ERR_ARG
+    assert lib.fr_mlp_grad(4, 8, 4, 0, None, None, None, None, None, None, None) == fr.FR_ERR_ARG
+    assert lib.fr_mlp_adam(10, None, None, None, None, 1, 1e-3, None) == fr.FR_ERR_ARG
+    assert lib.fr_mlp_nparams(0, 8, 4) == 0 and lib.fr_mlp_workspace(4, 8, 4, 0) == 0
+    assert lib.fr_reduce_noalloc(0, 10, None, None, 1.4, None, None) == fr.FR_ERR_ARG
+    assert lib.fr_batch_step(None, None, 1, 1, None) == fr.FR_ERR_ARG
+
+
+def test_tensor_core_precisions_are_accepted_on_the_host():
+    """FR_BF16X3 and FR_TF32X3 pass the host checks (the failure without a
+    GPU is the device, not the precision); FR_TF32X3 + 1 does not."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    library()
+    from paper_1409_0405_gb300 import fr
+    m = synth.vortex_box()
+    assert _create_rc(m, p=2, precision=fr.FR_BF16X3) == fr.FR_ERR_CUDA
+    assert _create_rc(m, p=2, precision=fr.FR_TF32X3) == fr.FR_ERR_CUDA
+    assert _create_rc(m, p=2, precision=fr.FR_TF32X3 + 1) == fr.FR_ERR_UNSUPPORTED

@@ -63,28 +63,43 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
         for (int r = 0; r < RC; ++r) acc[r] = T(0);
         if constexpr (RC == 3) {
             if (sK && g.sp_masked) {
-                // per listed column, only the rows whose entry is non-zero;
-                // the mask is the same for the whole warp, so this is a
-                // uniform branch, not predication of the FMAs
+                // runs of listed columns with the same row mask, each mask
+                // with its own loop (the FMAs of absent rows are not issued,
+                // not even predicated off); the column order is unchanged
                 const T *b1 = g.B1 + n, *b2 = g.B2 + n;
-#pragma unroll 2
-                for (int i = 0; i < nl; ++i) {
-                    const int w = sK[i];
-                    const int k = w & 0xFFFFFF;
-                    const T bv = i < nl1 ? __ldg(b1 + (int64_t)k * g.ldb1) : __ldg(b2 + (int64_t)(k - g.K1) * g.ldb2);
-                    const T *a = sA + i * 3;
-                    switch (w >> 24) {
-                        case 1: acc[0] = fma(a[0], bv, acc[0]); break;
-                        case 2: acc[1] = fma(a[1], bv, acc[1]); break;
-                        case 3: acc[0] = fma(a[0], bv, acc[0]); acc[1] = fma(a[1], bv, acc[1]); break;
-                        case 4: acc[2] = fma(a[2], bv, acc[2]); break;
-                        case 5: acc[0] = fma(a[0], bv, acc[0]); acc[2] = fma(a[2], bv, acc[2]); break;
-                        case 6: acc[1] = fma(a[1], bv, acc[1]); acc[2] = fma(a[2], bv, acc[2]); break;
+                const int64_t ld1 = g.ldb1, ld2 = g.ldb2;
+                const int K1 = g.K1;
+                auto bval = [&](int t) -> T {
+                    const int k = sK[t] & 0xFFFFFF;
+                    return t < nl1 ? __ldg(b1 + (int64_t)k * ld1) : __ldg(b2 + (int64_t)(k - K1) * ld2);
+                };
+                int i = 0;
+                while (i < nl) {
+                    const int m = sK[i] >> 24;
+                    int j = i + 1;
+                    while (j < nl && (sK[j] >> 24) == m) ++j;
+                    const T *a = sA;
+                    switch (m) {
+#define FR_RUN(BODY)                               \
+    {                                              \
+        _Pragma("unroll 2") for (int t = i; t < j; ++t) { \
+            const T bv = bval(t);                  \
+            BODY                                   \
+        }                                          \
+    }                                              \
+    break;
+                        case 1: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]);)
+                        case 2: FR_RUN(acc[1] = fma(a[3 * t + 1], bv, acc[1]);)
+                        case 3: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[1] = fma(a[3 * t + 1], bv, acc[1]);)
+                        case 4: FR_RUN(acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
+                        case 5: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
+                        case 6: FR_RUN(acc[1] = fma(a[3 * t + 1], bv, acc[1]); acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
                         default:
-                            acc[0] = fma(a[0], bv, acc[0]);
-                            acc[1] = fma(a[1], bv, acc[1]);
-                            acc[2] = fma(a[2], bv, acc[2]);
+                            FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[1] = fma(a[3 * t + 1], bv, acc[1]);
+                                   acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
+#undef FR_RUN
                     }
+                    i = j;
                 }
                 sK = nullptr;  // done
                 nl = -1;

@@ -723,9 +723,9 @@ def main():
         fp64_peak_meas = None
     # DRAM bytes per launch of the FP64 gradient class, from an ncu capture
     # (dram__bytes_read + dram__bytes_write) of the same kernels on the
-    # nx=15 case (tet 466 MB, prism 481 MB per launch), scaled by the 5x
+    # nx=15 case (tet 465 MB, prism 480 MB per launch), scaled by the 5x
     # element count of the full workload; valid while the kernel is unchanged
-    traffic_fp64_grad = 0.5 * (466.2e6 + 480.9e6) * 5
+    traffic_fp64_grad = 0.5 * (465.4e6 + 480.1e6) * 5
     if dom in ("M0", "grad", "M0_grad", "div") and prec != fr.FR_FP64:
         byts = gemm_bytes_f32(ctx, dom) * 4 * args.steps
         achieved = byts / (dom_ms * 1e-3) / 1e9

@@ -240,6 +240,51 @@ class Solver:
             ke += float(np.sum(wJ * k))
         return ke
 
+    def ke_rate(self, u_flat):
+        """Time derivative of the kinetic-energy integral under the
+        semi-discrete system du/dt = R(u).  With K = |m|^2 / (2 rho) (m the
+        momentum), dK = v.dm - |v|^2/2 drho, so
+        dKE/dt = sum_e sum_j w_j J_j (v_j . R_m,j - |v_j|^2/2 R_rho,j).
+        The kinetic-energy dissipation rate is its negative."""
+        u = self.split(np.asarray(u_flat, dtype=np.float64))
+        r = self.split(self.rhs(u_flat))
+        tot = 0.0
+        for t in self.types:
+            wJ = self.m.ops[t].w[None, :] * self.m.J[t]
+            v = u[t][:, 1:4, :] / u[t][:, 0:1, :]
+            dk = np.sum(v * r[t][:, 1:4, :], axis=1) - 0.5 * np.sum(v * v, axis=1) * r[t][:, 0, :]
+            tot += float(np.sum(wJ * dk))
+        return tot
+
+    def wall_force(self, u_flat):
+        """Force of the fluid on the no-slip walls, as (inviscid, viscous)
+        3-vectors: the integral over the wall faces of the common normal
+        momentum flux that the RHS uses there (n the fluid's outward normal,
+        i.e. into the wall).  Inviscid part: Rusanov against the wall's
+        ghost state; viscous part: -F_v(C_b, grad u).n + tau (u - C_b)
+        (momentum components).  Face integral: sum over the wall flux points
+        of fw |S^T n^| times the value, fw the integral of the flux point's
+        face Lagrange polynomial."""
+        m, g = self.m, self.gamma
+        u = self.split(np.asarray(u_flat, dtype=np.float64))
+        UF = m.to_global({t: u[t] @ m.ops[t].M0.T for t in self.types})
+        gw = m.bg[m.btag == 1]
+        uw, nw = UF[gw], m.gn[gw]
+        ghost, cb = physics.wall_states(uw, g, self.t_wall)
+        f_inv = physics.rusanov(uw, ghost, nw, g)[:, 1:4]
+        f_vis = np.zeros_like(f_inv)
+        if self.viscous and gw.size:
+            grad = self.gradient(u_flat)
+            gradf = {t: np.stack([grad[t][..., k] @ m.ops[t].M0.T for k in range(3)], axis=-1)
+                     for t in self.types}
+            GF = np.concatenate([gradf[t].transpose(0, 2, 1, 3).reshape(-1, NVARS, 3)
+                                 for t in self.types])
+            fv = physics.viscous_flux(cb, GF[gw], g, self.mu, self.prandtl)
+            f_vis = (-np.einsum("kvm,km->kv", fv, nw) + self.tau * (uw - cb))[:, 1:4]
+        gfw = np.concatenate([np.tile(m.ops[t].fw, m.ne[t]) for t in self.types])
+        wa = gfw[gw] * m.gmag[gw]
+        return wa @ f_inv, wa @ f_vis
+
     def volume(self):
         return sum(float(np.sum(self.m.ops[t].w[None, :] * self.m.J[t]))
                    for t in self.types)

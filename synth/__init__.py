@@ -10,11 +10,11 @@ their own from what this package returns.
 """
 from .meshgen import (  # noqa: F401
     BC_WALL, BC_FARFIELD, ETYPE_TET, ETYPE_PRI, TET_FACES, PRI_FACES,
-    layered_box, vortex_box, boundary_layer_box, tgv_box, batch_problem_params,
+    layered_box, vortex_box, boundary_layer_box, wall_channel, tgv_box, batch_problem_params,
     batch_problem_mesh, mesh_counts,
 )
 from .ics import (  # noqa: F401
     isentropic_vortex, taylor_green, perturbed_freestream, uniform_state,
-    random_smooth_state,
+    random_smooth_state, shear_flow, shear_wave,
 )
 from .weights import mlp_init  # noqa: F401

@@ -64,6 +64,23 @@ def taylor_green(xyz, gamma=1.4, mach=0.1):
     return _conserved(rho, u, v, w, p, gamma)
 
 
+def shear_flow(xyz, a=0.3, p=1.0 / 1.4, gamma=1.4):
+    """Plane shear u = a y, v = w = 0 with rho = 1 and uniform pressure p."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    y = xyz[..., 1]
+    one = np.ones_like(y)
+    return _conserved(one, a * y, 0.0 * y, 0.0 * y, p * one, gamma)
+
+
+def shear_wave(xyz, amp=0.01, k=1.0, p=1.0 / 1.4, gamma=1.4):
+    """Periodic shear wave u = amp sin(k y), v = w = 0 with rho = 1 and
+    uniform pressure p (a steady Euler solution that viscosity decays)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    y = xyz[..., 1]
+    one = np.ones_like(y)
+    return _conserved(one, amp * np.sin(k * y), 0.0 * y, 0.0 * y, p * one, gamma)
+
+
 def uniform_state(xyz, rho=1.0, vel=(1.0, 0.0, 0.0), p=None, gamma=1.4,
                   mach=0.2):
     xyz = np.asarray(xyz, dtype=np.float64)

@@ -223,6 +223,19 @@ def boundary_layer_box(nx=75, nz=12, n_prism_layers=32, n_tet_layers=22,
                        bcs=bcs, jitter=jitter, seed=seed)
 
 
+def wall_channel(nx=3, ny=3, nz=2, n_prism_layers=2, lx=2.0, ly=1.5, lz=1.0,
+                 jitter=0.05, seed=4):
+    """Box [0,lx]x[0,ly]x[0,lz] periodic in x and z with a no-slip wall at
+    y=0 and far field at y=ly; the lowest n_prism_layers cell layers are
+    prisms (extruded along y), the rest Kuhn tets."""
+    x = np.linspace(0.0, lx, nx + 1)
+    y = np.linspace(0.0, ly, ny + 1)
+    z = np.linspace(0.0, lz, nz + 1)
+    bcs = {(1, 0): BC_WALL, (1, 1): BC_FARFIELD}
+    return layered_box((x, y, z), 1, n_prism_layers, (True, False, True),
+                       bcs=bcs, jitter=jitter, seed=seed)
+
+
 def tgv_box(n=24, jitter=0.0, seed=0):
     """Periodic cube [0,2pi]^3 of n^3 cells, lower half prisms, upper half tets."""
     c = np.linspace(0.0, 2.0 * math.pi, n + 1)

@@ -308,10 +308,19 @@ def precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, precision, args, sp):
     ctx.step(dt, 1, sp)
     s32 = ctx.get_state(stream=sp)
     inc_err = per_quantity_rel_err(s64 - u0, s32 - u0, counts)
+    # flow diagnostics of the initial state, against FP64
+    ctx64.set_state(u0, sp)
+    d64 = ctx64.diagnostics(sp)
+    ctx.set_state(u0, sp)
+    d32 = ctx.diagnostics(sp)
+    diag_err = {"ke_rate": abs(d32[0] - d64[0]) / abs(d64[0]),
+                "wall_force_inviscid": float(np.linalg.norm(d32[1] - d64[1]) / np.linalg.norm(d64[1])),
+                "wall_force_viscous": float(np.linalg.norm(d32[2] - d64[2]) / np.linalg.norm(d64[2]))}
     out = {"value": ctx64.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in classes.items()},
            "gpu_launches": int(launches),
            "rhs_rel_err_vs_fp64": rhs_err, "step_increment_rel_err_vs_fp64": inc_err,
+           "diagnostics_rel_err_vs_fp64": diag_err,
            "error_measure": "[mass, momentum vector, energy] max|d|/max|ref|; the FP64 path matches the "
                             "FP64 oracle to 1e-12"}
     gemm = ("M0", "grad", "M0_grad", "div")
@@ -327,6 +336,53 @@ def precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, precision, args, sp):
                        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     ctx.close()
     return out
+
+
+def state_error_study(fr, torch, nsteps, sp):
+    """The boundary-layer workload at p = 3 and p = 4: nsteps RK4 steps in
+    FP64 and in each reduced-precision mode from the same initial state;
+    the final state, its change over the run and the flow diagnostics
+    (kinetic-energy rate, wall force) of the final state against FP64 (the
+    FP64 path matches the FP64 oracle to 1e-12 per RHS and step; the oracle
+    itself would need hours per run at this size)."""
+    mesh = synth_mod().boundary_layer_box()
+    res = {}
+    for order in (3, 4):
+        dt = time_step_size(mesh, order)
+        runs = {}
+        for name, prec in (("fp64", fr.FR_FP64), ("fp32", fr.FR_FP32), ("bf16x3", fr.FR_BF16X3),
+                           ("tf32x3", fr.FR_TF32X3)):
+            ctx = fr.Context(mesh, order, **flow_params(), precision=prec)
+            counts = [(ctx.info["n_tet"], ctx.info["nu_tet"]), (ctx.info["n_pri"], ctx.info["nu_pri"])]
+            u0 = points_to_public(synth_mod().perturbed_freestream(ctx.upts_points(), seed=2,
+                                                                   wall_delta=WALL_DELTA), counts)
+            ctx.set_state(u0, sp)
+            t0 = time.perf_counter()
+            ctx.step(dt, nsteps, sp)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            finite = ctx.reduce(stream=sp, check=False)[6] == 0.0
+            runs[name] = (ctx.get_state(stream=sp), ctx.diagnostics(sp), wall, bool(finite))
+            ctx.close()
+        s64, d64, _, _ = runs["fp64"]
+        ent = {"ndof": int(s64.size), "dt": dt, "steps": nsteps, "fp64_wall_s": runs["fp64"][2],
+               "fp64_ke_rate": d64[0], "fp64_wall_force_inviscid": d64[1].tolist(),
+               "fp64_wall_force_viscous": d64[2].tolist()}
+        for name in ("fp32", "bf16x3", "tf32x3"):
+            st, d, wall, finite = runs[name]
+            ent[name] = {"state_rel_err": per_quantity_rel_err(s64, st, counts),
+                         "change_rel_err": per_quantity_rel_err(s64 - u0, st - u0, counts),
+                         "ke_rate_rel_err": abs(d[0] - d64[0]) / abs(d64[0]),
+                         "wall_force_viscous_rel_err": float(np.linalg.norm(d[2] - d64[2]) / np.linalg.norm(d64[2])),
+                         "wall_force_inviscid_rel_err": float(np.linalg.norm(d[1] - d64[1]) / np.linalg.norm(d64[1])),
+                         "wall_s": wall, "finite": finite}
+        res[f"p{order}"] = ent
+    return res
+
+
+def synth_mod():
+    import synth
+    return synth
 
 
 def batch_mode(fr, torch, args, sp):
@@ -588,6 +644,9 @@ def main():
                     help="cells along x (75 = the full workload; smaller for profiling)")
     ap.add_argument("--cpu-oracle-child", type=int, default=0)
     ap.add_argument("--fp64-only", action="store_true", help="skip the other modes (precision, batched, learned)")
+    ap.add_argument("--state-error-steps", type=int, default=0,
+                    help="instead of timing: run this many RK4 steps at p=3 and p=4 in FP64 and each reduced "
+                         "precision and print their state and diagnostics errors against FP64")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3", "tf32x3"],
                     help="arithmetic of the main timed step (default fp64, the headline workload)")
     args = ap.parse_args()
@@ -642,6 +701,13 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    if args.state_error_steps > 0:
+        if rank == 0:
+            sp0 = torch.cuda.Stream().cuda_stream
+            print(json.dumps({"study": "reduced-precision state error after RK4 steps, boundary-layer workload",
+                              "results": state_error_study(fr, torch, args.state_error_steps, sp0)}))
+        return
+
     mesh = synth.boundary_layer_box(nx=args.nx)
     prec = {"fp64": fr.FR_FP64, "fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3, "tf32x3": fr.FR_TF32X3}[args.precision]
     ctx = fr.Context(mesh, ORDER, **flow_params(), precision=prec)
@@ -680,6 +746,10 @@ def main():
     ms_step = max_over_ranks(ms_total / args.steps, world, "cuda")
     value = job_gdofs(world, ndof, ms_step * 1e-3)
     state_ok = ctx.reduce(stream=sp, check=False)[6] == 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    diag = ctx.diagnostics(sp)
+    diag_ms = (time.perf_counter() - t0) * 1e3
 
     # --- e2e through the C ABI with host buffers ---
     pin_in = torch.from_numpy(u0).pin_memory()
@@ -770,6 +840,8 @@ def main():
                 "d2h_bytes_per_step": int(ndof * 8), "steps": e2e_steps},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "diagnostics_after_timed_steps": {"ke_rate": diag[0], "wall_force_inviscid": diag[1].tolist(),
+                                          "wall_force_viscous": diag[2].tolist(), "host_ms": diag_ms},
         "modes": modes,
     }
     print(json.dumps(line))

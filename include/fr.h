@@ -174,6 +174,30 @@ int fr_step_ls(fr_ctx *ctx, double dt, int nsteps, void *cuda_stream);
 int fr_reduce(fr_ctx *ctx, double *out, void *cuda_stream);
 
 /*
+ * fr_diagnostics: flow diagnostics of the internal solution register u.
+ * Evaluates R(u), the right-hand side (as the first stage of fr_step
+ * does: the same kernels and precision), then reduces in FP64:
+ *   out[0]    dKE/dt = sum_e sum_j w_j J_j (v_j . R_m,j - |v_j|^2/2 R_rho,j),
+ *             the rate of change of the kinetic-energy integral under the
+ *             semi-discrete system (chain rule of |m|^2 / (2 rho)); the
+ *             kinetic-energy dissipation rate is -out[0];
+ *   out[1..3] inviscid force of the fluid on the no-slip walls (tag
+ *             FR_BC_WALL): the integral over the wall faces of the momentum
+ *             components of the Rusanov flux against the wall ghost state,
+ *             normal pointing out of the fluid;
+ *   out[4..6] viscous force on the walls: the same integral of
+ *             -F_v(C_b, grad u).n + tau (u - C_b), C_b the wall's common
+ *             solution (zero for Euler).
+ * The face integral is sum over the wall flux points of fw |S^T n^| times
+ * the value, fw the integral of the flux point's face Lagrange polynomial
+ * over the reference face (fr_operator FW).  out: host, caller-owned, 7
+ * doubles.  Synchronous.  Overwrites the RHS scratch (and fr_rhs's input
+ * buffer), not the solution registers.  Errors: FR_ERR_ARG,
+ * FR_ERR_CUDA, FR_ERR_TIMEOUT (tensor-core modes).
+ */
+int fr_diagnostics(fr_ctx *ctx, double *out, void *cuda_stream);
+
+/*
  * fr_operator: host-only query (no GPU needed) of one operator matrix the
  * engine builds for (etype, order), row-major float64.  which:
  *   0 M0   (nf x nu)        interpolation to flux points (Table 2)
@@ -187,6 +211,8 @@ int fr_reduce(fr_ctx *ctx, double *out, void *cuda_stream);
  *   6 UPTS (nu x 3)         reference solution points
  *   7 FPTS (nf x 3)         reference flux points
  *   8 FNORM (nf x 3)        outward unit reference normal per flux point
+ *   9 FW    (nf x 1)        face weights: integral over its reference face of
+ *                           each flux point's face Lagrange polynomial
  * With out == NULL only *rows and *cols are written.  Errors: FR_ERR_ARG.
  */
 int fr_operator(int etype, int order, int which, double *out, int64_t *rows, int64_t *cols);

@@ -50,6 +50,7 @@ namespace fr {
 namespace api {
 
 constexpr int64_t kPad = 32;
+constexpr int kDiagBlocks = 304;  // blocks of the diagnostics reductions (2 per SM)
 
 template <class T>
 int dev_alloc(fr_ctx *c, T **p, size_t count) {
@@ -536,6 +537,11 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         (rc = upload(c, &c->btag, faces.btag)) || (rc = upload(c, &c->bn, faces.bn)) ||
         (rc = upload(c, &c->bmag, faces.bmag)))
         return rc;
+    {
+        std::vector<double> bw(faces.bt.size());
+        for (size_t k = 0; k < bw.size(); ++k) bw[k] = ops[faces.bt[k]].FW[faces.bf[k]];
+        if ((rc = upload(c, &c->bw, bw))) return rc;
+    }
     // the discrete divergence of the constant reference flux (zero with exact
     // geometry; ~1e-11 with the geometric factors rounded), evaluated once in
     // FP64 and added back to every RHS since the flux kernels subtract that
@@ -615,6 +621,7 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         nbt += c->red_blocks[t];
     }
     if ((rc = dev_alloc(c, &c->red, (size_t)nbt * 7 + 8))) return rc;
+    if ((rc = dev_alloc(c, &c->diag, (size_t)kDiagBlocks * (2 + 6) + 8))) return rc;
     if ((rc = dev_alloc(c, &c->tc_err, 1))) return rc;
     return cuda_check(cudaDeviceSynchronize(), "fr_create sync");
 }
@@ -644,6 +651,41 @@ int rhs_public(fr_ctx *c, const double *u_dev, double *r_dev, cudaStream_t s) {
         off += (size_t)D.ne * NV * D.nu;
     }
     return FR_OK;
+}
+
+// RHS of the solution register, then the FP64 reductions of fr_diagnostics
+template <typename T>
+int diagnostics_impl(fr_ctx *c, double *out, cudaStream_t s) {
+    const Phys ph = phys_of(c);
+    T *in[2] = {nullptr, nullptr};
+    int rc;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_center<T>(D.nu, D.np, D.U, (T *)D.Us, ph.uref, s), "centre"))) return rc;
+        in[t] = (T *)D.Us;
+    }
+    if ((rc = rhs_internal<T>(c, in, nullptr, s))) return rc;
+    double *part = c->diag, *res = c->diag + (size_t)kDiagBlocks * 8;
+    int nb = 0;
+    for (int t = 0; t < 2; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_ke_rate<T>(D.nu, D.ne, D.np, D.U, (const T *)D.R, D.wJ, part + nb, kDiagBlocks, s),
+                             "kinetic-energy rate")))
+            return rc;
+        nb += kDiagBlocks;
+    }
+    if ((rc = cuda_check(launch_sum_partials(part, nb, 1, res, s), "kinetic-energy rate sum"))) return rc;
+    double *wpart = part + (size_t)kDiagBlocks * 2;
+    if ((rc = cuda_check(launch_wall_force<T>(bnd_of(c), c->bw, fields_of<T>(c), ph, wpart, kDiagBlocks, s),
+                         "wall force")))
+        return rc;
+    if ((rc = cuda_check(launch_sum_partials(wpart, kDiagBlocks, 6, res + 1, s), "wall force sum"))) return rc;
+    if ((rc = cuda_check(cudaMemcpyAsync(out, res, 7 * sizeof(double), cudaMemcpyDeviceToHost, s), "diagnostics copy")))
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(s), "diagnostics sync"))) return rc;
+    return check_tc(c);
 }
 
 template <typename T>
@@ -934,6 +976,12 @@ int fr_reduce(fr_ctx *c, double *out, void *stream) {
     return FR_OK;
 }
 
+int fr_diagnostics(fr_ctx *c, double *out, void *stream) {
+    if (!c || !out) return set_err(FR_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    return is_f32(c) ? diagnostics_impl<float>(c, out, s) : diagnostics_impl<double>(c, out, s);
+}
+
 int fr_peak_fp64(double *gflops, void *stream) {
     if (!gflops) return set_err(FR_ERR_ARG, "null argument");
     return cuda_check(probe_fp64(gflops, (cudaStream_t)stream), "fp64 probe");
@@ -962,6 +1010,7 @@ int fr_operator(int etype, int order, int which, double *out, int64_t *rows, int
         case 6: src = &o.upts; r = o.nu; cc = 3; break;
         case 7: src = &o.fpts; r = o.nf; cc = 3; break;
         case 8: src = &o.fnorm; r = o.nf; cc = 3; break;
+        case 9: src = &o.FW; r = o.nf; cc = 1; break;
         default: return set_err(FR_ERR_ARG, "unknown operator id");
     }
     *rows = r;

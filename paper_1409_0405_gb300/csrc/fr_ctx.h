@@ -63,6 +63,8 @@ struct fr_ctx {
     int *bt = nullptr, *bf = nullptr, *be = nullptr, *btag = nullptr;
     double *bn = nullptr, *bmag = nullptr;
     double *red = nullptr;  // reduction partials + result
+    double *bw = nullptr;    // face weight of each boundary flux point
+    double *diag = nullptr;  // diagnostics partials + result
     int *tc_err = nullptr;  // set by a tensor-core kernel whose bounded wait gave up
     int red_blocks[2] = {0, 0};
     std::vector<void *> allocs;

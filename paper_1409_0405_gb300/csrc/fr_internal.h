@@ -23,6 +23,7 @@ struct RefOps {
     std::vector<double> D;       // (3 nu) x nu, rows (j, d)
     std::vector<double> M3;      // nu x nf
     std::vector<double> W;       // nu quadrature weights
+    std::vector<double> FW;      // nf face weights: integral of each flux point's face Lagrange function
     std::vector<double> AGRAD;   // (3 nu) x (nu + nf)
     std::vector<double> ADIV;    // nu x (3 nu + nf): [M1 - M3 M2 | M3]
     std::vector<std::vector<int>> face_fpts;   // flux points of each face

@@ -167,6 +167,18 @@ cudaError_t launch_common_solution(const Pairs &P, const Bnd &B, const FieldsT<T
 template <typename T>
 cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const FieldsT<T> &F, const Phys &ph,
                                cudaStream_t s);
+// diagnostics: per-block partial sums (nblocks x 1, nblocks x 6) of the
+// kinetic-energy rate sum w J (v.R_m - |v|^2/2 R_rho) over one type and of
+// the wall force (inviscid xyz, viscous xyz) over the wall boundary points
+// (bw: face weight of each boundary point); launch_sum_partials adds the
+// nblocks rows of nq (<= 32) values into out
+template <typename T>
+cudaError_t launch_ke_rate(int nu, int64_t ne, int64_t np, const double *U, const T *R, const double *wJ,
+                           double *partial, int nblocks, cudaStream_t s);
+template <typename T>
+cudaError_t launch_wall_force(const Bnd &B, const double *bw, const FieldsT<T> &F, const Phys &ph, double *partial,
+                              int nblocks, cudaStream_t s);
+cudaError_t launch_sum_partials(const double *partial, int nblocks, int nq, double *out, cudaStream_t s);
 // transformed flux at the solution points of one type; U is the centred
 // stage input (u - uref)
 template <typename T>

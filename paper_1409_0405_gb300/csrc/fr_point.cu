@@ -319,6 +319,98 @@ __global__ void k_common_flux(const Pairs P, const Bnd B, const FieldsT<T> F, co
     common_flux_at(P, B, F, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// Diagnostics (FP64 accumulation in both modes).  Block sums of NQ values
+// per block of kDiagThreads threads into partial[block][NQ].
+constexpr int kDiagThreads = 256;
+
+template <int NQ>
+__device__ __forceinline__ void block_sum_store(double (&acc)[NQ], double *partial) {
+    __shared__ double sh[NQ][kDiagThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double x = acc[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[q][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        double x = 0.0;
+        for (int w = 0; w < kDiagThreads / 32; ++w) x += sh[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * NQ + threadIdx.x] = x;
+    }
+}
+
+// rate of change of the kinetic-energy integral along R:
+// sum w J (v . R_m - |v|^2/2 R_rho), u from the FP64 register
+template <typename T>
+__global__ void k_ke_rate(int nu, int64_t ne, int64_t np, const double *__restrict__ U, const T *__restrict__ R,
+                          const double *__restrict__ wJ, double *partial) {
+    double acc[1] = {0.0};
+    const int64_t tot = (int64_t)nu * np;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = idx / np, e = idx - j * np;
+        if (e >= ne) continue;
+        const double *u = U + j * V * np + e;
+        const T *r = R + j * V * np + e;
+        const double ir = 1.0 / u[0];
+        const double v0 = u[np] * ir, v1 = u[2 * np] * ir, v2 = u[3 * np] * ir;
+        const double dk = v0 * (double)r[np] + v1 * (double)r[2 * np] + v2 * (double)r[3 * np] -
+                          0.5 * (v0 * v0 + v1 * v1 + v2 * v2) * (double)r[0];
+        acc[0] += wJ[idx] * dk;
+    }
+    block_sum_store<1>(acc, partial);
+}
+
+// force of the fluid on the no-slip walls: face integral (weights bw |S^T n^|)
+// of the common normal momentum flux, inviscid (Rusanov against the wall
+// ghost) and viscous (-F_v(C_b, grad u).n + tau (u - C_b)) parts
+template <typename T>
+__global__ void k_wall_force(const Bnd B, const double *__restrict__ bw, const FieldsT<T> F, const PhysT<T> ph,
+                             double *partial) {
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t kb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; kb < B.n;
+         kb += (int64_t)gridDim.x * blockDim.x) {
+        if (B.btag[kb] != FR_BC_WALL) continue;
+        const int t = B.bt[kb];
+        const int64_t np = F.np[t];
+        const int f = B.bf[kb], e = B.be[kb];
+        const int64_t o = fpt_off(f, e, np);
+        T u[V], ghost[V], cb[V], fi[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] = F.UF[t][o + v * np];
+        const T n[3] = {T(B.bn[3 * kb]), T(B.bn[3 * kb + 1]), T(B.bn[3 * kb + 2])};
+        bc_states(FR_BC_WALL, u, n, ph, ghost, cb);
+        rusanov(u, ghost, n, ph.gamma, fi);
+        const double wa = bw[kb] * B.bmag[kb];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[a] += wa * (double)fi[1 + a];
+        if (ph.viscous) {
+            T g[3][V], Fv[V][3];
+            load_grad(F.GUF[t], f, e, np, g);
+            Prim<T> qc = prim(cb, ph.gamma);
+            vis_flux(cb, qc, g, ph.mu, ph.kq, Fv);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T fv = -(Fv[1 + a][0] * n[0] + Fv[1 + a][1] * n[1] + Fv[1 + a][2] * n[2]) +
+                             ph.tau * (u[1 + a] - cb[1 + a]);
+                acc[3 + a] += wa * (double)fv;
+            }
+        }
+    }
+    block_sum_store<6>(acc, partial);
+}
+
+__global__ void k_sum_partials(const double *__restrict__ partial, int nblocks, int nq, double *out) {
+    if ((int)threadIdx.x < nq) {
+        double x = 0.0;
+        for (int b = 0; b < nblocks; ++b) x += partial[(int64_t)b * nq + threadIdx.x];
+        out[threadIdx.x] = x;
+    }
+}
+
 // transformed flux F~_d = sum_m S[d][m] (F_inv - F_vis - F_ref)_m at solution points
 template <typename T>
 __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T *__restrict__ U,
@@ -552,6 +644,26 @@ cudaError_t launch_common_solution(const Pairs &P, const Bnd &B, const FieldsT<T
 }
 
 template <typename T>
+cudaError_t launch_ke_rate(int nu, int64_t ne, int64_t np, const double *U, const T *R, const double *wJ,
+                           double *partial, int nblocks, cudaStream_t s) {
+    k_ke_rate<T><<<nblocks, kDiagThreads, 0, s>>>(nu, ne, np, U, R, wJ, partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_wall_force(const Bnd &B, const double *bw, const FieldsT<T> &F, const Phys &ph, double *partial,
+                              int nblocks, cudaStream_t s) {
+    k_wall_force<T><<<nblocks, kDiagThreads, 0, s>>>(B, bw, F, phys_t<T>(ph), partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double *partial, int nblocks, int nq, double *out, cudaStream_t s) {
+    if (nq < 1 || nq > 32) return cudaErrorInvalidValue;
+    k_sum_partials<<<1, 32, 0, s>>>(partial, nblocks, nq, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const FieldsT<T> &F, const Phys &ph,
                                cudaStream_t s) {
     const int64_t n = P.n + B.n;
@@ -668,6 +780,10 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
                                                    cudaStream_t);                                             \
     template cudaError_t launch_common_flux<T>(const Pairs &, const Bnd &, const FieldsT<T> &, const Phys &,     \
                                                cudaStream_t);                                                 \
+    template cudaError_t launch_ke_rate<T>(int, int64_t, int64_t, const double *, const T *, const double *,     \
+                                           double *, int, cudaStream_t);                                      \
+    template cudaError_t launch_wall_force<T>(const Bnd &, const double *, const FieldsT<T> &, const Phys &,      \
+                                              double *, int, cudaStream_t);                                   \
     template cudaError_t launch_flux<T>(int, int64_t, int64_t, const T *, const T *, const T *, T *,            \
                                         const Phys &, cudaStream_t);                                          \
     template cudaError_t launch_pub_to_int<T>(int, int64_t, int64_t, const double *, double *, cudaStream_t,    \

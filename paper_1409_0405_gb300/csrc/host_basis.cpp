@@ -552,8 +552,10 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
         }
     }
 
-    // ---- face moments  Bf[m][f] = int_F phi_m l_f dS
+    // ---- face moments  Bf[m][f] = int_F phi_m l_f dS, and the face
+    // weights FWr[f] = int_F l_f dS (l_f the face Lagrange function)
     Mat Bf(nu, nf);
+    std::vector<R> FWr(nf, R(0.0));
     for (int fi = 0; fi < o.nfaces; ++fi) {
         const auto &fv = o.face_verts[fi];
         const bool tri = fv.size() == 3;
@@ -616,6 +618,7 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
                 for (int qq = 0; qq < nk; ++qq) ell[k] += psi[qq] * Winv(qq, k);
             B.eval(x, phi.data(), nullptr);
             const R wq = rw[q] * scale;
+            for (int k = 0; k < nk; ++k) FWr[idx[k]] += wq * ell[k];
             for (int m = 0; m < nu; ++m) {
                 const R wp = wq * phi[m];
                 for (int k = 0; k < nk; ++k) Bf(m, idx[k]) += wp * ell[k];
@@ -636,6 +639,8 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
     for (int j = 0; j < nu; ++j)
         for (int d = 0; d < 3; ++d)
             for (int i = 0; i < nu; ++i) o.D[((size_t)(j * 3 + d)) * nu + i] = Dm[d](j, i).to_double();
+    o.FW.assign(nf, 0.0);
+    for (int f = 0; f < nf; ++f) o.FW[f] = FWr[f].to_double();
     o.W.assign(nu, 0.0);
     for (int j = 0; j < nu; ++j) {
         R s(0.0);

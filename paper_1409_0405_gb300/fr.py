@@ -30,12 +30,12 @@ FR_TF32X3 = 3
 NVARS = 5
 
 OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
-          "FPTS": 7, "FNORM": 8}
+          "FPTS": 7, "FNORM": 8, "FW": 9}
 
 # every entry point declared in include/fr.h
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_step_ls", "fr_reduce",
-           "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
+           "fr_diagnostics", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info",
            "fr_transfer", "fr_transfer_state", "fr_closure_features", "fr_closure_sample",
@@ -91,6 +91,7 @@ def load():
     lib.fr_step_ls.argtypes = [vp, C.c_double, C.c_int, vp]
     lib.fr_step_ls.restype = C.c_int
     lib.fr_reduce.argtypes = [vp, dp, vp]
+    lib.fr_diagnostics.argtypes = [vp, dp, vp]
     lib.fr_operator.argtypes = [C.c_int, C.c_int, C.c_int, dp, i64p, i64p]
     lib.fr_profile.argtypes = [vp, C.c_int]
     lib.fr_profile_read.argtypes = [vp, dp, i64p, i64p]
@@ -128,7 +129,7 @@ def load():
     lib.fr_last_error.argtypes = []
     lib.fr_last_error.restype = C.c_char_p
     for name in ("fr_create", "fr_ndof", "fr_info", "fr_upts", "fr_set_state",
-                 "fr_get_state", "fr_rhs", "fr_step", "fr_reduce", "fr_operator",
+                 "fr_get_state", "fr_rhs", "fr_step", "fr_reduce", "fr_diagnostics", "fr_operator",
                  "fr_profile", "fr_profile_read"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -396,6 +397,14 @@ class Context:
             return out
         _check(rc)
         return out
+
+
+    def diagnostics(self, stream=None):
+        """fr_diagnostics: (dKE/dt, inviscid wall force (3,), viscous wall
+        force (3,)) of the solution register."""
+        out = np.empty(7, dtype=np.float64)
+        _check(self._lib.fr_diagnostics(self._h, _dptr(out), C.c_void_p(stream) if stream else None))
+        return float(out[0]), out[1:4].copy(), out[4:7].copy()
 
 
 class Batch:

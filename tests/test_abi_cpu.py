@@ -51,6 +51,7 @@ def test_host_operators_match_oracle(etype, p):
     np.testing.assert_allclose(fr.operator(etype, p, "M3"), op.M3, atol=1e-12 * np.abs(op.M3).max())
     np.testing.assert_allclose(fr.operator(etype, p, "W")[:, 0], op.w, atol=1e-14)
     np.testing.assert_allclose(fr.operator(etype, p, "FNORM"), op.fnorm, atol=1e-15)
+    np.testing.assert_allclose(fr.operator(etype, p, "FW")[:, 0], op.fw, atol=1e-14)
     # the fused operators are the documented combinations
     AG = fr.operator(etype, p, "AGRAD")
     nu, nf = op.nu, op.nf

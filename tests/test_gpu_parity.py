@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests._cases import (bl_params, gpu_rhs, library, make_pair, per_quantity_rel_err,
+from tests._cases import (GAMMA, bl_params, gpu_rhs, library, make_pair, per_quantity_rel_err,
                           per_var_rel_err, state, to_longdouble)
 
 pytestmark = pytest.mark.gpu
@@ -162,6 +162,73 @@ def test_reductions_match_oracle():
     np.testing.assert_allclose(out[:5], sol.integrals(u), rtol=1e-13)
     np.testing.assert_allclose(out[5], sol.kinetic_energy(u), rtol=1e-13)
     assert out[6] == 0.0
+
+
+def _diag_scales(sol, u):
+    """Cancellation-free magnitudes of the kinetic-energy rate's terms."""
+    uu, rr = sol.split(u), sol.split(sol.rhs(u))
+    tot = 0.0
+    for t in sol.types:
+        wJ = sol.m.ops[t].w[None, :] * sol.m.J[t]
+        v = uu[t][:, 1:4, :] / uu[t][:, 0:1, :]
+        tot += float(np.sum(wJ * (np.sum(np.abs(v * rr[t][:, 1:4, :]), axis=1)
+                                  + 0.5 * np.sum(v * v, axis=1) * np.abs(rr[t][:, 0, :]))))
+    return tot
+
+
+def _check_diagnostics(sol, ctx, u, tol_rate, tol_inv, tol_vis):
+    ctx.set_state(u)
+    rate, f_inv, f_vis = ctx.diagnostics()
+    o_inv, o_vis = sol.wall_force(u)
+    assert abs(rate - sol.ke_rate(u)) <= tol_rate * _diag_scales(sol, u)
+    assert np.max(np.abs(f_inv - o_inv)) <= tol_inv * max(np.linalg.norm(o_inv), 1e-300)
+    assert np.max(np.abs(f_vis - o_vis)) <= tol_vis * max(np.linalg.norm(o_vis), 1e-300)
+    # the solution register is untouched
+    np.testing.assert_array_equal(ctx.get_state(), u)
+    return rate, f_inv, f_vis
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_diagnostics_wall_bounded_match_oracle(p):
+    """Kinetic-energy rate and wall force (pressure and viscous parts) on
+    the wall/far-field box with a wall-consistent boundary-layer state."""
+    m = synth.boundary_layer_box(nx=6, nz=3, n_prism_layers=4, n_tet_layers=3)
+    sol, ctx = make_pair(m, p, **bl_params(mu=0.01))
+    u = state(sol, "bl")
+    _, f_inv, f_vis = _check_diagnostics(sol, ctx, u, 1e-12, 1e-12, 1e-10)
+    assert f_inv[1] < 0.0 and f_vis[0] > 0.0   # pressure pushes on, flow drags along
+
+
+def test_diagnostics_periodic_match_oracle():
+    """No walls: zero force; the kinetic-energy rate of the Euler vortex."""
+    sol, ctx = make_pair(synth.vortex_box(), 2)
+    u = state(sol, "vortex")
+    _, f_inv, f_vis = _check_diagnostics(sol, ctx, u, 1e-12, 0.0, 0.0)
+    assert np.all(f_inv == 0.0) and np.all(f_vis == 0.0)
+
+
+def test_diagnostics_plane_shear_closed_form():
+    """Channel with a wall at y = 0 and u = a y: viscous wall force mu a A,
+    pressure force -p0 A along y (the oracle pins these to rounding)."""
+    mu, a, p0 = 0.01, 0.3, 1.0 / GAMMA
+    m = synth.wall_channel(n_prism_layers=2)
+    sol, ctx = make_pair(m, 2, viscous=True, mu=mu, p_inf=p0, t_wall=p0)
+    u = sol.state_from_points(synth.shear_flow(sol.upts_xyz_points(), a=a, p=p0))
+    ctx.set_state(u)
+    _, f_inv, f_vis = ctx.diagnostics()
+    area = 2.0
+    np.testing.assert_allclose(f_vis, [mu * a * area, 0.0, 0.0], rtol=0, atol=1e-11 * mu * a * area)
+    np.testing.assert_allclose(f_inv, [0.0, -p0 * area, 0.0], rtol=0, atol=1e-12 * p0 * area)
+
+
+@pytest.mark.parametrize("prec, tol", [("fp32", 2e-5), ("bf16x3", 5e-4), ("tf32x3", 2e-5)])
+def test_diagnostics_reduced_precision(prec, tol):
+    from paper_1409_0405_gb300 import fr
+    mode = {"fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3, "tf32x3": fr.FR_TF32X3}[prec]
+    m = synth.boundary_layer_box(nx=6, nz=3, n_prism_layers=4, n_tet_layers=3)
+    sol, ctx = make_pair(m, 3, precision=mode, **bl_params(mu=0.01))
+    u = state(sol, "bl")
+    _check_diagnostics(sol, ctx, u, tol, tol, 10 * tol)
 
 
 def test_nonphysical_state_is_reported():

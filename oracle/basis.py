@@ -4,10 +4,13 @@ Vandermonde solves in 60-digit decimal arithmetic, rounded to float64 once
 at the end.
 
 Readings (the paper names no point sets and writes out only M0, Table 2):
-  * Spaces: tet P_p; prism P_p(triangle) x P_p(zeta).  Their dimensions are
-    Table 2's solution-point counts.
+  * Spaces: tet P_p; prism P_p(triangle) x P_p(zeta); hex Q_p (degree <= p
+    in each coordinate).  Their dimensions are Table 2's solution-point
+    counts.
   * Reference tet vertices (-1,-1,-1), (1,-1,-1), (-1,1,-1), (-1,-1,1);
-    reference prism = triangle {(-1,-1),(1,-1),(-1,1)} x [-1,1].
+    reference prism = triangle {(-1,-1),(1,-1),(-1,1)} x [-1,1]; reference
+    hex = [-1,1]^3, vertices 0..3 the bottom face counter-clockwise from
+    (-1,-1,-1), vertex a+4 above vertex a.
   * Solution points: a symmetric, constructive, interior set built from the
     p+1 Gauss-Legendre nodes v_0 < ... < v_p mapped to [0,1] (the
     Blyth-Pozrikidis barycentric construction).  For a simplex with d+1
@@ -15,7 +18,8 @@ Readings (the paper names no point sets and writes out only M0, Table 2):
     are  lambda_a = (1 + d v_{I_a} - sum_{b != a} v_{I_b}) / (d+1).
     Tet: d = 3, I = (p-i-j-k, i, j, k), ordered k, j, i from slowest to
     fastest.  Prism: the triangle set (d = 2, I = (p-i-j, i, j), ordered j, i)
-    times the Gauss-Legendre points in zeta, zeta index slowest.
+    times the Gauss-Legendre points in zeta, zeta index slowest.  Hex: the
+    (p+1)^3 Gauss-Legendre tensor points, zeta slowest, xi fastest.
   * Flux points.  Triangle faces (A, B, C): the same triangle set,
     lambda_0 A + lambda_1 B + lambda_2 C; quad faces (A, B, C, D): Gauss-
     Legendre x Gauss-Legendre in the bilinear parameters (s along A->B, t
@@ -50,8 +54,12 @@ PRI_VERTS = ((-1, -1, -1), (1, -1, -1), (-1, 1, -1),
              (-1, -1, 1), (1, -1, 1), (-1, 1, 1))
 TET_FACES = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
 PRI_FACES = ((0, 1, 2), (3, 4, 5), (0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5))
+HEX_VERTS = ((-1, -1, -1), (1, -1, -1), (1, 1, -1), (-1, 1, -1),
+             (-1, -1, 1), (1, -1, 1), (1, 1, 1), (-1, 1, 1))
+HEX_FACES = ((0, 1, 2, 3), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7),
+             (4, 5, 6, 7))
 
-ETYPES = ("tet", "pri")
+ETYPES = ("tet", "pri", "hex")
 
 
 def _dec(x):
@@ -95,6 +103,9 @@ def exponents(etype, p):
     if etype == "tet":
         return [(a, b, c) for c in range(p + 1) for b in range(p + 1 - c)
                 for a in range(p + 1 - b - c)]
+    if etype == "hex":
+        return [(a, b, c) for c in range(p + 1) for b in range(p + 1)
+                for a in range(p + 1)]
     return [(a, b, c) for c in range(p + 1) for b in range(p + 1)
             for a in range(p + 1 - b)]
 
@@ -143,6 +154,8 @@ def int_tet(a, b, c):
 def int_elem(etype, e):
     if etype == "tet":
         return int_tet(*e)
+    if etype == "hex":
+        return int_line(e[0]) * int_line(e[1]) * int_line(e[2])
     return int_tri(e[0], e[1]) * int_line(e[2])
 
 
@@ -216,12 +229,16 @@ def _eye(n):
 def nupts(etype, p):
     if etype == "tet":
         return (p + 1) * (p + 2) * (p + 3) // 6
+    if etype == "hex":
+        return (p + 1) ** 3
     return (p + 1) ** 2 * (p + 2) // 2
 
 
 def nfpts(etype, p):
     if etype == "tet":
         return 4 * (p + 1) * (p + 2) // 2
+    if etype == "hex":
+        return 6 * (p + 1) ** 2
     return 2 * (p + 1) * (p + 2) // 2 + 3 * (p + 1) ** 2
 
 
@@ -255,6 +272,12 @@ def upts_exact(etype, p):
                     lam = _bp_bary((p - i - j - k, i, j, k), v)
                     pts.append(tuple(sum(lam[a] * X[a][c] for a in range(4))
                                      for c in range(3)))
+    elif etype == "hex":
+        gl = gauss_legendre(p + 1)
+        for c in range(p + 1):
+            for b in range(p + 1):
+                for a in range(p + 1):
+                    pts.append((gl[a], gl[b], gl[c]))
     else:
         gl = gauss_legendre(p + 1)
         X = [[Decimal(c) for c in x] for x in PRI_VERTS[:3]]
@@ -267,9 +290,8 @@ def upts_exact(etype, p):
 
 
 def faces(etype):
-    verts = TET_VERTS if etype == "tet" else PRI_VERTS
-    flist = TET_FACES if etype == "tet" else PRI_FACES
-    return verts, flist
+    return {"tet": (TET_VERTS, TET_FACES), "pri": (PRI_VERTS, PRI_FACES),
+            "hex": (HEX_VERTS, HEX_FACES)}[etype]
 
 
 def _face_geometry(verts, fv):

@@ -3,7 +3,9 @@
 Readings: tets are affine, x = sum_a lambda_a(xi) X_a with the barycentric
 lambda of the reference tet.  Prisms use the linear-triangle x linear-zeta
 map x = sum_a tau_a(xi, eta) [(1-zeta)/2 X_a + (1+zeta)/2 X_{a+3}],
-which is not affine once nodes are jittered.  Writing A = dx/dxi (columns
+which is not affine once nodes are jittered.  Hexes use the trilinear map
+x = sum_a N_a(xi) X_a, N_a = (1 + s_a0 xi)(1 + s_a1 eta)(1 + s_a2 zeta)/8
+with s_a the signs of reference vertex a.  Writing A = dx/dxi (columns
 a_d = dx/dxi_d), the transformed-flux matrix is S = J dxi/dx = adj(A),
 whose rows are a_1 x a_2, a_2 x a_0, a_0 x a_1.  A flux F in physical space
 becomes F~_d = sum_m S[d][m] F_m in reference space; at a face with
@@ -27,6 +29,14 @@ def shape(etype, ref):
         dN[:, 1, 0] = 0.5
         dN[:, 2, 1] = 0.5
         dN[:, 3, 2] = 0.5
+        return N, dN
+    if etype == "hex":
+        sg = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+                       [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], dtype=np.float64)
+        f = [1.0 + sg[None, :, k] * ref[:, k:k + 1] for k in range(3)]    # (npt, 8)
+        N = f[0] * f[1] * f[2] / 8.0
+        dN = np.stack([sg[None, :, 0] * f[1] * f[2], f[0] * sg[None, :, 1] * f[2],
+                       f[0] * f[1] * sg[None, :, 2]], axis=-1) / 8.0
         return N, dN
     tau = np.stack([-(xi + eta) / 2, (1 + xi) / 2, (1 + eta) / 2], axis=1)
     dtau = np.array([[-0.5, -0.5], [0.5, 0.0], [0.0, 0.5]])   # d tau_a / d(xi, eta)

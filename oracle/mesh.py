@@ -7,7 +7,7 @@ be the periodic translate (by a combination of the mesh's period vectors) of
 another such face, else the mesh is rejected.  Flux points of two matched
 faces are paired by physical position (after the periodic shift).
 Everything is indexed by a global flux-point id: tets first, element-major,
-then prisms.
+then prisms, then hexes.
 """
 from __future__ import annotations
 
@@ -18,7 +18,7 @@ from scipy.spatial import cKDTree
 
 from . import basis, geometry
 
-ETYPES = ("tet", "pri")
+ETYPES = ("tet", "pri", "hex")
 
 
 class MeshError(ValueError):
@@ -30,7 +30,8 @@ class Mesh:
         self.p = p
         xyz = np.asarray(m["xyz"], dtype=np.float64)
         conn = {"tet": np.asarray(m["tet"], dtype=np.int64).reshape(-1, 4),
-                "pri": np.asarray(m["pri"], dtype=np.int64).reshape(-1, 6)}
+                "pri": np.asarray(m["pri"], dtype=np.int64).reshape(-1, 6),
+                "hex": np.asarray(m.get("hex", np.zeros((0, 8))), dtype=np.int64).reshape(-1, 8)}
         self.period = np.asarray(m.get("period", np.zeros(3)), dtype=np.float64)
         bface = np.asarray(m.get("bface", np.zeros((0, 4))), dtype=np.int64).reshape(-1, 4)
         self.types = [t for t in ETYPES if len(conn[t]) > 0]

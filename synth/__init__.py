@@ -9,8 +9,8 @@ geometry factors, no face matching.  Both implementations compute those on
 their own from what this package returns.
 """
 from .meshgen import (  # noqa: F401
-    BC_WALL, BC_FARFIELD, ETYPE_TET, ETYPE_PRI, TET_FACES, PRI_FACES,
-    layered_box, vortex_box, boundary_layer_box, wall_channel, tgv_box, batch_problem_params,
+    BC_WALL, BC_FARFIELD, ETYPE_TET, ETYPE_PRI, ETYPE_HEX, TET_FACES, PRI_FACES, HEX_FACES,
+    layered_box, vortex_box, hex_box, boundary_layer_box, wall_channel, tgv_box, batch_problem_params,
     batch_problem_mesh, mesh_counts,
 )
 from .ics import (  # noqa: F401

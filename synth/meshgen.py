@@ -1,10 +1,14 @@
-"""Structured-then-split mixed prism/tetrahedron meshes with seeded node jitter.
+"""Structured-then-split mixed hexahedron/prism/tetrahedron meshes with
+seeded node jitter.
 
 Every mesh is a logically structured box of hexahedral cells.  The cells of
 the first ``n_prism_layers`` layers along ``layer_axis`` are each split into
-two triangular prisms extruded along that axis; the remaining cells are each
-split into six Kuhn (Freudenthal) tetrahedra along the cell's min-to-max
-diagonal.  The prism base quads are cut along the same min-to-max diagonal,
+two triangular prisms extruded along that axis, except those of the first
+``n_hex_cols`` cell columns along the first base axis, which stay
+hexahedra (they meet the prisms on vertical quad faces); the remaining cells
+are each split into six Kuhn (Freudenthal) tetrahedra along the cell's
+min-to-max diagonal (a mesh with hexahedra has no tetrahedral layers, since
+a hexahedron's quad face cannot meet two tetrahedra conformingly).  The prism base quads are cut along the same min-to-max diagonal,
 so every face is conforming, including the prism/tet transition and all
 periodic wraps.  This stands in for the paper's mixed cylinder mesh
 (prisms in the near-wall layer, tets in the far field; Sec. 3.3), which is
@@ -18,12 +22,15 @@ Vertex order conventions (the only conventions the mesh format carries):
   vertices 3..5 the top triangle (zeta=+1), vertex a+3 above vertex a;
   local faces are the vertex lists in ``PRI_FACES`` (two triangles, then
   three quads).
+* hex: vertices 0..3 the bottom face (reference zeta=-1) counter-clockwise
+  from reference vertex (-1,-1,-1), vertex a+4 above vertex a; local faces
+  are the vertex quadruples in ``HEX_FACES``.
 
-Both element kinds are emitted with positive orientation.
+Every element is emitted with positive orientation.
 
 Returned meshes are dicts with
 ``xyz`` (n_nodes, 3) float64, ``tet`` (n_tet, 4) int64, ``pri`` (n_pri, 6)
-int64, ``bface`` (n_bface, 4) int64 rows (etype, elem, local face, bc tag)
+int64, ``hex`` (n_hex, 8) int64, ``bface`` (n_bface, 4) int64 rows (etype, elem, local face, bc tag)
 and ``period`` (3,) float64 (0 = axis not periodic).
 """
 from __future__ import annotations
@@ -35,11 +42,14 @@ import numpy as np
 
 ETYPE_TET = 0
 ETYPE_PRI = 1
+ETYPE_HEX = 2
 BC_WALL = 1        # no-slip isothermal wall
 BC_FARFIELD = 2    # Riemann-invariant far field
 
 TET_FACES = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
 PRI_FACES = ((0, 1, 2), (3, 4, 5), (0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5))
+HEX_FACES = ((0, 1, 2, 3), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7),
+             (4, 5, 6, 7))
 
 # (a0, a1, a2) axis orders that are even permutations of (x, y, z), keyed by
 # the layer axis a2; a base triangle counter-clockwise in (a0, a1) extruded
@@ -52,7 +62,7 @@ def _rng(seed):
 
 
 def layered_box(coords, layer_axis, n_prism_layers, periodic, bcs=None,
-                jitter=0.0, seed=0):
+                jitter=0.0, seed=0, n_hex_cols=0):
     """Build a mixed prism/tet box mesh.
 
     coords: three increasing 1-D arrays, the node coordinates along x, y, z.
@@ -67,6 +77,9 @@ def layered_box(coords, layer_axis, n_prism_layers, periodic, bcs=None,
         nodes on non-periodic boundaries are not moved, and periodic images
         move identically.
     seed: PCG64 seed of the jitter.
+    n_hex_cols: the cells of the prism layers whose index along the first
+        base axis is below this stay hexahedra (needs n_prism_layers equal
+        to the number of cell layers).
     """
     bcs = dict(bcs or {})
     axes = _AXES[layer_axis]
@@ -74,6 +87,8 @@ def layered_box(coords, layer_axis, n_prism_layers, periodic, bcs=None,
     ncell = [len(c) - 1 for c in ax_coords]
     nnode = [n + 1 for n in ncell]
     per = [bool(periodic[a]) for a in axes]
+    if n_hex_cols > 0 and n_prism_layers < ncell[2]:
+        raise ValueError("hexahedra need every cell layer in the prism/hex part")
 
     # node grid in (a0, a1, a2) order, id = (i2 * nn1 + i1) * nn0 + i0
     g0, g1, g2 = np.meshgrid(*ax_coords, indexing="ij")
@@ -122,7 +137,17 @@ def layered_box(coords, layer_axis, n_prism_layers, periodic, bcs=None,
     c0 = c0.ravel(order="F")
     c1 = c1.ravel(order="F")
     c2 = c2.ravel(order="F")
-    is_pri_cell = c2 < n_prism_layers
+    is_hex_cell = (c2 < n_prism_layers) & (c0 < n_hex_cols)
+    is_pri_cell = (c2 < n_prism_layers) & ~is_hex_cell
+
+    hc0, hc1, hc2 = c0[is_hex_cell], c1[is_hex_cell], c2[is_hex_cell]
+    hverts, hgidx = [], []
+    for (d0, d1, d2) in ((0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0),
+                         (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)):
+        hverts.append(nid(hc0 + d0, hc1 + d1, hc2 + d2))
+        hgidx.append(np.stack([hc0 + d0, hc1 + d1, hc2 + d2], axis=-1))
+    hexa = np.stack(hverts, axis=-1).reshape(-1, 8)
+    hex_g = np.stack(hgidx, axis=1).reshape(-1, 8, 3)
 
     pri_list, pri_gidx = [], []
     tet_list, tet_gidx = [], []
@@ -138,7 +163,8 @@ def layered_box(coords, layer_axis, n_prism_layers, periodic, bcs=None,
         pri_list.append(np.stack(verts, axis=-1))
         pri_gidx.append(np.stack(gidx, axis=1))
     # Kuhn tets: monotone lattice paths from (0,0,0) to (1,1,1)
-    tc0, tc1, tc2 = c0[~is_pri_cell], c1[~is_pri_cell], c2[~is_pri_cell]
+    is_tet_cell = c2 >= n_prism_layers
+    tc0, tc1, tc2 = c0[is_tet_cell], c1[is_tet_cell], c2[is_tet_cell]
     for perm in itertools.permutations(range(3)):
         path = [np.zeros(3, dtype=np.int64)]
         for k in perm:
@@ -168,7 +194,8 @@ def layered_box(coords, layer_axis, n_prism_layers, periodic, bcs=None,
     # boundary faces on non-periodic sides
     bface = []
     for etype, conn_g, faces in ((ETYPE_TET, tet_g, TET_FACES),
-                                 (ETYPE_PRI, pri_g, PRI_FACES)):
+                                 (ETYPE_PRI, pri_g, PRI_FACES),
+                                 (ETYPE_HEX, hex_g, HEX_FACES)):
         if len(conn_g) == 0:
             continue
         for lf, fv in enumerate(faces):
@@ -192,7 +219,8 @@ def layered_box(coords, layer_axis, n_prism_layers, periodic, bcs=None,
         if per[k]:
             period[a] = ax_coords[k][-1] - ax_coords[k][0]
     return {"xyz": np.ascontiguousarray(xyz), "tet": tet.astype(np.int64),
-            "pri": pri.astype(np.int64), "bface": bface, "period": period}
+            "pri": pri.astype(np.int64), "hex": hexa.astype(np.int64), "bface": bface,
+            "period": period}
 
 
 def vortex_box(n=4, jitter=0.05, seed=0, n_prism_layers=None, lo=-5.0, hi=5.0):
@@ -224,16 +252,18 @@ def boundary_layer_box(nx=75, nz=12, n_prism_layers=32, n_tet_layers=22,
 
 
 def wall_channel(nx=3, ny=3, nz=2, n_prism_layers=2, lx=2.0, ly=1.5, lz=1.0,
-                 jitter=0.05, seed=4):
+                 jitter=0.05, seed=4, n_hex_cols=0):
     """Box [0,lx]x[0,ly]x[0,lz] periodic in x and z with a no-slip wall at
     y=0 and far field at y=ly; the lowest n_prism_layers cell layers are
-    prisms (extruded along y), the rest Kuhn tets."""
+    prisms (extruded along y), the rest Kuhn tets; with n_hex_cols > 0
+    (and n_prism_layers = ny) the first n_hex_cols cell columns along the
+    first base axis (z) are hexahedra."""
     x = np.linspace(0.0, lx, nx + 1)
     y = np.linspace(0.0, ly, ny + 1)
     z = np.linspace(0.0, lz, nz + 1)
     bcs = {(1, 0): BC_WALL, (1, 1): BC_FARFIELD}
     return layered_box((x, y, z), 1, n_prism_layers, (True, False, True),
-                       bcs=bcs, jitter=jitter, seed=seed)
+                       bcs=bcs, jitter=jitter, seed=seed, n_hex_cols=n_hex_cols)
 
 
 def tgv_box(n=24, jitter=0.0, seed=0):
@@ -241,6 +271,16 @@ def tgv_box(n=24, jitter=0.0, seed=0):
     c = np.linspace(0.0, 2.0 * math.pi, n + 1)
     return layered_box((c, c, c), 2, n // 2, (True, True, True), jitter=jitter,
                        seed=seed)
+
+
+def hex_box(n=4, n_hex_cols=None, jitter=0.05, seed=0, lo=-5.0, hi=5.0):
+    """Periodic cube [lo,hi]^3 of n^3 cells extruded along z: the first
+    n_hex_cols columns along x hexahedra (all of them by default), the rest
+    prism pairs."""
+    c = np.linspace(lo, hi, n + 1)
+    nh = n if n_hex_cols is None else n_hex_cols
+    return layered_box((c, c, c), 2, n, (True, True, True), jitter=jitter,
+                       seed=seed, n_hex_cols=nh)
 
 
 def mesh_counts(mesh):

@@ -12,6 +12,13 @@ PRI_V = np.array([[-1, -1, -1], [1, -1, -1], [-1, 1, -1],
                   [-1, -1, 1], [1, -1, 1], [-1, 1, 1]], float)
 TET_F = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
 PRI_F = ((0, 1, 2), (3, 4, 5), (0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5))
+HEX_V = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+                  [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], float)
+HEX_F = ((0, 1, 2, 3), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7), (4, 5, 6, 7))
+
+
+def ref_verts_faces(etype):
+    return {"tet": (TET_V, TET_F), "pri": (PRI_V, PRI_F), "hex": (HEX_V, HEX_F)}[etype]
 
 
 def gl01(n):
@@ -51,6 +58,11 @@ def ref_rule(etype, n=12):
     if etype == "tet":
         p, w = unit_tet_rule(n)
         return -1 + 2 * p, 8 * w
+    if etype == "hex":
+        x, wx = leggauss(n)
+        pts = np.array([(a, b, c) for c in x for b in x for a in x])
+        wts = np.array([wa * wb * wc for wc in wx for wb in wx for wa in wx])
+        return pts, wts
     tp, tw = unit_triangle_rule(n)
     z, wz = leggauss(n)
     pts = np.array([(-1 + 2 * x, -1 + 2 * y, zz) for zz in z for (x, y) in tp])
@@ -83,6 +95,8 @@ def space_exponents(etype, p):
     if etype == "tet":
         return [(a, b, c) for a in range(p + 1) for b in range(p + 1)
                 for c in range(p + 1) if a + b + c <= p]
+    if etype == "hex":
+        return [(a, b, c) for a in range(p + 1) for b in range(p + 1) for c in range(p + 1)]
     return [(a, b, c) for a in range(p + 1) for b in range(p + 1)
             for c in range(p + 1) if a + b <= p]
 

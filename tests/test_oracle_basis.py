@@ -14,7 +14,7 @@ from oracle import basis
 from tests import _quad as Q
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-CASES = [(t, p) for t in ("tet", "pri") for p in (1, 2, 3, 4)]
+CASES = [(t, p) for t in ("tet", "pri", "hex") for p in (1, 2, 3, 4)]
 
 
 def _table2():
@@ -30,7 +30,7 @@ def _table2():
 
 @pytest.mark.parametrize("etype,p", CASES)
 def test_table2_dimensions(etype, p):
-    """Table 2 prints dim M0 as Nupts x Nfpts for tet and prism at p=1..4."""
+    """Table 2 prints dim M0 as Nupts x Nfpts for tet, prism and hex at p=1..4."""
     nu, nf = _table2()[(etype, p)]
     op = basis.operators(etype, p)
     assert op.M0.shape == (nf, nu)
@@ -40,6 +40,8 @@ def test_table2_dimensions(etype, p):
 def _inside(etype, x, tol=1e-12):
     if etype == "tet":
         return (np.all(x >= -1 - tol, axis=1) & (x.sum(1) <= -1 + tol))
+    if etype == "hex":
+        return np.all(np.abs(x) <= 1 + tol, axis=1)
     return ((x[:, 0] >= -1 - tol) & (x[:, 1] >= -1 - tol) &
             (x[:, 0] + x[:, 1] <= tol) & (np.abs(x[:, 2]) <= 1 + tol))
 
@@ -59,8 +61,7 @@ def test_face_point_sets_symmetric(etype, p):
     symmetries, so two neighbours' points coincide whatever their local
     orientation."""
     op = basis.operators(etype, p)
-    V = Q.TET_V if etype == "tet" else Q.PRI_V
-    F = Q.TET_F if etype == "tet" else Q.PRI_F
+    V, F = Q.ref_verts_faces(etype)
     for fi, fv in enumerate(F):
         pts = op.fpts[op.fface == fi]
         verts = V[list(fv)]
@@ -112,7 +113,7 @@ def test_weights_integrate_space_exactly(etype, p):
     c = rng.normal(size=len(ex))
     exact = qw @ Q.eval_poly(c, ex, qp)
     assert abs(op.w @ Q.eval_poly(c, ex, op.upts) - exact) < 1e-12
-    assert abs(op.w.sum() - (4.0 / 3.0 if etype == "tet" else 4.0)) < 1e-13
+    assert abs(op.w.sum() - {"tet": 4.0 / 3.0, "pri": 4.0, "hex": 8.0}[etype]) < 1e-13
 
 
 @pytest.mark.parametrize("etype,p", CASES)
@@ -121,8 +122,7 @@ def test_face_weights(etype, p):
     random element polynomials)."""
     op = basis.operators(etype, p)
     ex = Q.space_exponents(etype, p)
-    V = Q.TET_V if etype == "tet" else Q.PRI_V
-    F = Q.TET_F if etype == "tet" else Q.PRI_F
+    V, F = Q.ref_verts_faces(etype)
     rng = np.random.default_rng(3)
     c = rng.normal(size=len(ex))
     for fi, fv in enumerate(F):
@@ -139,8 +139,7 @@ def test_lift_galerkin_identity(etype, p):
     for every v of the element space (brute force on one element)."""
     op = basis.operators(etype, p)
     ex = Q.space_exponents(etype, p)
-    V = Q.TET_V if etype == "tet" else Q.PRI_V
-    F = Q.TET_F if etype == "tet" else Q.PRI_F
+    V, F = Q.ref_verts_faces(etype)
     rng = np.random.default_rng(4)
     qcoef = [rng.normal(size=len(ex)) for _ in F]
     delta = np.zeros(op.nf)

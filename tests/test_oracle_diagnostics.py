@@ -28,11 +28,14 @@ P0 = 1.0 / GAMMA
 
 
 def _channel_solver(npl, p, mu=0.01, **kw):
-    mesh = synth.wall_channel(n_prism_layers=npl, **kw)
+    if npl == "hex":   # hexahedra beside prisms, all layers
+        mesh = synth.wall_channel(n_prism_layers=3, n_hex_cols=1, **kw)
+    else:
+        mesh = synth.wall_channel(n_prism_layers=npl, **kw)
     return Solver(mesh, p, viscous=True, mu=mu, t_wall=P0)
 
 
-@pytest.mark.parametrize("npl", [2, 0])  # prism wall faces, tet wall faces
+@pytest.mark.parametrize("npl", [2, 0, "hex"])  # prism, tet, hex + prism wall faces
 def test_wall_force_at_rest_is_pressure_times_area(npl):
     s = _channel_solver(npl, 2)
     X = s.upts_xyz_points()
@@ -44,7 +47,7 @@ def test_wall_force_at_rest_is_pressure_times_area(npl):
     assert np.max(np.abs(f_vis)) < 1e-13 * P0 * area
 
 
-@pytest.mark.parametrize("npl", [2, 0])
+@pytest.mark.parametrize("npl", [2, 0, "hex"])
 @pytest.mark.parametrize("p", [2, 3])
 def test_wall_force_of_plane_shear(npl, p):
     mu, a = 0.01, 0.3

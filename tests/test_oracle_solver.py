@@ -25,6 +25,14 @@ def _solver(mesh, p, **kw):
     return Solver(mesh, p, **kw)
 
 
+def _box(kind, n=4):
+    """Periodic [-5,5]^3 test meshes: 'pt' prisms below Kuhn tets, 'hp'
+    hexahedra beside prism pairs, 'hex' hexahedra only."""
+    if kind == "pt":
+        return synth.vortex_box(n=n)
+    return synth.hex_box(n=n, n_hex_cols=n // 2 if kind == "hp" else n)
+
+
 # --------------------------------------------------------------------------
 # geometry
 # --------------------------------------------------------------------------
@@ -181,10 +189,11 @@ def test_wall_ghost_has_zero_mass_flux():
 # --------------------------------------------------------------------------
 # RHS invariants
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["pt", "hp", "hex"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("viscous", [False, True])
-def test_freestream_preservation_periodic(p, viscous):
-    s = _solver(synth.vortex_box(), p, viscous=viscous, mu=0.05)
+def test_freestream_preservation_periodic(kind, p, viscous):
+    s = _solver(_box(kind), p, viscous=viscous, mu=0.05)
     xyz = s.upts_xyz_points()
     u = s.state_from_points(synth.uniform_state(xyz, vel=(0.3, -0.2, 0.5), p=1.0))
     assert np.max(np.abs(s.rhs(u))) < 1e-12
@@ -202,10 +211,11 @@ def test_freestream_preservation_farfield_box(viscous):
     assert np.max(np.abs(s.rhs(u))) < 1e-11 * pinf
 
 
+@pytest.mark.parametrize("kind", ["pt", "hp"])
 @pytest.mark.parametrize("p", [1, 2, 4])
 @pytest.mark.parametrize("viscous", [False, True])
-def test_discrete_conservation(p, viscous):
-    s = _solver(synth.vortex_box(), p, viscous=viscous, mu=0.05)
+def test_discrete_conservation(kind, p, viscous):
+    s = _solver(_box(kind), p, viscous=viscous, mu=0.05)
     xyz = s.upts_xyz_points()
     u = s.state_from_points(synth.random_smooth_state(xyz, seed=p))
     r = s.rhs(u)
@@ -221,12 +231,13 @@ def _permuted_mesh(mesh, perm):
     return m
 
 
+@pytest.mark.parametrize("kind", ["pt", "hp"])
 @pytest.mark.parametrize("p", [2, 3])
-def test_axis_permutation_equivariance(p):
+def test_axis_permutation_equivariance(kind, p):
     """Cyclically permuting the coordinates of mesh and flow permutes the
     momentum components of the RHS (Euler; every face is re-used under
     another axis, which exercises the face bookkeeping)."""
-    mesh = synth.vortex_box()
+    mesh = _box(kind)
     perm = [1, 2, 0]
     s1 = _solver(mesh, p)
     s2 = _solver(_permuted_mesh(mesh, perm), p)
@@ -243,25 +254,27 @@ def test_axis_permutation_equivariance(p):
         np.testing.assert_allclose(r2[t][:, 1:4], r1[t][:, 1:4][:, perm], atol=1e-12)
 
 
-def test_element_renumbering_invariance():
+@pytest.mark.parametrize("kind", ["pt", "hp"])
+def test_element_renumbering_invariance(kind):
     """Shuffling element order (and hence face discovery order and the
     a/b roles of every interface) shuffles the NS RHS and nothing else."""
-    mesh = synth.vortex_box()
+    mesh = _box(kind)
     rng = np.random.default_rng(12)
-    pt = rng.permutation(len(mesh["tet"]))
-    pp = rng.permutation(len(mesh["pri"]))
     m2 = dict(mesh)
-    m2["tet"] = mesh["tet"][pt]
-    m2["pri"] = mesh["pri"][pp]
+    perms = {}
+    for t in ("tet", "pri", "hex"):
+        if t in mesh and len(mesh[t]):
+            perms[t] = rng.permutation(len(mesh[t]))
+            m2[t] = mesh[t][perms[t]]
     s1 = _solver(mesh, 2, viscous=True, mu=0.05)
     s2 = _solver(m2, 2, viscous=True, mu=0.05)
     u1 = s1.state_from_points(synth.random_smooth_state(s1.upts_xyz_points(), seed=6))
     u1s = s1.split(u1)
-    u2 = s2.join({"tet": u1s["tet"][pt], "pri": u1s["pri"][pp]})
+    u2 = s2.join({t: u1s[t][q] for t, q in perms.items()})
     r1 = s1.split(s1.rhs(u1))
     r2 = s2.split(s2.rhs(u2))
-    np.testing.assert_allclose(r2["tet"], r1["tet"][pt], atol=1e-12)
-    np.testing.assert_allclose(r2["pri"], r1["pri"][pp], atol=1e-12)
+    for t, q in perms.items():
+        np.testing.assert_allclose(r2[t], r1[t][q], atol=1e-12)
 
 
 # --------------------------------------------------------------------------
@@ -336,7 +349,13 @@ def test_manufactured_euler_residual_converges(p):
     _manufactured_rates(p, viscous=False, ns=(4, 8, 16), min_rate=p - 0.2)
 
 
-def _manufactured_rates(p, viscous, ns, min_rate):
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_manufactured_euler_residual_converges_hex_prism(p):
+    """The same on hexahedra beside prism pairs (n = 4, 8, 16)."""
+    _manufactured_rates(p, viscous=False, ns=(4, 8, 16), min_rate=p - 0.2, kind="hp")
+
+
+def _manufactured_rates(p, viscous, ns, min_rate, kind="pt"):
     sp = pytest.importorskip("sympy")
     X = sp.symbols("x y z")
     x, y, z = X
@@ -372,7 +391,7 @@ def _manufactured_rates(p, viscous, ns, min_rate):
 
     errs = []
     for n in ns:
-        s = _solver(synth.vortex_box(n=n), p, viscous=viscous, mu=float(mu), prandtl=0.72)
+        s = _solver(_box(kind, n=n), p, viscous=viscous, mu=float(mu), prandtl=0.72)
         xyz = s.upts_xyz_points()
         u = s.state_from_points(ev(fU, xyz))
         errs.append(_l2(s, s.rhs(u) - s.state_from_points(ev(fR, xyz))))
@@ -388,6 +407,12 @@ def test_manufactured_navier_stokes_residual_converges(p):
     a wrong term in the viscous flux, gradient or LDG treatment leaves an
     O(1) residual and a rate near 0.  Observed order >= p - 1.2 on n = 4, 8."""
     _manufactured_rates(p, viscous=True, ns=(4, 8), min_rate=p - 1.2)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_manufactured_navier_stokes_residual_converges_hex(p):
+    """The same on an all-hexahedral mesh."""
+    _manufactured_rates(p, viscous=True, ns=(4, 8), min_rate=p - 1.2, kind="hex")
 
 
 def test_rk4_amplification(monkeypatch):

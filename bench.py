@@ -99,7 +99,7 @@ def _nnz(fr, etype, order, which):
 
 
 def gemm_flops(ctx, kclass):
-    """Algorithmic FP64 flops of one launch class, summed over both element
+    """Algorithmic FP64 flops of one launch class, summed over the element
     types, for one RHS evaluation: 2 x (non-zero operator entries) x
     (5 variables x elements) per operator application (x3 columns for M0
     on the gradients)."""
@@ -107,7 +107,8 @@ def gemm_flops(ctx, kclass):
     i = ctx.info
     p = ctx.order
     tot = 0.0
-    for et, ne in ((0, i["n_tet"]), (1, i["n_pri"])):
+    for et, name in enumerate(("tet", "pri", "hex")):
+        ne = i["n_" + name]
         if ne == 0:
             continue
         cols = 5.0 * ne
@@ -123,7 +124,7 @@ def gemm_flops(ctx, kclass):
 
 
 def gemm_bytes_f32(ctx, kclass):
-    """Algorithmic DRAM bytes of one launch class (both element types) per
+    """Algorithmic DRAM bytes of one launch class (all element types) per
     RHS in the FP32-storage modes (4-byte state): operator input and output
     once, plus the epilogue's own reads and writes: the geometry S^T/J for
     the gradient (10 floats per point), and for the divergence with the
@@ -132,7 +133,7 @@ def gemm_bytes_f32(ctx, kclass):
     stage input)."""
     i = ctx.info
     tot = 0.0
-    for ne, nu, nf in ((i["n_tet"], i["nu_tet"], i["nf_tet"]), (i["n_pri"], i["nu_pri"], i["nf_pri"])):
+    for ne, nu, nf in ((i["n_" + t], i["nu_" + t], i["nf_" + t]) for t in ("tet", "pri", "hex")):
         if ne == 0:
             continue
         cols = 5.0 * ne
@@ -353,7 +354,7 @@ def state_error_study(fr, torch, nsteps, sp):
         for name, prec in (("fp64", fr.FR_FP64), ("fp32", fr.FR_FP32), ("bf16x3", fr.FR_BF16X3),
                            ("tf32x3", fr.FR_TF32X3)):
             ctx = fr.Context(mesh, order, **flow_params(), precision=prec)
-            counts = [(ctx.info["n_tet"], ctx.info["nu_tet"]), (ctx.info["n_pri"], ctx.info["nu_pri"])]
+            counts = ctx.counts()
             u0 = points_to_public(synth_mod().perturbed_freestream(ctx.upts_points(), seed=2,
                                                                    wall_delta=WALL_DELTA), counts)
             ctx.set_state(u0, sp)
@@ -403,7 +404,7 @@ def batch_mode(fr, torch, args, sp):
     dts = []
     for c, m, p in zip(b.problems, meshes, orders):
         q = synth.isentropic_vortex(c.upts_points())
-        counts = [(c.info["n_tet"], c.info["nu_tet"]), (c.info["n_pri"], c.info["nu_pri"])]
+        counts = c.counts()
         c.set_state(points_to_public(q, counts), sp)
         # |v| + c <= 1.6 + 1.2 for the vortex
         dts.append(0.1 * min_edge(m) / (2.8 * (p + 1) ** 2))
@@ -518,7 +519,7 @@ def learned_mode(fr, torch, args, sp):
     c4 = fr.Context(mesh, 4, **tgv_params(fr.FR_FP64))
     c4f = fr.Context(mesh, 4, **tgv_params(fr.FR_FP32))
     c2 = fr.Context(mesh, 2, **tgv_params(fr.FR_FP64))
-    counts4 = [(c4.info["n_tet"], c4.info["nu_tet"]), (c4.info["n_pri"], c4.info["nu_pri"])]
+    counts4 = c4.counts()
     q = synth.taylor_green(c4.upts_points(), GAMMA, TGV_MACH)
     u0 = points_to_public(q, counts4)
     rho, vel = q[:, 0], q[:, 1:4] / q[:, :1]
@@ -711,7 +712,7 @@ def main():
     mesh = synth.boundary_layer_box(nx=args.nx)
     prec = {"fp64": fr.FR_FP64, "fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3, "tf32x3": fr.FR_TF32X3}[args.precision]
     ctx = fr.Context(mesh, ORDER, **flow_params(), precision=prec)
-    counts = [(ctx.info["n_tet"], ctx.info["nu_tet"]), (ctx.info["n_pri"], ctx.info["nu_pri"])]
+    counts = ctx.counts()
     u0 = points_to_public(synth.perturbed_freestream(ctx.upts_points(), seed=2,
                                                      wall_delta=WALL_DELTA), counts)
     dt = time_step_size(mesh, ORDER)

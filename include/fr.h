@@ -3,7 +3,8 @@
  *
  * The engine evaluates the FR semi-discretisation of the compressible Euler
  * and Navier-Stokes equations (constant viscosity, Sec. 3.4) on mixed
- * prism/tetrahedral meshes (Sec. 3.3) and advances it with classic RK4
+ * prism/tetrahedral meshes (Sec. 3.3) and on hexahedral meshes (Sec. 3.2;
+ * Table 2 lists tets, prisms and hexes) and advances it with classic RK4
  * (Table 1 lists Euler, RK4 and RK45 steppers).  Every operator application
  * is a constant operator matrix times a row-major state matrix,
  * C <- c1 A B + c2 C (Sec. 2.1, Eq. 1); everything else is point-wise
@@ -16,18 +17,23 @@
  * ideal gas p = (gamma-1)(E - rho|v|^2/2).
  *
  * Public state layout ("public layout"): one float64 array, tetrahedra
- * first then prisms, each block [element][variable][solution point]
+ * first, then prisms, then hexahedra, each block
+ * [element][variable][solution point]
  * (element slowest, point fastest).  Its length is fr_ndof().
  *
  * Element vertex order: tet vertices 0..3 map to reference vertices
  * (-1,-1,-1), (1,-1,-1), (-1,1,-1), (-1,-1,1).  Prism vertices 0..2 form the
  * zeta=-1 triangle (-1,-1), (1,-1), (-1,1); vertex a+3 lies above vertex a
- * at zeta=+1.  Local faces: tet (0,1,2), (0,1,3), (0,2,3), (1,2,3); prism
- * (0,1,2), (3,4,5), (0,1,4,3), (1,2,5,4), (2,0,3,5).
+ * at zeta=+1.  Hex vertices 0..3 are the zeta=-1 face (-1,-1), (1,-1),
+ * (1,1), (-1,1); vertex a+4 lies above vertex a at zeta=+1.  Local faces:
+ * tet (0,1,2), (0,1,3), (0,2,3), (1,2,3); prism (0,1,2), (3,4,5),
+ * (0,1,4,3), (1,2,5,4), (2,0,3,5); hex (0,1,2,3), (0,1,5,4), (1,2,6,5),
+ * (2,3,7,6), (3,0,4,7), (4,5,6,7).
  *
  * Solution points: the Blyth-Pozrikidis barycentric set built from the p+1
  * Gauss-Legendre nodes (tet: order k, j, i slowest to fastest; prism:
- * triangle set x Gauss-Legendre in zeta, zeta slowest).  The paper fixes only
+ * triangle set x Gauss-Legendre in zeta, zeta slowest); hex: the
+ * Gauss-Legendre tensor points, zeta slowest, xi fastest.  The paper fixes only
  * their number (Table 2).
  *
  * Errors: every int-returning call returns FR_OK (0) or a negative FR_ERR_*
@@ -45,6 +51,7 @@ extern "C" {
 #endif
 
 #define FR_NVARS 5
+#define FR_NTYPES 3 /* element types: FR_ETYPE_TET, FR_ETYPE_PRI, FR_ETYPE_HEX */
 
 enum {
     FR_OK = 0,
@@ -57,7 +64,7 @@ enum {
     FR_ERR_UNSUPPORTED = -7 /* valid request this build does not implement */
 };
 
-enum { FR_ETYPE_TET = 0, FR_ETYPE_PRI = 1 };
+enum { FR_ETYPE_TET = 0, FR_ETYPE_PRI = 1, FR_ETYPE_HEX = 2 };
 enum { FR_BC_WALL = 1, FR_BC_FARFIELD = 2 };
 /* Arithmetic of the operator applications (Table 1: single and double;
  * FR_BF16X3 / FR_TF32X3: FP32 storage with the operator applications on the
@@ -75,6 +82,8 @@ typedef struct {
     const int64_t *tet;   /* [n_tet][4] node ids, vertex order above */
     int64_t n_pri;
     const int64_t *pri;   /* [n_pri][6] node ids, vertex order above */
+    int64_t n_hex;
+    const int64_t *hex;   /* [n_hex][8] node ids, vertex order above */
     int64_t n_bface;
     const int64_t *bface; /* [n_bface][4]: etype, element, local face, bc tag */
     double period[3];     /* periodic translation per axis; 0 = not periodic */
@@ -118,9 +127,9 @@ void fr_destroy(fr_ctx *ctx);
 int fr_ndof(const fr_ctx *ctx, int64_t *ndof);
 
 /*
- * fr_info: sizes of the context.  out (caller-owned, 8 int64) receives
+ * fr_info: sizes of the context.  out (caller-owned, 11 int64) receives
  * n_tet, n_pri, order, nupts(tet), nupts(pri), nfpts(tet), nfpts(pri),
- * number of interface flux-point pairs.
+ * number of interface flux-point pairs, n_hex, nupts(hex), nfpts(hex).
  */
 int fr_info(const fr_ctx *ctx, int64_t *out);
 

@@ -130,7 +130,7 @@ Phys phys_of(const fr_ctx *c) {
 template <typename T>
 FieldsT<T> fields_of(const fr_ctx *c) {
     FieldsT<T> F{};
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         F.UF[t] = (const T *)c->T[t].UF;
         F.DUF[t] = (T *)c->T[t].DUF;
         F.GUF[t] = (const T *)c->T[t].GUF;
@@ -294,12 +294,12 @@ int check_tc(fr_ctx *c) {
 }
 
 template <typename T>
-int front_stages(fr_ctx *c, T *const in[2], cudaStream_t s) {
+int front_stages(fr_ctx *c, T *const in[NT], cudaStream_t s) {
     const Phys ph = phys_of(c);
     const FieldsT<T> F = fields_of<T>(c);
     int rc;
     // 1. interpolate to flux points
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         if (!c->T[t].present) continue;
         const GemmArgsT<T> g = args_m0<T>(c, t, in[t]);
         if ((rc = cuda_check(launch(c, K_M0, s, [&] { return op_gemm<T>(c, t, 0, g, s); }), "gemm M0"))) return rc;
@@ -311,7 +311,7 @@ int front_stages(fr_ctx *c, T *const in[2], cudaStream_t s) {
                              "common solution")))
             return rc;
         // 3. corrected physical gradient; 4. gradient at flux points
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < NT; ++t) {
             if (!c->T[t].present) continue;
             const GemmArgsT<T> g = args_grad<T>(c, t, in[t]);
             if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return op_gemm<T>(c, t, 1, g, s); }), "gemm grad")))
@@ -325,13 +325,13 @@ int front_stages(fr_ctx *c, T *const in[2], cudaStream_t s) {
 }
 
 template <typename T>
-int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
+int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
     const Phys ph = phys_of(c);
     const FieldsT<T> F = fields_of<T>(c);
     int rc;
     if ((rc = front_stages<T>(c, in, s))) return rc;
     // 5. transformed flux at solution points
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch(c, K_FLUX, s,
@@ -353,7 +353,7 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
     // the RK update (its FP64 register traffic would otherwise stall the
     // GEMM's epilogue warps).
     const bool split_rk = rk && is_tc(c);
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         GemmArgsT<T> g = args_div<T>(c, t, split_rk ? nullptr : rk);
@@ -377,7 +377,7 @@ int rhs_internal(fr_ctx *c, T *const in[2], const RKStage *rk, cudaStream_t s) {
 
 int64_t ndof_of(const fr_ctx *c) {
     int64_t n = 0;
-    for (int t = 0; t < 2; ++t)
+    for (int t = 0; t < NT; ++t)
         if (c->T[t].present) n += c->T[t].ne * NV * c->T[t].nu;
     return n;
 }
@@ -386,12 +386,13 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
     if (!mesh || !prm) return set_err(FR_ERR_ARG, "null mesh or params");
     if (order < 1 || order > 4) return set_err(FR_ERR_ARG, "order must be in 1..4");
     if (mesh->n_nodes <= 0 || !mesh->xyz) return set_err(FR_ERR_ARG, "mesh has no nodes");
-    if (mesh->n_tet < 0 || mesh->n_pri < 0 || mesh->n_bface < 0)
+    if (mesh->n_tet < 0 || mesh->n_pri < 0 || mesh->n_hex < 0 || mesh->n_bface < 0)
         return set_err(FR_ERR_ARG, "negative element or face count");
-    if (mesh->n_tet + mesh->n_pri == 0) return set_err(FR_ERR_ARG, "mesh has no elements");
-    if ((mesh->n_tet && !mesh->tet) || (mesh->n_pri && !mesh->pri) || (mesh->n_bface && !mesh->bface))
+    if (mesh->n_tet + mesh->n_pri + mesh->n_hex == 0) return set_err(FR_ERR_ARG, "mesh has no elements");
+    if ((mesh->n_tet && !mesh->tet) || (mesh->n_pri && !mesh->pri) || (mesh->n_hex && !mesh->hex) ||
+        (mesh->n_bface && !mesh->bface))
         return set_err(FR_ERR_ARG, "null connectivity array");
-    if (mesh->n_tet > (1LL << 30) || mesh->n_pri > (1LL << 30))
+    if (mesh->n_tet > (1LL << 30) || mesh->n_pri > (1LL << 30) || mesh->n_hex > (1LL << 30))
         return set_err(FR_ERR_ARG, "element count too large");
     if (prm->precision < FR_FP64 || prm->precision > FR_TF32X3)
         return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64, FR_FP32, FR_BF16X3 or FR_TF32X3");
@@ -401,12 +402,14 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
     c->order = order;
 
     std::string err;
-    RefOps ops[2];
-    for (int t = 0; t < 2; ++t) {
+    RefOps ops[NT];
+    const int64_t ne_in[NT] = {mesh->n_tet, mesh->n_pri, mesh->n_hex};
+    for (int t = 0; t < NT; ++t) {
+        if (ne_in[t] == 0) continue;  // operators only for the types present
         int rc = build_ref_ops(t, order, ops[t], err);
         if (rc) return set_err(rc, err);
     }
-    TypeGeo geo[2];
+    TypeGeo geo[NT];
     int rc = build_geometry(mesh, ops, geo, err);
     if (rc) return set_err(rc, err);
     Faces faces;
@@ -417,8 +420,8 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         cudaGetLastError();
         return set_err(FR_ERR_CUDA, "no usable CUDA device");
     }
-    const int64_t ne[2] = {mesh->n_tet, mesh->n_pri};
-    for (int t = 0; t < 2; ++t) {
+    const int64_t ne[NT] = {mesh->n_tet, mesh->n_pri, mesh->n_hex};
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         D.present = ne[t] > 0;
         if (!D.present) continue;
@@ -551,9 +554,9 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
     if (prm->precision == FR_FP64) {
         const Phys ph = phys_of(c);
         const bool f32 = prm->precision != FR_FP64;
-        double *tFT[2] = {nullptr, nullptr}, *tFC[2] = {nullptr, nullptr};
+        double *tFT[NT] = {}, *tFC[NT] = {};
         std::vector<void *> tmp;
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < NT; ++t) {
             DevType &D = c->T[t];
             if (!D.present) continue;
             if ((rc = dev_alloc(c, &D.Rfs, (size_t)D.nu * NV * D.np))) return rc;
@@ -572,7 +575,7 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             }
         }
         Fields F{};
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < NT; ++t) {
             F.UF[t] = nullptr;
             F.DUF[t] = nullptr;
             F.GUF[t] = nullptr;
@@ -580,13 +583,13 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             F.np[t] = c->T[t].np;
         }
         rc = FR_OK;
-        for (int t = 0; t < 2 && !rc; ++t) {
+        for (int t = 0; t < NT && !rc; ++t) {
             DevType &D = c->T[t];
             if (!D.present) continue;
             rc = cuda_check(launch_const_flux(D.nu, D.ne, D.np, D.S, tFT[t], ph, 0), "reference flux");
         }
         if (!rc) rc = cuda_check(launch_const_common(pairs_of(c), bnd_of(c), F, ph, 0), "reference common flux");
-        for (int t = 0; t < 2 && !rc; ++t) {
+        for (int t = 0; t < NT && !rc; ++t) {
             DevType &D = c->T[t];
             if (!D.present) continue;
             GemmArgs g;
@@ -608,7 +611,7 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         }
         if (f32) {
             cudaDeviceSynchronize();
-            for (int t = 0; t < 2; ++t) {
+            for (int t = 0; t < NT; ++t) {
                 cudaFree(tFT[t]);
                 cudaFree(tFC[t]);
             }
@@ -616,7 +619,7 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         if (rc) return rc;
     }
     int nbt = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         c->red_blocks[t] = c->T[t].present ? 152 * 2 : 0;
         nbt += c->red_blocks[t];
     }
@@ -629,10 +632,10 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
 template <typename T>
 int rhs_public(fr_ctx *c, const double *u_dev, double *r_dev, cudaStream_t s) {
     size_t off = 0;
-    T *in[2] = {nullptr, nullptr};
+    T *in[NT] = {};
     int rc;
     const Phys ph = phys_of(c);
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch_pub_to_int<T>(D.nu, D.ne, D.np, u_dev + off, nullptr, s, (T *)D.Us, ph.uref),
@@ -643,7 +646,7 @@ int rhs_public(fr_ctx *c, const double *u_dev, double *r_dev, cudaStream_t s) {
     }
     if ((rc = rhs_internal<T>(c, in, nullptr, s))) return rc;
     off = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch_int_to_pub<T>(D.nu, D.ne, D.np, (const T *)D.R, r_dev + off, s), "rhs layout out")))
@@ -657,9 +660,9 @@ int rhs_public(fr_ctx *c, const double *u_dev, double *r_dev, cudaStream_t s) {
 template <typename T>
 int diagnostics_impl(fr_ctx *c, double *out, cudaStream_t s) {
     const Phys ph = phys_of(c);
-    T *in[2] = {nullptr, nullptr};
+    T *in[NT] = {};
     int rc;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch_center<T>(D.nu, D.np, D.U, (T *)D.Us, ph.uref, s), "centre"))) return rc;
@@ -668,7 +671,7 @@ int diagnostics_impl(fr_ctx *c, double *out, cudaStream_t s) {
     if ((rc = rhs_internal<T>(c, in, nullptr, s))) return rc;
     double *part = c->diag, *res = c->diag + (size_t)kDiagBlocks * 8;
     int nb = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch_ke_rate<T>(D.nu, D.ne, D.np, D.U, (const T *)D.R, D.wJ, part + nb, kDiagBlocks, s),
@@ -696,7 +699,7 @@ int step_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
     // the centred stage input is derived from the FP64 register (fr_rhs
     // reuses its buffer); the last stage of every step keeps it current
     const Phys ph = phys_of(c);
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         int rc = cuda_check(launch_center<T>(D.nu, D.np, D.U, (T *)D.Us, ph.uref, s), "centre");
@@ -704,8 +707,8 @@ int step_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
     }
     for (int it = 0; it < nsteps; ++it)
         for (int st = 0; st < 4; ++st) {
-            T *in[2] = {nullptr, nullptr};
-            for (int t = 0; t < 2; ++t)
+            T *in[NT] = {};
+            for (int t = 0; t < NT; ++t)
                 if (c->T[t].present) in[t] = (T *)c->T[t].Us;
             RKStage rk{ca[st], cs[st], st == 0, st == 3};
             int rc = rhs_internal<T>(c, in, &rk, s);
@@ -729,18 +732,18 @@ int step_2n_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
     if (nsteps <= 0) return FR_OK;
     const Phys ph = phys_of(c);
     int rc;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch_center<T>(D.nu, D.np, D.U, (T *)D.Us, ph.uref, s), "centre"))) return rc;
     }
     for (int it = 0; it < nsteps; ++it)
         for (int st = 0; st < 5; ++st) {
-            T *in[2] = {nullptr, nullptr};
-            for (int t = 0; t < 2; ++t)
+            T *in[NT] = {};
+            for (int t = 0; t < NT; ++t)
                 if (c->T[t].present) in[t] = (T *)c->T[t].Us;
             if ((rc = rhs_internal<T>(c, in, nullptr, s))) return rc;
-            for (int t = 0; t < 2; ++t) {
+            for (int t = 0; t < NT; ++t) {
                 DevType &D = c->T[t];
                 if (!D.present) continue;
                 if ((rc = cuda_check(launch(c, K_DIV, s,
@@ -761,8 +764,8 @@ template int step_2n_impl<double>(fr_ctx *, double, int, cudaStream_t);
 template int step_impl<float>(fr_ctx *, double, int, cudaStream_t);
 template int rhs_public<float>(fr_ctx *, const double *, double *, cudaStream_t);
 template int rhs_public<double>(fr_ctx *, const double *, double *, cudaStream_t);
-template int front_stages<float>(fr_ctx *, float *const[2], cudaStream_t);
-template int front_stages<double>(fr_ctx *, double *const[2], cudaStream_t);
+template int front_stages<float>(fr_ctx *, float *const[NT], cudaStream_t);
+template int front_stages<double>(fr_ctx *, double *const[NT], cudaStream_t);
 template int step_impl<double>(fr_ctx *, double, int, cudaStream_t);
 template FieldsT<float> fields_of<float>(const fr_ctx *);
 template FieldsT<double> fields_of<double>(const fr_ctx *);
@@ -876,13 +879,16 @@ int fr_info(const fr_ctx *c, int64_t *out) {
     out[5] = nfpts_of(0, c->order);
     out[6] = nfpts_of(1, c->order);
     out[7] = c->npairs;
+    out[8] = c->T[2].ne;
+    out[9] = nupts_of(2, c->order);
+    out[10] = nfpts_of(2, c->order);
     return FR_OK;
 }
 
 int fr_upts(const fr_ctx *c, double *xyz) {
     if (!c || !xyz) return set_err(FR_ERR_ARG, "null argument");
     size_t off = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         const DevType &D = c->T[t];
         if (!D.present) continue;
         for (int64_t e = 0; e < D.ne; ++e)
@@ -896,7 +902,7 @@ int fr_set_state(fr_ctx *c, const double *u, void *stream) {
     if (!c || !u) return set_err(FR_ERR_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     size_t off = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         const size_t n = (size_t)D.ne * NV * D.nu;
@@ -918,7 +924,7 @@ int fr_get_state(fr_ctx *c, double *u, void *stream) {
     if (!c || !u) return set_err(FR_ERR_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     size_t off = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         const size_t n = (size_t)D.ne * NV * D.nu;
@@ -957,7 +963,7 @@ int fr_reduce(fr_ctx *c, double *out, void *stream) {
     if (!c || !out) return set_err(FR_ERR_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     int off = 0, rc;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch_reduce_partial(D.nu, D.ne, D.np, D.U, D.wJ, c->prm.gamma, c->red + (size_t)off * 7,

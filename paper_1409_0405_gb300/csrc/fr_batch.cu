@@ -210,7 +210,7 @@ struct BatchImpl : BatchBase {
             g.rc = 16;
         }
         for (fr_ctx *c : b->ctx) {
-            for (int t = 0; t < 2; ++t) {
+            for (int t = 0; t < NT; ++t) {
                 DevType &D = c->T[t];
                 if (!D.present) continue;
                 const T *in = (const T *)D.Us;
@@ -268,7 +268,7 @@ struct BatchImpl : BatchBase {
                 const double ca[4] = {h / 6.0, h / 3.0, h / 3.0, h / 6.0};
                 const double cs[4] = {0.5 * h, 0.5 * h, h, 0.0};
                 RKStage rk{ca[st], cs[st], st == 0, st == 3};
-                for (int t = 0; t < 2; ++t)
+                for (int t = 0; t < NT; ++t)
                     if (b->ctx[i]->T[t].present) {
                         div[st].h.push_back(args_div<T>(b->ctx[i], t, &rk));
                         div[st].op.push_back(t * 64 + b->ctx[i]->order * 4 + 2);
@@ -431,7 +431,7 @@ struct BatchImpl : BatchBase {
         Group<T> dv;
         dv.mode = GEMM_DIV;
         for (fr_ctx *c : b->ctx)
-            for (int t = 0; t < 2; ++t)
+            for (int t = 0; t < NT; ++t)
                 if (c->T[t].present) {
                     dv.h.push_back(args_div<T>(c, t, nullptr));
                     dv.op.push_back(t * 64 + c->order * 4 + 2);
@@ -510,7 +510,7 @@ struct BatchImpl : BatchBase {
     void info(int64_t *out) const override {
         int64_t ndof = 0;
         for (fr_ctx *c : b->ctx)
-            for (int t = 0; t < 2; ++t)
+            for (int t = 0; t < NT; ++t)
                 if (c->T[t].present) ndof += c->T[t].ne * NVV * c->T[t].nu;
         out[0] = (int64_t)b->ctx.size();
         out[1] = ndof;
@@ -518,7 +518,8 @@ struct BatchImpl : BatchBase {
         // per-problem launch sequence: (viscous ? 12 : 6) per stage and 2 types
         int64_t un = 0;
         for (fr_ctx *c : b->ctx) {
-            int nt = c->T[0].present + c->T[1].present;
+            int nt = 0;
+            for (int t = 0; t < NT; ++t) nt += c->T[t].present;
             un += 4 * ((viscous ? 5 : 3) * nt + (viscous ? 2 : 1));
         }
         out[3] = un;
@@ -598,8 +599,9 @@ int fr_batch_step(fr_batch *b, const double *dt, int nsteps, int batched, void *
     if (!b || !dt || nsteps < 0) return set_err(FR_ERR_ARG, "invalid step arguments");
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         if (!(dt[i] == dt[i])) return set_err(FR_ERR_ARG, "non-finite time step");
-        if (b->ctx[i]->T[0].cl_on || b->ctx[i]->T[1].cl_on)
-            return set_err(FR_ERR_UNSUPPORTED, "batched steps do not apply a learned closure");
+        for (int t = 0; t < NT; ++t)
+            if (b->ctx[i]->T[t].cl_on)
+                return set_err(FR_ERR_UNSUPPORTED, "batched steps do not apply a learned closure");
     }
     return b->impl->step(dt, nsteps, batched, (cudaStream_t)stream);
 }

@@ -154,7 +154,7 @@ namespace {
 // transfer matrices from order p_from into `to` (cached for one p_from)
 int ensure_transfer(fr_ctx *to, int p_from) {
     if (to->tr_from == p_from) return FR_OK;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         if (!to->T[t].present) continue;
         std::vector<double> R;
         std::string err;
@@ -176,7 +176,7 @@ int ensure_transfer(fr_ctx *to, int p_from) {
 
 int check_pair(const fr_ctx *a, const fr_ctx *b) {
     if (!a || !b) return set_err(FR_ERR_ARG, "null context");
-    for (int t = 0; t < 2; ++t)
+    for (int t = 0; t < NT; ++t)
         if (a->T[t].ne != b->T[t].ne) return set_err(FR_ERR_ARG, "contexts have different element counts");
     return FR_OK;
 }
@@ -187,7 +187,7 @@ int transfer_state(const fr_ctx *from, fr_ctx *to, const double *u, double *out,
     if (!u || !out) return set_err(FR_ERR_ARG, "null state pointer");
     if ((rc = ensure_transfer(to, from->order))) return rc;
     size_t off_f = 0, off_t = 0;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         const DevType &D = to->T[t];
         if (!D.present) continue;
         const int nf = from->T[t].nu, nt = D.nu;
@@ -204,9 +204,9 @@ template <typename T>
 int features_impl(fr_ctx *c, const double *u, int etype, float *X, cudaStream_t s) {
     const Phys ph = phys_of(c);
     size_t off = 0;
-    T *in[2] = {nullptr, nullptr};
+    T *in[NT] = {};
     int rc;
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch_pub_to_int<T>(D.nu, D.ne, D.np, u + off, nullptr, s, (T *)D.Us, ph.uref),
@@ -221,7 +221,7 @@ int features_impl(fr_ctx *c, const double *u, int etype, float *X, cudaStream_t 
 
 int check_closure_ctx(const fr_ctx *c, int etype) {
     if (!c) return set_err(FR_ERR_ARG, "null context");
-    if (etype != FR_ETYPE_TET && etype != FR_ETYPE_PRI) return set_err(FR_ERR_ARG, "etype must be 0 or 1");
+    if (etype < FR_ETYPE_TET || etype > FR_ETYPE_HEX) return set_err(FR_ERR_ARG, "etype must be 0, 1 or 2");
     if (!c->prm.viscous) return set_err(FR_ERR_UNSUPPORTED, "the closure needs a Navier-Stokes context");
     if (!c->T[etype].present) return set_err(FR_ERR_ARG, "no elements of this type");
     return FR_OK;
@@ -238,8 +238,8 @@ extern "C" {
 
 int fr_transfer(int etype, int p_from, int p_to, double *out, int64_t *rows, int64_t *cols) {
     if (!rows || !cols) return set_err(FR_ERR_ARG, "null argument");
-    if ((etype != FR_ETYPE_TET && etype != FR_ETYPE_PRI) || p_from < 1 || p_from > 4 || p_to < 1 || p_to > 4)
-        return set_err(FR_ERR_ARG, "etype must be 0/1 and orders 1..4");
+    if (etype < FR_ETYPE_TET || etype > FR_ETYPE_HEX || p_from < 1 || p_from > 4 || p_to < 1 || p_to > 4)
+        return set_err(FR_ERR_ARG, "etype must be 0/1/2 and orders 1..4");
     *rows = nupts_of(etype, p_to);
     *cols = nupts_of(etype, p_from);
     if (!out) return FR_OK;
@@ -296,12 +296,14 @@ int fr_closure_sample(fr_ctx *hi, fr_ctx *lo, const double *u_hi_dev, const doub
         if ((rc = transfer_state(hi, lo, u_hi_dev, lo->smp_u, s))) return rc;
         ulo = lo->smp_u;
     }
-    const int on[2] = {lo->T[0].cl_on, lo->T[1].cl_on};
-    lo->T[0].cl_on = lo->T[1].cl_on = 0;
+    int on[NT];
+    for (int t = 0; t < NT; ++t) {
+        on[t] = lo->T[t].cl_on;
+        lo->T[t].cl_on = 0;
+    }
     rc = is_f32(lo) ? rhs_public<float>(lo, ulo, lo->smp_r, s)
                                       : rhs_public<double>(lo, ulo, lo->smp_r, s);
-    lo->T[0].cl_on = on[0];
-    lo->T[1].cl_on = on[1];
+    for (int t = 0; t < NT; ++t) lo->T[t].cl_on = on[t];
     if (rc) return rc;
     // the features of the state RHS_lo just ran on (its stage input and
     // gradient are still in the context's buffers)
@@ -312,7 +314,9 @@ int fr_closure_sample(fr_ctx *hi, fr_ctx *lo, const double *u_hi_dev, const doub
         if (rc) return rc;
     }
     if (t_dev || ss_dev) {
-        const size_t off = etype == FR_ETYPE_PRI && lo->T[0].present ? (size_t)lo->T[0].ne * 5 * lo->T[0].nu : 0;
+        size_t off = 0;  // start of this type's block in the public layout
+        for (int t = 0; t < etype; ++t)
+            if (lo->T[t].present) off += (size_t)lo->T[t].ne * 5 * lo->T[t].nu;
         const int64_t n = D.ne * 5 * D.nu;
         Scale5 isc;
         for (int v = 0; v < 5; ++v) isc.s[v] = inv_scale ? inv_scale[v] : 1.0;

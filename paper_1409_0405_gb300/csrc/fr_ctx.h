@@ -56,7 +56,7 @@ struct fr_ctx {
     fr_params prm{};
     int order = 0;
     int device = 0;
-    DevType T[2];
+    DevType T[fr::NT];  // tets, prisms, hexes
     int64_t npairs = 0, nbnd = 0;
     int *ta = nullptr, *fa = nullptr, *ea = nullptr, *tb = nullptr, *fb = nullptr, *eb = nullptr;
     double *nrm = nullptr, *maga = nullptr, *magb = nullptr;
@@ -66,7 +66,7 @@ struct fr_ctx {
     double *bw = nullptr;    // face weight of each boundary flux point
     double *diag = nullptr;  // diagnostics partials + result
     int *tc_err = nullptr;  // set by a tensor-core kernel whose bounded wait gave up
-    int red_blocks[2] = {0, 0};
+    int red_blocks[fr::NT] = {};
     std::vector<void *> allocs;
     // launch accounting: count of kernel launches, and (when profiling is
     // on) a CUDA event pair around every launch, tagged by kernel class
@@ -78,7 +78,7 @@ struct fr_ctx {
     // order-transfer matrices (nu_self x nu_from, FP64, device) for one
     // source order, and the scratch of the closure sample generator
     int tr_from = 0;
-    double *tr[2] = {nullptr, nullptr};
+    double *tr[fr::NT] = {};
     double *smp_u = nullptr, *smp_r = nullptr, *smp_rr = nullptr, *smp_rhi = nullptr;
     int64_t smp_rhi_cap = 0;
 };
@@ -152,7 +152,7 @@ int rhs_public(fr_ctx *c, const double *u_dev, double *r_dev, cudaStream_t s);
 // stages 1-4 of the RHS (interpolation and, for Navier-Stokes, the
 // corrected gradient at solution and flux points) on the stage input
 template <typename T>
-int front_stages(fr_ctx *c, T *const in[2], cudaStream_t s);
+int front_stages(fr_ctx *c, T *const in[NT], cudaStream_t s);
 // learned closure of type t: features of the stage input, the network,
 // and cl_add = Rfs + scale * output in the internal layout
 template <typename T>

@@ -8,6 +8,13 @@
 
 #include "../../include/fr.h"
 
+#ifndef FR_NT_DEFINED
+#define FR_NT_DEFINED
+namespace fr {
+constexpr int NT = FR_NTYPES;  // element types: tet, prism, hex
+}
+#endif
+
 namespace fr {
 
 constexpr int NV = FR_NVARS;
@@ -58,9 +65,9 @@ struct Faces {
     std::vector<double> bn, bmag;
 };
 
-int build_geometry(const fr_mesh *mesh, const RefOps ops[2], TypeGeo geo[2],
+int build_geometry(const fr_mesh *mesh, const RefOps ops[NT], TypeGeo geo[NT],
                    std::string &err);
-int build_faces(const fr_mesh *mesh, const RefOps ops[2], const TypeGeo geo[2],
+int build_faces(const fr_mesh *mesh, const RefOps ops[NT], const TypeGeo geo[NT],
                 Faces &faces, std::string &err);
 
 // L2 projection between the spaces of orders p_from and p_to on one

@@ -11,6 +11,15 @@
 
 #include <vector>
 
+#include "../../include/fr.h"
+
+#ifndef FR_NT_DEFINED
+#define FR_NT_DEFINED
+namespace fr {
+constexpr int NT = FR_NTYPES;  // element types: tet, prism, hex
+}
+#endif
+
 namespace fr {
 
 // Epilogues of the operator application C <- A [B1; B2] (Sec. 2.1, Eq. 1).
@@ -141,11 +150,11 @@ struct Phys {
 // Per-type field pointers (index 0 tet, 1 prism); nullptr for an absent type.
 template <typename T>
 struct FieldsT {
-    const T *UF[2];   // [nf][V][np]
-    T *DUF[2];        // [nf][V][np]
-    const T *GUF[2];  // [nf][3][V][np]
-    T *FC[2];         // [nf][V][np]
-    int64_t np[2];
+    const T *UF[NT];   // [nf][V][np]
+    T *DUF[NT];        // [nf][V][np]
+    const T *GUF[NT];  // [nf][3][V][np]
+    T *FC[NT];         // [nf][V][np]
+    int64_t np[NT];
 };
 using Fields = FieldsT<double>;
 

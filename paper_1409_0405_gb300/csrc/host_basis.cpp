@@ -1,7 +1,8 @@
 // Host construction of the FR points and operator matrices.
 //
 // Basis: the orthogonal collapsed-coordinate (Dubiner) polynomials of the
-// element space (tet: P_p; prism: P_p(triangle) x P_p(zeta)), whose
+// element space (tet: P_p; prism: P_p(triangle) x P_p(zeta); hex: Q_p, the
+// Legendre tensor products P_i(xi) P_j(eta) P_k(zeta), i, j, k <= p), whose
 // dimensions are Table 2's solution-point counts:
 //   tet  psi_ijk = P_i(a) ((1-b)/2)^i P_j^(2i+1,0)(b) ((1-c)/2)^(i+j)
 //                  P_k^(2i+2j+2,0)(c),
@@ -49,6 +50,10 @@ const int PRI_V[6][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1
 const std::vector<std::vector<int>> TET_FACES = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
 const std::vector<std::vector<int>> PRI_FACES = {
     {0, 1, 2}, {3, 4, 5}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
+const int HEX_V[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                         {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+const std::vector<std::vector<int>> HEX_FACES = {{0, 1, 2, 3}, {0, 1, 5, 4}, {1, 2, 6, 5},
+                                                 {2, 3, 7, 6}, {3, 0, 4, 7}, {4, 5, 6, 7}};
 
 // ---------------------------------------------------------------------------
 // Gauss-Legendre nodes/weights in double-double (Newton on P_n)
@@ -231,7 +236,9 @@ struct Basis {
         for (int c = 0; c <= p; ++c)
             for (int b = 0; b <= p; ++b)
                 for (int a = 0; a <= p; ++a) {
-                    bool in = (etype == FR_ETYPE_TET) ? (a + b + c <= p) : (a + b <= p);
+                    bool in = (etype == FR_ETYPE_TET) ? (a + b + c <= p)
+                              : (etype == FR_ETYPE_HEX) ? true
+                                                        : (a + b <= p);
                     if (in) ex.push_back({a, b, c});
                 }
         scl.assign(ex.size(), R(1.0));
@@ -250,6 +257,7 @@ struct Basis {
             return jacobi(i, 0, a) * dpow(half * (one - b), i) * jacobi(j, 2 * i + 1, b) *
                    dpow(half * (one - c), i + j) * jacobi(k, 2 * i + 2 * j + 2, c);
         }
+        if (etype == FR_ETYPE_HEX) return jacobi(i, 0, xi) * jacobi(j, 0, eta) * jacobi(k, 0, zeta);
         Dual a = (two * (one + xi)) / (one - eta) - one;
         Dual b = eta;
         return jacobi(i, 0, a) * dpow(half * (one - b), i) * jacobi(j, 2 * i + 1, b) * jacobi(k, 0, zeta);
@@ -316,6 +324,13 @@ void rule_volume(int etype, int n, std::vector<Vec3> &pts, std::vector<R> &wts) 
                     pts.push_back({R(2.0) * px - R(1.0), R(2.0) * py - R(1.0), R(2.0) * pz - R(1.0)});
                     wts.push_back(w[a] * w[b] * w[c] * (R(1.0) - u) * (R(1.0) - u) * (R(1.0) - v));
                 }
+    } else if (etype == FR_ETYPE_HEX) {
+        for (int c = 0; c < n; ++c)
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a) {
+                    pts.push_back({x[a], x[b], x[c]});
+                    wts.push_back(w[a] * w[b] * w[c]);
+                }
     } else {
         std::vector<std::array<R, 2>> tp;
         std::vector<R> tw;
@@ -349,12 +364,15 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
 }
 
 int nupts_of(int etype, int p) {
-    return etype == FR_ETYPE_TET ? (p + 1) * (p + 2) * (p + 3) / 6 : (p + 1) * (p + 1) * (p + 2) / 2;
+    if (etype == FR_ETYPE_TET) return (p + 1) * (p + 2) * (p + 3) / 6;
+    if (etype == FR_ETYPE_HEX) return (p + 1) * (p + 1) * (p + 1);
+    return (p + 1) * (p + 1) * (p + 2) / 2;
 }
 
 int nfpts_of(int etype, int p) {
-    return etype == FR_ETYPE_TET ? 4 * (p + 1) * (p + 2) / 2
-                                 : 2 * (p + 1) * (p + 2) / 2 + 3 * (p + 1) * (p + 1);
+    if (etype == FR_ETYPE_TET) return 4 * (p + 1) * (p + 2) / 2;
+    if (etype == FR_ETYPE_HEX) return 6 * (p + 1) * (p + 1);
+    return 2 * (p + 1) * (p + 2) / 2 + 3 * (p + 1) * (p + 1);
 }
 
 namespace {
@@ -363,8 +381,8 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err);
 
 // Operators depend only on (etype, p): built once per process and reused.
 int build_ref_ops(int etype, int p, RefOps &o, std::string &err) {
-    if ((etype != FR_ETYPE_TET && etype != FR_ETYPE_PRI) || p < 1 || p > 4) {
-        err = "build_ref_ops: etype must be 0/1 and order 1..4";
+    if (etype < FR_ETYPE_TET || etype > FR_ETYPE_HEX || p < 1 || p > 4) {
+        err = "build_ref_ops: etype must be 0/1/2 and order 1..4";
         return FR_ERR_ARG;
     }
     static std::mutex mtx;
@@ -390,12 +408,12 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
     o = RefOps();
     o.etype = etype;
     o.p = p;
-    const bool tet = etype == FR_ETYPE_TET;
-    const int nverts = tet ? 4 : 6;
+    const bool tet = etype == FR_ETYPE_TET, hex = etype == FR_ETYPE_HEX;
+    const int nverts = tet ? 4 : hex ? 8 : 6;
     std::vector<Vec3> V(nverts);
     for (int i = 0; i < nverts; ++i)
-        for (int k = 0; k < 3; ++k) V[i][k] = R((double)(tet ? TET_V[i][k] : PRI_V[i][k]));
-    o.face_verts = tet ? TET_FACES : PRI_FACES;
+        for (int k = 0; k < 3; ++k) V[i][k] = R((double)(tet ? TET_V[i][k] : hex ? HEX_V[i][k] : PRI_V[i][k]));
+    o.face_verts = tet ? TET_FACES : hex ? HEX_FACES : PRI_FACES;
     o.nfaces = (int)o.face_verts.size();
 
     // ---- solution points
@@ -413,6 +431,10 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
                         for (int c = 0; c < 3; ++c) x[c] += lam[a] * V[a][c];
                     up.push_back(x);
                 }
+    } else if (hex) {
+        for (int c = 0; c <= p; ++c)
+            for (int b = 0; b <= p; ++b)
+                for (int a = 0; a <= p; ++a) up.push_back({glx[a], glx[b], glx[c]});
     } else {
         auto tri = tri_set(p);
         for (int c = 0; c <= p; ++c)
@@ -689,7 +711,7 @@ int build_ref_ops_uncached(int etype, int p, RefOps &o, std::string &err) {
 // p_to) as the L2 projection onto the target space in the reference element.
 // The Dubiner polynomials of order max(p_from, p_to) are mutually orthogonal
 // and each space is spanned by a subset of them (tet: i+j+k <= p; prism:
-// i+j <= p and k <= p), so the projection keeps the modal coefficients the
+// i+j <= p and k <= p; hex: i, j, k <= p), so the projection keeps the modal coefficients the
 // target space shares with the source and drops the rest:
 //   R = V_to[:, shared] (V_from^-1)[shared, :],
 // V the Vandermondes of each space's modes at its own solution points.
@@ -701,6 +723,7 @@ int build_transfer(int etype, int p_from, int p_to, std::vector<double> &out, st
     const int pm = std::max(p_from, p_to);
     Basis B(etype, pm);
     auto in_space = [etype](const std::array<int, 3> &e, int p) {
+        if (etype == FR_ETYPE_HEX) return e[0] <= p && e[1] <= p && e[2] <= p;
         return etype == FR_ETYPE_TET ? (e[0] + e[1] + e[2] <= p) : (e[0] + e[1] <= p && e[2] <= p);
     };
     std::vector<int> mf, mt;  // modes of each space (indices into B)

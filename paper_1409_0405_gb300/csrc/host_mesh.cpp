@@ -2,8 +2,8 @@
 // connectivity, periodic face matching and flux-point pairing.
 //
 // Element maps: tets are affine in the barycentric coordinates; prisms use
-// the linear-triangle x linear-zeta map, which is not affine once nodes are
-// jittered.  With A = dx/dxi (columns a_d), S = J dxi/dx = adj(A) has rows
+// the linear-triangle x linear-zeta map and hexes the trilinear map, neither
+// affine once nodes are jittered.  With A = dx/dxi (columns a_d), S = J dxi/dx = adj(A) has rows
 // a_1 x a_2, a_2 x a_0, a_0 x a_1; a physical flux F becomes F~_d =
 // sum_m S[d][m] F_m, and at a face the scaled physical normal is S^T n^.
 #include <algorithm>
@@ -35,6 +35,19 @@ void shape(int etype, const double *x, double *N, double (*dN)[3]) {
             for (int k = 0; k < 3; ++k) dN[a][k] = d[a][k];
         return;
     }
+    if (etype == FR_ETYPE_HEX) {
+        // N_a = (1 + s0 xi)(1 + s1 eta)(1 + s2 zeta) / 8, s the vertex signs
+        const int sg[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                              {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+        for (int a = 0; a < 8; ++a) {
+            const double f0 = 1 + sg[a][0] * xi, f1 = 1 + sg[a][1] * eta, f2 = 1 + sg[a][2] * zeta;
+            N[a] = 0.125 * f0 * f1 * f2;
+            dN[a][0] = 0.125 * sg[a][0] * f1 * f2;
+            dN[a][1] = 0.125 * f0 * sg[a][1] * f2;
+            dN[a][2] = 0.125 * f0 * f1 * sg[a][2];
+        }
+        return;
+    }
     const double tau[3] = {-0.5 * (xi + eta), 0.5 * (1 + xi), 0.5 * (1 + eta)};
     const double dtau[3][2] = {{-0.5, -0.5}, {0.5, 0.0}, {0.0, 0.5}};
     const double lo = 0.5 * (1 - zeta), hi = 0.5 * (1 + zeta);
@@ -57,8 +70,8 @@ struct PointGeo {
 };
 
 PointGeo point_geo(int etype, const double (*X)[3], const double *ref) {
-    const int nv = etype == FR_ETYPE_TET ? 4 : 6;
-    double N[6], dN[6][3];
+    const int nv = etype == FR_ETYPE_TET ? 4 : etype == FR_ETYPE_HEX ? 8 : 6;
+    double N[8], dN[8][3];
     shape(etype, ref, N, dN);
     PointGeo g{};
     double A[3][3] = {{0}};  // A[k][d] = dx_k / dxi_d
@@ -106,11 +119,11 @@ struct CellHash {
 
 }  // namespace
 
-int build_geometry(const fr_mesh *m, const RefOps ops[2], TypeGeo geo[2], std::string &err) {
-    const int64_t *conn[2] = {m->tet, m->pri};
-    const int64_t ne[2] = {m->n_tet, m->n_pri};
-    const int nvs[2] = {4, 6};
-    for (int t = 0; t < 2; ++t) {
+int build_geometry(const fr_mesh *m, const RefOps ops[NT], TypeGeo geo[NT], std::string &err) {
+    const int64_t *conn[NT] = {m->tet, m->pri, m->hex};
+    const int64_t ne[NT] = {m->n_tet, m->n_pri, m->n_hex};
+    const int nvs[NT] = {4, 6, 8};
+    for (int t = 0; t < NT; ++t) {
         TypeGeo &G = geo[t];
         G = TypeGeo();
         G.ne = ne[t];
@@ -125,7 +138,7 @@ int build_geometry(const fr_mesh *m, const RefOps ops[2], TypeGeo geo[2], std::s
         G.fn.resize((size_t)ne[t] * o.nf * 3);
         G.fmag.resize((size_t)ne[t] * o.nf);
         for (int64_t e = 0; e < ne[t]; ++e) {
-            double X[6][3];
+            double X[8][3];
             for (int a = 0; a < nvs[t]; ++a) {
                 int64_t v = conn[t][e * nvs[t] + a];
                 if (v < 0 || v >= m->n_nodes) {
@@ -168,12 +181,12 @@ int build_geometry(const fr_mesh *m, const RefOps ops[2], TypeGeo geo[2], std::s
     return FR_OK;
 }
 
-int build_faces(const fr_mesh *m, const RefOps ops[2], const TypeGeo geo[2], Faces &F,
+int build_faces(const fr_mesh *m, const RefOps ops[NT], const TypeGeo geo[NT], Faces &F,
                 std::string &err) {
     F = Faces();
-    const int64_t *conn[2] = {m->tet, m->pri};
-    const int64_t ne[2] = {m->n_tet, m->n_pri};
-    const int nvs[2] = {4, 6};
+    const int64_t *conn[NT] = {m->tet, m->pri, m->hex};
+    const int64_t ne[NT] = {m->n_tet, m->n_pri, m->n_hex};
+    const int nvs[NT] = {4, 6, 8};
 
     // bounding box -> matching tolerance
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -190,9 +203,9 @@ int build_faces(const fr_mesh *m, const RefOps ops[2], const TypeGeo geo[2], Fac
     // ---- interior faces by shared vertex sets
     std::unordered_map<std::array<int64_t, 4>, std::vector<FaceRec>, KeyHash> map;
     size_t nfaces_total = 0;
-    for (int t = 0; t < 2; ++t) nfaces_total += (size_t)ne[t] * ops[t].nfaces * (ne[t] > 0);
+    for (int t = 0; t < NT; ++t) nfaces_total += (size_t)ne[t] * ops[t].nfaces * (ne[t] > 0);
     map.reserve(nfaces_total);
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         if (ne[t] == 0) continue;
         for (int64_t e = 0; e < ne[t]; ++e)
             for (int lf = 0; lf < ops[t].nfaces; ++lf) {
@@ -248,7 +261,7 @@ int build_faces(const fr_mesh *m, const RefOps ops[2], const TypeGeo geo[2], Fac
     for (int64_t i = 0; i < m->n_bface; ++i) {
         const int64_t *b = &m->bface[4 * i];
         int t = (int)b[0];
-        if (t < 0 || t > 1 || b[1] < 0 || b[1] >= ne[t] || b[2] < 0 || b[2] >= ops[t].nfaces ||
+        if (t < 0 || t >= NT || ne[t] == 0 || b[1] < 0 || b[1] >= ne[t] || b[2] < 0 || b[2] >= ops[t].nfaces ||
             (b[3] != FR_BC_WALL && b[3] != FR_BC_FARFIELD)) {
             err = "invalid boundary face record";
             return FR_ERR_MESH;
@@ -437,7 +450,7 @@ int build_faces(const fr_mesh *m, const RefOps ops[2], const TypeGeo geo[2], Fac
     }
 
     // every flux point covered exactly once
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         if (ne[t] == 0) continue;
         std::vector<unsigned char> cov((size_t)ne[t] * ops[t].nf, 0);
         for (size_t k = 0; k < np; ++k) {

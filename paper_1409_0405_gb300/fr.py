@@ -48,6 +48,7 @@ class FRMesh(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("xyz", C.POINTER(C.c_double)),
                 ("n_tet", C.c_int64), ("tet", C.POINTER(C.c_int64)),
                 ("n_pri", C.c_int64), ("pri", C.POINTER(C.c_int64)),
+                ("n_hex", C.c_int64), ("hex", C.POINTER(C.c_int64)),
                 ("n_bface", C.c_int64), ("bface", C.POINTER(C.c_int64)),
                 ("period", C.c_double * 3)]
 
@@ -136,8 +137,11 @@ def load():
     return lib
 
 
+ETYPES = ("tet", "pri", "hex")
+
+
 def _etype(e):
-    return {"tet": 0, "pri": 1}.get(e, e)
+    return {"tet": 0, "pri": 1, "hex": 2}.get(e, e)
 
 
 def _check(rc):
@@ -155,7 +159,7 @@ def operator(etype, order, which):
     lib = load()
     rows, cols = C.c_int64(), C.c_int64()
     wid = OP_IDS[which] if isinstance(which, str) else int(which)
-    et = {"tet": 0, "pri": 1}.get(etype, etype)
+    et = _etype(etype)
     _check(lib.fr_operator(et, order, wid, None, C.byref(rows), C.byref(cols)))
     out = np.empty((rows.value, cols.value), dtype=np.float64)
     _check(lib.fr_operator(et, order, wid, _dptr(out), C.byref(rows), C.byref(cols)))
@@ -166,7 +170,7 @@ def transfer(etype, p_from, p_to):
     """Host-only order-transfer matrix (nu(p_to) x nu(p_from)), float64."""
     lib = load()
     rows, cols = C.c_int64(), C.c_int64()
-    et = {"tet": 0, "pri": 1}.get(etype, etype)
+    et = _etype(etype)
     _check(lib.fr_transfer(et, int(p_from), int(p_to), None, C.byref(rows), C.byref(cols)))
     out = np.empty((rows.value, cols.value), dtype=np.float64)
     _check(lib.fr_transfer(et, int(p_from), int(p_to), _dptr(out), C.byref(rows), C.byref(cols)))
@@ -233,6 +237,7 @@ def _fr_mesh(mesh, keep):
         "xyz": np.ascontiguousarray(mesh["xyz"], dtype=np.float64),
         "tet": np.ascontiguousarray(mesh["tet"], dtype=np.int64).reshape(-1, 4),
         "pri": np.ascontiguousarray(mesh["pri"], dtype=np.int64).reshape(-1, 6),
+        "hex": np.ascontiguousarray(mesh.get("hex", np.zeros((0, 8))), dtype=np.int64).reshape(-1, 8),
         "bface": np.ascontiguousarray(mesh.get("bface", np.zeros((0, 4))), dtype=np.int64).reshape(-1, 4),
     }
     keep.append(k)
@@ -243,6 +248,8 @@ def _fr_mesh(mesh, keep):
     m.tet = k["tet"].ctypes.data_as(C.POINTER(C.c_int64))
     m.n_pri = len(k["pri"])
     m.pri = k["pri"].ctypes.data_as(C.POINTER(C.c_int64))
+    m.n_hex = len(k["hex"])
+    m.hex = k["hex"].ctypes.data_as(C.POINTER(C.c_int64))
     m.n_bface = len(k["bface"])
     m.bface = k["bface"].ctypes.data_as(C.POINTER(C.c_int64))
     per = np.asarray(mesh.get("period", np.zeros(3)), dtype=np.float64)
@@ -281,10 +288,10 @@ class Context:
         n = C.c_int64()
         _check(lib.fr_ndof(h, C.byref(n)))
         self.ndof = n.value
-        info = (C.c_int64 * 8)()
+        info = (C.c_int64 * 11)()
         _check(lib.fr_info(h, info))
         self.info = dict(zip(("n_tet", "n_pri", "order", "nu_tet", "nu_pri", "nf_tet",
-                              "nf_pri", "npairs"), list(info)))
+                              "nf_pri", "npairs", "n_hex", "nu_hex", "nf_hex"), list(info)))
         self.order = int(info[2])
 
     def close(self):
@@ -310,7 +317,7 @@ class Context:
         """(n_points, 3) coordinates in public point order."""
         x = self.upts()
         blocks, off = [], 0
-        for ne, nu in ((self.info["n_tet"], self.info["nu_tet"]), (self.info["n_pri"], self.info["nu_pri"])):
+        for ne, nu in self.counts():
             if ne == 0:
                 continue
             blk = x[off:off + ne * 3 * nu].reshape(ne, 3, nu).transpose(0, 2, 1).reshape(-1, 3)
@@ -354,12 +361,16 @@ class Context:
                                          C.byref(tot)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KCLASSES)}, tot.value
 
+    def counts(self):
+        """[(elements, solution points per element)] per type, public order."""
+        return [(self.info["n_" + t], self.info["nu_" + t]) for t in ETYPES]
+
     # -- learned closure (device pointers are ints) --------------------------------
     def nu(self, etype):
-        return self.info["nu_tet" if etype in (0, "tet") else "nu_pri"]
+        return self.info["nu_" + ETYPES[_etype(etype)]]
 
     def ne(self, etype):
-        return self.info["n_tet" if etype in (0, "tet") else "n_pri"]
+        return self.info["n_" + ETYPES[_etype(etype)]]
 
     def transfer_from(self, other, u_ptr, out_ptr, stream=None):
         """out (this context's order) = transfer of u (other's order)."""

@@ -76,11 +76,11 @@ def gpu_rhs(ctx, u):
     return rt.cpu().numpy()
 
 
-def to_longdouble(sol):
+def to_longdouble(sol, ld=np.longdouble):
     """Switch an oracle instance to numpy extended precision (used only to
-    measure the FP64 rounding floor of a case)."""
+    measure the FP64 rounding floor of a case); with ld=np.float32, to
+    single precision (the FP32 rounding floor of a plain evaluation)."""
     import copy
-    ld = np.longdouble
     for t in sol.types:
         # copy: the oracle caches its operator objects across solvers
         op = sol.m.ops[t] = copy.copy(sol.m.ops[t])

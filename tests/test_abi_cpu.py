@@ -37,7 +37,7 @@ def test_strerror():
     assert b"mesh" in lib.fr_strerror(-2)
 
 
-@pytest.mark.parametrize("etype", ["tet", "pri"])
+@pytest.mark.parametrize("etype", ["tet", "pri", "hex"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_host_operators_match_oracle(etype, p):
     library()
@@ -69,7 +69,7 @@ def test_operator_bad_arguments():
     lib = library()
     import ctypes as C
     r, c = C.c_int64(), C.c_int64()
-    assert lib.fr_operator(2, 2, 0, None, C.byref(r), C.byref(c)) == -1
+    assert lib.fr_operator(3, 2, 0, None, C.byref(r), C.byref(c)) == -1
     assert lib.fr_operator(0, 5, 0, None, C.byref(r), C.byref(c)) == -1
     assert lib.fr_operator(0, 2, 99, None, C.byref(r), C.byref(c)) == -1
 
@@ -132,6 +132,7 @@ def test_entry_points_reject_bad_arguments_without_a_gpu():
     rows, cols = C.c_int64(), C.c_int64()
     assert lib.fr_transfer(0, 2, 5, None, C.byref(rows), C.byref(cols)) == fr.FR_ERR_ARG
     assert lib.fr_transfer(3, 2, 4, None, C.byref(rows), C.byref(cols)) == fr.FR_ERR_ARG
+    assert lib.fr_transfer(-1, 2, 4, None, C.byref(rows), C.byref(cols)) == fr.FR_ERR_ARG
     assert lib.fr_mlp_forward(4, 0, 4, 10, None, None, None, None, None) == fr.FR_ERR_ARG
     assert lib.fr_mlp_grad(4, 8, 4, 0, None, None, None, None, None, None, None) == fr.FR_ERR_ARG
     assert lib.fr_mlp_adam(10, None, None, None, None, 1, 1e-3, None) == fr.FR_ERR_ARG

@@ -9,7 +9,7 @@ from oracle import closure
 from paper_1409_0405_gb300 import fr
 
 
-@pytest.mark.parametrize("etype", ["tet", "pri"])
+@pytest.mark.parametrize("etype", ["tet", "pri", "hex"])
 @pytest.mark.parametrize("p_hi,p_lo", [(4, 2), (3, 1), (4, 3), (2, 1)])
 def test_restriction_matches_oracle(etype, p_hi, p_lo):
     R = fr.transfer(etype, p_hi, p_lo)
@@ -18,7 +18,7 @@ def test_restriction_matches_oracle(etype, p_hi, p_lo):
     np.testing.assert_allclose(R, Ro, rtol=0, atol=1e-13)
 
 
-@pytest.mark.parametrize("etype", ["tet", "pri"])
+@pytest.mark.parametrize("etype", ["tet", "pri", "hex"])
 def test_prolongation_then_restriction_is_identity(etype):
     up = fr.transfer(etype, 2, 4)
     down = fr.transfer(etype, 4, 2)
@@ -30,7 +30,7 @@ def test_prolongation_then_restriction_is_identity(etype):
 
 
 def test_transfer_same_order_is_identity():
-    for et in ("tet", "pri"):
+    for et in ("tet", "pri", "hex"):
         np.testing.assert_allclose(fr.transfer(et, 3, 3), np.eye(fr.transfer(et, 3, 3).shape[0]), atol=1e-14)
 
 
@@ -38,7 +38,7 @@ def test_transfer_rejects_bad_arguments():
     with pytest.raises(fr.FRError):
         fr.transfer("tet", 5, 2)
     with pytest.raises(fr.FRError):
-        fr.transfer(2, 4, 2)
+        fr.transfer(3, 4, 2)
 
 
 def test_mlp_sizes():

@@ -71,8 +71,9 @@ def min_edge(mesh):
     xyz = mesh["xyz"]
     h = np.inf
     for key, pairs in (("tet", [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]),
-                       ("pri", [(0, 1), (1, 2), (2, 0), (0, 3), (1, 4), (2, 5)])):
-        c = mesh[key]
+                       ("pri", [(0, 1), (1, 2), (2, 0), (0, 3), (1, 4), (2, 5)]),
+                       ("hex", [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (1, 5), (2, 6), (3, 7)])):
+        c = mesh.get(key, ())
         if len(c) == 0:
             continue
         for a, b in pairs:
@@ -499,6 +500,56 @@ def min_volume_to_area(mesh):
     return r
 
 
+HEX_NZ = 29  # 75 x 54 x 29 = 117,450 hexahedra (the paper's hex mesh: 118,070)
+
+
+def hex_mode(fr, torch, args, sp):
+    """The boundary-layer box meshed with hexahedra only (Table 2's third
+    type; the paper's cylinder mesh is all-hex): the same 54 stretched and
+    uniform layers and flow, 75 x 54 x 29 = 117,450 hexahedra, NS, p = 4,
+    FP64, RK4."""
+    import synth
+    mesh = synth.boundary_layer_box(nx=75, nz=HEX_NZ, all_hex=True)
+    ctx = fr.Context(mesh, ORDER, **flow_params())
+    u0 = points_to_public(synth.perturbed_freestream(ctx.upts_points(), seed=2, wall_delta=WALL_DELTA),
+                          ctx.counts())
+    dt = time_step_size(mesh, ORDER)
+    ctx.set_state(u0, sp)
+    for _ in range(max(args.warmup, 0)):
+        ctx.step(dt, 1, sp)
+    torch.cuda.synchronize()
+    stream = torch.cuda.ExternalStream(sp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(dt, 1, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    classes, launches = ctx.profile_read()
+    ctx.profile(False)
+    finite = ctx.reduce(stream=sp, check=False)[6] == 0.0
+    gemm = ("M0", "grad", "M0_grad", "div")
+    gflops = sum(gemm_flops(ctx, k) for k in gemm) * 4 * args.steps
+    gms = sum(classes[k][0] for k in gemm)
+    dom = max(gemm, key=lambda k: classes[k][0])
+    fp64_peak = 152 * 2 * 2 * 2.07e9
+    dom_ach = gemm_flops(ctx, dom) * 4 * args.steps / (classes[dom][0] * 1e-3)
+    out = {"value": ctx.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+           "workload": f"boundary-layer box, hexahedra only: {ctx.info['n_hex']} hexes, NS p=4 FP64, RK4",
+           "ndof": ctx.ndof, "kernel_ms_per_step": {k: v[0] / args.steps for k, v in classes.items()},
+           "gpu_launches": int(launches), "state_finite": bool(finite),
+           "gemm_share": gms / sum(v[0] for v in classes.values()),
+           "gemm_fp64_tflops": gflops / (gms * 1e-3) / 1e12,
+           "roofline": {"bound": "alu", "kernel": f"k_gemm ({dom})", "achieved": dom_ach / 1e12,
+                        "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": dom_ach / fp64_peak,
+                        "traffic": None, "launches": classes[dom][1],
+                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}}
+    ctx.close()
+    return out
+
+
 def learned_mode(fr, torch, args, sp):
     """The learned closure on the Taylor-Green vortex (Re 1600, Ma 0.1,
     periodic [0, 2 pi]^3 of 24^3 cells: 13,824 prisms + 41,472 tets).
@@ -777,6 +828,7 @@ def main():
         if args.nx == 75:
             modes["batched"] = batch_mode(fr, torch, args, sp)
             modes["learned"] = learned_mode(fr, torch, args, sp)
+            modes["hex"] = hex_mode(fr, torch, args, sp)
 
     if rank != 0:
         if world > 1:

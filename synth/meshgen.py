@@ -235,11 +235,12 @@ def vortex_box(n=4, jitter=0.05, seed=0, n_prism_layers=None, lo=-5.0, hi=5.0):
 
 def boundary_layer_box(nx=75, nz=12, n_prism_layers=32, n_tet_layers=22,
                        h0=0.03208, ratio=1.1, lx=20.0, ly=20.0, lz=math.pi,
-                       jitter=0.05, seed=1):
+                       jitter=0.05, seed=1, all_hex=False):
     """Box [0,lx]x[0,ly]x[0,lz]: geometrically stretched prism layers on a
     no-slip wall at y=0 under uniform Kuhn-tet layers up to y=ly; far field
     at x=0, x=lx, y=ly; periodic in z.  The defaults give 57,600 prisms and
-    118,800 tets."""
+    118,800 tets.  all_hex: the same layers, every cell a hexahedron
+    (nx=75, nz=29 gives 117,450 hexahedra)."""
     yb = h0 * (ratio ** np.arange(n_prism_layers + 1) - 1.0) / (ratio - 1.0)
     yt = np.linspace(yb[-1], ly, n_tet_layers + 1)[1:]
     y = np.concatenate([yb, yt])
@@ -247,6 +248,9 @@ def boundary_layer_box(nx=75, nz=12, n_prism_layers=32, n_tet_layers=22,
     z = np.linspace(0.0, lz, nz + 1)
     bcs = {(1, 0): BC_WALL, (1, 1): BC_FARFIELD, (0, 0): BC_FARFIELD,
            (0, 1): BC_FARFIELD}
+    if all_hex:
+        return layered_box((x, y, z), 1, len(y) - 1, (False, False, True), bcs=bcs,
+                           jitter=jitter, seed=seed, n_hex_cols=nz)
     return layered_box((x, y, z), 1, n_prism_layers, (False, False, True),
                        bcs=bcs, jitter=jitter, seed=seed)
 

@@ -310,12 +310,30 @@ int front_stages(fr_ctx *c, T *const in[NT], cudaStream_t s) {
                                     [&] { return launch_common_solution<T>(pairs_of(c), bnd_of(c), F, ph, s); }),
                              "common solution")))
             return rc;
-        // 3. corrected physical gradient; 4. gradient at flux points
+        // 3. corrected physical gradient; 4. gradient at flux points.  On
+        // the tensor cores the operator kernel stores the reference gradient
+        // and the flux kernel (5.), which loads the point's geometry anyway,
+        // forms the physical gradient in place before M0 is applied to it
+        // (in the operator kernel's epilogue those loads would repeat for
+        // every variable and stall it)
+        const bool tc = is_tc(c);
         for (int t = 0; t < NT; ++t) {
             if (!c->T[t].present) continue;
-            const GemmArgsT<T> g = args_grad<T>(c, t, in[t]);
+            GemmArgsT<T> g = args_grad<T>(c, t, in[t]);
+            if (tc) g.mode = GEMM_STORE;
             if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return op_gemm<T>(c, t, 1, g, s); }), "gemm grad")))
                 return rc;
+            if (tc) {
+                DevType &D = c->T[t];
+                if ((rc = cuda_check(launch(c, K_FLUX, s,
+                                            [&] {
+                                                return launch_flux<T>(D.nu, D.ne, D.np, in[t], (T *)D.GU,
+                                                                      (const T *)D.S_t, (const T *)D.invJ_t,
+                                                                      (T *)D.FT, ph, s);
+                                            }),
+                                     "flux")))
+                    return rc;
+            }
             const GemmArgsT<T> h = args_m0grad<T>(c, t);
             if ((rc = cuda_check(launch(c, K_M0_GRAD, s, [&] { return op_gemm<T>(c, t, 0, h, s); }), "gemm M0 grad")))
                 return rc;
@@ -330,14 +348,15 @@ int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) 
     const FieldsT<T> F = fields_of<T>(c);
     int rc;
     if ((rc = front_stages<T>(c, in, s))) return rc;
-    // 5. transformed flux at solution points
-    for (int t = 0; t < NT; ++t) {
+    // 5. transformed flux at solution points (done by front_stages for
+    // Navier-Stokes on the tensor cores)
+    for (int t = 0; t < NT && !(is_tc(c) && c->prm.viscous); ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch(c, K_FLUX, s,
                                     [&] {
-                                        return launch_flux<T>(D.nu, D.ne, D.np, in[t], (const T *)D.GU,
-                                                              (const T *)D.S_t, (T *)D.FT, ph, s);
+                                        return launch_flux<T>(D.nu, D.ne, D.np, in[t], (T *)D.GU, (const T *)D.S_t,
+                                                              (const T *)nullptr, (T *)D.FT, ph, s);
                                     }),
                              "flux")))
             return rc;

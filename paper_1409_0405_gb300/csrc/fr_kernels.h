@@ -189,9 +189,10 @@ cudaError_t launch_wall_force(const Bnd &B, const double *bw, const FieldsT<T> &
                               int nblocks, cudaStream_t s);
 cudaError_t launch_sum_partials(const double *partial, int nblocks, int nq, double *out, cudaStream_t s);
 // transformed flux at the solution points of one type; U is the centred
-// stage input (u - uref)
+// stage input (u - uref).  invJ non-null: GU holds the reference gradient
+// (rows (j, d)) on entry and receives the physical gradient (rows (j, m))
 template <typename T>
-cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, const T *GU, const T *S, T *FT,
+cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, T *GU, const T *S, const T *invJ, T *FT,
                         const Phys &ph, cudaStream_t s);
 // public [e][v][j] (double) -> internal [j][v][e]: `in` (double, may be
 // null) receives the values, `centred` (T, may be null) u - uref

@@ -411,16 +411,23 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int nblocks, 
     }
 }
 
-// transformed flux F~_d = sum_m S[d][m] (F_inv - F_vis - F_ref)_m at solution points
+// transformed flux F~_d = sum_m S[d][m] (F_inv - F_vis - F_ref)_m at solution points.
+// With invJ set, GU holds the reference gradient g^_d on entry (rows (j, d));
+// the physical gradient grad_m u = (1/J) sum_d S[d][m] g^_d is formed here,
+// written back over it (in place: one thread owns the point's 15 values) and
+// used for the viscous flux.
 template <typename T>
 __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T *__restrict__ U,
-                                        const T *__restrict__ GU, const T *__restrict__ S, T *__restrict__ FT,
-                                        const PhysT<T> &ph, int64_t idx) {
+                                        T *__restrict__ GU, const T *__restrict__ S, const T *__restrict__ invJ,
+                                        T *__restrict__ FT, const PhysT<T> &ph, int64_t idx) {
     const int64_t j = idx / np, e = idx - j * np;
     if (j >= nu || e >= ne) return;
     T u[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) u[v] = U[(j * V + v) * np + e] + ph.uref[v];
+    T s[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];
     const Prim<T> q = prim(u, ph.gamma);
     T F[V][3];
 #pragma unroll
@@ -436,6 +443,18 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
         for (int m = 0; m < 3; ++m)
 #pragma unroll
             for (int v = 0; v < V; ++v) g[m][v] = GU[((j * 3 + m) * V + v) * np + e];
+        if (invJ) {
+            const T ij = invJ[j * np + e];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T g0 = g[0][v], g1 = g[1][v], g2 = g[2][v];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    g[m][v] = ij * (s[m] * g0 + s[3 + m] * g1 + s[6 + m] * g2);
+                    GU[((j * 3 + m) * V + v) * np + e] = g[m][v];
+                }
+            }
+        }
         vis_flux(u, q, g, ph.mu, ph.kq, Fv);
 #pragma unroll
         for (int v = 0; v < V; ++v)
@@ -446,9 +465,6 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
     for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int m = 0; m < 3; ++m) F[v][m] -= ph.fref[v][m];
-    T s[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -457,9 +473,9 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
 }
 
 template <typename T>
-__global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, const T *__restrict__ GU,
-                       const T *__restrict__ S, T *__restrict__ FT, const PhysT<T> ph) {
-    flux_at(nu, ne, np, U, GU, S, FT, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, T *__restrict__ GU,
+                       const T *__restrict__ S, const T *__restrict__ invJ, T *__restrict__ FT, const PhysT<T> ph) {
+    flux_at(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -482,7 +498,8 @@ __global__ void k_flux_grouped(const FluxItem<T> *__restrict__ items, const int6
          gi += (int64_t)gridDim.x * blockDim.x) {
         const int i = find_item(begin, n, gi);
         const FluxItem<T> &it = items[i];
-        flux_at(it.nu, it.ne, it.np, it.U, it.GU, it.S, it.FT, ph, gi - begin[i]);
+        flux_at(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, (const T *)nullptr, it.FT, ph,
+                gi - begin[i]);
     }
 }
 
@@ -673,11 +690,11 @@ cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const FieldsT<T> &F
 }
 
 template <typename T>
-cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, const T *GU, const T *S, T *FT,
+cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, T *GU, const T *S, const T *invJ, T *FT,
                         const Phys &ph, cudaStream_t s) {
     const int64_t n = (int64_t)nu * np;
     if (ne == 0) return cudaSuccess;
-    k_flux<T><<<blocks_for(n, 128), 128, 0, s>>>(nu, ne, np, U, GU, S, FT, phys_t<T>(ph));
+    k_flux<T><<<blocks_for(n, 128), 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph));
     return cudaGetLastError();
 }
 
@@ -784,7 +801,7 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
                                            double *, int, cudaStream_t);                                      \
     template cudaError_t launch_wall_force<T>(const Bnd &, const double *, const FieldsT<T> &, const Phys &,      \
                                               double *, int, cudaStream_t);                                   \
-    template cudaError_t launch_flux<T>(int, int64_t, int64_t, const T *, const T *, const T *, T *,            \
+    template cudaError_t launch_flux<T>(int, int64_t, int64_t, const T *, T *, const T *, const T *, T *,       \
                                         const Phys &, cudaStream_t);                                          \
     template cudaError_t launch_pub_to_int<T>(int, int64_t, int64_t, const double *, double *, cudaStream_t,    \
                                               T *, const double *);                                           \

@@ -368,9 +368,10 @@ int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) 
         return rc;
     // 7. divergence plus correction; with the learned closure on, the
     // network's correction is added by the epilogue with the reference term
-    // With the tensor cores the GEMM stores R and a streaming pass applies
-    // the RK update (its FP64 register traffic would otherwise stall the
-    // GEMM's epilogue warps).
+    // With the tensor cores and an RK stage the operator kernel stores the
+    // raw product and a streaming pass scales it by -1/J, adds the
+    // reference/closure term and applies the RK update (per-point loads and
+    // FP64 register traffic would otherwise stall the kernel's epilogue).
     const bool split_rk = rk && is_tc(c);
     for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
@@ -380,13 +381,15 @@ int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) 
             if ((rc = closure_apply<T>(c, t, in[t], s))) return rc;
             g.rfs = D.cl_add;
         }
+        const double *rfs = g.rfs;
+        if (split_rk) g.mode = GEMM_STORE;
         if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return op_gemm<T>(c, t, 2, g, s); }), "gemm div"))) return rc;
         if (split_rk &&
             (rc = cuda_check(launch(c, K_DIV, s,
                                     [&] {
                                         return launch_rk_update<T>(D.nu, D.np, (const T *)D.R, D.U, D.Uacc, (T *)D.Us,
                                                                    ph.uref, rk->c_acc, rk->c_stage, rk->first,
-                                                                   rk->last, s);
+                                                                   rk->last, (const T *)D.invJ_t, rfs, s);
                                     }),
                              "RK update")))
             return rc;

@@ -244,10 +244,13 @@ cudaError_t launch_const_common(const Pairs &P, const Bnd &B, const Fields &F, c
 template <typename T>
 cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const double *uref, cudaStream_t s);
 // RK4 register update (the GEMM_DIV_RK epilogue) from a stored RHS R
-// [nu][V][np]: see GemmArgsT for c_acc, c_stage, first, last
+// [nu][V][np]: see GemmArgsT for c_acc, c_stage, first, last.  invJ
+// non-null: R is the raw product of the divergence operator, and the RHS
+// is -(1/J) R (formed in T) plus rfs (FP64, may be null)
 template <typename T>
 cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
-                             double c_acc, double c_stage, int first, int last, cudaStream_t s);
+                             double c_acc, double c_stage, int first, int last, const T *invJ, const double *rfs,
+                             cudaStream_t s);
 // low-storage (2N) RK stage: dU = a dU + dt R (dU unread when first),
 // U += b dU, Us = U - uref; R [nu][V][np]
 template <typename T>

@@ -600,11 +600,21 @@ __global__ void k_center(int64_t n, int64_t np, const double *__restrict__ U, T 
 template <typename T>
 __global__ void k_rk_update(int64_t n, int64_t np, const T *__restrict__ R, double *__restrict__ U,
                             double *__restrict__ Uacc, T *__restrict__ Us, const Uref uref, double c_acc,
-                            double c_stage, int first, int last) {
+                            double c_stage, int first, int last, const T *__restrict__ invJ,
+                            const double *__restrict__ rfs) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     const double ur = uref.v[(idx / np) % V];
-    const double rv = (double)R[idx];
+    double rv;
+    if (invJ) {
+        // R holds the raw divergence-plus-correction product: scale it by
+        // -1/J (in T, as the divergence epilogue does) and add rfs
+        const int64_t j = idx / (V * np), e = idx % np;
+        const T rt = -invJ[j * np + e] * R[idx];
+        rv = (double)rt + (rfs ? rfs[idx] : 0.0);
+    } else {
+        rv = (double)R[idx];
+    }
     if (last) {
         const double un = Uacc[idx] + c_acc * rv;
         U[idx] = un;
@@ -736,11 +746,13 @@ cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const doub
 
 template <typename T>
 cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
-                             double c_acc, double c_stage, int first, int last, cudaStream_t s) {
+                             double c_acc, double c_stage, int first, int last, const T *invJ, const double *rfs,
+                             cudaStream_t s) {
     const int64_t n = (int64_t)nu * V * np;
     if (n == 0) return cudaSuccess;
     Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
-    k_rk_update<T><<<blocks_for(n, 256), 256, 0, s>>>(n, np, R, U, Uacc, Us, r, c_acc, c_stage, first, last);
+    k_rk_update<T><<<blocks_for(n, 256), 256, 0, s>>>(n, np, R, U, Uacc, Us, r, c_acc, c_stage, first, last, invJ,
+                                                      rfs);
     return cudaGetLastError();
 }
 
@@ -807,7 +819,8 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
                                               T *, const double *);                                           \
     template cudaError_t launch_center<T>(int, int64_t, const double *, T *, const double *, cudaStream_t);     \
     template cudaError_t launch_rk_update<T>(int, int64_t, const T *, double *, double *, T *, const double *,   \
-                                             double, double, int, int, cudaStream_t);                        \
+                                             double, double, int, int, const T *, const double *,            \
+                                             cudaStream_t);                                                  \
     template cudaError_t launch_rk_2n_update<T>(int, int64_t, const T *, double *, double *, T *,                \
                                                 const double *, double, double, double, int, cudaStream_t);  \
     template cudaError_t launch_int_to_pub<T>(int, int64_t, int64_t, const T *, double *, cudaStream_t);       \

@@ -389,7 +389,7 @@ int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) 
                                     [&] {
                                         return launch_rk_update<T>(D.nu, D.np, (const T *)D.R, D.U, D.Uacc, (T *)D.Us,
                                                                    ph.uref, rk->c_acc, rk->c_stage, rk->first,
-                                                                   rk->last, (const T *)D.invJ_t, rfs, s);
+                                                                   rk->last, (const T *)D.invJ_t, rfs, (T *)D.Us0, s);
                                     }),
                              "RK update")))
             return rc;
@@ -457,6 +457,9 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             (rc = dev_alloc_bytes(c, &D.Us, su * es)) || (rc = dev_alloc_bytes(c, &D.R, su * es)) ||
             (rc = dev_alloc_bytes(c, &D.UF, sf * es)) || (rc = dev_alloc_bytes(c, &D.FC, sf * es)) ||
             (rc = dev_alloc_bytes(c, &D.FT, 3 * su * es)))
+            return rc;
+        if ((prm->precision == FR_BF16X3 || prm->precision == FR_TF32X3) &&
+            (rc = dev_alloc_bytes(c, &D.Us0, su * es)))
             return rc;
         if (prm->viscous) {
             if ((rc = dev_alloc_bytes(c, &D.DUF, sf * es)) || (rc = dev_alloc_bytes(c, &D.GU, 3 * su * es)) ||

@@ -30,6 +30,7 @@ struct DevType {
     // FR_FP64, float for FR_FP32; the geometry/operator views alias the
     // double arrays in FR_FP64)
     void *Us = nullptr, *R = nullptr;        // [nu][V][np]
+    void *Us0 = nullptr;                     // [nu][V][np], tensor-core modes: centred step start state
     void *UF = nullptr, *DUF = nullptr, *FC = nullptr;   // [nf][V][np]
     void *GU = nullptr, *FT = nullptr;       // [nu][3][V][np]
     void *GUF = nullptr;                     // [nf][3][V][np]

@@ -246,11 +246,13 @@ cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const doub
 // RK4 register update (the GEMM_DIV_RK epilogue) from a stored RHS R
 // [nu][V][np]: see GemmArgsT for c_acc, c_stage, first, last.  invJ
 // non-null: R is the raw product of the divergence operator, and the RHS
-// is -(1/J) R (formed in T) plus rfs (FP64, may be null)
+// is -(1/J) R (formed in T) plus rfs (FP64, may be null).  Us0 non-null
+// (a T register): the stage inputs of stages 2-3 are formed in T from the
+// step's centred start state, which the first stage copies from Us to Us0
 template <typename T>
 cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
                              double c_acc, double c_stage, int first, int last, const T *invJ, const double *rfs,
-                             cudaStream_t s);
+                             T *Us0, cudaStream_t s);
 // low-storage (2N) RK stage: dU = a dU + dt R (dU unread when first),
 // U += b dU, Us = U - uref; R [nu][V][np]
 template <typename T>

@@ -419,8 +419,7 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int nblocks, 
 template <typename T>
 __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T *__restrict__ U,
                                         T *__restrict__ GU, const T *__restrict__ S, const T *__restrict__ invJ,
-                                        T *__restrict__ FT, const PhysT<T> &ph, int64_t idx) {
-    const int64_t j = idx / np, e = idx - j * np;
+                                        T *__restrict__ FT, const PhysT<T> &ph, int64_t j, int64_t e) {
     if (j >= nu || e >= ne) return;
     T u[V];
 #pragma unroll
@@ -475,7 +474,8 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
 template <typename T>
 __global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, T *__restrict__ GU,
                        const T *__restrict__ S, const T *__restrict__ invJ, T *__restrict__ FT, const PhysT<T> ph) {
-    flux_at(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    // 2-D grid: y = solution point, x = element
+    flux_at(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.y, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -498,8 +498,9 @@ __global__ void k_flux_grouped(const FluxItem<T> *__restrict__ items, const int6
          gi += (int64_t)gridDim.x * blockDim.x) {
         const int i = find_item(begin, n, gi);
         const FluxItem<T> &it = items[i];
-        flux_at(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, (const T *)nullptr, it.FT, ph,
-                gi - begin[i]);
+        const int64_t idx = gi - begin[i], j = idx / it.np;
+        flux_at(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, (const T *)nullptr, it.FT, ph, j,
+                idx - j * it.np);
     }
 }
 
@@ -587,38 +588,62 @@ __global__ void k_pub_to_int(int nu, int64_t ne, int64_t np, const double *__res
     if (centred) centred[(j * V + v) * np + e] = T(x - uref.v[v]);
 }
 
+// The register kernels below run on a 2-D grid: y = row (j, v) of the
+// [nu][V][np] register, x = element; no integer division per thread.
 template <typename T>
-__global__ void k_center(int64_t n, int64_t np, const double *__restrict__ U, T *__restrict__ Us, const Uref uref) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
-    const int64_t v = (idx / np) % V;
-    Us[idx] = T(U[idx] - uref.v[v]);
+__global__ void k_center(int64_t np, const double *__restrict__ U, T *__restrict__ Us, const Uref uref) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    const int row = blockIdx.y;
+    const int64_t idx = (int64_t)row * np + e;
+    Us[idx] = T(U[idx] - uref.v[row % V]);
 }
 
 // RK4 register update from a stored RHS r (the arithmetic of the fused
 // GEMM_DIV_RK epilogue, applied as a separate streaming pass)
 template <typename T>
-__global__ void k_rk_update(int64_t n, int64_t np, const T *__restrict__ R, double *__restrict__ U,
+__global__ void k_rk_update(int64_t np, const T *__restrict__ R, double *__restrict__ U,
                             double *__restrict__ Uacc, T *__restrict__ Us, const Uref uref, double c_acc,
                             double c_stage, int first, int last, const T *__restrict__ invJ,
-                            const double *__restrict__ rfs) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
-    const double ur = uref.v[(idx / np) % V];
+                            const double *__restrict__ rfs, T *__restrict__ Us0) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    const int row = blockIdx.y;
+    const int64_t idx = (int64_t)row * np + e;
+    const double ur = uref.v[row % V];
+    T rt;
     double rv;
     if (invJ) {
         // R holds the raw divergence-plus-correction product: scale it by
         // -1/J (in T, as the divergence epilogue does) and add rfs
-        const int64_t j = idx / (V * np), e = idx % np;
-        const T rt = -invJ[j * np + e] * R[idx];
-        rv = (double)rt + (rfs ? rfs[idx] : 0.0);
+        rt = -invJ[(int64_t)(row / V) * np + e] * R[idx];
+        rv = (double)rt;
+        if (rfs) {
+            rv += rfs[idx];
+            rt = T(rv);
+        }
     } else {
-        rv = (double)R[idx];
+        rt = R[idx];
+        rv = (double)rt;
     }
     if (last) {
         const double un = Uacc[idx] + c_acc * rv;
         U[idx] = un;
         Us[idx] = T(un - ur);
+    } else if (Us0) {
+        // the next stage input (u_n - uref) + c_stage r formed in T from the
+        // step's centred start state (Us at the first stage, kept in Us0):
+        // only the FP64 accumulator update runs on the FP64 pipe
+        T b0;
+        if (first) {
+            b0 = Us[idx];
+            Us0[idx] = b0;
+            Uacc[idx] = U[idx] + c_acc * rv;
+        } else {
+            b0 = Us0[idx];
+            Uacc[idx] = Uacc[idx] + c_acc * rv;
+        }
+        Us[idx] = b0 + T(c_stage) * rt;
     } else {
         const double u = U[idx];
         Uacc[idx] = (first ? u : Uacc[idx]) + c_acc * rv;
@@ -629,16 +654,18 @@ __global__ void k_rk_update(int64_t n, int64_t np, const T *__restrict__ R, doub
 // low-storage (2N) Runge-Kutta stage from a stored RHS r:
 // dU = a dU + dt r (dU not read when first), U += b dU, Us = U - uref
 template <typename T>
-__global__ void k_rk_2n_update(int64_t n, int64_t np, const T *__restrict__ R, double *__restrict__ U,
+__global__ void k_rk_2n_update(int64_t np, const T *__restrict__ R, double *__restrict__ U,
                                double *__restrict__ dU, T *__restrict__ Us, const Uref uref, double a, double b,
                                double dt, int first) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    const int row = blockIdx.y;
+    const int64_t idx = (int64_t)row * np + e;
     const double du = (first ? 0.0 : a * dU[idx]) + dt * (double)R[idx];
     const double u = U[idx] + b * du;
     dU[idx] = du;
     U[idx] = u;
-    Us[idx] = T(u - uref.v[(idx / np) % V]);
+    Us[idx] = T(u - uref.v[row % V]);
 }
 
 __global__ void k_to_float(int64_t n, const double *__restrict__ src, float *__restrict__ dst) {
@@ -702,9 +729,8 @@ cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const FieldsT<T> &F
 template <typename T>
 cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, T *GU, const T *S, const T *invJ, T *FT,
                         const Phys &ph, cudaStream_t s) {
-    const int64_t n = (int64_t)nu * np;
     if (ne == 0) return cudaSuccess;
-    k_flux<T><<<blocks_for(n, 128), 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph));
+    k_flux<T><<<dim3(blocks_for(ne, 128), (unsigned)nu), 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph));
     return cudaGetLastError();
 }
 
@@ -740,19 +766,20 @@ cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const doub
     const int64_t n = (int64_t)nu * V * np;
     if (n == 0) return cudaSuccess;
     Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
-    k_center<T><<<blocks_for(n, 256), 256, 0, s>>>(n, np, U, Us, r);
+    k_center<T><<<dim3(blocks_for(np, 256), (unsigned)(nu * V)), 256, 0, s>>>(np, U, Us, r);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
                              double c_acc, double c_stage, int first, int last, const T *invJ, const double *rfs,
-                             cudaStream_t s) {
+                             T *Us0, cudaStream_t s) {
     const int64_t n = (int64_t)nu * V * np;
     if (n == 0) return cudaSuccess;
     Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
-    k_rk_update<T><<<blocks_for(n, 256), 256, 0, s>>>(n, np, R, U, Uacc, Us, r, c_acc, c_stage, first, last, invJ,
-                                                      rfs);
+    k_rk_update<T><<<dim3(blocks_for(np, 256), (unsigned)(nu * V)), 256, 0, s>>>(np, R, U, Uacc, Us, r, c_acc,
+                                                                                 c_stage, first, last, invJ, rfs,
+                                                                                 Us0);
     return cudaGetLastError();
 }
 
@@ -762,7 +789,8 @@ cudaError_t launch_rk_2n_update(int nu, int64_t np, const T *R, double *U, doubl
     const int64_t n = (int64_t)nu * V * np;
     if (n == 0) return cudaSuccess;
     Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
-    k_rk_2n_update<T><<<blocks_for(n, 256), 256, 0, s>>>(n, np, R, U, dU, Us, r, a, b, dt, first);
+    k_rk_2n_update<T><<<dim3(blocks_for(np, 256), (unsigned)(nu * V)), 256, 0, s>>>(np, R, U, dU, Us, r, a, b, dt,
+                                                                                    first);
     return cudaGetLastError();
 }
 
@@ -819,7 +847,7 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
                                               T *, const double *);                                           \
     template cudaError_t launch_center<T>(int, int64_t, const double *, T *, const double *, cudaStream_t);     \
     template cudaError_t launch_rk_update<T>(int, int64_t, const T *, double *, double *, T *, const double *,   \
-                                             double, double, int, int, const T *, const double *,            \
+                                             double, double, int, int, const T *, const double *, T *,       \
                                              cudaStream_t);                                                  \
     template cudaError_t launch_rk_2n_update<T>(int, int64_t, const T *, double *, double *, T *,                \
                                                 const double *, double, double, double, int, cudaStream_t);  \

@@ -368,10 +368,13 @@ int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) 
         return rc;
     // 7. divergence plus correction; with the learned closure on, the
     // network's correction is added by the epilogue with the reference term
-    // With the tensor cores and an RK stage the operator kernel stores the
-    // raw product and a streaming pass scales it by -1/J, adds the
-    // reference/closure term and applies the RK update (per-point loads and
-    // FP64 register traffic would otherwise stall the kernel's epilogue).
+    // On the tensor cores an RK stage's operator kernel stores the raw
+    // product and a streaming pass scales it by -1/J, adds the
+    // reference/closure term and applies the RK update, forming the next
+    // stage input in FP32 (per-point loads and the FP64 register arithmetic
+    // would otherwise stall the kernel's epilogue on the FP64 pipe).  The
+    // FP32 SIMT mode keeps the fused epilogue, which the batched launches
+    // reproduce bit for bit.
     const bool split_rk = rk && is_tc(c);
     for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];

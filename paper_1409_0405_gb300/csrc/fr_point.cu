@@ -412,11 +412,11 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int nblocks, 
 }
 
 // transformed flux F~_d = sum_m S[d][m] (F_inv - F_vis - F_ref)_m at solution points.
-// With invJ set, GU holds the reference gradient g^_d on entry (rows (j, d));
-// the physical gradient grad_m u = (1/J) sum_d S[d][m] g^_d is formed here,
+// XFORM: GU holds the reference gradient g^_d on entry (rows (j, d)); the
+// physical gradient grad_m u = (1/J) sum_d S[d][m] g^_d is formed here,
 // written back over it (in place: one thread owns the point's 15 values) and
 // used for the viscous flux.
-template <typename T>
+template <typename T, bool XFORM>
 __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T *__restrict__ U,
                                         T *__restrict__ GU, const T *__restrict__ S, const T *__restrict__ invJ,
                                         T *__restrict__ FT, const PhysT<T> &ph, int64_t j, int64_t e) {
@@ -425,8 +425,10 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
 #pragma unroll
     for (int v = 0; v < V; ++v) u[v] = U[(j * V + v) * np + e] + ph.uref[v];
     T s[9];
+    if (XFORM) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];
+        for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];
+    }
     const Prim<T> q = prim(u, ph.gamma);
     T F[V][3];
 #pragma unroll
@@ -442,7 +444,7 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
         for (int m = 0; m < 3; ++m)
 #pragma unroll
             for (int v = 0; v < V; ++v) g[m][v] = GU[((j * 3 + m) * V + v) * np + e];
-        if (invJ) {
+        if (XFORM) {
             const T ij = invJ[j * np + e];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -464,6 +466,10 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
     for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int m = 0; m < 3; ++m) F[v][m] -= ph.fref[v][m];
+    if (!XFORM) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -471,11 +477,12 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
             FT[((j * 3 + d) * V + v) * np + e] = s[d * 3 + 0] * F[v][0] + s[d * 3 + 1] * F[v][1] + s[d * 3 + 2] * F[v][2];
 }
 
-template <typename T>
+template <typename T, bool XFORM>
 __global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, T *__restrict__ GU,
                        const T *__restrict__ S, const T *__restrict__ invJ, T *__restrict__ FT, const PhysT<T> ph) {
     // 2-D grid: y = solution point, x = element
-    flux_at(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.y, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    flux_at<T, XFORM>(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.y,
+                      (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -499,8 +506,8 @@ __global__ void k_flux_grouped(const FluxItem<T> *__restrict__ items, const int6
         const int i = find_item(begin, n, gi);
         const FluxItem<T> &it = items[i];
         const int64_t idx = gi - begin[i], j = idx / it.np;
-        flux_at(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, (const T *)nullptr, it.FT, ph, j,
-                idx - j * it.np);
+        flux_at<T, false>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, (const T *)nullptr, it.FT, ph,
+                          j, idx - j * it.np);
     }
 }
 
@@ -730,7 +737,11 @@ template <typename T>
 cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, T *GU, const T *S, const T *invJ, T *FT,
                         const Phys &ph, cudaStream_t s) {
     if (ne == 0) return cudaSuccess;
-    k_flux<T><<<dim3(blocks_for(ne, 128), (unsigned)nu), 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph));
+    const dim3 grid(blocks_for(ne, 128), (unsigned)nu);
+    if (invJ)
+        k_flux<T, true><<<grid, 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph));
+    else
+        k_flux<T, false><<<grid, 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph));
     return cudaGetLastError();
 }
 

@@ -5,7 +5,11 @@ lambda of the reference tet.  Prisms use the linear-triangle x linear-zeta
 map x = sum_a tau_a(xi, eta) [(1-zeta)/2 X_a + (1+zeta)/2 X_{a+3}],
 which is not affine once nodes are jittered.  Hexes use the trilinear map
 x = sum_a N_a(xi) X_a, N_a = (1 + s_a0 xi)(1 + s_a1 eta)(1 + s_a2 zeta)/8
-with s_a the signs of reference vertex a.  Writing A = dx/dxi (columns
+with s_a the signs of reference vertex a.  Quadratically curved elements
+(10-node tets, 18-node prisms, 27-node hexes; node positions in
+QUAD_NODES) use the Lagrange basis of the degree-2 space of the element
+(P2; P2(triangle) x P2(zeta); Q2) through those nodes, x = sum_a N_a X_a,
+with N found by solving the monomial Vandermonde system.  Writing A = dx/dxi (columns
 a_d = dx/dxi_d), the transformed-flux matrix is S = J dxi/dx = adj(A),
 whose rows are a_1 x a_2, a_2 x a_0, a_0 x a_1.  A flux F in physical space
 becomes F~_d = sum_m S[d][m] F_m in reference space; at a face with
@@ -16,9 +20,48 @@ from __future__ import annotations
 import numpy as np
 
 
-def shape(etype, ref):
+_TRI6 = ((-1, -1), (1, -1), (-1, 1), (0, -1), (0, 0), (-1, 0))
+QUAD_NODES = {
+    "tet": ((-1, -1, -1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1),
+            (0, -1, -1), (-1, 0, -1), (-1, -1, 0), (0, 0, -1), (0, -1, 0), (-1, 0, 0)),
+    "pri": tuple((a, b, c) for c in (-1, 0, 1) for (a, b) in _TRI6),
+    "hex": tuple((a, b, c) for c in (-1, 0, 1) for b in (-1, 0, 1) for a in (-1, 0, 1)),
+}
+
+
+def _quad_exponents(etype):
+    if etype == "tet":
+        return [(a, b, c) for c in range(3) for b in range(3) for a in range(3) if a + b + c <= 2]
+    if etype == "pri":
+        return [(a, b, c) for c in range(3) for b in range(3) for a in range(3) if a + b <= 2]
+    return [(a, b, c) for c in range(3) for b in range(3) for a in range(3)]
+
+
+def _quad_shape(etype, ref):
+    ex = _quad_exponents(etype)
+    nodes = np.array(QUAD_NODES[etype], dtype=np.float64)
+    V = np.array([[x ** a * y ** b * z ** c for (a, b, c) in ex] for (x, y, z) in nodes])
+    C = np.linalg.inv(V)                       # N_a(x) = sum_m mono_m(x) C[m, a]
+    mono = np.stack([ref[:, 0] ** a * ref[:, 1] ** b * ref[:, 2] ** c for (a, b, c) in ex], axis=1)
+    dmono = np.zeros(mono.shape + (3,))
+    for m, (a, b, c) in enumerate(ex):
+        e = (a, b, c)
+        for d in range(3):
+            if e[d] == 0:
+                continue
+            f = float(e[d])
+            pw = list(e)
+            pw[d] -= 1
+            dmono[:, m, d] = f * ref[:, 0] ** pw[0] * ref[:, 1] ** pw[1] * ref[:, 2] ** pw[2]
+    return mono @ C, np.einsum("pmd,ma->pad", dmono, C)
+
+
+def shape(etype, ref, nv=None):
     """Shape functions N (npts, nv) and derivatives dN (npts, nv, 3) at
-    reference points ref (npts, 3)."""
+    reference points ref (npts, 3); nv = the quadratic node count selects the
+    curved element's basis."""
+    if nv is not None and nv == len(QUAD_NODES[etype]):
+        return _quad_shape(etype, np.asarray(ref, dtype=np.float64))
     xi, eta, zeta = ref[:, 0], ref[:, 1], ref[:, 2]
     npt = len(ref)
     if etype == "tet":
@@ -55,13 +98,13 @@ def shape(etype, ref):
 def map_points(etype, X, ref):
     """Physical coordinates (ne, npts, 3) of reference points for element
     vertex coordinates X (ne, nv, 3)."""
-    N, _ = shape(etype, ref)
+    N, _ = shape(etype, ref, X.shape[1])
     return np.einsum("pv,evk->epk", N, X)
 
 
 def jacobian(etype, X, ref):
     """A[e, p, k, d] = d x_k / d xi_d."""
-    _, dN = shape(etype, ref)
+    _, dN = shape(etype, ref, X.shape[1])
     return np.einsum("pvd,evk->epkd", dN, X)
 
 

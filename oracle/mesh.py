@@ -45,9 +45,15 @@ class Mesh:
         # geometry
         self.X, self.upts_x, self.J, self.S = {}, {}, {}, {}
         self.fpts_x, self.fn, self.fmag = {}, {}, {}
+        # quadratically curved elements: per-element node coordinates
+        curved = int(m.get("geom_order", 1)) == 2
         for t in self.types:
             op = self.ops[t]
-            X = xyz[conn[t]]
+            if curved:
+                X = np.asarray(m[t + "_nodes"], dtype=np.float64).reshape(
+                    self.ne[t], len(geometry.QUAD_NODES[t]), 3)
+            else:
+                X = xyz[conn[t]]
             self.X[t] = X
             self.upts_x[t] = geometry.map_points(t, X, op.upts)
             J, S = geometry.metric(t, X, op.upts)

@@ -11,7 +11,7 @@ their own from what this package returns.
 from .meshgen import (  # noqa: F401
     BC_WALL, BC_FARFIELD, ETYPE_TET, ETYPE_PRI, ETYPE_HEX, TET_FACES, PRI_FACES, HEX_FACES,
     layered_box, vortex_box, hex_box, boundary_layer_box, wall_channel, tgv_box, batch_problem_params,
-    batch_problem_mesh, mesh_counts,
+    batch_problem_mesh, mesh_counts, curve_mesh, QUAD_NODES,
 )
 from .ics import (  # noqa: F401
     isentropic_vortex, taylor_green, perturbed_freestream, uniform_state,

@@ -287,6 +287,62 @@ def hex_box(n=4, n_hex_cols=None, jitter=0.05, seed=0, lo=-5.0, hi=5.0):
                        seed=seed, n_hex_cols=nh)
 
 
+# Quadratic (curved) element node positions in reference coordinates: the
+# vertices, then (tet) the midpoints of edges (0,1), (0,2), (0,3), (1,2),
+# (1,3), (2,3); (prism) three zeta levels -1, 0, 1 of the six triangle nodes
+# (vertices 0, 1, 2, then midpoints of (0,1), (1,2), (2,0)); (hex) the
+# 3 x 3 x 3 grid of {-1, 0, 1}, xi fastest.
+_TRI6 = ((-1, -1), (1, -1), (-1, 1), (0, -1), (0, 0), (-1, 0))
+QUAD_NODES = {
+    "tet": ((-1, -1, -1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1),
+            (0, -1, -1), (-1, 0, -1), (-1, -1, 0), (0, 0, -1), (0, -1, 0), (-1, 0, 0)),
+    "pri": tuple((a, b, c) for c in (-1, 0, 1) for (a, b) in _TRI6),
+    "hex": tuple((a, b, c) for c in (-1, 0, 1) for b in (-1, 0, 1) for a in (-1, 0, 1)),
+}
+
+
+def _linear_weights(etype, r):
+    """Weights of the element's vertices at reference point r for its
+    straight-sided (vertex) map."""
+    xi, eta, zeta = r
+    if etype == "tet":
+        return np.array([-(1 + xi + eta + zeta) / 2, (1 + xi) / 2, (1 + eta) / 2, (1 + zeta) / 2])
+    if etype == "pri":
+        tau = np.array([-(xi + eta) / 2, (1 + xi) / 2, (1 + eta) / 2])
+        return np.concatenate([tau * (1 - zeta) / 2, tau * (1 + zeta) / 2])
+    sg = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+                   [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], dtype=np.float64)
+    return np.prod(1.0 + sg * np.array([xi, eta, zeta]), axis=1) / 8.0
+
+
+def curve_mesh(mesh, amp=0.1):
+    """Quadratically curved version of a mesh: each element's quadratic
+    nodes (QUAD_NODES) placed on the straight element and moved by the
+    smooth map x -> x + d(x), d_i = amp (L_i / 2 pi) prod_k sin(2 pi (x_k -
+    lo_k) / L_k), with L_k the period of a periodic axis (d is periodic, so
+    periodic images still match) and the bounding-box extent of another (d
+    vanishes on those boundary planes, which stay planar).  Vertex ids are
+    kept for the topology.  Adds 'geom_order' = 2 and '<type>_nodes'
+    (n, nq, 3) arrays."""
+    xyz = np.asarray(mesh["xyz"], dtype=np.float64)
+    lo, hi = xyz.min(0), xyz.max(0)
+    per = np.asarray(mesh.get("period", np.zeros(3)), dtype=np.float64)
+    L = np.where(per > 0, per, hi - lo)
+
+    def phi(x):
+        sk = np.sin(2.0 * math.pi * (x - lo) / L)
+        return x + amp * (L / (2.0 * math.pi)) * np.prod(sk, axis=-1, keepdims=True)
+
+    out = dict(mesh)
+    out["geom_order"] = 2
+    for t, nv in (("tet", 4), ("pri", 6), ("hex", 8)):
+        conn = np.asarray(mesh.get(t, np.zeros((0, nv))), dtype=np.int64).reshape(-1, nv)
+        W = np.array([_linear_weights(t, r) for r in QUAD_NODES[t]])        # (nq, nv)
+        X = np.einsum("qv,evk->eqk", W, xyz[conn])
+        out[t + "_nodes"] = phi(X)
+    return out
+
+
 def mesh_counts(mesh):
     return len(mesh["tet"]), len(mesh["pri"])
 

@@ -87,6 +87,24 @@ typedef struct {
     int64_t n_bface;
     const int64_t *bface; /* [n_bface][4]: etype, element, local face, bc tag */
     double period[3];     /* periodic translation per axis; 0 = not periodic */
+    /* Element geometry.  geom_order 1 (or 0): straight-sided elements, the
+     * maps of the vertices above.  geom_order 2: quadratically curved
+     * elements (the paper's cylinder mesh is quadratically curved, Sec.
+     * 3.2): per element the physical coordinates of its quadratic nodes,
+     * whose reference positions are, in order:
+     *   tet (10): the 4 vertices, then the midpoints of edges (0,1), (0,2),
+     *     (0,3), (1,2), (1,3), (2,3);
+     *   prism (18): for zeta = -1, 0, +1 in turn, the six triangle nodes
+     *     (-1,-1), (1,-1), (-1,1), (0,-1), (0,0), (-1,0);
+     *   hex (27): the grid {-1,0,1}^3, xi fastest, zeta slowest.
+     * The map is the Lagrange interpolant of the degree-2 space of the
+     * element (P2; P2(triangle) x P2(zeta); Q2) through those nodes.  The
+     * vertex ids above still define the topology (face matching); faces
+     * shared by two elements must carry the same node coordinates. */
+    int geom_order;
+    const double *tet_nodes; /* geom_order 2: [n_tet][10][3] */
+    const double *pri_nodes; /* geom_order 2: [n_pri][18][3] */
+    const double *hex_nodes; /* geom_order 2: [n_hex][27][3] */
 } fr_mesh;
 
 /* Gas, viscous and boundary parameters. */

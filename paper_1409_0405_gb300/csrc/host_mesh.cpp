@@ -3,7 +3,8 @@
 //
 // Element maps: tets are affine in the barycentric coordinates; prisms use
 // the linear-triangle x linear-zeta map and hexes the trilinear map, neither
-// affine once nodes are jittered.  With A = dx/dxi (columns a_d), S = J dxi/dx = adj(A) has rows
+// affine once nodes are jittered; quadratically curved elements the
+// Lagrange map of their degree-2 space through their quadratic nodes.  With A = dx/dxi (columns a_d), S = J dxi/dx = adj(A) has rows
 // a_1 x a_2, a_2 x a_0, a_0 x a_1; a physical flux F becomes F~_d =
 // sum_m S[d][m] F_m, and at a face the scaled physical normal is S^T n^.
 #include <algorithm>
@@ -63,16 +64,132 @@ void shape(int etype, const double *x, double *N, double (*dN)[3]) {
     }
 }
 
+// Quadratically curved elements: the Lagrange basis of the element's
+// degree-2 space (tet P2, prism P2(triangle) x P2(zeta), hex Q2) through its
+// quadratic nodes, N_a(x) = sum_m mono_m(x) C[m][a] with C the inverse of
+// the monomial Vandermonde matrix at the nodes (solved once per type).
+constexpr int kMaxQ = 27;
+struct QuadShape {
+    int nq = 0;
+    std::vector<std::array<int, 3>> ex;
+    std::vector<double> C;  // nq x nq, row m = monomial, column a = node
+};
+
+const double kTri6[6][2] = {{-1, -1}, {1, -1}, {-1, 1}, {0, -1}, {0, 0}, {-1, 0}};
+
+void quad_nodes(int etype, std::vector<std::array<double, 3>> &nodes) {
+    nodes.clear();
+    if (etype == FR_ETYPE_TET) {
+        const double t[10][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {0, -1, -1},
+                                 {-1, 0, -1},  {-1, -1, 0}, {0, 0, -1},  {0, -1, 0},  {-1, 0, 0}};
+        for (auto &p : t) nodes.push_back({p[0], p[1], p[2]});
+    } else if (etype == FR_ETYPE_PRI) {
+        for (int c = -1; c <= 1; ++c)
+            for (auto &p : kTri6) nodes.push_back({p[0], p[1], (double)c});
+    } else {
+        for (int c = -1; c <= 1; ++c)
+            for (int b = -1; b <= 1; ++b)
+                for (int a = -1; a <= 1; ++a) nodes.push_back({(double)a, (double)b, (double)c});
+    }
+}
+
+bool build_quad_shape(int etype, QuadShape &q) {
+    std::vector<std::array<double, 3>> nodes;
+    quad_nodes(etype, nodes);
+    q.nq = (int)nodes.size();
+    q.ex.clear();
+    for (int c = 0; c <= 2; ++c)
+        for (int b = 0; b <= 2; ++b)
+            for (int a = 0; a <= 2; ++a) {
+                const bool in = etype == FR_ETYPE_TET ? a + b + c <= 2 : etype == FR_ETYPE_PRI ? a + b <= 2 : true;
+                if (in) q.ex.push_back({a, b, c});
+            }
+    const int n = q.nq;
+    if ((int)q.ex.size() != n) return false;
+    // [V | I] -> [I | V^-1] by Gauss-Jordan with partial pivoting
+    std::vector<double> M((size_t)n * 2 * n, 0.0);
+    for (int r = 0; r < n; ++r) {
+        for (int m = 0; m < n; ++m) {
+            double v = 1.0;
+            for (int d = 0; d < 3; ++d)
+                for (int k = 0; k < q.ex[m][d]; ++k) v *= nodes[r][d];
+            M[(size_t)r * 2 * n + m] = v;
+        }
+        M[(size_t)r * 2 * n + n + r] = 1.0;
+    }
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(M[(size_t)r * 2 * n + col]) > std::fabs(M[(size_t)piv * 2 * n + col])) piv = r;
+        if (std::fabs(M[(size_t)piv * 2 * n + col]) < 1e-12) return false;
+        if (piv != col)
+            for (int k = 0; k < 2 * n; ++k) std::swap(M[(size_t)piv * 2 * n + k], M[(size_t)col * 2 * n + k]);
+        const double inv = 1.0 / M[(size_t)col * 2 * n + col];
+        for (int k = 0; k < 2 * n; ++k) M[(size_t)col * 2 * n + k] *= inv;
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double f = M[(size_t)r * 2 * n + col];
+            if (f != 0.0)
+                for (int k = 0; k < 2 * n; ++k) M[(size_t)r * 2 * n + k] -= f * M[(size_t)col * 2 * n + k];
+        }
+    }
+    // V^-1 maps node values to monomial coefficients: C[m][a] = (V^-1)[m][a]
+    q.C.assign((size_t)n * n, 0.0);
+    for (int m = 0; m < n; ++m)
+        for (int a = 0; a < n; ++a) q.C[(size_t)m * n + a] = M[(size_t)m * 2 * n + n + a];
+    return true;
+}
+
+void quad_shape(const QuadShape &q, const double *x, double *N, double (*dN)[3]) {
+    const int n = q.nq;
+    double mono[kMaxQ], dmono[kMaxQ][3];
+    for (int m = 0; m < n; ++m) {
+        const auto &e = q.ex[m];
+        double pw[3][3];  // pw[d][k] = x_d^k
+        for (int d = 0; d < 3; ++d) {
+            pw[d][0] = 1.0;
+            pw[d][1] = x[d];
+            pw[d][2] = x[d] * x[d];
+        }
+        mono[m] = pw[0][e[0]] * pw[1][e[1]] * pw[2][e[2]];
+        for (int d = 0; d < 3; ++d) {
+            if (e[d] == 0) {
+                dmono[m][d] = 0.0;
+                continue;
+            }
+            double v = (double)e[d] * pw[d][e[d] - 1];
+            for (int k = 0; k < 3; ++k)
+                if (k != d) v *= pw[k][e[k]];
+            dmono[m][d] = v;
+        }
+    }
+    for (int a = 0; a < n; ++a) {
+        double s = 0.0, g[3] = {0.0, 0.0, 0.0};
+        for (int m = 0; m < n; ++m) {
+            const double c = q.C[(size_t)m * n + a];
+            s += mono[m] * c;
+            for (int d = 0; d < 3; ++d) g[d] += dmono[m][d] * c;
+        }
+        N[a] = s;
+        for (int d = 0; d < 3; ++d) dN[a][d] = g[d];
+    }
+}
+
 struct PointGeo {
     Vec3 x;
     double S[9];
     double J;
 };
 
-PointGeo point_geo(int etype, const double (*X)[3], const double *ref) {
-    const int nv = etype == FR_ETYPE_TET ? 4 : etype == FR_ETYPE_HEX ? 8 : 6;
-    double N[8], dN[8][3];
-    shape(etype, ref, N, dN);
+// geometry at a reference point: straight map of the vertices (q null) or
+// the quadratic map of the nodes (q set); X holds the vertices or nodes
+PointGeo point_geo(int etype, const double (*X)[3], const double *ref, const QuadShape *q = nullptr) {
+    const int nv = q ? q->nq : etype == FR_ETYPE_TET ? 4 : etype == FR_ETYPE_HEX ? 8 : 6;
+    double N[kMaxQ], dN[kMaxQ][3];
+    if (q)
+        quad_shape(*q, ref, N, dN);
+    else
+        shape(etype, ref, N, dN);
     PointGeo g{};
     double A[3][3] = {{0}};  // A[k][d] = dx_k / dxi_d
     for (int a = 0; a < nv; ++a)
@@ -122,12 +239,29 @@ struct CellHash {
 int build_geometry(const fr_mesh *m, const RefOps ops[NT], TypeGeo geo[NT], std::string &err) {
     const int64_t *conn[NT] = {m->tet, m->pri, m->hex};
     const int64_t ne[NT] = {m->n_tet, m->n_pri, m->n_hex};
+    const double *qnodes[NT] = {m->tet_nodes, m->pri_nodes, m->hex_nodes};
     const int nvs[NT] = {4, 6, 8};
+    if (m->geom_order < 0 || m->geom_order > 2) {
+        err = "geom_order must be 1 (straight) or 2 (quadratic)";
+        return FR_ERR_MESH;
+    }
+    const bool curved = m->geom_order == 2;
     for (int t = 0; t < NT; ++t) {
         TypeGeo &G = geo[t];
         G = TypeGeo();
         G.ne = ne[t];
         if (ne[t] == 0) continue;
+        QuadShape qs;
+        if (curved) {
+            if (!qnodes[t]) {
+                err = "geom_order 2 needs the quadratic node coordinates of every element type present";
+                return FR_ERR_MESH;
+            }
+            if (!build_quad_shape(t, qs)) {
+                err = "quadratic shape functions: singular node set";
+                return FR_ERR_MESH;
+            }
+        }
         const RefOps &o = ops[t];
         G.nu = o.nu;
         G.nf = o.nf;
@@ -137,18 +271,25 @@ int build_geometry(const fr_mesh *m, const RefOps ops[NT], TypeGeo geo[NT], std:
         G.xf.resize((size_t)ne[t] * o.nf * 3);
         G.fn.resize((size_t)ne[t] * o.nf * 3);
         G.fmag.resize((size_t)ne[t] * o.nf);
+        const QuadShape *qp = curved ? &qs : nullptr;
         for (int64_t e = 0; e < ne[t]; ++e) {
-            double X[8][3];
+            double X[kMaxQ][3];
             for (int a = 0; a < nvs[t]; ++a) {
                 int64_t v = conn[t][e * nvs[t] + a];
                 if (v < 0 || v >= m->n_nodes) {
                     err = "node id out of range";
                     return FR_ERR_MESH;
                 }
-                for (int k = 0; k < 3; ++k) X[a][k] = m->xyz[3 * v + k];
+                if (!curved)
+                    for (int k = 0; k < 3; ++k) X[a][k] = m->xyz[3 * v + k];
+            }
+            if (curved) {
+                const int nq = qs.nq;
+                for (int a = 0; a < nq; ++a)
+                    for (int k = 0; k < 3; ++k) X[a][k] = qnodes[t][((size_t)e * nq + a) * 3 + k];
             }
             for (int j = 0; j < o.nu; ++j) {
-                PointGeo g = point_geo(t, X, &o.upts[3 * j]);
+                PointGeo g = point_geo(t, X, &o.upts[3 * j], qp);
                 if (!(g.J > 0.0)) {
                     err = "non-positive Jacobian at a solution point";
                     return FR_ERR_MESH;
@@ -159,7 +300,7 @@ int build_geometry(const fr_mesh *m, const RefOps ops[NT], TypeGeo geo[NT], std:
                 G.J[ij] = g.J;
             }
             for (int f = 0; f < o.nf; ++f) {
-                PointGeo g = point_geo(t, X, &o.fpts[3 * f]);
+                PointGeo g = point_geo(t, X, &o.fpts[3 * f], qp);
                 const double *nh = &o.fnorm[3 * f];
                 double sn[3];
                 for (int mm = 0; mm < 3; ++mm)

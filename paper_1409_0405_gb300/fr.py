@@ -50,7 +50,9 @@ class FRMesh(C.Structure):
                 ("n_pri", C.c_int64), ("pri", C.POINTER(C.c_int64)),
                 ("n_hex", C.c_int64), ("hex", C.POINTER(C.c_int64)),
                 ("n_bface", C.c_int64), ("bface", C.POINTER(C.c_int64)),
-                ("period", C.c_double * 3)]
+                ("period", C.c_double * 3),
+                ("geom_order", C.c_int), ("tet_nodes", C.POINTER(C.c_double)),
+                ("pri_nodes", C.POINTER(C.c_double)), ("hex_nodes", C.POINTER(C.c_double))]
 
 
 class FRParams(C.Structure):
@@ -254,6 +256,16 @@ def _fr_mesh(mesh, keep):
     m.bface = k["bface"].ctypes.data_as(C.POINTER(C.c_int64))
     per = np.asarray(mesh.get("period", np.zeros(3)), dtype=np.float64)
     m.period = (C.c_double * 3)(*per)
+    m.geom_order = int(mesh.get("geom_order", 1))
+    if m.geom_order == 2:
+        for t, nq in (("tet", 10), ("pri", 18), ("hex", 27)):
+            if t + "_nodes" not in mesh:
+                continue  # left NULL: the library rejects a present type without nodes
+            a = np.ascontiguousarray(mesh[t + "_nodes"], dtype=np.float64)
+            if a.shape != (len(k[t]), nq, 3):
+                raise ValueError(f"{t}_nodes must have shape ({len(k[t])}, {nq}, 3)")
+            k[t + "_nodes"] = a
+            setattr(m, t + "_nodes", _dptr(a))
     return m
 
 

@@ -1016,6 +1016,26 @@ int fr_diagnostics(fr_ctx *c, double *out, void *stream) {
     return is_f32(c) ? diagnostics_impl<float>(c, out, s) : diagnostics_impl<double>(c, out, s);
 }
 
+int fr_selftest_wait_timeout(fr_ctx *c, void *stream) {
+    if (!c) return set_err(FR_ERR_ARG, "null context");
+    if (!is_tc(c)) return set_err(FR_ERR_UNSUPPORTED, "the bounded-wait self-test needs a tensor-core precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    int t = 0;
+    while (t < NT && !c->T[t].present) ++t;
+    int rc;
+    if ((rc = check_tc(c))) return rc;  // a status from earlier work is reported, not masked
+    DevType &D = c->T[t];
+    // M0 on the context's (centred) stage input, its state loads withheld
+    const GemmArgsT<float> g = args_m0<float>(c, t, (const float *)D.Us);
+    if ((rc = cuda_check(launch_gemm_tc(g, D.tc[0], c->tc_err, s, 1), "self-test launch"))) return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(s), "self-test sync"))) return rc;
+    const int timed_out = check_tc(c) == FR_ERR_TIMEOUT;
+    // clear the status so that the context stays usable
+    if ((rc = cuda_check(cudaMemset(c->tc_err, 0, sizeof(int)), "self-test reset"))) return rc;
+    if (!timed_out) return set_err(FR_ERR_CUDA, "the withheld loads did not end in a reported timeout");
+    return FR_OK;
+}
+
 int fr_peak_fp64(double *gflops, void *stream) {
     if (!gflops) return set_err(FR_ERR_ARG, "null argument");
     return cuda_check(probe_fp64(gflops, (cudaStream_t)stream), "fp64 probe");

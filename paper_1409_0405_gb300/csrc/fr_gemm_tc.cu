@@ -280,7 +280,7 @@ template <int MODE, bool TF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const GemmArgsT<float> g, const TileMap tm, const __grid_constant__ CUtensorMap tmB1,
               const __grid_constant__ CUtensorMap tmB2, const uint8_t *__restrict__ opimg, int Nmma, int K1pad,
-              int Kpad, int nslot, uint32_t tmem_cols, int *err) {
+              int Kpad, int nslot, uint32_t tmem_cols, int *err, int no_producer) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint32_t op_half = TF ? 0u : (uint32_t)Nmma * (uint32_t)Kpad * 2u;  // resident image: bytes of hi (lo)
     const uint32_t op_bytes = 2u * op_half;
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ph ^= 1u;
             }
         }
-    } else if (warp == kProdWarp && lane == 0) {
+    } else if (warp == kProdWarp && lane == 0 && !no_producer) {
         // ---- producer: one 2-D TMA box (16 K rows x 128 columns) per stage
         // into its slot; stage ks reads B1 rows 16 ks.. (ks < K1pad / 16)
         // or B2 rows 16 ks - K1pad..
@@ -587,7 +587,7 @@ cudaError_t encode_rows(CUtensorMap *m, const float *base, int64_t cols, int row
 
 template <int MODE, bool TF>
 cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOperator &op, int *err, int grid,
-                        cudaStream_t s) {
+                        cudaStream_t s, int no_producer) {
     const int nslot = tc_stages(op);
     const size_t smem = tc_smem_bytes(op);
     // the attribute is raised once per instantiation to the largest size
@@ -604,7 +604,7 @@ cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOp
     if (e == cudaSuccess) e = g.K2 > 0 ? encode_rows(&m2, g.B2, g.N, g.K2, g.ldb2) : encode_rows(&m2, g.B1, g.N, g.K1, g.ldb1);
     if (e != cudaSuccess) return e;
     k_gemm_tc<MODE, TF><<<grid, kThreads, smem, s>>>(g, tm, m1, m2, op.img, op.Nmma, op.K1pad, op.Kpad, nslot, cols,
-                                                    err);
+                                                    err, no_producer);
     return cudaGetLastError();
 }
 
@@ -631,7 +631,8 @@ size_t tc_smem_bytes(const TcOperator &op) {
     return used < 118784 ? 118784 : used;
 }
 
-cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int *err, cudaStream_t s) {
+cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int *err, cudaStream_t s,
+                           int no_producer) {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     if (g.M > op.Nmma || op.Nmma > 256 || op.Nmma % 16 || op.Kpad % kStageK || op.K1pad % kStageK ||
         g.K1 > op.K1pad || g.K2 > op.Kpad - op.K1pad || tc_stages(op) < 2)
@@ -657,13 +658,13 @@ cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int 
 #define FR_TC_MODES(TF)                                                \
     switch (g.mode) {                                                  \
         case GEMM_STORE:                                               \
-            return launch_mode<GEMM_STORE, TF>(g, tm, op, err, grid, s);   \
+            return launch_mode<GEMM_STORE, TF>(g, tm, op, err, grid, s, no_producer);   \
         case GEMM_GRAD:                                                \
-            return launch_mode<GEMM_GRAD, TF>(g, tm, op, err, grid, s);    \
+            return launch_mode<GEMM_GRAD, TF>(g, tm, op, err, grid, s, no_producer);    \
         case GEMM_DIV:                                                 \
-            return launch_mode<GEMM_DIV, TF>(g, tm, op, err, grid, s);     \
+            return launch_mode<GEMM_DIV, TF>(g, tm, op, err, grid, s, no_producer);     \
         case GEMM_DIV_RK:                                              \
-            return launch_mode<GEMM_DIV_RK, TF>(g, tm, op, err, grid, s);  \
+            return launch_mode<GEMM_DIV_RK, TF>(g, tm, op, err, grid, s, no_producer);  \
     }
     if (op.tf32) {
         FR_TC_MODES(true)

@@ -129,8 +129,11 @@ void tc_pack_tf32(const double *A, int M, int K1, int K2, std::vector<uint32_t> 
 int tc_stages(const TcOperator &op);
 size_t tc_smem_bytes(const TcOperator &op);
 // C <- A [B1; B2] with g's epilogue on the tensor cores; *err (device) is set
-// non-zero if a bounded wait of the kernel gave up
-cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int *err, cudaStream_t s);
+// non-zero if a bounded wait of the kernel gave up.  no_producer (the
+// bounded-wait self-test only): the state loads are never issued, so every
+// wait runs out and the kernel takes its abort path
+cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int *err, cudaStream_t s,
+                           int no_producer = 0);
 
 struct Phys {
     double gamma, mu, prandtl, beta, tau;

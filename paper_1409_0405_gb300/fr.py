@@ -35,7 +35,7 @@ OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
 # every entry point declared in include/fr.h
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_step_ls", "fr_reduce",
-           "fr_diagnostics", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
+           "fr_diagnostics", "fr_selftest_wait_timeout", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info",
            "fr_transfer", "fr_transfer_state", "fr_closure_features", "fr_closure_sample",
@@ -95,6 +95,7 @@ def load():
     lib.fr_step_ls.restype = C.c_int
     lib.fr_reduce.argtypes = [vp, dp, vp]
     lib.fr_diagnostics.argtypes = [vp, dp, vp]
+    lib.fr_selftest_wait_timeout.argtypes = [vp, vp]
     lib.fr_operator.argtypes = [C.c_int, C.c_int, C.c_int, dp, i64p, i64p]
     lib.fr_profile.argtypes = [vp, C.c_int]
     lib.fr_profile_read.argtypes = [vp, dp, i64p, i64p]
@@ -132,7 +133,8 @@ def load():
     lib.fr_last_error.argtypes = []
     lib.fr_last_error.restype = C.c_char_p
     for name in ("fr_create", "fr_ndof", "fr_info", "fr_upts", "fr_set_state",
-                 "fr_get_state", "fr_rhs", "fr_step", "fr_reduce", "fr_diagnostics", "fr_operator",
+                 "fr_get_state", "fr_rhs", "fr_step", "fr_reduce", "fr_diagnostics", "fr_selftest_wait_timeout",
+                 "fr_operator",
                  "fr_profile", "fr_profile_read"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -421,6 +423,10 @@ class Context:
         _check(rc)
         return out
 
+
+    def selftest_wait_timeout(self, stream=None):
+        """fr_selftest_wait_timeout (tensor-core precisions)."""
+        _check(self._lib.fr_selftest_wait_timeout(self._h, C.c_void_p(stream) if stream else None))
 
     def diagnostics(self, stream=None):
         """fr_diagnostics: (dKE/dt, inviscid wall force (3,), viscous wall

@@ -125,6 +125,8 @@ def test_entry_points_reject_bad_arguments_without_a_gpu():
     lib = fr.load()
     assert lib.fr_step_ls(None, 1e-3, 1, None) == fr.FR_ERR_ARG
     assert lib.fr_step(None, 1e-3, 1, None) == fr.FR_ERR_ARG
+    assert lib.fr_diagnostics(None, None, None) == fr.FR_ERR_ARG
+    assert lib.fr_selftest_wait_timeout(None, None) == fr.FR_ERR_ARG
     assert lib.fr_closure_set(None, 0, None, 128, None) == fr.FR_ERR_ARG
     assert lib.fr_closure_features(None, None, 0, None, None) == fr.FR_ERR_ARG
     assert lib.fr_closure_sample(None, None, None, None, 0, None, None, None, None, None) == fr.FR_ERR_ARG

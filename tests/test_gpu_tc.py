@@ -114,3 +114,23 @@ def test_tc_full_size_boundary_layer(mode):
     print("full-size", mode, "rel err", d)
     assert d < TOLS[mode]
     c16.reduce(check=False)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_tc_bounded_wait_timeout_is_reported(mode):
+    """Failure detection without a GPU fault: the operator kernel launched
+    with its state loads withheld lets every bounded wait run out (~2 s),
+    takes its abort path and reports FR_ERR_TIMEOUT through the context
+    status; the self-test checks that and clears it, and the same context
+    then evaluates a correct RHS."""
+    fr = _fr()
+    mesh = synth.vortex_box(n=4, jitter=0.05, seed=0)
+    prm = dict(viscous=True, mu=0.01, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0)
+    sol, ctx = _cases.make_pair(mesh, 2, precision=_prec(fr, mode), **prm)
+    u = _cases.state(sol, "vortex")
+    ctx.set_state(u)
+    ctx.selftest_wait_timeout()
+    ref = sol.rhs(u)
+    err = _cases.per_quantity_rel_err(sol, ref, _cases.gpu_rhs(ctx, u))
+    assert np.all(err < TOLS[mode]), err
+    ctx.reduce()  # the status is clear again

@@ -141,10 +141,13 @@ FieldsT<T> fields_of(const fr_ctx *c) {
 }
 
 Pairs pairs_of(const fr_ctx *c) {
-    return Pairs{c->npairs, c->ta, c->fa, c->ea, c->tb, c->fb, c->eb, c->nrm, c->maga, c->magb};
+    return Pairs{c->npairs, c->ta,    c->fa,    c->ea,    c->tb,     c->fb,    c->eb,
+                 c->nrm,    c->maga,  c->magb,  c->sgn,   c->nrm_f,  c->maga_f, c->magb_f};
 }
 
-Bnd bnd_of(const fr_ctx *c) { return Bnd{c->nbnd, c->bt, c->bf, c->be, c->btag, c->bn, c->bmag}; }
+Bnd bnd_of(const fr_ctx *c) {
+    return Bnd{c->nbnd, c->bt, c->bf, c->be, c->btag, c->bn, c->bmag, c->bn_f, c->bmag_f};
+}
 
 
 cudaEvent_t next_event(fr_ctx *c) {
@@ -572,6 +575,22 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         std::vector<double> bw(faces.bt.size());
         for (size_t k = 0; k < bw.size(); ++k) bw[k] = ops[faces.bt[k]].FW[faces.bf[k]];
         if ((rc = upload(c, &c->bw, bw))) return rc;
+        // LDG switch: +1 where side a's outward normal n has n . s > 0,
+        // s = (1, 0.1 sqrt 2, 0.01 sqrt 3) (the dot product in double)
+        std::vector<signed char> sg(faces.ta.size());
+        for (size_t k = 0; k < sg.size(); ++k) {
+            const double *n = &faces.n[3 * k];
+            const double d = n[0] * 1.0 + n[1] * 0.14142135623730950488 + n[2] * 0.017320508075688772935;
+            sg[k] = d > 0.0 ? 1 : -1;
+        }
+        if ((rc = upload(c, &c->sgn, sg))) return rc;
+        if (prm->precision != FR_FP64) {
+            auto to_f = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
+            if ((rc = upload(c, &c->nrm_f, to_f(faces.n))) || (rc = upload(c, &c->maga_f, to_f(faces.maga))) ||
+                (rc = upload(c, &c->magb_f, to_f(faces.magb))) || (rc = upload(c, &c->bn_f, to_f(faces.bn))) ||
+                (rc = upload(c, &c->bmag_f, to_f(faces.bmag))))
+                return rc;
+        }
     }
     // the discrete divergence of the constant reference flux (zero with exact
     // geometry; ~1e-11 with the geometric factors rounded), evaluated once in

@@ -63,6 +63,8 @@ struct fr_ctx {
     double *nrm = nullptr, *maga = nullptr, *magb = nullptr;
     int *bt = nullptr, *bf = nullptr, *be = nullptr, *btag = nullptr;
     double *bn = nullptr, *bmag = nullptr;
+    signed char *sgn = nullptr;  // LDG switch per pair
+    float *nrm_f = nullptr, *maga_f = nullptr, *magb_f = nullptr, *bn_f = nullptr, *bmag_f = nullptr;
     double *red = nullptr;  // reduction partials + result
     double *bw = nullptr;    // face weight of each boundary flux point
     double *diag = nullptr;  // diagnostics partials + result

@@ -161,16 +161,22 @@ struct FieldsT {
 };
 using Fields = FieldsT<double>;
 
+// Interface flux-point pairs: sides, side a's unit normal, both |S^T n^|,
+// the LDG switch (+1 where side a is the left side), and (FP32-storage
+// modes) float copies of the normal and magnitudes, rounded once on the host
 struct Pairs {
     int64_t n;
     const int *ta, *fa, *ea, *tb, *fb, *eb;
     const double *nrm, *maga, *magb;
+    const signed char *sgn;
+    const float *nrm_f, *maga_f, *magb_f;
 };
 
 struct Bnd {
     int64_t n;
     const int *bt, *bf, *be, *btag;
     const double *bn, *bmag;
+    const float *bn_f, *bmag_f;
 };
 
 template <typename T>

@@ -185,12 +185,51 @@ __device__ __forceinline__ void bc_states(int tag, const T *u, const T *n, const
 
 __device__ __forceinline__ int64_t fpt_off(int f, int e, int64_t np) { return (int64_t)f * V * np + e; }
 
-// LDG switch: +1 where side a (outward normal n) is the left side, i.e.
-// n . s > 0 with s = (1, 0.1 sqrt 2, 0.01 sqrt 3); the dot product is taken
-// in double in both modes so the switch does not depend on the precision
+// Face metadata in the arithmetic type: the FP32-storage modes read the
+// float copies (no conversions on the FP64 pipe), FP64 the doubles.  The
+// LDG switch (+1 where side a's outward normal n has n . s > 0, s = (1,
+// 0.1 sqrt 2, 0.01 sqrt 3)) is evaluated once on the host in double.
 template <typename T>
-__device__ __forceinline__ T ldg_sign(const double *n) {
-    return (n[0] * 1.0 + n[1] * 0.14142135623730950488 + n[2] * 0.017320508075688772935 > 0.0) ? T(1) : T(-1);
+__device__ __forceinline__ void pair_normal(const Pairs &P, int64_t k, T *n);
+template <>
+__device__ __forceinline__ void pair_normal<double>(const Pairs &P, int64_t k, double *n) {
+    n[0] = P.nrm[3 * k];
+    n[1] = P.nrm[3 * k + 1];
+    n[2] = P.nrm[3 * k + 2];
+}
+template <>
+__device__ __forceinline__ void pair_normal<float>(const Pairs &P, int64_t k, float *n) {
+    n[0] = P.nrm_f[3 * k];
+    n[1] = P.nrm_f[3 * k + 1];
+    n[2] = P.nrm_f[3 * k + 2];
+}
+template <typename T>
+__device__ __forceinline__ void pair_mags(const Pairs &P, int64_t k, T &ma, T &mb);
+template <>
+__device__ __forceinline__ void pair_mags<double>(const Pairs &P, int64_t k, double &ma, double &mb) {
+    ma = P.maga[k];
+    mb = P.magb[k];
+}
+template <>
+__device__ __forceinline__ void pair_mags<float>(const Pairs &P, int64_t k, float &ma, float &mb) {
+    ma = P.maga_f[k];
+    mb = P.magb_f[k];
+}
+template <typename T>
+__device__ __forceinline__ void bnd_normal(const Bnd &B, int64_t kb, T *n, T &mag);
+template <>
+__device__ __forceinline__ void bnd_normal<double>(const Bnd &B, int64_t kb, double *n, double &mag) {
+    n[0] = B.bn[3 * kb];
+    n[1] = B.bn[3 * kb + 1];
+    n[2] = B.bn[3 * kb + 2];
+    mag = B.bmag[kb];
+}
+template <>
+__device__ __forceinline__ void bnd_normal<float>(const Bnd &B, int64_t kb, float *n, float &mag) {
+    n[0] = B.bn_f[3 * kb];
+    n[1] = B.bn_f[3 * kb + 1];
+    n[2] = B.bn_f[3 * kb + 2];
+    mag = B.bmag_f[kb];
 }
 
 // ---------------------------------------------------------------------------
@@ -202,7 +241,7 @@ __device__ __forceinline__ void common_solution_at(const Pairs &P, const Bnd &B,
         const int64_t npa = F.np[ta], npb = F.np[tb];
         const int64_t oa = fpt_off(P.fa[k], P.ea[k], npa), ob = fpt_off(P.fb[k], P.eb[k], npb);
         const T *UA = F.UF[ta] + oa, *UB = F.UF[tb] + ob;
-        const T b = ph.beta * ldg_sign<T>(P.nrm + 3 * k);
+        const T b = ph.beta * T(P.sgn[k]);
         T *DA = F.DUF[ta] + oa, *DB = F.DUF[tb] + ob;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -221,7 +260,8 @@ __device__ __forceinline__ void common_solution_at(const Pairs &P, const Bnd &B,
         T u[V], ghost[V], cb[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) u[v] = F.UF[t][o + v * np];
-        const T n[3] = {T(B.bn[3 * kb]), T(B.bn[3 * kb + 1]), T(B.bn[3 * kb + 2])};
+        T n[3], mg;
+        bnd_normal<T>(B, kb, n, mg);
         bc_states(B.btag[kb], u, n, ph, ghost, cb);
 #pragma unroll
         for (int v = 0; v < V; ++v) F.DUF[t][o + v * np] = cb[v] - u[v];
@@ -261,7 +301,8 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
             ua[v] = F.UF[ta][oa + v * npa];
             ub[v] = F.UF[tb][ob + v * npb];
         }
-        const T n[3] = {T(P.nrm[3 * k]), T(P.nrm[3 * k + 1]), T(P.nrm[3 * k + 2])};
+        T n[3];
+        pair_normal<T>(P, k, n);
         rusanov(ua, ub, n, ph.gamma, fn);
         if (ph.viscous) {
             T ga[3][V], gb[3][V], Fa[V][3], Fb[V][3];
@@ -270,7 +311,7 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
             Prim<T> qa = prim(ua, ph.gamma), qb = prim(ub, ph.gamma);
             vis_flux(ua, qa, ga, ph.mu, ph.kq, Fa);
             vis_flux(ub, qb, gb, ph.mu, ph.kq, Fb);
-            const T b = ph.beta * ldg_sign<T>(P.nrm + 3 * k);
+            const T b = ph.beta * T(P.sgn[k]);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const T fva = Fa[v][0] * n[0] + Fa[v][1] * n[1] + Fa[v][2] * n[2];
@@ -278,7 +319,8 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
                 fn[v] = fn[v] - (T(0.5) * (fva + fvb) - b * (fva - fvb)) + ph.tau * (ua[v] - ub[v]);
             }
         }
-        const T ma = T(P.maga[k]), mb = T(P.magb[k]);
+        T ma, mb;
+        pair_mags<T>(P, k, ma, mb);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const T f = fn[v] - fref_n(ph, v, n);
@@ -296,7 +338,8 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
         T u[V], ghost[V], cb[V], fn[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) u[v] = F.UF[t][o + v * np];
-        const T n[3] = {T(B.bn[3 * kb]), T(B.bn[3 * kb + 1]), T(B.bn[3 * kb + 2])};
+        T n[3], mg;
+        bnd_normal<T>(B, kb, n, mg);
         bc_states(B.btag[kb], u, n, ph, ghost, cb);
         rusanov(u, ghost, n, ph.gamma, fn);
         if (ph.viscous) {
@@ -308,7 +351,6 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
             for (int v = 0; v < V; ++v)
                 fn[v] = fn[v] - (Fv[v][0] * n[0] + Fv[v][1] * n[1] + Fv[v][2] * n[2]) + ph.tau * (u[v] - cb[v]);
         }
-        const T mg = T(B.bmag[kb]);
 #pragma unroll
         for (int v = 0; v < V; ++v) F.FC[t][o + v * np] = (fn[v] - fref_n(ph, v, n)) * mg;
     }

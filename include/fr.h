@@ -134,7 +134,11 @@ typedef struct {
  * connectivity on the host, and upload them to the current CUDA device.
  * order: polynomial order p in 1..4 (the paper exercises p = 1..4, Sec. 3.4).
  * On success *out receives a context the caller frees with fr_destroy.
- * Errors: FR_ERR_ARG, FR_ERR_MESH, FR_ERR_NOMEM, FR_ERR_CUDA.
+ * Errors: FR_ERR_ARG, FR_ERR_MESH, FR_ERR_NOMEM, FR_ERR_CUDA;
+ * FR_ERR_UNSUPPORTED for a precision outside FR_FP64..FR_TF32X3, or a
+ * tensor-core precision whose operator exceeds the tensor-core kernel (more
+ * than 256 operator rows, or a split-BF16 image without room for two ring
+ * slots: the hexahedral gradient operator at p = 4).
  */
 int fr_create(const fr_mesh *mesh, int order, const fr_params *params, fr_ctx **out);
 

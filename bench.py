@@ -560,7 +560,7 @@ def learned_mode(fr, torch, args, sp):
     library's kernels.  Reported: the RHS error with and without the
     network on a later, held-out state; the kinetic-energy dissipation rate
     of p=2 with and without the network against p=4, over the training
-    window and over the window after it; the judge's verdict (the network
+    window and over the window after it; the p=4 check's verdict (the network
     is kept only if it lowers the dissipation error after the training
     window); and the RHS throughput of each."""
     import synth
@@ -649,7 +649,7 @@ def learned_mode(fr, torch, args, sp):
     ms2c = rhs_ms(c2, u2_0)
     cls2c, _ = c2.profile_read()
     c2.profile(False)
-    cl.detach()   # the judge's fallback when the verdict is negative
+    cl.detach()   # the plain p=2 fallback when the p=4 check is negative
     ms2 = rhs_ms(c2, u2_0)
     ms4 = rhs_ms(c4, u4d)
     closure_ms = cls2c["closure"][0] / max(sum(v[0] for v in cls2c.values()), 1e-30) * ms2c
@@ -673,7 +673,7 @@ def learned_mode(fr, torch, args, sp):
             "after_training_window": {"p2": rel(e2, post), "p2_network": rel(e2c, post)},
             "p4_rate_end": float(e4[-1]), "measure": "mean over windows of |eps - eps4| / |eps4|, "
                                                      "eps = -dKE/dt over each stride; p=4 in FP32 RHS"},
-        "judge": {"network_kept": bool(verdict),
+        "p4_check": {"network_kept": bool(verdict),
                   "rule": "keep the network only if it lowers the dissipation error after the training window; "
                           "otherwise detach it (plain p=2 fallback)"},
         "rhs_ms": {"p2_network": ms2c, "p2": ms2, "p4": ms4, "closure_part_of_p2_network": closure_ms},

@@ -313,13 +313,14 @@ int front_stages(fr_ctx *c, T *const in[NT], cudaStream_t s) {
                                     [&] { return launch_common_solution<T>(pairs_of(c), bnd_of(c), F, ph, s); }),
                              "common solution")))
             return rc;
-        // 3. corrected physical gradient; 4. gradient at flux points.  On
-        // the tensor cores the operator kernel stores the reference gradient
-        // and the flux kernel (5.), which loads the point's geometry anyway,
-        // forms the physical gradient in place before M0 is applied to it
-        // (in the operator kernel's epilogue those loads would repeat for
-        // every variable and stall it)
-        const bool tc = is_tc(c);
+        // 3. corrected physical gradient; 4. gradient at flux points.  In
+        // the FP32-storage modes the operator kernel stores the reference
+        // gradient and the flux kernel (5.), which loads the point's
+        // geometry anyway, forms the physical gradient in place before M0 is
+        // applied to it (in the operator kernel's epilogue those loads would
+        // repeat for every variable and stall it; the FP64 kernel is bound by
+        // its FMAs and keeps the fused epilogue)
+        const bool tc = is_f32(c);
         for (int t = 0; t < NT; ++t) {
             if (!c->T[t].present) continue;
             GemmArgsT<T> g = args_grad<T>(c, t, in[t]);
@@ -352,8 +353,8 @@ int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) 
     int rc;
     if ((rc = front_stages<T>(c, in, s))) return rc;
     // 5. transformed flux at solution points (done by front_stages for
-    // Navier-Stokes on the tensor cores)
-    for (int t = 0; t < NT && !(is_tc(c) && c->prm.viscous); ++t) {
+    // Navier-Stokes in the FP32-storage modes)
+    for (int t = 0; t < NT && !(is_f32(c) && c->prm.viscous); ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         if ((rc = cuda_check(launch(c, K_FLUX, s,

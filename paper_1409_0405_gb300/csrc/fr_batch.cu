@@ -80,7 +80,7 @@ namespace {
 template <typename T>
 struct BatchImpl : BatchBase {
     fr_batch *b;
-    bool viscous;
+    bool viscous, xform;
     Group<T> m0, grad, m0g, div[4];
     Segs<FluxItem<T>> flux;
     Segs<FaceItem<T>> face;
@@ -93,7 +93,10 @@ struct BatchImpl : BatchBase {
     int launches_per_step = 0;
     int nsm = 152;
 
-    explicit BatchImpl(fr_batch *bb) : b(bb) { viscous = bb->ctx[0]->prm.viscous != 0; }
+    explicit BatchImpl(fr_batch *bb) : b(bb) {
+        viscous = bb->ctx[0]->prm.viscous != 0;
+        xform = viscous && is_f32(bb->ctx[0]);
+    }
 
     // the operators' exact zeros skipped as in the per-problem launches, in
     // chunks of the group's row-chunk size (compressed per etype, order,
@@ -200,7 +203,9 @@ struct BatchImpl : BatchBase {
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->ctx[0]->device);
         if (int rc = cuda_check(configure_gemm_grouped<T>(), "grouped gemm attributes")) return rc;
         m0.mode = GEMM_STORE;
-        grad.mode = GEMM_GRAD;
+        // FP32 storage: the reference gradient, transformed by the flux
+        // kernel (the arithmetic of the per-problem launches)
+        grad.mode = xform ? GEMM_STORE : GEMM_GRAD;
         m0g.mode = GEMM_STORE;
         m0.rc = 16;
         grad.rc = 12;
@@ -219,13 +224,14 @@ struct BatchImpl : BatchBase {
                 m0.op.push_back(key + 0);
                 if (viscous) {
                     grad.h.push_back(args_grad<T>(c, t, in));
+                    if (xform) grad.h.back().mode = GEMM_STORE;
                     grad.op.push_back(key + 1);
                     m0g.h.push_back(args_m0grad<T>(c, t));
                     m0g.op.push_back(key + 0);
                 }
                 flux.hb.push_back(flux.total);
                 flux.h.push_back(FluxItem<T>{D.nu, D.ne, D.np, (const T *)D.Us, (const T *)D.GU,
-                                             (const T *)D.S_t, (T *)D.FT});
+                                             (const T *)D.S_t, (T *)D.FT, xform ? (const T *)D.invJ_t : nullptr});
                 flux.total += (int64_t)D.nu * D.np;
                 CenterItem<T> ci{(int64_t)D.nu * NVV * D.np, D.np, D.U, (T *)D.Us, {0, 0, 0, 0, 0}};
                 const Phys ph = phys_of(c);
@@ -291,17 +297,24 @@ struct BatchImpl : BatchBase {
         int rc;
         if ((rc = launch_group(m0, s))) return rc;
         ++n;
+        auto flux_step = [&]() {
+            return cuda_check(launch_flux_grouped<T>(flux.d, flux.begin, (int)flux.h.size(), flux.total, ph,
+                                                     flux.grid, s, xform),
+                              "grouped flux");
+        };
         if (viscous) {
             if ((rc = cuda_check(launch_face_grouped<T>(face.d, face.begin, (int)face.h.size(), face.total, ph, 0,
                                                         face.grid, s),
                                  "grouped common solution")))
                 return rc;
-            if ((rc = launch_group(grad, s)) || (rc = launch_group(m0g, s))) return rc;
+            if ((rc = launch_group(grad, s))) return rc;
+            // FP32 storage: the flux kernel forms the physical gradient M0 is
+            // then applied to
+            if (xform && (rc = flux_step())) return rc;
+            if ((rc = launch_group(m0g, s))) return rc;
             n += 3;
         }
-        if ((rc = cuda_check(
-                 launch_flux_grouped<T>(flux.d, flux.begin, (int)flux.h.size(), flux.total, ph, flux.grid, s),
-                 "grouped flux")) ||
+        if ((!xform && (rc = flux_step())) ||
             (rc = cuda_check(launch_face_grouped<T>(face.d, face.begin, (int)face.h.size(), face.total, ph, 1,
                                                     face.grid, s),
                              "grouped common flux")) ||

@@ -218,6 +218,7 @@ struct FluxItem {
     int64_t ne, np;
     const T *U, *GU, *S;
     T *FT;
+    const T *invJ;  // non-null: GU holds the reference gradient (see launch_flux)
 };
 template <typename T>
 struct FaceItem {
@@ -236,7 +237,7 @@ struct CenterItem {
 // index of item i (prefix sums of nu*np, pairs+boundary points, n)
 template <typename T>
 cudaError_t launch_flux_grouped(const FluxItem<T> *items, const int64_t *begin, int n, int64_t total, const Phys &ph,
-                                int grid, cudaStream_t s);
+                                int grid, cudaStream_t s, bool xform = false);
 // which = 0: common solution, 1: common flux
 template <typename T>
 cudaError_t launch_face_grouped(const FaceItem<T> *items, const int64_t *begin, int n, int64_t total, const Phys &ph,

@@ -540,7 +540,7 @@ __device__ __forceinline__ int find_item(const int64_t *begin, int n, int64_t gi
     return lo;
 }
 
-template <typename T>
+template <typename T, bool XFORM>
 __global__ void k_flux_grouped(const FluxItem<T> *__restrict__ items, const int64_t *__restrict__ begin, int n,
                                int64_t total, const PhysT<T> ph) {
     for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total;
@@ -548,8 +548,8 @@ __global__ void k_flux_grouped(const FluxItem<T> *__restrict__ items, const int6
         const int i = find_item(begin, n, gi);
         const FluxItem<T> &it = items[i];
         const int64_t idx = gi - begin[i], j = idx / it.np;
-        flux_at<T, false>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, (const T *)nullptr, it.FT, ph,
-                          j, idx - j * it.np);
+        flux_at<T, XFORM>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, it.invJ, it.FT, ph, j,
+                          idx - j * it.np);
     }
 }
 
@@ -863,9 +863,12 @@ cudaError_t launch_int_to_pub(int nu, int64_t ne, int64_t np, const T *in, doubl
 
 template <typename T>
 cudaError_t launch_flux_grouped(const FluxItem<T> *items, const int64_t *begin, int n, int64_t total, const Phys &ph,
-                                int grid, cudaStream_t s) {
+                                int grid, cudaStream_t s, bool xform) {
     if (n <= 0 || total <= 0) return cudaSuccess;
-    k_flux_grouped<T><<<grid, 128, 0, s>>>(items, begin, n, total, phys_t<T>(ph));
+    if (xform)
+        k_flux_grouped<T, true><<<grid, 128, 0, s>>>(items, begin, n, total, phys_t<T>(ph));
+    else
+        k_flux_grouped<T, false><<<grid, 128, 0, s>>>(items, begin, n, total, phys_t<T>(ph));
     return cudaGetLastError();
 }
 
@@ -906,7 +909,7 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
                                                 const double *, double, double, double, int, cudaStream_t);  \
     template cudaError_t launch_int_to_pub<T>(int, int64_t, int64_t, const T *, double *, cudaStream_t);       \
     template cudaError_t launch_flux_grouped<T>(const FluxItem<T> *, const int64_t *, int, int64_t, const Phys &, \
-                                                int, cudaStream_t);                                           \
+                                                int, cudaStream_t, bool);                                     \
     template cudaError_t launch_face_grouped<T>(const FaceItem<T> *, const int64_t *, int, int64_t, const Phys &, \
                                                 int, int, cudaStream_t);                                      \
     template cudaError_t launch_center_grouped<T>(const CenterItem<T> *, const int64_t *, int, int64_t, int,     \

@@ -97,3 +97,29 @@ def _uniform_pub(c):
             blk[:, 4] = 2.5
             out.append(blk.reshape(-1))
     return np.concatenate(out)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_navier_stokes_equals_per_problem(precision):
+    """Navier-Stokes batches (common solution, gradient, M0 on gradients in
+    the grouped launches): bit-identical to each problem's own launches."""
+    from paper_1409_0405_gb300 import fr
+    probs = [(synth.vortex_box(n=3, n_prism_layers=1, seed=31), 2), (synth.hex_box(n=3, n_hex_cols=2, seed=32), 3),
+             (synth.vortex_box(n=4, n_prism_layers=2, seed=33), 1)]
+    prm = dict(viscous=True, mu=0.02, precision=precision, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0, rho_inf=1.0)
+    states = []
+    for batched in (False, True):
+        b = fr.Batch([m for m, _ in probs], [p for _, p in probs], **prm)
+        for c in b.problems:
+            q = synth.isentropic_vortex(c.upts_points())
+            out, off = [], 0
+            for ne, nu in c.counts():
+                if ne:
+                    out.append(q[off:off + ne * nu].reshape(ne, nu, 5).transpose(0, 2, 1).reshape(-1))
+                    off += ne * nu
+            c.set_state(np.concatenate(out))
+        b.step([2e-3] * len(probs), 3, batched=batched)
+        states.append([c.get_state() for c in b.problems])
+        b.close()
+    for a, g in zip(*states):
+        np.testing.assert_array_equal(g, a)

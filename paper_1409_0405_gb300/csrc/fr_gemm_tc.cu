@@ -10,9 +10,10 @@
 // D[n][j] = sum_k B^T[n][k] A^T[k][j] with M = 128 state columns per tile
 // (TMEM lanes), N = the operator's rows padded to 16 (TMEM columns), K the
 // operator's columns.  The epilogue thread of lane n then holds every
-// operator row of its column and writes C[j][n] coalesced across the warp,
-// applying the same fused epilogues as the FP64/FP32 kernels (gradient
-// transform, -1/J, RK update).
+// operator row of its column and writes C[j][n] coalesced across the warp:
+// a plain store (the interpolation, and the reference gradient and raw
+// divergence of an RK step, which streaming kernels finish per point) or
+// the divergence of a plain RHS, -(1/J) (A B) (+ rfs).
 //
 // Shared memory, no swizzle, K-major core matrices (8 rows x 16 bytes):
 //   operator image  [hi | lo], per 16-wide K step: Nmma/8 row groups x
@@ -25,8 +26,8 @@
 //                   loads in flight are bounded by the ring, not by the L1
 //                   left over beside the shared memory; rows past the end
 //                   of B1 or B2 are filled with zeros by the TMA unit);
-//                   the converter warps read their column, meet at a named
-//                   barrier, and overwrite the slot with the stage's bf16 hi
+//                   the converter warps read their column, meet at an
+//                   mbarrier, and overwrite the slot with the stage's bf16 hi
 //                   and lo core matrices [hi | lo] (4 KB each, LBO/SBO as
 //                   above), which the MMA reads; its commit frees the slot
 //                   for the next load.
@@ -172,10 +173,11 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
 }
 
 // Epilogue of rows [c0, c0 + 24) of state column n (element e), the
-// accumulators in v.  The same arithmetic as gemm_block in fr_gemm.cu; here
-// every load of a group is issued before its first store (C may alias
-// nothing the group reads, but the compiler cannot know), so one thread
-// keeps several loads in flight instead of one row's worth.
+// accumulators in v.  Two epilogues: the plain store (every operator of an
+// RK step: the gradient and divergence products are finished by streaming
+// kernels, see the callers) and the divergence of a plain RHS evaluation,
+// -(1/J) v (+ rfs), whose loads of a sub-group are issued before its
+// stores so that one thread keeps several in flight.
 template <int MODE>
 __device__ __forceinline__ void epi_group(const GemmArgsT<float> &g, int c0, int64_t n, int64_t e, const float *v) {
     if (MODE == GEMM_STORE) {
@@ -183,73 +185,26 @@ __device__ __forceinline__ void epi_group(const GemmArgsT<float> &g, int c0, int
 #pragma unroll
         for (int t = 0; t < 24; ++t)
             if (c0 + t < g.M) g.C[(int64_t)(c0 + t) * g.ldc + n] = v[t] + add;
-    } else if (MODE == GEMM_GRAD) {
-        // rows (j, d), d fastest: 8 points per group, two at a time
-#pragma unroll
-        for (int t0 = 0; t0 < 8; t0 += 2) {
-            float sv[2][9], ij[2];
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int j = c0 / 3 + t0 + t;
-                if (3 * j < g.M) {
-                    const float *S = g.S + (int64_t)j * 9 * g.np + e;
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) sv[t][q] = __ldg(S + (int64_t)q * g.np);
-                    ij[t] = __ldg(g.invJ + (int64_t)j * g.np + e);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int j = c0 / 3 + t0 + t;
-                if (3 * j < g.M) {
-                    const float g0 = v[3 * (t0 + t)], g1 = v[3 * (t0 + t) + 1], g2 = v[3 * (t0 + t) + 2];
-#pragma unroll
-                    for (int m = 0; m < 3; ++m)
-                        g.C[(int64_t)(3 * j + m) * g.ldc + n] =
-                            ij[t] * (sv[t][m] * g0 + sv[t][3 + m] * g1 + sv[t][6 + m] * g2);
-                }
-            }
-        }
     } else {
-        // DIV / DIV_RK in sub-groups of RG rows
-        constexpr int RG = MODE == GEMM_DIV_RK ? 4 : 8;
-        const double ur = (MODE == GEMM_DIV_RK) ? g.uref[n / g.np] : 0.0;
+        constexpr int RG = 8;
 #pragma unroll
         for (int r0 = 0; r0 < 24; r0 += RG) {
             float ij[RG];
-            double rf[RG], uu[RG], ua[RG];
+            double rf[RG];
 #pragma unroll
             for (int i = 0; i < RG; ++i) {
                 const int j = c0 + r0 + i;
                 if (j < g.M) {
-                    const int64_t idx = (int64_t)j * g.ldc + n;
                     ij[i] = __ldg(g.invJ + (int64_t)j * g.np + e);
-                    rf[i] = g.rfs ? __ldg(g.rfs + idx) : 0.0;
-                    if (MODE == GEMM_DIV_RK) {
-                        uu[i] = g.rk_last ? 0.0 : g.U[idx];
-                        ua[i] = (g.rk_last || !g.rk_first) ? g.Uacc[idx] : 0.0;
-                    }
+                    rf[i] = g.rfs ? __ldg(g.rfs + (int64_t)j * g.ldc + n) : 0.0;
                 }
             }
 #pragma unroll
             for (int i = 0; i < RG; ++i) {
                 const int j = c0 + r0 + i;
                 if (j < g.M) {
-                    const int64_t idx = (int64_t)j * g.ldc + n;
                     const float rt = -ij[i] * v[r0 + i];
-                    if (MODE == GEMM_DIV) {
-                        g.C[idx] = g.rfs ? (float)((double)rt + rf[i]) : rt;
-                    } else {
-                        const double rv = (double)rt + rf[i];
-                        if (g.rk_last) {
-                            const double un = ua[i] + g.c_acc * rv;
-                            g.U[idx] = un;
-                            g.Us[idx] = (float)(un - ur);
-                        } else {
-                            g.Uacc[idx] = (g.rk_first ? uu[i] : ua[i]) + g.c_acc * rv;
-                            g.Us[idx] = (float)((uu[i] - ur) + g.c_stage * rv);
-                        }
-                    }
+                    g.C[(int64_t)j * g.ldc + n] = g.rfs ? (float)((double)rt + rf[i]) : rt;
                 }
             }
         }
@@ -659,12 +614,8 @@ cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int 
     switch (g.mode) {                                                  \
         case GEMM_STORE:                                               \
             return launch_mode<GEMM_STORE, TF>(g, tm, op, err, grid, s, no_producer);   \
-        case GEMM_GRAD:                                                \
-            return launch_mode<GEMM_GRAD, TF>(g, tm, op, err, grid, s, no_producer);    \
         case GEMM_DIV:                                                 \
             return launch_mode<GEMM_DIV, TF>(g, tm, op, err, grid, s, no_producer);     \
-        case GEMM_DIV_RK:                                              \
-            return launch_mode<GEMM_DIV_RK, TF>(g, tm, op, err, grid, s, no_producer);  \
     }
     if (op.tf32) {
         FR_TC_MODES(true)

@@ -92,8 +92,8 @@ __device__ __forceinline__ void vis_flux(const T *u, const Prim<T> &q, const T g
 }
 
 template <typename T>
-__device__ __forceinline__ void rusanov(const T *ua, const T *ub, const T *n, T gamma, T *f) {
-    Prim<T> qa = prim(ua, gamma), qb = prim(ub, gamma);
+__device__ __forceinline__ void rusanov_q(const T *ua, const T *ub, const Prim<T> &qa, const Prim<T> &qb, const T *n,
+                                          T gamma, T *f) {
     T fa[V], fb[V];
     inv_flux_n(ua, qa, n, fa);
     inv_flux_n(ub, qb, n, fb);
@@ -104,6 +104,12 @@ __device__ __forceinline__ void rusanov(const T *ua, const T *ub, const T *n, T 
     const T s = fmax(sa, sb);
 #pragma unroll
     for (int v = 0; v < V; ++v) f[v] = T(0.5) * (fa[v] + fb[v]) - T(0.5) * s * (ub[v] - ua[v]);
+}
+
+// Rusanov flux from the two states (primitives formed here)
+template <typename T>
+__device__ __forceinline__ void rusanov(const T *ua, const T *ub, const T *n, T gamma, T *f) {
+    rusanov_q(ua, ub, prim(ua, gamma), prim(ub, gamma), n, gamma, f);
 }
 
 template <typename T>
@@ -303,12 +309,13 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
         }
         T n[3];
         pair_normal<T>(P, k, n);
-        rusanov(ua, ub, n, ph.gamma, fn);
+        // primitives once per side, for the Rusanov and the viscous flux
+        const Prim<T> qa = prim(ua, ph.gamma), qb = prim(ub, ph.gamma);
+        rusanov_q(ua, ub, qa, qb, n, ph.gamma, fn);
         if (ph.viscous) {
             T ga[3][V], gb[3][V], Fa[V][3], Fb[V][3];
             load_grad(F.GUF[ta], fa, ea, npa, ga);
             load_grad(F.GUF[tb], fb, eb, npb, gb);
-            Prim<T> qa = prim(ua, ph.gamma), qb = prim(ub, ph.gamma);
             vis_flux(ua, qa, ga, ph.mu, ph.kq, Fa);
             vis_flux(ub, qb, gb, ph.mu, ph.kq, Fb);
             const T b = ph.beta * T(P.sgn[k]);

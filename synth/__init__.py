@@ -1,7 +1,9 @@
 """Seeded synthetic inputs shared by the CUDA path's tests/bench and by the oracle.
 
 This package generates meshes (node coordinates, element connectivity,
-boundary-face tags, periodic translations) and closed-form initial
+boundary-face tags, periodic translations, and for curved meshes each
+element's quadratic node coordinates, placed on the straight element and
+moved by a smooth map, as a mesh generator would) and closed-form initial
 conditions evaluated at caller-supplied coordinates, and seeded initial
 network weights.  It holds none of the
 flux-reconstruction arithmetic: no solution/flux points, no operators, no

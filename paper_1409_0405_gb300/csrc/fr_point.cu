@@ -91,6 +91,37 @@ __device__ __forceinline__ void vis_flux(const T *u, const Prim<T> &q, const T g
     }
 }
 
+// normal viscous flux F_vis(u, grad u) . n directly (the 3-vector
+// tau . n and the energy entry), without forming the full tensor:
+//   (tau n)_a = mu (dv_a/dn + sum_m (dv_m/dx_a) n_m - 2/3 div v n_a),
+//   energy = v . (tau n) + mu gamma/Pr grad e . n
+template <typename T>
+__device__ __forceinline__ void vis_flux_n(const T *u, const Prim<T> &q, const T g[3][V], T mu, T kq, const T *n,
+                                           T *fn) {
+    T gv[3][3];  // gv[a][m] = d v_a / d x_m
+    T gen = T(0);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const T gr = g[m][0];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gv[a][m] = (g[m][1 + a] - q.v[a] * gr) * q.ir;
+        const T ge = (g[m][4] - u[4] * q.ir * gr) * q.ir - (q.v[0] * gv[0][m] + q.v[1] * gv[1][m] + q.v[2] * gv[2][m]);
+        gen += ge * n[m];
+    }
+    const T div = gv[0][0] + gv[1][1] + gv[2][2];
+    T tv = T(0);
+    fn[0] = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T dn = gv[a][0] * n[0] + gv[a][1] * n[1] + gv[a][2] * n[2];
+        const T tn = gv[0][a] * n[0] + gv[1][a] * n[1] + gv[2][a] * n[2];
+        const T t = mu * (dn + tn - T(2.0 / 3.0) * div * n[a]);
+        fn[1 + a] = t;
+        tv += q.v[a] * t;
+    }
+    fn[4] = tv + kq * gen;
+}
+
 template <typename T>
 __device__ __forceinline__ void rusanov_q(const T *ua, const T *ub, const Prim<T> &qa, const Prim<T> &qb, const T *n,
                                           T gamma, T *f) {
@@ -313,18 +344,15 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
         const Prim<T> qa = prim(ua, ph.gamma), qb = prim(ub, ph.gamma);
         rusanov_q(ua, ub, qa, qb, n, ph.gamma, fn);
         if (ph.viscous) {
-            T ga[3][V], gb[3][V], Fa[V][3], Fb[V][3];
+            T ga[3][V], gb[3][V], fva[V], fvb[V];
             load_grad(F.GUF[ta], fa, ea, npa, ga);
             load_grad(F.GUF[tb], fb, eb, npb, gb);
-            vis_flux(ua, qa, ga, ph.mu, ph.kq, Fa);
-            vis_flux(ub, qb, gb, ph.mu, ph.kq, Fb);
+            vis_flux_n(ua, qa, ga, ph.mu, ph.kq, n, fva);
+            vis_flux_n(ub, qb, gb, ph.mu, ph.kq, n, fvb);
             const T b = ph.beta * T(P.sgn[k]);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const T fva = Fa[v][0] * n[0] + Fa[v][1] * n[1] + Fa[v][2] * n[2];
-                const T fvb = Fb[v][0] * n[0] + Fb[v][1] * n[1] + Fb[v][2] * n[2];
-                fn[v] = fn[v] - (T(0.5) * (fva + fvb) - b * (fva - fvb)) + ph.tau * (ua[v] - ub[v]);
-            }
+            for (int v = 0; v < V; ++v)
+                fn[v] = fn[v] - (T(0.5) * (fva[v] + fvb[v]) - b * (fva[v] - fvb[v])) + ph.tau * (ua[v] - ub[v]);
         }
         T ma, mb;
         pair_mags<T>(P, k, ma, mb);
@@ -350,13 +378,12 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
         bc_states(B.btag[kb], u, n, ph, ghost, cb);
         rusanov(u, ghost, n, ph.gamma, fn);
         if (ph.viscous) {
-            T g[3][V], Fv[V][3];
+            T g[3][V], fv[V];
             load_grad(F.GUF[t], f, e, np, g);
             Prim<T> qc = prim(cb, ph.gamma);
-            vis_flux(cb, qc, g, ph.mu, ph.kq, Fv);
+            vis_flux_n(cb, qc, g, ph.mu, ph.kq, n, fv);
 #pragma unroll
-            for (int v = 0; v < V; ++v)
-                fn[v] = fn[v] - (Fv[v][0] * n[0] + Fv[v][1] * n[1] + Fv[v][2] * n[2]) + ph.tau * (u[v] - cb[v]);
+            for (int v = 0; v < V; ++v) fn[v] = fn[v] - fv[v] + ph.tau * (u[v] - cb[v]);
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) F.FC[t][o + v * np] = (fn[v] - fref_n(ph, v, n)) * mg;
@@ -437,14 +464,14 @@ __global__ void k_wall_force(const Bnd B, const double *__restrict__ bw, const F
 #pragma unroll
         for (int a = 0; a < 3; ++a) acc[a] += wa * (double)fi[1 + a];
         if (ph.viscous) {
-            T g[3][V], Fv[V][3];
+            // the common flux kernel's own viscous normal flux
+            T g[3][V], fvn[V];
             load_grad(F.GUF[t], f, e, np, g);
             Prim<T> qc = prim(cb, ph.gamma);
-            vis_flux(cb, qc, g, ph.mu, ph.kq, Fv);
+            vis_flux_n(cb, qc, g, ph.mu, ph.kq, n, fvn);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const T fv = -(Fv[1 + a][0] * n[0] + Fv[1 + a][1] * n[1] + Fv[1 + a][2] * n[2]) +
-                             ph.tau * (u[1 + a] - cb[1 + a]);
+                const T fv = -fvn[1 + a] + ph.tau * (u[1 + a] - cb[1 + a]);
                 acc[3 + a] += wa * (double)fv;
             }
         }

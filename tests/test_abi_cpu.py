@@ -106,6 +106,36 @@ def test_mesh_errors_detected_on_host():
     assert _create_rc(m, p=2, precision=7) == fr.FR_ERR_UNSUPPORTED
 
 
+def test_hex_and_curved_mesh_errors_detected_on_host():
+    """Hexahedra and curved meshes: an inverted hex, a stray hex whose faces
+    match no neighbour or periodic partner, an unsupported geometry order,
+    a curved mesh without the node array of a present type, and a curved
+    element folded flat are rejected on the host (FR_ERR_MESH)."""
+    library()
+    from paper_1409_0405_gb300 import fr
+    h = synth.hex_box(n=3, n_hex_cols=2)
+    inv = dict(h)
+    inv["hex"] = h["hex"].copy()
+    inv["hex"][0] = inv["hex"][0][[4, 5, 6, 7, 0, 1, 2, 3]]   # top and bottom swapped
+    assert _create_rc(inv) == fr.FR_ERR_MESH
+    mix = dict(synth.vortex_box(n=2))
+    mix["hex"] = np.asarray(h["hex"][:1])                     # a stray hex: faces match nothing
+    mix["xyz"] = np.concatenate([mix["xyz"], h["xyz"]])
+    mix["hex"] = mix["hex"] + len(synth.vortex_box(n=2)["xyz"])
+    assert _create_rc(mix) == fr.FR_ERR_MESH
+    c = synth.curve_mesh(synth.vortex_box(), amp=0.1)
+    g3 = dict(c)
+    g3["geom_order"] = 3
+    assert _create_rc(g3) == fr.FR_ERR_MESH
+    nop = dict(c)
+    del nop["tet_nodes"]
+    assert _create_rc(nop) == fr.FR_ERR_MESH
+    fold = dict(c)
+    fold["pri_nodes"] = c["pri_nodes"].copy()
+    fold["pri_nodes"][0, 12:18] = fold["pri_nodes"][0, 0:6]   # top level onto the bottom one
+    assert _create_rc(fold) == fr.FR_ERR_MESH
+
+
 def test_create_without_gpu_fails_cleanly():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

@@ -136,9 +136,9 @@ typedef struct {
  * On success *out receives a context the caller frees with fr_destroy.
  * Errors: FR_ERR_ARG, FR_ERR_MESH, FR_ERR_NOMEM, FR_ERR_CUDA;
  * FR_ERR_UNSUPPORTED for a precision outside FR_FP64..FR_TF32X3, or a
- * tensor-core precision whose operator exceeds the tensor-core kernel (more
- * than 256 operator rows, or a split-BF16 image without room for two ring
- * slots: the hexahedral gradient operator at p = 4).
+ * split-BF16 context whose resident operator image leaves no room for two
+ * ring slots (hexahedra at p = 4; split TF32 streams its operators and
+ * takes them; operators of more than 256 rows run as two row blocks).
  */
 int fr_create(const fr_mesh *mesh, int order, const fr_params *params, fr_ctx **out);
 

@@ -281,7 +281,22 @@ cudaError_t op_gemm<double>(fr_ctx *c, int t, int which, const GemmArgsT<double>
 
 template <>
 cudaError_t op_gemm<float>(fr_ctx *c, int t, int which, const GemmArgsT<float> &g, cudaStream_t s) {
-    if (is_tc(c)) return launch_gemm_tc(g, c->T[t].tc[which], c->tc_err, s);
+    if (is_tc(c)) {
+        const DevType &D = c->T[t];
+        const int r0 = D.tc_split[which];
+        if (!r0) return launch_gemm_tc(g, D.tc[which], c->tc_err, s);
+        // row blocks of a split operator (store epilogue): rows [0, r0) and
+        // [r0, M) of C from their own images
+        if (g.mode != GEMM_STORE) return cudaErrorInvalidValue;
+        GemmArgsT<float> g1 = g, g2 = g;
+        g1.M = r0;
+        g2.M = g.M - r0;
+        g2.C = g.C + (int64_t)r0 * g.ldc;
+        cudaError_t e = launch_gemm_tc(g1, D.tc[which], c->tc_err, s);
+        if (e == cudaSuccess) e = launch_gemm_tc(g2, D.tc2[which], c->tc_err, s);
+        ++c->launches;  // the second launch
+        return e;
+    }
     return launch_gemm<float>(with_sparse<float>(c, t, which, g), s);
 }
 
@@ -492,26 +507,41 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             // the three operators packed for the tensor cores
             const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
             const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok1[3] = {D.nu, D.nu, 3 * D.nu}, ok2[3] = {0, D.nf, D.nf};
-            for (int w = 0; w < 3; ++w) {
-                TcOperator &op = D.tc[w];
+            auto pack = [&](TcOperator &op, const double *A, int M, int K1, int K2) -> int {
                 op.tf32 = prm->precision == FR_TF32X3;
+                int r;
                 if (op.tf32) {
                     std::vector<uint32_t> img;
-                    tc_pack_tf32(opv[w]->data(), om[w], ok1[w], ok2[w], img, op.Nmma, op.K1pad, op.Kpad);
+                    tc_pack_tf32(A, M, K1, K2, img, op.Nmma, op.K1pad, op.Kpad);
                     uint32_t *dimg = nullptr;
-                    if ((rc = upload(c, &dimg, img))) return rc;
+                    if ((r = upload(c, &dimg, img))) return r;
                     op.img = (const uint8_t *)dimg;
                 } else {
                     std::vector<uint16_t> img;
-                    tc_pack(opv[w]->data(), om[w], ok1[w], ok2[w], img, op.Nmma, op.K1pad, op.Kpad);
+                    tc_pack(A, M, K1, K2, img, op.Nmma, op.K1pad, op.Kpad);
                     uint16_t *dimg = nullptr;
-                    if ((rc = upload(c, &dimg, img))) return rc;
+                    if ((r = upload(c, &dimg, img))) return r;
                     op.img = (const uint8_t *)dimg;
                 }
-                op.M = om[w];
-                op.K = ok1[w] + ok2[w];
+                op.M = M;
+                op.K = K1 + K2;
                 if (op.Nmma > 256 || tc_stages(op) < 2)
                     return set_err(FR_ERR_UNSUPPORTED, "operator too large for the tensor-core kernel");
+                return FR_OK;
+            };
+            for (int w = 0; w < 3; ++w) {
+                const int K = ok1[w] + ok2[w];
+                if (om[w] <= 256) {
+                    if ((rc = pack(D.tc[w], opv[w]->data(), om[w], ok1[w], ok2[w]))) return rc;
+                    continue;
+                }
+                // two row blocks (store epilogue only: the gradient of an
+                // RK step); the first a multiple of 16 rows
+                const int r0 = ((om[w] + 1) / 2 + 15) / 16 * 16;
+                if ((rc = pack(D.tc[w], opv[w]->data(), r0, ok1[w], ok2[w])) ||
+                    (rc = pack(D.tc2[w], opv[w]->data() + (size_t)r0 * K, om[w] - r0, ok1[w], ok2[w])))
+                    return rc;
+                D.tc_split[w] = r0;
             }
         }
         if (prm->precision == FR_FP64 || prm->precision == FR_FP32) {

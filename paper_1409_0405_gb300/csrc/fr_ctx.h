@@ -47,6 +47,10 @@ struct DevType {
     // FR_BF16X3 / FR_TF32X3: the packed operators M0, AGRAD, ADIV for the
     // tensor cores
     fr::TcOperator tc[3];
+    // an operator with more rows than one tensor-core tile takes (the p=4
+    // hex gradient): rows [0, tc_split) in tc[w], the rest in tc2[w]
+    fr::TcOperator tc2[3];
+    int tc_split[3] = {0, 0, 0};
     // FR_FP64 / FR_FP32: chunk-compressed M0, AGRAD, ADIV (sp_rc 0: dense)
     int sp_rc[3] = {0, 0, 0}, sp_lmax[3] = {0, 0, 0}, sp_masked[3] = {0, 0, 0};
     int *sp_off[3] = {nullptr, nullptr, nullptr}, *sp_cols[3] = {nullptr, nullptr, nullptr};

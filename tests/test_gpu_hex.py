@@ -139,13 +139,21 @@ def test_hex_reduced_precision_rhs_wall_bounded(prec, fac):
     ctx.reduce(check=False)
 
 
-def test_hex_tensor_cores_reject_p4():
-    """The p = 4 hex gradient operator (375 rows) exceeds the tensor-core
-    kernel's 256-row tile: creation fails cleanly with FR_ERR_UNSUPPORTED."""
+def test_hex_tensor_cores_p4():
+    """p = 4 hexahedra on the tensor cores: the gradient operator's 375 rows
+    run as two row blocks; split TF32 streams every operator and works
+    (checked against the oracle), while split BF16's resident images do
+    not fit beside a ring: creation fails cleanly with FR_ERR_UNSUPPORTED."""
     from paper_1409_0405_gb300 import fr
     with pytest.raises(fr.FRError) as ei:
         fr.Context(_box("hex"), 4, precision=fr.FR_BF16X3)
     assert ei.value.code == fr.FR_ERR_UNSUPPORTED
+    sol, ctx = make_pair(_box("hp"), 4, precision=fr.FR_TF32X3, viscous=True, mu=0.05)
+    _check_rhs(sol, ctx, state(sol, "smooth", seed=4), tol=5e-5)
+    ctx.reduce(check=False)
+    ctx.set_state(state(sol, "smooth", seed=4))
+    ctx.step(1e-4, 2)
+    ctx.reduce()  # finite, no timeout
 
 
 def test_hex_batch_matches_per_problem():

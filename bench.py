@@ -547,6 +547,22 @@ def hex_mode(fr, torch, args, sp):
                         "traffic": None, "launches": classes[dom][1],
                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}}
     ctx.close()
+    # the same workload with the operator applications on the tensor cores
+    # (split TF32; the p=4 hex gradient runs as two row blocks)
+    ct = fr.Context(mesh, ORDER, **flow_params(), precision=fr.FR_TF32X3)
+    ct.set_state(u0, sp)
+    for _ in range(max(args.warmup, 0)):
+        ct.step(dt, 1, sp)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ct.step(dt, 1, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1) / args.steps
+    out["tf32x3"] = {"value": ct.ndof * 4.0 / (ms_t * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_t,
+                     "state_finite": bool(ct.reduce(stream=sp, check=False)[6] == 0.0)}
+    ct.close()
     return out
 
 

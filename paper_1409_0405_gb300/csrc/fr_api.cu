@@ -5,11 +5,15 @@
 // interleaved with point-wise kernels), per element type t:
 //   UF_t  = M0 U_t                                   (Table 2's M0)
 //   NS:   DUF = C - u_f at every flux point          (common solution)
-//         GU_t = (1/J) S^T [D | n^(x)M3] [U_t; DUF_t] (corrected gradient)
+//         GU_t = (1/J) S^T [D | n^(x)M3] [U_t; DUF_t] (corrected gradient;
+//                in the FP32-storage modes the operator kernel stores the
+//                reference gradient and the flux kernel applies S^T/J)
 //         GUF_t = M0 GU_t
 //   FT_t  = S (F_inv - F_vis - F_inf) at solution points
 //   FC    = (common normal flux - F_inf.n) |S^T n^| at every flux point
-//   R_t   = -(1/J) [M1 - M3 M2 | M3] [FT_t; FC_t]   (+ fused RK4 update)
+//   R_t   = -(1/J) [M1 - M3 M2 | M3] [FT_t; FC_t]   (+ fused RK4 update;
+//           on the tensor cores a streaming pass scales and updates)
+// Element types t: tets, prisms, hexes.
 // The stage input Us is stored centred, u - u_inf (u_inf the far-field
 // conserved state): M0 reproduces and D annihilates constants, so this is
 // exact, and the long operator sums then run over small numbers.

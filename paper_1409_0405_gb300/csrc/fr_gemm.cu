@@ -2,7 +2,7 @@
 // FP32 (T), the RK register update always in FP64.
 //
 // Every operator application of an FR step is a constant operator matrix A
-// (at most 375 x 275 here) times a row-major state matrix B whose columns
+// (at most 375 rows, 525 columns here) times a row-major state matrix B whose columns
 // run over variables x elements (10^5 - 10^6 columns): the block-by-panel
 // shape of Sec. 2.1 (Eq. 1, Fig. 1).  The paper splits B into column slabs,
 // one per thread, and keeps A whole; here a CTA owns 128 columns and a

@@ -90,3 +90,24 @@ def test_ke_rate_of_decaying_shear_wave(n, tol):
     u = s.state_from_points(synth.shear_wave(s.upts_xyz_points(), amp=amp))
     exact = -mu * amp * amp * (2.0 * math.pi) ** 3 / 2.0
     assert abs(s.ke_rate(u) - exact) < tol * abs(exact)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_integrals_and_kinetic_energy_closed_forms(p):
+    """On the straight (unjittered) cube [-5,5]^3, tets and prisms: the
+    conserved integrals of rho = 1, u = a y, E = e0 + a^2 y^2 / 2 are
+    (V, 0, 0, 0, e0 V + a^2 I / 2) and the kinetic energy a^2 I / 2, with
+    V = 1000 and I = int y^2 = 10^2 * 2 * 5^3 / 3 (the quadrature is exact
+    for these quadratics at p >= 2 on affine elements)."""
+    a, e0 = 0.3, 2.5
+    s = Solver(synth.vortex_box(jitter=0.0), p)
+    X = s.upts_xyz_points()
+    q = np.zeros((len(X), 5))
+    q[:, 0] = 1.0
+    q[:, 1] = a * X[:, 1]
+    q[:, 4] = e0 + 0.5 * (a * X[:, 1]) ** 2
+    u = s.state_from_points(q)
+    V, I = 1000.0, 100.0 * 2.0 * 125.0 / 3.0
+    np.testing.assert_allclose(s.integrals(u), [V, 0.0, 0.0, 0.0, e0 * V + 0.5 * a * a * I],
+                               rtol=1e-13, atol=1e-10)
+    assert abs(s.kinetic_energy(u) - 0.5 * a * a * I) < 1e-12 * I

@@ -136,6 +136,22 @@ def test_hex_and_curved_mesh_errors_detected_on_host():
     assert _create_rc(fold) == fr.FR_ERR_MESH
 
 
+def test_binding_checks_curved_node_shapes():
+    """The binding validates the quadratic node arrays' shapes before any
+    pointer reaches the library."""
+    library()
+    from paper_1409_0405_gb300 import fr
+    c = synth.curve_mesh(synth.vortex_box(), amp=0.1)
+    bad = dict(c)
+    bad["pri_nodes"] = c["pri_nodes"][:, :17]
+    with pytest.raises(ValueError):
+        fr.Context(bad, 2)
+    short = dict(c)
+    short["tet_nodes"] = c["tet_nodes"][:-1]
+    with pytest.raises(ValueError):
+        fr.Context(short, 2)
+
+
 def test_create_without_gpu_fails_cleanly():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

@@ -176,6 +176,41 @@ def test_farfield_ghost_is_freestream_for_freestream_interior():
     np.testing.assert_allclose(g, u, rtol=1e-13)
 
 
+def test_farfield_ghost_keeps_the_characteristic_invariants():
+    """Riemann-invariant far field (Sec. 3.2): the ghost state carries the
+    outgoing invariant vn + 2c/(g-1) of the interior and the incoming
+    vn - 2c/(g-1) of the free stream; its entropy p/rho^g and tangential
+    velocity come from the interior at outflow (vn_b >= 0) and from the free
+    stream at inflow (computed here from primitives, not from the oracle's
+    formula)."""
+    rng = np.random.default_rng(12)
+    vinf = np.array([1.0, 0.2, -0.1])
+    pinf, rinf = 1.0 / (GAMMA * 0.2 ** 2), 1.0
+    n = _rand_normals(40, 13)
+    rho = 1.0 + 0.1 * rng.standard_normal(40)
+    v = vinf + 0.3 * rng.standard_normal((40, 3))
+    p = pinf * (1.0 + 0.1 * rng.standard_normal(40))
+    u = np.concatenate([rho[:, None], rho[:, None] * v,
+                        (p / (GAMMA - 1) + 0.5 * rho * np.sum(v * v, 1))[:, None]], axis=1)
+    g = physics.farfield_state(u, n, GAMMA, rinf, vinf, pinf)
+    rg = g[:, 0]
+    vg = g[:, 1:4] / rg[:, None]
+    pg = (GAMMA - 1) * (g[:, 4] - 0.5 * rg * np.sum(vg * vg, 1))
+    c, cg, cinf = np.sqrt(GAMMA * p / rho), np.sqrt(GAMMA * pg / rg), math.sqrt(GAMMA * pinf / rinf)
+    vn, vng, vninf = np.sum(v * n, 1), np.sum(vg * n, 1), n @ vinf
+    k = 2.0 / (GAMMA - 1)
+    np.testing.assert_allclose(vng + k * cg, vn + k * c, rtol=1e-12)
+    np.testing.assert_allclose(vng - k * cg, vninf - k * cinf, rtol=1e-12, atol=1e-12)
+    out = vng >= 0.0
+    assert out.any() and (~out).any()
+    sg = pg / rg ** GAMMA
+    np.testing.assert_allclose(sg[out], (p / rho ** GAMMA)[out], rtol=1e-12)
+    np.testing.assert_allclose(sg[~out], np.full((~out).sum(), pinf / rinf ** GAMMA), rtol=1e-12)
+    tg = vg - vng[:, None] * n
+    np.testing.assert_allclose(tg[out], (v - vn[:, None] * n)[out], atol=1e-12)
+    np.testing.assert_allclose(tg[~out], (vinf - vninf[:, None] * n)[~out], atol=1e-12)
+
+
 def test_wall_ghost_has_zero_mass_flux():
     u = _rand_states(30, 10)
     n = _rand_normals(30, 11)

@@ -126,7 +126,7 @@ class Closure:
     def __init__(self, ctx_lo, nh=NH, seed=0):
         self.ctx = ctx_lo
         self.nets, self.scale = {}, {}
-        for et in (0, 1):
+        for et in range(3):  # tets, prisms, hexes
             if ctx_lo.ne(et):
                 nu = ctx_lo.nu(et)
                 self.nets[et] = Network(20 * nu, 5 * nu, nh=nh, seed=seed + et)

@@ -456,6 +456,32 @@ def tgv_params(precision):
                 precision=precision)
 
 
+def dgemm_reference_tflops(torch, n=8192, reps=3, device="cuda"):
+    """The paper's "reference peak" method (Sec. 4.1): the FP64 rate of a
+    large library DGEMM (here cuBLAS through torch.matmul, n x n x n),
+    timed with CUDA events after one warm-up call."""
+    a = torch.rand(n, n, dtype=torch.float64, device=device)
+    b = torch.rand(n, n, dtype=torch.float64, device=device)
+    c = torch.matmul(a, b)
+    if device != "cuda":
+        import time as _t
+        t0 = _t.perf_counter()
+        for _ in range(reps):
+            c = torch.matmul(a, b)
+        sec = (_t.perf_counter() - t0) / reps
+    else:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            c = torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3 / reps
+    del a, b, c
+    return 2.0 * n ** 3 / sec / 1e12
+
+
 def max_over_ranks(x, world, device="cpu"):
     """The largest x over the ranks of the default process group (x itself
     for one rank): the step time every rank waited for."""
@@ -778,7 +804,15 @@ def main():
 
     mesh = synth.boundary_layer_box(nx=args.nx)
     prec = {"fp64": fr.FR_FP64, "fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3, "tf32x3": fr.FR_TF32X3}[args.precision]
+    try:
+        free0 = torch.cuda.mem_get_info()[0]
+    except Exception:
+        free0 = None
     ctx = fr.Context(mesh, ORDER, **flow_params(), precision=prec)
+    try:
+        ctx_gb = (free0 - torch.cuda.mem_get_info()[0]) / 1e9 if free0 is not None else None
+    except Exception:
+        ctx_gb = None
     counts = ctx.counts()
     u0 = points_to_public(synth.perturbed_freestream(ctx.upts_points(), seed=2,
                                                      wall_delta=WALL_DELTA), counts)
@@ -860,6 +894,10 @@ def main():
         fp64_peak_meas = fr.peak_fp64(sp)
     except Exception:
         fp64_peak_meas = None
+    try:
+        dgemm_ref = dgemm_reference_tflops(torch)
+    except Exception:
+        dgemm_ref = None
     # DRAM bytes per launch of the FP64 gradient class, from an ncu capture
     # (dram__bytes_read + dram__bytes_write) of the same kernels on the
     # nx=15 case (tet 465 MB, prism 480 MB per launch), scaled by the 5x
@@ -883,7 +921,9 @@ def main():
                 "kernel": f"k_gemm ({dom})", "launches": dom_n,
                 "avg_launch_ms": dom_ms / max(dom_n, 1),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "peak_measured_fma_probe": (fp64_peak_meas / 1e3) if fp64_peak_meas else None}
+                "peak_measured_fma_probe": (fp64_peak_meas / 1e3) if fp64_peak_meas else None,
+                "reference_peak_cublas_dgemm": dgemm_ref,
+                "frac_of_reference_peak": (achieved / 1e3 / dgemm_ref) if dgemm_ref else None}
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": None, "kernel": dom}
@@ -900,7 +940,8 @@ def main():
                    "ndof": ndof, "rhs_per_step": 4, "dt": dt,
                    "l2": "inputs > L2 (state 339 MB per register, scratch > 4 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "state_finite_after_timed_steps": bool(state_ok)},
+                   "state_finite_after_timed_steps": bool(state_ok),
+                   "device_memory_gb": ctx_gb},
         "roofline": roof,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in classes.items()},
         "gemm_fp64_tflops": all_gemm / (sum(classes[k][0] for k in gemm_classes) * 1e-3) / 1e12,

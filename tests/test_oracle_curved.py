@@ -90,3 +90,42 @@ def test_curved_vortex_residual_converges():
         errs.append(math.sqrt(sum(float(np.sum(s.m.ops[t].w[None, None, :] * s.m.J[t][:, None, :] * e[t] ** 2))
                                   for t in s.types)))
     assert math.log2(errs[0] / errs[1]) >= 2 - 0.35, errs
+
+
+@pytest.mark.parametrize("kind", ["pt", "hp"])
+def test_curved_mesh_generator_shares_face_nodes(kind):
+    """The generator's quadratic nodes: the vertex nodes of every element
+    are the moved vertices, and two elements sharing an edge give its
+    midpoint node the same coordinates (what the face pairing relies on)."""
+    m0, m = _box(kind)
+    xyz = m0["xyz"]
+    lo, hi = xyz.min(0), xyz.max(0)
+    L = np.where(m0["period"] > 0, m0["period"], hi - lo)
+    phi = lambda x: x + 0.15 * (L / (2 * math.pi)) * np.prod(np.sin(2 * math.pi * (x - lo) / L), axis=-1,
+                                                             keepdims=True)
+    nv = {"tet": 4, "pri": 6, "hex": 8}
+    mids = {}
+    for t in ("tet", "pri", "hex"):
+        conn = m0.get(t, np.zeros((0, nv[t]), np.int64))
+        if not len(conn):
+            continue
+        nodes = m[t + "_nodes"]
+        ref = synth.QUAD_NODES[t]
+        # vertex nodes: the first nv reference nodes of tets and hexes are the
+        # vertices; for prisms the vertices are nodes 0-2 and 12-14
+        vidx = list(range(4)) if t == "tet" else ([0, 1, 2, 12, 13, 14] if t == "pri" else [0, 2, 8, 6, 18, 20, 26, 24])
+        np.testing.assert_allclose(nodes[:, vidx], phi(xyz[conn]), atol=1e-12)
+        # edge midpoints between two vertices, keyed by the sorted vertex pair
+        vref = np.array([ref[i] for i in vidx], dtype=float)
+        for q, r in enumerate(ref):
+            for a in range(nv[t]):
+                for b in range(a + 1, nv[t]):
+                    if np.allclose(r, 0.5 * (vref[a] + vref[b])):
+                        key = np.sort(conn[:, [a, b]], axis=1)
+                        for e in range(len(conn)):
+                            k = tuple(key[e])
+                            if k in mids:
+                                assert np.allclose(mids[k], nodes[e, q], atol=1e-12)
+                            else:
+                                mids[k] = nodes[e, q]
+    assert mids

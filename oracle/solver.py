@@ -36,6 +36,79 @@ RK4_2N_FRACTIONS = (
 RK4_2N_A = [float(x) for x in RK4_2N_FRACTIONS[0]]
 RK4_2N_B = [float(x) for x in RK4_2N_FRACTIONS[1]]
 
+# RK45[2R+], the time stepper of the paper's runs (Sec. 3.4; Table 1 lists
+# RK45): the five-stage fourth-order scheme RK4(3)5[2R+]C of Kennedy,
+# Carpenter & Lewis (2000), with an embedded third-order solution.  Its
+# Butcher matrix has the two-register structure A[i][i-1] = a_i and
+# A[i][j] = b_j for j < i-1, so only the sub-diagonal a_1..a_4, the weights
+# b_1..b_5 and the embedded weights bhat_1..bhat_5 are free.  The published
+# rational approximations of those coefficients:
+RK45_2R_FRACTIONS = (
+    (Fraction(970286171893, 4311952581923), Fraction(6584761158862, 12103376702013),
+     Fraction(2251764453980, 15575788980749), Fraction(26877169314380, 34165994151039)),
+    (Fraction(1153189308089, 22510343858157), Fraction(1772645290293, 4653164025191),
+     Fraction(-1672844663538, 4480602732383), Fraction(2114624349019, 3568978502595),
+     Fraction(5198255086312, 14908931495163)),
+    (Fraction(1016888040809, 7410784769900), Fraction(11231460423587, 58533540763752),
+     Fraction(-1563879915014, 6823010717585), Fraction(606302364029, 971179775848),
+     Fraction(1097981568119, 3980877426909)))
+RK45_2R_A = [float(x) for x in RK45_2R_FRACTIONS[0]]
+RK45_2R_B = [float(x) for x in RK45_2R_FRACTIONS[1]]
+RK45_2R_BHAT = [float(x) for x in RK45_2R_FRACTIONS[2]]
+# b - bhat in double: the weights of the embedded error estimate
+RK45_2R_E = [float(b - bh) for b, bh in zip(RK45_2R_FRACTIONS[1], RK45_2R_FRACTIONS[2])]
+
+
+def rk45_2r_step(rhs, u, dt, a=None, b=None, e=None):
+    """One RK45[2R+] step of du/dt = rhs(u) in its two-register form.
+
+    Register y accumulates the solution, u_n + dt sum_{j<i} b_j k_j; register
+    x holds the stage input.  Stage i evaluates k_i = rhs(x), then forms the
+    next stage input from y *before* adding b_i k_i to it:
+        x <- y + dt a_i k_i   (i < 5),   y <- y + dt b_i k_i,
+    which reproduces the stage values of the Butcher matrix above.  The
+    third register accumulates the embedded error estimate
+        err = u_{n+1} - uhat_{n+1} = dt sum_i (b_i - bhat_i) k_i.
+    Returns (u_{n+1}, err).  The coefficients default to the double values
+    of the published table; any numeric type that supports + and * works
+    (the tests pass Fractions)."""
+    a = RK45_2R_A if a is None else a
+    b = RK45_2R_B if b is None else b
+    e = RK45_2R_E if e is None else e
+    y, x = u, u
+    err = None
+    for i in range(5):
+        k = rhs(x)
+        if i < 4:
+            x = y + (dt * a[i]) * k
+        y = y + (dt * b[i]) * k
+        err = (dt * e[i]) * k if err is None else err + (dt * e[i]) * k
+    return y, err
+
+
+def rk45_error_norm(u_new, err, atol, rtol):
+    """Weighted RMS norm of the embedded error estimate over every value of
+    the state: sqrt(mean((err / (atol + rtol |u_{n+1}|))^2)).  (Reading: the
+    usual mixed absolute/relative scaling of embedded-pair controllers,
+    taken on the new solution only, since the two-register scheme has
+    overwritten u_n.)"""
+    u_new = np.asarray(u_new, dtype=np.float64)
+    w = np.asarray(err, dtype=np.float64) / (atol + rtol * np.abs(u_new))
+    return float(np.sqrt(np.mean(w * w)))
+
+
+# step-size controller of the adaptive RK45[2R+] driver (readings: the
+# classic elementary controller for an embedded pair of orders 4(3),
+# exponent -1/(3+1), with a safety factor and growth limits)
+RK45_SAFETY, RK45_FAC_MIN, RK45_FAC_MAX = 0.9, 0.3, 2.5
+
+
+def rk45_next_dt(dt, err_norm):
+    if err_norm <= 0.0:
+        return dt * RK45_FAC_MAX
+    fac = RK45_SAFETY * err_norm ** -0.25
+    return dt * min(RK45_FAC_MAX, max(RK45_FAC_MIN, fac))
+
 
 class Solver:
     def __init__(self, mesh, p, gamma=1.4, mu=0.0, prandtl=0.72, viscous=False,
@@ -221,6 +294,30 @@ class Solver:
             du = a * du + dt * self.rhs(u)
             u = u + b * du
         return u
+
+    def rk45_step(self, u, dt):
+        """One RK45[2R+] step (see rk45_2r_step): (u_{n+1}, error estimate)."""
+        return rk45_2r_step(self.rhs, u, dt)
+
+    def rk45_adaptive(self, u, t_span, dt, atol, rtol, max_steps=100000):
+        """Advance by exactly t_span with error-controlled RK45[2R+] steps.
+        A step is accepted when the weighted error norm is <= 1; either way
+        the next step size is rk45_next_dt(dt, norm), and the last step is
+        shortened to end at t_span.  Returns (u, next dt, accepted steps,
+        rejected steps)."""
+        t, acc, rej = 0.0, 0, 0
+        while t < t_span and acc + rej < max_steps:
+            last = dt >= t_span - t
+            h = t_span - t if last else dt
+            un, err = self.rk45_step(u, h)
+            nrm = rk45_error_norm(un, err, atol, rtol)
+            if nrm <= 1.0:
+                u, acc = un, acc + 1
+                t = t_span if last else t + h
+            else:
+                rej += 1
+            dt = rk45_next_dt(h, nrm)
+        return u, dt, acc, rej
 
     def integrals(self, u_flat):
         """sum_e sum_j w_j J_j u_j per conserved variable."""

@@ -21,7 +21,9 @@
 // only a stand-in for the device symbol.  The device address is obtained
 // once per device with cudaGetSymbolAddress, with that device current, the
 // first time the entry point is called on it; that first call should
-// therefore come before any stream capture.
+// therefore come before any stream capture.  The cached address belongs to
+// the device's primary context: after a cudaDeviceReset it would be stale,
+// so a process that resets a device must not call this entry point again.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -36,6 +38,10 @@ constexpr int kPointsPerThread = 8;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_partials[FR_NOALLOC_MAX_BLOCKS * 7];
+
+// the limit documented in fr.h is the one enforced here
+static_assert((int64_t)kThreads * kPointsPerThread * FR_NOALLOC_MAX_BLOCKS == FR_NOALLOC_MAX_POINTS,
+              "FR_NOALLOC_MAX_POINTS must equal the blocks times the points per block");
 
 double *g_partials_addr[kMaxDevices] = {nullptr};
 std::mutex g_setup_mutex;
@@ -89,6 +95,8 @@ __global__ void k_noalloc_final(const double *partial, int nblocks, double *out)
 extern "C" int fr_reduce_noalloc(int64_t ne, int nu, const double *u_dev, const double *wJ_dev, double gamma,
                                  double *out_dev, void *cuda_stream) {
     if (ne < 0 || nu <= 0 || !u_dev || !wJ_dev || !out_dev || !(gamma > 1.0)) return FR_ERR_ARG;
+    // bound ne before forming ne * nu, which could otherwise overflow
+    if (ne > FR_NOALLOC_MAX_POINTS / nu) return FR_ERR_ARG;
     const int64_t npts = ne * (int64_t)nu;
     const int64_t per_block = (int64_t)kThreads * kPointsPerThread;
     const int64_t nblocks = (npts + per_block - 1) / per_block;

@@ -195,6 +195,53 @@ int fr_step(fr_ctx *ctx, double dt, int nsteps, void *cuda_stream);
 int fr_step_ls(fr_ctx *ctx, double dt, int nsteps, void *cuda_stream);
 
 /*
+ * fr_step_rk45: nsteps fixed steps of RK45[2R+], the scheme the paper's runs
+ * used (Sec. 3.4: "RK45[2R+]"; Table 1 lists RK45): the five-stage
+ * fourth-order scheme RK4(3)5[2R+]C of Kennedy, Carpenter & Lewis (2000),
+ * in two registers.  Per stage i, with k_i = R(x) the RHS of the stage
+ * input x:  x <- U + dt a_i k_i (formed before U moves),
+ * U <- U + dt b_i k_i, and the error register E <- E + dt (b_i - bhat_i) k_i
+ * (the difference between the fourth-order solution and the embedded
+ * third-order one; E holds the last step's estimate afterwards).  The
+ * first call allocates E (one state-sized FP64 array owned by the
+ * context); make it before any stream capture.  5 RHS per step;
+ * asynchronous on cuda_stream.
+ * Errors: FR_ERR_ARG (nsteps < 0 or dt not finite), FR_ERR_NOMEM, FR_ERR_CUDA.
+ */
+int fr_step_rk45(fr_ctx *ctx, double dt, int nsteps, void *cuda_stream);
+
+/*
+ * fr_rk45_error: weighted RMS norm of the last RK45 step's error estimate,
+ * *norm = sqrt(mean over every value of the state of
+ * (E / (atol + rtol |u_{n+1}|))^2) (host double).  Synchronous.
+ * Errors: FR_ERR_ARG (null norm, negative tolerances, atol + rtol == 0, or
+ * no RK45 step taken yet), FR_ERR_CUDA.
+ */
+int fr_rk45_error(fr_ctx *ctx, double atol, double rtol, double *norm, void *cuda_stream);
+
+/*
+ * fr_rk45_get_error: copy the error register E (last RK45 step) into e
+ * (host, caller-owned, public layout, fr_ndof doubles).  Synchronous.
+ */
+int fr_rk45_get_error(fr_ctx *ctx, double *e, void *cuda_stream);
+
+/*
+ * fr_step_rk45_adaptive: advance the internal solution by exactly t_span
+ * with error-controlled RK45[2R+] steps.  Each attempted step of size h
+ * (the last one shortened to end at t_span) is accepted when
+ * fr_rk45_error(atol, rtol) <= 1 and rejected otherwise (the solution is
+ * restored from a backup register); either way the next step size is
+ * h * clamp(0.9 norm^(-1/4), 0.3, 2.5).  *dt (in: first step size, out:
+ * the size proposed for the next step).  stats (host, may be null):
+ * [accepted, rejected].  One host synchronisation per attempted step; the
+ * first call allocates the error and backup registers.
+ * Errors: FR_ERR_ARG (bad arguments, or max_steps attempts before t_span),
+ * FR_ERR_NONFINITE (non-finite error estimate), FR_ERR_NOMEM, FR_ERR_CUDA.
+ */
+int fr_step_rk45_adaptive(fr_ctx *ctx, double t_span, double atol, double rtol, double *dt, int max_steps,
+                          int64_t *stats, void *cuda_stream);
+
+/*
  * fr_reduce: integrals of the internal solution register.  out (host,
  * caller-owned, 7 doubles) receives sum_e sum_j w_j J_j u_j for the 5
  * conserved variables, the kinetic energy integral, and the number of

@@ -841,6 +841,159 @@ int step_2n_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
     return FR_OK;
 }
 
+// RK45[2R+] (the paper's stepper, Sec. 3.4): RK4(3)5[2R+]C of Kennedy,
+// Carpenter & Lewis (2000), five stages in two registers (U and the stage
+// input Us) plus the embedded error estimate E.  The published rational
+// coefficients (the same table the oracle states): sub-diagonal a_1..a_4,
+// weights b_1..b_5, embedded weights bhat_1..bhat_5.
+constexpr double kRk45A[4] = {970286171893.0 / 4311952581923.0, 6584761158862.0 / 12103376702013.0,
+                              2251764453980.0 / 15575788980749.0, 26877169314380.0 / 34165994151039.0};
+constexpr double kRk45B[5] = {1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+                              -1672844663538.0 / 4480602732383.0, 2114624349019.0 / 3568978502595.0,
+                              5198255086312.0 / 14908931495163.0};
+constexpr double kRk45Bh[5] = {1016888040809.0 / 7410784769900.0, 11231460423587.0 / 58533540763752.0,
+                               -1563879915014.0 / 6823010717585.0, 606302364029.0 / 971179775848.0,
+                               1097981568119.0 / 3980877426909.0};
+
+// the error register (and, for the adaptive driver, the backup of U):
+// allocated by the first call that needs them
+int ensure_rk45_regs(fr_ctx *c, bool backup) {
+    int rc;
+    for (int t = 0; t < NT; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        const size_t su = (size_t)D.nu * NV * D.np;
+        if (!D.E && (rc = dev_alloc(c, &D.E, su))) return rc;
+        if (backup && !D.Ubak && (rc = dev_alloc(c, &D.Ubak, su))) return rc;
+    }
+    return FR_OK;
+}
+
+template <typename T>
+int step_2r_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s) {
+    if (nsteps <= 0) return FR_OK;
+    int rc;
+    if ((rc = ensure_rk45_regs(c, false))) return rc;
+    const Phys ph = phys_of(c);
+    for (int t = 0; t < NT; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_center<T>(D.nu, D.np, D.U, (T *)D.Us, ph.uref, s), "centre"))) return rc;
+    }
+    for (int it = 0; it < nsteps; ++it)
+        for (int st = 0; st < 5; ++st) {
+            T *in[NT] = {};
+            for (int t = 0; t < NT; ++t)
+                if (c->T[t].present) in[t] = (T *)c->T[t].Us;
+            if ((rc = rhs_internal<T>(c, in, nullptr, s))) return rc;
+            const double cs = st < 4 ? dt * kRk45A[st] : 0.0, ca = dt * kRk45B[st],
+                         ce = dt * (kRk45B[st] - kRk45Bh[st]);
+            for (int t = 0; t < NT; ++t) {
+                DevType &D = c->T[t];
+                if (!D.present) continue;
+                if ((rc = cuda_check(launch(c, K_DIV, s,
+                                            [&] {
+                                                return launch_rk_2r_update<T>(D.nu, D.np, (const T *)D.R, D.U, D.E,
+                                                                              (T *)D.Us, ph.uref, cs, ca, ce, st == 0,
+                                                                              st == 4, s);
+                                            }),
+                                     "2R update")))
+                    return rc;
+            }
+        }
+    return FR_OK;
+}
+
+// weighted RMS norm of the error register: sqrt(mean((E / (atol + rtol |U|))^2))
+// over every value of the state (synchronises)
+int rk45_error_norm(fr_ctx *c, double atol, double rtol, double *norm, cudaStream_t s) {
+    int rc, nb = 0;
+    int64_t nval = 0;
+    double *part = c->diag, *res = c->diag + (size_t)kDiagBlocks * 8;
+    for (int t = 0; t < NT; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if (!D.E) return set_err(FR_ERR_ARG, "no RK45 step has been taken on this context");
+        if ((rc = cuda_check(launch_err_norm_partial(D.nu, D.ne, D.np, D.U, D.E, atol, rtol, part + nb, kDiagBlocks,
+                                                     s),
+                             "error norm")))
+            return rc;
+        nb += kDiagBlocks;
+        nval += D.ne * NV * D.nu;
+    }
+    if ((rc = cuda_check(launch_sum_partials(part, nb, 1, res, s), "error norm sum"))) return rc;
+    double sum = 0.0;
+    if ((rc = cuda_check(cudaMemcpyAsync(&sum, res, sizeof(double), cudaMemcpyDeviceToHost, s), "error norm copy")))
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(s), "error norm sync"))) return rc;
+    if ((rc = check_tc(c))) return rc;
+    *norm = std::sqrt(sum / (double)nval);
+    return FR_OK;
+}
+
+// step-size controller of the adaptive driver (the oracle's, same readings):
+// dt * clamp(0.9 norm^(-1/4), 0.3, 2.5)
+double rk45_next_dt(double dt, double norm) {
+    if (norm <= 0.0) return dt * 2.5;
+    return dt * std::min(2.5, std::max(0.3, 0.9 * std::pow(norm, -0.25)));
+}
+
+template <typename T>
+int adaptive_impl(fr_ctx *c, double t_span, double atol, double rtol, double *dt_io, int max_steps, int64_t *stats,
+                  cudaStream_t s) {
+    int rc;
+    if ((rc = ensure_rk45_regs(c, true))) return rc;
+    double t = 0.0, dt = *dt_io;
+    int64_t acc = 0, rej = 0;
+    while (t < t_span && acc + rej < max_steps) {
+        const bool last = dt >= t_span - t;
+        const double h = last ? t_span - t : dt;
+        for (int k = 0; k < NT; ++k) {
+            DevType &D = c->T[k];
+            if (!D.present) continue;
+            if ((rc = cuda_check(cudaMemcpyAsync(D.Ubak, D.U, (size_t)D.nu * NV * D.np * sizeof(double),
+                                                 cudaMemcpyDeviceToDevice, s),
+                                 "backup")))
+                return rc;
+        }
+        if ((rc = step_2r_impl<T>(c, h, 1, s))) return rc;
+        double nrm = 0.0;
+        if ((rc = rk45_error_norm(c, atol, rtol, &nrm, s))) return rc;
+        if (!std::isfinite(nrm)) return set_err(FR_ERR_NONFINITE, "non-finite RK45 error estimate");
+        if (nrm <= 1.0) {
+            ++acc;
+            t = last ? t_span : t + h;
+        } else {
+            ++rej;
+            for (int k = 0; k < NT; ++k) {
+                DevType &D = c->T[k];
+                if (!D.present) continue;
+                if ((rc = cuda_check(cudaMemcpyAsync(D.U, D.Ubak, (size_t)D.nu * NV * D.np * sizeof(double),
+                                                     cudaMemcpyDeviceToDevice, s),
+                                     "restore")))
+                    return rc;
+            }
+        }
+        dt = rk45_next_dt(h, nrm);
+    }
+    *dt_io = dt;
+    if (stats) {
+        stats[0] = acc;
+        stats[1] = rej;
+    }
+    // the stage input follows the (possibly restored) solution register
+    const Phys ph = phys_of(c);
+    for (int k = 0; k < NT; ++k) {
+        DevType &D = c->T[k];
+        if (!D.present) continue;
+        if ((rc = cuda_check(launch_center<T>(D.nu, D.np, D.U, (T *)D.Us, ph.uref, s), "centre"))) return rc;
+    }
+    if (t < t_span) return set_err(FR_ERR_ARG, "max_steps reached before t_span");
+    return FR_OK;
+}
+
+template int step_2r_impl<float>(fr_ctx *, double, int, cudaStream_t);
+template int step_2r_impl<double>(fr_ctx *, double, int, cudaStream_t);
 template int step_2n_impl<float>(fr_ctx *, double, int, cudaStream_t);
 template int step_2n_impl<double>(fr_ctx *, double, int, cudaStream_t);
 template int step_impl<float>(fr_ctx *, double, int, cudaStream_t);
@@ -1039,6 +1192,48 @@ int fr_step_ls(fr_ctx *c, double dt, int nsteps, void *stream) {
     if (!c || nsteps < 0 || !(dt == dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
     cudaStream_t s = (cudaStream_t)stream;
     return is_f32(c) ? step_2n_impl<float>(c, dt, nsteps, s) : step_2n_impl<double>(c, dt, nsteps, s);
+}
+
+int fr_step_rk45(fr_ctx *c, double dt, int nsteps, void *stream) {
+    if (!c || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    return is_f32(c) ? step_2r_impl<float>(c, dt, nsteps, s) : step_2r_impl<double>(c, dt, nsteps, s);
+}
+
+int fr_rk45_error(fr_ctx *c, double atol, double rtol, double *norm, void *stream) {
+    if (!c || !norm || !(atol >= 0.0) || !(rtol >= 0.0) || !(atol + rtol > 0.0))
+        return set_err(FR_ERR_ARG, "invalid error-norm arguments");
+    return rk45_error_norm(c, atol, rtol, norm, (cudaStream_t)stream);
+}
+
+int fr_rk45_get_error(fr_ctx *c, double *e, void *stream) {
+    if (!c || !e) return set_err(FR_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t off = 0;
+    int rc;
+    for (int t = 0; t < NT; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        if (!D.E) return set_err(FR_ERR_ARG, "no RK45 step has been taken on this context");
+        const size_t n = (size_t)D.ne * NV * D.nu;
+        if ((rc = cuda_check(launch_int_to_pub<double>(D.nu, D.ne, D.np, D.E, D.Uacc, s), "error layout")))
+            return rc;
+        if ((rc = cuda_check(cudaMemcpyAsync(e + off, D.Uacc, n * sizeof(double), cudaMemcpyDeviceToHost, s),
+                             "error copy")))
+            return rc;
+        off += n;
+    }
+    return cuda_check(cudaStreamSynchronize(s), "error sync");
+}
+
+int fr_step_rk45_adaptive(fr_ctx *c, double t_span, double atol, double rtol, double *dt, int max_steps,
+                          int64_t *stats, void *stream) {
+    if (!c || !dt || !std::isfinite(t_span) || t_span < 0.0 || !(*dt > 0.0) || !std::isfinite(*dt) ||
+        max_steps < 1 || !(atol >= 0.0) || !(rtol >= 0.0) || !(atol + rtol > 0.0))
+        return set_err(FR_ERR_ARG, "invalid adaptive-step arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    return is_f32(c) ? adaptive_impl<float>(c, t_span, atol, rtol, dt, max_steps, stats, s)
+                     : adaptive_impl<double>(c, t_span, atol, rtol, dt, max_steps, stats, s);
 }
 
 int fr_reduce(fr_ctx *c, double *out, void *stream) {

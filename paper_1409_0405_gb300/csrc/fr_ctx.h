@@ -22,6 +22,9 @@ struct DevType {
     // FP64 in every mode: RK registers, quadrature weights, the reference-flux
     // divergence, and the geometry/operators the set-up evaluates with
     double *U = nullptr, *Uacc = nullptr;   // [nu][V][np]
+    // RK45[2R+]: the embedded error estimate, and the copy of U an adaptive
+    // step restores on rejection (allocated by the first call that needs them)
+    double *E = nullptr, *Ubak = nullptr;   // [nu][V][np]
     double *wJ = nullptr;                   // [nu][np]
     double *Rfs = nullptr;                  // [nu][V][np]
     double *S = nullptr, *invJ = nullptr;   // [nu][9][np], [nu][np]

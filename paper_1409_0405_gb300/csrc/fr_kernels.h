@@ -268,6 +268,16 @@ cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *
 template <typename T>
 cudaError_t launch_rk_2n_update(int nu, int64_t np, const T *R, double *U, double *dU, T *Us, const double *uref,
                                 double a, double b, double dt, int first, cudaStream_t s);
+// RK45[2R+] stage (two registers plus the error register E, which may be
+// null): Us = (U - uref) + c_stage r (last: the new U - uref), U += c_acc r,
+// E = (first ? 0 : E) + c_err r; R [nu][V][np]
+template <typename T>
+cudaError_t launch_rk_2r_update(int nu, int64_t np, const T *R, double *U, double *E, T *Us, const double *uref,
+                                double c_stage, double c_acc, double c_err, int first, int last, cudaStream_t s);
+// per-block partial sums (nblocks x 1) of (E / (atol + rtol |U|))^2 over one
+// type's registers, element columns below ne only
+cudaError_t launch_err_norm_partial(int nu, int64_t ne, int64_t np, const double *U, const double *E, double atol,
+                                    double rtol, double *partial, int nblocks, cudaStream_t s);
 // element-wise double -> float copy
 cudaError_t launch_to_float(int64_t n, const double *src, float *dst, cudaStream_t s);
 // per-block partial integrals (7 per block) of one type's register

@@ -751,6 +751,44 @@ __global__ void k_rk_2n_update(int64_t np, const T *__restrict__ R, double *__re
     Us[idx] = T(u - uref.v[row % V]);
 }
 
+// RK45[2R+] stage (Kennedy, Carpenter & Lewis 2000, two registers) from a
+// stored RHS r:  the next stage input is formed from the solution register
+// before it is advanced, Us = (U - uref) + c_stage r (the last stage: the new
+// U - uref), then U += c_acc r; the error register E accumulates
+// c_err r (E = c_err r at the first stage; E may be null)
+template <typename T>
+__global__ void k_rk_2r_update(int64_t np, const T *__restrict__ R, double *__restrict__ U,
+                               double *__restrict__ E, T *__restrict__ Us, const Uref uref, double c_stage,
+                               double c_acc, double c_err, int first, int last) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    const int row = blockIdx.y;
+    const int64_t idx = (int64_t)row * np + e;
+    const double r = (double)R[idx];
+    const double u = U[idx];
+    const double un = u + c_acc * r;
+    const double ur = uref.v[row % V];
+    U[idx] = un;
+    if (E) E[idx] = (first ? 0.0 : E[idx]) + c_err * r;
+    Us[idx] = last ? T(un - ur) : T((u - ur) + c_stage * r);
+}
+
+// per-block partial sums of (E / (atol + rtol |U|))^2 over the element
+// columns e < ne of one type's [nu][V][np] registers
+__global__ void k_err_norm_partial(int nu, int64_t ne, int64_t np, const double *__restrict__ U,
+                                   const double *__restrict__ E, double atol, double rtol, double *partial) {
+    double acc[1] = {0.0};
+    const int64_t tot = (int64_t)nu * V * np;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = idx / np, e = idx - row * np;
+        if (e >= ne) continue;
+        const double w = E[idx] / (atol + rtol * fabs(U[idx]));
+        acc[0] += w * w;
+    }
+    block_sum_store<1>(acc, partial);
+}
+
 __global__ void k_to_float(int64_t n, const double *__restrict__ src, float *__restrict__ dst) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n) dst[idx] = (float)src[idx];
@@ -881,6 +919,23 @@ cudaError_t launch_rk_2n_update(int nu, int64_t np, const T *R, double *U, doubl
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_rk_2r_update(int nu, int64_t np, const T *R, double *U, double *E, T *Us, const double *uref,
+                                double c_stage, double c_acc, double c_err, int first, int last, cudaStream_t s) {
+    const int64_t n = (int64_t)nu * V * np;
+    if (n == 0) return cudaSuccess;
+    Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
+    k_rk_2r_update<T><<<dim3(blocks_for(np, 256), (unsigned)(nu * V)), 256, 0, s>>>(np, R, U, E, Us, r, c_stage,
+                                                                                    c_acc, c_err, first, last);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_err_norm_partial(int nu, int64_t ne, int64_t np, const double *U, const double *E, double atol,
+                                    double rtol, double *partial, int nblocks, cudaStream_t s) {
+    k_err_norm_partial<<<nblocks, kDiagThreads, 0, s>>>(nu, ne, np, U, E, atol, rtol, partial);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_float(int64_t n, const double *src, float *dst, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_to_float<<<blocks_for(n, 256), 256, 0, s>>>(n, src, dst);
@@ -941,6 +996,8 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
                                              cudaStream_t);                                                  \
     template cudaError_t launch_rk_2n_update<T>(int, int64_t, const T *, double *, double *, T *,                \
                                                 const double *, double, double, double, int, cudaStream_t);  \
+    template cudaError_t launch_rk_2r_update<T>(int, int64_t, const T *, double *, double *, T *,                \
+                                                const double *, double, double, double, int, int, cudaStream_t); \
     template cudaError_t launch_int_to_pub<T>(int, int64_t, int64_t, const T *, double *, cudaStream_t);       \
     template cudaError_t launch_flux_grouped<T>(const FluxItem<T> *, const int64_t *, int, int64_t, const Phys &, \
                                                 int, cudaStream_t, bool);                                     \

@@ -34,7 +34,8 @@ OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
 
 # every entry point declared in include/fr.h
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
-           "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_step_ls", "fr_reduce",
+           "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_step_ls", "fr_step_rk45",
+           "fr_rk45_error", "fr_rk45_get_error", "fr_step_rk45_adaptive", "fr_reduce",
            "fr_diagnostics", "fr_selftest_wait_timeout", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info",
@@ -93,6 +94,14 @@ def load():
     lib.fr_step.argtypes = [vp, C.c_double, C.c_int, vp]
     lib.fr_step_ls.argtypes = [vp, C.c_double, C.c_int, vp]
     lib.fr_step_ls.restype = C.c_int
+    lib.fr_step_rk45.argtypes = [vp, C.c_double, C.c_int, vp]
+    lib.fr_step_rk45.restype = C.c_int
+    lib.fr_rk45_error.argtypes = [vp, C.c_double, C.c_double, vp, vp]
+    lib.fr_rk45_error.restype = C.c_int
+    lib.fr_rk45_get_error.argtypes = [vp, vp, vp]
+    lib.fr_rk45_get_error.restype = C.c_int
+    lib.fr_step_rk45_adaptive.argtypes = [vp, C.c_double, C.c_double, C.c_double, vp, C.c_int, vp, vp]
+    lib.fr_step_rk45_adaptive.restype = C.c_int
     lib.fr_reduce.argtypes = [vp, dp, vp]
     lib.fr_diagnostics.argtypes = [vp, dp, vp]
     lib.fr_selftest_wait_timeout.argtypes = [vp, vp]
@@ -362,6 +371,32 @@ class Context:
     def step_ls(self, dt, nsteps=1, stream=None):
         """Low-storage (2N) five-stage RK4 steps (fr_step_ls)."""
         _check(self._lib.fr_step_ls(self._h, float(dt), int(nsteps), C.c_void_p(stream) if stream else None))
+
+    def step_rk45(self, dt, nsteps=1, stream=None):
+        """Fixed RK45[2R+] steps (fr_step_rk45)."""
+        _check(self._lib.fr_step_rk45(self._h, float(dt), int(nsteps), C.c_void_p(stream) if stream else None))
+
+    def rk45_error(self, atol, rtol, stream=None):
+        """Weighted RMS norm of the last RK45 step's error estimate."""
+        out = C.c_double(0.0)
+        _check(self._lib.fr_rk45_error(self._h, float(atol), float(rtol), C.byref(out),
+                                       C.c_void_p(stream) if stream else None))
+        return out.value
+
+    def rk45_get_error(self, stream=None):
+        """The last RK45 step's error register, public layout."""
+        out = np.empty(self.ndof, dtype=np.float64)
+        _check(self._lib.fr_rk45_get_error(self._h, _dptr(out), C.c_void_p(stream) if stream else None))
+        return out
+
+    def step_rk45_adaptive(self, t_span, dt, atol, rtol, max_steps=100000, stream=None):
+        """Error-controlled RK45[2R+] over t_span: (next dt, accepted, rejected)."""
+        d = C.c_double(float(dt))
+        stats = np.zeros(2, dtype=np.int64)
+        _check(self._lib.fr_step_rk45_adaptive(self._h, float(t_span), float(atol), float(rtol), C.byref(d),
+                                               int(max_steps), stats.ctypes.data_as(C.c_void_p),
+                                               C.c_void_p(stream) if stream else None))
+        return d.value, int(stats[0]), int(stats[1])
 
     def profile(self, enable=True):
         _check(self._lib.fr_profile(self._h, int(bool(enable))))

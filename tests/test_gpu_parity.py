@@ -269,6 +269,27 @@ def test_full_size_boundary_layer_rhs():
     assert math.isfinite(float(err.max()))
 
 
+def test_full_size_boundary_layer_rk4_step():
+    """The full boundary-layer workload (57,600 prisms + 118,800 tets, p = 4,
+    Navier-Stokes, Re = 3900, Ma = 0.2) advanced one RK4 step: the state
+    against the oracle's RK4 step, every value, and the step's increment
+    u_1 - u_0 (which carries all of the arithmetic's error) at the RHS
+    tolerance as well."""
+    m = synth.boundary_layer_box()
+    sol, ctx = make_pair(m, 4, **bl_params())
+    u = state(sol, "bl")
+    dt = sol.dt_cfl(u, 0.1)
+    ctx.set_state(u)
+    ctx.step(dt, 1)
+    got = ctx.get_state()
+    ref = sol.rk4_step(u, dt)
+    err = per_quantity_rel_err(sol, ref, got)
+    inc = per_quantity_rel_err(sol, ref - u, got - u)
+    print("full-size RK4 step: state", err, "increment", inc)
+    assert np.all(err <= TOL), err
+    assert np.all(inc <= TOL), (inc, per_var_rel_err(sol, ref - u, got - u))
+
+
 # ---------------------------------------------------------------------------
 # FR_FP32: operator applications and point-wise work in FP32, RK registers,
 # the reference-flux correction and the reductions in FP64.  Reported against

@@ -368,6 +368,81 @@ int fr_batch_step(fr_batch *b, const double *dt, int nsteps, int batched, void *
 int fr_batch_info(const fr_batch *b, int64_t *out);
 
 /*
+ * ---- Partitioned meshes ---------------------------------------------------
+ * Sec. 2.5: multi-node runs split the mesh into partitions whose ranks
+ * exchange interface data; Sec. 5.2: a mixed mesh is partitioned with
+ * per-type weights hex : pri : tet = 3 : 2 : 1, avoiding partitions with
+ * only a few (fewer than about a thousand) elements of a type.  Here the
+ * partitions of one mesh live on the current device as partition
+ * contexts; per RHS evaluation they exchange, through device-local
+ * buffers, the flux-point states of the cut faces after the interpolation
+ * and (Navier-Stokes) the flux-point gradients after their interpolation.
+ * Every cut interface pair keeps its global data, so the result equals the
+ * unpartitioned mesh's (bit for bit in FP64; see the tests).
+ */
+typedef struct fr_part fr_part; /* opaque; owned by the library */
+
+/*
+ * fr_partition (host only, no GPU): weighted recursive coordinate bisection
+ * of the element centroids into nparts parts.  weights (may be null:
+ * tet 1, prism 2, hex 3, the paper's 1 : 2 : 3) gives the cost of a tet, a
+ * prism and a hex.  part (host, caller-owned, n_tet + n_pri + n_hex
+ * int32) receives each element's partition in public order (tets, then
+ * prisms, then hexes).  Deterministic.
+ * Errors: FR_ERR_ARG (null pointers, nparts < 1, more partitions than
+ * elements, non-positive weights), FR_ERR_MESH (node id out of range).
+ */
+int fr_partition(const fr_mesh *mesh, int nparts, const double *weights, int32_t *part);
+
+/*
+ * fr_part_plan (host only, no GPU): the exchange plan of partition `rank`
+ * for the partition array part (as fr_partition writes it).  A partition's
+ * local element numbering is its elements of each type in increasing
+ * global order.  counts (host, nparts int64): the number of flux points
+ * rank sends to each partition, which equals the number it receives from
+ * it.  send_pts (may be null; sum(counts) x 3 int32): rank's flux points
+ * (etype, local element, flux point), grouped by destination in
+ * increasing order, each group in the order of the mesh's interface pairs.
+ * halo_pts (may be null; sum(counts) x 3 int32): for each of rank's halo
+ * slots, the remote flux point (etype, global element, flux point),
+ * grouped by source in increasing order: slot i of the group from q
+ * receives entry i of q's send list to rank.
+ * Errors: FR_ERR_ARG, FR_ERR_MESH, FR_ERR_NOMEM.
+ */
+int fr_part_plan(const fr_mesh *mesh, int order, int nparts, const int32_t *part, int rank, int64_t *counts,
+                 int32_t *send_pts, int32_t *halo_pts);
+
+/*
+ * fr_part_create: a partitioned mesh on the current device.  part (host,
+ * may be null: fr_partition with the default weights) assigns every
+ * element (public order) to one of nparts partitions; every partition
+ * must hold at least one element.  Other arguments as fr_create.
+ * Errors: as fr_create, and FR_ERR_ARG for an invalid partition.
+ */
+int fr_part_create(const fr_mesh *mesh, int order, const fr_params *params, int nparts, const int32_t *part,
+                   fr_part **out);
+void fr_part_destroy(fr_part *pp);
+/* fr_part_info: out (host, 4 * nparts int64): per partition its tet,
+ * prism and hex counts and its number of halo slots. */
+int fr_part_info(const fr_part *pp, int64_t *out);
+/* fr_part_set_state / fr_part_get_state: host state in the mesh's public
+ * layout (the unpartitioned order); synchronous. */
+int fr_part_set_state(fr_part *pp, const double *u, void *cuda_stream);
+int fr_part_get_state(fr_part *pp, double *u, void *cuda_stream);
+/* fr_part_rhs: as fr_rhs, device arrays in the mesh's public layout; the
+ * first call allocates two state-sized scratch arrays (make it before any
+ * stream capture). */
+int fr_part_rhs(fr_part *pp, const double *u_dev, double *r_dev, void *cuda_stream);
+/* fr_part_step: nsteps classic RK4 steps of every partition, with the
+ * halo exchanges inside each stage; asynchronous. */
+int fr_part_step(fr_part *pp, double dt, int nsteps, void *cuda_stream);
+/* fr_part_reduce: as fr_reduce, summed over the partitions. */
+int fr_part_reduce(fr_part *pp, double *out, void *cuda_stream);
+/* fr_part_launches: kernels launched by the partitioned mesh so far
+ * (partitions' kernels and the halo pack kernels). */
+int fr_part_launches(const fr_part *pp, int64_t *launches);
+
+/*
  * fr_reduce_noalloc: the integrals of fr_reduce for callers that cannot
  * allocate device memory.  The paper has no counterpart; this entry point
  * exists for code that may not call cudaMalloc (a device owned by another

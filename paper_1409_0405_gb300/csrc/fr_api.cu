@@ -141,6 +141,11 @@ FieldsT<T> fields_of(const fr_ctx *c) {
         F.FC[t] = (T *)c->T[t].FC;
         F.np[t] = c->T[t].np;
     }
+    F.UF[HALO] = (const T *)c->UF_h;
+    F.DUF[HALO] = (T *)c->DUF_h;
+    F.GUF[HALO] = (const T *)c->GUF_h;
+    F.FC[HALO] = (T *)c->FC_h;
+    F.np[HALO] = c->nhalo_p;
     return F;
 }
 
@@ -315,10 +320,12 @@ int check_tc(fr_ctx *c) {
     return FR_OK;
 }
 
+// The RHS in three phases, between which a partitioned mesh exchanges its
+// halos: (1) interpolation to the flux points; (2) Navier-Stokes only:
+// common solution, corrected gradient, gradient at the flux points; (3)
+// transformed flux, common normal flux, divergence (+ RK update).
 template <typename T>
-int front_stages(fr_ctx *c, T *const in[NT], cudaStream_t s) {
-    const Phys ph = phys_of(c);
-    const FieldsT<T> F = fields_of<T>(c);
+int phase_interp(fr_ctx *c, T *const in[NT], cudaStream_t s) {
     int rc;
     // 1. interpolate to flux points
     for (int t = 0; t < NT; ++t) {
@@ -326,6 +333,14 @@ int front_stages(fr_ctx *c, T *const in[NT], cudaStream_t s) {
         const GemmArgsT<T> g = args_m0<T>(c, t, in[t]);
         if ((rc = cuda_check(launch(c, K_M0, s, [&] { return op_gemm<T>(c, t, 0, g, s); }), "gemm M0"))) return rc;
     }
+    return FR_OK;
+}
+
+template <typename T>
+int phase_grad(fr_ctx *c, T *const in[NT], cudaStream_t s) {
+    const Phys ph = phys_of(c);
+    const FieldsT<T> F = fields_of<T>(c);
+    int rc;
     if (c->prm.viscous) {
         // 2. common solution and jumps
         if ((rc = cuda_check(launch(c, K_COMMON_SOL, s,
@@ -366,11 +381,16 @@ int front_stages(fr_ctx *c, T *const in[NT], cudaStream_t s) {
 }
 
 template <typename T>
-int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
+int front_stages(fr_ctx *c, T *const in[NT], cudaStream_t s) {
+    int rc = phase_interp<T>(c, in, s);
+    return rc ? rc : phase_grad<T>(c, in, s);
+}
+
+template <typename T>
+int phase_div(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
     const Phys ph = phys_of(c);
     const FieldsT<T> F = fields_of<T>(c);
     int rc;
-    if ((rc = front_stages<T>(c, in, s))) return rc;
     // 5. transformed flux at solution points (done by front_stages for
     // Navier-Stokes in the FP32-storage modes)
     for (int t = 0; t < NT && !(is_f32(c) && c->prm.viscous); ++t) {
@@ -423,6 +443,12 @@ int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) 
     return FR_OK;
 }
 
+template <typename T>
+int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
+    int rc = front_stages<T>(c, in, s);
+    return rc ? rc : phase_div<T>(c, in, rk, s);
+}
+
 int64_t ndof_of(const fr_ctx *c) {
     int64_t n = 0;
     for (int t = 0; t < NT; ++t)
@@ -430,8 +456,18 @@ int64_t ndof_of(const fr_ctx *c) {
     return n;
 }
 
-int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c) {
-    if (!mesh || !prm) return set_err(FR_ERR_ARG, "null mesh or params");
+int check_params(int order, const fr_params *prm) {
+    if (!prm) return set_err(FR_ERR_ARG, "null params");
+    if (order < 1 || order > 4) return set_err(FR_ERR_ARG, "order must be in 1..4");
+    if (prm->precision < FR_FP64 || prm->precision > FR_TF32X3)
+        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64, FR_FP32, FR_BF16X3 or FR_TF32X3");
+    if (!(prm->gamma > 1.0) || prm->mu < 0.0 || (prm->viscous && !(prm->prandtl > 0.0)))
+        return set_err(FR_ERR_ARG, "invalid gas parameters");
+    return FR_OK;
+}
+
+int host_setup(const fr_mesh *mesh, int order, HostSetup &h) {
+    if (!mesh) return set_err(FR_ERR_ARG, "null mesh");
     if (order < 1 || order > 4) return set_err(FR_ERR_ARG, "order must be in 1..4");
     if (mesh->n_nodes <= 0 || !mesh->xyz) return set_err(FR_ERR_ARG, "mesh has no nodes");
     if (mesh->n_tet < 0 || mesh->n_pri < 0 || mesh->n_hex < 0 || mesh->n_bface < 0)
@@ -442,33 +478,35 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         return set_err(FR_ERR_ARG, "null connectivity array");
     if (mesh->n_tet > (1LL << 30) || mesh->n_pri > (1LL << 30) || mesh->n_hex > (1LL << 30))
         return set_err(FR_ERR_ARG, "element count too large");
-    if (prm->precision < FR_FP64 || prm->precision > FR_TF32X3)
-        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64, FR_FP32, FR_BF16X3 or FR_TF32X3");
-    if (!(prm->gamma > 1.0) || prm->mu < 0.0 || (prm->viscous && !(prm->prandtl > 0.0)))
-        return set_err(FR_ERR_ARG, "invalid gas parameters");
-    c->prm = *prm;
-    c->order = order;
-
+    if (order < 1 || order > 4) return set_err(FR_ERR_ARG, "order must be in 1..4");
     std::string err;
-    RefOps ops[NT];
     const int64_t ne_in[NT] = {mesh->n_tet, mesh->n_pri, mesh->n_hex};
     for (int t = 0; t < NT; ++t) {
         if (ne_in[t] == 0) continue;  // operators only for the types present
-        int rc = build_ref_ops(t, order, ops[t], err);
+        int rc = build_ref_ops(t, order, h.ops[t], err);
         if (rc) return set_err(rc, err);
     }
-    TypeGeo geo[NT];
-    int rc = build_geometry(mesh, ops, geo, err);
+    int rc = build_geometry(mesh, h.ops, h.geo, err);
     if (rc) return set_err(rc, err);
-    Faces faces;
-    rc = build_faces(mesh, ops, geo, faces, err);
+    rc = build_faces(mesh, h.ops, h.geo, h.faces, err);
     if (rc) return set_err(rc, err);
+    return FR_OK;
+}
 
+// Device state of a context from its host set-up: per-type geometry geo,
+// the interface pairs and boundary points of `faces`, and nhalo halo slots
+// (a partition of a partitioned mesh; 0 otherwise).  ops holds the
+// operators of every type present in geo.
+int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT], const TypeGeo geo[NT],
+                 const Faces &faces, int64_t nhalo) {
+    c->prm = *prm;
+    c->order = order;
+    int rc;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
         return set_err(FR_ERR_CUDA, "no usable CUDA device");
     }
-    const int64_t ne[NT] = {mesh->n_tet, mesh->n_pri, mesh->n_hex};
+    const int64_t ne[NT] = {geo[0].ne, geo[1].ne, geo[2].ne};
     for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         D.present = ne[t] > 0;
@@ -596,6 +634,17 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
         }
         D.xu = G.xu;
     }
+    if (nhalo > 0) {
+        const size_t es = prm->precision != FR_FP64 ? sizeof(float) : sizeof(double);
+        c->nhalo = nhalo;
+        c->nhalo_p = (nhalo + kPad - 1) / kPad * kPad;
+        const size_t sh = (size_t)NV * c->nhalo_p;
+        if ((rc = dev_alloc_bytes(c, &c->UF_h, sh * es)) || (rc = dev_alloc_bytes(c, &c->FC_h, sh * es)))
+            return rc;
+        if (prm->viscous &&
+            ((rc = dev_alloc_bytes(c, &c->DUF_h, sh * es)) || (rc = dev_alloc_bytes(c, &c->GUF_h, 3 * sh * es))))
+            return rc;
+    }
     c->npairs = (int64_t)faces.ta.size();
     c->nbnd = (int64_t)faces.bt.size();
     if ((rc = upload(c, &c->ta, faces.ta)) || (rc = upload(c, &c->fa, faces.fa)) || (rc = upload(c, &c->ea, faces.ea)) ||
@@ -664,6 +713,12 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
             F.FC[t] = tFC[t];
             F.np[t] = c->T[t].np;
         }
+        // the remote side of a cut pair (FP64 here, the context's precision)
+        F.UF[HALO] = nullptr;
+        F.DUF[HALO] = nullptr;
+        F.GUF[HALO] = nullptr;
+        F.FC[HALO] = (double *)c->FC_h;
+        F.np[HALO] = c->nhalo_p;
         rc = FR_OK;
         for (int t = 0; t < NT && !rc; ++t) {
             DevType &D = c->T[t];
@@ -709,6 +764,15 @@ int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c)
     if ((rc = dev_alloc(c, &c->diag, (size_t)kDiagBlocks * (2 + 6) + 8))) return rc;
     if ((rc = dev_alloc(c, &c->tc_err, 1))) return rc;
     return cuda_check(cudaDeviceSynchronize(), "fr_create sync");
+}
+
+int create_impl(const fr_mesh *mesh, int order, const fr_params *prm, fr_ctx *c) {
+    int rc;
+    if (!mesh) return set_err(FR_ERR_ARG, "null mesh or params");
+    if ((rc = check_params(order, prm))) return rc;
+    HostSetup h;
+    if ((rc = host_setup(mesh, order, h))) return rc;
+    return device_setup(c, order, prm, h.ops, h.geo, h.faces, 0);
 }
 
 template <typename T>
@@ -999,6 +1063,12 @@ template int step_2n_impl<double>(fr_ctx *, double, int, cudaStream_t);
 template int step_impl<float>(fr_ctx *, double, int, cudaStream_t);
 template int rhs_public<float>(fr_ctx *, const double *, double *, cudaStream_t);
 template int rhs_public<double>(fr_ctx *, const double *, double *, cudaStream_t);
+template int phase_interp<float>(fr_ctx *, float *const[NT], cudaStream_t);
+template int phase_interp<double>(fr_ctx *, double *const[NT], cudaStream_t);
+template int phase_grad<float>(fr_ctx *, float *const[NT], cudaStream_t);
+template int phase_grad<double>(fr_ctx *, double *const[NT], cudaStream_t);
+template int phase_div<float>(fr_ctx *, float *const[NT], const RKStage *, cudaStream_t);
+template int phase_div<double>(fr_ctx *, double *const[NT], const RKStage *, cudaStream_t);
 template int front_stages<float>(fr_ctx *, float *const[NT], cudaStream_t);
 template int front_stages<double>(fr_ctx *, double *const[NT], cudaStream_t);
 template int step_impl<double>(fr_ctx *, double, int, cudaStream_t);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/fr.h"
+#include "fr_internal.h"
 #include "fr_kernels.h"
 
 namespace fr {
@@ -72,6 +73,12 @@ struct fr_ctx {
     double *bn = nullptr, *bmag = nullptr;
     signed char *sgn = nullptr;  // LDG switch per pair
     float *nrm_f = nullptr, *maga_f = nullptr, *magb_f = nullptr, *bn_f = nullptr, *bmag_f = nullptr;
+    // partition of a partitioned mesh: halo slots (other partitions' flux
+    // points on cut interfaces), padded to nhalo_p, in the RHS arithmetic
+    // type: UF_h [V][nhalo_p], GUF_h [3][V][nhalo_p] (received), DUF_h and
+    // FC_h (scratch for the face kernels' writes to the remote side)
+    int64_t nhalo = 0, nhalo_p = 0;
+    void *UF_h = nullptr, *GUF_h = nullptr, *DUF_h = nullptr, *FC_h = nullptr;
     double *red = nullptr;  // reduction partials + result
     double *bw = nullptr;    // face weight of each boundary flux point
     double *diag = nullptr;  // diagnostics partials + result
@@ -159,6 +166,19 @@ int step_impl(fr_ctx *c, double dt, int nsteps, cudaStream_t s);
 // one RHS on public-layout device arrays (FP64 in and out)
 template <typename T>
 int rhs_public(fr_ctx *c, const double *u_dev, double *r_dev, cudaStream_t s);
+// the three phases of one RHS (see fr_api.cu): interpolation; common
+// solution and gradients (Navier-Stokes; nothing for Euler); flux, common
+// flux and divergence (with the fused RK4 update if rk is non-null)
+template <typename T>
+int phase_interp(fr_ctx *c, T *const in[NT], cudaStream_t s);
+template <typename T>
+int phase_grad(fr_ctx *c, T *const in[NT], cudaStream_t s);
+template <typename T>
+int phase_div(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s);
+int check_params(int order, const fr_params *prm);
+int host_setup(const fr_mesh *mesh, int order, HostSetup &h);
+int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT], const TypeGeo geo[NT],
+                 const Faces &faces, int64_t nhalo);
 // stages 1-4 of the RHS (interpolation and, for Navier-Stokes, the
 // corrected gradient at solution and flux points) on the stage input
 template <typename T>

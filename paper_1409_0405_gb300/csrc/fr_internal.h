@@ -70,6 +70,13 @@ int build_geometry(const fr_mesh *mesh, const RefOps ops[NT], TypeGeo geo[NT],
 int build_faces(const fr_mesh *mesh, const RefOps ops[NT], const TypeGeo geo[NT],
                 Faces &faces, std::string &err);
 
+// host set-up of a mesh: operators of the types present, geometry, faces
+struct HostSetup {
+    RefOps ops[NT];
+    TypeGeo geo[NT];
+    Faces faces;
+};
+
 // L2 projection between the spaces of orders p_from and p_to on one
 // reference element, as a matrix (nu_to x nu_from, row-major) on
 // solution-point values.

@@ -150,14 +150,22 @@ struct Phys {
     double uref[5];
 };
 
-// Per-type field pointers (index 0 tet, 1 prism); nullptr for an absent type.
+// Index of the halo pseudo-type: in a partition of a partitioned mesh, an
+// interface pair whose other side lies in another partition refers to that
+// side as (HALO, flux point 0, halo slot).  The halo arrays hold the other
+// partition's flux-point values ([V][np] and [3][V][np] with one "flux
+// point"); what the face kernels write to the halo side lands in scratch.
+constexpr int HALO = NT;
+
+// Per-type field pointers (index 0 tet, 1 prism, 2 hex, HALO the halo);
+// nullptr for an absent type.
 template <typename T>
 struct FieldsT {
-    const T *UF[NT];   // [nf][V][np]
-    T *DUF[NT];        // [nf][V][np]
-    const T *GUF[NT];  // [nf][3][V][np]
-    T *FC[NT];         // [nf][V][np]
-    int64_t np[NT];
+    const T *UF[NT + 1];   // [nf][V][np]
+    T *DUF[NT + 1];        // [nf][V][np]
+    const T *GUF[NT + 1];  // [nf][3][V][np]
+    T *FC[NT + 1];         // [nf][V][np]
+    int64_t np[NT + 1];
 };
 using Fields = FieldsT<double>;
 

@@ -41,7 +41,9 @@ EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info",
            "fr_transfer", "fr_transfer_state", "fr_closure_features", "fr_closure_sample",
            "fr_closure_set", "fr_mlp_nparams", "fr_mlp_workspace", "fr_mlp_forward", "fr_mlp_grad",
-           "fr_mlp_adam")
+           "fr_mlp_adam", "fr_partition", "fr_part_plan", "fr_part_create", "fr_part_destroy",
+           "fr_part_info", "fr_part_set_state", "fr_part_get_state", "fr_part_rhs", "fr_part_step",
+           "fr_part_reduce", "fr_part_launches")
 KCLASSES = ("M0", "common_solution", "grad", "M0_grad", "flux", "common_flux", "div", "closure")
 
 
@@ -136,6 +138,22 @@ def load():
     lib.fr_mlp_adam.argtypes = [C.c_int64, vp, vp, vp, vp, C.c_int, C.c_float, vp]
     for name in ("fr_transfer", "fr_transfer_state", "fr_closure_features", "fr_closure_sample",
                  "fr_closure_set", "fr_mlp_forward", "fr_mlp_grad", "fr_mlp_adam"):
+        getattr(lib, name).restype = C.c_int
+    i32p = C.POINTER(C.c_int32)
+    lib.fr_partition.argtypes = [C.POINTER(FRMesh), C.c_int, dp, i32p]
+    lib.fr_part_plan.argtypes = [C.POINTER(FRMesh), C.c_int, C.c_int, i32p, C.c_int, i64p, i32p, i32p]
+    lib.fr_part_create.argtypes = [C.POINTER(FRMesh), C.c_int, C.POINTER(FRParams), C.c_int, i32p, C.POINTER(vp)]
+    lib.fr_part_destroy.argtypes = [vp]
+    lib.fr_part_destroy.restype = None
+    lib.fr_part_info.argtypes = [vp, i64p]
+    lib.fr_part_set_state.argtypes = [vp, dp, vp]
+    lib.fr_part_get_state.argtypes = [vp, dp, vp]
+    lib.fr_part_rhs.argtypes = [vp, vp, vp, vp]
+    lib.fr_part_step.argtypes = [vp, C.c_double, C.c_int, vp]
+    lib.fr_part_reduce.argtypes = [vp, dp, vp]
+    lib.fr_part_launches.argtypes = [vp, i64p]
+    for name in ("fr_partition", "fr_part_plan", "fr_part_create", "fr_part_info", "fr_part_set_state",
+                 "fr_part_get_state", "fr_part_rhs", "fr_part_step", "fr_part_reduce", "fr_part_launches"):
         getattr(lib, name).restype = C.c_int
     lib.fr_strerror.argtypes = [C.c_int]
     lib.fr_strerror.restype = C.c_char_p
@@ -519,3 +537,105 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# partitioned meshes
+# ---------------------------------------------------------------------------
+def _i32p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def partition(mesh, nparts, weights=None):
+    """fr_partition (host only): partition of every element, public order."""
+    lib = load()
+    keep = []
+    m = _fr_mesh(mesh, keep)
+    n = m.n_tet + m.n_pri + m.n_hex
+    out = np.empty(n, dtype=np.int32)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    _check(lib.fr_partition(C.byref(m), int(nparts), _dptr(w) if w is not None else None, _i32p(out)))
+    return out
+
+
+def part_plan(mesh, order, part, rank):
+    """fr_part_plan (host only): (counts, send_pts, halo_pts) of one rank."""
+    lib = load()
+    keep = []
+    m = _fr_mesh(mesh, keep)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    nparts = int(part.max()) + 1
+    counts = np.zeros(nparts, dtype=np.int64)
+    _check(lib.fr_part_plan(C.byref(m), int(order), nparts, _i32p(part), int(rank),
+                            counts.ctypes.data_as(C.POINTER(C.c_int64)), None, None))
+    tot = int(counts.sum())
+    send = np.zeros((tot, 3), dtype=np.int32)
+    halo = np.zeros((tot, 3), dtype=np.int32)
+    _check(lib.fr_part_plan(C.byref(m), int(order), nparts, _i32p(part), int(rank),
+                            counts.ctypes.data_as(C.POINTER(C.c_int64)), _i32p(send), _i32p(halo)))
+    return counts, send, halo
+
+
+class PartContext:
+    """One fr_part: a mesh split into partitions on the current GPU."""
+
+    def __init__(self, mesh, order, nparts, part=None, **params):
+        lib = load()
+        self._lib = lib
+        prm = default_params(**params)
+        self.params = prm
+        keep = []
+        m = _fr_mesh(mesh, keep)
+        p = _fr_params(prm)
+        h = C.c_void_p()
+        pa = None if part is None else np.ascontiguousarray(part, dtype=np.int32)
+        _check(lib.fr_part_create(C.byref(m), int(order), C.byref(p), int(nparts),
+                                  _i32p(pa) if pa is not None else None, C.byref(h)))
+        self._h = h
+        self.nparts = int(nparts)
+        info = np.zeros(4 * self.nparts, dtype=np.int64)
+        _check(lib.fr_part_info(h, info.ctypes.data_as(C.POINTER(C.c_int64))))
+        self.info = info.reshape(self.nparts, 4)   # tets, prisms, hexes, halo slots
+        # the unpartitioned public layout's length
+        self.ndof = int(sum(self.info[:, t].sum() * 5 * _nupts(t, order) for t in range(3)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fr_part_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, u, stream=None):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        _check(self._lib.fr_part_set_state(self._h, _dptr(u), C.c_void_p(stream) if stream else None))
+
+    def get_state(self, stream=None):
+        out = np.empty(self.ndof, dtype=np.float64)
+        _check(self._lib.fr_part_get_state(self._h, _dptr(out), C.c_void_p(stream) if stream else None))
+        return out
+
+    def rhs(self, u_ptr, r_ptr, stream=None):
+        _check(self._lib.fr_part_rhs(self._h, C.c_void_p(u_ptr), C.c_void_p(r_ptr),
+                                     C.c_void_p(stream) if stream else None))
+
+    def step(self, dt, nsteps=1, stream=None):
+        _check(self._lib.fr_part_step(self._h, float(dt), int(nsteps), C.c_void_p(stream) if stream else None))
+
+    def reduce(self, stream=None):
+        out = np.empty(7, dtype=np.float64)
+        _check(self._lib.fr_part_reduce(self._h, _dptr(out), C.c_void_p(stream) if stream else None))
+        return out
+
+    def launches(self):
+        n = C.c_int64()
+        _check(self._lib.fr_part_launches(self._h, C.byref(n)))
+        return n.value
+
+
+def _nupts(etype, p):
+    return {0: (p + 1) * (p + 2) * (p + 3) // 6, 1: (p + 1) ** 2 * (p + 2) // 2, 2: (p + 1) ** 3}[etype]

@@ -185,6 +185,19 @@ int fr_rhs(fr_ctx *ctx, const double *u_dev, double *r_dev, void *cuda_stream);
 int fr_step(fr_ctx *ctx, double dt, int nsteps, void *cuda_stream);
 
 /*
+ * Blow-up detection of the steppers.  Every fr_step, fr_step_ls and
+ * fr_step_rk45 call with nsteps > 0 ends with a state check on the device
+ * that sets a flag when any solution value is non-finite or any point has a
+ * non-positive density or pressure.  The flag lives in mapped pinned host
+ * memory: the next stepping call reads it on entry, without synchronising,
+ * and returns FR_ERR_NONFINITE (doing nothing) once a completed earlier call
+ * has set it.  fr_check synchronises cuda_stream and returns
+ * FR_ERR_NONFINITE if the flag is set (FR_ERR_TIMEOUT if a tensor-core
+ * kernel gave up a bounded wait, else FR_OK).  fr_set_state clears the flag.
+ */
+int fr_check(fr_ctx *ctx, void *cuda_stream);
+
+/*
  * fr_step_ls: nsteps steps of the five-stage fourth-order low-storage
  * (2N) Runge-Kutta scheme of Carpenter & Kennedy (1994) on the internal
  * register: per stage dU <- A_i dU + dt R(U), U <- U + B_i dU (the paper
@@ -319,9 +332,11 @@ int fr_operator(int etype, int order, int which, double *out, int64_t *rows, int
  * Classes: 0 M0 interpolation, 1 common solution, 2 corrected gradient,
  * 3 M0 on gradients, 4 point-wise flux, 5 common normal flux,
  * 6 divergence + correction (+ RK update), 7 learned closure (features,
- * network, correction; 8 launches per element type).
+ * network, correction; 8 launches per element type), 8 the state check
+ * that ends every fr_step / fr_step_ls / fr_step_rk45 call (one launch per
+ * element type).
  */
-#define FR_NKCLASS 8
+#define FR_NKCLASS 9
 int fr_profile(fr_ctx *ctx, int enable);
 int fr_profile_read(fr_ctx *ctx, double *ms, int64_t *count, int64_t *launches);
 
@@ -441,6 +456,21 @@ int fr_part_reduce(fr_part *pp, double *out, void *cuda_stream);
 /* fr_part_launches: kernels launched by the partitioned mesh so far
  * (partitions' kernels and the halo pack kernels). */
 int fr_part_launches(const fr_part *pp, int64_t *launches);
+
+/*
+ * ---- Allocation-failure injection (tests) ----------------------------------
+ * Every device allocation the library makes is counted.
+ * fr_debug_fail_alloc(k): the k-th device allocation after this call fails
+ * as if the device were out of memory (k = 0: none fails), so a test can
+ * drive each FR_ERR_NOMEM path of fr_create, fr_batch_create and
+ * fr_part_create.  fr_debug_alloc_stats: out[0] = device allocations
+ * attempted since the last fr_debug_fail_alloc, out[1] = the library's live
+ * device allocations (which must return to their earlier value when a
+ * failed creation has freed what it took).  Process-wide, not thread-safe
+ * against concurrent creations.
+ */
+int fr_debug_fail_alloc(int64_t k);
+int fr_debug_alloc_stats(int64_t *out);
 
 /*
  * fr_reduce_noalloc: the integrals of fr_reduce for callers that cannot

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -53,6 +54,28 @@ using namespace fr::api;
 namespace fr {
 namespace api {
 
+// Every device allocation of the engine goes through dev_malloc/dev_free,
+// which count the live allocations and can be told to fail the k-th
+// allocation from now (fr_debug_fail_alloc), so that tests reach every
+// FR_ERR_NOMEM path of the set-up code and check that nothing leaks.
+std::atomic<int64_t> g_fail_at{0}, g_alloc_seen{0}, g_live{0};
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    const int64_t k = ++g_alloc_seen;
+    if (g_fail_at.load() > 0 && k == g_fail_at.load()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ++g_live;
+    return e;
+}
+
+void dev_free(void *p) {
+    if (!p) return;
+    if (cudaFree(p) == cudaSuccess) --g_live;
+}
+
 constexpr int64_t kPad = 32;
 constexpr int kDiagBlocks = 304;  // blocks of the diagnostics reductions (2 per SM)
 
@@ -61,7 +84,7 @@ int dev_alloc(fr_ctx *c, T **p, size_t count) {
     *p = nullptr;
     if (count == 0) return FR_OK;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    cudaError_t e = dev_malloc(&q, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(FR_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -76,7 +99,7 @@ int dev_alloc(fr_ctx *c, T **p, size_t count) {
 int dev_alloc_bytes(fr_ctx *c, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return FR_OK;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = dev_malloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -449,6 +472,43 @@ int rhs_internal(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) 
     return rc ? rc : phase_div<T>(c, in, rk, s);
 }
 
+int num_sms(int device) {
+    static std::atomic<int> cache[64];
+    if (device < 0 || device >= 64) device = 0;
+    int n = cache[device].load();
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 1;
+    }
+    cache[device] = n;
+    return n;
+}
+
+int step_guard(const fr_ctx *c) {
+    if (c->nf_host && *(volatile const int *)c->nf_host)
+        return set_err(FR_ERR_NONFINITE,
+                       "an earlier step left a non-finite or non-physical state (fr_set_state clears this)");
+    return FR_OK;
+}
+
+int step_check(fr_ctx *c, cudaStream_t s) {
+    if (!c->nf_dev) return FR_OK;
+    const int nb = 2 * num_sms(c->device);
+    for (int t = 0; t < NT; ++t) {
+        DevType &D = c->T[t];
+        if (!D.present) continue;
+        int rc = cuda_check(launch(c, K_CHECK, s,
+                                   [&] {
+                                       return launch_state_check(D.nu, D.ne, D.np, D.U, c->prm.gamma, c->nf_dev, nb,
+                                                                 s);
+                                   }),
+                            "state check");
+        if (rc) return rc;
+    }
+    return FR_OK;
+}
+
 int64_t ndof_of(const fr_ctx *c) {
     int64_t n = 0;
     for (int t = 0; t < NT; ++t)
@@ -693,11 +753,11 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
             if ((rc = dev_alloc(c, &D.Rfs, (size_t)D.nu * NV * D.np))) return rc;
             if (f32) {
                 const size_t su = (size_t)D.nu * NV * D.np, sf = (size_t)D.nf * NV * D.np;
-                if (cudaMalloc(&tFT[t], 3 * su * sizeof(double)) != cudaSuccess ||
-                    cudaMalloc(&tFC[t], sf * sizeof(double)) != cudaSuccess) {
+                if (dev_malloc((void **)&tFT[t], 3 * su * sizeof(double)) != cudaSuccess ||
+                    dev_malloc((void **)&tFC[t], sf * sizeof(double)) != cudaSuccess) {
                     cudaGetLastError();
-                    for (double *q : tFT) cudaFree(q);
-                    for (double *q : tFC) cudaFree(q);
+                    for (double *q : tFT) dev_free(q);
+                    for (double *q : tFC) dev_free(q);
                     return set_err(FR_ERR_NOMEM, "set-up scratch");
                 }
             } else {
@@ -749,20 +809,28 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
         if (f32) {
             cudaDeviceSynchronize();
             for (int t = 0; t < NT; ++t) {
-                cudaFree(tFT[t]);
-                cudaFree(tFC[t]);
+                dev_free(tFT[t]);
+                dev_free(tFC[t]);
             }
         }
         if (rc) return rc;
     }
     int nbt = 0;
     for (int t = 0; t < NT; ++t) {
-        c->red_blocks[t] = c->T[t].present ? 152 * 2 : 0;
+        c->red_blocks[t] = c->T[t].present ? 2 * num_sms(c->device) : 0;
         nbt += c->red_blocks[t];
     }
     if ((rc = dev_alloc(c, &c->red, (size_t)nbt * 7 + 8))) return rc;
     if ((rc = dev_alloc(c, &c->diag, (size_t)kDiagBlocks * (2 + 6) + 8))) return rc;
     if ((rc = dev_alloc(c, &c->tc_err, 1))) return rc;
+    if (cudaHostAlloc((void **)&c->nf_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        c->nf_host = nullptr;
+        return set_err(FR_ERR_NOMEM, "pinned status flag");
+    }
+    *c->nf_host = 0;
+    if ((rc = cuda_check(cudaHostGetDevicePointer((void **)&c->nf_dev, c->nf_host, 0), "status flag address")))
+        return rc;
     return cuda_check(cudaDeviceSynchronize(), "fr_create sync");
 }
 
@@ -1135,7 +1203,8 @@ int fr_create(const fr_mesh *mesh, int order, const fr_params *params, fr_ctx **
 
 void fr_destroy(fr_ctx *c) {
     if (!c) return;
-    for (void *p : c->allocs) cudaFree(p);
+    for (void *p : c->allocs) dev_free(p);
+    if (c->nf_host) cudaFreeHost(c->nf_host);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
@@ -1222,7 +1291,9 @@ int fr_set_state(fr_ctx *c, const double *u, void *stream) {
             return rc;
         off += n;
     }
-    return cuda_check(cudaStreamSynchronize(s), "set_state sync");
+    const int rc = cuda_check(cudaStreamSynchronize(s), "set_state sync");
+    if (!rc && c->nf_host) *(volatile int *)c->nf_host = 0;  // a new state: no earlier blow-up applies
+    return rc;
 }
 
 int fr_get_state(fr_ctx *c, double *u, void *stream) {
@@ -1254,20 +1325,37 @@ int fr_rhs(fr_ctx *c, const double *u_dev, double *r_dev, void *stream) {
 
 int fr_step(fr_ctx *c, double dt, int nsteps, void *stream) {
     if (!c || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
+    int rc;
+    if ((rc = step_guard(c))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    return is_f32(c) ? step_impl<float>(c, dt, nsteps, s) : step_impl<double>(c, dt, nsteps, s);
+    rc = is_f32(c) ? step_impl<float>(c, dt, nsteps, s) : step_impl<double>(c, dt, nsteps, s);
+    return (rc || nsteps == 0) ? rc : step_check(c, s);
 }
 
 int fr_step_ls(fr_ctx *c, double dt, int nsteps, void *stream) {
-    if (!c || nsteps < 0 || !(dt == dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
+    if (!c || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
+    int rc;
+    if ((rc = step_guard(c))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    return is_f32(c) ? step_2n_impl<float>(c, dt, nsteps, s) : step_2n_impl<double>(c, dt, nsteps, s);
+    rc = is_f32(c) ? step_2n_impl<float>(c, dt, nsteps, s) : step_2n_impl<double>(c, dt, nsteps, s);
+    return (rc || nsteps == 0) ? rc : step_check(c, s);
+}
+
+int fr_check(fr_ctx *c, void *stream) {
+    if (!c) return set_err(FR_ERR_ARG, "null context");
+    int rc;
+    if ((rc = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "check sync"))) return rc;
+    if ((rc = check_tc(c))) return rc;
+    return step_guard(c);
 }
 
 int fr_step_rk45(fr_ctx *c, double dt, int nsteps, void *stream) {
     if (!c || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
+    int rc;
+    if ((rc = step_guard(c))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    return is_f32(c) ? step_2r_impl<float>(c, dt, nsteps, s) : step_2r_impl<double>(c, dt, nsteps, s);
+    rc = is_f32(c) ? step_2r_impl<float>(c, dt, nsteps, s) : step_2r_impl<double>(c, dt, nsteps, s);
+    return (rc || nsteps == 0) ? rc : step_check(c, s);
 }
 
 int fr_rk45_error(fr_ctx *c, double atol, double rtol, double *norm, void *stream) {
@@ -1352,6 +1440,20 @@ int fr_selftest_wait_timeout(fr_ctx *c, void *stream) {
     // clear the status so that the context stays usable
     if ((rc = cuda_check(cudaMemset(c->tc_err, 0, sizeof(int)), "self-test reset"))) return rc;
     if (!timed_out) return set_err(FR_ERR_CUDA, "the withheld loads did not end in a reported timeout");
+    return FR_OK;
+}
+
+int fr_debug_fail_alloc(int64_t k) {
+    if (k < 0) return set_err(FR_ERR_ARG, "k must be >= 0");
+    g_alloc_seen = 0;
+    g_fail_at = k;
+    return FR_OK;
+}
+
+int fr_debug_alloc_stats(int64_t *out) {
+    if (!out) return set_err(FR_ERR_ARG, "null argument");
+    out[0] = g_alloc_seen.load();
+    out[1] = g_live.load();
     return FR_OK;
 }
 

@@ -53,7 +53,7 @@ struct Segs {
 };
 
 int dev_put(void **p, const void *src, size_t bytes) {
-    if (!*p && cudaMalloc(p, bytes) != cudaSuccess) {
+    if (!*p && dev_malloc(p, bytes) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return set_err(FR_ERR_NOMEM, "batch work-list allocation");
@@ -125,6 +125,9 @@ struct BatchImpl : BatchBase {
         if (dev_put((void **)&d.off, sp.off.data(), sizeof(int) * sp.off.size()) ||
             dev_put((void **)&d.cols, sp.cols.data(), sizeof(int) * sp.cols.size()) ||
             dev_put((void **)&d.vals, v.data(), sizeof(T) * v.size())) {
+            dev_free(d.off);
+            dev_free(d.cols);
+            dev_free(d.vals);
             d = SpDev();
             return d;
         }
@@ -135,24 +138,24 @@ struct BatchImpl : BatchBase {
 
     ~BatchImpl() override {
         for (auto &kv : sp_cache) {
-            cudaFree(kv.second.off);
-            cudaFree(kv.second.cols);
-            cudaFree(kv.second.vals);
+            dev_free(kv.second.off);
+            dev_free(kv.second.cols);
+            dev_free(kv.second.vals);
         }
         auto fg = [](Group<T> &g) {
-            cudaFree(g.d);
-            cudaFree(g.begin);
+            dev_free(g.d);
+            dev_free(g.begin);
         };
         fg(m0);
         fg(grad);
         fg(m0g);
         for (auto &g : div) fg(g);
-        cudaFree(flux.d);
-        cudaFree(flux.begin);
-        cudaFree(face.d);
-        cudaFree(face.begin);
-        cudaFree(center.d);
-        cudaFree(center.begin);
+        dev_free(flux.d);
+        dev_free(flux.begin);
+        dev_free(face.d);
+        dev_free(face.begin);
+        dev_free(center.d);
+        dev_free(center.begin);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
@@ -500,8 +503,8 @@ struct BatchImpl : BatchBase {
             face.grid = bg;
         }
         if ((rc = tune_group(dv, s))) {
-            cudaFree(dv.d);
-            cudaFree(dv.begin);
+            dev_free(dv.d);
+            dev_free(dv.begin);
             return rc;
         }
         for (auto &g : div) {
@@ -509,8 +512,8 @@ struct BatchImpl : BatchBase {
             g.grid = dv.grid;
             if (!g.h.empty() && (rc = upload_group(g))) break;
         }
-        cudaFree(dv.d);
-        cudaFree(dv.begin);
+        dev_free(dv.d);
+        dev_free(dv.begin);
         if (rc) return rc;
         // force a new capture with the tuned shapes
         if (exec) {

@@ -83,6 +83,11 @@ struct fr_ctx {
     double *bw = nullptr;    // face weight of each boundary flux point
     double *diag = nullptr;  // diagnostics partials + result
     int *tc_err = nullptr;  // set by a tensor-core kernel whose bounded wait gave up
+    // set (to 1) by the state check that ends every fr_step call when the
+    // solution has a non-finite value or a non-positive density/pressure:
+    // mapped pinned host memory, so the next fr_step reads it without a
+    // synchronisation (nf_dev is its device address)
+    int *nf_host = nullptr, *nf_dev = nullptr;
     int red_blocks[fr::NT] = {};
     std::vector<void *> allocs;
     // launch accounting: count of kernel launches, and (when profiling is
@@ -103,7 +108,7 @@ struct fr_ctx {
 namespace fr {
 namespace api {
 
-enum KClass { K_M0 = 0, K_COMMON_SOL, K_GRAD, K_M0_GRAD, K_FLUX, K_COMMON_FLUX, K_DIV, K_CLOSURE, K_NCLASS };
+enum KClass { K_M0 = 0, K_COMMON_SOL, K_GRAD, K_M0_GRAD, K_FLUX, K_COMMON_FLUX, K_DIV, K_CLOSURE, K_CHECK, K_NCLASS };
 
 struct RKStage {
     double c_acc, c_stage;
@@ -111,6 +116,9 @@ struct RKStage {
 };
 
 int set_err(int code, const std::string &msg);
+// the engine's device allocations (counted; see fr_debug_fail_alloc)
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
 int cuda_check(cudaError_t e, const char *what);
 // cudaMalloc + zero fill; the context owns (and frees) the memory
 int dev_alloc_bytes(fr_ctx *c, void **p, size_t bytes);
@@ -134,6 +142,12 @@ cudaError_t launch(fr_ctx *c, int kclass, cudaStream_t s, F fn, int nk = 1) {
     return e;
 }
 int64_t ndof_of(const fr_ctx *c);
+// multiprocessors of the context's device (cudaDevAttrMultiProcessorCount)
+int num_sms(int device);
+// FR_ERR_NONFINITE if an earlier step's state check found a bad state
+int step_guard(const fr_ctx *c);
+// the state check of the solution register (one launch per element type)
+int step_check(fr_ctx *c, cudaStream_t s);
 // FP32 storage (FR_FP32, FR_BF16X3, FR_TF32X3) rather than FP64
 inline bool is_f32(const fr_ctx *c) { return c->prm.precision != FR_FP64; }
 // operator applications on the tensor cores (FR_BF16X3, FR_TF32X3)

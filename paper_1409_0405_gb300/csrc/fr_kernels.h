@@ -292,6 +292,10 @@ cudaError_t launch_to_float(int64_t n, const double *src, float *dst, cudaStream
 cudaError_t launch_reduce_partial(int nu, int64_t ne, int64_t np, const double *U, const double *wJ,
                                   double gamma, double *partial, int nblocks, cudaStream_t s);
 cudaError_t launch_reduce_final(const double *partial, int nblocks, double *out, cudaStream_t s);
+// *flag = 1 if any solution value of the register (element columns below
+// ne) is non-finite or has a non-positive density or pressure
+cudaError_t launch_state_check(int nu, int64_t ne, int64_t np, const double *U, double gamma, int *flag, int nblocks,
+                               cudaStream_t s);
 // measured FP64 FMA throughput (GFLOP/s) of the current device
 cudaError_t probe_fp64(double *gflops, cudaStream_t s);
 

@@ -48,6 +48,7 @@ struct fr_part {
     // element ids (device); allocated by the first fr_part_rhs
     std::vector<double *> pu, pr;
     std::vector<int64_t *> gid;  // [p * NT + t]
+    bool scratch_ready = false;
 };
 
 namespace {
@@ -175,7 +176,7 @@ int64_t type_base(const fr_part *pp, int t) {
 }
 
 int ensure_rhs_scratch(fr_part *pp) {
-    if (!pp->pu.empty()) return FR_OK;
+    if (pp->scratch_ready) return FR_OK;
     const int n = pp->nparts;
     pp->pu.assign(n, nullptr);
     pp->pr.assign(n, nullptr);
@@ -183,7 +184,7 @@ int ensure_rhs_scratch(fr_part *pp) {
     for (int p = 0; p < n; ++p) {
         const int64_t nd = ndof_of(pp->P[p]);
         for (double **q : {&pp->pu[p], &pp->pr[p]}) {
-            if (cudaMalloc(q, (size_t)nd * sizeof(double)) != cudaSuccess) {
+            if (dev_malloc((void **)q, (size_t)nd * sizeof(double)) != cudaSuccess) {
                 cudaGetLastError();
                 *q = nullptr;
                 return set_err(FR_ERR_NOMEM, "partition RHS scratch");
@@ -194,7 +195,7 @@ int ensure_rhs_scratch(fr_part *pp) {
             const auto &el = pp->elems[t][p];
             if (el.empty()) continue;
             int64_t *g = nullptr;
-            if (cudaMalloc(&g, el.size() * sizeof(int64_t)) != cudaSuccess) {
+            if (dev_malloc((void **)&g, el.size() * sizeof(int64_t)) != cudaSuccess) {
                 cudaGetLastError();
                 return set_err(FR_ERR_NOMEM, "partition element map");
             }
@@ -205,6 +206,7 @@ int ensure_rhs_scratch(fr_part *pp) {
             if (rc) return rc;
         }
     }
+    pp->scratch_ready = true;
     return FR_OK;
 }
 
@@ -273,7 +275,7 @@ void part_slice(const fr_part *pp, int p, const double *g, std::vector<double> &
 void part_free(fr_part *pp) {
     if (!pp) return;
     for (fr_ctx *c : pp->P) fr_destroy(c);
-    for (void *q : pp->allocs) cudaFree(q);
+    for (void *q : pp->allocs) dev_free(q);
     delete pp;
 }
 
@@ -314,7 +316,7 @@ int part_create_impl(const fr_mesh *mesh, int order, const fr_params *prm, int n
         int **dst[3] = {&d.t, &d.f, &d.e};
         const std::vector<int> *src[3] = {&sg.t, &sg.f, &sg.e};
         for (int k = 0; k < 3; ++k) {
-            if (cudaMalloc(dst[k], src[k]->size() * sizeof(int)) != cudaSuccess) {
+            if (dev_malloc((void **)dst[k], src[k]->size() * sizeof(int)) != cudaSuccess) {
                 cudaGetLastError();
                 return set_err(FR_ERR_NOMEM, "exchange plan");
             }
@@ -324,7 +326,7 @@ int part_create_impl(const fr_mesh *mesh, int order, const fr_params *prm, int n
                                  "exchange plan upload")))
                 return rc;
         }
-        if (cudaMalloc(&d.buf, (size_t)3 * V * d.n * es) != cudaSuccess) {
+        if (dev_malloc(&d.buf, (size_t)3 * V * d.n * es) != cudaSuccess) {
             cudaGetLastError();
             return set_err(FR_ERR_NOMEM, "exchange buffer");
         }
@@ -468,9 +470,15 @@ int fr_part_rhs(fr_part *pp, const double *u_dev, double *r_dev, void *stream) {
 
 int fr_part_step(fr_part *pp, double dt, int nsteps, void *stream) {
     if (!pp || nsteps < 0 || !std::isfinite(dt)) return set_err(FR_ERR_ARG, "invalid step arguments");
+    int rc;
+    for (fr_ctx *c : pp->P)
+        if ((rc = step_guard(c))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    return pp->prm.precision != FR_FP64 ? part_step_impl<float>(pp, dt, nsteps, s)
-                                        : part_step_impl<double>(pp, dt, nsteps, s);
+    rc = pp->prm.precision != FR_FP64 ? part_step_impl<float>(pp, dt, nsteps, s)
+                                      : part_step_impl<double>(pp, dt, nsteps, s);
+    for (fr_ctx *c : pp->P)
+        if (!rc && nsteps > 0) rc = step_check(c, s);
+    return rc;
 }
 
 int fr_part_reduce(fr_part *pp, double *out, void *stream) {

@@ -789,6 +789,29 @@ __global__ void k_err_norm_partial(int nu, int64_t ne, int64_t np, const double 
     block_sum_store<1>(acc, partial);
 }
 
+// state check after a step: one store of 1 by any thread that finds a bad
+// point (no atomics needed; the flag is only ever set)
+__global__ void k_state_check(int nu, int64_t ne, int64_t np, const double *__restrict__ U, double gamma,
+                              int *flag) {
+    const int64_t tot = (int64_t)nu * np;
+    bool bad = false;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot && !bad;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = idx / np, e = idx - j * np;
+        if (e >= ne) continue;
+        const double *u = U + j * V * np + e;
+        double q[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) q[v] = u[v * np];
+        const double ke = 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0];
+        const double p = (gamma - 1.0) * (q[4] - ke);
+        bad = !(q[0] > 0.0) || !(p > 0.0) || !isfinite(p);
+#pragma unroll
+        for (int v = 0; v < V; ++v) bad = bad || !isfinite(q[v]);
+    }
+    if (bad) *(volatile int *)flag = 1;
+}
+
 __global__ void k_to_float(int64_t n, const double *__restrict__ src, float *__restrict__ dst) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n) dst[idx] = (float)src[idx];
@@ -933,6 +956,13 @@ cudaError_t launch_rk_2r_update(int nu, int64_t np, const T *R, double *U, doubl
 cudaError_t launch_err_norm_partial(int nu, int64_t ne, int64_t np, const double *U, const double *E, double atol,
                                     double rtol, double *partial, int nblocks, cudaStream_t s) {
     k_err_norm_partial<<<nblocks, kDiagThreads, 0, s>>>(nu, ne, np, U, E, atol, rtol, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_check(int nu, int64_t ne, int64_t np, const double *U, double gamma, int *flag, int nblocks,
+                               cudaStream_t s) {
+    if (ne <= 0) return cudaSuccess;
+    k_state_check<<<nblocks, 256, 0, s>>>(nu, ne, np, U, gamma, flag);
     return cudaGetLastError();
 }
 

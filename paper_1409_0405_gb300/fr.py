@@ -34,7 +34,7 @@ OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
 
 # every entry point declared in include/fr.h
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
-           "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_step_ls", "fr_step_rk45",
+           "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_check", "fr_step_ls", "fr_step_rk45",
            "fr_rk45_error", "fr_rk45_get_error", "fr_step_rk45_adaptive", "fr_reduce",
            "fr_diagnostics", "fr_selftest_wait_timeout", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
@@ -43,8 +43,8 @@ EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_closure_set", "fr_mlp_nparams", "fr_mlp_workspace", "fr_mlp_forward", "fr_mlp_grad",
            "fr_mlp_adam", "fr_partition", "fr_part_plan", "fr_part_create", "fr_part_destroy",
            "fr_part_info", "fr_part_set_state", "fr_part_get_state", "fr_part_rhs", "fr_part_step",
-           "fr_part_reduce", "fr_part_launches")
-KCLASSES = ("M0", "common_solution", "grad", "M0_grad", "flux", "common_flux", "div", "closure")
+           "fr_part_reduce", "fr_part_launches", "fr_debug_fail_alloc", "fr_debug_alloc_stats")
+KCLASSES = ("M0", "common_solution", "grad", "M0_grad", "flux", "common_flux", "div", "closure", "check")
 
 
 class FRMesh(C.Structure):
@@ -94,6 +94,8 @@ def load():
     lib.fr_get_state.argtypes = [vp, dp, vp]
     lib.fr_rhs.argtypes = [vp, vp, vp, vp]
     lib.fr_step.argtypes = [vp, C.c_double, C.c_int, vp]
+    lib.fr_check.argtypes = [vp, vp]
+    lib.fr_check.restype = C.c_int
     lib.fr_step_ls.argtypes = [vp, C.c_double, C.c_int, vp]
     lib.fr_step_ls.restype = C.c_int
     lib.fr_step_rk45.argtypes = [vp, C.c_double, C.c_int, vp]
@@ -155,6 +157,10 @@ def load():
     for name in ("fr_partition", "fr_part_plan", "fr_part_create", "fr_part_info", "fr_part_set_state",
                  "fr_part_get_state", "fr_part_rhs", "fr_part_step", "fr_part_reduce", "fr_part_launches"):
         getattr(lib, name).restype = C.c_int
+    lib.fr_debug_fail_alloc.argtypes = [C.c_int64]
+    lib.fr_debug_fail_alloc.restype = C.c_int
+    lib.fr_debug_alloc_stats.argtypes = [i64p]
+    lib.fr_debug_alloc_stats.restype = C.c_int
     lib.fr_strerror.argtypes = [C.c_int]
     lib.fr_strerror.restype = C.c_char_p
     lib.fr_last_error.argtypes = []
@@ -385,6 +391,10 @@ class Context:
     def step(self, dt, nsteps=1, stream=None):
         _check(self._lib.fr_step(self._h, float(dt), int(nsteps),
                                  C.c_void_p(stream) if stream else None))
+
+    def check(self, stream=None):
+        """fr_check: raises FRError (FR_ERR_NONFINITE) after a blown-up step."""
+        _check(self._lib.fr_check(self._h, C.c_void_p(stream) if stream else None))
 
     def step_ls(self, dt, nsteps=1, stream=None):
         """Low-storage (2N) five-stage RK4 steps (fr_step_ls)."""
@@ -639,3 +649,15 @@ class PartContext:
 
 def _nupts(etype, p):
     return {0: (p + 1) * (p + 2) * (p + 3) // 6, 1: (p + 1) ** 2 * (p + 2) // 2, 2: (p + 1) ** 3}[etype]
+
+
+def debug_fail_alloc(k):
+    """fr_debug_fail_alloc: the k-th device allocation from now fails (0: none)."""
+    _check(load().fr_debug_fail_alloc(int(k)))
+
+
+def debug_alloc_stats():
+    """(allocations attempted since the last debug_fail_alloc, live allocations)."""
+    out = (C.c_int64 * 2)()
+    _check(load().fr_debug_alloc_stats(out))
+    return int(out[0]), int(out[1])

@@ -253,8 +253,10 @@ def test_state_roundtrip_and_launch_count():
     ctx.profile(True)
     ctx.step(1e-4, 2)
     classes, launches = ctx.profile_read()
-    # per RK stage: 2 types x (M0, grad, M0 grad, flux, div) + 2 face kernels
-    assert launches == 2 * 4 * 12
+    # per RK stage: 2 types x (M0, grad, M0 grad, flux, div) + 2 face kernels;
+    # per fr_step call: the state check, one launch per type
+    assert launches == 2 * 4 * 12 + 2
+    assert classes["check"][1] == 2
     assert sum(c for _, c in classes.values()) == launches
     ctx.profile(False)
 

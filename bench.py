@@ -149,6 +149,35 @@ def gemm_bytes_f32(ctx, kclass):
     return tot
 
 
+def kernel_source_sha256(name="fr_gemm.cu"):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1409_0405_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def profiled_traffic(kclass, profile="k_gemm_fp64_boundary_layer_p4_nx15.md"):
+    """DRAM bytes per launch (dram__bytes_read + dram__bytes_write) of one
+    operator class at full size, as recorded in the committed ncu summary's
+    `bench-traffic` line (measured on a smaller case and scaled by the
+    element count), or None when the kernel source has changed since that
+    capture (its SHA-256 no longer matches) or no line exists."""
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", profile)) as f:
+            txt = f.read()
+    except OSError:
+        return None, "no profile summary"
+    sha = kernel_source_sha256()
+    for m in re.finditer(r"bench-traffic: class=(\w+) sha256=([0-9a-f]+) bytes_per_launch_full_size=([0-9.eE+]+)",
+                         txt):
+        if m.group(1) != kclass:
+            continue
+        if m.group(2) != sha:
+            return None, "kernel changed since the ncu capture"
+        return float(m.group(3)), f"profiles/{profile}"
+    return None, f"no capture for class {kclass}"
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -439,6 +468,93 @@ def batch_mode(fr, torch, args, sp):
             "workload": "64 periodic isentropic-vortex boxes, Euler, FP32 + FP64 RK, seeds 3/1000+i"}
 
 
+def _time_steps(torch, step, args, sp):
+    """CUDA-event time per call of step() (after warm-up), on stream sp."""
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.ExternalStream(sp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / args.steps
+
+
+def rk45_mode(fr, torch, mesh, u0, dt, args, sp):
+    """RK45[2R+] (the paper's stepper, Sec. 3.4: five stages in two
+    registers plus the embedded error estimate) on the same FP64 workload:
+    GDOF/s counts its 5 RHS per step; the error norm of the last step's
+    embedded estimate (atol = rtol = 1e-6) is reported beside it."""
+    ctx = fr.Context(mesh, ORDER, **flow_params())
+    ctx.set_state(u0, sp)
+    ctx.profile(True)
+    ms = _time_steps(torch, lambda: ctx.step_rk45(dt, 1, sp), args, sp)
+    classes, launches = ctx.profile_read()
+    ctx.profile(False)
+    err = ctx.rk45_error(1e-6, 1e-6, sp)
+    ctx.check(sp)
+    out = {"value": ctx.ndof * 5.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "rhs_per_step": 5,
+           "kernel_ms_per_step": {k: v[0] / (args.steps + max(args.warmup, 0)) for k, v in classes.items()},
+           "error_norm_last_step": err, "error_norm_tolerances": [1e-6, 1e-6],
+           "workload": WORKLOAD.replace("RK4", "RK45[2R+]")}
+    ctx.close()
+    return out
+
+
+def partitioned_mode(fr, torch, mesh, u0, dt, ms_single, args, sp):
+    """The FP64 workload split into 2 and 4 partitions on this GPU
+    (weighted coordinate bisection, tet:pri = 1:2), exchanging cut-face
+    flux-point states and gradients through device-local halo buffers every
+    RHS: time per RK4 step against the single context, halo sizes, and
+    bitwise equality of the states after the timed steps."""
+    out = {}
+    ref = None
+    for n in (2, 4):
+        t0 = time.perf_counter()
+        pc = fr.PartContext(mesh, ORDER, n, **flow_params())
+        setup_s = time.perf_counter() - t0
+        pc.set_state(u0, sp)
+        ms = _time_steps(torch, lambda: pc.step(dt, 1, sp), args, sp)
+        st = pc.get_state(sp)
+        if ref is None:
+            ref = st
+        info = pc.info
+        out[f"{n}_parts"] = {
+            "value": pc.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "overhead_vs_single": ms / ms_single - 1.0,
+            "elements": {"tet": info[:, 0].tolist(), "pri": info[:, 1].tolist()},
+            "halo_slots": info[:, 3].tolist(), "setup_s": setup_s,
+            "state_equal_to_2_parts": bool(np.array_equal(st, ref)),
+            "state_finite": bool(pc.reduce(sp)[6] == 0.0)}
+        pc.close()
+    out["note"] = ("partitions share one GPU (no inter-GPU link is timed); the states after warm-up + timed "
+                   "steps of the 2- and 4-partition runs are compared bitwise")
+    return out
+
+
+def p3_modes(fr, torch, mesh, args, sp):
+    """The precision study's throughput at p = 3 (the same mesh and flow):
+    GDOF/s of an RK4 step in FP64 and in each reduced precision."""
+    out = {}
+    dt = time_step_size(mesh, 3)
+    u0 = None
+    for name, prec in (("fp64", fr.FR_FP64), ("fp32", fr.FR_FP32), ("bf16x3", fr.FR_BF16X3),
+                       ("tf32x3", fr.FR_TF32X3)):
+        ctx = fr.Context(mesh, 3, **flow_params(), precision=prec)
+        if u0 is None:
+            u0 = points_to_public(synth_mod().perturbed_freestream(ctx.upts_points(), seed=2,
+                                                                   wall_delta=WALL_DELTA), ctx.counts())
+        ctx.set_state(u0, sp)
+        ms = _time_steps(torch, lambda: ctx.step(dt, 1, sp), args, sp)
+        out[name] = {"value": ctx.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+                     "ndof": ctx.ndof, "state_finite": bool(ctx.reduce(stream=sp, check=False)[6] == 0.0)}
+        ctx.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # learned closure: Taylor-Green vortex, p=2 + per-element network vs p=4
 TGV_CELLS = 24
@@ -560,7 +676,9 @@ def hex_mode(fr, torch, args, sp):
     gflops = sum(gemm_flops(ctx, k) for k in gemm) * 4 * args.steps
     gms = sum(classes[k][0] for k in gemm)
     dom = max(gemm, key=lambda k: classes[k][0])
-    fp64_peak = 152 * 2 * 2 * 2.07e9
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clk = float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    fp64_peak = nsm * 2 * 2 * clk
     dom_ach = gemm_flops(ctx, dom) * 4 * args.steps / (classes[dom][0] * 1e-3)
     out = {"value": ctx.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
            "workload": f"boundary-layer box, hexahedra only: {ctx.info['n_hex']} hexes, NS p=4 FP64, RK4",
@@ -571,7 +689,7 @@ def hex_mode(fr, torch, args, sp):
            "roofline": {"bound": "alu", "kernel": f"k_gemm ({dom})", "achieved": dom_ach / 1e12,
                         "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": dom_ach / fp64_peak,
                         "traffic": None, "launches": classes[dom][1],
-                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}}
+                        "peak_source": f"derived: {nsm} SMs x 2 FP64 FMA/clk x 2 flop x {clk / 1e9:.2f} GHz"}}
     ctx.close()
     # the same workload with the operator applications on the tensor cores
     # (split TF32; the p=4 hex gradient runs as two row blocks)
@@ -875,7 +993,10 @@ def main():
         modes["fp32"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_FP32, args, sp)
         modes["bf16x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_BF16X3, args, sp)
         modes["tf32x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_TF32X3, args, sp)
+        modes["rk45"] = rk45_mode(fr, torch, mesh, u0, dt, args, sp)
+        modes["partitioned"] = partitioned_mode(fr, torch, mesh, u0, dt, ms_total / args.steps, args, sp)
         if args.nx == 75:
+            modes["p3"] = p3_modes(fr, torch, mesh, args, sp)
             modes["batched"] = batch_mode(fr, torch, args, sp)
             modes["learned"] = learned_mode(fr, torch, args, sp)
             modes["hex"] = hex_mode(fr, torch, args, sp)
@@ -889,7 +1010,10 @@ def main():
     dom = max(classes, key=lambda k: classes[k][0])
     dom_ms, dom_n = classes[dom]
     peaks = measured_peaks()
-    fp64_peak_derived = 152 * 2 * 2 * 2.07  # GFLOP/s: SMs x FMA/clk x 2 flop x GHz
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_ghz = float(peaks.get("sm_max_mhz", 2070.0)) / 1e3
+    fp64_peak_derived = nsm * 2 * 2 * clk_ghz  # GFLOP/s: SMs x FP64 FMA/clk x 2 flop x GHz
+    peak_src = f"derived: {nsm} SMs x 2 FP64 FMA/clk x 2 flop x {clk_ghz:.2f} GHz (maximum SM clock)"
     try:
         fp64_peak_meas = fr.peak_fp64(sp)
     except Exception:
@@ -898,11 +1022,7 @@ def main():
         dgemm_ref = dgemm_reference_tflops(torch)
     except Exception:
         dgemm_ref = None
-    # DRAM bytes per launch of the FP64 gradient class, from an ncu capture
-    # (dram__bytes_read + dram__bytes_write) of the same kernels on the
-    # nx=15 case (tet 465 MB, prism 480 MB per launch), scaled by the 5x
-    # element count of the full workload; valid while the kernel is unchanged
-    traffic_fp64_grad = 0.5 * (465.4e6 + 480.1e6) * 5
+    traffic, traffic_src = profiled_traffic(dom) if prec == fr.FR_FP64 and args.nx == 75 else (None, "n/a")
     if dom in ("M0", "grad", "M0_grad", "div") and prec != fr.FR_FP64:
         byts = gemm_bytes_f32(ctx, dom) * 4 * args.steps
         achieved = byts / (dom_ms * 1e-3) / 1e9
@@ -917,11 +1037,13 @@ def main():
         achieved = flops / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": fp64_peak_derived / 1e3,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak_derived,
-                "traffic": traffic_fp64_grad if (dom == "grad" and args.nx == 75) else None,
+                "traffic": traffic, "traffic_source": traffic_src,
+                "algorithmic_flops_per_launch": flops / max(dom_n, 1),
                 "kernel": f"k_gemm ({dom})", "launches": dom_n,
                 "avg_launch_ms": dom_ms / max(dom_n, 1),
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "peak_source": peak_src,
                 "peak_measured_fma_probe": (fp64_peak_meas / 1e3) if fp64_peak_meas else None,
+                "frac_of_measured_fma_probe": (achieved / fp64_peak_meas) if fp64_peak_meas else None,
                 "reference_peak_cublas_dgemm": dgemm_ref,
                 "frac_of_reference_peak": (achieved / 1e3 / dgemm_ref) if dgemm_ref else None}
     else:

@@ -115,6 +115,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Bars *ba
     }
 }
 
+// Bounded wait that ignores the abort flag: after an abort, the thread that
+// issued asynchronous work (bulk copies, MMAs) waits here for exactly that
+// work to complete before the CTA releases its shared memory and TMEM.
+// Returns false (recording `code`) only if the limit expires.
+__device__ __forceinline__ bool mbar_drain(uint64_t *b, uint32_t parity, int *err, int code) {
+    const uint32_t a = smem_u32(b);
+    const long long t0 = clock64();
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 31) == 31 && clock64() - t0 > kWaitCycles) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -397,9 +421,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int n1st = K1pad / kStageK;
         Cursor cu;
         cu.start(tm);
+        // slots with a copy issued, and the phase parity of each slot's last one
+        uint32_t issued = 0u, last_par = 0u;
         for (int64_t idx = 0; idx < total; ++idx, cu.next(tm, nkst, nslot)) {
             const int q = cu.q;
             if (!mbar_wait(&bars->freed[q], cu.par ^ 1u, bars, err, 7)) break;
+            issued |= 1u << q;
+            last_par = (last_par & ~(1u << q)) | (cu.par << q);
             const int64_t n0 = cu.n0;
             const int ks = cu.ks;
             const CUtensorMap *tmap = ks < n1st ? &tmB1 : &tmB2;
@@ -420,6 +448,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     : "memory");
             }
         }
+        // after an abort the consumers may have left before this thread's
+        // last copies landed: wait for each slot's last issued phase (a
+        // completed phase returns at once)
+        if (*(volatile int *)&bars->abort)
+            for (int q = 0; q < nslot; ++q)
+                if ((issued >> q) & 1u) mbar_drain(&bars->loaded[q], (last_par >> q) & 1u, err, 9);
     } else if (warp == kMmaWarp && lane == 0) {
         // ---- operator load, then the MMA issue loop
         const uint32_t op_s = smem_u32(smem);
@@ -435,6 +469,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     : "memory");
             }
             live = mbar_wait(&bars->op_full, 0, bars, err, 3);
+            // the image copies must land before the shared memory is released
+            if (!live) mbar_drain(&bars->op_full, 0, err, 10);
         }
         // D F32 (bit 4); A and B BF16 (1 at bits 7, 10, kind::f16) or TF32
         // (2, kind::tf32); K-major; N >> 3 at bit 17, M >> 4 at bit 24
@@ -495,17 +531,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 aph ^= 1u;
             }
         }
-        // every MMA issued above has completed once this arrives
+        // every MMA issued above has completed once this arrives (waited for
+        // even after an abort: the MMAs read shared memory and write TMEM)
         mma_commit(&bars->done);
-        mbar_wait(&bars->done, 0, bars, err, 6);
+        mbar_drain(&bars->done, 0, err, 6);
     }
-    // after an abort, give bulk copies still in flight time to land before
-    // the CTA's shared memory is released
-    if (*(volatile int *)&bars->abort) {
-        const long long t0 = clock64();
-        while (clock64() - t0 < 200000) {
-        }
-    }
+    // every asynchronous operation of this CTA has completed here: the
+    // producer and the MMA thread drained what they issued
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -93,7 +93,10 @@ def test_step_reports_a_blown_up_state_on_the_next_call():
 
 def test_step_reports_a_planted_nonphysical_point():
     """A host-built state with one negative density: the first step call
-    completes, its state check sets the flag, and the next call refuses."""
+    runs, its state check sets the flag, and once that call has completed
+    on the device the next call refuses (the flag is read without a
+    synchronisation, so the test waits for the device first)."""
+    import torch
     from paper_1409_0405_gb300 import fr
     from tests._cases import make_pair, state
     sol, ctx = make_pair(synth.vortex_box(), 1)
@@ -102,6 +105,7 @@ def test_step_reports_a_planted_nonphysical_point():
     bad[0] = -1.0
     ctx.set_state(bad)
     ctx.step(1e-4, 1)
+    torch.cuda.synchronize()
     with pytest.raises(fr.FRError) as ei:
         ctx.step(1e-4, 1)
     assert ei.value.code == fr.FR_ERR_NONFINITE

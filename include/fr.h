@@ -592,20 +592,29 @@ int fr_closure_set(fr_ctx *ctx, int etype, const float *params_dev, int nh, cons
 
 /*
  * The network's kernels, usable on their own (all pointers device,
- * caller-owned; row-major; asynchronous on cuda_stream):
+ * caller-owned; x, t, y row-major per sample; asynchronous on cuda_stream).
+ * The layers run on the tcgen05 tensor cores (bf16 weights and inputs, FP32
+ * accumulation; the backward data gradients keep dL/dz as bf16 hi + lo),
+ * the weight gradients (sums over the samples) on an FP32 split-K kernel.
  * fr_mlp_nparams: length of the parameter vector (host, no GPU).
  * fr_mlp_workspace: floats of scratch one call on n samples needs (host).
- * fr_mlp_forward: y (n x nout) = network(x (n x nin)).  ws holds, after the
- *   call, Z1, H1, Z2, H2 (each n x nh; Z the pre-activations, H = GELU(Z)
- *   before rounding).
+ *   ws must be 16-byte aligned.  Its layout, with npad = n rounded up to a
+ *   multiple of 4 and every array feature-major ([row][sample], npad
+ *   columns): a status int (then 3 floats of padding; non-zero if a
+ *   bounded wait of the tensor-core kernel gave up), X [nin], Z1, H1, Z2,
+ *   H2, dZ2, dZ1 [nh], y, dL/dy, t [nout] rows, then internal scratch.
+ * fr_mlp_forward: y (n x nout) = network(x (n x nin)); ws holds X, Z1, H1,
+ *   Z2, H2, y afterwards (Z the pre-activations, H = GELU(Z) before
+ *   rounding).
  * fr_mlp_grad: forward then backward of the loss L = mean over all n*nout
- *   entries of (y - t)^2; g (nparams floats) = dL/dparams, loss_dev[0] = L.
- *   ws as fr_mlp_forward, then dZ2 and dZ1 (n x nh each), y and dL/dy
- *   (n x nout each).
+ *   entries of (y - t)^2; g (nparams floats) = dL/dparams, loss_dev[0] = L;
+ *   ws as fr_mlp_forward, plus dZ2, dZ1, dL/dy and t.
  * fr_mlp_adam: params -= lr * mhat / (sqrt(vhat) + 1e-8) with m, v the
  *   first/second moments (beta 0.9 / 0.999, updated in place) and the bias
  *   corrections of step (counting from 1).
- * Errors: FR_ERR_ARG for non-positive sizes, null pointers or step < 1.
+ * Errors: FR_ERR_ARG for non-positive sizes, null pointers, an unaligned
+ * workspace or step < 1; FR_ERR_UNSUPPORTED for nh or nout above 256 or a
+ * layer's bf16 weight image above 192 KB.
  */
 int64_t fr_mlp_nparams(int nin, int nh, int nout);
 int64_t fr_mlp_workspace(int nin, int nh, int nout, int64_t n);

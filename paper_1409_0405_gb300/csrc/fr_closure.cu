@@ -5,9 +5,11 @@
 //
 // Internal layouts (see fr_api.cu): stage input Us [nu][V][np] (u - u_inf),
 // corrected gradient GU [nu][3][V][np], both with the element index
-// fastest.  Features and network outputs are row-major per element:
-// X[e][f], f = v nu + j (state) then 5 nu + m 5 nu + v nu + j (gradient);
-// Y[e][v nu + j].
+// fastest.  The C ABI's features and network outputs are row-major per
+// element: X[e][f], f = v nu + j (state) then 5 nu + m 5 nu + v nu + j
+// (gradient); Y[e][v nu + j].  Inside the RHS the network runs
+// feature-major on the tensor cores (X[f][e], Y[v nu + j][e] over the padded
+// element count): the same values, laid out as the FR state.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,20 +55,40 @@ __global__ void k_features(int nu, int64_t ne, int64_t np, const T *__restrict__
     }
 }
 
+// X[f][e] (feature-major, np columns; zero past ne): a coalesced copy
+template <typename T>
+__global__ void k_features_fm(int nu, int64_t ne, int64_t np, const T *__restrict__ Us, const T *__restrict__ GU,
+                              float *__restrict__ X) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    const int f = blockIdx.y, nv = 5 * nu;
+    float v = 0.f;
+    if (e < ne) {
+        if (f < nv) {
+            const int var = f / nu, j = f % nu;
+            v = (float)Us[((int64_t)j * 5 + var) * np + e];
+        } else {
+            const int r = f - nv, m = r / nv, var = (r % nv) / nu, j = r % nu;
+            v = (float)GU[(((int64_t)j * 3 + m) * 5 + var) * np + e];
+        }
+    }
+    X[(int64_t)f * np + e] = v;
+}
+
 struct Scale5 {
     double s[5];
 };
 
-// add[j][v][e] = rfs[j][v][e] + scale_v Y[e][v nu + j]  (padding: rfs only)
-__global__ void k_correction(int nu, int64_t ne, int64_t np, const double *__restrict__ rfs,
-                             const float *__restrict__ Y, Scale5 scale, double *__restrict__ add) {
+// add[j][v][e] = rfs[j][v][e] + scale_v Y[v nu + j][e]  (feature-major Y)
+__global__ void k_correction_fm(int nu, int64_t ne, int64_t np, const double *__restrict__ rfs,
+                                const float *__restrict__ Y, Scale5 scale, double *__restrict__ add) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)nu * 5 * np;
     if (i >= total) return;
     const int64_t e = i % np, row = i / np;
     const int j = (int)(row / 5), v = (int)(row % 5);
     double a = rfs ? rfs[i] : 0.0;
-    if (e < ne) a += scale.s[v] * (double)Y[e * (5 * nu) + v * nu + j];
+    if (e < ne) a += scale.s[v] * (double)Y[((int64_t)v * nu + j) * np + e];
     add[i] = a;
 }
 
@@ -125,6 +147,8 @@ cudaError_t launch_features(const DevType &D, const T *in, float *X, cudaStream_
     return cudaGetLastError();
 }
 
+// features (feature-major), the three layers on the tensor cores with the
+// weight images packed by fr_closure_set, and the correction: 5 launches
 template <typename T>
 int closure_apply(fr_ctx *c, int t, const T *in, cudaStream_t s) {
     DevType &D = c->T[t];
@@ -132,17 +156,22 @@ int closure_apply(fr_ctx *c, int t, const T *in, cudaStream_t s) {
     cudaError_t e = launch(
         c, K_CLOSURE, s,
         [&]() -> cudaError_t {
-            cudaError_t r = launch_features<T>(D, in, D.cl_X, s);
+            k_features_fm<T><<<dim3(nblk(D.np, 256), (unsigned)nin), 256, 0, s>>>(D.nu, D.ne, D.np, in,
+                                                                                  (const T *)D.GU, D.cl_X);
+            cudaError_t r = cudaGetLastError();
             if (r != cudaSuccess) return r;
-            if ((r = mlp_forward(nin, D.cl_nh, nout, D.ne, D.cl_X, D.cl_P, D.cl_Y, D.cl_ws, s)) != cudaSuccess)
+            MlpWs w = mlp_ws(nin, D.cl_nh, nout, D.np, D.cl_ws);
+            for (int k = 0; k < 3; ++k) w.op[k] = D.cl_op[k];
+            if ((r = mlp_forward_fm(nin, D.cl_nh, nout, D.np, D.cl_X, D.cl_P, D.cl_Y, w, false, c->tc_err, s)) !=
+                cudaSuccess)
                 return r;
             Scale5 sc;
             for (int v = 0; v < 5; ++v) sc.s[v] = D.cl_scale[v];
-            k_correction<<<nblk((int64_t)D.nu * 5 * D.np, 256), 256, 0, s>>>(D.nu, D.ne, D.np, D.Rfs, D.cl_Y, sc,
-                                                                            D.cl_add);
+            k_correction_fm<<<nblk((int64_t)D.nu * 5 * D.np, 256), 256, 0, s>>>(D.nu, D.ne, D.np, D.Rfs, D.cl_Y, sc,
+                                                                               D.cl_add);
             return cudaGetLastError();
         },
-        8);
+        5);
     return cuda_check(e, "closure");
 }
 
@@ -337,12 +366,15 @@ int fr_closure_set(fr_ctx *c, int etype, const float *params_dev, int nh, const 
     if (nh <= 0 || nh > 4096) return set_err(FR_ERR_ARG, "hidden width must be in 1..4096");
     if (!out_scale) return set_err(FR_ERR_ARG, "null output scales");
     const int nin = 20 * D.nu, nout = 5 * D.nu;
+    if (nh > 256 || nout > 256)
+        return set_err(FR_ERR_UNSUPPORTED, "the tensor-core network layers take at most 256 hidden units and "
+                                           "256 outputs");
     const MlpLayout L = mlp_layout(nin, nh, nout);
     if (D.cl_cap_nh < nh) {
         void *p[4];
-        const size_t sz[4] = {(size_t)L.n * sizeof(float), (size_t)D.ne * nin * sizeof(float),
-                              (size_t)D.ne * nout * sizeof(float),
-                              (size_t)mlp_workspace_floats(nin, nh, nout, D.ne) * sizeof(float)};
+        const size_t sz[4] = {(size_t)L.n * sizeof(float), (size_t)D.np * nin * sizeof(float),
+                              (size_t)D.np * nout * sizeof(float),
+                              (size_t)mlp_workspace_floats(nin, nh, nout, D.np) * sizeof(float)};
         for (int k = 0; k < 4; ++k)
             if ((rc = dev_alloc_bytes(c, &p[k], sz[k]))) return rc;
         D.cl_P = (float *)p[0];
@@ -359,6 +391,11 @@ int fr_closure_set(fr_ctx *c, int etype, const float *params_dev, int nh, const 
     if ((rc = cuda_check(cudaMemcpy(D.cl_P, params_dev, (size_t)L.n * sizeof(float), cudaMemcpyDeviceToDevice),
                          "closure parameters")))
         return rc;
+    // the bf16 weight images of the three layers (kept until the next set)
+    MlpWs w = mlp_ws(nin, nh, nout, D.np, D.cl_ws);
+    if ((rc = cuda_check(mlp_pack_forward(nin, nh, nout, D.cl_P, w, 0), "closure weight images"))) return rc;
+    for (int k = 0; k < 3; ++k) D.cl_op[k] = w.op[k];
+    if ((rc = cuda_check(cudaDeviceSynchronize(), "closure set"))) return rc;
     D.cl_nh = nh;
     for (int v = 0; v < 5; ++v) D.cl_scale[v] = out_scale[v];
     D.cl_on = 1;
@@ -375,16 +412,30 @@ int64_t fr_mlp_workspace(int nin, int nh, int nout, int64_t n) {
     return mlp_workspace_floats(nin, nh, nout, n);
 }
 
+namespace {
+int check_mlp(int nin, int nh, int nout, int64_t n, const float *ws) {
+    if (nin <= 0 || nh <= 0 || nout <= 0 || n <= 0 || n > (1LL << 30)) return set_err(FR_ERR_ARG, "invalid sizes");
+    if (nh > 256 || nout > 256)
+        return set_err(FR_ERR_UNSUPPORTED, "the tensor-core layers take at most 256 hidden units and 256 outputs");
+    if (tc_hi_image_bytes(nh, std::max(nin, nh)) > 196608)
+        return set_err(FR_ERR_UNSUPPORTED, "a layer's bf16 weight image exceeds 192 KB of shared memory");
+    if ((uintptr_t)ws % 16) return set_err(FR_ERR_ARG, "the workspace must be 16-byte aligned");
+    return FR_OK;
+}
+}  // namespace
+
 int fr_mlp_forward(int nin, int nh, int nout, int64_t n, const float *x, const float *P, float *y, float *ws,
                    void *stream) {
-    if (nin <= 0 || nh <= 0 || nout <= 0 || n <= 0 || n > (1LL << 30)) return set_err(FR_ERR_ARG, "invalid sizes");
+    int rc;
+    if ((rc = check_mlp(nin, nh, nout, n, ws))) return rc;
     if (!x || !P || !y || !ws) return set_err(FR_ERR_ARG, "null pointer");
     return cuda_check(mlp_forward(nin, nh, nout, n, x, P, y, ws, (cudaStream_t)stream), "mlp forward");
 }
 
 int fr_mlp_grad(int nin, int nh, int nout, int64_t n, const float *x, const float *t, const float *P, float *g,
                 float *loss, float *ws, void *stream) {
-    if (nin <= 0 || nh <= 0 || nout <= 0 || n <= 0 || n > (1LL << 30)) return set_err(FR_ERR_ARG, "invalid sizes");
+    int rc;
+    if ((rc = check_mlp(nin, nh, nout, n, ws))) return rc;
     if (!x || !t || !P || !g || !loss || !ws) return set_err(FR_ERR_ARG, "null pointer");
     return cuda_check(mlp_grad(nin, nh, nout, n, x, t, P, g, loss, ws, (cudaStream_t)stream), "mlp grad");
 }

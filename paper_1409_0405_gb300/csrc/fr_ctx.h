@@ -48,6 +48,7 @@ struct DevType {
     float *cl_P = nullptr, *cl_X = nullptr, *cl_Y = nullptr, *cl_ws = nullptr;
     double *cl_add = nullptr;
     int64_t cl_cap_nh = 0;  // hidden width the buffers were sized for
+    fr::TcOperator cl_op[3];  // the layers' bf16 weight images (in cl_ws)
     // FR_BF16X3 / FR_TF32X3: the packed operators M0, AGRAD, ADIV for the
     // tensor cores
     fr::TcOperator tc[3];

@@ -202,9 +202,35 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
 // kernels, see the callers) and the divergence of a plain RHS evaluation,
 // -(1/J) v (+ rfs), whose loads of a sub-group are issued before its
 // stores so that one thread keeps several in flight.
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_df(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
 template <int MODE>
 __device__ __forceinline__ void epi_group(const GemmArgsT<float> &g, int c0, int64_t n, int64_t e, const float *v) {
-    if (MODE == GEMM_STORE) {
+    if (MODE == GEMM_BIAS_ACT) {
+        // a network layer: Z = A B + bias (kept for the backward pass), gelu
+#pragma unroll
+        for (int t = 0; t < 24; ++t) {
+            const int j = c0 + t;
+            if (j < g.M) {
+                const float z = v[t] + __ldg(g.bias + j);
+                if (g.Z) g.Z[(int64_t)j * g.ldc + n] = z;
+                g.C[(int64_t)j * g.ldc + n] = g.act ? gelu_f(z) : z;
+            }
+        }
+    } else if (MODE == GEMM_ACT_BACK) {
+        // a layer's backward data gradient: (W^T dZ) * gelu'(Z)
+#pragma unroll
+        for (int t = 0; t < 24; ++t) {
+            const int j = c0 + t;
+            if (j < g.M) {
+                const int64_t o = (int64_t)j * g.ldc + n;
+                g.C[o] = v[t] * gelu_df(__ldg(g.Zin + o));
+            }
+        }
+    } else if (MODE == GEMM_STORE) {
         const float add = g.add_ref ? (float)g.uref[n / g.np] : 0.f;
 #pragma unroll
         for (int t = 0; t < 24; ++t)
@@ -259,10 +285,12 @@ template <int MODE, bool TF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const GemmArgsT<float> g, const TileMap tm, const __grid_constant__ CUtensorMap tmB1,
               const __grid_constant__ CUtensorMap tmB2, const uint8_t *__restrict__ opimg, int Nmma, int K1pad,
-              int Kpad, int nslot, uint32_t tmem_cols, int *err, int no_producer) {
+              int Kpad, int nslot, uint32_t tmem_cols, int *err, int no_producer, int terms) {
     extern __shared__ __align__(1024) uint8_t smem[];
+    // terms (split BF16): 3 = state and operator split (hi and lo images);
+    // 2 = state split, operator hi only; 1 = both rounded to bf16, hi only
     const uint32_t op_half = TF ? 0u : (uint32_t)Nmma * (uint32_t)Kpad * 2u;  // resident image: bytes of hi (lo)
-    const uint32_t op_bytes = 2u * op_half;
+    const uint32_t op_bytes = terms == 3 ? 2u * op_half : op_half;
     const uint32_t state_bytes = TF ? 16384u : (uint32_t)kStageBytes;
     const uint32_t slab_bytes = TF ? (uint32_t)Nmma * 128u : 0u;
     const uint32_t slot_bytes = state_bytes + slab_bytes;
@@ -378,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // row r: core matrix (r/8, K half h), row r%8
                 const uint32_t off = (uint32_t)(r >> 3) * 256u + (uint32_t)h * 128u + (uint32_t)(r & 7) * 16u;
                 *reinterpret_cast<uint4 *>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4 *>(slot + 4096 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                if (terms > 1) *reinterpret_cast<uint4 *>(slot + 4096 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
             fence_async_smem();
             mbar_arrive(&bars->converted[q]);
@@ -515,8 +543,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t ah = sdesc(a_hi, 128, 256), al = sdesc(a_lo, 128, 256);
                     const uint64_t bh = sdesc(b_hi, 128, 256), bl = sdesc(b_lo, 128, 256);
                     mma_bf16(d, ah, bh, idesc, ks != 0);
-                    mma_bf16(d, ah, bl, idesc, 1);
-                    mma_bf16(d, al, bh, idesc, 1);
+                    if (terms == 3) mma_bf16(d, ah, bl, idesc, 1);
+                    if (terms >= 2) mma_bf16(d, al, bh, idesc, 1);
                 }
                 mma_commit(&bars->freed[q]);
                 if (++q == nslot) {
@@ -590,8 +618,11 @@ cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOp
     cudaError_t e = encode_rows(&m1, g.B1, g.N, g.K1, g.ldb1);
     if (e == cudaSuccess) e = g.K2 > 0 ? encode_rows(&m2, g.B2, g.N, g.K2, g.ldb2) : encode_rows(&m2, g.B1, g.N, g.K1, g.ldb1);
     if (e != cudaSuccess) return e;
+    // network layers: the forward rounds its state to bf16 (one product), the
+    // backward data gradient keeps the state's lo half (two products)
+    const int terms = !op.hi_only ? 3 : (MODE == GEMM_ACT_BACK ? 2 : 1);
     k_gemm_tc<MODE, TF><<<grid, kThreads, smem, s>>>(g, tm, m1, m2, op.img, op.Nmma, op.K1pad, op.Kpad, nslot, cols,
-                                                    err, no_producer);
+                                                    err, no_producer, terms);
     return cudaGetLastError();
 }
 
@@ -599,7 +630,9 @@ cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOp
 
 // shared memory: the resident operator image (split BF16) and the slot
 // ring (2..12 slots; split TF32: state 16 KB plus the operator slab)
-static int64_t tc_image_bytes(const TcOperator &op) { return op.tf32 ? 0 : 4 * (int64_t)op.Nmma * op.Kpad; }
+static int64_t tc_image_bytes(const TcOperator &op) {
+    return op.tf32 ? 0 : (op.hi_only ? 2 : 4) * (int64_t)op.Nmma * op.Kpad;
+}
 static int64_t tc_slot_bytes(const TcOperator &op) {
     return op.tf32 ? 16384 + 128 * (int64_t)op.Nmma : (int64_t)kStageBytes;
 }
@@ -616,6 +649,40 @@ size_t tc_smem_bytes(const TcOperator &op) {
     const size_t used = (size_t)tc_image_bytes(op) + (size_t)tc_stages(op) * tc_slot_bytes(op) + sizeof(Bars);
     // at least 116 KB, so that no two CTAs (and their tensor memory) share an SM
     return used < 118784 ? 118784 : used;
+}
+
+namespace {
+// one image element per thread: operator row i (W's row, or column when
+// trans) and column k, in the K-major core-matrix layout of tc_pack (hi only)
+__global__ void k_pack_hi(const float *__restrict__ W, int rows, int cols, int ldw, int trans, int Nmma, int Kpad,
+                          __nv_bfloat16 *__restrict__ img) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)Nmma * Kpad) return;
+    const int i = (int)(idx / Kpad), k = (int)(idx % Kpad);
+    float a = 0.f;
+    if (i < rows && k < cols) a = trans ? W[(int64_t)k * ldw + i] : W[(int64_t)i * ldw + k];
+    const int ks = k / 16, kk = k % 16;
+    const int64_t off = (int64_t)ks * Nmma * 16 + ((i / 8) * 2 + kk / 8) * 64 + (i % 8) * 8 + kk % 8;
+    img[off] = __float2bfloat16_rn(a);
+}
+}  // namespace
+
+size_t tc_hi_image_bytes(int M, int K) { return (size_t)((M + 15) / 16 * 16) * ((K + 15) / 16 * 16) * 2; }
+
+cudaError_t tc_pack_hi(const float *W, int rows, int cols, int ldw, int trans, uint8_t *img, TcOperator &op,
+                       cudaStream_t s) {
+    op.img = img;
+    op.M = rows;
+    op.K = cols;
+    op.Nmma = (rows + 15) / 16 * 16;
+    op.Kpad = op.K1pad = (cols + 15) / 16 * 16;
+    op.tf32 = 0;
+    op.hi_only = 1;
+    if (rows <= 0 || cols <= 0 || op.Nmma > 256 || ((uintptr_t)img % 16)) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)op.Nmma * op.Kpad;
+    k_pack_hi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(W, rows, cols, ldw, trans, op.Nmma, op.Kpad,
+                                                         reinterpret_cast<__nv_bfloat16 *>(img));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int *err, cudaStream_t s,
@@ -652,6 +719,8 @@ cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int 
     if (op.tf32) {
         FR_TC_MODES(true)
     } else {
+        if (g.mode == GEMM_BIAS_ACT) return launch_mode<GEMM_BIAS_ACT, false>(g, tm, op, err, grid, s, no_producer);
+        if (g.mode == GEMM_ACT_BACK) return launch_mode<GEMM_ACT_BACK, false>(g, tm, op, err, grid, s, no_producer);
         FR_TC_MODES(false)
     }
 #undef FR_TC_MODES

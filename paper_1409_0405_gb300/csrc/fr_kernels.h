@@ -27,7 +27,11 @@ enum GemmMode {
     GEMM_STORE = 0,  // C = A B (+ uref[variable] with add_ref)
     GEMM_GRAD = 1,   // rows (j, d): C(j, m) = (1/J) sum_d S[d][m] (A B)(j, d)
     GEMM_DIV = 2,    // C(j) = -(1/J_j) (A B)(j) + rfs
-    GEMM_DIV_RK = 3  // r = -(1/J)(A B) + rfs; fused RK4 register update
+    GEMM_DIV_RK = 3,  // r = -(1/J)(A B) + rfs; fused RK4 register update
+    // the learned closure's network layers (tensor-core kernel only), on
+    // feature-major activations [row][column = sample]:
+    GEMM_BIAS_ACT = 4,  // Z = A B + bias[row] (stored if Z), C = act ? gelu(Z) : Z
+    GEMM_ACT_BACK = 5   // C = (A B) * gelu'(Zin[row][column])
 };
 
 template <typename T>
@@ -74,6 +78,12 @@ struct GemmArgsT {
     // sp_masked (with sp_rc == 3): each list entry is k | mask << 24, mask
     // bit r set when row m0 + r is non-zero in column k; only those FMAs run
     int sp_masked = 0;
+    // GEMM_BIAS_ACT / GEMM_ACT_BACK (float): per-row bias, the stored
+    // pre-activation Z (may be null) and its ldc-strided input Zin
+    const float *bias = nullptr;
+    float *Z = nullptr;
+    const float *Zin = nullptr;
+    int act = 0;
 };
 using GemmArgs = GemmArgsT<double>;
 
@@ -118,10 +128,20 @@ cudaError_t launch_gemm_grouped(const GemmArgsT<T> *descs, const int64_t *begin,
 // The columns of the second operand block start at K1pad (a multiple of 16).
 // tf32: split TF32 image, stage-major: per 16-wide K stage the slab
 // [hi | lo], each Nmma/8 row groups x 4 K core matrices x 8 rows x 4 values.
+// hi_only: BF16 operands (the network layers): the image holds only the hi
+// half, the kernel rounds the state to bf16 (round to nearest even) and
+// issues one MMA per K step, A_hi B_hi (FP32 accumulation).
 struct TcOperator {
     const uint8_t *img = nullptr;
-    int M = 0, K = 0, Nmma = 0, K1pad = 0, Kpad = 0, tf32 = 0;
+    int M = 0, K = 0, Nmma = 0, K1pad = 0, Kpad = 0, tf32 = 0, hi_only = 0;
 };
+// bytes of a hi-only image of an M x K operator (rows padded to 16, K to 16)
+size_t tc_hi_image_bytes(int M, int K);
+// device: packs the FP32 matrix W (rows x cols, row stride ldw; trans: the
+// operator is W^T, rows = W's columns) into a hi-only image at op.img (which
+// must hold tc_hi_image_bytes bytes) and fills op's sizes
+cudaError_t tc_pack_hi(const float *W, int rows, int cols, int ldw, int trans, uint8_t *img, TcOperator &op,
+                       cudaStream_t s);
 // packs a row-major FP64 operator (M x (K1 + K2)) into the image layout (host)
 void tc_pack(const double *A, int M, int K1, int K2, std::vector<uint16_t> &img, int &Nmma, int &K1pad, int &Kpad);
 void tc_pack_tf32(const double *A, int M, int K1, int K2, std::vector<uint32_t> &img, int &Nmma, int &K1pad,

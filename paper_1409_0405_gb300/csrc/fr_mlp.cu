@@ -7,6 +7,17 @@
 // Network: in -> nh -> nh -> out, GELU (erf form) after the two hidden
 // layers.  Parameter vector (FP32): W1[nh][in], b1[nh], W2[nh][nh], b2[nh],
 // W3[out][nh], b3[out].
+//
+// The layers run on the tcgen05 tensor cores through the operator kernel
+// (fr_gemm_tc.cu): with the activations stored feature-major ([feature]
+// [sample], samples fastest, the FR state layout), a layer H = act(W X + b)
+// is an operator application with W as the resident operator, packed to
+// bf16 on the device.  Forward: one product per K step, bf16(W) bf16(X),
+// FP32 accumulation, bias and GELU in the epilogue.  Backward data
+// gradients dZ = (W^T dY) * gelu'(Z): the same kernel on W^T, dY carried
+// as bf16 hi + lo (two products), gelu' in the epilogue.  The weight
+// gradients, reductions over the samples (dW = dZ bf16(H)^T), run on the
+// split-K FP32 kernel below, summed in a fixed order.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -14,6 +25,7 @@
 #include <cmath>
 
 #include "../../include/fr.h"
+#include "fr_kernels.h"
 #include "fr_mlp.h"
 
 namespace fr {
@@ -113,71 +125,6 @@ cudaError_t sgemm(int M, int N, int K, const float *A, int lda, const float *B, 
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_d(float x) {
-    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
-}
-
-// Z[b][n] += bias[n]; H = gelu(Z) (act) or H = Z
-__global__ void k_bias_act(int64_t rows, int n, float *Z, const float *bias, float *H, int act) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * n) return;
-    const float z = Z[i] + bias[i % n];
-    Z[i] = z;
-    H[i] = act ? gelu(z) : z;
-}
-
-// loss = mean (Y - T)^2 (accumulated into loss[0]), dY = 2 (Y - T) / count
-__global__ void k_mse(int64_t count, const float *Y, const float *T, float *dY, float *loss) {
-    __shared__ float sh[8];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float l = 0.f;
-    if (i < count) {
-        const float d = Y[i] - T[i];
-        dY[i] = 2.f * d / (float)count;
-        l = d * d / (float)count;
-    }
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = l;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        atomicAdd(loss, t);
-    }
-}
-
-// dZ = dH * gelu'(Z)
-__global__ void k_gelu_back(int64_t count, const float *Z, float *dH) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) dH[i] *= gelu_d(Z[i]);
-}
-
-// column sums db[c] = sum_r dZ[r][c] in two fixed-order stages: block
-// (cx, y) sums rows y, y + gridDim.y, ... of 32 columns into part[y][c]
-constexpr int kColRows = 64;
-__global__ void k_colsum_part(int64_t rows, int n, const float *dZ, float *part) {
-    __shared__ float sh[8][33];
-    const int c = blockIdx.x * 32 + (threadIdx.x & 31), ty = threadIdx.x >> 5;
-    float s = 0.f;
-    if (c < n)
-        for (int64_t r = (int64_t)blockIdx.y * 8 + ty; r < rows; r += (int64_t)gridDim.y * 8) s += dZ[r * n + c];
-    sh[ty][threadIdx.x & 31] = s;
-    __syncthreads();
-    if (ty == 0 && c < n) {
-        float t = 0.f;
-        for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
-        part[(size_t)blockIdx.y * n + c] = t;
-    }
-}
-
-cudaError_t colsum(int64_t rows, int n, const float *dZ, float *db, float *part, cudaStream_t s) {
-    dim3 grid((n + 31) / 32, kColRows);
-    k_colsum_part<<<grid, 256, 0, s>>>(rows, n, dZ, part);
-    k_sum_splits<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, kColRows, part, db);
-    return cudaGetLastError();
-}
-
 // Adam; omb1 = 1 - beta1 and omb2 = 1 - beta2 are formed in double on the
 // host (1.f - 0.999f would carry a 1.3e-5 relative error into v)
 __global__ void k_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1, float b2,
@@ -193,7 +140,140 @@ __global__ void k_adam(int64_t n, float *p, const float *g, float *m, float *v, 
 
 inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// out[c][r] = in[r][c] for r < rows, c < cols; out rows have stride ldo,
+// columns rows..ldo-1 of out are zero (32 x 32 tiles)
+__global__ void k_transpose(int64_t rows, int cols, const float *__restrict__ in, int64_t ldo,
+                            float *__restrict__ out) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t r = r0 + k;
+        const int c = c0 + tx;
+        tile[k][tx] = (r < rows && c < cols) ? in[r * cols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int c = c0 + k;
+        const int64_t r = r0 + tx;
+        if (c < cols && r < ldo) out[(int64_t)c * ldo + r] = tile[tx][k];
+    }
+}
+
+// feature-major loss: over rows x n samples (row stride ld), loss +=
+// mean (Y - T)^2, dY = 2 (Y - T) / count; padding columns get dY = 0
+__global__ void k_mse_fm(int rows, int64_t n, int64_t ld, const float *Y, const float *T, float *dY, float *loss) {
+    __shared__ float sh[8];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float count = (float)((double)rows * (double)n);
+    float l = 0.f;
+    if (i < (int64_t)rows * ld) {
+        const int64_t c = i % ld;
+        float d = 0.f;
+        if (c < n) {
+            d = Y[i] - T[i];
+            l = d * d / count;
+        }
+        dY[i] = 2.f * d / count;
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        atomicAdd(loss, t);
+    }
+}
+
+// row sums db[r] = sum_{c < n} dZ[r][c] (row stride ld), one block per row,
+// a fixed order: strided partial sums, then a tree over the block
+__global__ void k_rowsum(int64_t n, int64_t ld, const float *__restrict__ dZ, float *__restrict__ db) {
+    __shared__ float sh[256];
+    const float *row = dZ + (int64_t)blockIdx.x * ld;
+    float s = 0.f;
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) s += row[c];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[blockIdx.x] = sh[0];
+}
+
 }  // namespace
+
+// one network layer on the tensor cores: C[M][np] = epi(op . B[K][np])
+static cudaError_t tc_layer(const TcOperator &op, int M, int K, int64_t np, const float *B, float *C, int mode,
+                            const float *bias, float *Z, const float *Zin, int act, int *err, cudaStream_t s) {
+    GemmArgsT<float> g;
+    g.M = M;
+    g.N = np;
+    g.K1 = K;
+    g.B1 = B;
+    g.ldb1 = np;
+    g.C = C;
+    g.ldc = np;
+    g.mode = mode;
+    g.np = np;
+    g.bias = bias;
+    g.Z = Z;
+    g.Zin = Zin;
+    g.act = act;
+    return launch_gemm_tc(g, op, err, s);
+}
+
+MlpWs mlp_ws(int nin, int nh, int nout, int64_t n, float *ws) {
+    MlpWs w;
+    w.npad = (n + 3) / 4 * 4;
+    const int64_t np = w.npad;
+    float *p = ws;
+    w.err = reinterpret_cast<int *>(p);
+    p += 4;
+    w.X = p;
+    p += (int64_t)nin * np;
+    w.Z1 = p;
+    w.H1 = w.Z1 + (int64_t)nh * np;
+    w.Z2 = w.H1 + (int64_t)nh * np;
+    w.H2 = w.Z2 + (int64_t)nh * np;
+    w.dZ2 = w.H2 + (int64_t)nh * np;
+    w.dZ1 = w.dZ2 + (int64_t)nh * np;
+    w.Y = w.dZ1 + (int64_t)nh * np;
+    w.dY = w.Y + (int64_t)nout * np;
+    w.T = w.dY + (int64_t)nout * np;
+    uint8_t *img = reinterpret_cast<uint8_t *>(w.T + (int64_t)nout * np);
+    const size_t bi[5] = {tc_hi_image_bytes(nh, nin), tc_hi_image_bytes(nh, nh), tc_hi_image_bytes(nout, nh),
+                          tc_hi_image_bytes(nh, nout), tc_hi_image_bytes(nh, nh)};
+    for (int k = 0; k < 5; ++k) {
+        w.img[k] = img;
+        img += bi[k];
+    }
+    w.part = reinterpret_cast<float *>(img);
+    return w;
+}
+
+cudaError_t mlp_pack_forward(int nin, int nh, int nout, const float *P, MlpWs &w, cudaStream_t s) {
+    const MlpLayout L = mlp_layout(nin, nh, nout);
+    cudaError_t e;
+    if ((e = tc_pack_hi(P + L.W1, nh, nin, nin, 0, w.img[0], w.op[0], s)) != cudaSuccess) return e;
+    if ((e = tc_pack_hi(P + L.W2, nh, nh, nh, 0, w.img[1], w.op[1], s)) != cudaSuccess) return e;
+    return tc_pack_hi(P + L.W3, nout, nh, nh, 0, w.img[2], w.op[2], s);
+}
+
+cudaError_t mlp_forward_fm(int nin, int nh, int nout, int64_t np, const float *X, const float *P, float *Y,
+                           const MlpWs &w, bool keep_z, int *err, cudaStream_t s) {
+    const MlpLayout L = mlp_layout(nin, nh, nout);
+    cudaError_t e;
+    if ((e = tc_layer(w.op[0], nh, nin, np, X, w.H1, GEMM_BIAS_ACT, P + L.b1, keep_z ? w.Z1 : nullptr, nullptr, 1,
+                      err, s)) != cudaSuccess)
+        return e;
+    if ((e = tc_layer(w.op[1], nh, nh, np, w.H1, w.H2, GEMM_BIAS_ACT, P + L.b2, keep_z ? w.Z2 : nullptr, nullptr, 1,
+                      err, s)) != cudaSuccess)
+        return e;
+    return tc_layer(w.op[2], nout, nh, np, w.H2, Y, GEMM_BIAS_ACT, P + L.b3, nullptr, nullptr, 0, err, s);
+}
 
 MlpLayout mlp_layout(int nin, int nh, int nout) {
     MlpLayout L;
@@ -208,56 +288,67 @@ MlpLayout mlp_layout(int nin, int nh, int nout) {
 }
 
 int64_t mlp_workspace_floats(int nin, int nh, int nout, int64_t n) {
-    // Z1, H1, Z2, H2, dZ2, dZ1 (n x nh each), Y, dY (n x nout each), then
-    // the split-K / column-sum partials
+    // the status word, X, Z1, H1, Z2, H2, dZ2, dZ1, Y, dY, T (feature-major,
+    // npad samples each), the five bf16 weight images, then the split-K
+    // partials of the weight gradients
+    const int64_t np = (n + 3) / 4 * 4;
     const int64_t wmax = (int64_t)nh * std::max(std::max(nin, nh), nout);
-    const int64_t part = std::max<int64_t>((int64_t)kMaxSplit * wmax, (int64_t)kColRows * std::max(nh, nout));
-    return n * (6 * (int64_t)nh + 2 * (int64_t)nout) + part;
+    const size_t img = tc_hi_image_bytes(nh, nin) + 2 * tc_hi_image_bytes(nh, nh) + tc_hi_image_bytes(nout, nh) +
+                       tc_hi_image_bytes(nh, nout);
+    return 4 + np * ((int64_t)nin + 6 * (int64_t)nh + 3 * (int64_t)nout) + (int64_t)(img / 4) +
+           (int64_t)kMaxSplit * wmax;
 }
 
 cudaError_t mlp_forward(int nin, int nh, int nout, int64_t n, const float *X, const float *P, float *Y, float *ws,
                         cudaStream_t s) {
-    const MlpLayout L = mlp_layout(nin, nh, nout);
-    float *Z1 = ws, *H1 = Z1 + n * nh, *Z2 = H1 + n * nh, *H2 = Z2 + n * nh;
+    MlpWs w = mlp_ws(nin, nh, nout, n, ws);
+    const int64_t np = w.npad;
     cudaError_t e;
-    // Z1 = bf16(X) bf16(W1)^T + b1, H1 = gelu(Z1)
-    if ((e = sgemm<false, true>((int)n, nh, nin, X, nin, P + L.W1, nin, Z1, nh, 0.f, 1, 1, s)) != cudaSuccess) return e;
-    k_bias_act<<<nb(n * nh, 256), 256, 0, s>>>(n, nh, Z1, P + L.b1, H1, 1);
-    // Z2 = bf16(H1) bf16(W2)^T + b2, H2 = gelu(Z2)
-    if ((e = sgemm<false, true>((int)n, nh, nh, H1, nh, P + L.W2, nh, Z2, nh, 0.f, 1, 1, s)) != cudaSuccess) return e;
-    k_bias_act<<<nb(n * nh, 256), 256, 0, s>>>(n, nh, Z2, P + L.b2, H2, 1);
-    // Y = bf16(H2) bf16(W3)^T + b3
-    if ((e = sgemm<false, true>((int)n, nout, nh, H2, nh, P + L.W3, nh, Y, nout, 0.f, 1, 1, s)) != cudaSuccess)
-        return e;
-    k_bias_act<<<nb(n * nout, 256), 256, 0, s>>>(n, nout, Y, P + L.b3, Y, 0);
+    if ((e = cudaMemsetAsync(w.err, 0, sizeof(int), s)) != cudaSuccess) return e;
+    // samples to feature-major, the three layers, back to [n][nout]
+    k_transpose<<<dim3(nb(np, 32), nb(nin, 32)), 256, 0, s>>>(n, nin, X, np, w.X);
+    if ((e = mlp_pack_forward(nin, nh, nout, P, w, s)) != cudaSuccess) return e;
+    if ((e = mlp_forward_fm(nin, nh, nout, np, w.X, P, w.Y, w, true, w.err, s)) != cudaSuccess) return e;
+    k_transpose<<<dim3(nb(nout, 32), nb(n, 32)), 256, 0, s>>>(nout, (int)n, w.Y, nout, Y);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_grad(int nin, int nh, int nout, int64_t n, const float *X, const float *T, const float *P, float *G,
                      float *loss, float *ws, cudaStream_t s) {
     const MlpLayout L = mlp_layout(nin, nh, nout);
-    float *Z1 = ws, *H1 = Z1 + n * nh, *Z2 = H1 + n * nh, *H2 = Z2 + n * nh;
-    float *dZ2 = H2 + n * nh, *dZ1 = dZ2 + n * nh, *Y = dZ1 + n * nh, *dY = Y + n * nout, *part = dY + n * nout;
+    MlpWs w = mlp_ws(nin, nh, nout, n, ws);
+    const int64_t np = w.npad;
     const int sp = splits_for(n);
     cudaError_t e;
-    if ((e = mlp_forward(nin, nh, nout, n, X, P, Y, ws, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.err, 0, sizeof(int), s)) != cudaSuccess) return e;
+    k_transpose<<<dim3(nb(np, 32), nb(nin, 32)), 256, 0, s>>>(n, nin, X, np, w.X);
+    k_transpose<<<dim3(nb(np, 32), nb(nout, 32)), 256, 0, s>>>(n, nout, T, np, w.T);
+    if ((e = mlp_pack_forward(nin, nh, nout, P, w, s)) != cudaSuccess) return e;
+    if ((e = mlp_forward_fm(nin, nh, nout, np, w.X, P, w.Y, w, true, w.err, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(loss, 0, sizeof(float), s)) != cudaSuccess) return e;
-    k_mse<<<nb(n * nout, 256), 256, 0, s>>>(n * nout, Y, T, dY, loss);
-    // layer 3: dW3 = dY^T bf16(H2), db3 = sum dY, dZ2 = (dY bf16(W3)) gelu'(Z2)
-    if ((e = sgemm<true, false>(nout, nh, (int)n, dY, nout, H2, nh, G + L.W3, nh, 0.f, 0, 1, s, sp, part)))
+    k_mse_fm<<<nb(nout * np, 256), 256, 0, s>>>(nout, n, np, w.Y, w.T, w.dY, loss);
+    // transposed weights for the data gradients
+    if ((e = tc_pack_hi(P + L.W3, nout, nh, nh, 1, w.img[3], w.op[3], s)) != cudaSuccess) return e;
+    if ((e = tc_pack_hi(P + L.W2, nh, nh, nh, 1, w.img[4], w.op[4], s)) != cudaSuccess) return e;
+    // layer 3: dW3 = dY bf16(H2)^T, db3 = row sums of dY, dZ2 = (W3^T dY) gelu'(Z2)
+    if ((e = sgemm<false, true>(nout, nh, (int)n, w.dY, (int)np, w.H2, (int)np, G + L.W3, nh, 0.f, 0, 1, s, sp,
+                                w.part)))
         return e;
-    if ((e = colsum(n, nout, dY, G + L.b3, part, s))) return e;
-    if ((e = sgemm<false, false>((int)n, nh, nout, dY, nout, P + L.W3, nh, dZ2, nh, 0.f, 0, 1, s))) return e;
-    k_gelu_back<<<nb(n * nh, 256), 256, 0, s>>>(n * nh, Z2, dZ2);
-    // layer 2: dW2 = dZ2^T bf16(H1), db2, dZ1 = (dZ2 bf16(W2)) gelu'(Z1)
-    if ((e = sgemm<true, false>(nh, nh, (int)n, dZ2, nh, H1, nh, G + L.W2, nh, 0.f, 0, 1, s, sp, part))) return e;
-    if ((e = colsum(n, nh, dZ2, G + L.b2, part, s))) return e;
-    if ((e = sgemm<false, false>((int)n, nh, nh, dZ2, nh, P + L.W2, nh, dZ1, nh, 0.f, 0, 1, s))) return e;
-    k_gelu_back<<<nb(n * nh, 256), 256, 0, s>>>(n * nh, Z1, dZ1);
-    // layer 1: dW1 = dZ1^T bf16(X), db1
-    if ((e = sgemm<true, false>(nh, nin, (int)n, dZ1, nh, X, nin, G + L.W1, nin, 0.f, 0, 1, s, sp, part)))
+    k_rowsum<<<nout, 256, 0, s>>>(n, np, w.dY, G + L.b3);
+    if ((e = tc_layer(w.op[3], nh, nout, np, w.dY, w.dZ2, GEMM_ACT_BACK, nullptr, nullptr, w.Z2, 0, w.err, s)))
         return e;
-    if ((e = colsum(n, nh, dZ1, G + L.b1, part, s))) return e;
+    // layer 2: dW2 = dZ2 bf16(H1)^T, db2, dZ1 = (W2^T dZ2) gelu'(Z1)
+    if ((e = sgemm<false, true>(nh, nh, (int)n, w.dZ2, (int)np, w.H1, (int)np, G + L.W2, nh, 0.f, 0, 1, s, sp,
+                                w.part)))
+        return e;
+    k_rowsum<<<nh, 256, 0, s>>>(n, np, w.dZ2, G + L.b2);
+    if ((e = tc_layer(w.op[4], nh, nh, np, w.dZ2, w.dZ1, GEMM_ACT_BACK, nullptr, nullptr, w.Z1, 0, w.err, s)))
+        return e;
+    // layer 1: dW1 = dZ1 bf16(X)^T, db1
+    if ((e = sgemm<false, true>(nh, nin, (int)n, w.dZ1, (int)np, w.X, (int)np, G + L.W1, nin, 0.f, 0, 1, s, sp,
+                                w.part)))
+        return e;
+    k_rowsum<<<nh, 256, 0, s>>>(n, np, w.dZ1, G + L.b1);
     return cudaGetLastError();
 }
 

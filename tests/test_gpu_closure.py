@@ -72,13 +72,23 @@ def _gemm_bound(a, b):
     return a.shape[1] * 2.0 ** -23 * (np.abs(a) @ np.abs(b).T) + 1e-30
 
 
-def _ws_views(ws, n):
-    Z1, H1, Z2, H2 = (ws[i * n * NH:(i + 1) * n * NH].reshape(n, NH) for i in range(4))
-    dZ2 = ws[4 * n * NH:5 * n * NH].reshape(n, NH)
-    dZ1 = ws[5 * n * NH:6 * n * NH].reshape(n, NH)
-    Y = ws[6 * n * NH:6 * n * NH + n * NOUT].reshape(n, NOUT)
-    dY = ws[6 * n * NH + n * NOUT:6 * n * NH + 2 * n * NOUT].reshape(n, NOUT)
-    return Z1, H1, Z2, H2, dZ2, dZ1, Y, dY
+def _ws_views(ws, n, nin=NIN, nh=NH, nout=NOUT):
+    """The workspace layout of include/fr.h: a status word (4 floats), then
+    feature-major arrays of npad = n rounded up to 4 columns: X [nin], Z1,
+    H1, Z2, H2, dZ2, dZ1 [nh], y, dL/dy [nout]; returned per sample (n x
+    rows), padding columns dropped."""
+    npad = (n + 3) // 4 * 4
+    off = 4 + nin * npad
+    out = []
+    for rows in (nh,) * 6 + (nout,) * 2:
+        out.append(ws[off:off + rows * npad].reshape(rows, npad)[:, :n].T)
+        off += rows * npad
+    return tuple(out)
+
+
+def _ws_status(ws_t):
+    """The status int of the workspace (non-zero: a tensor-core wait gave up)."""
+    return int(ws_t[:1].view(torch.int32).item())
 
 
 def test_mlp_forward_layers_match_oracle():
@@ -92,6 +102,7 @@ def test_mlp_forward_layers_match_oracle():
     fr.mlp_forward(NIN, NH, NOUT, NS, Xd.data_ptr(), P.data_ptr(), Y.data_ptr(), ws.data_ptr())
     Z1, H1, Z2, H2, *_ = _ws_views(_host(ws), NS)
     Yg = _host(Y)
+    assert _ws_status(ws) == 0
     # layer 1 from the inputs
     z1 = q(X) @ q(W1).T + b1
     assert np.all(np.abs(Z1 - z1) <= _gemm_bound(q(X), q(W1)) + 1.2e-7 * (np.abs(b1) + np.abs(z1)))
@@ -130,9 +141,15 @@ def test_mlp_grad_matches_oracle_backward():
     cache = (q(X), Z1, q(H1), Z2, q(H2))
     go = OC.backward(params, cache, dy, q=True)
     gg = OC.unpack(_host(G), NIN, NH, NOUT)
+    # W3, b3 use dL/dy as computed (FP32 sums); the earlier layers take dL/dz
+    # through the tensor cores as bf16 hi + lo, which carries at most 2^-18
+    # (3.8e-6) relative error per entry: a few units in 1e-5 of the largest
+    # gradient after the sums over samples
     for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), gg, go):
         scale = np.max(np.abs(b))
-        assert np.max(np.abs(a - b)) <= 2e-5 * scale, name
+        tol = 2e-5 if name in ("W3", "b3") else 1e-4
+        assert np.max(np.abs(a - b)) <= tol * scale, (name, np.max(np.abs(a - b)) / scale)
+    assert _ws_status(ws) == 0
 
 
 def test_mlp_grad_split_k_large_batch():
@@ -152,13 +169,13 @@ def test_mlp_grad_split_k_large_batch():
     fr.mlp_grad(NIN, NH, NOUT, n, Xd.data_ptr(), Td.data_ptr(), P.data_ptr(), G.data_ptr(), loss.data_ptr(),
                 ws.data_ptr())
     wsh = _host(ws)
-    Z1, H1, Z2, H2 = (wsh[i * n * NH:(i + 1) * n * NH].reshape(n, NH) for i in range(4))
-    Y = wsh[6 * n * NH:6 * n * NH + n * NOUT].reshape(n, NOUT)
+    Z1, H1, Z2, H2, _, _, Y, _ = _ws_views(wsh, n)
     _, dy = OC.mse(Y, T)
     go = OC.backward(params, (OC.bf16(X), Z1, OC.bf16(H1), Z2, OC.bf16(H2)), dy, q=True)
     gg = OC.unpack(_host(G), NIN, NH, NOUT)
     for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), gg, go):
-        assert np.max(np.abs(a - b)) <= 5e-5 * np.max(np.abs(b)), name
+        tol = 5e-5 if name in ("W3", "b3") else 2e-4
+        assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(b)), name
 
 
 def test_mlp_adam_matches_oracle():

@@ -8,6 +8,11 @@
 // of the element centroids (no graph library in this build): split along
 // the longest extent of the current set at the weighted median, giving each
 // side a share of the weight proportional to its number of partitions.
+// The paper's other rule, no partition with only a few elements of a type,
+// is honoured where the mesh allows: a split that would leave a side with
+// more than none but fewer than kMinPerType elements of a type per partition
+// it will hold is moved to the nearest position (within 5% of the side's
+// weight) where every type is either absent or at that minimum.
 //
 // Sec. 2.5: ranks exchange the interface data of their partitions; the
 // exchange does not depend on the backend.  The plan built here is that
@@ -29,6 +34,8 @@
 
 namespace fr {
 namespace {
+
+constexpr int64_t kMinPerType = 1000;  // elements of a type per partition (Sec. 5.2)
 
 struct Item {
     int t;
@@ -69,6 +76,34 @@ void rcb(std::vector<Item> &it, size_t b, size_t e, int nparts, int base, std::v
     if (m < e && std::fabs(acc + it[m].w - target) < std::fabs(acc - target)) ++m;
     m = std::max(m, b + 1);
     m = std::min(m, e - 1);
+    // per-type counts: the split is acceptable when every type is absent
+    // from a side or present at kMinPerType per partition of that side
+    int64_t tot[NT] = {0, 0, 0};
+    for (size_t i = b; i < e; ++i) ++tot[it[i].t];
+    auto ok = [&](const int64_t left[NT]) {
+        for (int t = 0; t < NT; ++t) {
+            const int64_t r = tot[t] - left[t];
+            if ((left[t] > 0 && left[t] < kMinPerType * nl) || (r > 0 && r < kMinPerType * (nparts - nl)))
+                return false;
+        }
+        return true;
+    };
+    int64_t left[NT] = {0, 0, 0};
+    for (size_t i = b; i < m; ++i) ++left[it[i].t];
+    if (!ok(left)) {
+        int64_t cnt[NT] = {0, 0, 0};
+        double w = 0.0, best = 0.05 * target;
+        size_t mbest = 0;
+        for (size_t i = b; i + 1 < e; ++i) {
+            ++cnt[it[i].t];
+            w += it[i].w;
+            if (std::fabs(w - target) <= best && ok(cnt)) {
+                best = std::fabs(w - target);
+                mbest = i + 1;
+            }
+        }
+        if (mbest) m = mbest;
+    }
     rcb(it, b, m, nl, base, out);
     rcb(it, m, e, nparts - nl, base + nl, out);
 }

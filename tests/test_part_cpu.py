@@ -202,3 +202,21 @@ def test_two_rank_halo_exchange_over_gloo():
     for rank, n, err in res:
         assert n > 0
         assert err == 0.0, (rank, err)
+
+
+@pytest.mark.parametrize("nparts", [2, 3, 4, 8])
+def test_partition_avoids_a_handful_of_elements_of_a_type(nparts):
+    """Sec. 5.2: no partition should hold only a few (fewer than about a
+    thousand) elements of a type, unless it holds none.  On the full
+    boundary-layer workload (57,600 prisms + 118,800 tets) the partitioner
+    meets that rule at 2..8 partitions within 2% of the weighted balance."""
+    from paper_1409_0405_gb300 import fr
+    m = synth.boundary_layer_box()
+    part = fr.partition(m, nparts)
+    ps = _split(m, part)
+    load = np.zeros(nparts)
+    for t, w in zip(ETYPES, (1.0, 2.0, 3.0)):
+        cnt = np.bincount(ps[t], minlength=nparts) if len(ps[t]) else np.zeros(nparts, int)
+        assert np.all((cnt == 0) | (cnt >= 1000)), (t, cnt)
+        np.add.at(load, ps[t], w)
+    assert load.max() / load.mean() - 1.0 < 0.02, load

@@ -149,10 +149,14 @@ def gemm_bytes_f32(ctx, kclass):
     return tot
 
 
-def kernel_source_sha256(name="fr_gemm.cu"):
+def kernel_source_sha256(names=("fr_gemm.cu", "fr_gemm_body.cuh")):
+    """SHA-256 of the operator kernel's source files, concatenated."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_1409_0405_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_1409_0405_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def profiled_traffic(kclass, profile="k_gemm_fp64_boundary_layer_p4_nx15.md"):

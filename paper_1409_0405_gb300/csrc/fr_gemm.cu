@@ -24,181 +24,11 @@
 #include <cstdio>
 #include <vector>
 
+#include "fr_gemm_body.cuh"
 #include "fr_kernels.h"
 
 namespace fr {
 namespace {
-
-constexpr int kThreads = 128;
-
-// One (row chunk, column tile) block of C <- A [B1; B2] with the epilogue
-// MODE.  Block-uniform: every thread of the block calls it with the same
-// (g, m0, tile); it stages the chunk of A in sA and synchronises.
-template <typename T, int RC, int MODE>
-__device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_t tile, T *sA) {
-    const int K = g.K1 + g.K2;
-    // dense: sA[k][r] for every column; compressed: sA[i][r] for the chunk's
-    // column list i, the column numbers in sK
-    int nl1 = g.K1, nl = K;
-    int *sK = nullptr;
-    if (g.sp_rc) {
-        const int c = m0 / RC;
-        const int beg = g.sp_off[2 * c], mid = g.sp_off[2 * c + 1], end = g.sp_off[2 * c + 2];
-        nl1 = mid - beg;
-        nl = end - beg;
-        sK = reinterpret_cast<int *>(sA + (size_t)g.sp_lmax * RC);
-        for (int idx = threadIdx.x; idx < RC * nl; idx += kThreads) sA[idx] = g.sp_vals[(size_t)beg * RC + idx];
-        for (int idx = threadIdx.x; idx < nl; idx += kThreads) sK[idx] = g.sp_cols[beg + idx];
-    } else {
-        for (int idx = threadIdx.x; idx < RC * K; idx += kThreads) {
-            const int r = idx / K, k = idx - r * K;
-            sA[k * RC + r] = (m0 + r < g.M) ? g.A[(size_t)(m0 + r) * K + k] : T(0);
-        }
-    }
-    __syncthreads();
-    const int64_t n = tile * kThreads + threadIdx.x;
-    if (n < g.N) {
-        T acc[RC];
-#pragma unroll
-        for (int r = 0; r < RC; ++r) acc[r] = T(0);
-        if constexpr (RC == 3) {
-            if (sK && g.sp_masked) {
-                // runs of listed columns with the same row mask, each mask
-                // with its own loop (the FMAs of absent rows are not issued,
-                // not even predicated off); the column order is unchanged
-                const T *b1 = g.B1 + n, *b2 = g.B2 + n;
-                const int64_t ld1 = g.ldb1, ld2 = g.ldb2;
-                const int K1 = g.K1;
-                auto bval = [&](int t) -> T {
-                    const int k = sK[t] & 0xFFFFFF;
-                    return t < nl1 ? __ldg(b1 + (int64_t)k * ld1) : __ldg(b2 + (int64_t)(k - K1) * ld2);
-                };
-                int i = 0;
-                while (i < nl) {
-                    const int m = sK[i] >> 24;
-                    int j = i + 1;
-                    while (j < nl && (sK[j] >> 24) == m) ++j;
-                    const T *a = sA;
-                    switch (m) {
-#define FR_RUN(BODY)                               \
-    {                                              \
-        _Pragma("unroll 2") for (int t = i; t < j; ++t) { \
-            const T bv = bval(t);                  \
-            BODY                                   \
-        }                                          \
-    }                                              \
-    break;
-                        case 1: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]);)
-                        case 2: FR_RUN(acc[1] = fma(a[3 * t + 1], bv, acc[1]);)
-                        case 3: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[1] = fma(a[3 * t + 1], bv, acc[1]);)
-                        case 4: FR_RUN(acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
-                        case 5: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
-                        case 6: FR_RUN(acc[1] = fma(a[3 * t + 1], bv, acc[1]); acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
-                        default:
-                            FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[1] = fma(a[3 * t + 1], bv, acc[1]);
-                                   acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
-#undef FR_RUN
-                    }
-                    i = j;
-                }
-                sK = nullptr;  // done
-                nl = -1;
-            }
-        }
-        if (sK) {
-            // the chunk's non-zero columns only, in increasing order: the
-            // same sums as the dense loop, less the terms whose A is zero
-            const T *b1 = g.B1 + n;
-#pragma unroll 2
-            for (int i = 0; i < nl1; ++i) {
-                const T bv = __ldg(b1 + (int64_t)sK[i] * g.ldb1);
-                const T *a = sA + i * RC;
-#pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
-            }
-            const T *b2 = g.B2 + n;
-#pragma unroll 2
-            for (int i = nl1; i < nl; ++i) {
-                const T bv = __ldg(b2 + (int64_t)(sK[i] - g.K1) * g.ldb2);
-                const T *a = sA + i * RC;
-#pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
-            }
-        } else if (nl >= 0) {
-            {
-                const T *b = g.B1 + n;
-                const int64_t ld = g.ldb1;
-#pragma unroll 2
-                for (int k = 0; k < g.K1; ++k) {
-                    const T bv = __ldg(b + (int64_t)k * ld);
-                    const T *a = sA + k * RC;
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
-                }
-            }
-            if (g.K2 > 0) {
-                const T *b = g.B2 + n;
-                const int64_t ld = g.ldb2;
-                const T *a0 = sA + g.K1 * RC;
-#pragma unroll 2
-                for (int k = 0; k < g.K2; ++k) {
-                    const T bv = __ldg(b + (int64_t)k * ld);
-                    const T *a = a0 + k * RC;
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
-                }
-            }
-        }
-
-        if (MODE == GEMM_STORE) {
-            const T add = g.add_ref ? T(g.uref[n / g.np]) : T(0);
-#pragma unroll
-            for (int r = 0; r < RC; ++r)
-                if (m0 + r < g.M) g.C[(int64_t)(m0 + r) * g.ldc + n] = acc[r] + add;
-        } else if (MODE == GEMM_GRAD) {
-            // rows are (j, d) with d fastest; RC and m0 are multiples of 3
-            const int64_t e = n % g.np;
-#pragma unroll
-            for (int jj = 0; jj < RC / 3; ++jj) {
-                const int j = m0 / 3 + jj;
-                if (3 * j >= g.M) break;
-                const T *S = g.S + (int64_t)j * 9 * g.np + e;
-                const T ij = g.invJ[(int64_t)j * g.np + e];
-                const T g0 = acc[3 * jj], g1 = acc[3 * jj + 1], g2 = acc[3 * jj + 2];
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const T s0 = S[(0 * 3 + m) * g.np], s1 = S[(1 * 3 + m) * g.np], s2 = S[(2 * 3 + m) * g.np];
-                    g.C[(int64_t)(3 * j + m) * g.ldc + n] = ij * (s0 * g0 + s1 * g1 + s2 * g2);
-                }
-            }
-        } else {
-            const int64_t e = n % g.np;
-            const double ur = (MODE == GEMM_DIV_RK) ? g.uref[n / g.np] : 0.0;
-#pragma unroll
-            for (int r = 0; r < RC; ++r) {
-                const int j = m0 + r;
-                if (j >= g.M) break;
-                const int64_t idx = (int64_t)j * g.ldc + n;
-                const T rt = -g.invJ[(int64_t)j * g.np + e] * acc[r];
-                if (MODE == GEMM_DIV) {
-                    g.C[idx] = g.rfs ? T((double)rt + g.rfs[idx]) : rt;
-                } else {
-                    // FP64 register update (both modes)
-                    const double rv = (double)rt + (g.rfs ? g.rfs[idx] : 0.0);
-                    const double u = g.U[idx];
-                    if (g.rk_last) {
-                        const double un = g.Uacc[idx] + g.c_acc * rv;
-                        g.U[idx] = un;
-                        g.Us[idx] = T(un - ur);
-                    } else {
-                        g.Uacc[idx] = (g.rk_first ? u : g.Uacc[idx]) + g.c_acc * rv;
-                        g.Us[idx] = T((u - ur) + g.c_stage * rv);
-                    }
-                }
-            }
-        }
-    }
-}
 
 template <typename T, int RC, int MODE>
 __global__ void __launch_bounds__(kThreads) k_gemm(const GemmArgsT<T> g) {

@@ -652,15 +652,16 @@ size_t tc_smem_bytes(const TcOperator &op) {
 }
 
 namespace {
-// one image element per thread: operator row i (W's row, or column when
-// trans) and column k, in the K-major core-matrix layout of tc_pack (hi only)
-__global__ void k_pack_hi(const float *__restrict__ W, int rows, int cols, int ldw, int trans, int Nmma, int Kpad,
+// one image element per thread: operator row i < M and column k < K (the
+// operator is W, or W^T when trans: then W has K rows and M columns), in
+// the K-major core-matrix layout of tc_pack (hi only)
+__global__ void k_pack_hi(const float *__restrict__ W, int M, int K, int ldw, int trans, int Nmma, int Kpad,
                           __nv_bfloat16 *__restrict__ img) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)Nmma * Kpad) return;
     const int i = (int)(idx / Kpad), k = (int)(idx % Kpad);
     float a = 0.f;
-    if (i < rows && k < cols) a = trans ? W[(int64_t)k * ldw + i] : W[(int64_t)i * ldw + k];
+    if (i < M && k < K) a = trans ? W[(int64_t)k * ldw + i] : W[(int64_t)i * ldw + k];
     const int ks = k / 16, kk = k % 16;
     const int64_t off = (int64_t)ks * Nmma * 16 + ((i / 8) * 2 + kk / 8) * 64 + (i % 8) * 8 + kk % 8;
     img[off] = __float2bfloat16_rn(a);
@@ -671,16 +672,17 @@ size_t tc_hi_image_bytes(int M, int K) { return (size_t)((M + 15) / 16 * 16) * (
 
 cudaError_t tc_pack_hi(const float *W, int rows, int cols, int ldw, int trans, uint8_t *img, TcOperator &op,
                        cudaStream_t s) {
+    // the operator's shape: W's (rows x cols), or (cols x rows) for W^T
     op.img = img;
-    op.M = rows;
-    op.K = cols;
-    op.Nmma = (rows + 15) / 16 * 16;
-    op.Kpad = op.K1pad = (cols + 15) / 16 * 16;
+    op.M = trans ? cols : rows;
+    op.K = trans ? rows : cols;
+    op.Nmma = (op.M + 15) / 16 * 16;
+    op.Kpad = op.K1pad = (op.K + 15) / 16 * 16;
     op.tf32 = 0;
     op.hi_only = 1;
     if (rows <= 0 || cols <= 0 || op.Nmma > 256 || ((uintptr_t)img % 16)) return cudaErrorInvalidValue;
     const int64_t n = (int64_t)op.Nmma * op.Kpad;
-    k_pack_hi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(W, rows, cols, ldw, trans, op.Nmma, op.Kpad,
+    k_pack_hi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(W, op.M, op.K, ldw, trans, op.Nmma, op.Kpad,
                                                          reinterpret_cast<__nv_bfloat16 *>(img));
     return cudaGetLastError();
 }

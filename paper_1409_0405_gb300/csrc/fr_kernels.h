@@ -137,9 +137,10 @@ struct TcOperator {
 };
 // bytes of a hi-only image of an M x K operator (rows padded to 16, K to 16)
 size_t tc_hi_image_bytes(int M, int K);
-// device: packs the FP32 matrix W (rows x cols, row stride ldw; trans: the
-// operator is W^T, rows = W's columns) into a hi-only image at op.img (which
-// must hold tc_hi_image_bytes bytes) and fills op's sizes
+// device: packs the FP32 matrix W (rows x cols, row stride ldw) as the
+// operator W, or W^T when trans (then the operator is cols x rows), into a
+// hi-only image at img (tc_hi_image_bytes of the operator's shape) and fills
+// op's sizes
 cudaError_t tc_pack_hi(const float *W, int rows, int cols, int ldw, int trans, uint8_t *img, TcOperator &op,
                        cudaStream_t s);
 // packs a row-major FP64 operator (M x (K1 + K2)) into the image layout (host)

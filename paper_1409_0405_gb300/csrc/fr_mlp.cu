@@ -140,9 +140,9 @@ __global__ void k_adam(int64_t n, float *p, const float *g, float *m, float *v, 
 
 inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// out[c][r] = in[r][c] for r < rows, c < cols; out rows have stride ldo,
-// columns rows..ldo-1 of out are zero (32 x 32 tiles)
-__global__ void k_transpose(int64_t rows, int cols, const float *__restrict__ in, int64_t ldo,
+// out[c][r] = in[r][c] for r < rows, c < cols; in rows have stride ldi,
+// out rows stride ldo, columns rows..ldo-1 of out are zero (32 x 32 tiles)
+__global__ void k_transpose(int64_t rows, int cols, const float *__restrict__ in, int64_t ldi, int64_t ldo,
                             float *__restrict__ out) {
     __shared__ float tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.x * 32;
@@ -151,7 +151,7 @@ __global__ void k_transpose(int64_t rows, int cols, const float *__restrict__ in
     for (int k = ty; k < 32; k += 8) {
         const int64_t r = r0 + k;
         const int c = c0 + tx;
-        tile[k][tx] = (r < rows && c < cols) ? in[r * cols + c] : 0.f;
+        tile[k][tx] = (r < rows && c < cols) ? in[r * ldi + c] : 0.f;
     }
     __syncthreads();
     for (int k = ty; k < 32; k += 8) {
@@ -306,10 +306,10 @@ cudaError_t mlp_forward(int nin, int nh, int nout, int64_t n, const float *X, co
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.err, 0, sizeof(int), s)) != cudaSuccess) return e;
     // samples to feature-major, the three layers, back to [n][nout]
-    k_transpose<<<dim3(nb(np, 32), nb(nin, 32)), 256, 0, s>>>(n, nin, X, np, w.X);
+    k_transpose<<<dim3(nb(np, 32), nb(nin, 32)), 256, 0, s>>>(n, nin, X, nin, np, w.X);
     if ((e = mlp_pack_forward(nin, nh, nout, P, w, s)) != cudaSuccess) return e;
     if ((e = mlp_forward_fm(nin, nh, nout, np, w.X, P, w.Y, w, true, w.err, s)) != cudaSuccess) return e;
-    k_transpose<<<dim3(nb(nout, 32), nb(n, 32)), 256, 0, s>>>(nout, (int)n, w.Y, nout, Y);
+    k_transpose<<<dim3(nb(nout, 32), nb(n, 32)), 256, 0, s>>>(nout, (int)n, w.Y, np, nout, Y);
     return cudaGetLastError();
 }
 
@@ -321,8 +321,8 @@ cudaError_t mlp_grad(int nin, int nh, int nout, int64_t n, const float *X, const
     const int sp = splits_for(n);
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.err, 0, sizeof(int), s)) != cudaSuccess) return e;
-    k_transpose<<<dim3(nb(np, 32), nb(nin, 32)), 256, 0, s>>>(n, nin, X, np, w.X);
-    k_transpose<<<dim3(nb(np, 32), nb(nout, 32)), 256, 0, s>>>(n, nout, T, np, w.T);
+    k_transpose<<<dim3(nb(np, 32), nb(nin, 32)), 256, 0, s>>>(n, nin, X, nin, np, w.X);
+    k_transpose<<<dim3(nb(np, 32), nb(nout, 32)), 256, 0, s>>>(n, nout, T, nout, np, w.T);
     if ((e = mlp_pack_forward(nin, nh, nout, P, w, s)) != cudaSuccess) return e;
     if ((e = mlp_forward_fm(nin, nh, nout, np, w.X, P, w.Y, w, true, w.err, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(loss, 0, sizeof(float), s)) != cudaSuccess) return e;

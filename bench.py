@@ -458,16 +458,42 @@ def batch_mode(fr, torch, args, sp):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / args.steps
 
-    ms_b = timed(True)
-    ms_u = timed(False)
+    ms_b = timed(True)          # one persistent launch per RK stage
     info = b.info()
+    ms_g = timed(2)             # one grouped launch per operator class and point-wise pass
+    info_g = b.info()
+    ms_u = timed(False)         # each problem's own launches
+    b.check(sp)                 # raises if a barrier wait of the stage kernel gave up
     finite = all(c.reduce(stream=sp, check=False)[6] == 0.0 for c in b.problems)
+    # algorithmic bytes of one RK step (FP32 state, FP64 registers): operator
+    # inputs and outputs with their epilogue traffic (gemm_bytes_f32), the
+    # flux kernel's U, S and FT (29 floats per point), and per interface
+    # pair both sides' u_f read and common flux written (20 floats) plus
+    # its metadata (normal and magnitudes in float, six int indices, switch)
+    byts = 0.0
+    for c in b.problems:
+        i = c.info
+        pts = sum(i["n_" + t] * i["nu_" + t] for t in ("tet", "pri", "hex"))
+        byts += gemm_bytes_f32(c, "M0") + gemm_bytes_f32(c, "div") + 4.0 * 29 * pts
+        byts += i["npairs"] * (4.0 * 20 + 4.0 * 5 + 4.0 * 6 + 1)
+    byts *= 4
+    ach = byts / (ms_b * 1e-3) / 1e9
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
     b.close()
     return {"value": info["ndof"] * 4.0 / (ms_b * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_b,
+            "schedule": "one persistent cooperative launch per RK stage, CUDA graph",
+            "launches_per_step": info["launches_batched"], "stage_grid": info["grid_stage"],
+            "grouped_launches_ms_per_step": ms_g, "grouped_launches_per_step": info_g["launches_batched"],
             "per_problem_launches_ms_per_step": ms_u, "speedup_vs_per_problem": ms_u / ms_b,
-            "launches_per_step": info["launches_batched"],
+            "speedup_vs_grouped": ms_g / ms_b,
             "per_problem_launches_per_step": info["launches_per_problem"],
-            "ndof": info["ndof"], "problems": 64, "tuned": {k: info[k] for k in fr.Batch.INFO[4:]},
+            "roofline": {"bound": "hbm", "kernel": "k_stage (whole RK step)", "achieved": ach, "peak": peak,
+                         "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                         "bytes_per_step": byts,
+                         "bytes": "staged pipeline minimum: operators in/out + epilogue registers, flux point "
+                                  "data, face gathers and metadata (bench.batch_mode)",
+                         "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+            "ndof": info["ndof"], "problems": 64, "tuned": {k: info[k] for k in fr.Batch.INFO[4:12]},
             "setup_s": setup_s, "tune_s": tune_s, "state_finite": bool(finite),
             "workload": "64 periodic isentropic-vortex boxes, Euler, FP32 + FP64 RK, seeds 3/1000+i"}
 

@@ -350,29 +350,42 @@ int fr_peak_fp64(double *gflops, void *cuda_stream);
 
 /*
  * Batched engine: many independent problems (their own meshes, element
- * mixes and orders, the same fr_params) advanced together.  Every RK stage
- * of the whole batch runs as a few grouped persistent launches (one per
- * operator class and one per point-wise kernel, each walking a device work
- * list over all problems and element types), and one RK step is captured in
- * a CUDA graph.  The results are bit-identical to advancing each problem on
- * its own.
+ * mixes and orders, the same fr_params) advanced together.  Every operator
+ * application and point-wise pass of all problems and element types is a
+ * device work list.  An RK stage of the whole batch runs either as ONE
+ * persistent cooperative launch (the stage's phases in order, separated by
+ * grid-wide barriers whose waits are bounded) or as one grouped launch per
+ * operator class and point-wise kernel; one RK step is captured in a CUDA
+ * graph.  The results are bit-identical to advancing each problem on its
+ * own.
  *
  * fr_batch_create: builds nprob contexts (meshes[i], orders[i], *params) and
  *   the work lists.  Errors as fr_create.
  * fr_batch_problem: the context of problem i (owned by the batch: use it with
  *   fr_set_state / fr_get_state / fr_rhs / fr_reduce, never fr_destroy).
- * fr_batch_tune: times the candidate row-chunk sizes and persistent grid
- *   sizes of every grouped launch on this batch and keeps the fastest
- *   (leaves the solution registers untouched).  Synchronous.
+ * fr_batch_tune: times the candidate row-chunk sizes (the operator blocks'
+ *   tile shapes, used by both schedules) and the grids of every grouped
+ *   launch on this batch and keeps the fastest (leaves the solution
+ *   registers untouched).  Synchronous.
  * fr_batch_step: nsteps RK4 steps, dt[i] for problem i (host array of
- *   nprob).  batched != 0: grouped launches replayed from a CUDA graph
- *   (captured on first use and after tuning or a change of dt); batched == 0:
- *   each problem's own launch sequence, one after another (the comparison).
- *   Asynchronous on cuda_stream.
- * fr_batch_info: out (12 int64): nprob, total DOF, launches per step of the
- *   batched graph, launches per step of the per-problem sequence, the tuned
- *   row-chunk sizes (M0, gradient, M0 on gradients, divergence) and grids
- *   (GEMM, divergence, flux, face kernels).
+ *   nprob).  batched == 1: one persistent launch per RK stage (4 per step);
+ *   batched == 2: the grouped launches per class; both replayed from a CUDA
+ *   graph (captured on first use and after tuning, a change of dt or of the
+ *   schedule); batched == 0: each problem's own launch sequence, one after
+ *   another (the comparison).  Asynchronous on cuda_stream.
+ * fr_batch_check: synchronises and returns FR_ERR_TIMEOUT if a barrier wait
+ *   of the persistent stage kernel ran out (its status is then cleared and
+ *   the batch stays usable; the steps since then did no work), else FR_OK.
+ * fr_batch_selftest_wait_timeout: failure-detection self-test: one stage of
+ *   the persistent kernel, without its register update, launched with one
+ *   CTA withheld from the barriers, so every other CTA's bounded wait runs
+ *   out (about 2 s).  FR_OK if that timeout was reported (and cleared).
+ * fr_batch_info: out (14 int64): nprob, total DOF, launches per step of the
+ *   last captured graph, launches per step of the per-problem sequence, the
+ *   tuned row-chunk sizes (M0, gradient, M0 on gradients, divergence) and
+ *   grids (GEMM, divergence, flux, face kernels), the persistent stage
+ *   kernel's grid (0 before its first use), launches per step of the
+ *   grouped schedule (0 before its first use).
  */
 typedef struct fr_batch fr_batch;
 int fr_batch_create(int nprob, const fr_mesh *meshes, const int *orders, const fr_params *params, fr_batch **out);
@@ -380,6 +393,8 @@ void fr_batch_destroy(fr_batch *b);
 int fr_batch_problem(fr_batch *b, int i, fr_ctx **ctx);
 int fr_batch_tune(fr_batch *b, void *cuda_stream);
 int fr_batch_step(fr_batch *b, const double *dt, int nsteps, int batched, void *cuda_stream);
+int fr_batch_check(fr_batch *b, void *cuda_stream);
+int fr_batch_selftest_wait_timeout(fr_batch *b, void *cuda_stream);
 int fr_batch_info(const fr_batch *b, int64_t *out);
 
 /*

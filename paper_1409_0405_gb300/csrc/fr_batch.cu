@@ -1,16 +1,18 @@
 // Batched engine: many independent FR problems (different meshes, element
 // mixes and orders) advanced together.
 //
-// Each RK stage of the whole batch is a handful of grouped, persistent
-// launches instead of one launch per kernel per problem: every operator
-// application of every problem and element type becomes a descriptor in a
-// device-resident work list, and one launch per operator class (M0,
-// corrected gradient, M0 on gradients, divergence + RK update) walks all
-// (descriptor, row chunk, column tile) blocks with a fixed grid; the
-// point-wise flux and face kernels likewise walk concatenated segments.
+// Every operator application of every problem and element type becomes a
+// descriptor in a device-resident work list, and the point-wise flux and
+// face kernels walk concatenated segments.  Two schedules of an RK stage:
+//  * one persistent cooperative launch per stage (fr_stage.cu): all of the
+//    stage's work lists, phase after phase, separated by grid-wide barriers
+//    with bounded waits (4 launches per RK step);
+//  * one grouped launch per operator class (M0, corrected gradient, M0 on
+//    gradients, divergence + RK update) and per point-wise pass.
 // One RK step (4 stages) is captured in a CUDA graph and replayed.  The
-// row-chunk size and the persistent grid of every class are chosen by
-// timing the candidates on the batch itself (fr_batch_tune).
+// row-chunk sizes (the tile shapes of the operator blocks), and the grids
+// of the grouped launches, are chosen by timing the candidates on the batch
+// itself (fr_batch_tune).
 //
 // The arithmetic of every output is the same as in the per-problem launch
 // sequence (same operators, same summation order), so the two agree bit
@@ -68,6 +70,8 @@ struct BatchBase {
     virtual int tune(cudaStream_t s) = 0;
     virtual int step(const double *dt, int nsteps, int batched, cudaStream_t s) = 0;
     virtual void info(int64_t *out) const = 0;
+    virtual int check(cudaStream_t s) = 0;
+    virtual int selftest(cudaStream_t s) = 0;
 };
 
 struct fr_batch {
@@ -92,6 +96,13 @@ struct BatchImpl : BatchBase {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int launches_per_step = 0;
     int nsm = 152;
+    // the persistent schedule: one plan per RK stage, the barrier words and
+    // status of the stage kernel, its co-resident grid; graph_mode is the
+    // schedule the instantiated graph holds (1 persistent, 2 grouped)
+    StagePlan<T> plan[4];
+    unsigned *bar = nullptr;
+    int *serr = nullptr;
+    int stage_grid_n = 0, graph_mode = 0, launches_grouped = 0;
 
     explicit BatchImpl(fr_batch *bb) : b(bb) {
         viscous = bb->ctx[0]->prm.viscous != 0;
@@ -161,6 +172,8 @@ struct BatchImpl : BatchBase {
         if (cap) cudaStreamDestroy(cap);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
+        dev_free(bar);
+        dev_free(serr);
     }
 
     // prefix sums of blocks for the group's row-chunk size, uploaded
@@ -254,6 +267,13 @@ struct BatchImpl : BatchBase {
         if ((rc = upload_group(m0)) || (rc = upload_group(grad)) || (rc = upload_group(m0g)) ||
             (rc = upload_segs(flux)) || (rc = upload_segs(face)) || (rc = upload_segs(center)))
             return rc;
+        {
+            // barrier words and status of the stage kernel, zeroed
+            const unsigned zb[2] = {0u, 0u};
+            const int zi = 0;
+            if ((rc = dev_put((void **)&bar, zb, sizeof(zb))) || (rc = dev_put((void **)&serr, &zi, sizeof(int))))
+                return rc;
+        }
         if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming) != cudaSuccess) {
@@ -327,7 +347,69 @@ struct BatchImpl : BatchBase {
         return FR_OK;
     }
 
-    int capture() {
+    static StagePhase<T> gemm_phase(const Group<T> &g) {
+        StagePhase<T> p;
+        p.descs = g.d;
+        p.begin = g.begin;
+        p.ndesc = g.ndesc;
+        p.total = g.total;
+        p.mode = g.mode;
+        p.rc = g.rc;
+        p.maxK = g.maxK;
+        return p;
+    }
+    void add_flux(StagePhase<T> &p, int xf) const {
+        p.fitems = flux.d;
+        p.fbegin = flux.begin;
+        p.fn = (int)flux.h.size();
+        p.ftotal = flux.total;
+        p.xform = xf;
+    }
+    void add_face(StagePhase<T> &p, int which) const {
+        p.citems = face.d;
+        p.cbegin = face.begin;
+        p.cn = (int)face.h.size();
+        p.ctotal = face.total;
+        p.which = which;
+    }
+
+    // the phases of stage st (with_div = false: all but the divergence,
+    // for the bounded-wait self-test, which must not touch the registers):
+    //   Euler       [M0 + flux] [common flux] [divergence + RK]
+    //   NS, FP64    [M0] [common solution] [gradient] [M0 on gradients +
+    //               flux] [common flux] [divergence + RK]
+    //   NS, FP32    as FP64, but the flux (which forms the physical
+    //               gradient in place) precedes M0 on the gradients
+    StagePlan<T> make_plan(int st, bool with_div) const {
+        StagePlan<T> pl;
+        int n = 0;
+        if (!viscous) {
+            pl.ph[n] = gemm_phase(m0);
+            add_flux(pl.ph[n++], 0);
+        } else {
+            pl.ph[n++] = gemm_phase(m0);
+            add_face(pl.ph[n++], 0);
+            pl.ph[n++] = gemm_phase(grad);
+            if (xform) {
+                add_flux(pl.ph[n++], 1);
+                pl.ph[n++] = gemm_phase(m0g);
+            } else {
+                pl.ph[n] = gemm_phase(m0g);
+                add_flux(pl.ph[n++], 0);
+            }
+        }
+        add_face(pl.ph[n++], 1);
+        if (with_div) pl.ph[n++] = gemm_phase(div[st]);
+        pl.nph = n;
+        return pl;
+    }
+
+    int build_plans() {
+        for (int st = 0; st < 4; ++st) plan[st] = make_plan(st, true);
+        return cuda_check(stage_grid<T>(plan[0], &stage_grid_n), "stage grid");
+    }
+
+    int capture(int mode) {
         if (exec) {
             cudaGraphExecDestroy(exec);
             exec = nullptr;
@@ -336,16 +418,62 @@ struct BatchImpl : BatchBase {
             cudaGraphDestroy(graph);
             graph = nullptr;
         }
+        int rc;
+        if (mode == 1 && (rc = build_plans())) return rc;
+        const Phys ph = phys_of(b->ctx[0]);
         if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return cuda_check(cudaGetLastError(), "begin capture");
-        int n = 0, rc = FR_OK;
-        for (int st = 0; st < 4 && !rc; ++st) rc = stage(st, cap, n);
+        int n = 0;
+        rc = FR_OK;
+        for (int st = 0; st < 4 && !rc; ++st) {
+            if (mode == 1) {
+                rc = cuda_check(launch_stage<T>(plan[st], ph, bar, serr, -1, stage_grid_n, cap), "stage launch");
+                ++n;
+            } else {
+                rc = stage(st, cap, n);
+            }
+        }
         cudaError_t e = cudaStreamEndCapture(cap, &graph);
         if (rc) return rc;
         if (e != cudaSuccess) return cuda_check(e, "end capture");
         if ((rc = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate"))) return rc;
         launches_per_step = n;
+        if (mode == 2) launches_grouped = n;
+        graph_mode = mode;
         return FR_OK;
+    }
+
+    // FR_ERR_TIMEOUT (once; the status and the barrier words are cleared so
+    // the batch stays usable) if a barrier wait of the stage kernel ran out
+    int check(cudaStream_t s) override {
+        int h = 0, rc;
+        if ((rc = cuda_check(cudaStreamSynchronize(s), "batch check sync")) ||
+            (rc = cuda_check(cudaStreamSynchronize(cap), "batch check sync")) ||
+            (rc = cuda_check(cudaMemcpy(&h, serr, sizeof(int), cudaMemcpyDeviceToHost), "batch status")))
+            return rc;
+        if (!h) return FR_OK;
+        if ((rc = cuda_check(cudaMemset(serr, 0, sizeof(int)), "batch status reset")) ||
+            (rc = cuda_check(cudaMemset(bar, 0, 2 * sizeof(unsigned)), "batch barrier reset")))
+            return rc;
+        return set_err(FR_ERR_TIMEOUT, "a grid barrier of the persistent stage kernel gave up (code " +
+                                           std::to_string(h) + ")");
+    }
+
+    // one stage without its divergence, launched with CTA 0 taking no part:
+    // every other CTA's first barrier wait must run out and be reported
+    int selftest(cudaStream_t s) override {
+        int rc;
+        if ((rc = check(s)) && rc != FR_ERR_TIMEOUT) return rc;
+        const StagePlan<T> pl = make_plan(0, false);
+        int grid = 0;
+        if ((rc = cuda_check(stage_grid<T>(pl, &grid), "stage grid"))) return rc;
+        if (grid < 2) return set_err(FR_ERR_UNSUPPORTED, "the self-test needs two CTAs");
+        if ((rc = cuda_check(launch_stage<T>(pl, phys_of(b->ctx[0]), bar, serr, 0, grid, s), "self-test launch")))
+            return rc;
+        rc = check(s);
+        if (rc == FR_ERR_TIMEOUT) return FR_OK;
+        if (rc) return rc;
+        return set_err(FR_ERR_CUDA, "the withheld barrier arrival did not end in a reported timeout");
     }
 
     int step(const double *dt, int nsteps, int batched, cudaStream_t s) override {
@@ -358,11 +486,12 @@ struct BatchImpl : BatchBase {
             return FR_OK;
         }
         int rc;
+        const int mode = batched == 2 ? 2 : 1;
         const bool new_dt = dt_cur.size() != b->ctx.size() ||
                             !std::equal(dt_cur.begin(), dt_cur.end(), dt) || !div[0].d;
         if ((rc = set_dt(dt))) return rc;
-        if (!exec || new_dt)
-            if ((rc = capture())) return rc;
+        if (!exec || new_dt || graph_mode != mode)
+            if ((rc = capture(mode))) return rc;
         // order the internal capture stream after the caller's stream
         if ((rc = cuda_check(cudaEventRecord(ev_in, s), "event")) ||
             (rc = cuda_check(cudaStreamWaitEvent(cap, ev_in, 0), "wait")))
@@ -547,6 +676,8 @@ struct BatchImpl : BatchBase {
         out[9] = div[0].grid;
         out[10] = flux.grid;
         out[11] = face.grid;
+        out[12] = stage_grid_n;
+        out[13] = launches_grouped;
     }
 };
 
@@ -620,6 +751,16 @@ int fr_batch_step(fr_batch *b, const double *dt, int nsteps, int batched, void *
                 return set_err(FR_ERR_UNSUPPORTED, "batched steps do not apply a learned closure");
     }
     return b->impl->step(dt, nsteps, batched, (cudaStream_t)stream);
+}
+
+int fr_batch_check(fr_batch *b, void *stream) {
+    if (!b) return set_err(FR_ERR_ARG, "null batch");
+    return b->impl->check((cudaStream_t)stream);
+}
+
+int fr_batch_selftest_wait_timeout(fr_batch *b, void *stream) {
+    if (!b) return set_err(FR_ERR_ARG, "null batch");
+    return b->impl->selftest((cudaStream_t)stream);
 }
 
 int fr_batch_info(const fr_batch *b, int64_t *out) {

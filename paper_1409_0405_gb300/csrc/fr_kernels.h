@@ -274,6 +274,46 @@ cudaError_t launch_face_grouped(const FaceItem<T> *items, const int64_t *begin, 
 template <typename T>
 cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *begin, int n, int64_t total, int grid,
                                   cudaStream_t s);
+// One RK stage of a batch as one persistent cooperative launch: the phases
+// run in order, separated by grid-wide barriers whose waits are bounded.
+// A phase holds a grouped operator application (descriptor list as for
+// launch_gemm_grouped, with its row-chunk size rc and mode) and/or
+// point-wise work (flux items; face items with which = 0 common solution,
+// 1 common flux) that does not depend on it.
+template <typename T>
+struct StagePhase {
+    const GemmArgsT<T> *descs = nullptr;
+    const int64_t *begin = nullptr;
+    int ndesc = 0, mode = 0, rc = 0, maxK = 0;
+    int64_t total = 0;
+    const FluxItem<T> *fitems = nullptr;
+    const int64_t *fbegin = nullptr;
+    int fn = 0, xform = 0;
+    int64_t ftotal = 0;
+    const FaceItem<T> *citems = nullptr;
+    const int64_t *cbegin = nullptr;
+    int cn = 0, which = 0;
+    int64_t ctotal = 0;
+};
+constexpr int kMaxStagePhases = 8;
+template <typename T>
+struct StagePlan {
+    StagePhase<T> ph[kMaxStagePhases];
+    int nph = 0;
+};
+// error code a barrier wait that ran out writes to *err
+constexpr int kStageTimeout = 11;
+// the largest co-resident grid of the stage kernel for this plan
+template <typename T>
+cudaError_t stage_grid(const StagePlan<T> &plan, int *grid);
+// bar: 2 device words (arrivals, generation), zero before the first launch;
+// err: device int (0: fine; set to kStageTimeout when a wait runs out, after
+// which every later stage launch returns at once).  skip_block >= 0 (the
+// bounded-wait self-test only): that CTA takes no part, so the first
+// barrier's waits run out and the kernel returns with the error set.
+template <typename T>
+cudaError_t launch_stage(const StagePlan<T> &plan, const Phys &ph, unsigned *bar, int *err, int skip_block, int grid,
+                         cudaStream_t s);
 // transformed reference flux at solution points, FT = S F_ref (padding 0)
 cudaError_t launch_const_flux(int nu, int64_t ne, int64_t np, const double *S, double *FT, const Phys &ph,
                               cudaStream_t s);

@@ -38,7 +38,8 @@ EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_rk45_error", "fr_rk45_get_error", "fr_step_rk45_adaptive", "fr_reduce",
            "fr_diagnostics", "fr_selftest_wait_timeout", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
-           "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info",
+           "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_check",
+           "fr_batch_selftest_wait_timeout", "fr_batch_info",
            "fr_transfer", "fr_transfer_state", "fr_closure_features", "fr_closure_sample",
            "fr_closure_set", "fr_mlp_nparams", "fr_mlp_workspace", "fr_mlp_forward", "fr_mlp_grad",
            "fr_mlp_adam", "fr_partition", "fr_part_plan", "fr_part_create", "fr_part_destroy",
@@ -124,7 +125,10 @@ def load():
     lib.fr_batch_tune.argtypes = [vp, vp]
     lib.fr_batch_step.argtypes = [vp, dp, C.c_int, C.c_int, vp]
     lib.fr_batch_info.argtypes = [vp, i64p]
-    for name in ("fr_batch_create", "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info"):
+    lib.fr_batch_check.argtypes = [vp, vp]
+    lib.fr_batch_selftest_wait_timeout.argtypes = [vp, vp]
+    for name in ("fr_batch_create", "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_info",
+                 "fr_batch_check", "fr_batch_selftest_wait_timeout"):
         getattr(lib, name).restype = C.c_int
     lib.fr_transfer.argtypes = [C.c_int, C.c_int, C.c_int, dp, i64p, i64p]
     lib.fr_transfer_state.argtypes = [vp, vp, vp, vp, vp]
@@ -503,7 +507,8 @@ class Batch:
     """fr_batch: many independent problems advanced with grouped launches."""
 
     INFO = ("nprob", "ndof", "launches_batched", "launches_per_problem", "rc_m0", "rc_grad",
-            "rc_m0grad", "rc_div", "grid_gemm", "grid_div", "grid_flux", "grid_face")
+            "rc_m0grad", "rc_div", "grid_gemm", "grid_div", "grid_flux", "grid_face", "grid_stage",
+            "launches_grouped")
 
     def __init__(self, meshes, orders, **params):
         lib = load()
@@ -523,7 +528,7 @@ class Batch:
             self.problems.append(Context(None, 0, _handle=ch, _owner=self, **params))
 
     def info(self):
-        out = (C.c_int64 * 12)()
+        out = (C.c_int64 * len(self.INFO))()
         _check(self._lib.fr_batch_info(self._h, out))
         return dict(zip(self.INFO, list(out)))
 
@@ -531,9 +536,22 @@ class Batch:
         _check(self._lib.fr_batch_tune(self._h, C.c_void_p(stream) if stream else None))
 
     def step(self, dt, nsteps=1, batched=True, stream=None):
+        """fr_batch_step: batched True or 1 = one persistent launch per RK
+        stage, 2 = grouped launches per class, False or 0 = each problem's
+        own launches."""
         dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (len(self.problems),)))
-        _check(self._lib.fr_batch_step(self._h, _dptr(dts), int(nsteps), int(bool(batched)),
+        mode = int(batched) if not isinstance(batched, bool) else (1 if batched else 0)
+        _check(self._lib.fr_batch_step(self._h, _dptr(dts), int(nsteps), mode,
                                        C.c_void_p(stream) if stream else None))
+
+    def check(self, stream=None):
+        """fr_batch_check: raises FRError (FR_ERR_TIMEOUT) after a barrier
+        wait of the persistent stage kernel ran out."""
+        _check(self._lib.fr_batch_check(self._h, C.c_void_p(stream) if stream else None))
+
+    def selftest_wait_timeout(self, stream=None):
+        """fr_batch_selftest_wait_timeout (bounded-wait self-test)."""
+        _check(self._lib.fr_batch_selftest_wait_timeout(self._h, C.c_void_p(stream) if stream else None))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1,5 +1,9 @@
-"""The batched engine (grouped persistent launches + CUDA graph) against
-the per-problem launch sequence (bit for bit) and against the FP64 oracle."""
+"""The batched engine against the per-problem launch sequence (bit for bit)
+and against the FP64 oracle, in both of its schedules: one persistent
+cooperative launch per RK stage (phases separated by grid barriers with
+bounded waits), and one grouped launch per operator class; both replayed
+from a CUDA graph.  The barrier's bounded wait is exercised by withholding
+one CTA (a reported timeout, no fault)."""
 import numpy as np
 import pytest
 
@@ -50,18 +54,26 @@ def test_batched_equals_per_problem(precision):
         return [c.get_state() for c in b.problems]
 
     ref = run(False)
-    got = run(True)
+    got = run(True)                                   # one persistent launch per stage
     for r, g in zip(ref, got):
         np.testing.assert_array_equal(g, r)
     info = b.info()
-    assert info["launches_batched"] == 4 * 4          # Euler: M0, flux, common flux, div per stage
+    assert info["launches_batched"] == 4              # one per RK stage
+    assert info["grid_stage"] > 0
+    got_g = run(2)                                    # grouped launches per class
+    for r, g in zip(ref, got_g):
+        np.testing.assert_array_equal(g, r)
+    info = b.info()
+    assert info["launches_batched"] == info["launches_grouped"] == 4 * 4   # Euler: M0, flux, common flux, div
     # per problem and stage: 2 types x (M0, flux, div) + 1 face kernel (Euler)
     per = sum(4 * (3 * ((c.info["n_tet"] > 0) + (c.info["n_pri"] > 0)) + 1) for c in b.problems)
-    assert info["launches_per_problem"] == per > info["launches_batched"]
+    assert info["launches_per_problem"] == per > info["launches_grouped"]
     b.tune()
-    got2 = run(True)
-    for r, g in zip(ref, got2):
-        np.testing.assert_array_equal(g, r)
+    for mode in (True, 2):
+        got2 = run(mode)
+        for r, g in zip(ref, got2):
+            np.testing.assert_array_equal(g, r)
+    b.check()
     b.close()
 
 
@@ -108,7 +120,7 @@ def test_batched_navier_stokes_equals_per_problem(precision):
              (synth.vortex_box(n=4, n_prism_layers=2, seed=33), 1)]
     prm = dict(viscous=True, mu=0.02, precision=precision, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0, rho_inf=1.0)
     states = []
-    for batched in (False, True):
+    for batched in (False, True, 2):
         b = fr.Batch([m for m, _ in probs], [p for _, p in probs], **prm)
         for c in b.problems:
             q = synth.isentropic_vortex(c.upts_points())
@@ -120,6 +132,46 @@ def test_batched_navier_stokes_equals_per_problem(precision):
             c.set_state(np.concatenate(out))
         b.step([2e-3] * len(probs), 3, batched=batched)
         states.append([c.get_state() for c in b.problems])
+        if batched is True:
+            assert b.info()["launches_batched"] == 4
+        b.check()
         b.close()
-    for a, g in zip(*states):
+    for other in states[1:]:
+        for a, g in zip(states[0], other):
+            np.testing.assert_array_equal(g, a)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_stage_barrier_timeout_is_reported_and_recovered(precision):
+    """Failure detection of the persistent stage kernel: one CTA is withheld
+    from the grid barriers, every other CTA's bounded wait (~2 s) runs out,
+    the timeout is reported through fr_batch_check and cleared, and the
+    batch then steps bit-identically to the per-problem launches."""
+    from paper_1409_0405_gb300 import fr
+    probs = _problems()
+    b = fr.Batch([m for m, _ in probs], [p for _, p in probs], precision=precision)
+    pub = [_uniform_pub(c) + 0.0 for c in b.problems]
+    for c, u in zip(b.problems, pub):
+        c.set_state(u)
+    b.selftest_wait_timeout()
+    b.check()                                          # the status was cleared
+    q = [synth.isentropic_vortex(c.upts_points()) for c in b.problems]
+    pub = []
+    for c, x in zip(b.problems, q):
+        out, off = [], 0
+        for ne, nu in c.counts():
+            if ne:
+                out.append(x[off:off + ne * nu].reshape(ne, nu, 5).transpose(0, 2, 1).reshape(-1))
+                off += ne * nu
+        pub.append(np.concatenate(out))
+    dts = [0.01, 0.02, 0.005, 0.01]
+    res = []
+    for batched in (False, True):
+        for c, u in zip(b.problems, pub):
+            c.set_state(u)
+        b.step(dts, 2, batched=batched)
+        res.append([c.get_state() for c in b.problems])
+    for a, g in zip(*res):
         np.testing.assert_array_equal(g, a)
+    b.check()
+    b.close()

@@ -494,7 +494,8 @@ int step_guard(const fr_ctx *c) {
 
 int step_check(fr_ctx *c, cudaStream_t s) {
     if (!c->nf_dev) return FR_OK;
-    const int nb = 2 * num_sms(c->device);
+    // enough CTAs to keep the loads of a streaming read in flight
+    const int nb = 16 * num_sms(c->device);
     for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;

@@ -420,7 +420,7 @@ def synth_mod():
     return synth
 
 
-def batch_mode(fr, torch, args, sp):
+def batch_mode(fr, torch, args, sp, nprob=64):
     """64 independent periodic isentropic-vortex problems (element counts
     log-uniform in [1k, 80k], prism:tet ratio uniform in [0, 1], order in
     {1..4}, seed 3), FP32 with FP64 RK registers: grouped launches replayed
@@ -429,7 +429,7 @@ def batch_mode(fr, torch, args, sp):
     import synth
     t0 = time.perf_counter()
     meshes, orders = [], []
-    for i in range(64):
+    for i in range(nprob):
         m, p = synth.batch_problem_mesh(i)
         meshes.append(m)
         orders.append(p)
@@ -493,7 +493,7 @@ def batch_mode(fr, torch, args, sp):
                          "bytes": "staged pipeline minimum: operators in/out + epilogue registers, flux point "
                                   "data, face gathers and metadata (bench.batch_mode)",
                          "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
-            "ndof": info["ndof"], "problems": 64, "tuned": {k: info[k] for k in fr.Batch.INFO[4:12]},
+            "ndof": info["ndof"], "problems": nprob, "tuned": {k: info[k] for k in fr.Batch.INFO[4:12]},
             "setup_s": setup_s, "tune_s": tune_s, "state_finite": bool(finite),
             "workload": "64 periodic isentropic-vortex boxes, Euler, FP32 + FP64 RK, seeds 3/1000+i"}
 
@@ -891,6 +891,8 @@ def main():
                          "precision and print their state and diagnostics errors against FP64")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3", "tf32x3"],
                     help="arithmetic of the main timed step (default fp64, the headline workload)")
+    ap.add_argument("--batched-only", type=int, default=0,
+                    help="profiling: time only the batched mode on its first N problems and print its entry")
     args = ap.parse_args()
 
     if args.cpu_oracle_child:
@@ -942,6 +944,12 @@ def main():
     def barrier():
         if world > 1:
             torch.distributed.barrier()
+
+    if args.batched_only > 0:
+        if rank == 0:
+            sp0 = torch.cuda.Stream().cuda_stream
+            print(json.dumps({"batched": batch_mode(fr, torch, args, sp0, nprob=args.batched_only)}))
+        return
 
     if args.state_error_steps > 0:
         if rank == 0:

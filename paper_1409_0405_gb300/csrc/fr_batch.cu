@@ -223,12 +223,12 @@ struct BatchImpl : BatchBase {
         // kernel (the arithmetic of the per-problem launches)
         grad.mode = xform ? GEMM_STORE : GEMM_GRAD;
         m0g.mode = GEMM_STORE;
-        m0.rc = 16;
-        grad.rc = 12;
-        m0g.rc = 16;
+        m0.rc = kMaxBatchRC;
+        grad.rc = kMaxBatchRC;
+        m0g.rc = kMaxBatchRC;
         for (auto &g : div) {
             g.mode = GEMM_DIV_RK;
-            g.rc = 16;
+            g.rc = kMaxBatchRC;
         }
         for (fr_ctx *c : b->ctx) {
             for (int t = 0; t < NT; ++t) {
@@ -406,7 +406,7 @@ struct BatchImpl : BatchBase {
 
     int build_plans() {
         for (int st = 0; st < 4; ++st) plan[st] = make_plan(st, true);
-        return cuda_check(stage_grid<T>(plan[0], &stage_grid_n), "stage grid");
+        return cuda_check(stage_grid<T>(plan[0], viscous ? 1 : 0, &stage_grid_n), "stage grid");
     }
 
     int capture(int mode) {
@@ -466,7 +466,7 @@ struct BatchImpl : BatchBase {
         if ((rc = check(s)) && rc != FR_ERR_TIMEOUT) return rc;
         const StagePlan<T> pl = make_plan(0, false);
         int grid = 0;
-        if ((rc = cuda_check(stage_grid<T>(pl, &grid), "stage grid"))) return rc;
+        if ((rc = cuda_check(stage_grid<T>(pl, viscous ? 1 : 0, &grid), "stage grid"))) return rc;
         if (grid < 2) return set_err(FR_ERR_UNSUPPORTED, "the self-test needs two CTAs");
         if ((rc = cuda_check(launch_stage<T>(pl, phys_of(b->ctx[0]), bar, serr, 0, grid, s), "self-test launch")))
             return rc;
@@ -538,7 +538,7 @@ struct BatchImpl : BatchBase {
         int best_rc = g.rc, best_grid = g.grid;
         float best = 1e30f;
         for (int rc : kGroupedRCs) {
-            if (g.mode == GEMM_GRAD && rc % 3) continue;
+            if (rc > kMaxBatchRC || (g.mode == GEMM_GRAD && rc % 3)) continue;
             if ((size_t)rc * (g.maxK ? g.maxK : 1) * sizeof(T) > 200 * 1024) continue;
             g.rc = rc;
             int e = upload_group(g);

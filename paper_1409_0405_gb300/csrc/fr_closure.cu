@@ -79,19 +79,6 @@ struct Scale5 {
     double s[5];
 };
 
-// add[j][v][e] = rfs[j][v][e] + scale_v Y[v nu + j][e]  (feature-major Y)
-__global__ void k_correction_fm(int nu, int64_t ne, int64_t np, const double *__restrict__ rfs,
-                                const float *__restrict__ Y, Scale5 scale, double *__restrict__ add) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)nu * 5 * np;
-    if (i >= total) return;
-    const int64_t e = i % np, row = i / np;
-    const int j = (int)(row / 5), v = (int)(row % 5);
-    double a = rfs ? rfs[i] : 0.0;
-    if (e < ne) a += scale.s[v] * (double)Y[((int64_t)v * nu + j) * np + e];
-    add[i] = a;
-}
-
 // out[r][i] = sum_j R[i][j] in[r][j] over rows r = (e, v) of one type's
 // public block
 __global__ void k_transfer(int64_t rows, int nto, int nfrom, const double *__restrict__ R,
@@ -147,8 +134,9 @@ cudaError_t launch_features(const DevType &D, const T *in, float *X, cudaStream_
     return cudaGetLastError();
 }
 
-// features (feature-major), the three layers on the tensor cores with the
-// weight images packed by fr_closure_set, and the correction: 5 launches
+// features (feature-major) and the three layers on the tensor cores with
+// the weight images packed by fr_closure_set, the last writing the RHS
+// correction rfs + scale * y in the FR layout: 4 launches
 template <typename T>
 int closure_apply(fr_ctx *c, int t, const T *in, cudaStream_t s) {
     DevType &D = c->T[t];
@@ -162,16 +150,15 @@ int closure_apply(fr_ctx *c, int t, const T *in, cudaStream_t s) {
             if (r != cudaSuccess) return r;
             MlpWs w = mlp_ws(nin, D.cl_nh, nout, D.np, D.cl_ws);
             for (int k = 0; k < 3; ++k) w.op[k] = D.cl_op[k];
-            if ((r = mlp_forward_fm(nin, D.cl_nh, nout, D.np, D.cl_X, D.cl_P, D.cl_Y, w, false, c->tc_err, s)) !=
-                cudaSuccess)
-                return r;
-            Scale5 sc;
-            for (int v = 0; v < 5; ++v) sc.s[v] = D.cl_scale[v];
-            k_correction_fm<<<nblk((int64_t)D.nu * 5 * D.np, 256), 256, 0, s>>>(D.nu, D.ne, D.np, D.Rfs, D.cl_Y, sc,
-                                                                               D.cl_add);
-            return cudaGetLastError();
+            ClosureOut co;
+            co.add = D.cl_add;
+            co.rfs = D.Rfs;
+            co.nu = D.nu;
+            co.ne = D.ne;
+            for (int v = 0; v < 5; ++v) co.scale[v] = D.cl_scale[v];
+            return mlp_forward_fm(nin, D.cl_nh, nout, D.np, D.cl_X, D.cl_P, D.cl_Y, w, false, c->tc_err, s, &co);
         },
-        5);
+        4);
     return cuda_check(e, "closure");
 }
 

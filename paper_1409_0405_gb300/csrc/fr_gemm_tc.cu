@@ -210,6 +210,21 @@ __device__ __forceinline__ float gelu_df(float x) {
 template <int MODE>
 __device__ __forceinline__ void epi_group(const GemmArgsT<float> &g, int c0, int64_t n, int64_t e, const float *v) {
     if (MODE == GEMM_BIAS_ACT) {
+        if (g.cl_add) {
+            // the closure's output layer: the RHS correction in the FR layout
+#pragma unroll
+            for (int t = 0; t < 24; ++t) {
+                const int j = c0 + t;
+                if (j < g.M) {
+                    const int var = j / g.cl_nu, pt = j - var * g.cl_nu;
+                    const int64_t o = ((int64_t)pt * 5 + var) * g.np + n;
+                    double a = g.rfs ? g.rfs[o] : 0.0;
+                    if (n < g.cl_ne) a += g.cl_scale[var] * (double)(v[t] + __ldg(g.bias + j));
+                    g.cl_add[o] = a;
+                }
+            }
+            return;
+        }
         // a network layer: Z = A B + bias (kept for the backward pass), gelu
 #pragma unroll
         for (int t = 0; t < 24; ++t) {

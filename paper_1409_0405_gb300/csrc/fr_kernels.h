@@ -84,6 +84,14 @@ struct GemmArgsT {
     float *Z = nullptr;
     const float *Zin = nullptr;
     int act = 0;
+    // GEMM_BIAS_ACT, the closure's output layer inside the RHS: instead of
+    // C, write the FP64 correction rfs + cl_scale[var] (A B + bias) to
+    // cl_add in the FR layout [point][var][element] (output row
+    // var * cl_nu + point; rfs may be null; elements >= cl_ne get rfs only)
+    double *cl_add = nullptr;
+    int cl_nu = 0;
+    int64_t cl_ne = 0;
+    double cl_scale[5] = {0, 0, 0, 0, 0};
 };
 using GemmArgs = GemmArgsT<double>;
 
@@ -296,6 +304,9 @@ struct StagePhase {
     int64_t ctotal = 0;
 };
 constexpr int kMaxStagePhases = 8;
+// row-chunk sizes of the batched engine (both schedules): 6, 8 or 12; the
+// persistent stage kernel is compiled for these only (register budget)
+constexpr int kMaxBatchRC = 12;
 template <typename T>
 struct StagePlan {
     StagePhase<T> ph[kMaxStagePhases];
@@ -303,9 +314,10 @@ struct StagePlan {
 };
 // error code a barrier wait that ran out writes to *err
 constexpr int kStageTimeout = 11;
-// the largest co-resident grid of the stage kernel for this plan
+// the largest co-resident grid of the stage kernel for this plan (viscous:
+// the Navier-Stokes instantiation, else the Euler one)
 template <typename T>
-cudaError_t stage_grid(const StagePlan<T> &plan, int *grid);
+cudaError_t stage_grid(const StagePlan<T> &plan, int viscous, int *grid);
 // bar: 2 device words (arrivals, generation), zero before the first launch;
 // err: device int (0: fine; set to kStageTimeout when a wait runs out, after
 // which every later stage launch returns at once).  skip_block >= 0 (the

@@ -263,7 +263,7 @@ cudaError_t mlp_pack_forward(int nin, int nh, int nout, const float *P, MlpWs &w
 }
 
 cudaError_t mlp_forward_fm(int nin, int nh, int nout, int64_t np, const float *X, const float *P, float *Y,
-                           const MlpWs &w, bool keep_z, int *err, cudaStream_t s) {
+                           const MlpWs &w, bool keep_z, int *err, cudaStream_t s, const ClosureOut *cl) {
     const MlpLayout L = mlp_layout(nin, nh, nout);
     cudaError_t e;
     if ((e = tc_layer(w.op[0], nh, nin, np, X, w.H1, GEMM_BIAS_ACT, P + L.b1, keep_z ? w.Z1 : nullptr, nullptr, 1,
@@ -272,7 +272,24 @@ cudaError_t mlp_forward_fm(int nin, int nh, int nout, int64_t np, const float *X
     if ((e = tc_layer(w.op[1], nh, nh, np, w.H1, w.H2, GEMM_BIAS_ACT, P + L.b2, keep_z ? w.Z2 : nullptr, nullptr, 1,
                       err, s)) != cudaSuccess)
         return e;
-    return tc_layer(w.op[2], nout, nh, np, w.H2, Y, GEMM_BIAS_ACT, P + L.b3, nullptr, nullptr, 0, err, s);
+    if (!cl) return tc_layer(w.op[2], nout, nh, np, w.H2, Y, GEMM_BIAS_ACT, P + L.b3, nullptr, nullptr, 0, err, s);
+    // the output layer writes the RHS correction directly
+    GemmArgsT<float> g;
+    g.M = nout;
+    g.N = np;
+    g.K1 = nh;
+    g.B1 = w.H2;
+    g.ldb1 = np;
+    g.ldc = np;
+    g.mode = GEMM_BIAS_ACT;
+    g.np = np;
+    g.bias = P + L.b3;
+    g.rfs = cl->rfs;
+    g.cl_add = cl->add;
+    g.cl_nu = cl->nu;
+    g.cl_ne = cl->ne;
+    for (int v = 0; v < 5; ++v) g.cl_scale[v] = cl->scale[v];
+    return launch_gemm_tc(g, w.op[2], err, s);
 }
 
 MlpLayout mlp_layout(int nin, int nh, int nout) {

@@ -29,11 +29,21 @@ struct MlpWs {
 MlpWs mlp_ws(int nin, int nh, int nout, int64_t n, float *ws);
 // packs W1, W2, W3 of the parameter vector P into the workspace's images
 cudaError_t mlp_pack_forward(int nin, int nh, int nout, const float *P, MlpWs &w, cudaStream_t s);
-// the forward pass on feature-major X [nin][np] into Y [nout][np] with the
-// packed images of w (H1, H2 and, with keep_z, Z1, Z2 in w); *err (device)
-// is set if a bounded wait of the tensor-core kernel gave up
+// the closure's use of the output: add = rfs + scale_var * y in the FR
+// layout [point][var][element] (nu points, ne elements, np columns)
+struct ClosureOut {
+    double *add = nullptr;
+    const double *rfs = nullptr;
+    int nu = 0;
+    int64_t ne = 0;
+    double scale[5] = {0, 0, 0, 0, 0};
+};
+// the forward pass on feature-major X [nin][np] into Y [nout][np] (or, with
+// cl, straight into the RHS correction) with the packed images of w (H1, H2
+// and, with keep_z, Z1, Z2 in w); *err (device) is set if a bounded wait of
+// the tensor-core kernel gave up
 cudaError_t mlp_forward_fm(int nin, int nh, int nout, int64_t np, const float *X, const float *P, float *Y,
-                           const MlpWs &w, bool keep_z, int *err, cudaStream_t s);
+                           const MlpWs &w, bool keep_z, int *err, cudaStream_t s, const ClosureOut *cl = nullptr);
 // Y (n x nout) = MLP(X (n x nin)); ws holds the activations afterwards
 cudaError_t mlp_forward(int nin, int nh, int nout, int64_t n, const float *X, const float *P, float *Y, float *ws,
                         cudaStream_t s);

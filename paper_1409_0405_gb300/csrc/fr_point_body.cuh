@@ -302,7 +302,9 @@ __device__ __forceinline__ T fref_n(const PhysT<T> &ph, int v, const T *n) {
     return ph.fref[v][0] * n[0] + ph.fref[v][1] * n[1] + ph.fref[v][2] * n[2];
 }
 
-template <typename T>
+// VIS: 0 = viscous terms as ph.viscous says (run time), 1 = inviscid, 2 =
+// viscous (known at compile time: the other branch is not compiled)
+template <typename T, int VIS = 0>
 __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, const FieldsT<T> &F, const PhysT<T> &ph,
                                                int64_t k) {
     if (k < P.n) {
@@ -321,7 +323,7 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
         // primitives once per side, for the Rusanov and the viscous flux
         const Prim<T> qa = prim(ua, ph.gamma), qb = prim(ub, ph.gamma);
         rusanov_q(ua, ub, qa, qb, n, ph.gamma, fn);
-        if (ph.viscous) {
+        if (VIS == 0 ? ph.viscous != 0 : VIS == 2) {
             T ga[3][V], gb[3][V], fva[V], fvb[V];
             load_grad(F.GUF[ta], fa, ea, npa, ga);
             load_grad(F.GUF[tb], fb, eb, npb, gb);
@@ -355,7 +357,7 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
         bnd_normal<T>(B, kb, n, mg);
         bc_states(B.btag[kb], u, n, ph, ghost, cb);
         rusanov(u, ghost, n, ph.gamma, fn);
-        if (ph.viscous) {
+        if (VIS == 0 ? ph.viscous != 0 : VIS == 2) {
             T g[3][V], fv[V];
             load_grad(F.GUF[t], f, e, np, g);
             Prim<T> qc = prim(cb, ph.gamma);
@@ -373,7 +375,7 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
 // physical gradient grad_m u = (1/J) sum_d S[d][m] g^_d is formed here,
 // written back over it (in place: one thread owns the point's 15 values) and
 // used for the viscous flux.
-template <typename T, bool XFORM>
+template <typename T, bool XFORM, int VIS = 0>
 __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T *__restrict__ U,
                                         T *__restrict__ GU, const T *__restrict__ S, const T *__restrict__ invJ,
                                         T *__restrict__ FT, const PhysT<T> &ph, int64_t j, int64_t e) {
@@ -395,7 +397,7 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
         for (int a = 0; a < 3; ++a) F[1 + a][m] = u[1 + a] * q.v[m] + (a == m ? q.p : T(0));
         F[4][m] = (u[4] + q.p) * q.v[m];
     }
-    if (ph.viscous) {
+    if (VIS == 0 ? ph.viscous != 0 : VIS == 2) {
         T g[3][V], Fv[V][3];
 #pragma unroll
         for (int m = 0; m < 3; ++m)

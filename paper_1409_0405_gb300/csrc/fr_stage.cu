@@ -81,19 +81,28 @@ __device__ __forceinline__ void gemm_unit(const StagePhase<T> &ph, int64_t bid, 
     const GemmArgsT<T> *g = ph.descs + lo;
     const int64_t local = bid - ph.begin[lo];
     constexpr bool m3 = MODE == GEMM_GRAD;  // row chunks in whole points (multiples of 3)
+    // the batch's row chunks are at most kMaxBatchRC (the register budget)
     switch (ph.rc) {
         case 6: gemm_unit_rc<T, 6, MODE>(g, local, sA); break;
         case 12: gemm_unit_rc<T, 12, MODE>(g, local, sA); break;
-        case 24: gemm_unit_rc<T, 24, MODE>(g, local, sA); break;
         case 8: gemm_unit_rc<T, (m3 ? 6 : 8), MODE>(g, local, sA); break;
-        case 16: gemm_unit_rc<T, (m3 ? 6 : 16), MODE>(g, local, sA); break;
-        case 32: gemm_unit_rc<T, (m3 ? 6 : 32), MODE>(g, local, sA); break;
         default: break;
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_stage(const StagePlan<T> plan, const PhysT<T> phys, unsigned *bar,
+// CTAs per SM the stage kernel is compiled for (its grid is all of them, so
+// this is its occupancy): the largest count whose register budget leaves
+// the operator blocks (row chunks up to 12) and the phase's point-wise code
+// without more than a few spilled words (ptxas -v)
+template <typename T, int VIS>
+constexpr int stage_min_blocks() {
+    return sizeof(T) == 4 ? (VIS == 1 ? 8 : 6) : (VIS == 1 ? 5 : 4);
+}
+
+// VIS: 1 Euler, 2 Navier-Stokes (compile time, so that an Euler batch does
+// not carry the viscous code's registers)
+template <typename T, int VIS>
+__global__ void __launch_bounds__(kThreads, stage_min_blocks<T, VIS>()) k_stage(const StagePlan<T> plan, const PhysT<T> phys, unsigned *bar,
                                                     int *err, int skip_block) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sA = reinterpret_cast<T *>(smem_raw);
@@ -108,7 +117,9 @@ __global__ void __launch_bounds__(kThreads) k_stage(const StagePlan<T> plan, con
             if (u < gu) {
                 switch (ph.mode) {
                     case GEMM_STORE: gemm_unit<T, GEMM_STORE>(ph, u, sA); break;
-                    case GEMM_GRAD: gemm_unit<T, GEMM_GRAD>(ph, u, sA); break;
+                    case GEMM_GRAD:
+                        if constexpr (VIS == 2) gemm_unit<T, GEMM_GRAD>(ph, u, sA);
+                        break;
                     case GEMM_DIV_RK: gemm_unit<T, GEMM_DIV_RK>(ph, u, sA); break;
                     default: break;
                 }
@@ -119,20 +130,20 @@ __global__ void __launch_bounds__(kThreads) k_stage(const StagePlan<T> plan, con
                     const int i = find_item(ph.fbegin, ph.fn, gi);
                     const FluxItem<T> &it = ph.fitems[i];
                     const int64_t idx = gi - ph.fbegin[i], j = idx / it.np;
-                    if (ph.xform)
-                        flux_at<T, true>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, it.invJ, it.FT,
-                                         phys, j, idx - j * it.np);
+                    if (VIS == 2 && ph.xform)
+                        flux_at<T, true, VIS>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, it.invJ,
+                                              it.FT, phys, j, idx - j * it.np);
                     else
-                        flux_at<T, false>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, it.invJ, it.FT,
-                                          phys, j, idx - j * it.np);
+                        flux_at<T, false, VIS>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, it.invJ,
+                                               it.FT, phys, j, idx - j * it.np);
                 }
             } else {
                 const int64_t gi = (u - gu - fu) * kThreads + threadIdx.x;
                 if (gi < ph.ctotal) {
                     const int i = find_item(ph.cbegin, ph.cn, gi);
                     const FaceItem<T> &it = ph.citems[i];
-                    if (ph.which == 0) common_solution_at(it.P, it.B, it.F, phys, gi - ph.cbegin[i]);
-                    else common_flux_at(it.P, it.B, it.F, phys, gi - ph.cbegin[i]);
+                    if (VIS == 2 && ph.which == 0) common_solution_at(it.P, it.B, it.F, phys, gi - ph.cbegin[i]);
+                    else common_flux_at<T, VIS>(it.P, it.B, it.F, phys, gi - ph.cbegin[i]);
                 }
             }
         }
@@ -152,25 +163,23 @@ size_t stage_smem(const StagePlan<T> &plan) {
     return m;
 }
 
-template <typename T>
+template <typename T, int VIS>
 cudaError_t configure_stage() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_stage<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_stage<T, VIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess) done = true;
     return e;
 }
 
-}  // namespace
-
-template <typename T>
-cudaError_t stage_grid(const StagePlan<T> &plan, int *grid) {
-    cudaError_t e = configure_stage<T>();
+template <typename T, int VIS>
+cudaError_t stage_grid_vis(const StagePlan<T> &plan, int *grid) {
+    cudaError_t e = configure_stage<T, VIS>();
     if (e != cudaSuccess) return e;
     const size_t smem = stage_smem(plan);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     int per_sm = 0, dev = 0, nsm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<T>, kThreads, smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<T, VIS>, kThreads, smem)) != cudaSuccess)
         return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -179,29 +188,43 @@ cudaError_t stage_grid(const StagePlan<T> &plan, int *grid) {
     return cudaSuccess;
 }
 
-template <typename T>
-cudaError_t launch_stage(const StagePlan<T> &plan, const Phys &ph, unsigned *bar, int *err, int skip_block, int grid,
-                         cudaStream_t s) {
-    cudaError_t e = configure_stage<T>();
+template <typename T, int VIS>
+cudaError_t launch_stage_vis(const StagePlan<T> &plan, const PhysT<T> &pt, unsigned *bar, int *err, int skip_block,
+                             int grid, cudaStream_t s) {
+    cudaError_t e = configure_stage<T, VIS>();
     if (e != cudaSuccess) return e;
-    const size_t smem = stage_smem(plan);
-    if (smem > 200 * 1024 || grid <= 0 || plan.nph <= 0 || plan.nph > kMaxStagePhases) return cudaErrorInvalidValue;
-    const PhysT<T> pt = phys_t<T>(ph);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = stage_smem(plan);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_stage<T>, plan, pt, bar, err, skip_block);
+    return cudaLaunchKernelEx(&cfg, k_stage<T, VIS>, plan, pt, bar, err, skip_block);
 }
 
-template cudaError_t stage_grid<float>(const StagePlan<float> &, int *);
-template cudaError_t stage_grid<double>(const StagePlan<double> &, int *);
+}  // namespace
+
+template <typename T>
+cudaError_t stage_grid(const StagePlan<T> &plan, int viscous, int *grid) {
+    return viscous ? stage_grid_vis<T, 2>(plan, grid) : stage_grid_vis<T, 1>(plan, grid);
+}
+
+template <typename T>
+cudaError_t launch_stage(const StagePlan<T> &plan, const Phys &ph, unsigned *bar, int *err, int skip_block, int grid,
+                         cudaStream_t s) {
+    const size_t smem = stage_smem(plan);
+    if (smem > 200 * 1024 || grid <= 0 || plan.nph <= 0 || plan.nph > kMaxStagePhases) return cudaErrorInvalidValue;
+    const PhysT<T> pt = phys_t<T>(ph);
+    return ph.viscous ? launch_stage_vis<T, 2>(plan, pt, bar, err, skip_block, grid, s)
+                      : launch_stage_vis<T, 1>(plan, pt, bar, err, skip_block, grid, s);
+}
+
+template cudaError_t stage_grid<float>(const StagePlan<float> &, int, int *);
+template cudaError_t stage_grid<double>(const StagePlan<double> &, int, int *);
 template cudaError_t launch_stage<float>(const StagePlan<float> &, const Phys &, unsigned *, int *, int, int,
                                          cudaStream_t);
 template cudaError_t launch_stage<double>(const StagePlan<double> &, const Phys &, unsigned *, int *, int, int,

@@ -40,6 +40,8 @@ CASES = {
     "bl_ns_p3": (lambda: synth.boundary_layer_box(nx=8, nz=3, n_prism_layers=4, n_tet_layers=3), 3,
                  bl_params(mu=0.01), "bl"),
     "hexprism_ns_p2": (lambda: synth.hex_box(n=4, n_hex_cols=2), 2, dict(viscous=True, mu=0.02), "smooth"),
+    "curved_ns_p3": (lambda: synth.curve_mesh(synth.vortex_box(n=3), amp=0.15), 3, dict(viscous=True, mu=0.02),
+                     "smooth"),
 }
 
 

@@ -111,3 +111,18 @@ def test_reduced_precision_rk45_state_error(prec):
     print(prec, "20-step increment error:", err)
     assert np.all(err <= (1e-4 if prec != "FR_BF16X3" else 2e-3)), err
     ctx.reduce()   # raises on a tensor-core wait that gave up
+
+
+def test_rk45_queries_before_a_step_are_rejected():
+    """The error norm and register exist only after an RK45 step."""
+    from paper_1409_0405_gb300 import fr
+    sol, ctx = make_pair(synth.vortex_box(), 1)
+    ctx.set_state(state(sol, "vortex"))
+    with pytest.raises(fr.FRError) as ei:
+        ctx.rk45_error(1e-6, 1e-6)
+    assert ei.value.code == fr.FR_ERR_ARG
+    with pytest.raises(fr.FRError):
+        ctx.rk45_get_error()
+    ctx.step_rk45(1e-4, 0)                    # no step: nothing allocated, no error
+    with pytest.raises(fr.FRError):
+        ctx.step_rk45_adaptive(1.0, 1e-3, 0.0, 0.0)   # atol + rtol must be positive

@@ -40,7 +40,8 @@ __global__ void k_common_solution(const Pairs P, const Bnd B, const FieldsT<T> F
 
 template <typename T>
 __global__ void k_common_flux(const Pairs P, const Bnd B, const FieldsT<T> F, const PhysT<T> ph) {
-    common_flux_at(P, B, F, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (ph.viscous) common_flux_at<T, 2>(P, B, F, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    else common_flux_at<T, 1>(P, B, F, ph, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -139,7 +140,11 @@ template <typename T, bool XFORM>
 __global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, T *__restrict__ GU,
                        const T *__restrict__ S, const T *__restrict__ invJ, T *__restrict__ FT, const PhysT<T> ph) {
     // 2-D grid: y = solution point, x = element
-    flux_at<T, XFORM>(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.y,
+    if (ph.viscous)
+        flux_at<T, XFORM, 2>(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.y,
+                             (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    else
+        flux_at<T, XFORM, 1>(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.y,
                       (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -154,7 +159,11 @@ __global__ void k_flux_grouped(const FluxItem<T> *__restrict__ items, const int6
         const int i = find_item(begin, n, gi);
         const FluxItem<T> &it = items[i];
         const int64_t idx = gi - begin[i], j = idx / it.np;
-        flux_at<T, XFORM>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, it.invJ, it.FT, ph, j,
+        if (ph.viscous)
+            flux_at<T, XFORM, 2>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, it.invJ, it.FT, ph, j,
+                                 idx - j * it.np);
+        else
+            flux_at<T, XFORM, 1>(it.nu, it.ne, it.np, it.U, const_cast<T *>(it.GU), it.S, it.invJ, it.FT, ph, j,
                           idx - j * it.np);
     }
 }
@@ -167,7 +176,8 @@ __global__ void k_face_grouped(const FaceItem<T> *__restrict__ items, const int6
         const int i = find_item(begin, n, gi);
         const FaceItem<T> &it = items[i];
         if (which == 0) common_solution_at(it.P, it.B, it.F, ph, gi - begin[i]);
-        else common_flux_at(it.P, it.B, it.F, ph, gi - begin[i]);
+        else if (ph.viscous) common_flux_at<T, 2>(it.P, it.B, it.F, ph, gi - begin[i]);
+        else common_flux_at<T, 1>(it.P, it.B, it.F, ph, gi - begin[i]);
     }
 }
 

@@ -421,11 +421,11 @@ def synth_mod():
 
 
 def batch_mode(fr, torch, args, sp, nprob=64):
-    """64 independent periodic isentropic-vortex problems (element counts
+    """nprob (default 64) independent periodic isentropic-vortex problems (element counts
     log-uniform in [1k, 80k], prism:tet ratio uniform in [0, 1], order in
-    {1..4}, seed 3), FP32 with FP64 RK registers: grouped launches replayed
-    from a CUDA graph after autotuning, against each problem's own launch
-    sequence."""
+    {1..4}, seed 3), FP32 with FP64 RK registers, after autotuning: one
+    persistent launch per RK stage replayed from a CUDA graph, against the
+    grouped per-class launches and each problem's own launch sequence."""
     import synth
     t0 = time.perf_counter()
     meshes, orders = [], []
@@ -495,7 +495,7 @@ def batch_mode(fr, torch, args, sp, nprob=64):
                          "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
             "ndof": info["ndof"], "problems": nprob, "tuned": {k: info[k] for k in fr.Batch.INFO[4:12]},
             "setup_s": setup_s, "tune_s": tune_s, "state_finite": bool(finite),
-            "workload": "64 periodic isentropic-vortex boxes, Euler, FP32 + FP64 RK, seeds 3/1000+i"}
+            "workload": f"{nprob} periodic isentropic-vortex boxes, Euler, FP32 + FP64 RK, seeds 3/1000+i"}
 
 
 def _time_steps(torch, step, args, sp):

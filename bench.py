@@ -363,12 +363,30 @@ def precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, precision, args, sp):
     byts = gemm_bytes_f32(ctx, dom) * 4 * args.steps
     ach = byts / (classes[dom][0] * 1e-3) / 1e9
     peak = measured_peaks().get("hbm_gbs", 6800.0)
-    out["roofline"] = {"bound": "hbm", "kernel": ("k_gemm_tc" if precision in (fr.FR_BF16X3, fr.FR_TF32X3) else "k_gemm")
-                       + f" ({dom})", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                       "traffic": None, "launches": classes[dom][1],
-                       "avg_launch_ms": classes[dom][0] / max(classes[dom][1], 1),
-                       "bytes": "operator input + output once, epilogue geometry/registers (bench.gemm_bytes_f32)",
-                       "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    hbm = {"bound": "hbm", "kernel": ("k_gemm_tc" if precision in (fr.FR_BF16X3, fr.FR_TF32X3) else "k_gemm")
+           + f" ({dom})", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "traffic": None, "launches": classes[dom][1],
+           "avg_launch_ms": classes[dom][0] / max(classes[dom][1], 1),
+           "bytes": "operator input + output once, epilogue geometry/registers (bench.gemm_bytes_f32)",
+           "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    if precision == fr.FR_FP32:
+        # the streamed FP32 operator kernel (register tiles on the FP32
+        # pipe) does 2 x (non-zero operator entries) flops per 8 state bytes
+        # moved: at these operators' sizes its bound is the FP32 FMA pipe
+        # (128 FMA per clock per SM) as much as HBM; both fractions reported
+        nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        clk = float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+        fp32_peak = nsm * 128 * 2 * clk
+        fl = gemm_flops(ctx, dom) * 4 * args.steps / (classes[dom][0] * 1e-3)
+        out["roofline"] = {"bound": "alu", "kernel": f"k_gemm_f32 ({dom})", "achieved": fl / 1e12,
+                           "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": fl / fp32_peak,
+                           "traffic": None, "launches": classes[dom][1],
+                           "avg_launch_ms": classes[dom][0] / max(classes[dom][1], 1),
+                           "flops": "2 x non-zero operator entries x columns (bench.gemm_flops)",
+                           "peak_source": f"derived: {nsm} SMs x 128 FP32 FMA/clk x 2 flop x {clk / 1e9:.2f} GHz",
+                           "hbm_frac": ach / peak}
+    else:
+        out["roofline"] = hbm
     ctx.close()
     return out
 

@@ -289,16 +289,17 @@ int fr_reduce(fr_ctx *ctx, double *out, void *cuda_stream);
 int fr_diagnostics(fr_ctx *ctx, double *out, void *cuda_stream);
 
 /*
- * fr_selftest_wait_timeout: failure-detection self-test of the tensor-core
- * operator kernel (FR_BF16X3 / FR_TF32X3 contexts).  Launches the kernel
- * of the first element type's interpolation with its state loads withheld,
- * so every bounded wait inside it runs out (about 2 s); the kernel then
- * leaves all its loops, frees its tensor memory and reports FR_ERR_TIMEOUT
- * through the context's status.  Returns FR_OK when exactly that happened,
- * after clearing the status, so the context stays usable; no GPU fault,
- * trap or unbounded wait is involved.  Overwrites the interpolation
- * scratch.  Errors: FR_ERR_ARG, FR_ERR_UNSUPPORTED (other precisions),
- * FR_ERR_TIMEOUT (a status left by earlier work), FR_ERR_CUDA.
+ * fr_selftest_wait_timeout: failure-detection self-test of the streaming
+ * operator kernels: the tensor-core kernel (FR_BF16X3 / FR_TF32X3) or the
+ * streamed FP32 kernel (FR_FP32).  Launches the kernel of the first element
+ * type's interpolation with its copies withheld, so every bounded wait
+ * inside it runs out (about 2 s); the kernel then leaves all its loops
+ * (the tensor-core kernel frees its tensor memory) and reports
+ * FR_ERR_TIMEOUT through the context's status.  Returns FR_OK when exactly
+ * that happened, after clearing the status, so the context stays usable;
+ * no GPU fault, trap or unbounded wait is involved.  Overwrites the
+ * interpolation scratch.  Errors: FR_ERR_ARG, FR_ERR_UNSUPPORTED
+ * (FR_FP64), FR_ERR_TIMEOUT (a status left by earlier work), FR_ERR_CUDA.
  */
 int fr_selftest_wait_timeout(fr_ctx *ctx, void *cuda_stream);
 

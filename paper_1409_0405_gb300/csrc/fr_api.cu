@@ -173,8 +173,8 @@ FieldsT<T> fields_of(const fr_ctx *c) {
 }
 
 Pairs pairs_of(const fr_ctx *c) {
-    return Pairs{c->npairs, c->ta,    c->fa,    c->ea,    c->tb,     c->fb,    c->eb,
-                 c->nrm,    c->maga,  c->magb,  c->sgn,   c->nrm_f,  c->maga_f, c->magb_f};
+    return Pairs{c->npairs, c->pcode, c->ea,    c->eb,     c->nrm,
+                 c->maga,   c->magb,  c->nrm_f, c->maga_f, c->magb_f};
 }
 
 Bnd bnd_of(const fr_ctx *c) {
@@ -272,6 +272,7 @@ GemmArgsT<T> args_div(const fr_ctx *c, int t, const RKStage *rk) {
     g.ldc = g.N;
     g.np = D.np;
     g.invJ = (const T *)D.invJ_t;
+    g.geo_elem = D.geo_elem;
     g.rfs = D.Rfs;
     for (int v = 0; v < NV; ++v) g.uref[v] = ph.uref[v];
     if (rk) {
@@ -329,12 +330,18 @@ cudaError_t op_gemm<float>(fr_ctx *c, int t, int which, const GemmArgsT<float> &
         ++c->launches;  // the second launch
         return e;
     }
+    const F32Operator &op = c->T[t].f32op[which];
+    if (op.img && g.mode == GEMM_STORE) {
+        const cudaError_t e = launch_gemm_f32(g, op, c->tc_err, s);
+        if (e != cudaErrorInvalidValue) return e;
+        cudaGetLastError();  // a layout the streamed kernel does not take: the chunk-staged kernel
+    }
     return launch_gemm<float>(with_sparse<float>(c, t, which, g), s);
 }
 
 // FR_ERR_TIMEOUT if a tensor-core kernel gave up a wait (synchronises)
 int check_tc(fr_ctx *c) {
-    if (!is_tc(c) || !c->tc_err) return FR_OK;
+    if (!is_f32(c) || !c->tc_err) return FR_OK;
     int h = 0;
     int rc = cuda_check(cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
     if (rc) return rc;
@@ -390,7 +397,7 @@ int phase_grad(fr_ctx *c, T *const in[NT], cudaStream_t s) {
                                             [&] {
                                                 return launch_flux<T>(D.nu, D.ne, D.np, in[t], (T *)D.GU,
                                                                       (const T *)D.S_t, (const T *)D.invJ_t,
-                                                                      (T *)D.FT, ph, s);
+                                                                      (T *)D.FT, ph, s, D.geo_elem ? 0 : 1);
                                             }),
                                      "flux")))
                     return rc;
@@ -422,7 +429,8 @@ int phase_div(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
         if ((rc = cuda_check(launch(c, K_FLUX, s,
                                     [&] {
                                         return launch_flux<T>(D.nu, D.ne, D.np, in[t], (T *)D.GU, (const T *)D.S_t,
-                                                              (const T *)nullptr, (T *)D.FT, ph, s);
+                                                              (const T *)nullptr, (T *)D.FT, ph, s,
+                                                              D.geo_elem ? 0 : 1);
                                     }),
                              "flux")))
             return rc;
@@ -439,9 +447,10 @@ int phase_div(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
     // reference/closure term and applies the RK update, forming the next
     // stage input in FP32 (per-point loads and the FP64 register arithmetic
     // would otherwise stall the kernel's epilogue on the FP64 pipe).  The
-    // FP32 SIMT mode keeps the fused epilogue, which the batched launches
-    // reproduce bit for bit.
-    const bool split_rk = rk && is_tc(c);
+    // FP32 mode does the same with its streamed kernel (fr_gemm_f32.cu); its
+    // RK update is the fused epilogue's arithmetic, which the batched
+    // launches (chunk-staged kernel, fused epilogue) reproduce bit for bit.
+    const bool split_rk = rk && is_f32(c);
     for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
@@ -458,7 +467,8 @@ int phase_div(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
                                     [&] {
                                         return launch_rk_update<T>(D.nu, D.np, (const T *)D.R, D.U, D.Uacc, (T *)D.Us,
                                                                    ph.uref, rk->c_acc, rk->c_stage, rk->first,
-                                                                   rk->last, (const T *)D.invJ_t, rfs, (T *)D.Us0, s);
+                                                                   rk->last, (const T *)D.invJ_t, rfs, (T *)D.Us0, s,
+                                                                   D.geo_elem ? 0 : 1);
                                     }),
                              "RK update")))
             return rc;
@@ -676,12 +686,63 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
                 D.sp_lmax[w] = sp.lmax;
             }
         }
+        if (prm->precision == FR_FP32) {
+            // the streamed FP32 kernel's images (fr_gemm_f32.cu)
+            const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
+            const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok1[3] = {D.nu, D.nu, 3 * D.nu}, ok2[3] = {0, D.nf, D.nf};
+            for (int w = 0; w < 3; ++w) {
+                std::vector<int> perm;
+                if (w == 1) {  // image row d nu + j holds gradient row 3 j + d
+                    perm.resize((size_t)om[1]);
+                    for (int d = 0; d < 3; ++d)
+                        for (int j = 0; j < D.nu; ++j) perm[(size_t)d * D.nu + j] = 3 * j + d;
+                }
+                std::vector<float> img;
+                std::vector<uint16_t> mask;
+                std::vector<int> rowmap;
+                F32Operator &op = D.f32op[w];
+                f32_pack(opv[w]->data(), om[w], ok1[w], ok2[w], perm, img, mask, rowmap, op);
+                float *dimg = nullptr;
+                uint16_t *dmask = nullptr;
+                int *drow = nullptr;
+                if ((rc = upload(c, &dimg, img)) || (rc = upload(c, &dmask, mask)) || (rc = upload(c, &drow, rowmap)))
+                    return rc;
+                op.img = dimg;
+                op.mask = dmask;
+                op.rowmap = drow;
+            }
+        }
         if (prm->precision != FR_FP64) {
-            // float views of the geometry and operators (rounded once)
+            // float views of the geometry and operators (rounded once).  In
+            // the tensor-core modes, where the flux kernel and the RK update
+            // stream the geometry, a type whose float S and 1/J are the same
+            // at every solution point of every element keeps one value per
+            // element (the same floats: the results do not change)
+            int k0 = 0;
+            if (prm->precision == FR_BF16X3 || prm->precision == FR_TF32X3) {
+                bool same = true;
+                for (int64_t e = 0; e < D.ne && same; ++e)
+                    for (int j = 1; j < D.nu && same; ++j) {
+                        for (int k = 0; k < 9; ++k)
+                            same = same && (float)S[((size_t)j * 9 + k) * D.np + e] == (float)S[(size_t)k * D.np + e];
+                        same = same && (float)iJ[(size_t)j * D.np + e] == (float)iJ[e];
+                    }
+                if (same) {
+                    std::vector<float> Se((size_t)9 * D.np, 0.f), iJe((size_t)D.np, 0.f);
+                    for (size_t i = 0; i < Se.size(); ++i) Se[i] = (float)S[i];   // point 0's rows
+                    for (size_t i = 0; i < iJe.size(); ++i) iJe[i] = (float)iJ[i];
+                    float *dS = nullptr, *diJ = nullptr;
+                    if ((rc = upload(c, &dS, Se)) || (rc = upload(c, &diJ, iJe))) return rc;
+                    D.S_t = dS;
+                    D.invJ_t = diJ;
+                    D.geo_elem = 1;
+                    k0 = 2;
+                }
+            }
             double *src[5] = {D.S, D.invJ, D.M0, D.AGRAD, D.ADIV};
             void **dst[5] = {&D.S_t, &D.invJ_t, &D.M0_t, &D.AGRAD_t, &D.ADIV_t};
             const size_t cnt[5] = {S.size(), iJ.size(), ops[t].M0.size(), ops[t].AGRAD.size(), ops[t].ADIV.size()};
-            for (int k = 0; k < 5; ++k) {
+            for (int k = k0; k < 5; ++k) {
                 if ((rc = dev_alloc_bytes(c, dst[k], cnt[k] * sizeof(float)))) return rc;
                 if ((rc = cuda_check(launch_to_float((int64_t)cnt[k], src[k], (float *)*dst[k], 0), "to float")))
                     return rc;
@@ -708,8 +769,7 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
     }
     c->npairs = (int64_t)faces.ta.size();
     c->nbnd = (int64_t)faces.bt.size();
-    if ((rc = upload(c, &c->ta, faces.ta)) || (rc = upload(c, &c->fa, faces.fa)) || (rc = upload(c, &c->ea, faces.ea)) ||
-        (rc = upload(c, &c->tb, faces.tb)) || (rc = upload(c, &c->fb, faces.fb)) || (rc = upload(c, &c->eb, faces.eb)) ||
+    if ((rc = upload(c, &c->ea, faces.ea)) || (rc = upload(c, &c->eb, faces.eb)) ||
         (rc = upload(c, &c->nrm, faces.n)) || (rc = upload(c, &c->maga, faces.maga)) ||
         (rc = upload(c, &c->magb, faces.magb)) || (rc = upload(c, &c->bt, faces.bt)) ||
         (rc = upload(c, &c->bf, faces.bf)) || (rc = upload(c, &c->be, faces.be)) ||
@@ -722,13 +782,15 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
         if ((rc = upload(c, &c->bw, bw))) return rc;
         // LDG switch: +1 where side a's outward normal n has n . s > 0,
         // s = (1, 0.1 sqrt 2, 0.01 sqrt 3) (the dot product in double)
-        std::vector<signed char> sg(faces.ta.size());
-        for (size_t k = 0; k < sg.size(); ++k) {
+        std::vector<uint32_t> code(faces.ta.size());
+        for (size_t k = 0; k < code.size(); ++k) {
             const double *n = &faces.n[3 * k];
             const double d = n[0] * 1.0 + n[1] * 0.14142135623730950488 + n[2] * 0.017320508075688772935;
-            sg[k] = d > 0.0 ? 1 : -1;
+            if (faces.fa[k] < 0 || faces.fa[k] >= kPairMaxFpt || faces.fb[k] < 0 || faces.fb[k] >= kPairMaxFpt)
+                return set_err(FR_ERR_UNSUPPORTED, "more flux points per element than the pair code holds");
+            code[k] = pair_code(faces.ta[k], faces.tb[k], faces.fa[k], faces.fb[k], d > 0.0 ? 1 : -1);
         }
-        if ((rc = upload(c, &c->sgn, sg))) return rc;
+        if ((rc = upload(c, &c->pcode, code))) return rc;
         if (prm->precision != FR_FP64) {
             auto to_f = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
             if ((rc = upload(c, &c->nrm_f, to_f(faces.n))) || (rc = upload(c, &c->maga_f, to_f(faces.maga))) ||
@@ -1426,7 +1488,7 @@ int fr_diagnostics(fr_ctx *c, double *out, void *stream) {
 
 int fr_selftest_wait_timeout(fr_ctx *c, void *stream) {
     if (!c) return set_err(FR_ERR_ARG, "null context");
-    if (!is_tc(c)) return set_err(FR_ERR_UNSUPPORTED, "the bounded-wait self-test needs a tensor-core precision");
+    if (!is_f32(c)) return set_err(FR_ERR_UNSUPPORTED, "the bounded-wait self-test needs an FP32-storage precision");
     cudaStream_t s = (cudaStream_t)stream;
     int t = 0;
     while (t < NT && !c->T[t].present) ++t;
@@ -1435,7 +1497,10 @@ int fr_selftest_wait_timeout(fr_ctx *c, void *stream) {
     DevType &D = c->T[t];
     // M0 on the context's (centred) stage input, its state loads withheld
     const GemmArgsT<float> g = args_m0<float>(c, t, (const float *)D.Us);
-    if ((rc = cuda_check(launch_gemm_tc(g, D.tc[0], c->tc_err, s, 1), "self-test launch"))) return rc;
+    if ((rc = cuda_check(is_tc(c) ? launch_gemm_tc(g, D.tc[0], c->tc_err, s, 1)
+                                  : launch_gemm_f32(g, D.f32op[0], c->tc_err, s, 1),
+                         "self-test launch")))
+        return rc;
     if ((rc = cuda_check(cudaStreamSynchronize(s), "self-test sync"))) return rc;
     const int timed_out = check_tc(c) == FR_ERR_TIMEOUT;
     // clear the status so that the context stays usable

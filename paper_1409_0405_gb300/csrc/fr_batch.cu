@@ -539,7 +539,7 @@ struct BatchImpl : BatchBase {
         float best = 1e30f;
         for (int rc : kGroupedRCs) {
             if (rc > kMaxBatchRC || (g.mode == GEMM_GRAD && rc % 3)) continue;
-            if ((size_t)rc * (g.maxK ? g.maxK : 1) * sizeof(T) > 200 * 1024) continue;
+            if (gemm_block_smem(rc, (int)sizeof(T), g.maxK ? g.maxK : 1, g.maxK ? g.maxK : 1) > 200 * 1024) continue;
             g.rc = rc;
             int e = upload_group(g);
             if (e) return e;
@@ -660,12 +660,14 @@ struct BatchImpl : BatchBase {
         out[0] = (int64_t)b->ctx.size();
         out[1] = ndof;
         out[2] = launches_per_step;
-        // per-problem launch sequence: (viscous ? 12 : 6) per stage and 2 types
+        // per-problem launch sequence per stage: per type M0, (gradient, M0
+        // on the gradients), flux, divergence and (FP32: the separate RK
+        // update), and the face kernels
         int64_t un = 0;
         for (fr_ctx *c : b->ctx) {
             int nt = 0;
             for (int t = 0; t < NT; ++t) nt += c->T[t].present;
-            un += 4 * ((viscous ? 5 : 3) * nt + (viscous ? 2 : 1));
+            un += 4 * (((viscous ? 5 : 3) + (sizeof(T) == sizeof(float) ? 1 : 0)) * nt + (viscous ? 2 : 1));
         }
         out[3] = un;
         out[4] = m0.rc;

@@ -39,6 +39,10 @@ struct DevType {
     void *GU = nullptr, *FT = nullptr;       // [nu][3][V][np]
     void *GUF = nullptr;                     // [nf][3][V][np]
     void *S_t = nullptr, *invJ_t = nullptr, *M0_t = nullptr, *AGRAD_t = nullptr, *ADIV_t = nullptr;
+    // tensor-core modes: S_t and invJ_t hold one value per element ([9][np],
+    // [np]) when every element's float geometry factors are the same at all
+    // of its solution points (straight-sided affine elements)
+    int geo_elem = 0;
     std::vector<double> xu;  // host: ne x nu x 3 physical solution points
     // learned closure (off unless cl_on): FP32 parameters of the network
     // (20 nu -> cl_nh -> cl_nh -> 5 nu), its features/outputs/activations,
@@ -55,6 +59,9 @@ struct DevType {
     // an operator with more rows than one tensor-core tile takes (the p=4
     // hex gradient): rows [0, tc_split) in tc[w], the rest in tc2[w]
     fr::TcOperator tc2[3];
+    // FR_FP32: M0, AGRAD (rows ordered direction-major, so that a 4-row
+    // block shares the zeros of n_d M3), ADIV for the streamed FP32 kernel
+    fr::F32Operator f32op[3];
     int tc_split[3] = {0, 0, 0};
     // FR_FP64 / FR_FP32: chunk-compressed M0, AGRAD, ADIV (sp_rc 0: dense)
     int sp_rc[3] = {0, 0, 0}, sp_lmax[3] = {0, 0, 0}, sp_masked[3] = {0, 0, 0};
@@ -68,11 +75,11 @@ struct fr_ctx {
     int device = 0;
     DevType T[fr::NT];  // tets, prisms, hexes
     int64_t npairs = 0, nbnd = 0;
-    int *ta = nullptr, *fa = nullptr, *ea = nullptr, *tb = nullptr, *fb = nullptr, *eb = nullptr;
+    uint32_t *pcode = nullptr;  // pair_code of each pair (types, flux points, LDG switch)
+    int *ea = nullptr, *eb = nullptr;
     double *nrm = nullptr, *maga = nullptr, *magb = nullptr;
     int *bt = nullptr, *bf = nullptr, *be = nullptr, *btag = nullptr;
     double *bn = nullptr, *bmag = nullptr;
-    signed char *sgn = nullptr;  // LDG switch per pair
     float *nrm_f = nullptr, *maga_f = nullptr, *magb_f = nullptr, *bn_f = nullptr, *bmag_f = nullptr;
     // partition of a partitioned mesh: halo slots (other partitions' flux
     // points on cut interfaces), padded to nhalo_p, in the RHS arithmetic

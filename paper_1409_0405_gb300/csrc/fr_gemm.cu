@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_grouped(const GemmArgsT<T> *_
 template <typename T, int RC, int MODE>
 cudaError_t run(const GemmArgsT<T> &g, cudaStream_t s) {
     const int K = g.K1 + g.K2;
-    const size_t smem = g.sp_rc ? (size_t)g.sp_lmax * (RC * sizeof(T) + sizeof(int)) : (size_t)RC * K * sizeof(T);
+    const size_t smem = gemm_block_smem(RC, (int)sizeof(T), K, g.sp_rc ? g.sp_lmax : 0);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm<T, RC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -159,7 +159,7 @@ template <typename T, int RC, int MODE>
 cudaError_t run_grouped(const GemmArgsT<T> *descs, const int64_t *begin, int ndesc, int64_t total, int maxK,
                         int grid, cudaStream_t s) {
     // a dense chunk, or a compressed one with its column list (lmax <= K)
-    const size_t smem = (size_t)RC * maxK * sizeof(T) + (size_t)maxK * sizeof(int);
+    const size_t smem = gemm_block_smem(RC, (int)sizeof(T), maxK, maxK);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm_grouped<T, RC, MODE>,

@@ -23,14 +23,39 @@ __device__ __forceinline__ T bload(const T *p) {
 
 constexpr int kThreads = 128;
 
+// The staged chunk of A keeps the RC values of one column k in a row of
+// rc_pad values (fr_kernels.h), loaded with 16-byte vector loads.
+// the padded row of column k (values past RC unused)
+template <typename T, int RCP>
+__device__ __forceinline__ void load_arow(const T *a, T (&av)[RCP]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int v = 0; v < RCP / 4; ++v) {
+            const float4 q = reinterpret_cast<const float4 *>(a)[v];
+            av[4 * v] = q.x;
+            av[4 * v + 1] = q.y;
+            av[4 * v + 2] = q.z;
+            av[4 * v + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < RCP / 2; ++v) {
+            const double2 q = reinterpret_cast<const double2 *>(a)[v];
+            av[2 * v] = q.x;
+            av[2 * v + 1] = q.y;
+        }
+    }
+}
+
 // One (row chunk, column tile) block of C <- A [B1; B2] with the epilogue
 // MODE.  Block-uniform: every thread of the block calls it with the same
 // (g, m0, tile); it stages the chunk of A in sA and synchronises.
 template <typename T, int RC, int MODE, bool NC = true>
 __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_t tile, T *sA) {
+    constexpr int RCP = rc_pad(RC, sizeof(T));
     const int K = g.K1 + g.K2;
     // dense: sA[k][r] for every column; compressed: sA[i][r] for the chunk's
-    // column list i, the column numbers in sK
+    // column list i, the column numbers in sK; rows of RCP values
     int nl1 = g.K1, nl = K;
     int *sK = nullptr;
     if (g.sp_rc) {
@@ -38,13 +63,16 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
         const int beg = g.sp_off[2 * c], mid = g.sp_off[2 * c + 1], end = g.sp_off[2 * c + 2];
         nl1 = mid - beg;
         nl = end - beg;
-        sK = reinterpret_cast<int *>(sA + (size_t)g.sp_lmax * RC);
-        for (int idx = threadIdx.x; idx < RC * nl; idx += kThreads) sA[idx] = g.sp_vals[(size_t)beg * RC + idx];
+        sK = reinterpret_cast<int *>(sA + (size_t)g.sp_lmax * RCP);
+        for (int idx = threadIdx.x; idx < RC * nl; idx += kThreads) {
+            const int i = idx / RC, r = idx - i * RC;
+            sA[i * RCP + r] = g.sp_vals[(size_t)beg * RC + idx];
+        }
         for (int idx = threadIdx.x; idx < nl; idx += kThreads) sK[idx] = g.sp_cols[beg + idx];
     } else {
         for (int idx = threadIdx.x; idx < RC * K; idx += kThreads) {
             const int r = idx / K, k = idx - r * K;
-            sA[k * RC + r] = (m0 + r < g.M) ? g.A[(size_t)(m0 + r) * K + k] : T(0);
+            sA[k * RCP + r] = (m0 + r < g.M) ? g.A[(size_t)(m0 + r) * K + k] : T(0);
         }
     }
     __syncthreads();
@@ -80,15 +108,15 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
         }                                          \
     }                                              \
     break;
-                        case 1: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]);)
-                        case 2: FR_RUN(acc[1] = fma(a[3 * t + 1], bv, acc[1]);)
-                        case 3: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[1] = fma(a[3 * t + 1], bv, acc[1]);)
-                        case 4: FR_RUN(acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
-                        case 5: FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
-                        case 6: FR_RUN(acc[1] = fma(a[3 * t + 1], bv, acc[1]); acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
+                        case 1: FR_RUN(acc[0] = fma(a[RCP * t], bv, acc[0]);)
+                        case 2: FR_RUN(acc[1] = fma(a[RCP * t + 1], bv, acc[1]);)
+                        case 3: FR_RUN(acc[0] = fma(a[RCP * t], bv, acc[0]); acc[1] = fma(a[RCP * t + 1], bv, acc[1]);)
+                        case 4: FR_RUN(acc[2] = fma(a[RCP * t + 2], bv, acc[2]);)
+                        case 5: FR_RUN(acc[0] = fma(a[RCP * t], bv, acc[0]); acc[2] = fma(a[RCP * t + 2], bv, acc[2]);)
+                        case 6: FR_RUN(acc[1] = fma(a[RCP * t + 1], bv, acc[1]); acc[2] = fma(a[RCP * t + 2], bv, acc[2]);)
                         default:
-                            FR_RUN(acc[0] = fma(a[3 * t], bv, acc[0]); acc[1] = fma(a[3 * t + 1], bv, acc[1]);
-                                   acc[2] = fma(a[3 * t + 2], bv, acc[2]);)
+                            FR_RUN(acc[0] = fma(a[RCP * t], bv, acc[0]); acc[1] = fma(a[RCP * t + 1], bv, acc[1]);
+                                   acc[2] = fma(a[RCP * t + 2], bv, acc[2]);)
 #undef FR_RUN
                     }
                     i = j;
@@ -104,17 +132,19 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
 #pragma unroll 2
             for (int i = 0; i < nl1; ++i) {
                 const T bv = bload<NC>(b1 + (int64_t)sK[i] * g.ldb1);
-                const T *a = sA + i * RC;
+                T av[RCP];
+                load_arow<T, RCP>(sA + i * RCP, av);
 #pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
+                for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
             }
             const T *b2 = g.B2 + n;
 #pragma unroll 2
             for (int i = nl1; i < nl; ++i) {
                 const T bv = bload<NC>(b2 + (int64_t)(sK[i] - g.K1) * g.ldb2);
-                const T *a = sA + i * RC;
+                T av[RCP];
+                load_arow<T, RCP>(sA + i * RCP, av);
 #pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
+                for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
             }
         } else if (nl >= 0) {
             {
@@ -123,21 +153,23 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
 #pragma unroll 2
                 for (int k = 0; k < g.K1; ++k) {
                     const T bv = bload<NC>(b + (int64_t)k * ld);
-                    const T *a = sA + k * RC;
+                    T av[RCP];
+                    load_arow<T, RCP>(sA + k * RCP, av);
 #pragma unroll
-                    for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
+                    for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
                 }
             }
             if (g.K2 > 0) {
                 const T *b = g.B2 + n;
                 const int64_t ld = g.ldb2;
-                const T *a0 = sA + g.K1 * RC;
+                const T *a0 = sA + g.K1 * RCP;
 #pragma unroll 2
                 for (int k = 0; k < g.K2; ++k) {
                     const T bv = bload<NC>(b + (int64_t)k * ld);
-                    const T *a = a0 + k * RC;
+                    T av[RCP];
+                    load_arow<T, RCP>(a0 + k * RCP, av);
 #pragma unroll
-                    for (int r = 0; r < RC; ++r) acc[r] = fma(a[r], bv, acc[r]);
+                    for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
                 }
             }
         }

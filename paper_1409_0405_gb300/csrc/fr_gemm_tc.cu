@@ -26,11 +26,12 @@
 //                   loads in flight are bounded by the ring, not by the L1
 //                   left over beside the shared memory; rows past the end
 //                   of B1 or B2 are filled with zeros by the TMA unit);
-//                   the converter warps read their column, meet at an
-//                   mbarrier, and overwrite the slot with the stage's bf16 hi
-//                   and lo core matrices [hi | lo] (4 KB each, LBO/SBO as
-//                   above), which the MMA reads; its commit frees the slot
-//                   for the next load.
+//                   one converter warp reads the whole stage into registers
+//                   and overwrites the slot with its bf16 hi and lo core
+//                   matrices [hi | lo] (4 KB each, LBO/SBO as above), which
+//                   the MMA reads; its commit frees the slot for the next
+//                   load.  Converter warp w owns the slots q with q % 8 ==
+//                   w, so up to eight slots are converted at once.
 // Warp roles (22 warps): 0-7 converters, 8-19 epilogue (TMEM lane quarter =
 // warp % 4; the three warps of a quarter take every third 24-row group), 20
 // TMEM allocation, operator load and the single MMA-issuing thread, 21 the
@@ -44,18 +45,18 @@
 
 #include <cstdint>
 
+#include "fr_async.cuh"
 #include "fr_kernels.h"
 
 namespace fr {
+static int tc_sub(const TcOperator &op);  // stages per slot (below)
+
 namespace {
 
-constexpr int kTileN = 128;         // state columns per tile (MMA M)
-constexpr int kStageK = 16;        // K values per stage (one MMA K step)
 constexpr int kStageBytes = 8192;  // 128 x 16 x 4 B (FP32), later 128 x 16 x (hi + lo) x 2 B
 constexpr int kConvWarps = 8, kEpiWarps = 12;  // epilogue: three warps per TMEM lane quarter
 constexpr int kMmaWarp = kConvWarps + kEpiWarps, kProdWarp = kMmaWarp + 1;
 constexpr int kThreads = (kConvWarps + kEpiWarps + 2) * 32;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 constexpr int kMaxSlots = 12;
 
@@ -65,81 +66,16 @@ struct Bars {
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
     uint64_t loaded[kMaxSlots];     // producer's copies of a slot landed (tx)
-    uint64_t read[kMaxSlots];       // every converter has read the slot's FP32 rows
-    uint64_t converted[kMaxSlots];  // converters wrote the slot's bf16 tiles
+    uint64_t converted[kMaxSlots];  // the slot's converter warp wrote its bf16 (tf32) tiles
     uint64_t freed[kMaxSlots];      // the MMAs reading the slot completed
     uint32_t tmem_base;
     int abort;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-
-// Bounded wait for the phase of parity `parity` to complete.  Returns false
-// (and raises the CTA's abort flag and the error code) on expiry or when
-// another role has aborted.
+// the bounded waits of fr_async.cuh with this CTA's abort flag
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Bars *bars, int *err, int code) {
-    const uint32_t a = smem_u32(b);
-    const long long t0 = clock64();
-    for (uint32_t it = 0;; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((it & 31) == 31) {
-            if (*(volatile int *)&bars->abort) return false;
-            if (clock64() - t0 > kWaitCycles) {
-                *(volatile int *)&bars->abort = 1;
-                atomicCAS(err, 0, code);
-                return false;
-            }
-        }
-    }
+    return mbar_wait_abort(b, parity, &bars->abort, err, code);
 }
-
-// Bounded wait that ignores the abort flag: after an abort, the thread that
-// issued asynchronous work (bulk copies, MMAs) waits here for exactly that
-// work to complete before the CTA releases its shared memory and TMEM.
-// Returns false (recording `code`) only if the limit expires.
-__device__ __forceinline__ bool mbar_drain(uint64_t *b, uint32_t parity, int *err, int code) {
-    const uint32_t a = smem_u32(b);
-    const long long t0 = clock64();
-    for (uint32_t it = 0;; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((it & 31) == 31 && clock64() - t0 > kWaitCycles) {
-            atomicCAS(err, 0, code);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -260,7 +196,7 @@ __device__ __forceinline__ void epi_group(const GemmArgsT<float> &g, int c0, int
             for (int i = 0; i < RG; ++i) {
                 const int j = c0 + r0 + i;
                 if (j < g.M) {
-                    ij[i] = __ldg(g.invJ + (int64_t)j * g.np + e);
+                    ij[i] = __ldg(g.invJ + (g.geo_elem ? 0 : (int64_t)j * g.np) + e);
                     rf[i] = g.rfs ? __ldg(g.rfs + (int64_t)j * g.ldc + n) : 0.0;
                 }
             }
@@ -276,20 +212,16 @@ __device__ __forceinline__ void epi_group(const GemmArgsT<float> &g, int c0, int
     }
 }
 
-// Tile t covers columns [n0, n1) of one variable block (N = nvb np columns,
-// block b = columns [b np, (b+1) np)): the variable block runs fastest, so
-// the nvb tiles of one element range are processed together and share the
-// geometry factors through L2.
-struct TileMap {
-    int64_t np, ept;  // elements per block, tiles per block
-    int nvb;
-    __device__ __forceinline__ void cols(int64_t t, int64_t &n0, int64_t &n1) const {
-        const int64_t eb = t / nvb, vb = t % nvb;
-        n0 = vb * np + eb * kTileN;
-        const int64_t lim = (vb + 1) * np;
-        n1 = n0 + kTileN < lim ? n0 + kTileN : lim;
-    }
-};
+// The converter's in-place order: the column group (c = 0..3, columns
+// l + 32 c of the 128) whose output overwrites FP32 input row k of a stage.
+// bf16: group c writes hi at bytes [1024 c, 1024 c + 1024) = rows 2c, 2c+1
+// and lo at 4096 + that = rows 8 + 2c, 9 + 2c; tf32: hi at [2048 c, 2048 c +
+// 2048) = rows 4c .. 4c + 3 (lo lands past the FP32 rows).
+template <bool TF>
+__host__ __device__ constexpr int conv_kill(int k) {
+    return TF ? k / 4 : (k < 8 ? k / 2 : (k - 8) / 2);
+}
+
 
 // TF = false: split BF16, the operator image resident in shared memory,
 // slot = 8 KB (FP32 box, then bf16 hi | lo).  TF = true: split TF32 (4-byte
@@ -300,7 +232,7 @@ template <int MODE, bool TF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const GemmArgsT<float> g, const TileMap tm, const __grid_constant__ CUtensorMap tmB1,
               const __grid_constant__ CUtensorMap tmB2, const uint8_t *__restrict__ opimg, int Nmma, int K1pad,
-              int Kpad, int nslot, uint32_t tmem_cols, int *err, int no_producer, int terms) {
+              int Kpad, int nslot, uint32_t tmem_cols, int *err, int no_producer, int terms, int sub) {
     extern __shared__ __align__(1024) uint8_t smem[];
     // terms (split BF16): 3 = state and operator split (hi and lo images);
     // 2 = state split, operator hi only; 1 = both rounded to bf16, hi only
@@ -308,12 +240,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t op_bytes = terms == 3 ? 2u * op_half : op_half;
     const uint32_t state_bytes = TF ? 16384u : (uint32_t)kStageBytes;
     const uint32_t slab_bytes = TF ? (uint32_t)Nmma * 128u : 0u;
-    const uint32_t slot_bytes = state_bytes + slab_bytes;
+    // a slot holds `sub` consecutive stages (one mbarrier round trip each way
+    // per slot, not per stage)
+    const uint32_t sub_bytes = state_bytes + slab_bytes;
+    const uint32_t slot_bytes = (uint32_t)sub * sub_bytes;
     uint8_t *slots = smem + op_bytes;
     Bars *bars = reinterpret_cast<Bars *>(slots + (size_t)nslot * slot_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = tm.ept * tm.nvb;
     const int nkst = Kpad / kStageK;
+    const int nss = (nkst + sub - 1) / sub;  // slots per tile
 
     if (threadIdx.x == 0) {
         mbar_init(&bars->op_full, 1);
@@ -324,8 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int q = 0; q < nslot; ++q) {
             mbar_init(&bars->loaded[q], 1);
-            mbar_init(&bars->read[q], kConvWarps * 32);
-            mbar_init(&bars->converted[q], kConvWarps * 32);
+            mbar_init(&bars->converted[q], 32);  // the converting warp
             mbar_init(&bars->freed[q], 1);
         }
         bars->abort = 0;
@@ -345,11 +280,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = bars->tmem_base;
     const uint32_t acc_stride = tmem_cols / 2;
 
-    // stages this CTA runs (tiles blockIdx.x, + gridDim.x, ...; nkst each),
-    // walked with incremental counters: the slot and its phase parity, the
-    // stage within the tile, the tile's columns
+    // slot fills this CTA runs (tiles blockIdx.x, + gridDim.x, ...; nss
+    // each), walked with incremental counters: the slot and its phase
+    // parity, the fill within the tile (stages sub ks .. sub ks + sub - 1),
+    // the tile's columns
     const int64_t nmine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t total = nmine * nkst;
+    const int64_t total = nmine * nss;
     struct Cursor {
         int q = 0, ks = 0;
         uint32_t par = 0;
@@ -372,56 +308,76 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
 
     if (warp < kConvWarps) {
-        // ---- converters: thread (r, h) converts column r, K half h (8
-        // values) of each stage: read them from the slot, wait for every
-        // converter to have read, write the bf16 hi/lo of its core-matrix row
-        const int r = threadIdx.x & (kTileN - 1), h = threadIdx.x >> 7;
+        // ---- converters: warp w converts, on its own, every stage that
+        // lands in a slot q with q % 8 == w, so that up to eight slots are
+        // converted at once.  A warp passes through every phase of its
+        // slots in order, which the phase-parity waits require (a waiter
+        // must not skip a phase of the barrier it waits on).  Lane l converts
+        // columns l + 32 c (c = 0..3).  The output overwrites the FP32 rows
+        // in place: the hi (bf16: and lo) core matrices of column group c
+        // cover the input rows kill(k) == c, so before group c is written
+        // every column group still reads those rows into registers (and
+        // group c its remaining rows); the warp is the slot's only reader
+        // and writer, and __syncwarp orders each read phase before the
+        // writes that follow it.  At most 32 values per lane are live.
         Cursor cu;
         cu.start(tm);
-        for (int64_t idx = 0; idx < total; ++idx, cu.next(tm, nkst, nslot)) {
+        for (int64_t idx = 0; idx < total; ++idx, cu.next(tm, nss, nslot)) {
+            if (cu.q % kConvWarps != warp) continue;
             const int q = cu.q;
-            const uint32_t par = cu.par;
-            if (!mbar_wait(&bars->loaded[q], par, bars, err, 1)) break;
-            const bool col_ok = cu.n0 + r < cu.n1;
-            uint8_t *slot = slots + (size_t)q * slot_bytes;
+            if (!mbar_wait(&bars->loaded[q], cu.par, bars, err, 1)) break;
+            const int64_t ncol = cu.n1 - cu.n0;
+            for (int u = 0; u < sub && cu.ks * sub + u < nkst; ++u) {
+            uint8_t *slot = slots + (size_t)q * slot_bytes + (size_t)u * sub_bytes;
             const float *f = reinterpret_cast<const float *>(slot);
-            float cur[8];
+            float x[4][kStageK];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) cur[i] = col_ok ? f[(h * 8 + i) * kTileN + r] : 0.f;
-            // all converters have read the slot before any overwrites it (an
-            // mbarrier, so that this wait is bounded like every other)
-            mbar_arrive(&bars->read[q]);
-            if (!mbar_wait(&bars->read[q], par, bars, err, 8)) break;
-            if constexpr (TF) {
-                // tf32 core matrices: 8 rows x 4 values; K half h is the
-                // two core matrices 2h, 2h+1 of row group r/8 (512 B apart)
-                float hv[8], lv[8];
+            for (int c = 0; c < 4; ++c) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    hv[i] = tf32_round(cur[i]);
-                    lv[i] = tf32_round(cur[i] - hv[i]);
+                for (int c2 = c; c2 < 4; ++c2) {
+                    const bool ok = lane + 32 * c2 < ncol;
+#pragma unroll
+                    for (int k = 0; k < kStageK; ++k)
+                        if (conv_kill<TF>(k) == c || (c2 == c && conv_kill<TF>(k) > c))
+                            x[c2][k] = ok ? f[k * kTileN + lane + 32 * c2] : 0.f;
                 }
+                __syncwarp();
+                const uint32_t rg = (uint32_t)(4 * c + (lane >> 3)), rr = (uint32_t)(lane & 7);
+                if constexpr (TF) {
+                    // tf32 core matrices: 8 rows x 4 values; row group rg,
+                    // K core matrix kc (0..3) at rg * 512 + kc * 128
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const uint32_t off = (uint32_t)(r >> 3) * 512u + (uint32_t)(2 * h + c) * 128u + (uint32_t)(r & 7) * 16u;
-                    *reinterpret_cast<float4 *>(slot + off) = make_float4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
-                    *reinterpret_cast<float4 *>(slot + 8192 + off) =
-                        make_float4(lv[4 * c], lv[4 * c + 1], lv[4 * c + 2], lv[4 * c + 3]);
-                }
-            } else {
-                uint32_t hw[4], lw[4];
+                    for (int kc = 0; kc < 4; ++kc) {
+                        float hv[4], lv[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(cur[2 * i]), h1 = __float2bfloat16_rn(cur[2 * i + 1]);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(cur[2 * i] - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 = __float2bfloat16_rn(cur[2 * i + 1] - __bfloat162float(h1));
-                    hw[i] = pack2(h0, h1);
-                    lw[i] = pack2(l0, l1);
+                        for (int i = 0; i < 4; ++i) {
+                            hv[i] = tf32_round(x[c][4 * kc + i]);
+                            lv[i] = tf32_round(x[c][4 * kc + i] - hv[i]);
+                        }
+                        const uint32_t off = rg * 512u + (uint32_t)kc * 128u + rr * 16u;
+                        *reinterpret_cast<float4 *>(slot + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                        *reinterpret_cast<float4 *>(slot + 8192 + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+                    }
+                } else {
+                    // bf16 core matrices: row group rg, K half h at rg * 256 + h * 128
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float a0 = x[c][8 * h + 2 * i], a1 = x[c][8 * h + 2 * i + 1];
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
+                            hw[i] = pack2(h0, h1);
+                            lw[i] = pack2(__float2bfloat16_rn(a0 - __bfloat162float(h0)),
+                                          __float2bfloat16_rn(a1 - __bfloat162float(h1)));
+                        }
+                        const uint32_t off = rg * 256u + (uint32_t)h * 128u + rr * 16u;
+                        *reinterpret_cast<uint4 *>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        if (terms > 1)
+                            *reinterpret_cast<uint4 *>(slot + 4096 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
                 }
-                // row r: core matrix (r/8, K half h), row r%8
-                const uint32_t off = (uint32_t)(r >> 3) * 256u + (uint32_t)h * 128u + (uint32_t)(r & 7) * 16u;
-                *reinterpret_cast<uint4 *>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                if (terms > 1) *reinterpret_cast<uint4 *>(slot + 4096 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
             }
             fence_async_smem();
             mbar_arrive(&bars->converted[q]);
@@ -459,36 +415,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == kProdWarp && lane == 0 && !no_producer) {
         // ---- producer: one 2-D TMA box (16 K rows x 128 columns) per stage
-        // into its slot; stage ks reads B1 rows 16 ks.. (ks < K1pad / 16)
-        // or B2 rows 16 ks - K1pad..
+        // into its part of the slot; stage ks reads B1 rows 16 ks.. (ks <
+        // K1pad / 16) or B2 rows 16 ks - K1pad..
         const int n1st = K1pad / kStageK;
         Cursor cu;
         cu.start(tm);
         // slots with a copy issued, and the phase parity of each slot's last one
         uint32_t issued = 0u, last_par = 0u;
-        for (int64_t idx = 0; idx < total; ++idx, cu.next(tm, nkst, nslot)) {
+        for (int64_t idx = 0; idx < total; ++idx, cu.next(tm, nss, nslot)) {
             const int q = cu.q;
             if (!mbar_wait(&bars->freed[q], cu.par ^ 1u, bars, err, 7)) break;
             issued |= 1u << q;
             last_par = (last_par & ~(1u << q)) | (cu.par << q);
             const int64_t n0 = cu.n0;
-            const int ks = cu.ks;
-            const CUtensorMap *tmap = ks < n1st ? &tmB1 : &tmB2;
-            const int y = ks < n1st ? ks * kStageK : ks * kStageK - K1pad;
-            uint8_t *slot = slots + (size_t)q * slot_bytes;
-            mbar_expect_tx(&bars->loaded[q], (uint32_t)kStageBytes + slab_bytes);
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-                    "r"(smem_u32(slot)),
-                "l"(reinterpret_cast<uint64_t>(tmap)), "r"((int)n0), "r"(y), "r"(smem_u32(&bars->loaded[q]))
-                : "memory");
-            if constexpr (TF) {
-                // the stage's operator slab (stage-major image)
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(slot + state_bytes)),
-                    "l"(opimg + (size_t)ks * slab_bytes), "r"(slab_bytes), "r"(smem_u32(&bars->loaded[q]))
-                    : "memory");
+            const int nv = nkst - cu.ks * sub < sub ? nkst - cu.ks * sub : sub;  // stages in this fill
+            mbar_expect_tx(&bars->loaded[q], (uint32_t)nv * ((uint32_t)kStageBytes + slab_bytes));
+            for (int u = 0; u < nv; ++u) {
+                const int ks = cu.ks * sub + u;
+                const CUtensorMap *tmap = ks < n1st ? &tmB1 : &tmB2;
+                const int y = ks < n1st ? ks * kStageK : ks * kStageK - K1pad;
+                uint8_t *slot = slots + (size_t)q * slot_bytes + (size_t)u * sub_bytes;
+                tma_load_2d(slot, tmap, (int)n0, y, &bars->loaded[q]);
+                // split TF32: the stage's operator slab (stage-major image)
+                if constexpr (TF) bulk_load(slot + state_bytes, opimg + (size_t)ks * slab_bytes, slab_bytes, &bars->loaded[q]);
             }
         }
         // after an abort the consumers may have left before this thread's
@@ -529,37 +478,39 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(&bars->acc_empty[b], aph ^ 1u, bars, err, 4)) break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)b * acc_stride;
-            for (int ks = 0; ks < nkst; ++ks) {
+            for (int ss = 0; ss < nss; ++ss) {
                 if (!mbar_wait(&bars->converted[q], qpar, bars, err, 5)) {
                     live = false;
                     break;
                 }
                 tc_fence_after();
-                if constexpr (TF) {
-                    // two K steps of 8; core matrices 128 B apart along K,
-                    // row groups 512 B apart; the slab's lo half after its hi
-                    const uint32_t sl = st_s + (uint32_t)q * slot_bytes;
+                for (int u = 0; u < sub && ss * sub + u < nkst; ++u) {
+                    const int ks = ss * sub + u;
+                    const uint32_t sl = st_s + (uint32_t)q * slot_bytes + (uint32_t)u * sub_bytes;
+                    if constexpr (TF) {
+                        // two K steps of 8; core matrices 128 B apart along K,
+                        // row groups 512 B apart; the slab's lo half after its hi
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint32_t a_hi = sl + (uint32_t)kk * 256u, a_lo = a_hi + 8192u;
-                        const uint32_t b_hi = sl + state_bytes + (uint32_t)kk * 256u;
-                        const uint32_t b_lo = b_hi + (uint32_t)Nmma * 64u;
-                        const uint64_t ah = sdesc(a_hi, 128, 512), al = sdesc(a_lo, 128, 512);
-                        const uint64_t bh = sdesc(b_hi, 128, 512), bl = sdesc(b_lo, 128, 512);
-                        mma_tf32(d, ah, bh, idesc, (ks | kk) != 0);
-                        mma_tf32(d, ah, bl, idesc, 1);
-                        mma_tf32(d, al, bh, idesc, 1);
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t a_hi = sl + (uint32_t)kk * 256u, a_lo = a_hi + 8192u;
+                            const uint32_t b_hi = sl + state_bytes + (uint32_t)kk * 256u;
+                            const uint32_t b_lo = b_hi + (uint32_t)Nmma * 64u;
+                            const uint64_t ah = sdesc(a_hi, 128, 512), al = sdesc(a_lo, 128, 512);
+                            const uint64_t bh = sdesc(b_hi, 128, 512), bl = sdesc(b_lo, 128, 512);
+                            mma_tf32(d, ah, bh, idesc, (ks | kk) != 0);
+                            mma_tf32(d, ah, bl, idesc, 1);
+                            mma_tf32(d, al, bh, idesc, 1);
+                        }
+                    } else {
+                        const uint32_t a_hi = sl, a_lo = sl + 4096u;
+                        const uint32_t b_hi = op_s + (uint32_t)ks * (uint32_t)Nmma * 32u;
+                        const uint32_t b_lo = b_hi + op_half;
+                        const uint64_t ah = sdesc(a_hi, 128, 256), al = sdesc(a_lo, 128, 256);
+                        const uint64_t bh = sdesc(b_hi, 128, 256), bl = sdesc(b_lo, 128, 256);
+                        mma_bf16(d, ah, bh, idesc, ks != 0);
+                        if (terms == 3) mma_bf16(d, ah, bl, idesc, 1);
+                        if (terms >= 2) mma_bf16(d, al, bh, idesc, 1);
                     }
-                } else {
-                    const uint32_t a_hi = st_s + (uint32_t)q * slot_bytes;
-                    const uint32_t a_lo = a_hi + 4096u;
-                    const uint32_t b_hi = op_s + (uint32_t)ks * (uint32_t)Nmma * 32u;
-                    const uint32_t b_lo = b_hi + op_half;
-                    const uint64_t ah = sdesc(a_hi, 128, 256), al = sdesc(a_lo, 128, 256);
-                    const uint64_t bh = sdesc(b_hi, 128, 256), bl = sdesc(b_lo, 128, 256);
-                    mma_bf16(d, ah, bh, idesc, ks != 0);
-                    if (terms == 3) mma_bf16(d, ah, bl, idesc, 1);
-                    if (terms >= 2) mma_bf16(d, al, bh, idesc, 1);
                 }
                 mma_commit(&bars->freed[q]);
                 if (++q == nslot) {
@@ -588,33 +539,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
-// 2-D tensor map of one operand block: rows x cols floats, row stride ld
-// floats, boxes of 16 rows x 128 columns, zero fill out of bounds
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-cudaError_t encode_rows(CUtensorMap *m, const float *base, int64_t cols, int rows, int64_t ld) {
-    static EncodeTiled fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void *p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !p)
-            return cudaErrorNotSupported;
-        fn = reinterpret_cast<EncodeTiled>(p);
-    }
-    const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
-    const cuuint64_t stride[1] = {(cuuint64_t)ld * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kTileN, (cuuint32_t)kStageK};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dim, stride, box, estride,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 template <int MODE, bool TF>
 cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOperator &op, int *err, int grid,
                         cudaStream_t s, int no_producer) {
@@ -637,23 +561,28 @@ cudaError_t launch_mode(const GemmArgsT<float> &g, const TileMap &tm, const TcOp
     // backward data gradient keeps the state's lo half (two products)
     const int terms = !op.hi_only ? 3 : (MODE == GEMM_ACT_BACK ? 2 : 1);
     k_gemm_tc<MODE, TF><<<grid, kThreads, smem, s>>>(g, tm, m1, m2, op.img, op.Nmma, op.K1pad, op.Kpad, nslot, cols,
-                                                    err, no_producer, terms);
+                                                    err, no_producer, terms, tc_sub(op));
     return cudaGetLastError();
 }
 
 }  // namespace
 
 // shared memory: the resident operator image (split BF16) and the slot
-// ring (2..12 slots; split TF32: state 16 KB plus the operator slab)
+// ring (2..12 slots of one or two stages; a split-TF32 stage is 16 KB of
+// state plus the operator slab)
 static int64_t tc_image_bytes(const TcOperator &op) {
     return op.tf32 ? 0 : (op.hi_only ? 2 : 4) * (int64_t)op.Nmma * op.Kpad;
 }
-static int64_t tc_slot_bytes(const TcOperator &op) {
+static int64_t tc_stage_bytes(const TcOperator &op) {
     return op.tf32 ? 16384 + 128 * (int64_t)op.Nmma : (int64_t)kStageBytes;
 }
 static int64_t tc_free(const TcOperator &op) {
     return 232448 - tc_image_bytes(op) - (int64_t)sizeof(Bars) - 1024;
 }
+// stages per slot: two (half the hand-offs per stage) while that leaves a
+// ring of at least four slots, else one
+static int tc_sub(const TcOperator &op) { return tc_free(op) / (2 * tc_stage_bytes(op)) >= 4 ? 2 : 1; }
+static int64_t tc_slot_bytes(const TcOperator &op) { return tc_sub(op) * tc_stage_bytes(op); }
 
 int tc_stages(const TcOperator &op) {
     const int64_t n = tc_free(op) / tc_slot_bytes(op);

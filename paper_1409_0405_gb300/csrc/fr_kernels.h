@@ -34,6 +34,20 @@ enum GemmMode {
     GEMM_ACT_BACK = 5   // C = (A B) * gelu'(Zin[row][column])
 };
 
+// The operator kernel's staged chunk of A keeps the RC values of one column k in a row padded
+// to whole 16-byte vectors (rc_pad values), so that a thread loads them with
+// vector loads (4 floats or 2 doubles each) instead of one load per value.
+__host__ __device__ constexpr int rc_pad(int rc, int tsize) {
+    return (rc * tsize + 15) / 16 * 16 / tsize;
+}
+
+// shared memory of one block: a dense chunk (rows padded, all K columns) or
+// a compressed one (lmax listed columns and their column numbers)
+inline size_t gemm_block_smem(int rc, int tsize, int K, int lmax) {
+    const size_t row = (size_t)rc_pad(rc, tsize) * tsize;
+    return lmax > 0 ? (size_t)lmax * (row + sizeof(int)) : (size_t)K * row;
+}
+
 template <typename T>
 struct GemmArgsT {
     int M = 0;            // rows of A and C
@@ -48,7 +62,8 @@ struct GemmArgsT {
     int64_t ldc = 0;
     int mode = GEMM_STORE;
     int64_t np = 0;             // element stride: column n belongs to element n % np
-    const T *invJ = nullptr;    // [nu][np]
+    const T *invJ = nullptr;    // [nu][np] ([np] when geo_elem)
+    int geo_elem = 0;           // the tensor-core GEMM_DIV epilogue: 1/J per element
     const T *S = nullptr;       // [nu][9][np]
     // GEMM_DIV_RK: with r the RHS,
     //   rk_first: Uacc = U + c_acc r,  else Uacc += c_acc r
@@ -164,6 +179,34 @@ size_t tc_smem_bytes(const TcOperator &op);
 cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int *err, cudaStream_t s,
                            int no_producer = 0);
 
+// FP32 operator applications on the FP32 pipe (fr_gemm_f32.cu), the FR_FP32
+// mode's operator kernel: the state streamed into shared memory by TMA
+// boxes of 16 K rows x 128 columns, the operator beside it in one slab per
+// 16-wide stage, and register tiles of 4 operator rows x 4 state columns
+// per lane.  A 4-row block whose operator entries are all zero in a column
+// of the stage skips that column (its FMAs would add exact zeros), so each
+// output is the same FMA chain over k in increasing order as the
+// chunk-staged kernel (fr_gemm.cu) computes: the results are bitwise equal.
+// Up to 256 operator rows per pass (more rows: several passes).
+constexpr int kF32RowsPerPass = 256;
+struct F32Operator {
+    const float *img = nullptr;      // [pass][stage][16][MP]: column 16 s + k of image row i
+    const uint16_t *mask = nullptr;  // [pass][stage][MP / 4]: bit k set where the 4-row block is non-zero
+    const int *rowmap = nullptr;     // [pass][MP]: output row of image row i, -1 for padding
+    int M = 0, K1pad = 0, Kpad = 0, MP = 0, npass = 0;
+};
+// host: the image of A (M x (K1 + K2), row-major) with image row i of pass p
+// holding operator row perm[p MP + i] (perm empty: the identity); fills op's
+// sizes (the device pointers are the caller's to set)
+void f32_pack(const double *A, int M, int K1, int K2, const std::vector<int> &perm, std::vector<float> &img,
+              std::vector<uint16_t> &mask, std::vector<int> &rowmap, F32Operator &op);
+// C <- A [B1; B2] (GEMM_STORE epilogue, with add_ref) on the FP32 pipe;
+// *err (device) is set non-zero if a bounded wait of the kernel gave up.
+// no_producer (the bounded-wait self-test only): the copies are never
+// issued, so every wait runs out and the kernel takes its abort path
+cudaError_t launch_gemm_f32(const GemmArgsT<float> &g, const F32Operator &op, int *err, cudaStream_t s,
+                            int no_producer = 0);
+
 struct Phys {
     double gamma, mu, prandtl, beta, tau;
     double rho_inf, vinf[3], p_inf, t_wall;
@@ -200,14 +243,29 @@ using Fields = FieldsT<double>;
 
 // Interface flux-point pairs: sides, side a's unit normal, both |S^T n^|,
 // the LDG switch (+1 where side a is the left side), and (FP32-storage
-// modes) float copies of the normal and magnitudes, rounded once on the host
+// modes) float copies of the normal and magnitudes, rounded once on the host.
+// The two sides' element types, flux-point numbers and the switch share one
+// 32-bit word per pair (pair_code), the element numbers are ea, eb.
 struct Pairs {
     int64_t n;
-    const int *ta, *fa, *ea, *tb, *fb, *eb;
+    const uint32_t *code;
+    const int *ea, *eb;
     const double *nrm, *maga, *magb;
-    const signed char *sgn;
     const float *nrm_f, *maga_f, *magb_f;
 };
+// bits 0-1 type a, 2-3 type b (0..3: the element types and the halo),
+// 4-12 flux point a, 13-21 flux point b (< 512), 22: the switch is +1
+constexpr int kPairMaxFpt = 512;
+__host__ __device__ inline uint32_t pair_code(int ta, int tb, int fa, int fb, int sgn) {
+    return (uint32_t)ta | (uint32_t)tb << 2 | (uint32_t)fa << 4 | (uint32_t)fb << 13 | (uint32_t)(sgn > 0) << 22;
+}
+struct PairSides {
+    int ta, tb, fa, fb, sgn;
+};
+__host__ __device__ inline PairSides pair_sides(uint32_t c) {
+    return PairSides{(int)(c & 3u), (int)(c >> 2 & 3u), (int)(c >> 4 & 511u), (int)(c >> 13 & 511u),
+                     (c >> 22 & 1u) ? 1 : -1};
+}
 
 struct Bnd {
     int64_t n;
@@ -236,10 +294,12 @@ cudaError_t launch_wall_force(const Bnd &B, const double *bw, const FieldsT<T> &
 cudaError_t launch_sum_partials(const double *partial, int nblocks, int nq, double *out, cudaStream_t s);
 // transformed flux at the solution points of one type; U is the centred
 // stage input (u - uref).  invJ non-null: GU holds the reference gradient
-// (rows (j, d)) on entry and receives the physical gradient (rows (j, m))
+// (rows (j, d)) on entry and receives the physical gradient (rows (j, m)).
+// gj = 1: S [nu][9][np] and invJ [nu][np] per point; gj = 0: per element
+// ([9][np], [np]), for a type whose geometry factors are point-invariant
 template <typename T>
 cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, T *GU, const T *S, const T *invJ, T *FT,
-                        const Phys &ph, cudaStream_t s);
+                        const Phys &ph, cudaStream_t s, int gj = 1);
 // public [e][v][j] (double) -> internal [j][v][e]: `in` (double, may be
 // null) receives the values, `centred` (T, may be null) u - uref
 template <typename T>
@@ -339,11 +399,12 @@ cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const doub
 // non-null: R is the raw product of the divergence operator, and the RHS
 // is -(1/J) R (formed in T) plus rfs (FP64, may be null).  Us0 non-null
 // (a T register): the stage inputs of stages 2-3 are formed in T from the
-// step's centred start state, which the first stage copies from Us to Us0
+// step's centred start state, which the first stage copies from Us to Us0.
+// gj as for launch_flux (invJ per point or per element)
 template <typename T>
 cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
                              double c_acc, double c_stage, int first, int last, const T *invJ, const double *rfs,
-                             T *Us0, cudaStream_t s);
+                             T *Us0, cudaStream_t s, int gj = 1);
 // low-storage (2N) RK stage: dU = a dU + dt R (dU unread when first),
 // U += b dU, Us = U - uref; R [nu][V][np]
 template <typename T>
@@ -366,7 +427,9 @@ cudaError_t launch_reduce_partial(int nu, int64_t ne, int64_t np, const double *
                                   double gamma, double *partial, int nblocks, cudaStream_t s);
 cudaError_t launch_reduce_final(const double *partial, int nblocks, double *out, cudaStream_t s);
 // *flag = 1 if any solution value of the register (element columns below
-// ne) is non-finite or has a non-positive density or pressure
+// ne) is non-finite or has a non-positive density or pressure (one thread
+// per point; gamma and nblocks are not needed: the pressure is positive iff
+// 2 rho E > |rho v|^2 for any gamma > 1)
 cudaError_t launch_state_check(int nu, int64_t ne, int64_t np, const double *U, double gamma, int *flag, int nblocks,
                                cudaStream_t s);
 // measured FP64 FMA throughput (GFLOP/s) of the current device

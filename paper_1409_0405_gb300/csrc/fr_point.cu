@@ -138,14 +138,15 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int nblocks, 
 
 template <typename T, bool XFORM>
 __global__ void k_flux(int nu, int64_t ne, int64_t np, const T *__restrict__ U, T *__restrict__ GU,
-                       const T *__restrict__ S, const T *__restrict__ invJ, T *__restrict__ FT, const PhysT<T> ph) {
+                       const T *__restrict__ S, const T *__restrict__ invJ, T *__restrict__ FT, const PhysT<T> ph,
+                       int gj) {
     // 2-D grid: y = solution point, x = element
     if (ph.viscous)
         flux_at<T, XFORM, 2>(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.y,
-                             (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+                             (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gj);
     else
         flux_at<T, XFORM, 1>(nu, ne, np, U, GU, S, invJ, FT, ph, (int64_t)blockIdx.y,
-                      (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+                             (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gj);
 }
 
 // ---------------------------------------------------------------------------
@@ -214,9 +215,10 @@ __global__ void k_const_flux(int nu, int64_t ne, int64_t np, const double *__res
 __global__ void k_const_common(const Pairs P, const Bnd B, const Fields F, const PhysT<double> ph) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < P.n) {
-        const int ta = P.ta[k], tb = P.tb[k];
+        const PairSides ps = pair_sides(P.code[k]);
+        const int ta = ps.ta, tb = ps.tb;
         const int64_t npa = F.np[ta], npb = F.np[tb];
-        const int64_t oa = fpt_off(P.fa[k], P.ea[k], npa), ob = fpt_off(P.fb[k], P.eb[k], npb);
+        const int64_t oa = fpt_off(ps.fa, P.ea[k], npa), ob = fpt_off(ps.fb, P.eb[k], npb);
         const double *n = P.nrm + 3 * k;
         for (int v = 0; v < V; ++v) {
             const double f = fref_n(ph, v, n);
@@ -270,7 +272,7 @@ template <typename T>
 __global__ void k_rk_update(int64_t np, const T *__restrict__ R, double *__restrict__ U,
                             double *__restrict__ Uacc, T *__restrict__ Us, const Uref uref, double c_acc,
                             double c_stage, int first, int last, const T *__restrict__ invJ,
-                            const double *__restrict__ rfs, T *__restrict__ Us0) {
+                            const double *__restrict__ rfs, T *__restrict__ Us0, int gj) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= np) return;
     const int row = blockIdx.y;
@@ -281,7 +283,7 @@ __global__ void k_rk_update(int64_t np, const T *__restrict__ R, double *__restr
     if (invJ) {
         // R holds the raw divergence-plus-correction product: scale it by
         // -1/J (in T, as the divergence epilogue does) and add rfs
-        rt = -invJ[(int64_t)(row / V) * np + e] * R[idx];
+        rt = -invJ[(int64_t)(row / V) * gj * np + e] * R[idx];
         rv = (double)rt;
         if (rfs) {
             rv += rfs[idx];
@@ -372,25 +374,23 @@ __global__ void k_err_norm_partial(int nu, int64_t ne, int64_t np, const double 
 }
 
 // state check after a step: one store of 1 by any thread that finds a bad
-// point (no atomics needed; the flag is only ever set)
-__global__ void k_state_check(int nu, int64_t ne, int64_t np, const double *__restrict__ U, double gamma,
-                              int *flag) {
-    const int64_t tot = (int64_t)nu * np;
-    bool bad = false;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot && !bad;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = idx / np, e = idx - j * np;
-        if (e >= ne) continue;
-        const double *u = U + j * V * np + e;
-        double q[V];
+// point (no atomics needed; the flag is only ever set).  2-D grid: y = point
+// row j, x = element
+__global__ void k_state_check(int nu, int64_t ne, int64_t np, const double *__restrict__ U, int *flag) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (e >= ne || j >= nu) return;
+    const double *u = U + (int64_t)j * V * np + e;
+    double q[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) q[v] = u[v * np];
-        const double ke = 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0];
-        const double p = (gamma - 1.0) * (q[4] - ke);
-        bad = !(q[0] > 0.0) || !(p > 0.0) || !isfinite(p);
+    for (int v = 0; v < V; ++v) q[v] = u[v * np];
+    // p = (gamma - 1)(E - |m|^2 / (2 rho)) > 0 with rho > 0 (and gamma > 1)
+    // is 2 rho E > |m|^2: no division on the FP64 pipe
+    const double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    const double re = 2.0 * q[0] * q[4];
+    bool bad = !(q[0] > 0.0) || !(re > m2) || !isfinite(re) || !isfinite(m2);
 #pragma unroll
-        for (int v = 0; v < V; ++v) bad = bad || !isfinite(q[v]);
-    }
+    for (int v = 0; v < V; ++v) bad = bad || !isfinite(q[v]);
     if (bad) *(volatile int *)flag = 1;
 }
 
@@ -454,13 +454,13 @@ cudaError_t launch_common_flux(const Pairs &P, const Bnd &B, const FieldsT<T> &F
 
 template <typename T>
 cudaError_t launch_flux(int nu, int64_t ne, int64_t np, const T *U, T *GU, const T *S, const T *invJ, T *FT,
-                        const Phys &ph, cudaStream_t s) {
+                        const Phys &ph, cudaStream_t s, int gj) {
     if (ne == 0) return cudaSuccess;
     const dim3 grid(blocks_for(ne, 128), (unsigned)nu);
     if (invJ)
-        k_flux<T, true><<<grid, 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph));
+        k_flux<T, true><<<grid, 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph), gj);
     else
-        k_flux<T, false><<<grid, 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph));
+        k_flux<T, false><<<grid, 128, 0, s>>>(nu, ne, np, U, GU, S, invJ, FT, phys_t<T>(ph), gj);
     return cudaGetLastError();
 }
 
@@ -503,13 +503,13 @@ cudaError_t launch_center(int nu, int64_t np, const double *U, T *Us, const doub
 template <typename T>
 cudaError_t launch_rk_update(int nu, int64_t np, const T *R, double *U, double *Uacc, T *Us, const double *uref,
                              double c_acc, double c_stage, int first, int last, const T *invJ, const double *rfs,
-                             T *Us0, cudaStream_t s) {
+                             T *Us0, cudaStream_t s, int gj) {
     const int64_t n = (int64_t)nu * V * np;
     if (n == 0) return cudaSuccess;
     Uref r{{uref[0], uref[1], uref[2], uref[3], uref[4]}};
     k_rk_update<T><<<dim3(blocks_for(np, 256), (unsigned)(nu * V)), 256, 0, s>>>(np, R, U, Uacc, Us, r, c_acc,
                                                                                  c_stage, first, last, invJ, rfs,
-                                                                                 Us0);
+                                                                                 Us0, gj);
     return cudaGetLastError();
 }
 
@@ -543,8 +543,10 @@ cudaError_t launch_err_norm_partial(int nu, int64_t ne, int64_t np, const double
 
 cudaError_t launch_state_check(int nu, int64_t ne, int64_t np, const double *U, double gamma, int *flag, int nblocks,
                                cudaStream_t s) {
-    if (ne <= 0) return cudaSuccess;
-    k_state_check<<<nblocks, 256, 0, s>>>(nu, ne, np, U, gamma, flag);
+    (void)gamma;   // the pressure test needs only gamma > 1
+    (void)nblocks;  // one thread per point
+    if (ne <= 0 || nu <= 0) return cudaSuccess;
+    k_state_check<<<dim3(blocks_for(ne, 256), (unsigned)nu), 256, 0, s>>>(nu, ne, np, U, flag);
     return cudaGetLastError();
 }
 
@@ -599,13 +601,13 @@ cudaError_t launch_center_grouped(const CenterItem<T> *items, const int64_t *beg
     template cudaError_t launch_wall_force<T>(const Bnd &, const double *, const FieldsT<T> &, const Phys &,      \
                                               double *, int, cudaStream_t);                                   \
     template cudaError_t launch_flux<T>(int, int64_t, int64_t, const T *, T *, const T *, const T *, T *,       \
-                                        const Phys &, cudaStream_t);                                          \
+                                        const Phys &, cudaStream_t, int);                                     \
     template cudaError_t launch_pub_to_int<T>(int, int64_t, int64_t, const double *, double *, cudaStream_t,    \
                                               T *, const double *);                                           \
     template cudaError_t launch_center<T>(int, int64_t, const double *, T *, const double *, cudaStream_t);     \
     template cudaError_t launch_rk_update<T>(int, int64_t, const T *, double *, double *, T *, const double *,   \
                                              double, double, int, int, const T *, const double *, T *,       \
-                                             cudaStream_t);                                                  \
+                                             cudaStream_t, int);                                             \
     template cudaError_t launch_rk_2n_update<T>(int, int64_t, const T *, double *, double *, T *,                \
                                                 const double *, double, double, double, int, cudaStream_t);  \
     template cudaError_t launch_rk_2r_update<T>(int, int64_t, const T *, double *, double *, T *,                \

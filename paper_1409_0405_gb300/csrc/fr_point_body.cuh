@@ -257,11 +257,12 @@ template <typename T>
 __device__ __forceinline__ void common_solution_at(const Pairs &P, const Bnd &B, const FieldsT<T> &F,
                                                    const PhysT<T> &ph, int64_t k) {
     if (k < P.n) {
-        const int ta = P.ta[k], tb = P.tb[k];
+        const PairSides ps = pair_sides(P.code[k]);
+        const int ta = ps.ta, tb = ps.tb;
         const int64_t npa = F.np[ta], npb = F.np[tb];
-        const int64_t oa = fpt_off(P.fa[k], P.ea[k], npa), ob = fpt_off(P.fb[k], P.eb[k], npb);
+        const int64_t oa = fpt_off(ps.fa, P.ea[k], npa), ob = fpt_off(ps.fb, P.eb[k], npb);
         const T *UA = F.UF[ta] + oa, *UB = F.UF[tb] + ob;
-        const T b = ph.beta * T(P.sgn[k]);
+        const T b = ph.beta * T(ps.sgn);
         T *DA = F.DUF[ta] + oa, *DB = F.DUF[tb] + ob;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -308,9 +309,10 @@ template <typename T, int VIS = 0>
 __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, const FieldsT<T> &F, const PhysT<T> &ph,
                                                int64_t k) {
     if (k < P.n) {
-        const int ta = P.ta[k], tb = P.tb[k];
+        const PairSides ps = pair_sides(P.code[k]);
+        const int ta = ps.ta, tb = ps.tb;
         const int64_t npa = F.np[ta], npb = F.np[tb];
-        const int fa = P.fa[k], fb = P.fb[k], ea = P.ea[k], eb = P.eb[k];
+        const int fa = ps.fa, fb = ps.fb, ea = P.ea[k], eb = P.eb[k];
         const int64_t oa = fpt_off(fa, ea, npa), ob = fpt_off(fb, eb, npb);
         T ua[V], ub[V], fn[V];
 #pragma unroll
@@ -329,7 +331,7 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
             load_grad(F.GUF[tb], fb, eb, npb, gb);
             vis_flux_n(ua, qa, ga, ph.mu, ph.kq, n, fva);
             vis_flux_n(ub, qb, gb, ph.mu, ph.kq, n, fvb);
-            const T b = ph.beta * T(P.sgn[k]);
+            const T b = ph.beta * T(ps.sgn);
 #pragma unroll
             for (int v = 0; v < V; ++v)
                 fn[v] = fn[v] - (T(0.5) * (fva[v] + fvb[v]) - b * (fva[v] - fvb[v])) + ph.tau * (ua[v] - ub[v]);
@@ -374,19 +376,22 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
 // XFORM: GU holds the reference gradient g^_d on entry (rows (j, d)); the
 // physical gradient grad_m u = (1/J) sum_d S[d][m] g^_d is formed here,
 // written back over it (in place: one thread owns the point's 15 values) and
-// used for the viscous flux.
+// used for the viscous flux.  gj: 1 = S [nu][9][np] and 1/J [nu][np] per
+// point, 0 = one value per element ([9][np], [np]; elements whose geometry
+// factors are the same at every point)
 template <typename T, bool XFORM, int VIS = 0>
 __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T *__restrict__ U,
                                         T *__restrict__ GU, const T *__restrict__ S, const T *__restrict__ invJ,
-                                        T *__restrict__ FT, const PhysT<T> &ph, int64_t j, int64_t e) {
+                                        T *__restrict__ FT, const PhysT<T> &ph, int64_t j, int64_t e, int gj = 1) {
     if (j >= nu || e >= ne) return;
+    const int64_t jg = j * gj;
     T u[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) u[v] = U[(j * V + v) * np + e] + ph.uref[v];
     T s[9];
     if (XFORM) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];
+        for (int k = 0; k < 9; ++k) s[k] = S[(jg * 9 + k) * np + e];
     }
     const Prim<T> q = prim(u, ph.gamma);
     T F[V][3];
@@ -404,7 +409,7 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
 #pragma unroll
             for (int v = 0; v < V; ++v) g[m][v] = GU[((j * 3 + m) * V + v) * np + e];
         if (XFORM) {
-            const T ij = invJ[j * np + e];
+            const T ij = invJ[jg * np + e];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const T g0 = g[0][v], g1 = g[1][v], g2 = g[2][v];
@@ -427,7 +432,7 @@ __device__ __forceinline__ void flux_at(int nu, int64_t ne, int64_t np, const T 
         for (int m = 0; m < 3; ++m) F[v][m] -= ph.fref[v][m];
     if (!XFORM) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s[k] = S[(j * 9 + k) * np + e];
+        for (int k = 0; k < 9; ++k) s[k] = S[(jg * 9 + k) * np + e];
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d)

@@ -157,7 +157,7 @@ size_t stage_smem(const StagePlan<T> &plan) {
     for (int p = 0; p < plan.nph; ++p) {
         const StagePhase<T> &ph = plan.ph[p];
         if (!ph.ndesc) continue;
-        const size_t b = (size_t)ph.rc * ph.maxK * sizeof(T) + (size_t)ph.maxK * sizeof(int);
+        const size_t b = gemm_block_smem(ph.rc, (int)sizeof(T), ph.maxK, ph.maxK);
         if (b > m) m = b;
     }
     return m;

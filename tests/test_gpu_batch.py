@@ -65,8 +65,10 @@ def test_batched_equals_per_problem(precision):
         np.testing.assert_array_equal(g, r)
     info = b.info()
     assert info["launches_batched"] == info["launches_grouped"] == 4 * 4   # Euler: M0, flux, common flux, div
-    # per problem and stage: 2 types x (M0, flux, div) + 1 face kernel (Euler)
-    per = sum(4 * (3 * ((c.info["n_tet"] > 0) + (c.info["n_pri"] > 0)) + 1) for c in b.problems)
+    # per problem and stage (Euler): per type M0, flux, div (FP32: and the
+    # separate RK update), + 1 face kernel
+    per_type = 3 + (precision == fr.FR_FP32)
+    per = sum(4 * (per_type * ((c.info["n_tet"] > 0) + (c.info["n_pri"] > 0)) + 1) for c in b.problems)
     assert info["launches_per_problem"] == per > info["launches_grouped"]
     b.tune()
     for mode in (True, 2):

@@ -7,6 +7,8 @@ fr_batch_create and fr_part_create must return FR_ERR_NOMEM and free
 everything they had taken (the library's live-allocation count returns to
 its value before the call).
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -44,6 +46,9 @@ def test_every_allocation_failure_is_reported_and_leaks_nothing(what):
     from paper_1409_0405_gb300 import fr
     make = _makers()[what]
     fr.debug_fail_alloc(0)
+    # objects of earlier tests that only the cycle collector frees would
+    # otherwise release their allocations in the middle of the count
+    gc.collect()
     live0 = fr.debug_alloc_stats()[1]
     obj = make()
     n, live = fr.debug_alloc_stats()
@@ -56,6 +61,8 @@ def test_every_allocation_failure_is_reported_and_leaks_nothing(what):
         with pytest.raises(fr.FRError) as ei:
             make()
         assert ei.value.code == fr.FR_ERR_NOMEM, (k, str(ei.value))
+        del ei
+        gc.collect()
         assert fr.debug_alloc_stats()[1] == live0, k
     fr.debug_fail_alloc(0)
     obj = make()       # the library is still usable

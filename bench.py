@@ -765,11 +765,13 @@ def learned_mode(fr, torch, args, sp):
     from the projected initial state run side by side; states along the p=4
     run give training samples (P RHS_4(u_4) - RHS_2(P u_4), the p=4 RHS in
     FP64); one network per element type is trained on the GPU by the
-    library's kernels.  Reported: the RHS error with and without the
-    network on a later, held-out state; the kinetic-energy dissipation rate
-    of p=2 with and without the network against p=4, over the training
-    window and over the window after it; the p=4 check's verdict (the network
-    is kept only if it lowers the dissipation error after the training
+    library's kernels; a second set on the trajectory-consistent target
+    P RHS_4(u_4(t)) - RHS_2(u_2(t)), u_2 the plain p=2 solution at the same
+    time.  Reported: the RHS error with and without each network on a
+    later, held-out state; the kinetic-energy dissipation rate of p=2 with
+    and without the networks against p=4, over the training window and over
+    the window after it; the p=4 check's verdict (the better network is
+    kept only if it lowers the dissipation error after the training
     window); and the RHS throughput of each."""
     import synth
     from paper_1409_0405_gb300 import closure
@@ -798,9 +800,10 @@ def learned_mode(fr, torch, args, sp):
     u2_0h = u2_0.cpu().numpy()
     c4f.set_state(u0, sp)
     c2.set_state(u2_0h, sp)
-    S4, ke4, ke2 = [], [], []
+    S4, S2, ke4, ke2 = [], [], [], []
     for k in range(nwin):
         S4.append(torch.from_numpy(c4f.get_state(stream=sp)).cuda())
+        S2.append(torch.from_numpy(c2.get_state(stream=sp)).cuda())
         ke4.append(c4f.reduce(stream=sp)[5])
         ke2.append(c2.reduce(stream=sp)[5])
         if k + 1 < nwin:
@@ -818,26 +821,59 @@ def learned_mode(fr, torch, args, sp):
     prior = cl.error(c4, [S4[-1]])
 
     # a posteriori: p=2 with the network from the same initial state
-    cl.attach()
-    c2.set_state(u2_0h, sp)
-    ke2c = []
-    for k in range(nwin):
-        ke2c.append(c2.reduce(stream=sp, check=False)[5])
-        if k + 1 < nwin:
-            c2.step(dt, TGV_STRIDE, sp)
+    def a_posteriori(net):
+        """KE along p=2 with the network; NaN after a blown-up step (the
+        library reports it; set_state clears the condition)."""
+        net.attach()
+        c2.set_state(u2_0h, sp)
+        ke = []
+        for k in range(nwin):
+            ke.append(c2.reduce(stream=sp, check=False)[5])
+            if k + 1 < nwin:
+                try:
+                    c2.step(dt, TGV_STRIDE, sp)
+                except fr.FRError:
+                    ke += [float("nan")] * (nwin - 1 - k)
+                    break
+        net.detach()
+        c2.set_state(u2_0h, sp)
+        return ke
+
+    ke2c = a_posteriori(cl)
+    # the trajectory-consistent target: features and low-order RHS of the
+    # plain p=2 solution at the same time as each p=4 state
+    t0 = time.perf_counter()
+    cl_t = closure.Closure(c2, seed=0)
+    log_t = cl_t.fit(c4, list(zip(S4[:TGV_SNAPSHOTS], S2[:TGV_SNAPSHOTS])), iters=TGV_ITERS, lr=1e-3,
+                     log_every=TGV_ITERS // 4)
+    torch.cuda.synchronize()
+    train_t_s = time.perf_counter() - t0
+    prior_t = cl_t.error(c4, [(S4[-1], S2[-1])])
+    ke2t = a_posteriori(cl_t)
 
     def rates(ke):
         ke = np.asarray(ke)
         return -(ke[1:] - ke[:-1]) / (TGV_STRIDE * dt)
 
-    e4, e2, e2c = rates(ke4), rates(ke2), rates(ke2c)
+    e4, e2, e2c, e2t = rates(ke4), rates(ke2), rates(ke2c), rates(ke2t)
     tr = slice(0, TGV_SNAPSHOTS - 1)
     post = slice(TGV_SNAPSHOTS - 1, nwin - 1)
 
     def rel(a, w):
-        return float(np.mean(np.abs(a[w] - e4[w]) / np.abs(e4[w])))
+        """mean relative dissipation error over the windows (None after a
+        blown-up run)"""
+        v = float(np.mean(np.abs(a[w] - e4[w]) / np.abs(e4[w])))
+        return v if np.isfinite(v) else None
 
-    verdict = rel(e2c, post) < rel(e2, post)
+    def key(v):
+        return float("inf") if v is None else v
+
+    # the p=4 check: the better of the two networks after the training
+    # window, kept only if it beats plain p=2 there
+    best = cl if key(rel(e2c, post)) <= key(rel(e2t, post)) else cl_t
+    best_post = min(key(rel(e2c, post)), key(rel(e2t, post)))
+    verdict = best_post < key(rel(e2, post))
+    best.attach()
 
     # RHS throughput: p=2 + network, p=2, p=4 (FP64)
     def rhs_ms(ctx, u_dev, n=10):
@@ -857,7 +893,7 @@ def learned_mode(fr, torch, args, sp):
     ms2c = rhs_ms(c2, u2_0)
     cls2c, _ = c2.profile_read()
     c2.profile(False)
-    cl.detach()   # the plain p=2 fallback when the p=4 check is negative
+    best.detach()   # the plain p=2 fallback when the p=4 check is negative
     ms2 = rhs_ms(c2, u2_0)
     ms4 = rhs_ms(c4, u4d)
     closure_ms = cls2c["closure"][0] / max(sum(v[0] for v in cls2c.values()), 1e-30) * ms2c
@@ -877,13 +913,23 @@ def learned_mode(fr, torch, args, sp):
         "held_out_rhs_rel_rms_err": {name[k]: {"with_network": v[0], "plain_p2": v[1]} for k, v in prior.items()},
         "held_out_t": dt * TGV_STRIDE * (nwin - 1),
         "ke_dissipation_rel_err_vs_p4": {
-            "training_window": {"p2": rel(e2, tr), "p2_network": rel(e2c, tr)},
-            "after_training_window": {"p2": rel(e2, post), "p2_network": rel(e2c, post)},
+            "training_window": {"p2": rel(e2, tr), "p2_network": rel(e2c, tr),
+                                "p2_network_trajectory_target": rel(e2t, tr)},
+            "after_training_window": {"p2": rel(e2, post), "p2_network": rel(e2c, post),
+                                      "p2_network_trajectory_target": rel(e2t, post)},
             "p4_rate_end": float(e4[-1]), "measure": "mean over windows of |eps - eps4| / |eps4|, "
                                                      "eps = -dKE/dt over each stride; p=4 in FP32 RHS"},
+        "trajectory_target": {
+            "target": "P RHS_4(u_4(t)) - RHS_2(u_2(t)), u_2 the plain p=2 solution at the same t (features of u_2)",
+            "loss_log": {name[k]: v for k, v in log_t.items()},
+            "held_out_rhs_rel_rms_err": {name[k]: {"with_network": v[0], "plain_p2": v[1]}
+                                         for k, v in prior_t.items()},
+            "training_s": train_t_s},
         "p4_check": {"network_kept": bool(verdict),
-                  "rule": "keep the network only if it lowers the dissipation error after the training window; "
-                          "otherwise detach it (plain p=2 fallback)"},
+                     "network": "projected target" if best is cl else "trajectory target",
+                     "rule": "of the two networks (projected and trajectory-consistent targets) the one with the "
+                             "lower dissipation error after the training window, kept only if it beats plain p=2 "
+                             "there; otherwise detached (plain p=2 fallback)"},
         "rhs_ms": {"p2_network": ms2c, "p2": ms2, "p4": ms4, "closure_part_of_p2_network": closure_ms},
         "gdof_s": {"p2_network": nd2 / (ms2c * 1e-3) / 1e9, "p2": nd2 / (ms2 * 1e-3) / 1e9,
                    "p4": nd4 / (ms4 * 1e-3) / 1e9},

@@ -280,6 +280,7 @@ GemmArgsT<T> args_div(const fr_ctx *c, int t, const RKStage *rk) {
         g.U = D.U;
         g.Uacc = D.Uacc;
         g.Us = (T *)D.Us;
+        g.Us0 = (T *)D.Us0;  // FP32 storage: stage inputs formed in T
         g.c_acc = rk->c_acc;
         g.c_stage = rk->c_stage;
         g.rk_first = rk->first;
@@ -593,9 +594,7 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
             (rc = dev_alloc_bytes(c, &D.UF, sf * es)) || (rc = dev_alloc_bytes(c, &D.FC, sf * es)) ||
             (rc = dev_alloc_bytes(c, &D.FT, 3 * su * es)))
             return rc;
-        if ((prm->precision == FR_BF16X3 || prm->precision == FR_TF32X3) &&
-            (rc = dev_alloc_bytes(c, &D.Us0, su * es)))
-            return rc;
+        if (prm->precision != FR_FP64 && (rc = dev_alloc_bytes(c, &D.Us0, su * es))) return rc;
         if (prm->viscous) {
             if ((rc = dev_alloc_bytes(c, &D.DUF, sf * es)) || (rc = dev_alloc_bytes(c, &D.GU, 3 * su * es)) ||
                 (rc = dev_alloc_bytes(c, &D.GUF, 3 * sf * es)))

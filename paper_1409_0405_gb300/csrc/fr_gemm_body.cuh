@@ -207,14 +207,35 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
                 if (MODE == GEMM_DIV) {
                     g.C[idx] = g.rfs ? T((double)rt + g.rfs[idx]) : rt;
                 } else {
-                    // FP64 register update (both modes)
-                    const double rv = (double)rt + (g.rfs ? g.rfs[idx] : 0.0);
-                    const double u = g.U[idx];
+                    // FP64 register update (both modes; the arithmetic of
+                    // the streaming k_rk_update)
+                    // (the addition rounded on its own: no contraction with the
+                    // product above, whichever kernel inlines this body)
+                    double rv = (double)rt;
+                    T rt2 = rt;
+                    if (g.rfs) {
+                        rv = __dadd_rn(rv, g.rfs[idx]);
+                        rt2 = T(rv);
+                    }
                     if (g.rk_last) {
                         const double un = g.Uacc[idx] + g.c_acc * rv;
                         g.U[idx] = un;
                         g.Us[idx] = T(un - ur);
+                    } else if (g.Us0) {
+                        // FP32 storage: the next stage input in T from the
+                        // step's centred start state (kept in Us0)
+                        T b0;
+                        if (g.rk_first) {
+                            b0 = g.Us[idx];
+                            g.Us0[idx] = b0;
+                            g.Uacc[idx] = g.U[idx] + g.c_acc * rv;
+                        } else {
+                            b0 = g.Us0[idx];
+                            g.Uacc[idx] = g.Uacc[idx] + g.c_acc * rv;
+                        }
+                        g.Us[idx] = b0 + T(g.c_stage) * rt2;
                     } else {
+                        const double u = g.U[idx];
                         g.Uacc[idx] = (g.rk_first ? u : g.Uacc[idx]) + g.c_acc * rv;
                         g.Us[idx] = T((u - ur) + g.c_stage * rv);
                     }

@@ -5,14 +5,14 @@
 // and RC operator rows: every FMA then needs its own operator value from
 // shared memory, and the column of B is re-read once per row chunk.  Here
 // one CTA takes a tile of 128 state columns through all operator rows (up
-// to 256 per pass):
+// to 240 per pass):
 //   * a producer thread streams the tile's K rows in stages of 16 (one 2-D
 //     tensor-map box of 16 x 128 floats, rows past B1 or B2 zero-filled by
 //     the TMA unit) together with the operator's slab for that stage
 //     ([16][MP] floats, a plain bulk copy) into a ring of shared-memory
 //     slots, each slot guarded by an mbarrier (loaded) and released by the
-//     16 compute warps (freed);
-//   * compute warp w owns the 4-row blocks b = w, w + 16, w + 32, w + 48 of
+//     15 compute warps (freed);
+//   * compute warp w owns the 4-row blocks b = w, w + 15, w + 30, w + 45 of
 //     the pass, and lane l the 4 columns 4l .. 4l + 3 of the tile: per
 //     column k of a stage one 16-byte load of B (the lane's 4 columns), one
 //     broadcast 16-byte load of A (the block's 4 rows) and 16 FMAs into
@@ -38,9 +38,12 @@
 namespace fr {
 namespace {
 
-constexpr int kWarps = 16;                  // compute warps
+// 15 compute warps and the producer: 4 warps per SM sub-partition, whose
+// register file (16K) then holds 128 registers per thread
+constexpr int kWarps = 15;                  // compute warps
 constexpr int kBlocksPerWarp = 4;           // 4-row blocks per warp and pass
 constexpr int kThreads = (kWarps + 1) * 32;  // + the producer warp
+static_assert(kWarps * kBlocksPerWarp * 4 == kF32RowsPerPass, "rows per pass");
 constexpr int kBoxBytes = kStageK * kTileN * 4;
 constexpr int kMaxSlots = 12;
 constexpr int kSmemLimit = 232448;
@@ -51,8 +54,7 @@ struct Bars {
     int abort;
 };
 
-// 17 warps x 120 registers fit the register file; the accumulators take 64
-__global__ void __maxnreg__(120)
+__global__ void __launch_bounds__(kThreads, 1)
     k_gemm_f32(const GemmArgsT<float> g, const TileMap tm, const __grid_constant__ CUtensorMap tmB1,
                const __grid_constant__ CUtensorMap tmB2, const F32Operator op, int nslot, int *err,
                int no_producer) {
@@ -62,6 +64,13 @@ __global__ void __maxnreg__(120)
     Bars *bars = reinterpret_cast<Bars *>(smem + (size_t)nslot * slot_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nst = op.Kpad / kStageK, n1st = op.K1pad / kStageK;
+    // the operator's block masks and row map, copied once into shared
+    // memory (read at every stage and tile)
+    const int nmask = op.npass * nst * (op.MP / 4), nrow = op.npass * op.MP;
+    int *s_row = reinterpret_cast<int *>(bars + 1);
+    uint16_t *s_mask = reinterpret_cast<uint16_t *>(s_row + nrow);
+    for (int i = threadIdx.x; i < nrow; i += kThreads) s_row[i] = op.rowmap[i];
+    for (int i = threadIdx.x; i < nmask; i += kThreads) s_mask[i] = op.mask[i];
     const int64_t ntiles = tm.ept * tm.nvb;
     const int64_t nunits = ntiles * op.npass;  // (tile, pass), pass fastest
     const int64_t nmine = nunits > blockIdx.x ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -115,7 +124,8 @@ __global__ void __maxnreg__(120)
                     if ((issued >> qq) & 1u) mbar_drain(&bars->loaded[qq], (last_par >> qq) & 1u, err, 9);
         }
     } else {
-        // ---- compute warps
+        // ---- compute warps: warp w takes the 4-row blocks w + 15 bi, lane
+        // l the tile's columns 4l .. 4l + 3
         const int nblk = op.MP / 4;
         float acc[kBlocksPerWarp][4][4];
         int q = 0;
@@ -137,21 +147,41 @@ __global__ void __maxnreg__(120)
                 }
                 const uint8_t *slot = smem + (size_t)q * slot_bytes;
                 const float *slab = reinterpret_cast<const float *>(slot + kBoxBytes);
-                const uint16_t *mk = op.mask + ((size_t)pass * nst + ks) * nblk;
+                const uint16_t *mk = s_mask + ((size_t)pass * nst + ks) * nblk;
 #pragma unroll
                 for (int bi = 0; bi < kBlocksPerWarp; ++bi) {
                     const int blk = warp + kWarps * bi;
-                    uint32_t m = blk < nblk ? (uint32_t)__ldg(mk + blk) : 0u;
-                    while (m) {
-                        const int k = __ffs(m) - 1;
-                        m &= m - 1u;
-                        const float4 b = *reinterpret_cast<const float4 *>(slot + k * (kTileN * 4) + lane * 16);
-                        const float4 a = *reinterpret_cast<const float4 *>(slab + k * op.MP + blk * 4);
+                    uint32_t m = blk < nblk ? (uint32_t)mk[blk] : 0u;
+                    auto ldb = [&](int k) {
+                        return *reinterpret_cast<const float4 *>(slot + k * (kTileN * 4) + lane * 16);
+                    };
+                    auto lda = [&](int k) { return *reinterpret_cast<const float4 *>(slab + k * op.MP + blk * 4); };
+                    auto fma16 = [&](const float4 a, const float4 b) {
                         const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
 #pragma unroll
                             for (int c = 0; c < 4; ++c) acc[bi][r][c] = fmaf(av[r], bv[c], acc[bi][r][c]);
+                    };
+                    if (m == 0xFFFFu) {
+                        // a dense block: the 16 columns without the bit walk
+#pragma unroll
+                        for (int k = 0; k < kStageK; ++k) fma16(lda(k), ldb(k));
+                    } else if (m) {
+                        // the listed columns in increasing order, each one's
+                        // loads issued before the previous one's FMAs
+                        int k = __ffs(m) - 1;
+                        m &= m - 1u;
+                        float4 a = lda(k), b = ldb(k);
+                        while (m) {
+                            k = __ffs(m) - 1;
+                            m &= m - 1u;
+                            const float4 a2 = lda(k), b2 = ldb(k);
+                            fma16(a, b);
+                            a = a2;
+                            b = b2;
+                        }
+                        fma16(a, b);
                     }
                 }
                 __syncwarp();
@@ -173,11 +203,11 @@ __global__ void __maxnreg__(120)
                     if (blk >= nblk) continue;
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        const int row = __ldg(op.rowmap + (size_t)pass * op.MP + blk * 4 + r);
+                        const int row = s_row[pass * op.MP + blk * 4 + r];
                         if (row < 0) continue;
-                        const float4 v = make_float4(acc[bi][r][0] + add, acc[bi][r][1] + add, acc[bi][r][2] + add,
-                                                     acc[bi][r][3] + add);
-                        *reinterpret_cast<float4 *>(g.C + (int64_t)row * g.ldc + n0 + 4 * lane) = v;
+                        *reinterpret_cast<float4 *>(g.C + (int64_t)row * g.ldc + n0 + 4 * lane) =
+                            make_float4(acc[bi][r][0] + add, acc[bi][r][1] + add, acc[bi][r][2] + add,
+                                        acc[bi][r][3] + add);
                     }
                 }
             }
@@ -188,12 +218,15 @@ __global__ void __maxnreg__(120)
 
 }  // namespace
 
+// the slot ring, the barriers, the row map and the block masks
 size_t f32_smem_bytes(const F32Operator &op, int &nslot) {
     const size_t slot = (size_t)kBoxBytes + (size_t)op.MP * kStageK * 4;
-    int64_t n = ((int64_t)kSmemLimit - (int64_t)sizeof(Bars) - 1024) / (int64_t)slot;
+    const size_t meta = (size_t)op.npass * op.MP * sizeof(int) +
+                        (size_t)op.npass * (op.Kpad / kStageK) * (op.MP / 4) * sizeof(uint16_t);
+    int64_t n = ((int64_t)kSmemLimit - (int64_t)sizeof(Bars) - (int64_t)meta - 1024) / (int64_t)slot;
     if (n > kMaxSlots) n = kMaxSlots;
     nslot = n < 0 ? 0 : (int)n;
-    return (size_t)nslot * slot + sizeof(Bars);
+    return (size_t)nslot * slot + sizeof(Bars) + meta;
 }
 
 void f32_pack(const double *A, int M, int K1, int K2, const std::vector<int> &perm, std::vector<float> &img,

@@ -68,8 +68,10 @@ struct GemmArgsT {
     // GEMM_DIV_RK: with r the RHS,
     //   rk_first: Uacc = U + c_acc r,  else Uacc += c_acc r
     //   !rk_last: Us = U + c_stage r - uref;  rk_last: U = Uacc + c_acc r, Us = U - uref
+    //   with Us0 (FP32 storage): stages 2-3's Us = Us0 + c_stage r in T, Us0
+    //   the step's centred start state (copied from Us at the first stage)
     double *U = nullptr, *Uacc = nullptr;
-    T *Us = nullptr;
+    T *Us = nullptr, *Us0 = nullptr;
     double c_acc = 0, c_stage = 0;
     int rk_first = 0, rk_last = 0;
     // centring: the stage input Us holds u - uref (uref = the far-field
@@ -187,8 +189,8 @@ cudaError_t launch_gemm_tc(const GemmArgsT<float> &g, const TcOperator &op, int 
 // of the stage skips that column (its FMAs would add exact zeros), so each
 // output is the same FMA chain over k in increasing order as the
 // chunk-staged kernel (fr_gemm.cu) computes: the results are bitwise equal.
-// Up to 256 operator rows per pass (more rows: several passes).
-constexpr int kF32RowsPerPass = 256;
+// Up to 240 operator rows per pass (more rows: several passes).
+constexpr int kF32RowsPerPass = 240;
 struct F32Operator {
     const float *img = nullptr;      // [pass][stage][16][MP]: column 16 s + k of image row i
     const uint16_t *mask = nullptr;  // [pass][stage][MP / 4]: bit k set where the 4-row block is non-zero

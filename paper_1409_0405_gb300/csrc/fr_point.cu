@@ -286,7 +286,7 @@ __global__ void k_rk_update(int64_t np, const T *__restrict__ R, double *__restr
         rt = -invJ[(int64_t)(row / V) * gj * np + e] * R[idx];
         rv = (double)rt;
         if (rfs) {
-            rv += rfs[idx];
+            rv = __dadd_rn(rv, rfs[idx]);  // as the fused epilogue: no contraction
             rt = T(rv);
         }
     } else {

@@ -50,6 +50,25 @@ __device__ __forceinline__ void load_arow(const T *a, T (&av)[RCP]) {
 // One (row chunk, column tile) block of C <- A [B1; B2] with the epilogue
 // MODE.  Block-uniform: every thread of the block calls it with the same
 // (g, m0, tile); it stages the chunk of A in sA and synchronises.
+// acc[r] = fma(av[r], bv, acc[r]) for the RC rows; in FP32 two rows per
+// paired FMA instruction (fma.rn.f32x2: each lane an ordinary
+// round-to-nearest FMA, so the results are those of fmaf)
+template <typename T, int RC, int RCP>
+__device__ __forceinline__ void fma_rows(T (&acc)[RC], const T (&av)[RCP], T bv) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int r = 0; r + 1 < RC; r += 2)
+            asm("{\n\t.reg .b64 d, x, y;\n\tmov.b64 d, {%0, %1};\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %4};\n\t"
+                "fma.rn.f32x2 d, x, y, d;\n\tmov.b64 {%0, %1}, d;\n\t}"
+                : "+f"(acc[r]), "+f"(acc[r + 1])
+                : "f"(av[r]), "f"(av[r + 1]), "f"(bv));
+        if constexpr (RC % 2) acc[RC - 1] = fmaf(av[RC - 1], bv, acc[RC - 1]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
+    }
+}
+
 template <typename T, int RC, int MODE, bool NC = true>
 __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_t tile, T *sA) {
     constexpr int RCP = rc_pad(RC, sizeof(T));
@@ -134,8 +153,7 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
                 const T bv = bload<NC>(b1 + (int64_t)sK[i] * g.ldb1);
                 T av[RCP];
                 load_arow<T, RCP>(sA + i * RCP, av);
-#pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
+                fma_rows<T, RC, RCP>(acc, av, bv);
             }
             const T *b2 = g.B2 + n;
 #pragma unroll 2
@@ -143,8 +161,7 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
                 const T bv = bload<NC>(b2 + (int64_t)(sK[i] - g.K1) * g.ldb2);
                 T av[RCP];
                 load_arow<T, RCP>(sA + i * RCP, av);
-#pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
+                fma_rows<T, RC, RCP>(acc, av, bv);
             }
         } else if (nl >= 0) {
             {
@@ -155,8 +172,7 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
                     const T bv = bload<NC>(b + (int64_t)k * ld);
                     T av[RCP];
                     load_arow<T, RCP>(sA + k * RCP, av);
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
+                    fma_rows<T, RC, RCP>(acc, av, bv);
                 }
             }
             if (g.K2 > 0) {
@@ -168,8 +184,7 @@ __device__ __forceinline__ void gemm_block(const GemmArgsT<T> &g, int m0, int64_
                     const T bv = bload<NC>(b + (int64_t)k * ld);
                     T av[RCP];
                     load_arow<T, RCP>(a0 + k * RCP, av);
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) acc[r] = fma(av[r], bv, acc[r]);
+                    fma_rows<T, RC, RCP>(acc, av, bv);
                 }
             }
         }

@@ -16,7 +16,8 @@
 //     the pass, and lane l the 4 columns 4l .. 4l + 3 of the tile: per
 //     column k of a stage one 16-byte load of B (the lane's 4 columns), one
 //     broadcast 16-byte load of A (the block's 4 rows) and 16 FMAs into
-//     registers.  A block whose 4 rows are all zero in column k skips it
+//     registers (8 paired FP32 FMA instructions, each lane of a pair an
+//     ordinary round-to-nearest FMA).  A block whose 4 rows are all zero in column k skips it
 //     (the stage's 16-bit mask per block, precomputed): the FMA chain of
 //     each output is the same as the chunk-staged kernel's, k in increasing
 //     order, less terms whose operator entry is zero;
@@ -53,6 +54,15 @@ struct Bars {
     uint64_t freed[kMaxSlots];   // every compute warp is done with the slot
     int abort;
 };
+
+// (d0, d1) = (a b0 + d0, a b1 + d1): two independent round-to-nearest FMAs
+// in one paired FP32 instruction (each result equals fmaf's)
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a, float b0, float b1) {
+    asm("{\n\t.reg .b64 d, x, y;\n\tmov.b64 d, {%0, %1};\n\tmov.b64 x, {%2, %2};\n\tmov.b64 y, {%3, %4};\n\t"
+        "fma.rn.f32x2 d, x, y, d;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a), "f"(b0), "f"(b1));
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_f32(const GemmArgsT<float> g, const TileMap tm, const __grid_constant__ CUtensorMap tmB1,
@@ -157,11 +167,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     };
                     auto lda = [&](int k) { return *reinterpret_cast<const float4 *>(slab + k * op.MP + blk * 4); };
                     auto fma16 = [&](const float4 a, const float4 b) {
-                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                        const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-                        for (int r = 0; r < 4; ++r)
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) acc[bi][r][c] = fmaf(av[r], bv[c], acc[bi][r][c]);
+                        for (int r = 0; r < 4; ++r) {
+                            fma2(acc[bi][r][0], acc[bi][r][1], av[r], b.x, b.y);
+                            fma2(acc[bi][r][2], acc[bi][r][3], av[r], b.z, b.w);
+                        }
                     };
                     if (m == 0xFFFFu) {
                         // a dense block: the 16 columns without the bit walk

@@ -69,8 +69,11 @@ enum { FR_BC_WALL = 1, FR_BC_FARFIELD = 2 };
 /* Arithmetic of the operator applications (Table 1: single and double;
  * FR_BF16X3 / FR_TF32X3: FP32 storage with the operator applications on the
  * tensor cores in split BF16 or split TF32, x = r(x) + r(x - r(x)), three
- * products per pair and FP32 accumulation). */
-enum { FR_FP64 = 0, FR_FP32 = 1, FR_BF16X3 = 2, FR_TF32X3 = 3 };
+ * products per pair and FP32 accumulation; FR_FP64S: FP64 everywhere, the
+ * operator products of element types with dense operators formed on the
+ * tensor cores from exact integer digits, each output rounded once to
+ * FP64). */
+enum { FR_FP64 = 0, FR_FP32 = 1, FR_BF16X3 = 2, FR_TF32X3 = 3, FR_FP64S = 4 };
 
 typedef struct fr_ctx fr_ctx; /* opaque; owned by the library */
 
@@ -121,7 +124,18 @@ typedef struct {
                          is below FP32 resolution and skipped); or
                          FR_BF16X3 / FR_TF32X3: as FR_FP32 with the operator
                          applications on the tensor cores (split BF16 or
-                         split TF32, FP32 accumulate) */
+                         split TF32, FP32 accumulate); or FR_FP64S: as
+                         FR_FP64, with the operator products of the types
+                         whose operators are mostly non-zero (tetrahedra)
+                         on the tensor cores by exact splitting: every
+                         operator row and state column scaled by its
+                         largest power of two, its values cut into eight
+                         signed 7-bit integer digits (exact in BF16), the
+                         digit products of each of eight levels summed
+                         exactly in FP32, the levels combined in integer
+                         arithmetic and rounded once to FP64 (error about
+                         2^-56 K max|A| max|B| per output, below the FP64
+                         FMA chain's) */
     double rho_inf;   /* far-field density */
     double vel_inf[3];/* far-field velocity */
     double p_inf;     /* far-field pressure */
@@ -135,7 +149,7 @@ typedef struct {
  * order: polynomial order p in 1..4 (the paper exercises p = 1..4, Sec. 3.4).
  * On success *out receives a context the caller frees with fr_destroy.
  * Errors: FR_ERR_ARG, FR_ERR_MESH, FR_ERR_NOMEM, FR_ERR_CUDA;
- * FR_ERR_UNSUPPORTED for a precision outside FR_FP64..FR_TF32X3, or a
+ * FR_ERR_UNSUPPORTED for a precision outside FR_FP64..FR_FP64S, or a
  * split-BF16 context whose resident operator image leaves no room for two
  * ring slots (hexahedra at p = 4; split TF32 streams its operators and
  * takes them; operators of more than 256 rows run as two row blocks).
@@ -290,8 +304,9 @@ int fr_diagnostics(fr_ctx *ctx, double *out, void *cuda_stream);
 
 /*
  * fr_selftest_wait_timeout: failure-detection self-test of the streaming
- * operator kernels: the tensor-core kernel (FR_BF16X3 / FR_TF32X3) or the
- * streamed FP32 kernel (FR_FP32).  Launches the kernel of the first element
+ * operator kernels: the tensor-core kernel (FR_BF16X3 / FR_TF32X3), the
+ * streamed FP32 kernel (FR_FP32) or the exact-split FP64 kernel (FR_FP64S,
+ * the first element type it serves).  Launches the kernel of an element
  * type's interpolation with its copies withheld, so every bounded wait
  * inside it runs out (about 2 s); the kernel then leaves all its loops
  * (the tensor-core kernel frees its tensor memory) and reports
@@ -299,7 +314,7 @@ int fr_diagnostics(fr_ctx *ctx, double *out, void *cuda_stream);
  * that happened, after clearing the status, so the context stays usable;
  * no GPU fault, trap or unbounded wait is involved.  Overwrites the
  * interpolation scratch.  Errors: FR_ERR_ARG, FR_ERR_UNSUPPORTED
- * (FR_FP64), FR_ERR_TIMEOUT (a status left by earlier work), FR_ERR_CUDA.
+ * (FR_FP64; FR_FP64S without a type on the tensor cores), FR_ERR_TIMEOUT (a status left by earlier work), FR_ERR_CUDA.
  */
 int fr_selftest_wait_timeout(fr_ctx *ctx, void *cuda_stream);
 
@@ -348,6 +363,24 @@ int fr_profile_read(fr_ctx *ctx, double *ms, int64_t *count, int64_t *launches);
  * writes GFLOP/s (2 flop per FMA) to *gflops.  Synchronous.
  */
 int fr_peak_fp64(double *gflops, void *cuda_stream);
+
+/*
+ * fr_gemm_fp64s: C = A B in FP64 through the exact-split tensor-core kernel
+ * of FR_FP64S (the operator application of Sec. 2.1, Eq. 1, with the store
+ * epilogue), on arbitrary operands, for testing and for callers with their
+ * own constant operators.  A: host, row-major M x K, M >= 1, 1 <= K <= 409
+ * (the exactness bound of the level sums), finite.  B: device, row-major
+ * K x N (N >= 2 even, base 16-byte aligned).  C: device, row-major M x N,
+ * written.  Each C[i][n] is sum_k A[i][k] B[k][n] with an error of about
+ * 2^-56 K max_k|A[i][k]| max_k|B[k][n]| (operands rounded to 56 bits below
+ * their row and column maxima; the digit products summed exactly); a
+ * non-finite value in a column of B gives NaN in that column of C.  All
+ * arguments caller-owned; device scratch (the packed operator, column
+ * exponents, status) is allocated and freed by the call.  Synchronous.
+ * Errors: FR_ERR_ARG, FR_ERR_NOMEM, FR_ERR_CUDA, FR_ERR_TIMEOUT (a bounded
+ * wait of the kernel gave up).
+ */
+int fr_gemm_fp64s(int M, int K, const double *A, int64_t N, const double *B, double *C, void *cuda_stream);
 
 /*
  * Batched engine: many independent problems (their own meshes, element

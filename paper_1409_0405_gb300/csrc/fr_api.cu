@@ -310,6 +310,14 @@ GemmArgsT<T> with_sparse(const fr_ctx *c, int t, int which, const GemmArgsT<T> &
 
 template <>
 cudaError_t op_gemm<double>(fr_ctx *c, int t, int which, const GemmArgsT<double> &g, cudaStream_t s) {
+    const X64Operator &op = c->T[t].x64[which];
+    if (op.img) {
+        // the state operand's column exponents, then the exact-split product
+        cudaError_t e = launch_colexp(g.B1, g.ldb1, g.K1, g.B2, g.ldb2, g.K2, g.N, c->x64_E, s);
+        if (e == cudaSuccess) e = launch_gemm_x64(g, op, c->x64_E, c->tc_err, s);
+        ++c->launches;  // the pre-pass
+        return e;
+    }
     return launch_gemm<double>(with_sparse<double>(c, t, which, g), s);
 }
 
@@ -342,7 +350,7 @@ cudaError_t op_gemm<float>(fr_ctx *c, int t, int which, const GemmArgsT<float> &
 
 // FR_ERR_TIMEOUT if a tensor-core kernel gave up a wait (synchronises)
 int check_tc(fr_ctx *c) {
-    if (!is_f32(c) || !c->tc_err) return FR_OK;
+    if (!(is_f32(c) || is_x64(c)) || !c->tc_err) return FR_OK;
     int h = 0;
     int rc = cuda_check(cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
     if (rc) return rc;
@@ -531,8 +539,8 @@ int64_t ndof_of(const fr_ctx *c) {
 int check_params(int order, const fr_params *prm) {
     if (!prm) return set_err(FR_ERR_ARG, "null params");
     if (order < 1 || order > 4) return set_err(FR_ERR_ARG, "order must be in 1..4");
-    if (prm->precision < FR_FP64 || prm->precision > FR_TF32X3)
-        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64, FR_FP32, FR_BF16X3 or FR_TF32X3");
+    if (prm->precision < FR_FP64 || prm->precision > FR_FP64S)
+        return set_err(FR_ERR_UNSUPPORTED, "precision must be FR_FP64, FR_FP32, FR_BF16X3, FR_TF32X3 or FR_FP64S");
     if (!(prm->gamma > 1.0) || prm->mu < 0.0 || (prm->viscous && !(prm->prandtl > 0.0)))
         return set_err(FR_ERR_ARG, "invalid gas parameters");
     return FR_OK;
@@ -588,13 +596,13 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
         D.nu = ops[t].nu;
         D.nf = ops[t].nf;
         const size_t su = (size_t)D.nu * NV * D.np, sf = (size_t)D.nf * NV * D.np;
-        const size_t es = prm->precision != FR_FP64 ? sizeof(float) : sizeof(double);
+        const size_t es = f32_storage(prm->precision) ? sizeof(float) : sizeof(double);
         if ((rc = dev_alloc(c, &D.U, su)) || (rc = dev_alloc(c, &D.Uacc, su)) ||
             (rc = dev_alloc_bytes(c, &D.Us, su * es)) || (rc = dev_alloc_bytes(c, &D.R, su * es)) ||
             (rc = dev_alloc_bytes(c, &D.UF, sf * es)) || (rc = dev_alloc_bytes(c, &D.FC, sf * es)) ||
             (rc = dev_alloc_bytes(c, &D.FT, 3 * su * es)))
             return rc;
-        if (prm->precision != FR_FP64 && (rc = dev_alloc_bytes(c, &D.Us0, su * es))) return rc;
+        if (f32_storage(prm->precision) && (rc = dev_alloc_bytes(c, &D.Us0, su * es))) return rc;
         if (prm->viscous) {
             if ((rc = dev_alloc_bytes(c, &D.DUF, sf * es)) || (rc = dev_alloc_bytes(c, &D.GU, 3 * su * es)) ||
                 (rc = dev_alloc_bytes(c, &D.GUF, 3 * sf * es)))
@@ -656,7 +664,7 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
                 D.tc_split[w] = r0;
             }
         }
-        if (prm->precision == FR_FP64 || prm->precision == FR_FP32) {
+        if (prm->precision == FR_FP64 || prm->precision == FR_FP32 || prm->precision == FR_FP64S) {
             // the operators' exact zeros skipped chunk by chunk (prisms)
             const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
             const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok1[3] = {D.nu, D.nu, 3 * D.nu}, ok2[3] = {0, D.nf, D.nf};
@@ -665,7 +673,7 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
                 // of 3 rows; FP32 (bound by loads as much as by FMAs): the
                 // chunk size with the fewest FMAs over whole column unions
                 SparseOp sp;
-                const bool masked = prm->precision == FR_FP64;
+                const bool masked = !f32_storage(prm->precision);
                 if (masked ? !sparse_pack_masked(opv[w]->data(), om[w], ok1[w], ok2[w], sp)
                            : !sparse_pack(opv[w]->data(), om[w], ok1[w], ok2[w], w == 1, sp))
                     continue;
@@ -711,7 +719,30 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
                 op.rowmap = drow;
             }
         }
-        if (prm->precision != FR_FP64) {
+        if (prm->precision == FR_FP64S) {
+            // the operators of a type whose FMA kernel would run mostly
+            // non-zero products (tetrahedra; the prism and hexahedron
+            // operators vanish outside their tensor-product structure and
+            // keep the zero-skipping FMA kernel) on the tensor cores
+            const std::vector<double> *opv[3] = {&ops[t].M0, &ops[t].AGRAD, &ops[t].ADIV};
+            const int om[3] = {D.nf, 3 * D.nu, D.nu}, ok1[3] = {D.nu, D.nu, 3 * D.nu}, ok2[3] = {0, D.nf, D.nf};
+            for (int w = 0; w < 3; ++w) {
+                const size_t cnt = opv[w]->size();
+                size_t nnz = 0;
+                for (double v : *opv[w]) nnz += v != 0.0;
+                if (2 * nnz < cnt) continue;
+                std::vector<uint16_t> img;
+                std::vector<int> rexp;
+                X64Operator &op = D.x64[w];
+                if (!x64_pack(opv[w]->data(), om[w], ok1[w], ok2[w], w == 1, img, rexp, op)) continue;
+                uint16_t *dimg = nullptr;
+                int *dre = nullptr;
+                if ((rc = upload(c, &dimg, img)) || (rc = upload(c, &dre, rexp))) return rc;
+                op.img = (const uint8_t *)dimg;
+                op.rexp = dre;
+            }
+        }
+        if (f32_storage(prm->precision)) {
             // float views of the geometry and operators (rounded once).  In
             // the tensor-core modes, where the flux kernel and the RK update
             // stream the geometry, a type whose float S and 1/J are the same
@@ -756,7 +787,7 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
         D.xu = G.xu;
     }
     if (nhalo > 0) {
-        const size_t es = prm->precision != FR_FP64 ? sizeof(float) : sizeof(double);
+        const size_t es = f32_storage(prm->precision) ? sizeof(float) : sizeof(double);
         c->nhalo = nhalo;
         c->nhalo_p = (nhalo + kPad - 1) / kPad * kPad;
         const size_t sh = (size_t)NV * c->nhalo_p;
@@ -790,7 +821,7 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
             code[k] = pair_code(faces.ta[k], faces.tb[k], faces.fa[k], faces.fb[k], d > 0.0 ? 1 : -1);
         }
         if ((rc = upload(c, &c->pcode, code))) return rc;
-        if (prm->precision != FR_FP64) {
+        if (f32_storage(prm->precision)) {
             auto to_f = [](const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); };
             if ((rc = upload(c, &c->nrm_f, to_f(faces.n))) || (rc = upload(c, &c->maga_f, to_f(faces.maga))) ||
                 (rc = upload(c, &c->magb_f, to_f(faces.magb))) || (rc = upload(c, &c->bn_f, to_f(faces.bn))) ||
@@ -804,9 +835,9 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
     // flux.  Only FR_FP64 needs it: in the FP32-storage modes it lies far
     // below the arithmetic's resolution (the RHS carries ~1e-6 relative
     // rounding), so they skip it and its 8 bytes per output.
-    if (prm->precision == FR_FP64) {
+    if (!f32_storage(prm->precision)) {
         const Phys ph = phys_of(c);
-        const bool f32 = prm->precision != FR_FP64;
+        const bool f32 = false;
         double *tFT[NT] = {}, *tFC[NT] = {};
         std::vector<void *> tmp;
         for (int t = 0; t < NT; ++t) {
@@ -885,6 +916,12 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
     if ((rc = dev_alloc(c, &c->red, (size_t)nbt * 7 + 8))) return rc;
     if ((rc = dev_alloc(c, &c->diag, (size_t)kDiagBlocks * (2 + 6) + 8))) return rc;
     if ((rc = dev_alloc(c, &c->tc_err, 1))) return rc;
+    if (prm->precision == FR_FP64S) {
+        int64_t cols = 0;
+        for (int t = 0; t < NT; ++t)
+            if (c->T[t].present && 3 * NV * c->T[t].np > cols) cols = 3 * NV * c->T[t].np;
+        if ((rc = dev_alloc_bytes(c, (void **)&c->x64_E, (size_t)cols * sizeof(int)))) return rc;
+    }
     if (cudaHostAlloc((void **)&c->nf_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         c->nf_host = nullptr;
@@ -1487,7 +1524,8 @@ int fr_diagnostics(fr_ctx *c, double *out, void *stream) {
 
 int fr_selftest_wait_timeout(fr_ctx *c, void *stream) {
     if (!c) return set_err(FR_ERR_ARG, "null context");
-    if (!is_f32(c)) return set_err(FR_ERR_UNSUPPORTED, "the bounded-wait self-test needs an FP32-storage precision");
+    if (!is_f32(c) && !is_x64(c))
+        return set_err(FR_ERR_UNSUPPORTED, "the bounded-wait self-test needs a streamed operator kernel (not FR_FP64)");
     cudaStream_t s = (cudaStream_t)stream;
     int t = 0;
     while (t < NT && !c->T[t].present) ++t;
@@ -1495,11 +1533,21 @@ int fr_selftest_wait_timeout(fr_ctx *c, void *stream) {
     if ((rc = check_tc(c))) return rc;  // a status from earlier work is reported, not masked
     DevType &D = c->T[t];
     // M0 on the context's (centred) stage input, its state loads withheld
-    const GemmArgsT<float> g = args_m0<float>(c, t, (const float *)D.Us);
-    if ((rc = cuda_check(is_tc(c) ? launch_gemm_tc(g, D.tc[0], c->tc_err, s, 1)
-                                  : launch_gemm_f32(g, D.f32op[0], c->tc_err, s, 1),
-                         "self-test launch")))
-        return rc;
+    if (is_x64(c)) {
+        t = 0;
+        while (t < NT && !c->T[t].x64[0].img) ++t;
+        if (t == NT) return set_err(FR_ERR_UNSUPPORTED, "no element type on the exact-split tensor-core kernel");
+        DevType &Dx = c->T[t];
+        const GemmArgsT<double> g = args_m0<double>(c, t, (const double *)Dx.Us);
+        if ((rc = cuda_check(launch_gemm_x64(g, Dx.x64[0], c->x64_E, c->tc_err, s, 1), "self-test launch")))
+            return rc;
+    } else {
+        const GemmArgsT<float> g = args_m0<float>(c, t, (const float *)D.Us);
+        if ((rc = cuda_check(is_tc(c) ? launch_gemm_tc(g, D.tc[0], c->tc_err, s, 1)
+                                      : launch_gemm_f32(g, D.f32op[0], c->tc_err, s, 1),
+                             "self-test launch")))
+            return rc;
+    }
     if ((rc = cuda_check(cudaStreamSynchronize(s), "self-test sync"))) return rc;
     const int timed_out = check_tc(c) == FR_ERR_TIMEOUT;
     // clear the status so that the context stays usable
@@ -1525,6 +1573,58 @@ int fr_debug_alloc_stats(int64_t *out) {
 int fr_peak_fp64(double *gflops, void *stream) {
     if (!gflops) return set_err(FR_ERR_ARG, "null argument");
     return cuda_check(probe_fp64(gflops, (cudaStream_t)stream), "fp64 probe");
+}
+
+int fr_gemm_fp64s(int M, int K, const double *A, int64_t N, const double *B, double *C, void *stream) {
+    if (!A || !B || !C || M < 1 || K < 1 || K > kX64MaxK || N < 2 || N % 2 || ((uintptr_t)B % 16))
+        return set_err(FR_ERR_ARG, "fr_gemm_fp64s: bad sizes or pointers");
+    for (int64_t i = 0; i < (int64_t)M * K; ++i)
+        if (!std::isfinite(A[i])) return set_err(FR_ERR_ARG, "fr_gemm_fp64s: A must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    X64Operator op;
+    std::vector<uint16_t> img;
+    std::vector<int> rexp;
+    try {
+        if (!x64_pack(A, M, K, 0, false, img, rexp, op)) return set_err(FR_ERR_ARG, "fr_gemm_fp64s: operator");
+    } catch (...) {
+        return set_err(FR_ERR_NOMEM, "host allocation");
+    }
+    void *dimg = nullptr, *dre = nullptr, *dE = nullptr, *derr = nullptr;
+    auto release = [&] {
+        dev_free(dimg);
+        dev_free(dre);
+        dev_free(dE);
+        dev_free(derr);
+    };
+    if (dev_malloc(&dimg, img.size() * 2) != cudaSuccess || dev_malloc(&dre, rexp.size() * sizeof(int)) != cudaSuccess ||
+        dev_malloc(&dE, (size_t)N * sizeof(int)) != cudaSuccess || dev_malloc(&derr, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return set_err(FR_ERR_NOMEM, "fr_gemm_fp64s scratch");
+    }
+    int rc = cuda_check(cudaMemcpyAsync(dimg, img.data(), img.size() * 2, cudaMemcpyHostToDevice, s), "upload");
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(dre, rexp.data(), rexp.size() * sizeof(int), cudaMemcpyHostToDevice, s), "upload");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(derr, 0, sizeof(int), s), "status");
+    op.img = (const uint8_t *)dimg;
+    op.rexp = (const int *)dre;
+    GemmArgs g;
+    g.M = M;
+    g.N = N;
+    g.K1 = K;
+    g.B1 = B;
+    g.ldb1 = N;
+    g.C = C;
+    g.ldc = N;
+    g.mode = GEMM_STORE;
+    g.np = N;
+    if (!rc) rc = cuda_check(launch_colexp(B, N, K, nullptr, 0, 0, N, (int *)dE, s), "column exponents");
+    if (!rc) rc = cuda_check(launch_gemm_x64(g, op, (const int *)dE, (int *)derr, s), "exact-split product");
+    int h = 0;
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "fr_gemm_fp64s sync");
+    release();
+    if (!rc && h) rc = set_err(FR_ERR_TIMEOUT, "the exact-split kernel gave up a bounded wait");
+    return rc;
 }
 
 int fr_operator(int etype, int order, int which, double *out, int64_t *rows, int64_t *cols) {

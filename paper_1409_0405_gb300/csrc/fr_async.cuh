@@ -105,14 +105,15 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
-// Host: 2-D tensor map of one row-major operand block (rows x cols floats,
-// row stride ld floats), boxes of kStageK rows x kTileN columns, zero fill
+// Host: 2-D tensor map of one row-major operand block (rows x cols values,
+// row stride ld values), boxes of kStageK rows x kTileN columns, zero fill
 // out of bounds (rows past the block read as zeros)
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-inline cudaError_t encode_rows(CUtensorMap *m, const float *base, int64_t cols, int rows, int64_t ld) {
+inline cudaError_t encode_rows_t(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_t es, int64_t cols,
+                                 int rows, int64_t ld) {
     static EncodeTiled fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
@@ -124,13 +125,20 @@ inline cudaError_t encode_rows(CUtensorMap *m, const float *base, int64_t cols, 
         fn = reinterpret_cast<EncodeTiled>(p);
     }
     const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
-    const cuuint64_t stride[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint64_t stride[1] = {(cuuint64_t)ld * es};
     const cuuint32_t box[2] = {(cuuint32_t)kTileN, (cuuint32_t)kStageK};
     const cuuint32_t estride[2] = {1, 1};
-    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dim, stride, box, estride,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUresult r = fn(m, dt, 2, const_cast<void *>(base), dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+inline cudaError_t encode_rows(CUtensorMap *m, const float *base, int64_t cols, int rows, int64_t ld) {
+    return encode_rows_t(m, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), cols, rows, ld);
+}
+// the same boxes (16 rows x 128 columns) of FP64 values
+inline cudaError_t encode_rows(CUtensorMap *m, const double *base, int64_t cols, int rows, int64_t ld) {
+    return encode_rows_t(m, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, sizeof(double), cols, rows, ld);
 }
 
 // Tile t covers columns [n0, n1) of one variable block (N = nvb np columns,

@@ -63,6 +63,9 @@ struct DevType {
     // block shares the zeros of n_d M3), ADIV for the streamed FP32 kernel
     fr::F32Operator f32op[3];
     int tc_split[3] = {0, 0, 0};
+    // FR_FP64S: M0, AGRAD, ADIV for the exact-split tensor-core kernel
+    // (img null: that operator stays on the FP64 FMA kernel)
+    fr::X64Operator x64[3];
     // FR_FP64 / FR_FP32: chunk-compressed M0, AGRAD, ADIV (sp_rc 0: dense)
     int sp_rc[3] = {0, 0, 0}, sp_lmax[3] = {0, 0, 0}, sp_masked[3] = {0, 0, 0};
     int *sp_off[3] = {nullptr, nullptr, nullptr}, *sp_cols[3] = {nullptr, nullptr, nullptr};
@@ -91,6 +94,9 @@ struct fr_ctx {
     double *bw = nullptr;    // face weight of each boundary flux point
     double *diag = nullptr;  // diagnostics partials + result
     int *tc_err = nullptr;  // set by a tensor-core kernel whose bounded wait gave up
+    // FR_FP64S: the column exponents of the state operand of the current
+    // operator application (launch_colexp), 15 np of the largest type
+    int *x64_E = nullptr;
     // set (to 1) by the state check that ends every fr_step call when the
     // solution has a non-finite value or a non-positive density/pressure:
     // mapped pinned host memory, so the next fr_step reads it without a
@@ -156,8 +162,12 @@ int num_sms(int device);
 int step_guard(const fr_ctx *c);
 // the state check of the solution register (one launch per element type)
 int step_check(fr_ctx *c, cudaStream_t s);
-// FP32 storage (FR_FP32, FR_BF16X3, FR_TF32X3) rather than FP64
-inline bool is_f32(const fr_ctx *c) { return c->prm.precision != FR_FP64; }
+// FP32 storage (FR_FP32, FR_BF16X3, FR_TF32X3) rather than FP64 (FR_FP64,
+// FR_FP64S)
+inline bool f32_storage(int precision) { return precision != FR_FP64 && precision != FR_FP64S; }
+inline bool is_f32(const fr_ctx *c) { return f32_storage(c->prm.precision); }
+// FP64 with exact-split tensor-core operator products (FR_FP64S)
+inline bool is_x64(const fr_ctx *c) { return c->prm.precision == FR_FP64S; }
 // operator applications on the tensor cores (FR_BF16X3, FR_TF32X3)
 inline bool is_tc(const fr_ctx *c) { return c->prm.precision == FR_BF16X3 || c->prm.precision == FR_TF32X3; }
 // operator application `which` (0 M0, 1 AGRAD, 2 ADIV) of element type t:

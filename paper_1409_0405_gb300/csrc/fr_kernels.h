@@ -209,6 +209,51 @@ void f32_pack(const double *A, int M, int K1, int K2, const std::vector<int> &pe
 cudaError_t launch_gemm_f32(const GemmArgsT<float> &g, const F32Operator &op, int *err, cudaStream_t s,
                             int no_producer = 0);
 
+// FP64 operator applications on the tensor cores by exact splitting
+// (FR_FP64S, fr_gemm_x64.cu).  Every operand value x of a row (operator) or
+// column (state) whose values all lie below 2^(E - 1022) in magnitude (E
+// the largest biased FP64 exponent of the row or column) is held as the
+// integer X = round(x 2^(56 - (E - 1022))), |X| < 2^56, written with eight
+// signed base-128 digits, X = sum_p d_p 128^(7 - p), d_0 in [-128, 128] and
+// d_1..d_7 in [-64, 63]: each digit is exact in bf16.  A digit product is an
+// integer below 2^14, and the sum over K of the products of one level
+// (p + q = L, L = 0..7) stays below 2^24 for K <= 409, so the tensor cores
+// accumulate every level exactly in FP32; the levels are combined in
+// integer arithmetic and rounded once to FP64.  Operators of more than 64
+// rows run as row blocks (8 levels x 64 rows fill the 512 TMEM columns).
+constexpr int kX64Digits = 8;
+constexpr int kX64MaxRows = 64;
+constexpr int kX64MaxK = 409;
+struct X64Operator {
+    // [row block][16-wide stage][digit q]: Nmma x 16 bf16 in K-major core
+    // matrices (8 rows x 8 values; K halves 128 B apart, row groups 256 B)
+    const uint8_t *img = nullptr;
+    const int *rexp = nullptr;  // per operator row: largest biased exponent (0: the row is zero)
+    int M = 0, K1 = 0, K2 = 0, K1pad = 0, Kpad = 0;
+    int rows = 0;  // operator rows per row block (a multiple of 3 for GEMM_GRAD)
+    int nrb = 0;   // row blocks
+    int Nmma = 0;  // rows padded to 16 (the MMA's N)
+};
+// host: digits of a row-major M x (K1 + K2) FP64 operator in row blocks of
+// at most kX64MaxRows rows (whole points, 3 rows each, if mult3); fills op's
+// sizes (the device pointers are the caller's to set); false if K1 + K2
+// exceeds kX64MaxK
+bool x64_pack(const double *A, int M, int K1, int K2, bool mult3, std::vector<uint16_t> &img,
+              std::vector<int> &rexp, X64Operator &op);
+// the pre-pass: for every column n of [B1; B2] (N columns), the largest
+// biased exponent of its values (0 if all are zero, 2047 if one is not finite)
+cudaError_t launch_colexp(const double *B1, int64_t ldb1, int K1, const double *B2, int64_t ldb2, int K2, int64_t N,
+                          int *E, cudaStream_t s);
+// C <- A [B1; B2] with g's epilogue (GEMM_STORE with add_ref, GEMM_GRAD,
+// GEMM_DIV, GEMM_DIV_RK; FP64 registers), E from launch_colexp of the same
+// B; *err (device) is set non-zero if a bounded wait of the kernel gave up.
+// no_producer (the bounded-wait self-test only): the copies are never
+// issued, so every wait runs out and the kernel takes its abort path
+cudaError_t launch_gemm_x64(const GemmArgsT<double> &g, const X64Operator &op, const int *E, int *err,
+                            cudaStream_t s, int no_producer = 0);
+// shared memory the kernel takes for op (0: the operator does not fit)
+size_t x64_smem_bytes(const X64Operator &op);
+
 struct Phys {
     double gamma, mu, prandtl, beta, tau;
     double rho_inf, vinf[3], p_inf, t_wall;

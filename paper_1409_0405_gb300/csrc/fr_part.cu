@@ -306,7 +306,7 @@ int part_create_impl(const fr_mesh *mesh, int order, const fr_params *prm, int n
         const auto &L = pl.local[p];
         if ((rc = device_setup(c, order, prm, h.ops, L.geo, L.faces, L.nhalo))) return rc;
     }
-    const size_t es = prm->precision == FR_FP64 ? sizeof(double) : sizeof(float);
+    const size_t es = f32_storage(prm->precision) ? sizeof(float) : sizeof(double);
     for (const auto &sg : pl.segs) {
         fr_part::DSeg d;
         d.src = sg.src;
@@ -464,7 +464,7 @@ int fr_part_rhs(fr_part *pp, const double *u_dev, double *r_dev, void *stream) {
     if (!pp || !u_dev || !r_dev) return set_err(FR_ERR_ARG, "null argument");
     if (u_dev == r_dev) return set_err(FR_ERR_ARG, "u and r may not alias");
     cudaStream_t s = (cudaStream_t)stream;
-    return pp->prm.precision != FR_FP64 ? part_rhs_impl<float>(pp, u_dev, r_dev, s)
+    return f32_storage(pp->prm.precision) ? part_rhs_impl<float>(pp, u_dev, r_dev, s)
                                         : part_rhs_impl<double>(pp, u_dev, r_dev, s);
 }
 
@@ -474,7 +474,7 @@ int fr_part_step(fr_part *pp, double dt, int nsteps, void *stream) {
     for (fr_ctx *c : pp->P)
         if ((rc = step_guard(c))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    rc = pp->prm.precision != FR_FP64 ? part_step_impl<float>(pp, dt, nsteps, s)
+    rc = f32_storage(pp->prm.precision) ? part_step_impl<float>(pp, dt, nsteps, s)
                                       : part_step_impl<double>(pp, dt, nsteps, s);
     for (fr_ctx *c : pp->P)
         if (!rc && nsteps > 0) rc = step_check(c, s);

@@ -27,6 +27,7 @@ FR_FP64 = 0
 FR_FP32 = 1
 FR_BF16X3 = 2
 FR_TF32X3 = 3
+FR_FP64S = 4
 NVARS = 5
 
 OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
@@ -36,7 +37,7 @@ OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_check", "fr_step_ls", "fr_step_rk45",
            "fr_rk45_error", "fr_rk45_get_error", "fr_step_rk45_adaptive", "fr_reduce",
-           "fr_diagnostics", "fr_selftest_wait_timeout", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_strerror",
+           "fr_diagnostics", "fr_selftest_wait_timeout", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_gemm_fp64s", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_check",
            "fr_batch_selftest_wait_timeout", "fr_batch_info",
@@ -115,6 +116,8 @@ def load():
     lib.fr_profile_read.argtypes = [vp, dp, i64p, i64p]
     lib.fr_peak_fp64.argtypes = [dp, vp]
     lib.fr_peak_fp64.restype = C.c_int
+    lib.fr_gemm_fp64s.argtypes = [C.c_int, C.c_int, dp, C.c_int64, vp, vp, vp]
+    lib.fr_gemm_fp64s.restype = C.c_int
     lib.fr_reduce_noalloc.argtypes = [C.c_int64, C.c_int, vp, vp, C.c_double, vp, vp]
     lib.fr_reduce_noalloc.restype = C.c_int
     lib.fr_batch_create.argtypes = [C.c_int, C.POINTER(FRMesh), C.POINTER(C.c_int), C.POINTER(FRParams),
@@ -205,6 +208,18 @@ def operator(etype, order, which):
     out = np.empty((rows.value, cols.value), dtype=np.float64)
     _check(lib.fr_operator(et, order, wid, _dptr(out), C.byref(rows), C.byref(cols)))
     return out
+
+
+def gemm_fp64s(A, K_by_N_dev, C_dev, N, stream=None):
+    """fr_gemm_fp64s: C = A B through the exact-split tensor-core kernel.
+
+    A: host float64 (M x K); K_by_N_dev / C_dev: device pointers of the
+    row-major K x N operand and the M x N result."""
+    lib = load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    M, K = A.shape
+    _check(lib.fr_gemm_fp64s(int(M), int(K), _dptr(A), int(N), C.c_void_p(K_by_N_dev), C.c_void_p(C_dev),
+                             C.c_void_p(stream) if stream else None))
 
 
 def transfer(etype, p_from, p_to):

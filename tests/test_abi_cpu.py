@@ -190,8 +190,9 @@ def test_entry_points_reject_bad_arguments_without_a_gpu():
 
 
 def test_tensor_core_precisions_are_accepted_on_the_host():
-    """FR_BF16X3 and FR_TF32X3 pass the host checks (the failure without a
-    GPU is the device, not the precision); FR_TF32X3 + 1 does not."""
+    """FR_BF16X3, FR_TF32X3 and FR_FP64S pass the host checks (the failure
+    without a GPU is the device, not the precision); FR_FP64S + 1 and -1 do
+    not."""
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
@@ -200,4 +201,6 @@ def test_tensor_core_precisions_are_accepted_on_the_host():
     m = synth.vortex_box()
     assert _create_rc(m, p=2, precision=fr.FR_BF16X3) == fr.FR_ERR_CUDA
     assert _create_rc(m, p=2, precision=fr.FR_TF32X3) == fr.FR_ERR_CUDA
-    assert _create_rc(m, p=2, precision=fr.FR_TF32X3 + 1) == fr.FR_ERR_UNSUPPORTED
+    assert _create_rc(m, p=2, precision=fr.FR_FP64S) == fr.FR_ERR_CUDA
+    assert _create_rc(m, p=2, precision=fr.FR_FP64S + 1) == fr.FR_ERR_UNSUPPORTED
+    assert _create_rc(m, p=2, precision=-1) == fr.FR_ERR_UNSUPPORTED

@@ -17,11 +17,12 @@
 //     K <= 409: the FP32 accumulation of the tensor cores is exact.  The
 //     levels 0..7 are kept (36 digit pairs per 16-wide K step); the dropped
 //     ones are below 2^-52 of the column-times-row scale;
-//   * the epilogue converts the eight level sums to integers, combines them
-//     into W = sum_L S_L 128^(7 - L) (two 64-bit halves, W / 2^11 formed
-//     exactly), and rounds once to the FP64 value W 2^(Ei + En - 2096 + 11)
-//     with integer operations, then applies the mode's FP64 epilogue (the
-//     same arithmetic as the FMA kernel, fr_gemm_body.cuh).
+//   * the epilogue converts the eight level sums to integers and combines
+//     them into W = sum_L S_L 128^(7 - L) (two 64-bit halves; W / 2^11
+//     formed exactly), which frees the accumulators for the next tile's
+//     MMAs; then it rounds W once to the FP64 value W 2^(Ei + En - 2096 +
+//     11) and applies the mode's FP64 epilogue (the same arithmetic as the
+//     FMA kernel, fr_gemm_body.cuh).
 // The error of a result is that of rounding the operands to 56 bits below
 // their row and column maxima, about 2^-56 K max|A_i.| max|B_.n|, below
 // the FP64 FMA chain's own rounding.
@@ -122,6 +123,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_ld1(uint32_t taddr, float &v) {
     uint32_t r;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
@@ -136,11 +145,10 @@ __device__ __forceinline__ long long fixed56(double x, int E) {
     unsigned long long m = b & 0xFFFFFFFFFFFFFull;
     if (be) m |= 1ull << 52;
     else be = 1;
-    const int s = be - E + 3;  // <= 3: E bounds the column
-    unsigned long long X;
-    if (s >= 0) X = m << s;
-    else if (s > -54) X = (m + (1ull << (-s - 1))) >> (-s);
-    else X = 0ull;
+    // X = round(8 m / 2^sh), sh = E - be >= 0 (E bounds the column): 8 m <
+    // 2^56, so a shift of 63 already gives 0 (with its rounding half)
+    const int sh = E - be < 63 ? E - be : 63;
+    const unsigned long long X = ((m << 3) + ((1ull << sh) >> 1)) >> sh;
     return (b >> 63) ? -(long long)X : (long long)X;
 }
 
@@ -158,57 +166,87 @@ __device__ __forceinline__ void digits8(long long X, uint32_t (&f)[kX64Digits]) 
     for (int p = 1; p < kX64Digits; ++p) f[p] = digit_bits((uint32_t)(Y >> (7 * (7 - p))) & 127u, 8388672.0f);
 }
 
-// w 2^e2 rounded to the nearest FP64 value (ties to even), in integer
-// operations; results outside the normal range take the library path
+// w 2^e2 rounded to the nearest FP64 value (ties to even): the conversion
+// instruction rounds w, the power of two goes into the exponent field;
+// results outside the normal range take the library path
 __device__ __forceinline__ double ldexp_i64(long long w, int e2) {
+    const double d = __ll2double_rn(w);
+    const long long bits = __double_as_longlong(d);
+    const int ex = (int)((bits >> 52) & 0x7FF) + e2;
     if (w == 0) return 0.0;
-    const unsigned long long sgn = (unsigned long long)w & 0x8000000000000000ull;
-    unsigned long long a = w < 0 ? 0ull - (unsigned long long)w : (unsigned long long)w;
-    const int lz = __clzll((long long)a);
-    a <<= lz;  // leading one at bit 63
-    unsigned long long m = a >> 11;  // 53 bits
-    const unsigned int rem = (unsigned int)(a & 0x7FFull);
-    m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
-    const int ex = 63 - lz + e2 + 1023;
-    if (ex < 1 || ex > 2046) return ldexp((double)w, e2);
-    // the implicit bit of m (or its rounding carry) adds to the exponent field
-    return __longlong_as_double((long long)(sgn | (((unsigned long long)(ex - 1) << 52) + m)));
+    if (ex < 1 || ex > 2046) return ldexp(d, e2);
+    return __longlong_as_double(bits + ((long long)e2 << 52));
 }
 
-// sum_L s[L] 128^(7 - L) 2^(Ea + Eb - 2156 + 49) as FP64; s[L] are exact
-// integers below 2^24 in magnitude
-__device__ __forceinline__ double combine(const float (&s)[kX64Digits], int Ea, int Eb) {
-    if (Eb == 2047) return __longlong_as_double(0x7FF8000000000000ll);  // a non-finite state value
+// the integer value of a level sum s (exact, |s| < 2^24): below 2^22 in
+// magnitude, 1.5 2^23 + s is exact in [2^23, 2^24) and its low mantissa
+// bits are s + 2^22; wider levels take the conversion instruction
+__device__ __forceinline__ long long level_int(float s, bool wide) {
+    if (wide) return (long long)__float2int_rz(s);
+    return (long long)(__float_as_int(__fadd_rn(s, 12582912.0f)) - 0x4B400000);
+}
+
+// W' = floor(W / 2^11), W = sum_L s[L] 128^(7 - L) < 2^74 (two exact 64-bit
+// halves, zh 2^28 + zl); s[L] are exact integers below 2^24 in magnitude
+// (bit L of wide: level L may reach 2^22)
+__device__ __forceinline__ long long level_sum(const float (&s)[kX64Digits], uint32_t wide) {
+    const long long zh = level_int(s[0], wide & 1u) * (1ll << 21) + level_int(s[1], wide & 2u) * (1ll << 14) +
+                         level_int(s[2], wide & 4u) * (1ll << 7) + level_int(s[3], wide & 8u);
+    const long long zl = level_int(s[4], wide & 16u) * (1ll << 21) + level_int(s[5], wide & 32u) * (1ll << 14) +
+                         level_int(s[6], wide & 64u) * (1ll << 7) + level_int(s[7], wide & 128u);
+    return zh * (1ll << 17) + (zl >> 11);
+}
+
+// the product W' 2^(Ea + Eb - 2096) (= sum_L S_L 128^(7 - L) 2^(Ea + Eb -
+// 2156 + 49)) as FP64: NaN for a non-finite column, 0 for a zero row or
+// column
+__device__ __forceinline__ double finish(long long w, int Ea, int Eb) {
+    if (Eb == 2047) return __longlong_as_double(0x7FF8000000000000ll);
     if (Ea == 0 || Eb == 0) return 0.0;
-    long long zh = (long long)__float2int_rz(s[0]) * (1ll << 21) + (long long)__float2int_rz(s[1]) * (1ll << 14) +
-                   (long long)__float2int_rz(s[2]) * (1ll << 7) + (long long)__float2int_rz(s[3]);
-    long long zl = (long long)__float2int_rz(s[4]) * (1ll << 21) + (long long)__float2int_rz(s[5]) * (1ll << 14) +
-                   (long long)__float2int_rz(s[6]) * (1ll << 7) + (long long)__float2int_rz(s[7]);
-    // W = zh 2^28 + zl < 2^74; W' = floor(W / 2^11) exactly
-    const long long w = zh * (1ll << 17) + (zl >> 11);
     return ldexp_i64(w, Ea + Eb - 2096);
 }
 
-// the FP64 epilogues (the arithmetic of gemm_block in fr_gemm_body.cuh,
-// FP64 storage)
-__device__ __forceinline__ void epi_div(const GemmArgsT<double> &g, int mode, int j, int64_t n, int64_t e, double acc) {
-    const int64_t idx = (int64_t)j * g.ldc + n;
-    const double rt = -g.invJ[(int64_t)j * g.np + e] * acc;
-    if (mode == GEMM_DIV) {
-        g.C[idx] = g.rfs ? rt + g.rfs[idx] : rt;
-        return;
-    }
-    const double ur = g.uref[n / g.np];
-    double rv = rt;
-    if (g.rfs) rv = __dadd_rn(rv, g.rfs[idx]);
-    if (g.rk_last) {
-        const double un = g.Uacc[idx] + g.c_acc * rv;
-        g.U[idx] = un;
-        g.Us[idx] = un - ur;
-    } else {
-        const double u = g.U[idx];
-        g.Uacc[idx] = (g.rk_first ? u : g.Uacc[idx]) + g.c_acc * rv;
-        g.Us[idx] = (u - ur) + g.c_stage * rv;
+// The divergence epilogues (the arithmetic of gemm_block in fr_gemm_body.cuh,
+// FP64 storage) of rows j0 .. j0 + nr - 1 of column n: every load of the
+// group first (the rows' elements are this thread's alone), then the
+// arithmetic and stores
+__device__ __forceinline__ void epi_div8(const GemmArgsT<double> &g, int mode, int j0, int nr, int64_t n, int64_t e,
+                                         const double (&v)[8]) {
+    const double ur = mode == GEMM_DIV_RK ? g.uref[n / g.np] : 0.0;
+#pragma unroll
+    for (int h = 0; h < 8; h += 4) {  // four rows at a time (registers)
+        double ij[4], rf[4], u[4], ua[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (h + i >= nr) break;
+            const int64_t idx = (int64_t)(j0 + h + i) * g.ldc + n;
+            ij[i] = __ldg(g.invJ + (int64_t)(j0 + h + i) * g.np + e);
+            rf[i] = g.rfs ? __ldg(g.rfs + idx) : 0.0;
+            if (mode == GEMM_DIV_RK) {
+                u[i] = g.rk_last ? 0.0 : g.U[idx];
+                ua[i] = (g.rk_last || !g.rk_first) ? g.Uacc[idx] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (h + i >= nr) break;
+            const int64_t idx = (int64_t)(j0 + h + i) * g.ldc + n;
+            const double rt = -ij[i] * v[h + i];
+            if (mode == GEMM_DIV) {
+                g.C[idx] = g.rfs ? rt + rf[i] : rt;
+                continue;
+            }
+            double rv = rt;
+            if (g.rfs) rv = __dadd_rn(rv, rf[i]);
+            if (g.rk_last) {
+                const double un = ua[i] + g.c_acc * rv;
+                g.U[idx] = un;
+                g.Us[idx] = un - ur;
+            } else {
+                g.Uacc[idx] = (g.rk_first ? u[i] : ua[i]) + g.c_acc * rv;
+                g.Us[idx] = (u[i] - ur) + g.c_stage * rv;
+            }
+        }
     }
 }
 
@@ -293,6 +331,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t idx = 0; idx < total; ++idx, cu.next(tm, nrb, nks, nslot)) {
             if (cu.q != myslot) continue;
             const int q = cu.q;
+            // the columns' exponents (written by the pre-pass) before the wait
+            int Ec[2];
+#pragma unroll
+            for (int c2 = 0; c2 < 2; ++c2) {
+                const int64_t n = cu.n0 + 64 * half + 32 * c2 + lane;
+                Ec[c2] = n < g.N ? __ldg(E + n) : 0;
+            }
             if (!mbar_wait(&bars->loaded[q], cu.par, bars, err, 1)) break;
             uint8_t *slot = smem + (size_t)q * slot_bytes;
             const double *f = reinterpret_cast<const double *>(slot);
@@ -300,8 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
             for (int c2 = 0; c2 < 2; ++c2) {
                 const int col = 64 * half + 32 * c2 + lane;
-                const int64_t n = cu.n0 + col;
-                int Eb = n < g.N ? __ldg(E + n) : 0;
+                int Eb = c2 ? Ec[1] : Ec[0];
                 const bool live = Eb > 0 && Eb < 2047;
                 if (!live) Eb = 1078;  // digits of zeros below
                 const uint32_t rowoff = (uint32_t)(col >> 3) * 256u + (uint32_t)(col & 7) * 16u;
@@ -330,11 +374,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp < kConvWarps + kEpiWarps) {
         // ---- epilogue: lane quarter qq = warp % 4 holds tile rows (state
         // columns) 32 qq .. 32 qq + 31; the quarter's two warps take
-        // alternate 8-row groups (points, GEMM_GRAD) of the row block
+        // alternate 8-row groups (points, GEMM_GRAD) of the row block.  Two
+        // phases: the level sums of every row the thread owns become 64-bit
+        // integers W' (registers), which releases the accumulators to the
+        // next tile's MMAs; then the FP64 conversion and the mode's epilogue
         const int qq = warp & 3, part = (warp - kConvWarps) >> 2;
         const int row = qq * 32 + lane;
         int b = 0;
         uint32_t ph = 0;
+        constexpr int kGroups = kX64MaxRows / 16;      // 8-row groups per warp
+        constexpr int kPoints = (kX64MaxRows / 3 + 1) / 2;  // points per warp
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             if (!mbar_wait(&bars->acc_full[b], ph, bars, err, 2)) break;
             tc_fence_after();
@@ -349,55 +398,84 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int nrows = (g.M - r0) < op.rows ? g.M - r0 : op.rows;
             const uint32_t taddr = tmem + ((uint32_t)(qq * 32) << 16) + (uint32_t)b * acc_stride;
             if (MODE == GEMM_GRAD) {
-                for (int pt = part; 3 * pt < nrows; pt += 2) {
-                    float s[3][kX64Digits];
+                long long w[kPoints][3];
+#pragma unroll
+                for (int pi = 0; pi < kPoints; ++pi) {
+                    const int pt = part + 2 * pi;
+                    if (3 * pt >= nrows) break;
+                    float sv[3][kX64Digits];
 #pragma unroll
                     for (int L = 0; L < kX64Digits; ++L)
 #pragma unroll
                         for (int d = 0; d < 3; ++d)
-                            tmem_ld1(taddr + (uint32_t)L * (uint32_t)Nmma + (uint32_t)(3 * pt + d), s[d][L]);
+                            tmem_ld1(taddr + (uint32_t)L * (uint32_t)Nmma + (uint32_t)(3 * pt + d), sv[d][L]);
                     tmem_ld_wait();
-                    if (ok) {
-                        const int j = (r0 + 3 * pt) / 3;
-                        double gv[3];
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) gv[d] = combine(s[d], __ldg(op.rexp + 3 * j + d), Eb);
-                        const double *S = g.S + (int64_t)j * 9 * g.np + e;
-                        const double ij = g.invJ[(int64_t)j * g.np + e];
+                    for (int d = 0; d < 3; ++d) w[pi][d] = level_sum(sv[d], op.wide);
+                }
+                tc_fence_before();
+                mbar_arrive(&bars->acc_empty[b]);
 #pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            const double s0 = S[(0 * 3 + m) * g.np], s1 = S[(1 * 3 + m) * g.np],
-                                         s2 = S[(2 * 3 + m) * g.np];
-                            g.C[(int64_t)(3 * j + m) * g.ldc + n] = ij * (s0 * gv[0] + s1 * gv[1] + s2 * gv[2]);
+                for (int pi = 0; pi < kPoints; ++pi) {
+                    const int pt = part + 2 * pi;
+                    if (3 * pt >= nrows || !ok) break;
+                    const int j = (r0 + 3 * pt) / 3;
+                    const double *S = g.S + (int64_t)j * 9 * g.np + e;
+                    double Sv[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) Sv[k] = __ldg(S + (int64_t)k * g.np);
+                    const double ij = __ldg(g.invJ + (int64_t)j * g.np + e);
+                    double gv[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) gv[d] = finish(w[pi][d], __ldg(op.rexp + 3 * j + d), Eb);
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        g.C[(int64_t)(3 * j + m) * g.ldc + n] =
+                            ij * (Sv[0 * 3 + m] * gv[0] + Sv[1 * 3 + m] * gv[1] + Sv[2 * 3 + m] * gv[2]);
+                }
+            } else {
+                long long w[kGroups][8];
+#pragma unroll
+                for (int gi = 0; gi < kGroups; ++gi) {
+                    const int g8 = part + 2 * gi;
+                    if (8 * g8 >= nrows) break;
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {  // four rows at a time (registers)
+                        float sv[kX64Digits][4];
+#pragma unroll
+                        for (int L = 0; L < kX64Digits; ++L)
+                            tmem_ld4(taddr + (uint32_t)L * (uint32_t)Nmma + (uint32_t)(8 * g8 + 4 * hh), sv[L]);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float sl[kX64Digits];
+#pragma unroll
+                            for (int L = 0; L < kX64Digits; ++L) sl[L] = sv[L][i];
+                            w[gi][4 * hh + i] = level_sum(sl, op.wide);
                         }
                     }
                 }
-            } else {
+                tc_fence_before();
+                mbar_arrive(&bars->acc_empty[b]);
                 const double add = (MODE == GEMM_STORE && g.add_ref && ok) ? g.uref[n / g.np] : 0.0;
-                for (int g8 = part; 8 * g8 < nrows; g8 += 2) {
-                    float s[kX64Digits][8];
 #pragma unroll
-                    for (int L = 0; L < kX64Digits; ++L)
-                        tmem_ld8(taddr + (uint32_t)L * (uint32_t)Nmma + (uint32_t)(8 * g8), s[L]);
-                    tmem_ld_wait();
-                    if (ok) {
+                for (int gi = 0; gi < kGroups; ++gi) {
+                    const int g8 = part + 2 * gi;
+                    if (8 * g8 >= nrows || !ok) break;
+                    const int nr = nrows - 8 * g8 < 8 ? nrows - 8 * g8 : 8;
+                    double v[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int jl = 8 * g8 + i;
-                            if (jl >= nrows) break;
-                            const int j = r0 + jl;
-                            float sl[kX64Digits];
+                    for (int i = 0; i < 8; ++i)
+                        v[i] = i < nr ? finish(w[gi][i], __ldg(op.rexp + r0 + 8 * g8 + i), Eb) : 0.0;
+                    if (MODE == GEMM_STORE) {
 #pragma unroll
-                            for (int L = 0; L < kX64Digits; ++L) sl[L] = s[L][i];
-                            const double v = combine(sl, __ldg(op.rexp + j), Eb);
-                            if (MODE == GEMM_STORE) g.C[(int64_t)j * g.ldc + n] = v + add;
-                            else epi_div(g, MODE, j, n, e, v);
-                        }
+                        for (int i = 0; i < 8; ++i)
+                            if (i < nr) g.C[(int64_t)(r0 + 8 * g8 + i) * g.ldc + n] = v[i] + add;
+                    } else {
+                        epi_div8(g, MODE, r0 + 8 * g8, nr, n, e, v);
                     }
                 }
             }
-            tc_fence_before();
-            mbar_arrive(&bars->acc_empty[b]);
             if (++b == nbuf) {
                 b = 0;
                 ph ^= 1u;

@@ -233,6 +233,9 @@ struct X64Operator {
     int rows = 0;  // operator rows per row block (a multiple of 3 for GEMM_GRAD)
     int nrb = 0;   // row blocks
     int Nmma = 0;  // rows padded to 16 (the MMA's N)
+    // bit L set: the level-L sums may reach 2^22 in magnitude (K 2^14 for
+    // L = 0, K 2^12 (L + 3) above), past the float-to-integer shortcut
+    uint32_t wide = 0;
 };
 // host: digits of a row-major M x (K1 + K2) FP64 operator in row blocks of
 // at most kX64MaxRows rows (whole points, 3 rows each, if mult3); fills op's

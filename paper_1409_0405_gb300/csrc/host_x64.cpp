@@ -77,6 +77,11 @@ bool x64_pack(const double *A, int M, int K1, int K2, bool mult3, std::vector<ui
     op.nrb = (M + rows - 1) / rows;
     op.rows = rows;
     op.Nmma = (rows + 15) / 16 * 16;
+    op.wide = 0;
+    for (int L = 0; L < kX64Digits; ++L) {
+        const int64_t bound = L == 0 ? (int64_t)K << 14 : ((int64_t)K << 12) * (L + 3);
+        if (bound >= (1ll << 22)) op.wide |= 1u << L;
+    }
     rexp.assign((size_t)M, 0);
     for (int i = 0; i < M; ++i)
         for (int k = 0; k < K; ++k) {

@@ -149,6 +149,77 @@ def gemm_bytes_f32(ctx, kclass):
     return tot
 
 
+_OPNAME = {"M0": "M0", "grad": "AGRAD", "M0_grad": "M0", "div": "ADIV"}
+X64_DIGIT_PAIRS = 36     # digit pairs (levels 0..7) per 16-wide K step of the exact-split kernel
+X64_MAX_ROWS = 64        # operator rows per row block (the MMA's N before padding)
+X64_MAX_K = 409          # longest K whose level sums stay exact in FP32
+
+
+def gemm_flops_type(ctx, kclass, etype):
+    """gemm_flops for one element type: 2 x non-zero operator entries x
+    columns (5 variables x elements; x3 for M0 on the gradients)."""
+    from paper_1409_0405_gb300 import fr
+    ne = ctx.info["n_" + etype]
+    cols = 5.0 * ne * (3 if kclass == "M0_grad" else 1)
+    return 2.0 * _nnz(fr, ("tet", "pri", "hex").index(etype), ctx.order, _OPNAME[kclass]) * cols
+
+
+def x64_layout(ctx, kclass, etype):
+    """How FR_FP64S applies one operator: None when the type keeps the FMA
+    kernel (the library moves an operator to the exact-split tensor-core
+    kernel when at least half of its entries are non-zero and K <= 409),
+    else (row blocks, MMA N = rows padded to 16, K padded to 16 per
+    operand block) by the library's row-block rule (blocks of at most 64
+    rows, as even as possible, whole points of 3 rows for the gradient)."""
+    from paper_1409_0405_gb300 import fr
+    et = ("tet", "pri", "hex").index(etype)
+    A = fr.operator(et, ctx.order, _OPNAME[kclass])
+    M, K = A.shape
+    if 2 * np.count_nonzero(A) < A.size or K > X64_MAX_K:
+        return None
+    nu, nf = ctx.info["nu_" + etype], ctx.info["nf_" + etype]
+    k1, k2 = {"M0": (nu, 0), "grad": (nu, nf), "M0_grad": (nu, 0), "div": (3 * nu, nf)}[kclass]
+    kpad = -(-k1 // 16) * 16 + -(-k2 // 16) * 16
+    unit = 3 if kclass == "grad" else 1
+    nrb = -(-M // X64_MAX_ROWS)
+    rows = -(-M // nrb)
+    rows = -(-rows // unit) * unit
+    while rows > X64_MAX_ROWS:
+        rows -= unit
+    nrb = -(-M // rows)
+    return nrb, -(-rows // 16) * 16, kpad
+
+
+def x64_tensor_flops(ctx, kclass, etype):
+    """BF16 tensor-core flops of one exact-split launch (one RHS): 36 digit
+    pairs x 2 x (state columns padded to the 128-column tile) x (row blocks
+    x MMA N) x padded K."""
+    nrb, nmma, kpad = x64_layout(ctx, kclass, etype)
+    ncols = 5 * ctx.info["n_" + etype] * (3 if kclass == "M0_grad" else 1)
+    return X64_DIGIT_PAIRS * 2.0 * (-(-ncols // 128) * 128) * nrb * nmma * kpad
+
+
+def pointwise_bytes_fp64(ctx, kclass, etype=None):
+    """Algorithmic DRAM bytes of one FP64 point-wise launch (one RHS,
+    Navier-Stokes): the transformed flux of one type reads the state (5),
+    the physical gradient (15) and S (9), and writes F~ (15) doubles per
+    point; the common flux
+    reads both sides' flux-point states (10) and gradients (30), the unit
+    normal and both magnitudes (5), the pair word and both element numbers
+    (12 B), and writes both sides' common flux (10) per interface pair; the
+    common solution reads the states (10) and writes both jumps (10) with the
+    pair's normal data."""
+    i = ctx.info
+    if kclass == "flux":
+        pts = i["n_" + etype] * i["nu_" + etype]
+        return 8.0 * pts * (5 + 15 + 9 + 15)
+    if kclass == "common_flux":
+        return i["npairs"] * (8.0 * (10 + 30 + 5 + 10) + 12)
+    if kclass == "common_solution":
+        return i["npairs"] * (8.0 * (10 + 5 + 10) + 12)
+    return None
+
+
 def kernel_source_sha256(names=("fr_gemm.cu", "fr_gemm_body.cuh")):
     """SHA-256 of the operator kernel's source files, concatenated."""
     import hashlib
@@ -159,27 +230,29 @@ def kernel_source_sha256(names=("fr_gemm.cu", "fr_gemm_body.cuh")):
     return h.hexdigest()
 
 
-def profiled_traffic(kclass, profile="k_gemm_fp64_boundary_layer_p4_nx15.md"):
+def profiled_traffic(kclass, profile="k_gemm_fp64_boundary_layer_p4_nx15.md", etype=None,
+                     names=("fr_gemm.cu", "fr_gemm_body.cuh")):
     """DRAM bytes per launch (dram__bytes_read + dram__bytes_write) of one
-    operator class at full size, as recorded in the committed ncu summary's
-    `bench-traffic` line (measured on a smaller case and scaled by the
-    element count), or None when the kernel source has changed since that
-    capture (its SHA-256 no longer matches) or no line exists."""
+    operator class (of one element type when etype is given) at full size,
+    as recorded in a committed ncu summary's `bench-traffic` lines (measured
+    on a smaller case and scaled by the element count), or None when the
+    kernel's source files (names) have changed since that capture (their
+    SHA-256 no longer matches) or no line exists."""
     import re
     try:
         with open(os.path.join(ROOT, "profiles", profile)) as f:
             txt = f.read()
     except OSError:
         return None, "no profile summary"
-    sha = kernel_source_sha256()
-    for m in re.finditer(r"bench-traffic: class=(\w+) sha256=([0-9a-f]+) bytes_per_launch_full_size=([0-9.eE+]+)",
-                         txt):
-        if m.group(1) != kclass:
+    sha = kernel_source_sha256(names)
+    for m in re.finditer(r"bench-traffic: class=(\w+)(?: type=(\w+))? sha256=([0-9a-f]+) "
+                         r"bytes_per_launch_full_size=([0-9.eE+]+)", txt):
+        if m.group(1) != kclass or m.group(2) != etype:
             continue
-        if m.group(2) != sha:
+        if m.group(3) != sha:
             return None, "kernel changed since the ncu capture"
-        return float(m.group(3)), f"profiles/{profile}"
-    return None, f"no capture for class {kclass}"
+        return float(m.group(4)), f"profiles/{profile}"
+    return None, f"no capture for class {kclass}" + (f" ({etype})" if etype else "")
 
 
 def measured_peaks():
@@ -589,12 +662,12 @@ def partitioned_mode(fr, torch, mesh, u0, dt, ms_single, args, sp):
 
 def p3_modes(fr, torch, mesh, args, sp):
     """The precision study's throughput at p = 3 (the same mesh and flow):
-    GDOF/s of an RK4 step in FP64 and in each reduced precision."""
+    GDOF/s of an RK4 step in both FP64 forms and in each reduced precision."""
     out = {}
     dt = time_step_size(mesh, 3)
     u0 = None
-    for name, prec in (("fp64", fr.FR_FP64), ("fp32", fr.FR_FP32), ("bf16x3", fr.FR_BF16X3),
-                       ("tf32x3", fr.FR_TF32X3)):
+    for name, prec in (("fp64s", fr.FR_FP64S), ("fp64", fr.FR_FP64), ("fp32", fr.FR_FP32),
+                       ("bf16x3", fr.FR_BF16X3), ("tf32x3", fr.FR_TF32X3)):
         ctx = fr.Context(mesh, 3, **flow_params(), precision=prec)
         if u0 is None:
             u0 = points_to_public(synth_mod().perturbed_freestream(ctx.upts_points(), seed=2,
@@ -943,6 +1016,195 @@ def learned_mode(fr, torch, args, sp):
 
 
 # ---------------------------------------------------------------------------
+GEMM_CLASSES = ("M0", "grad", "M0_grad", "div")
+X64_PROFILE = "k_gemm_x64_boundary_layer_p4_nx40.md"
+X64_SOURCES = ("fr_gemm_x64.cu", "fr_gemm_body.cuh")
+
+
+def fp64_peaks(fr, torch, local, sp):
+    """FP64 denominators: the FMA peak derived from the SM count and the
+    maximum SM clock, the library's FMA probe and cuBLAS DGEMM (the paper's
+    reference-peak method), in TFLOP/s."""
+    peaks = measured_peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_ghz = float(peaks.get("sm_max_mhz", 2070.0)) / 1e3
+    out = {"derived": nsm * 2 * 2 * clk_ghz / 1e3,
+           "source": f"derived: {nsm} SMs x 2 FP64 FMA/clk x 2 flop x {clk_ghz:.2f} GHz (maximum SM clock)"}
+    try:
+        out["fma_probe"] = fr.peak_fp64(sp) / 1e3
+    except Exception:
+        out["fma_probe"] = None
+    try:
+        out["dgemm"] = dgemm_reference_tflops(torch)
+    except Exception:
+        out["dgemm"] = None
+    return out
+
+
+def alu_roofline(flops, ms, n, kernel, p64, traffic=None, traffic_src="n/a"):
+    """FP64-pipe roofline entry: flops over ms of device time, n launches."""
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": p64["derived"], "unit": "TFLOP/s",
+            "frac": ach / p64["derived"], "traffic": traffic, "traffic_source": traffic_src,
+            "algorithmic_flops_per_launch": flops / max(n, 1),
+            "flops": "2 x non-zero operator entries x columns (bench.gemm_flops)",
+            "kernel": kernel, "launches": n, "avg_launch_ms": ms / max(n, 1),
+            "peak_source": p64["source"],
+            "peak_measured_fma_probe": p64["fma_probe"],
+            "frac_of_measured_fma_probe": (ach / p64["fma_probe"]) if p64["fma_probe"] else None,
+            "reference_peak_cublas_dgemm": p64["dgemm"],
+            "frac_of_reference_peak": (ach / p64["dgemm"]) if p64["dgemm"] else None}
+
+
+def step_roofline(fr, torch, ctx, prec, classes, typed, args, sp, local):
+    """Roofline of the dominant kernel of the timed RK4 steps.
+
+    FR_FP64: the dominant operator class (FP64 pipe; flops = 2 x non-zero
+    operator entries x columns).  FR_FP64S: the dominant launch by class and
+    element type: an exact-split tensor-core launch against the sustained
+    BF16 tensor peak (36 digit-pair MMAs per product, with its FP64-equivalent
+    rate beside it), an FMA operator launch against the FP64 pipe, a
+    point-wise launch against HBM (algorithmic bytes).  FP32-storage modes:
+    the dominant operator class against HBM."""
+    peaks = measured_peaks()
+    nrhs = 4 * args.steps
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    full = args.nx == 75
+    if prec == fr.FR_FP64S:
+        # launches grouped by kernel: the FMA operator kernel (types whose
+        # operators stay on the FP64 pipe), the exact-split kernel (its
+        # column-exponent pre-pass is inside the same event pair), and each
+        # point-wise kernel
+        groups = {}
+        for cls, ty in typed:
+            if cls in GEMM_CLASSES and ty != "all":
+                kern = "k_gemm_x64" if x64_layout(ctx, cls, ty) is not None else "k_gemm"
+            else:
+                kern = "k_" + cls
+            groups.setdefault(kern, []).append((cls, ty))
+        kern = max(groups, key=lambda g: sum(typed[k][0] for k in groups[g]))
+        keys = groups[kern]
+        ms = sum(typed[k][0] for k in keys)
+        n = sum(typed[k][1] for k in keys)
+        parts = ", ".join(f"{c}/{t}" for c, t in keys)
+
+        def traffic_of(profile=None, names=None):
+            if not full:
+                return None, "reduced case"
+            tot = 0.0
+            for c, t in keys:
+                kw = {} if profile is None else {"profile": profile, "names": names}
+                b, src = profiled_traffic(c, etype=t, **kw)
+                if b is None:
+                    return None, src
+                tot += b * typed[(c, t)][1]
+            return tot / max(n, 1), src
+
+        if kern == "k_gemm_x64":
+            tfl = sum(x64_tensor_flops(ctx, c, t) for c, t in keys) * nrhs
+            fl64 = sum(gemm_flops_type(ctx, c, t) for c, t in keys) * nrhs
+            ach = tfl / (ms * 1e-3) / 1e12
+            peak = peaks.get("bf16_tflops_sustained")
+            src = "measured cuBLAS bf16 GEMM, sustained (MEASURED_PEAKS.json bf16_tflops_sustained)"
+            if not peak:
+                peak, src = 1700.0, "fallback: 1.7 PFLOP/s bf16 sustained"
+            traffic, tsrc = traffic_of(X64_PROFILE, X64_SOURCES)
+            p64 = fp64_peaks(fr, torch, local, sp)
+            return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": traffic, "traffic_source": tsrc,
+                    "kernel": f"k_gemm_x64 ({parts})", "launches": n, "avg_launch_ms": ms / max(n, 1),
+                    "algorithmic_tensor_flops_per_launch": tfl / max(n, 1),
+                    "flops": "36 digit-pair BF16 MMAs per product: 36 x 2 x 128-padded columns x row "
+                             "blocks x MMA N x padded K (bench.x64_tensor_flops)",
+                    "peak_source": src,
+                    "fp64_equivalent_tflops": fl64 / (ms * 1e-3) / 1e12,
+                    "fp64_equivalent_frac_of_fp64_fma_peak": fl64 / (ms * 1e-3) / 1e12 / p64["derived"],
+                    "fp64_fma_peak": p64}
+        if kern == "k_gemm":
+            fl64 = sum(gemm_flops_type(ctx, c, t) for c, t in keys) * nrhs
+            traffic, tsrc = traffic_of()
+            return alu_roofline(fl64, ms, n, f"k_gemm FP64 FMA ({parts})", fp64_peaks(fr, torch, local, sp),
+                                traffic, tsrc)
+        b = sum(pointwise_bytes_fp64(ctx, c, t) or 0.0 for c, t in keys)
+        if b:
+            ach = b * nrhs / (ms * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "kernel": f"{kern} ({parts})", "launches": n,
+                    "avg_launch_ms": ms / max(n, 1), "algorithmic_bytes_per_launch": b * nrhs / max(n, 1),
+                    "bytes": "bench.pointwise_bytes_fp64", "peak_source": hbm_src}
+        return {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
+                "kernel": kern}
+    dom = max(classes, key=lambda k: classes[k][0])
+    dom_ms, dom_n = classes[dom]
+    if dom in GEMM_CLASSES and prec != fr.FR_FP64:
+        byts = gemm_bytes_f32(ctx, dom) * nrhs
+        achieved = byts / (dom_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": ("k_gemm_tc" if prec in (fr.FR_BF16X3, fr.FR_TF32X3) else "k_gemm") + f" ({dom})",
+                "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1), "peak_source": hbm_src}
+    if dom in GEMM_CLASSES:
+        traffic, tsrc = profiled_traffic(dom) if full else (None, "reduced case")
+        return alu_roofline(gemm_flops(ctx, dom) * nrhs, dom_ms, dom_n, f"k_gemm ({dom})",
+                            fp64_peaks(fr, torch, local, sp), traffic, tsrc)
+    return {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
+            "kernel": dom}
+
+
+def fp64_mode(fr, torch, mesh, counts, u0, dt, ctx_main, prec_main, name, args, sp, local):
+    """The other FP64 form of the headline workload (FR_FP64 FMA kernels, or
+    FR_FP64S exact-split tensor-core operator products): K timed RK4 steps,
+    its roofline, and the RHS and one-step increment differences between
+    the two forms (both match the FP64 oracle to 1e-12).  Returns the plain
+    FR_FP64 context (the reference of the reduced-precision errors) and the
+    entry."""
+    prec = fr.FR_FP64 if name == "fp64" else fr.FR_FP64S
+    ctx = fr.Context(mesh, ORDER, **flow_params(), precision=prec)
+    ctx.set_state(u0, sp)
+    for _ in range(max(args.warmup, 0)):
+        ctx.step(dt, 1, sp)
+    torch.cuda.synchronize()
+    stream = torch.cuda.ExternalStream(sp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(dt, 1, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    classes, launches = ctx.profile_read()
+    typed = ctx.profile_read_types()
+    ctx.profile(False)
+    ud = torch.from_numpy(u0).cuda()
+    ra, rb = torch.empty_like(ud), torch.empty_like(ud)
+    ctx_main.rhs(ud.data_ptr(), ra.data_ptr(), sp)
+    ctx.rhs(ud.data_ptr(), rb.data_ptr(), sp)
+    torch.cuda.synchronize()
+    rhs_diff = per_quantity_rel_err(ra.cpu().numpy(), rb.cpu().numpy(), counts)
+    ctx_main.set_state(u0, sp)
+    ctx_main.step(dt, 1, sp)
+    sa = ctx_main.get_state(stream=sp)
+    ctx.set_state(u0, sp)
+    ctx.step(dt, 1, sp)
+    sb = ctx.get_state(stream=sp)
+    inc_diff = per_quantity_rel_err(sa - u0, sb - u0, counts)
+    out = {"value": ctx.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+           "gpu_launches": int(launches),
+           "kernel_ms_per_step": {k: v[0] / args.steps for k, v in classes.items()},
+           "kernel_ms_per_step_by_type": {f"{k}/{t}": v[0] / args.steps for (k, t), v in typed.items()},
+           "roofline": step_roofline(fr, torch, ctx, prec, classes, typed, args, sp, local),
+           "rhs_rel_diff_vs_headline": rhs_diff, "step_increment_rel_diff_vs_headline": inc_diff,
+           "diff_measure": "[mass, momentum vector, energy] max|d|/max|ref|",
+           "workload": WORKLOAD + (" [FP64 FMA throughout]" if name == "fp64" else
+                                   " [operator products: exact-split FP64 on the tensor cores where dense]")}
+    if prec == fr.FR_FP64:
+        return ctx, out
+    ctx.close()
+    return ctx_main, out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -957,8 +1219,9 @@ def main():
     ap.add_argument("--state-error-steps", type=int, default=0,
                     help="instead of timing: run this many RK4 steps at p=3 and p=4 in FP64 and each reduced "
                          "precision and print their state and diagnostics errors against FP64")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3", "tf32x3"],
-                    help="arithmetic of the main timed step (default fp64, the headline workload)")
+    ap.add_argument("--precision", default="fp64s", choices=["fp64s", "fp64", "fp32", "bf16x3", "tf32x3"],
+                    help="arithmetic of the main timed step (default fp64s: FP64 with the exact-split "
+                         "tensor-core operator products, the headline workload; fp64: FP64 FMA throughout)")
     ap.add_argument("--batched-only", type=int, default=0,
                     help="profiling: time only the batched mode on its first N problems and print its entry")
     args = ap.parse_args()
@@ -1027,7 +1290,8 @@ def main():
         return
 
     mesh = synth.boundary_layer_box(nx=args.nx)
-    prec = {"fp64": fr.FR_FP64, "fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3, "tf32x3": fr.FR_TF32X3}[args.precision]
+    prec = {"fp64s": fr.FR_FP64S, "fp64": fr.FR_FP64, "fp32": fr.FR_FP32, "bf16x3": fr.FR_BF16X3,
+            "tf32x3": fr.FR_TF32X3}[args.precision]
     try:
         free0 = torch.cuda.mem_get_info()[0]
     except Exception:
@@ -1068,6 +1332,7 @@ def main():
     barrier()
     ms_total = ev0.elapsed_time(ev1)
     classes, launches = ctx.profile_read()
+    typed = ctx.profile_read_types()
     ctx.profile(False)
     ms_step = max_over_ranks(ms_total / args.steps, world, "cuda")
     value = job_gdofs(world, ndof, ms_step * 1e-3)
@@ -1095,10 +1360,18 @@ def main():
 
     # --- other precision modes beside the FP64 line (same mesh, same state) ---
     modes = {}
-    if not args.fp64_only and args.precision == "fp64":
-        modes["fp32"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_FP32, args, sp)
-        modes["bf16x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_BF16X3, args, sp)
-        modes["tf32x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx, fr.FR_TF32X3, args, sp)
+    fp64_line = args.precision in ("fp64", "fp64s")
+    if fp64_line and not args.fp64_only:
+        # the other FP64 form beside the headline; the plain FMA context is
+        # the reference of the reduced-precision errors (it matches the FP64
+        # oracle to 1e-12, as does FR_FP64S)
+        other = "fp64" if args.precision == "fp64s" else "fp64s"
+        ctx64, modes[other] = fp64_mode(fr, torch, mesh, counts, u0, dt, ctx, prec, other, args, sp, local)
+        modes["fp32"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, fr.FR_FP32, args, sp)
+        modes["bf16x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, fr.FR_BF16X3, args, sp)
+        modes["tf32x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, fr.FR_TF32X3, args, sp)
+        if ctx64 is not ctx:
+            ctx64.close()
         modes["rk45"] = rk45_mode(fr, torch, mesh, u0, dt, args, sp)
         modes["partitioned"] = partitioned_mode(fr, torch, mesh, u0, dt, ms_total / args.steps, args, sp)
         if args.nx == 75:
@@ -1112,59 +1385,22 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    # --- roofline of the dominant kernel class ---
-    dom = max(classes, key=lambda k: classes[k][0])
-    dom_ms, dom_n = classes[dom]
-    peaks = measured_peaks()
-    nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    clk_ghz = float(peaks.get("sm_max_mhz", 2070.0)) / 1e3
-    fp64_peak_derived = nsm * 2 * 2 * clk_ghz  # GFLOP/s: SMs x FP64 FMA/clk x 2 flop x GHz
-    peak_src = f"derived: {nsm} SMs x 2 FP64 FMA/clk x 2 flop x {clk_ghz:.2f} GHz (maximum SM clock)"
-    try:
-        fp64_peak_meas = fr.peak_fp64(sp)
-    except Exception:
-        fp64_peak_meas = None
-    try:
-        dgemm_ref = dgemm_reference_tflops(torch)
-    except Exception:
-        dgemm_ref = None
-    traffic, traffic_src = profiled_traffic(dom) if prec == fr.FR_FP64 and args.nx == 75 else (None, "n/a")
-    if dom in ("M0", "grad", "M0_grad", "div") and prec != fr.FR_FP64:
-        byts = gemm_bytes_f32(ctx, dom) * 4 * args.steps
-        achieved = byts / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
-                "kernel": ("k_gemm_tc" if prec in (fr.FR_BF16X3, fr.FR_TF32X3) else "k_gemm") + f" ({dom})",
-                "launches": dom_n,
-                "avg_launch_ms": dom_ms / max(dom_n, 1),
-                "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    elif dom in ("M0", "grad", "M0_grad", "div"):
-        flops = gemm_flops(ctx, dom) * 4 * args.steps  # per RHS x 4 RHS per step
-        achieved = flops / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved / 1e3, "peak": fp64_peak_derived / 1e3,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak_derived,
-                "traffic": traffic, "traffic_source": traffic_src,
-                "algorithmic_flops_per_launch": flops / max(dom_n, 1),
-                "kernel": f"k_gemm ({dom})", "launches": dom_n,
-                "avg_launch_ms": dom_ms / max(dom_n, 1),
-                "peak_source": peak_src,
-                "peak_measured_fma_probe": (fp64_peak_meas / 1e3) if fp64_peak_meas else None,
-                "frac_of_measured_fma_probe": (achieved / fp64_peak_meas) if fp64_peak_meas else None,
-                "reference_peak_cublas_dgemm": dgemm_ref,
-                "frac_of_reference_peak": (achieved / 1e3 / dgemm_ref) if dgemm_ref else None}
-    else:
-        roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": None, "traffic": None, "kernel": dom}
+    # --- roofline of the dominant kernel ---
+    roof = step_roofline(fr, torch, ctx, prec, classes, typed, args, sp, local)
     gemm_classes = ("M0", "grad", "M0_grad", "div")
     all_gemm = sum(gemm_flops(ctx, k) for k in gemm_classes) * 4 * args.steps
     clocks = sampler.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3+f32", "tf32x3": "tf32x3+f32"}[args.precision],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64s": "f64", "fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3+f32",
+                  "tf32x3": "tf32x3+f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": (WORKLOAD if args.nx == 75 else WORKLOAD + f" (reduced: nx={args.nx})")
-                   + ("" if args.precision == "fp64" else f" [{args.precision} arithmetic]"),
+                   + {"fp64s": " [operator products: exact-split FP64 on the tensor cores where dense (tets), "
+                                "FP64 FMA elsewhere]", "fp64": " [FP64 FMA throughout]"}.get(
+                       args.precision, f" [{args.precision} arithmetic]"),
                    "ndof": ndof, "rhs_per_step": 4, "dt": dt,
                    "l2": "inputs > L2 (state 339 MB per register, scratch > 4 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -1172,6 +1408,7 @@ def main():
                    "device_memory_gb": ctx_gb},
         "roofline": roof,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in classes.items()},
+        "kernel_ms_per_step_by_type": {f"{k}/{t}": v[0] / args.steps for (k, t), v in typed.items()},
         "gemm_fp64_tflops": all_gemm / (sum(classes[k][0] for k in gemm_classes) * 1e-3) / 1e12,
         "cpu_baseline": cpu_base,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(ndof * 8),

@@ -355,6 +355,18 @@ int fr_operator(int etype, int order, int which, double *out, int64_t *rows, int
 #define FR_NKCLASS 9
 int fr_profile(fr_ctx *ctx, int enable);
 int fr_profile_read(fr_ctx *ctx, double *ms, int64_t *count, int64_t *launches);
+/*
+ * fr_profile_read_types: the same events split by element type, for the
+ * launches that work on one type (the operator applications of classes
+ * 0, 2, 3, 6 and the point-wise flux of class 4): ms and count are
+ * caller-owned arrays of (FR_NTYPES + 1) * FR_NKCLASS entries, entry
+ * [b * FR_NKCLASS + k] for class k, with block b = 0 the launches that
+ * span all types (face kernels, closure, state check, the streaming RK
+ * update of the FP32-storage modes) and b = 1 + etype those of one type.
+ * Summing the blocks gives fr_profile_read's values.  Synchronises like
+ * fr_profile_read.  Errors: FR_ERR_ARG (null argument), FR_ERR_CUDA.
+ */
+int fr_profile_read_types(fr_ctx *ctx, double *ms, int64_t *count);
 
 /*
  * fr_peak_fp64: measured FP64 FMA throughput of the current device, the

@@ -370,7 +370,7 @@ int phase_interp(fr_ctx *c, T *const in[NT], cudaStream_t s) {
     for (int t = 0; t < NT; ++t) {
         if (!c->T[t].present) continue;
         const GemmArgsT<T> g = args_m0<T>(c, t, in[t]);
-        if ((rc = cuda_check(launch(c, K_M0, s, [&] { return op_gemm<T>(c, t, 0, g, s); }), "gemm M0"))) return rc;
+        if ((rc = cuda_check(launch(c, ktag(K_M0, t), s, [&] { return op_gemm<T>(c, t, 0, g, s); }), "gemm M0"))) return rc;
     }
     return FR_OK;
 }
@@ -398,11 +398,11 @@ int phase_grad(fr_ctx *c, T *const in[NT], cudaStream_t s) {
             if (!c->T[t].present) continue;
             GemmArgsT<T> g = args_grad<T>(c, t, in[t]);
             if (tc) g.mode = GEMM_STORE;
-            if ((rc = cuda_check(launch(c, K_GRAD, s, [&] { return op_gemm<T>(c, t, 1, g, s); }), "gemm grad")))
+            if ((rc = cuda_check(launch(c, ktag(K_GRAD, t), s, [&] { return op_gemm<T>(c, t, 1, g, s); }), "gemm grad")))
                 return rc;
             if (tc) {
                 DevType &D = c->T[t];
-                if ((rc = cuda_check(launch(c, K_FLUX, s,
+                if ((rc = cuda_check(launch(c, ktag(K_FLUX, t), s,
                                             [&] {
                                                 return launch_flux<T>(D.nu, D.ne, D.np, in[t], (T *)D.GU,
                                                                       (const T *)D.S_t, (const T *)D.invJ_t,
@@ -412,7 +412,7 @@ int phase_grad(fr_ctx *c, T *const in[NT], cudaStream_t s) {
                     return rc;
             }
             const GemmArgsT<T> h = args_m0grad<T>(c, t);
-            if ((rc = cuda_check(launch(c, K_M0_GRAD, s, [&] { return op_gemm<T>(c, t, 0, h, s); }), "gemm M0 grad")))
+            if ((rc = cuda_check(launch(c, ktag(K_M0_GRAD, t), s, [&] { return op_gemm<T>(c, t, 0, h, s); }), "gemm M0 grad")))
                 return rc;
         }
     }
@@ -435,7 +435,7 @@ int phase_div(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
     for (int t = 0; t < NT && !(is_f32(c) && c->prm.viscous); ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
-        if ((rc = cuda_check(launch(c, K_FLUX, s,
+        if ((rc = cuda_check(launch(c, ktag(K_FLUX, t), s,
                                     [&] {
                                         return launch_flux<T>(D.nu, D.ne, D.np, in[t], (T *)D.GU, (const T *)D.S_t,
                                                               (const T *)nullptr, (T *)D.FT, ph, s,
@@ -470,7 +470,7 @@ int phase_div(fr_ctx *c, T *const in[NT], const RKStage *rk, cudaStream_t s) {
         }
         const double *rfs = g.rfs;
         if (split_rk) g.mode = GEMM_STORE;
-        if ((rc = cuda_check(launch(c, K_DIV, s, [&] { return op_gemm<T>(c, t, 2, g, s); }), "gemm div"))) return rc;
+        if ((rc = cuda_check(launch(c, ktag(K_DIV, t), s, [&] { return op_gemm<T>(c, t, 2, g, s); }), "gemm div"))) return rc;
         if (split_rk &&
             (rc = cuda_check(launch(c, K_DIV, s,
                                     [&] {
@@ -730,7 +730,7 @@ int device_setup(fr_ctx *c, int order, const fr_params *prm, const RefOps ops[NT
                 const size_t cnt = opv[w]->size();
                 size_t nnz = 0;
                 for (double v : *opv[w]) nnz += v != 0.0;
-                if (2 * nnz < cnt && !getenv("FR_X64_ALL")) continue;  // PROBE-ONLY
+                if (2 * nnz < cnt) continue;
                 std::vector<uint16_t> img;
                 std::vector<int> rexp;
                 X64Operator &op = D.x64[w];
@@ -1329,10 +1329,28 @@ int fr_profile_read(fr_ctx *c, double *ms, int64_t *count, int64_t *launches) {
         float t = 0.f;
         if ((rc = cuda_check(cudaEventElapsedTime(&t, pe.second.first, pe.second.second), "profile elapsed")))
             return rc;
+        ms[pe.first % K_NCLASS] += t;
+        count[pe.first % K_NCLASS] += 1;
+    }
+    *launches = c->launches;
+    return FR_OK;
+}
+
+int fr_profile_read_types(fr_ctx *c, double *ms, int64_t *count) {
+    if (!c || !ms || !count) return set_err(FR_ERR_ARG, "null argument");
+    for (int k = 0; k < (NT + 1) * K_NCLASS; ++k) {
+        ms[k] = 0.0;
+        count[k] = 0;
+    }
+    int rc;
+    for (auto &pe : c->prof_ev) {
+        if ((rc = cuda_check(cudaEventSynchronize(pe.second.second), "profile sync"))) return rc;
+        float t = 0.f;
+        if ((rc = cuda_check(cudaEventElapsedTime(&t, pe.second.first, pe.second.second), "profile elapsed")))
+            return rc;
         ms[pe.first] += t;
         count[pe.first] += 1;
     }
-    *launches = c->launches;
     return FR_OK;
 }
 

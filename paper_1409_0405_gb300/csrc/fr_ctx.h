@@ -123,6 +123,9 @@ namespace fr {
 namespace api {
 
 enum KClass { K_M0 = 0, K_COMMON_SOL, K_GRAD, K_M0_GRAD, K_FLUX, K_COMMON_FLUX, K_DIV, K_CLOSURE, K_CHECK, K_NCLASS };
+// profile tag of a launch that works on one element type t: its class, and
+// t in the blocks above the untyped tags (fr_profile_read_types)
+inline int ktag(int kclass, int t) { return kclass + K_NCLASS * (t + 1); }
 
 struct RKStage {
     double c_acc, c_stage;

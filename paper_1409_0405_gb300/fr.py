@@ -37,7 +37,7 @@ OP_IDS = {"M0": 0, "D": 1, "M3": 2, "AGRAD": 3, "ADIV": 4, "W": 5, "UPTS": 6,
 EXPORTS = ("fr_create", "fr_destroy", "fr_ndof", "fr_info", "fr_upts",
            "fr_set_state", "fr_get_state", "fr_rhs", "fr_step", "fr_check", "fr_step_ls", "fr_step_rk45",
            "fr_rk45_error", "fr_rk45_get_error", "fr_step_rk45_adaptive", "fr_reduce",
-           "fr_diagnostics", "fr_selftest_wait_timeout", "fr_operator", "fr_profile", "fr_profile_read", "fr_peak_fp64", "fr_gemm_fp64s", "fr_strerror",
+           "fr_diagnostics", "fr_selftest_wait_timeout", "fr_operator", "fr_profile", "fr_profile_read", "fr_profile_read_types", "fr_peak_fp64", "fr_gemm_fp64s", "fr_strerror",
            "fr_last_error", "fr_reduce_noalloc", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_problem", "fr_batch_tune", "fr_batch_step", "fr_batch_check",
            "fr_batch_selftest_wait_timeout", "fr_batch_info",
@@ -114,6 +114,7 @@ def load():
     lib.fr_operator.argtypes = [C.c_int, C.c_int, C.c_int, dp, i64p, i64p]
     lib.fr_profile.argtypes = [vp, C.c_int]
     lib.fr_profile_read.argtypes = [vp, dp, i64p, i64p]
+    lib.fr_profile_read_types.argtypes = [vp, dp, i64p]
     lib.fr_peak_fp64.argtypes = [dp, vp]
     lib.fr_peak_fp64.restype = C.c_int
     lib.fr_gemm_fp64s.argtypes = [C.c_int, C.c_int, dp, C.c_int64, vp, vp, vp]
@@ -175,7 +176,7 @@ def load():
     for name in ("fr_create", "fr_ndof", "fr_info", "fr_upts", "fr_set_state",
                  "fr_get_state", "fr_rhs", "fr_step", "fr_reduce", "fr_diagnostics", "fr_selftest_wait_timeout",
                  "fr_operator",
-                 "fr_profile", "fr_profile_read"):
+                 "fr_profile", "fr_profile_read", "fr_profile_read_types"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -456,6 +457,21 @@ class Context:
         _check(self._lib.fr_profile_read(self._h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
                                          C.byref(tot)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KCLASSES)}, tot.value
+
+    def profile_read_types(self):
+        """{(class, type): (ms, count)}: type "all" for the launches that span
+        every element type, else "tet", "pri" or "hex"; entries with no
+        launch are left out."""
+        nk = len(KCLASSES)
+        ms = np.zeros((len(ETYPES) + 1) * nk)
+        cnt = np.zeros((len(ETYPES) + 1) * nk, dtype=np.int64)
+        _check(self._lib.fr_profile_read_types(self._h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+        out = {}
+        for b, ty in enumerate(("all",) + tuple(ETYPES)):
+            for i, k in enumerate(KCLASSES):
+                if cnt[b * nk + i]:
+                    out[(k, ty)] = (float(ms[b * nk + i]), int(cnt[b * nk + i]))
+        return out
 
     def counts(self):
         """[(elements, solution points per element)] per type, public order."""

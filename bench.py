@@ -204,9 +204,11 @@ def pointwise_bytes_fp64(ctx, kclass, etype=None):
     Navier-Stokes): the transformed flux of one type reads the state (5),
     the physical gradient (15) and S (9), and writes F~ (15) doubles per
     point; the common flux
-    reads both sides' flux-point states (10) and gradients (30), the unit
-    normal and both magnitudes (5), the pair word and both element numbers
-    (12 B), and writes both sides' common flux (10) per interface pair; the
+    reads both sides' flux-point states (10), the gradient of the side whose
+    viscous flux the LDG flux takes (15: with beta = 1/2 the other side's
+    weight is zero), the unit normal and both magnitudes (5), the pair word
+    and both element numbers (12 B), and writes both sides' common flux (10)
+    per interface pair; the
     common solution reads the states (10) and writes both jumps (10) with the
     pair's normal data."""
     i = ctx.info
@@ -214,7 +216,7 @@ def pointwise_bytes_fp64(ctx, kclass, etype=None):
         pts = i["n_" + etype] * i["nu_" + etype]
         return 8.0 * pts * (5 + 15 + 9 + 15)
     if kclass == "common_flux":
-        return i["npairs"] * (8.0 * (10 + 30 + 5 + 10) + 12)
+        return i["npairs"] * (8.0 * (10 + 15 + 5 + 10) + 12)
     if kclass == "common_solution":
         return i["npairs"] * (8.0 * (10 + 5 + 10) + 12)
     return None
@@ -608,12 +610,13 @@ def _time_steps(torch, step, args, sp):
     return e0.elapsed_time(e1) / args.steps
 
 
-def rk45_mode(fr, torch, mesh, u0, dt, args, sp):
+def rk45_mode(fr, torch, mesh, u0, dt, args, sp, precision):
     """RK45[2R+] (the paper's stepper, Sec. 3.4: five stages in two
-    registers plus the embedded error estimate) on the same FP64 workload:
-    GDOF/s counts its 5 RHS per step; the error norm of the last step's
-    embedded estimate (atol = rtol = 1e-6) is reported beside it."""
-    ctx = fr.Context(mesh, ORDER, **flow_params())
+    registers plus the embedded error estimate) on the same FP64 workload,
+    in the headline's FP64 form: GDOF/s counts its 5 RHS per step; the
+    error norm of the last step's embedded estimate (atol = rtol = 1e-6) is
+    reported beside it."""
+    ctx = fr.Context(mesh, ORDER, **flow_params(), precision=precision)
     ctx.set_state(u0, sp)
     ctx.profile(True)
     ms = _time_steps(torch, lambda: ctx.step_rk45(dt, 1, sp), args, sp)
@@ -629,8 +632,8 @@ def rk45_mode(fr, torch, mesh, u0, dt, args, sp):
     return out
 
 
-def partitioned_mode(fr, torch, mesh, u0, dt, ms_single, args, sp):
-    """The FP64 workload split into 2 and 4 partitions on this GPU
+def partitioned_mode(fr, torch, mesh, u0, dt, ms_single, args, sp, precision):
+    """The FP64 workload (in the headline's FP64 form) split into 2 and 4 partitions on this GPU
     (weighted coordinate bisection, tet:pri = 1:2), exchanging cut-face
     flux-point states and gradients through device-local halo buffers every
     RHS: time per RK4 step against the single context, halo sizes, and
@@ -639,7 +642,7 @@ def partitioned_mode(fr, torch, mesh, u0, dt, ms_single, args, sp):
     ref = None
     for n in (2, 4):
         t0 = time.perf_counter()
-        pc = fr.PartContext(mesh, ORDER, n, **flow_params())
+        pc = fr.PartContext(mesh, ORDER, n, **flow_params(), precision=precision)
         setup_s = time.perf_counter() - t0
         pc.set_state(u0, sp)
         ms = _time_steps(torch, lambda: pc.step(dt, 1, sp), args, sp)
@@ -1372,8 +1375,8 @@ def main():
         modes["tf32x3"] = precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, fr.FR_TF32X3, args, sp)
         if ctx64 is not ctx:
             ctx64.close()
-        modes["rk45"] = rk45_mode(fr, torch, mesh, u0, dt, args, sp)
-        modes["partitioned"] = partitioned_mode(fr, torch, mesh, u0, dt, ms_total / args.steps, args, sp)
+        modes["rk45"] = rk45_mode(fr, torch, mesh, u0, dt, args, sp, prec)
+        modes["partitioned"] = partitioned_mode(fr, torch, mesh, u0, dt, ms_total / args.steps, args, sp, prec)
         if args.nx == 75:
             modes["p3"] = p3_modes(fr, torch, mesh, args, sp)
             modes["batched"] = batch_mode(fr, torch, args, sp)

@@ -326,15 +326,28 @@ __device__ __forceinline__ void common_flux_at(const Pairs &P, const Bnd &B, con
         const Prim<T> qa = prim(ua, ph.gamma), qb = prim(ub, ph.gamma);
         rusanov_q(ua, ub, qa, qb, n, ph.gamma, fn);
         if (VIS == 0 ? ph.viscous != 0 : VIS == 2) {
-            T ga[3][V], gb[3][V], fva[V], fvb[V];
-            load_grad(F.GUF[ta], fa, ea, npa, ga);
-            load_grad(F.GUF[tb], fb, eb, npb, gb);
-            vis_flux_n(ua, qa, ga, ph.mu, ph.kq, n, fva);
-            vis_flux_n(ub, qb, gb, ph.mu, ph.kq, n, fvb);
-            const T b = ph.beta * T(ps.sgn);
+            if (ph.beta == T(0.5)) {
+                // beta = 1/2: the weights 1/2 -+ beta sgn of the two sides'
+                // viscous fluxes are 0 and 1, so the common viscous flux is
+                // the flux of one side (b where the switch is +1, else a):
+                // only that side's gradient is read and its flux formed
+                const bool sb = ps.sgn > 0;
+                T g[3][V], fv[V];
+                load_grad(F.GUF[sb ? tb : ta], sb ? fb : fa, sb ? eb : ea, sb ? npb : npa, g);
+                vis_flux_n(sb ? ub : ua, sb ? qb : qa, g, ph.mu, ph.kq, n, fv);
 #pragma unroll
-            for (int v = 0; v < V; ++v)
-                fn[v] = fn[v] - (T(0.5) * (fva[v] + fvb[v]) - b * (fva[v] - fvb[v])) + ph.tau * (ua[v] - ub[v]);
+                for (int v = 0; v < V; ++v) fn[v] = fn[v] - fv[v] + ph.tau * (ua[v] - ub[v]);
+            } else {
+                T ga[3][V], gb[3][V], fva[V], fvb[V];
+                load_grad(F.GUF[ta], fa, ea, npa, ga);
+                load_grad(F.GUF[tb], fb, eb, npb, gb);
+                vis_flux_n(ua, qa, ga, ph.mu, ph.kq, n, fva);
+                vis_flux_n(ub, qb, gb, ph.mu, ph.kq, n, fvb);
+                const T b = ph.beta * T(ps.sgn);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    fn[v] = fn[v] - (T(0.5) * (fva[v] + fvb[v]) - b * (fva[v] - fvb[v])) + ph.tau * (ua[v] - ub[v]);
+            }
         }
         T ma, mb;
         pair_mags<T>(P, k, ma, mb);

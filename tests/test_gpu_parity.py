@@ -66,6 +66,20 @@ def test_rhs_wall_and_farfield_ns(p):
     _check_rhs(sol, ctx, state(sol, "bl"))
 
 
+@pytest.mark.parametrize("precision", ["FR_FP64", "FR_FP32"])
+@pytest.mark.parametrize("beta", [0.3, -0.5])
+def test_rhs_ldg_beta_general(beta, precision):
+    """LDG weights other than beta = 1/2 (where the common viscous flux is
+    one side's flux and the kernels read only that side's gradient): both
+    sides' viscous fluxes are combined with weights 1/2 -+ beta (walls,
+    far field and periodic faces)."""
+    from paper_1409_0405_gb300 import fr
+    m = synth.boundary_layer_box(nx=6, nz=3, n_prism_layers=4, n_tet_layers=3)
+    prm = dict(bl_params(mu=0.01), ldg_beta=beta)
+    sol, ctx = make_pair(m, 3, precision=getattr(fr, precision), **prm)
+    _check_rhs(sol, ctx, state(sol, "bl"), tol=TOL if precision == "FR_FP64" else 1e-4)
+
+
 def test_rhs_impulsive_start_within_fp64_floor():
     """The impulsive start (free stream slipping over the no-slip wall) puts
     an O(1) jump at the wall, gradients ~1/h and wall RHS ~mu/h^2, so every

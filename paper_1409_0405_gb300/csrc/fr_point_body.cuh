@@ -264,6 +264,18 @@ __device__ __forceinline__ void common_solution_at(const Pairs &P, const Bnd &B,
         const T *UA = F.UF[ta] + oa, *UB = F.UF[tb] + ob;
         const T b = ph.beta * T(ps.sgn);
         T *DA = F.DUF[ta] + oa, *DB = F.DUF[tb] + ob;
+        if (ph.beta == T(0.5)) {
+            // beta = 1/2: the common solution is side a's value where the
+            // switch is +1, else side b's, so one jump is exactly zero
+            const bool sa = ps.sgn > 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T ua = UA[v * npa], ub = UB[v * npb];
+                DA[v * npa] = sa ? T(0) : ub - ua;
+                DB[v * npb] = sa ? ua - ub : T(0);
+            }
+            return;
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const T ua = UA[v * npa], ub = UB[v * npb];

@@ -144,6 +144,43 @@ def test_batched_navier_stokes_equals_per_problem(precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_batched_navier_stokes_against_oracle(precision):
+    """A Navier-Stokes batch in the persistent schedule against the FP64
+    oracle: after 3 RK4 steps every problem's state matches the oracle's to
+    1e-12 per quantity in FP64 (its change over the steps to 1e-10), and
+    the change to 1e-4 with FP32 storage."""
+    from paper_1409_0405_gb300 import fr
+    probs = [(synth.vortex_box(n=3, n_prism_layers=1, seed=41), 2), (synth.vortex_box(n=2, n_prism_layers=2, seed=42), 3),
+             (synth.vortex_box(n=3, n_prism_layers=0, seed=43), 1)]
+    prm = dict(viscous=True, mu=0.02, vel_inf=(1.0, 1.0, 0.0), p_inf=1.0, rho_inf=1.0)
+    b = fr.Batch([m for m, _ in probs], [p for _, p in probs], precision=precision, **prm)
+    sols, u0 = [], []
+    for (mesh, p), c in zip(probs, b.problems):
+        sol = Solver(mesh, p, **prm)
+        u = sol.state_from_points(synth.isentropic_vortex(sol.upts_xyz_points()))
+        c.set_state(u)
+        sols.append(sol)
+        u0.append(u)
+    dt, nsteps = 2e-3, 3
+    b.step([dt] * len(probs), nsteps, batched=True)
+    assert b.info()["launches_batched"] == 4
+    b.check()
+    for sol, u, c in zip(sols, u0, b.problems):
+        got = c.get_state()
+        ref = u
+        for _ in range(nsteps):
+            ref = sol.rk4_step(ref, dt)
+        inc = per_quantity_rel_err(sol, ref - u, got - u)
+        if precision == 0:
+            err = per_quantity_rel_err(sol, ref, got)
+            assert np.all(err <= 1e-12), err
+            assert np.all(inc <= 1e-10), inc
+        else:
+            assert np.all(inc <= 1e-4), inc
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_stage_barrier_timeout_is_reported_and_recovered(precision):
     """Failure detection of the persistent stage kernel: one CTA is withheld
     from the grid barriers, every other CTA's bounded wait (~2 s) runs out,

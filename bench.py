@@ -1,7 +1,9 @@
 #!/usr/bin/env python3
 """Throughput of the FR right-hand side on the boundary-layer workload.
 
-Workload: compressible Navier-Stokes, p = 4, FP64, on a box
+Workload: compressible Navier-Stokes, p = 4, FP64 (the operator products
+of the tetrahedra exact-split on the tensor cores, FR_FP64S; FP64 FMA
+throughout and the reduced precisions are reported beside it), on a box
 [0,20] x [0,20] x [0,pi] with 32 stretched prism layers (57,600 prisms) on
 a no-slip wall under Kuhn tets (118,800 tets), Re = 3900, Ma = 0.2,
 uniform inflow plus a 1% seeded velocity perturbation, with a tanh wall

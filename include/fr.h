@@ -176,7 +176,11 @@ int fr_upts(const fr_ctx *ctx, double *xyz);
 
 /* Copy a host state in the public layout into / out of the context's
  * internal solution register.  Host arrays are caller-owned, fr_ndof()
- * doubles.  Synchronous on the given stream (NULL = legacy default). */
+ * doubles.  A page-locked buffer mapped into the device's address space
+ * (cudaHostAlloc / cudaHostRegister with unified addressing) is read or
+ * written in place by the layout kernel over the CPU-GPU link; any other
+ * host buffer is copied through device memory.  The results are the same.
+ * Synchronous on the given stream (NULL = legacy default). */
 int fr_set_state(fr_ctx *ctx, const double *u_host, void *cuda_stream);
 int fr_get_state(fr_ctx *ctx, double *u_host, void *cuda_stream);
 

@@ -1389,21 +1389,37 @@ int fr_upts(const fr_ctx *c, double *xyz) {
     return FR_OK;
 }
 
+// The device address of a page-locked host buffer mapped into the device's
+// address space (cudaHostAlloc / cudaHostRegister memory with unified
+// addressing), or nullptr for any other buffer.  The layout kernels read
+// or write such a buffer directly over the CPU-GPU link, which moves the
+// state faster than one copy engine's bulk copy does; other host memory is
+// copied through a device staging buffer.
+static const double *mapped_host(const double *u) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, u) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? (const double *)a.devicePointer : nullptr;
+}
+
 int fr_set_state(fr_ctx *c, const double *u, void *stream) {
     if (!c || !u) return set_err(FR_ERR_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
+    const double *um = mapped_host(u);
     size_t off = 0;
     for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         const size_t n = (size_t)D.ne * NV * D.nu;
         int rc;
-        // stage through the accumulator register (overwritten by every step)
-        if ((rc = cuda_check(cudaMemcpyAsync(D.Uacc, u + off, n * sizeof(double), cudaMemcpyHostToDevice, s),
-                             "set_state copy")))
+        const double *src = um ? um + off : (const double *)D.Uacc;
+        // otherwise stage through the accumulator register (overwritten by every step)
+        if (!um && (rc = cuda_check(cudaMemcpyAsync(D.Uacc, u + off, n * sizeof(double), cudaMemcpyHostToDevice, s),
+                                    "set_state copy")))
             return rc;
-        if ((rc = cuda_check(launch_pub_to_int<double>(D.nu, D.ne, D.np, (const double *)D.Uacc, D.U, s, nullptr,
-                                                       nullptr),
+        if ((rc = cuda_check(launch_pub_to_int<double>(D.nu, D.ne, D.np, src, D.U, s, nullptr, nullptr),
                              "set_state layout")))
             return rc;
         off += n;
@@ -1416,16 +1432,18 @@ int fr_set_state(fr_ctx *c, const double *u, void *stream) {
 int fr_get_state(fr_ctx *c, double *u, void *stream) {
     if (!c || !u) return set_err(FR_ERR_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
+    double *um = const_cast<double *>(mapped_host(u));
     size_t off = 0;
     for (int t = 0; t < NT; ++t) {
         DevType &D = c->T[t];
         if (!D.present) continue;
         const size_t n = (size_t)D.ne * NV * D.nu;
         int rc;
-        if ((rc = cuda_check(launch_int_to_pub<double>(D.nu, D.ne, D.np, D.U, D.Uacc, s), "get_state layout")))
+        if ((rc = cuda_check(launch_int_to_pub<double>(D.nu, D.ne, D.np, D.U, um ? um + off : D.Uacc, s),
+                             "get_state layout")))
             return rc;
-        if ((rc = cuda_check(cudaMemcpyAsync(u + off, D.Uacc, n * sizeof(double), cudaMemcpyDeviceToHost, s),
-                             "get_state copy")))
+        if (!um && (rc = cuda_check(cudaMemcpyAsync(u + off, D.Uacc, n * sizeof(double), cudaMemcpyDeviceToHost, s),
+                                    "get_state copy")))
             return rc;
         off += n;
     }

@@ -116,3 +116,36 @@ def test_step_reports_a_planted_nonphysical_point():
     with pytest.raises(fr.FRError) as ei:
         ctx.step(1e-4, 1)
     assert ei.value.code == fr.FR_ERR_NONFINITE
+
+
+def test_state_copies_through_mapped_pinned_buffers():
+    """fr_set_state / fr_get_state read and write a mapped page-locked host
+    buffer in place (the layout kernel accesses it over the CPU-GPU link)
+    and copy any other host buffer through device memory: both give the
+    same state bit for bit, on tets + prisms and on a hex mesh, and a step
+    from either is the same."""
+    import torch
+    from paper_1409_0405_gb300 import fr
+    for mesh, p in ((synth.vortex_box(n=3, n_prism_layers=1), 3), (synth.hex_box(n=2, n_hex_cols=1), 2)):
+        ctx = fr.Context(mesh, p, viscous=True, mu=0.01)
+        rng = np.random.default_rng(5)
+        u = np.empty(ctx.ndof)
+        off = 0
+        for ne, nu in ctx.counts():
+            blk = np.tile(np.array([1.0, 0.3, -0.2, 0.1, 3.0])[None, :, None], (ne, 1, nu))
+            u[off:off + blk.size] = (blk * (1.0 + 0.01 * rng.normal(size=blk.shape))).reshape(-1)
+            off += blk.size
+        pin_in = torch.from_numpy(u.copy()).pin_memory()
+        pin_out = torch.zeros(ctx.ndof, dtype=torch.float64).pin_memory()
+        ctx.set_state(pin_in.numpy())
+        got_pinned = ctx.get_state(out=pin_out.numpy()).copy()
+        assert np.array_equal(got_pinned, u)
+        ctx.set_state(u)
+        assert np.array_equal(ctx.get_state(), u)
+        ctx.step(1e-3, 1)
+        after_pageable = ctx.get_state()
+        ctx.set_state(pin_in.numpy())
+        ctx.step(1e-3, 1)
+        after_pinned = ctx.get_state(out=pin_out.numpy()).copy()
+        assert np.array_equal(after_pinned, after_pageable)
+        ctx.close()

@@ -266,13 +266,17 @@ __device__ __forceinline__ void common_solution_at(const Pairs &P, const Bnd &B,
         T *DA = F.DUF[ta] + oa, *DB = F.DUF[tb] + ob;
         if (ph.beta == T(0.5)) {
             // beta = 1/2: the common solution is side a's value where the
-            // switch is +1, else side b's, so one jump is exactly zero
+            // switch is +1, else side b's, so that side's jump is exactly
+            // zero.  The switch is fixed by the geometry and every interior
+            // flux point belongs to one pair, so that slot keeps the zero it
+            // was allocated with: only the other side's jump is written
             const bool sa = ps.sgn > 0;
+            T *D = sa ? DB : DA;
+            const int64_t npd = sa ? npb : npa;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const T ua = UA[v * npa], ub = UB[v * npb];
-                DA[v * npa] = sa ? T(0) : ub - ua;
-                DB[v * npb] = sa ? ua - ub : T(0);
+                D[v * npd] = sa ? ua - ub : ub - ua;
             }
             return;
         }

@@ -92,7 +92,8 @@ def test_tc_rk_step_matches_fp32_mode():
 def test_tc_full_size_boundary_layer(mode):
     """The benchmark workload (42.4 M DOF, p=4 NS with walls and far field):
     the tensor-core RHS against the FR_FP64 RHS of the library (which
-    matches the FP64 oracle to 1e-12)."""
+    matches the FP64 oracle to 1e-12 at this size), per conserved quantity
+    (mass, momentum vector, energy: max |d| / max |ref| each)."""
     fr = _fr()
     mesh = synth.boundary_layer_box()
     prm = _cases.bl_params()
@@ -110,9 +111,18 @@ def test_tc_full_size_boundary_layer(mode):
     c64.rhs(u.data_ptr(), r64.data_ptr())
     c16.rhs(u.data_ptr(), r16.data_ptr())
     torch.cuda.synchronize()
-    d = (r16 - r64).abs().max().item() / r64.abs().max().item()
-    print("full-size", mode, "rel err", d)
-    assert d < TOLS[mode]
+    a, b = r64.cpu().numpy(), r16.cpu().numpy()
+    num, den, off = np.zeros(3), np.zeros(3), 0
+    for ne, nu in counts:
+        ra = a[off:off + ne * 5 * nu].reshape(ne, 5, nu)
+        rb = b[off:off + ne * 5 * nu].reshape(ne, 5, nu)
+        for k, sl in enumerate((slice(0, 1), slice(1, 4), slice(4, 5))):
+            num[k] = max(num[k], float(np.max(np.linalg.norm(rb[:, sl] - ra[:, sl], axis=1))))
+            den[k] = max(den[k], float(np.max(np.linalg.norm(ra[:, sl], axis=1))))
+        off += ne * 5 * nu
+    d = num / den
+    print("full-size", mode, "rel err per quantity", d)
+    assert np.all(d < TOLS[mode]), d
     c16.reduce(check=False)
 
 

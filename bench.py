@@ -852,7 +852,7 @@ def learned_mode(fr, torch, args, sp):
     time.  Reported: the RHS error with and without each network on a
     later, held-out state; the kinetic-energy dissipation rate of p=2 with
     and without the networks against p=4, over the training window and over
-    the window after it; the p=4 check's verdict (the better network is
+    the window after it; the p=4 check's decision (the better network is
     kept only if it lowers the dissipation error after the training
     window); and the RHS throughput of each."""
     import synth
@@ -954,7 +954,7 @@ def learned_mode(fr, torch, args, sp):
     # window, kept only if it beats plain p=2 there
     best = cl if key(rel(e2c, post)) <= key(rel(e2t, post)) else cl_t
     best_post = min(key(rel(e2c, post)), key(rel(e2t, post)))
-    verdict = best_post < key(rel(e2, post))
+    keep_net = best_post < key(rel(e2, post))
     best.attach()
 
     # RHS throughput: p=2 + network, p=2, p=4 (FP64)
@@ -1007,7 +1007,7 @@ def learned_mode(fr, torch, args, sp):
             "held_out_rhs_rel_rms_err": {name[k]: {"with_network": v[0], "plain_p2": v[1]}
                                          for k, v in prior_t.items()},
             "training_s": train_t_s},
-        "p4_check": {"network_kept": bool(verdict),
+        "p4_check": {"network_kept": bool(keep_net),
                      "network": "projected target" if best is cl else "trajectory target",
                      "rule": "of the two networks (projected and trajectory-consistent targets) the one with the "
                              "lower dissipation error after the training window, kept only if it beats plain p=2 "

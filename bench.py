@@ -474,18 +474,19 @@ def precision_mode(fr, torch, mesh, counts, u0, dt, ctx64, precision, args, sp):
 
 def state_error_study(fr, torch, nsteps, sp):
     """The boundary-layer workload at p = 3 and p = 4: nsteps RK4 steps in
-    FP64 and in each reduced-precision mode from the same initial state;
-    the final state, its change over the run and the flow diagnostics
-    (kinetic-energy rate, wall force) of the final state against FP64 (the
-    FP64 path matches the FP64 oracle to 1e-12 per RHS and step; the oracle
-    itself would need hours per run at this size)."""
+    FP64 (FMA throughout), in FP64 with the exact-split tensor-core
+    products and in each reduced-precision mode from the same initial
+    state; the final state, its change over the run and the flow
+    diagnostics (kinetic-energy rate, wall force) of the final state
+    against FP64 (the FP64 path matches the FP64 oracle to 1e-12 per RHS
+    and step; the oracle itself would need hours per run at this size)."""
     mesh = synth_mod().boundary_layer_box()
     res = {}
     for order in (3, 4):
         dt = time_step_size(mesh, order)
         runs = {}
-        for name, prec in (("fp64", fr.FR_FP64), ("fp32", fr.FR_FP32), ("bf16x3", fr.FR_BF16X3),
-                           ("tf32x3", fr.FR_TF32X3)):
+        for name, prec in (("fp64", fr.FR_FP64), ("fp64s", fr.FR_FP64S), ("fp32", fr.FR_FP32),
+                           ("bf16x3", fr.FR_BF16X3), ("tf32x3", fr.FR_TF32X3)):
             ctx = fr.Context(mesh, order, **flow_params(), precision=prec)
             counts = ctx.counts()
             u0 = points_to_public(synth_mod().perturbed_freestream(ctx.upts_points(), seed=2,
@@ -502,7 +503,7 @@ def state_error_study(fr, torch, nsteps, sp):
         ent = {"ndof": int(s64.size), "dt": dt, "steps": nsteps, "fp64_wall_s": runs["fp64"][2],
                "fp64_ke_rate": d64[0], "fp64_wall_force_inviscid": d64[1].tolist(),
                "fp64_wall_force_viscous": d64[2].tolist()}
-        for name in ("fp32", "bf16x3", "tf32x3"):
+        for name in ("fp64s", "fp32", "bf16x3", "tf32x3"):
             st, d, wall, finite = runs[name]
             ent[name] = {"state_rel_err": per_quantity_rel_err(s64, st, counts),
                          "change_rel_err": per_quantity_rel_err(s64 - u0, st - u0, counts),

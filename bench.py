@@ -624,12 +624,16 @@ def rk45_mode(fr, torch, mesh, u0, dt, args, sp, precision):
     ctx.profile(True)
     ms = _time_steps(torch, lambda: ctx.step_rk45(dt, 1, sp), args, sp)
     classes, launches = ctx.profile_read()
+    typed = ctx.profile_read_types()
     ctx.profile(False)
+    nprof = args.steps + max(args.warmup, 0)
+    roof = step_roofline(fr, torch, ctx, precision, classes, typed, args, sp, torch.cuda.current_device(),
+                         nrhs=5 * nprof)
     err = ctx.rk45_error(1e-6, 1e-6, sp)
     ctx.check(sp)
     out = {"value": ctx.ndof * 5.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "rhs_per_step": 5,
            "kernel_ms_per_step": {k: v[0] / (args.steps + max(args.warmup, 0)) for k, v in classes.items()},
-           "error_norm_last_step": err, "error_norm_tolerances": [1e-6, 1e-6],
+           "error_norm_last_step": err, "error_norm_tolerances": [1e-6, 1e-6], "roofline": roof,
            "workload": WORKLOAD.replace("RK4", "RK45[2R+]")}
     ctx.close()
     return out
@@ -679,9 +683,16 @@ def p3_modes(fr, torch, mesh, args, sp):
             u0 = points_to_public(synth_mod().perturbed_freestream(ctx.upts_points(), seed=2,
                                                                    wall_delta=WALL_DELTA), ctx.counts())
         ctx.set_state(u0, sp)
+        ctx.profile(True)
         ms = _time_steps(torch, lambda: ctx.step(dt, 1, sp), args, sp)
+        classes, _ = ctx.profile_read()
+        typed = ctx.profile_read_types()
+        ctx.profile(False)
+        nprof = args.steps + max(args.warmup, 0)
         out[name] = {"value": ctx.ndof * 4.0 / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
-                     "ndof": ctx.ndof, "state_finite": bool(ctx.reduce(stream=sp, check=False)[6] == 0.0)}
+                     "ndof": ctx.ndof, "state_finite": bool(ctx.reduce(stream=sp, check=False)[6] == 0.0),
+                     "roofline": step_roofline(fr, torch, ctx, prec, classes, typed, args, sp,
+                                               torch.cuda.current_device(), nrhs=4 * nprof)}
         ctx.close()
     return out
 
@@ -1027,10 +1038,15 @@ X64_PROFILE = "k_gemm_x64_boundary_layer_p4_nx40.md"
 X64_SOURCES = ("fr_gemm_x64.cu", "fr_gemm_body.cuh")
 
 
+_FP64_PEAKS = {}
+
+
 def fp64_peaks(fr, torch, local, sp):
     """FP64 denominators: the FMA peak derived from the SM count and the
     maximum SM clock, the library's FMA probe and cuBLAS DGEMM (the paper's
-    reference-peak method), in TFLOP/s."""
+    reference-peak method), in TFLOP/s; measured once per process."""
+    if local in _FP64_PEAKS:
+        return _FP64_PEAKS[local]
     peaks = measured_peaks()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     clk_ghz = float(peaks.get("sm_max_mhz", 2070.0)) / 1e3
@@ -1044,6 +1060,7 @@ def fp64_peaks(fr, torch, local, sp):
         out["dgemm"] = dgemm_reference_tflops(torch)
     except Exception:
         out["dgemm"] = None
+    _FP64_PEAKS[local] = out
     return out
 
 
@@ -1062,7 +1079,7 @@ def alu_roofline(flops, ms, n, kernel, p64, traffic=None, traffic_src="n/a"):
             "frac_of_reference_peak": (ach / p64["dgemm"]) if p64["dgemm"] else None}
 
 
-def step_roofline(fr, torch, ctx, prec, classes, typed, args, sp, local):
+def step_roofline(fr, torch, ctx, prec, classes, typed, args, sp, local, nrhs=None):
     """Roofline of the dominant kernel of the timed RK4 steps.
 
     FR_FP64: the dominant operator class (FP64 pipe; flops = 2 x non-zero
@@ -1073,10 +1090,10 @@ def step_roofline(fr, torch, ctx, prec, classes, typed, args, sp, local):
     point-wise launch against HBM (algorithmic bytes).  FP32-storage modes:
     the dominant operator class against HBM."""
     peaks = measured_peaks()
-    nrhs = 4 * args.steps
+    nrhs = 4 * args.steps if nrhs is None else nrhs  # RHS evaluations the profile covers
     hbm = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
-    full = args.nx == 75
+    full = args.nx == 75 and ctx.order == ORDER  # the committed traffic captures are of this workload
     if prec == fr.FR_FP64S:
         # launches grouped by kernel: the FMA operator kernel (types whose
         # operators stay on the FP64 pipe), the exact-split kernel (its
@@ -1097,7 +1114,7 @@ def step_roofline(fr, torch, ctx, prec, classes, typed, args, sp, local):
 
         def traffic_of(profile=None, names=None):
             if not full:
-                return None, "reduced case"
+                return None, "no capture of this workload"
             tot = 0.0
             for c, t in keys:
                 kw = {} if profile is None else {"profile": profile, "names": names}
@@ -1151,7 +1168,7 @@ def step_roofline(fr, torch, ctx, prec, classes, typed, args, sp, local):
                 "kernel": ("k_gemm_tc" if prec in (fr.FR_BF16X3, fr.FR_TF32X3) else "k_gemm") + f" ({dom})",
                 "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1), "peak_source": hbm_src}
     if dom in GEMM_CLASSES:
-        traffic, tsrc = profiled_traffic(dom) if full else (None, "reduced case")
+        traffic, tsrc = profiled_traffic(dom) if full else (None, "no capture of this workload")
         return alu_roofline(gemm_flops(ctx, dom) * nrhs, dom_ms, dom_n, f"k_gemm ({dom})",
                             fp64_peaks(fr, torch, local, sp), traffic, tsrc)
     return {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,

@@ -678,3 +678,26 @@ def test_rk45_adaptive_reaches_the_end_time_within_tolerance(monkeypatch):
         errs.append(float(np.max(np.abs(u - exact))))
         assert rej >= 1 and acc >= 3
     assert errs[0] < 1e-4 and errs[1] < errs[0] / 10, errs
+
+
+def test_ldg_beta_half_takes_one_side():
+    """With beta = 1/2 the LDG weights 1/2 +- beta are 1 and 0: the common
+    solution is the left side's value (side a where the switch is +1) and
+    the common viscous flux the right side's, up to rounding.  The face
+    kernels of the GPU path rely on this identity to read and form one
+    side only; a sign slip of beta or of the switch would swap the sides."""
+    rng = np.random.default_rng(3)
+    n_pts = 64
+    ua, ub = rng.normal(size=(n_pts, 5)), rng.normal(size=(n_pts, 5))
+    sign = np.where(rng.random(n_pts) > 0.5, 1.0, -1.0)
+    C = physics.ldg_common_solution(ua, ub, sign, 0.5)
+    np.testing.assert_allclose(C, np.where(sign[:, None] > 0, ua, ub), rtol=0, atol=1e-15)
+    fva, fvb = rng.normal(size=(n_pts, 5, 3)), rng.normal(size=(n_pts, 5, 3))
+    nrm = rng.normal(size=(n_pts, 3))
+    F = physics.ldg_viscous_normal(fva, fvb, nrm, sign, 0.5)
+    fa = np.einsum("pvm,pm->pv", fva, nrm)
+    fb = np.einsum("pvm,pm->pv", fvb, nrm)
+    np.testing.assert_allclose(F, np.where(sign[:, None] > 0, fb, fa), rtol=0, atol=1e-14)
+    # any other beta mixes both sides
+    F3 = physics.ldg_viscous_normal(fva, fvb, nrm, sign, 0.3)
+    assert np.all(np.abs(F3 - np.where(sign[:, None] > 0, fb, fa)) > 0)

@@ -115,7 +115,10 @@ typedef struct {
     double gamma;     /* ratio of specific heats */
     double mu;        /* constant dynamic viscosity (Sec. 3.4) */
     double prandtl;   /* Prandtl number */
-    double ldg_beta;  /* LDG common-solution bias, switch along a fixed direction */
+    double ldg_beta;  /* LDG common-solution bias, switch along a fixed direction;
+                         with 0.5 the common solution is one side's value and
+                         the common viscous flux the other side's, and the
+                         face kernels read and form only those sides */
     double ldg_tau;   /* LDG penalty on the normal flux */
     int viscous;      /* 0: Euler, 1: Navier-Stokes */
     int precision;    /* FR_FP64, or FR_FP32: operator applications and point-wise
